@@ -1,0 +1,168 @@
+"""CPU oracle for C := alpha*op(A)*op(B) + beta*C (paper Section 1.2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline legs of ``bench.py`` may import this package.  The product path
+(``paper_1609_00076_gb300``) never imports it, and this package never imports
+the product: the two share no code.
+
+Contents
+--------
+* ``dgemm_rows`` / ``dgemm``: the plain definition, element by element, with
+  compensated (Dot2, Ogita-Rump-Oishi 2005) accumulation, in C (oracle.c).
+* ``abs_bound_rows``: G = |alpha||op(A)||op(B)| + |beta||C0|, the magnitude in the
+  componentwise bound |C - C_exact| <= 2 k 2^-53 G.
+* ``ozaki_dgemm_rows``: a plain CPU model of the split emulation (ozaki_model.c),
+  same digits, same level order, same segment order as the GPU emulation but
+  written independently (floating-point digit recursion instead of bit fields).
+
+Matrices are passed as 1-D float64 numpy arrays in column-major order with an
+explicit leading dimension, exactly as in the BLAS statement (Section 2.1:
+element (i, j) lives at index j*ld + i).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["oracle.c", "ozaki_model.c"]
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no value-changing FP optimisation)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIB_PATH):
+        lib_mtime = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= lib_mtime for s in srcs):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-pthread", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    d, i64, c, i = ctypes.c_double, ctypes.c_int64, ctypes.c_char, ctypes.c_int
+    vp = ctypes.c_void_p
+    lib.oracle_dgemm_rows.argtypes = [c, c, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp,
+                                      i64, vp, i64, i]
+    lib.oracle_dgemm_rows.restype = i
+    lib.oracle_abs_bound_rows.argtypes = lib.oracle_dgemm_rows.argtypes
+    lib.oracle_abs_bound_rows.restype = i
+    lib.oracle_dgemm.argtypes = [c, c, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, i]
+    lib.oracle_dgemm.restype = i
+    lib.oracle_ozaki_dgemm_rows.argtypes = [c, c, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64,
+                                            i, i, i64, vp, i64, vp, i64, i]
+    lib.oracle_ozaki_dgemm_rows.restype = i
+    lib.oracle_ozaki_exponent.argtypes = [d]
+    lib.oracle_ozaki_exponent.restype = i
+    lib.oracle_ozaki_split.argtypes = [d, i, i, i, vp]
+    lib.oracle_ozaki_split.restype = None
+    lib.oracle_num_threads.argtypes = []
+    lib.oracle_num_threads.restype = i
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data
+
+
+def _as_f64(a):
+    if a is None:
+        return None
+    a = np.asarray(a)
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("oracle matrices are contiguous float64 1-D buffers")
+    return a
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def _rows_arg(rows, m):
+    if rows is None:
+        return None, m
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    return r, int(r.size)
+
+
+def dgemm_rows(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc, rows=None,
+               nthreads=0):
+    """Rows ``rows`` (default: all) of alpha*op(A)*op(B) + beta*C0 as an
+    (nrows x n) column-major buffer (leading dimension nrows).  C0 is not modified."""
+    lib = _load()
+    r, nr = _rows_arg(rows, m)
+    out = np.empty(max(1, nr) * max(1, n), dtype=np.float64)
+    rc = lib.oracle_dgemm_rows(transa.encode(), transb.encode(), m, n, k, float(alpha),
+                               _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, float(beta),
+                               _ptr(_as_f64(C0)), ldc, _ptr(r), nr, out.ctypes.data, max(1, nr),
+                               int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_dgemm_rows: invalid argument {rc}")
+    return out[: nr * n]
+
+
+def dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, nthreads=0):
+    """In place, the exact dgemm argument list: C is overwritten.  Returns the
+    BLAS status (0, or the index of the first invalid argument)."""
+    lib = _load()
+    return lib.oracle_dgemm(transa.encode(), transb.encode(), m, n, k, float(alpha),
+                            _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, float(beta),
+                            _ptr(_as_f64(C)), ldc, int(nthreads))
+
+
+def abs_bound_rows(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc, rows=None,
+                   nthreads=0):
+    """Rows of |alpha||op(A)||op(B)| + |beta||C0| (same layout as dgemm_rows)."""
+    lib = _load()
+    r, nr = _rows_arg(rows, m)
+    out = np.empty(max(1, nr) * max(1, n), dtype=np.float64)
+    rc = lib.oracle_abs_bound_rows(transa.encode(), transb.encode(), m, n, k, float(alpha),
+                                   _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, float(beta),
+                                   _ptr(_as_f64(C0)), ldc, _ptr(r), nr, out.ctypes.data,
+                                   max(1, nr), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_abs_bound_rows: invalid argument {rc}")
+    return out[: nr * n]
+
+
+def ozaki_dgemm_rows(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc, slices,
+                     bits=7, kseg=8192, rows=None, nthreads=0):
+    """Rows of the split emulation (model of the GPU path) with ``slices`` digits of
+    ``bits`` bits per operand and level sums over segments of ``kseg`` indices."""
+    lib = _load()
+    r, nr = _rows_arg(rows, m)
+    out = np.empty(max(1, nr) * max(1, n), dtype=np.float64)
+    rc = lib.oracle_ozaki_dgemm_rows(transa.encode(), transb.encode(), m, n, k, float(alpha),
+                                     _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, float(beta),
+                                     _ptr(_as_f64(C0)), ldc, int(slices), int(bits), int(kseg),
+                                     _ptr(r), nr, out.ctypes.data, max(1, nr), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_ozaki_dgemm_rows: status {rc}")
+    return out[: nr * n]
+
+
+def ozaki_exponent(x: float) -> int:
+    return _load().oracle_ozaki_exponent(float(x))
+
+
+def ozaki_split(x: float, sigma: int, slices: int, bits: int = 7) -> list[int]:
+    out = np.zeros(16, dtype=np.int32)
+    _load().oracle_ozaki_split(float(x), int(sigma), int(slices), int(bits), out.ctypes.data)
+    return [int(v) for v in out[:slices]]
