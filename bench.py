@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 DGEMM library: C := alpha*op(A)*op(B) + beta*C.
+
+Metric: DGEMM TFLOP/s (useful flops 2mnk per call) against the FP64 peak, for
+the native FP64-MMA path, on the large square workload m = n = k = 8192
+(FP64 operands uniform on [-1, 1), N,N, alpha = 1, beta = 0; every input is
+larger than L2, so no flush is needed between timed calls).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one DGEMM call on device-resident inputs.  Timing: W untimed
+warm-up steps, then K steps between CUDA events on the launching stream, with a
+barrier and a device synchronisation on both sides; the max over ranks is taken.
+Multi-GPU runs are independent replicas (each rank its own problem, no
+collective on the data path): value = total useful flops of all ranks / max time.
+
+Rank 0 prints one JSON line.  `--impl reference` times the CPU oracle instead
+(a bounded sample of rows of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DGEMM TFLOP/s vs FP64 peak: native vs emulated at FP64 accuracy; p99 latency"
+M = N = K = 8192
+
+
+def workload_name():
+    return (f"dgemm m=n=k={M}, transa=transb=N, lda=ldb=ldc={M}, alpha=1, beta=0, "
+            f"A,B uniform[-1,1) FP64")
+
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to FP64
+NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
+# dram bytes (read + write) per launch of the dominant kernel from one ncu capture of this
+# workload; None until captured for the current kernel
+TRAFFIC_PER_LAUNCH = {"native": None}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------
+# CPU oracle legs (the reference arm and the cpu_baseline)
+# ------------------------------------------------------------------------------
+_HOST_INPUTS: dict = {}
+
+
+def host_inputs(seed: int):
+    """The workload's A and B as column-major host buffers (cached per seed)."""
+    from paper_1609_00076_gb300 import synth
+    if seed not in _HOST_INPUTS:
+        _HOST_INPUTS[seed] = (synth.matrix("uniform", M, K, M, seed, pad=0.0),
+                              synth.matrix("uniform", K, N, K, seed + 1, pad=0.0))
+    return _HOST_INPUTS[seed]
+
+
+def oracle_sample(target_s: float, seed: int = 2000):
+    """Times the CPU oracle on rows of the workload; returns (TFLOP/s, seconds, rows, threads)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    A, B = host_inputs(seed)
+    threads = oracle.num_threads()
+    # calibrate on a few rows, then size the sample to about target_s seconds
+    rows = list(range(0, M, M // 4))[:max(1, min(4, threads // 4 or 1))]
+    t0 = time.perf_counter()
+    oracle.dgemm_rows("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, None, M, rows=rows, nthreads=threads)
+    dt = time.perf_counter() - t0
+    per_row = dt / len(rows)
+    nrows = int(max(1, min(M, target_s / max(per_row, 1e-6))))
+    rows = [int(r) for r in (np.arange(nrows) * (M // max(nrows, 1))) % M]
+    t0 = time.perf_counter()
+    oracle.dgemm_rows("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, None, M, rows=rows, nthreads=threads)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * len(rows) * N * K
+    return flops / dt / 1e12, dt, len(rows), threads
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    vals = []
+    total_t = 0.0
+    info = None
+    for i in range(warm + steps):
+        v, dt, nrows, threads = oracle_sample(target_s=max(2.0, 60.0 / (warm + steps)), seed=2000 + i % 2)
+        info = (nrows, threads)
+        if i >= warm:
+            vals.append(v)
+            total_t += dt
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * total_t / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "path": "cpu oracle (Dot2 triple loop)", "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": info[1], "kind": "oracle",
+                         "sample": f"{info[0]} rows x {N} columns of the {M}^3 product per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm, synth
+    gbdgemm.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    seed = 2000 + rank
+    A_h, B_h = host_inputs(seed)
+    A = torch.from_numpy(A_h).to(dev)
+    B = torch.from_numpy(B_h).to(dev)
+    C = torch.zeros(M * N, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    flops = 2.0 * M * N * K
+
+    def step(s):
+        rc = gbdgemm.gbd_dgemm("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, stream=s)
+        if rc != 0:
+            raise gbdgemm.GbdError(rc, gbdgemm.gbd_last_error())
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+    torch.cuda.synchronize()
+    gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+
+    sampler = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step(stream)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = sampler.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+    total_ms = max_over_ranks(pg, total_ms, dev)
+    value = world * flops * args.steps / (total_ms / 1000.0) / 1e12
+
+    # --- end to end through the C ABI with host buffers (pinned), copies inside the region ---
+    A_p = torch.from_numpy(A_h).pin_memory()
+    B_p = torch.from_numpy(B_h).pin_memory()
+    C_p = torch.empty(M * N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            A.copy_(A_p, non_blocking=True)
+            B.copy_(B_p, non_blocking=True)
+            step(stream)
+            C_p.copy_(C, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
+    e2e_val = world * flops * e2e_steps / (e2e_ms / 1000.0) / 1e12
+
+    if rank != 0:
+        return 0
+    peaks, src = load_peaks()
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64 / NOMINAL_BF16
+    kernel_ms = statistics.mean(per)
+    achieved = flops / (kernel_ms / 1000.0) / 1e12
+    cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=12.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "path": "native (mma.sync f64)", "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": TRAFFIC_PER_LAUNCH["native"],
+                     "peak_source": f"{src} bf16 {peaks['bf16_tflops']} x nominal fp64/bf16 "
+                                    f"{NOMINAL_FP64}/{NOMINAL_BF16}"},
+        "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": cpu_threads, "kind": "oracle",
+                         "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
+        "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
+                "d2h_bytes_per_step": M * N * 8},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="m = n = k of the square workload (8192 is the benchmark; smaller sizes are for profiling)")
+    args = ap.parse_args()
+    global M, N, K
+    M = N = K = args.size
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank, pg)
+        return run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

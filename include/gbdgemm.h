@@ -1,0 +1,92 @@
+/*
+ * gbdgemm.h -- C ABI of the GB300 (sm_103a) double-precision GEMM library.
+ *
+ * The operation is the BLAS dgemm of the BLISlab paper (Huang and van de Geijn,
+ * FLAME Working Note #80, Section 1.2):
+ *
+ *     C := alpha * op(A) * op(B) + beta * C,     op(X) = X  or  X^T,
+ *
+ * with C m x n, op(A) m x k and op(B) k x n.  All matrices are column-major with
+ * a leading dimension (Section 2.1): element (i, j) of X is X[i + j*ldx], and the
+ * matrix may sit inside a larger array (an interior pointer with ldx larger than
+ * its row count is legal).  A is stored m x k when transa is 'N' and k x m when
+ * it is 'T'; B is stored k x n for 'N' and n x k for 'T'.
+ *
+ * Conventions shared by every entry point:
+ *  - All matrix pointers are DEVICE pointers owned by the caller; the library
+ *    never allocates, frees or retains them.  A and B must not overlap C.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream) unless stated otherwise.
+ *  - transa/transb accept 'N','n','T','t','C','c'; 'C' means 'T' for real data.
+ *  - Quick returns follow the reference BLAS: nothing is done when m == 0 or
+ *    n == 0, or when (alpha == 0 or k == 0) and beta == 1.  When alpha == 0 or
+ *    k == 0, C := beta*C and A, B are not read.  When beta == 0, C is not read
+ *    on input (NaN/Inf already in C do not propagate).
+ *  - Return value: 0 on success; a positive value is the 1-based position of
+ *    the first invalid argument in the dgemm argument list (reference-BLAS
+ *    xerbla numbering: 1 transa, 2 transb, 3 m, 4 n, 5 k, 8 lda, 10 ldb,
+ *    13 ldc); a negative value is one of the GBD_ERR_* codes below.  No
+ *    exception ever crosses this boundary.
+ *  - Results are deterministic: the same call on the same inputs gives the
+ *    same bits, independent of other work on the device.
+ */
+#ifndef GBDGEMM_H
+#define GBDGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBD_API __attribute__((visibility("default")))
+#else
+#define GBD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBD_OK 0
+#define GBD_ERR_CUDA (-1)        /* a CUDA runtime/driver call failed (see gbd_last_error) */
+#define GBD_ERR_WORKSPACE (-2)   /* workspace missing, too small or misaligned */
+#define GBD_ERR_TIMEOUT (-3)     /* a bounded device-side wait gave up (watchdog) */
+#define GBD_ERR_DEVICE (-4)      /* the current device is not an sm_103 GPU */
+#define GBD_ERR_LIMIT (-5)       /* a size is outside what the kernel supports */
+#define GBD_ERR_ARG (-6)         /* an argument outside the dgemm list is invalid */
+
+/* Library version, major*10000 + minor*100 + patch. */
+GBD_API int gbd_version(void);
+
+/* Human-readable text for the last error raised by the calling thread (never NULL). */
+GBD_API const char* gbd_last_error(void);
+
+/*
+ * Native double-precision GEMM on the FP64 tensor-core MMA (mma.sync f64).
+ *
+ * Computes C := alpha*op(A)*op(B) + beta*C (Section 1.2) with FP64 products and
+ * FP64 accumulation in a fixed order; the epilogue forms fma(alpha, acc, beta*c)
+ * (alpha*acc when beta == 0).  Tiles are staged in shared memory by the Tensor
+ * Memory Accelerator when A and B start on 16-byte boundaries and lda, ldb are
+ * even, and by per-element asynchronous copies otherwise (odd leading
+ * dimensions and interior pointers such as the paper's lda = 3 example).
+ * Arguments are those of the BLAS call; A, B, C are device pointers; lda >=
+ * max(1, rows of A as stored), ldb likewise, ldc >= max(1, m).
+ * Returns 0, a BLAS argument index, or GBD_ERR_*.  Asynchronous on stream.
+ */
+GBD_API int gbd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                      double* C, int64_t ldc, void* stream);
+
+/*
+ * Reads and clears the device error word of the current device that the
+ * kernels set when a bounded wait gives up.  Synchronises `stream` first.
+ * Returns 0 when no wait gave up since the last call, GBD_ERR_TIMEOUT when one
+ * did, or GBD_ERR_CUDA.
+ */
+GBD_API int gbd_check_device_error(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBDGEMM_H */

@@ -1,0 +1,178 @@
+// runtime.cu -- host-side plumbing of the library: error text, argument checks,
+// device checks, the device error word and tensor-map encoding.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace gbd {
+
+namespace {
+thread_local char g_msg[512] = "no error";
+
+// Error word set by bounded device-side waits (one per device context; never
+// allocated, so reading it needs no set-up beyond the symbol address).
+__device__ unsigned int g_device_error = 0;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned int* g_err_ptr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
+int g_dev_ok[kMaxDevices] = {};  // 0 unknown, 1 ok, -1 not sm_103
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
+__global__ void k_scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc) {
+  const int64_t total = m * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % m, j = idx / m;
+    double* c = C + j * ldc + i;
+    *c = (beta == 0.0) ? 0.0 : beta * *c;  // beta == 0: C is not read
+  }
+}
+}  // namespace
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_error(GBD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int trans_code(char t) {
+  if (t == 'N' || t == 'n') return 0;
+  if (t == 'T' || t == 't' || t == 'C' || t == 'c') return 1;
+  return -1;
+}
+
+int check_dgemm_args(char transa, char transb, int64_t m, int64_t n, int64_t k, int64_t lda,
+                     int64_t ldb, int64_t ldc) {
+  const int ta = trans_code(transa), tb = trans_code(transb);
+  auto mx = [](int64_t a) { return a > 1 ? a : (int64_t)1; };
+  int bad = 0;
+  if (ta < 0) bad = 1;
+  else if (tb < 0) bad = 2;
+  else if (m < 0) bad = 3;
+  else if (n < 0) bad = 4;
+  else if (k < 0) bad = 5;
+  else if (lda < mx(ta ? k : m)) bad = 8;
+  else if (ldb < mx(tb ? n : k)) bad = 10;
+  else if (ldc < mx(m)) bad = 13;
+  if (bad) set_error(bad, "dgemm: parameter %d had an illegal value", bad);
+  return bad;
+}
+
+int current_device(int* device, int* num_sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return set_error(GBD_ERR_DEVICE, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_dev_ok[dev] == 0) {
+    int major = 0, minor = 0, sms = 0;
+    if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return cuda_fail(e, "cudaDeviceGetAttribute");
+    g_dev_ok[dev] = (major == 10 && minor == 3) ? 1 : -1;
+    g_sm_count[dev] = sms;
+    if (g_dev_ok[dev] < 0)
+      return set_error(GBD_ERR_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a",
+                       dev, major, minor);
+  }
+  if (g_dev_ok[dev] < 0) return set_error(GBD_ERR_DEVICE, "device %d is not sm_103", dev);
+  if (device) *device = dev;
+  if (num_sms) *num_sms = g_sm_count[dev];
+  return GBD_OK;
+}
+
+unsigned int* device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_err_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    g_err_ptr[dev] = static_cast<unsigned int*>(p);
+  }
+  return g_err_ptr[dev];
+}
+
+int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
+                   uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer,
+                   CUtensorMapSwizzle swizzle) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                       cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return set_error(GBD_ERR_CUDA, "cuTensorMapEncodeTiled entry point not found");
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+  }
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = g_encode(out, dtype, 2, const_cast<void*>(base), dims, strides, box, estride,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_error(GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d): dims %llu x %llu pitch %llu box %u x %u",
+                     (int)r, (unsigned long long)inner, (unsigned long long)outer,
+                     (unsigned long long)pitch_bytes, box_inner, box_outer);
+  return GBD_OK;
+}
+
+int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t stream) {
+  if (m == 0 || n == 0 || beta == 1.0) return GBD_OK;
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  const int64_t total = m * n;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  k_scale_c<<<(unsigned)blocks, 256, 0, stream>>>(m, n, beta, C, ldc);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "scale kernel launch");
+}
+
+}  // namespace gbd
+
+extern "C" {
+
+int gbd_version(void) { return 100; }  // 0.1.0
+
+const char* gbd_last_error(void) { return gbd::g_msg; }
+
+int gbd_check_device_error(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return gbd::cuda_fail(e, "cudaStreamSynchronize");
+  unsigned int* p = gbd::device_error_word();
+  if (!p) return gbd::set_error(GBD_ERR_CUDA, "device error word not reachable");
+  unsigned int v = 0, zero = 0;
+  if ((e = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return gbd::cuda_fail(e, "read device error word");
+  if (v == 0) return GBD_OK;
+  if ((e = cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return gbd::cuda_fail(e, "clear device error word");
+  return gbd::set_error(GBD_ERR_TIMEOUT, "a bounded device wait gave up (error bits 0x%x)", v);
+}
+
+}  // extern "C"

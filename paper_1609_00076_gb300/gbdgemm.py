@@ -1,0 +1,153 @@
+"""Thin ctypes binding of libgbdgemm.so (include/gbdgemm.h).
+
+Argument marshalling only: every step of every call runs in the CUDA library.
+The functions keep the C names and argument order.  Matrix arguments accept a
+torch tensor (its data_ptr() is passed), a raw integer device address, or None.
+``stream`` accepts a torch.cuda.Stream, a raw cudaStream_t integer, or None for
+torch's current stream.
+
+There is no CPU fallback: if the shared library cannot be built or loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbdgemm.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "gbdgemm.h")
+
+GBD_OK = 0
+GBD_ERR_CUDA = -1
+GBD_ERR_WORKSPACE = -2
+GBD_ERR_TIMEOUT = -3
+GBD_ERR_DEVICE = -4
+GBD_ERR_LIMIT = -5
+GBD_ERR_ARG = -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GbdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gbdgemm error {code}: {msg}")
+        self.code = code
+
+
+def load(build_if_missing: bool = True):
+    """Load libgbdgemm.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise GbdError(GBD_ERR_CUDA, f"{LIB_PATH} is missing and could not be built")
+        lib = ctypes.CDLL(LIB_PATH)
+        _declare(lib)
+        _lib = lib
+        return lib
+
+
+def _declare(lib):
+    c, i64, d, i, vp, sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_size_t)
+    lib.gbd_version.argtypes = []
+    lib.gbd_version.restype = i
+    lib.gbd_last_error.argtypes = []
+    lib.gbd_last_error.restype = ctypes.c_char_p
+    lib.gbd_dgemm.argtypes = [c, c, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
+    lib.gbd_dgemm.restype = i
+    lib.gbd_check_device_error.argtypes = [vp]
+    lib.gbd_check_device_error.restype = i
+    for name, argt, rest in _EXTRA_DECLS:
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = argt
+            f.restype = rest
+
+
+# (name, argtypes, restype) of the entry points declared further down the header
+_EXTRA_DECLS: list = []
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/gbdgemm.h."""
+    with open(HEADER_PATH) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbd_[a-z0-9_]+)\s*\(", text)))
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"expected a device tensor or address, got {type(x)!r}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"expected a stream, got {type(s)!r}")
+
+
+def _t(ch: str) -> bytes:
+    b = ch.encode() if isinstance(ch, str) else bytes(ch)
+    if len(b) != 1:
+        raise ValueError("trans must be one character")
+    return b
+
+
+def gbd_version() -> int:
+    return load().gbd_version()
+
+
+def gbd_last_error() -> str:
+    return load().gbd_last_error().decode(errors="replace")
+
+
+def check(rc: int) -> int:
+    """Raise GbdError for a non-zero status, with the library's message."""
+    if rc != 0:
+        raise GbdError(rc, gbd_last_error())
+    return rc
+
+
+def gbd_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None) -> int:
+    """C := alpha*op(A)*op(B) + beta*C on the native FP64 MMA path; returns the status."""
+    return load().gbd_dgemm(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                            int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc),
+                            _stream(stream))
+
+
+def gbd_check_device_error(stream=None) -> int:
+    return load().gbd_check_device_error(_stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# torch helpers for the column-major layout (Section 2.1 of the paper)
+# ---------------------------------------------------------------------------
+def colmajor_view(buf, rows: int, cols: int, ld: int):
+    """rows x cols column-major view (strides (1, ld)) of a flat tensor of ld*cols elements."""
+    return buf[: ld * cols].view(cols, ld)[:, :rows].t() if cols else buf[:0].view(0, 0)
+
+
+def to_device(np_buf, device="cuda"):
+    """Copy a flat numpy float64 buffer to a flat device tensor."""
+    import torch
+    return torch.from_numpy(np_buf).to(device)

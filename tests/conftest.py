@@ -65,3 +65,49 @@ def first_mismatch(mine: np.ndarray, ref: np.ndarray, tol: np.ndarray | None, ro
     i, j = idx % rows, idx // rows
     extra = "" if tol is None else f", tol {tol[idx]!r}"
     return f"C[{i}][{j}] != C_ref, {mine[idx]!r}, {ref[idx]!r}{extra} ({int(bad.sum())} bad)"
+
+
+# --------------------------------------------------------------------------
+# GPU helpers: run a library call on device copies of numpy buffers that are
+# surrounded by guard bands of sentinel NaNs, and check the guards afterwards.
+# --------------------------------------------------------------------------
+GUARD = 64
+
+
+class DeviceBuf:
+    """A flat float64 device buffer holding `host` between two guard bands."""
+
+    def __init__(self, host: np.ndarray | None, n: int | None = None, offset: int = 0):
+        import torch
+        from paper_1609_00076_gb300 import synth
+        if host is None:
+            host = np.full(n, synth.SENTINEL)
+        self.n = host.size
+        self.offset = offset  # extra elements between the guard and the data (alignment tests)
+        full = np.full(GUARD + offset + self.n + GUARD, synth.SENTINEL)
+        full[GUARD + offset: GUARD + offset + self.n] = host
+        self.t = torch.from_numpy(full).cuda()
+
+    @property
+    def ptr(self) -> int:
+        return self.t.data_ptr() + 8 * (GUARD + self.offset)
+
+    def host(self) -> np.ndarray:
+        full = self.t.cpu().numpy()
+        return full[GUARD + self.offset: GUARD + self.offset + self.n].copy()
+
+    def guards_intact(self) -> bool:
+        from paper_1609_00076_gb300 import synth
+        full = self.t.cpu().numpy().view(np.uint64)
+        g1 = full[: GUARD + self.offset]
+        g2 = full[GUARD + self.offset + self.n:]
+        return bool((g1 == synth.SENTINEL_BITS).all() and (g2 == synth.SENTINEL_BITS).all())
+
+
+def padding_intact(C: np.ndarray, m: int, n: int, ldc: int) -> bool:
+    """Rows m..ldc-1 of every column still hold the sentinel (nothing wrote there)."""
+    from paper_1609_00076_gb300 import synth
+    if ldc == m or n == 0:
+        return True
+    v = C[: ldc * n].reshape(n, ldc)[:, m:].view(np.uint64)
+    return bool((v == synth.SENTINEL_BITS).all())
