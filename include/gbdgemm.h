@@ -78,6 +78,58 @@ GBD_API int gbd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k,
                       double* C, int64_t ldc, void* stream);
 
 /*
+ * Report of one emulated call (filled when the `info` argument is not NULL).
+ */
+typedef struct gbd_emu_info {
+  int slices;       /* digit slices per operand that were used */
+  int digit_bits;   /* bits per digit (7) */
+  int products;     /* slice products computed: slices*(slices+1)/2 */
+  double mu_min;    /* automatic mode: min over rows i of sum_p |a_ip| 2^-sigma_i (else 0) */
+  double nu_min;    /* automatic mode: min over columns j of sum_p |b_pj| 2^-tau_j (else 0) */
+  double bound_est; /* automatic mode: estimated componentwise relative error bound (else 0) */
+} gbd_emu_info;
+
+/*
+ * Bytes of device workspace that gbd_dgemm_emu needs for an m x n x k problem
+ * with `slices` digit slices per operand (0 = automatic: sized for the maximum,
+ * 9).  Returns 0 for negative sizes.  Host-only; needs no GPU.
+ */
+GBD_API size_t gbd_dgemm_emu_workspace_size(int64_t m, int64_t n, int64_t k, int slices);
+
+/*
+ * Double-precision GEMM emulated on the BF16 tensor cores (tcgen05) with the
+ * error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59,
+ * 2012), in fixed-point digit form; the operation and the argument list are
+ * those of gbd_dgemm (Section 1.2 of the paper).
+ *
+ * Steps: per-row exponents sigma_i of op(A) and per-column exponents tau_j of
+ * op(B); `slices` digits of 7 bits per entry (truncation of a_ip 2^-sigma_i);
+ * for each level g = 2..slices+1 the exact integer sum of the digit products
+ * with t + u = g, on tcgen05.mma with FP32 accumulation over chunks of 256 that
+ * is exact by construction; then C := beta*C and, from the smallest level to
+ * the largest, C := fma(alpha 2^(sigma_i + tau_j - 7g), P_g, C) in FP64.
+ *
+ * slices: 1..9, or 0 to choose the smallest count whose estimated componentwise
+ *   error stays below `tol` (relative to |alpha||op(A)||op(B)|; tol <= 0 means
+ *   the FP64 bound 2 k 2^-53).  Automatic mode reads 16 bytes back from the
+ *   device and therefore synchronises `stream`; with slices > 0 the call is
+ *   fully asynchronous.
+ * workspace: device memory of at least gbd_dgemm_emu_workspace_size(m, n, k,
+ *   slices) bytes, 256-byte aligned, owned by the caller; its contents on entry
+ *   do not matter and it must not be reused until the call has completed on
+ *   `stream`.
+ * info: optional report (may be NULL).
+ * Rows of op(A) or columns of op(B) holding Inf or NaN give NaN in the matching
+ * rows/columns of C.  Supported sizes: m, n < 4194240, k < 2^31.
+ * Returns 0, a BLAS argument index, or GBD_ERR_* (GBD_ERR_WORKSPACE when the
+ * workspace is missing, small or misaligned; GBD_ERR_ARG for a bad `slices`).
+ */
+GBD_API int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                          const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                          double* C, int64_t ldc, int slices, double tol, void* workspace,
+                          size_t workspace_bytes, gbd_emu_info* info, void* stream);
+
+/*
  * Reads and clears the device error word of the current device that the
  * kernels set when a bounded wait gives up.  Synchronises `stream` first.
  * Returns 0 when no wait gave up since the last call, GBD_ERR_TIMEOUT when one

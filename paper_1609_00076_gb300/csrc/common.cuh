@@ -34,6 +34,10 @@ unsigned int* device_error_word();
 int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
                    uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer,
                    CUtensorMapSwizzle swizzle);
+// tiled tensor map of any rank (dims[0] contiguous; pitches_bytes[i] = stride of dim i+1)
+int encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const void* base,
+                const uint64_t* dims, const uint64_t* pitches_bytes, const uint32_t* box,
+                CUtensorMapSwizzle swizzle);
 // launches the C := beta*C quick path (alpha == 0 or k == 0)
 int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t stream);
 

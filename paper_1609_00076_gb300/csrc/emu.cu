@@ -1,0 +1,135 @@
+// emu.cu -- host side of the split emulation: workspace sizing, slice-count
+// selection and the launch sequence of gbd_dgemm_emu.
+#include <cmath>
+#include <cstdint>
+
+#include "emu.cuh"
+
+namespace gbd {
+namespace emu {
+namespace {
+
+constexpr double kU = 1.1102230246251565e-16;  // 2^-53
+
+// A-priori relative error of s slices (digits of b bits), as a fraction of
+// |alpha| (|op(A)||op(B)|)_ij, for row/column magnitude sums mu, nu (in units of
+// 2^sigma_i, 2^tau_j) and inner dimension k:
+//   |err_ij| <= |alpha| 2^(sigma_i + tau_j - s b) (mu_i + nu_j + (s-1)(1+2^-b) k)
+// and (|op(A)||op(B)|)_ij is estimated as 2^(sigma_i + tau_j) mu_i nu_j / k, with a
+// safety factor of 8 for the estimate.
+double relative_bound(int s, double mu_min, double nu_min, int64_t k) {
+  const double kk = (double)k;
+  const double trunc = std::ldexp(1.0, -s * kDigitBits) * (2.0 * kk + (s - 1) * (1.0 + std::ldexp(1.0, -kDigitBits)) * kk);
+  const double ab = mu_min * nu_min / kk / 8.0;
+  return ab > 0.0 ? trunc / ab : INFINITY;
+}
+
+}  // namespace
+
+int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* bound) {
+  for (int s = 1; s <= kMaxSlices; ++s) {
+    const double b = relative_bound(s, mu_min, nu_min, k);
+    if (b <= tol || s == kMaxSlices) {
+      if (bound) *bound = b;
+      return s;
+    }
+  }
+  return kMaxSlices;
+}
+
+}  // namespace emu
+}  // namespace gbd
+
+extern "C" {
+
+size_t gbd_dgemm_emu_workspace_size(int64_t m, int64_t n, int64_t k, int slices) {
+  if (m < 0 || n < 0 || k < 0) return 0;
+  if (slices <= 0 || slices > gbd::emu::kMaxSlices) slices = gbd::emu::kMaxSlices;
+  return gbd::emu::layout(m, n, k, slices, nullptr, nullptr);
+}
+
+int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                  int64_t ldc, int slices, double tol, void* workspace, size_t workspace_bytes,
+                  gbd_emu_info* info, void* stream) {
+  using namespace gbd;
+  using namespace gbd::emu;
+  int rc = check_dgemm_args(transa, transb, m, n, k, lda, ldb, ldc);
+  if (rc) return rc;
+  if (info) {
+    info->slices = 0;
+    info->digit_bits = kDigitBits;
+    info->products = 0;
+    info->mu_min = 0.0;
+    info->nu_min = 0.0;
+    info->bound_est = 0.0;
+  }
+  if (slices < 0 || slices > kMaxSlices)
+    return set_error(GBD_ERR_ARG, "dgemm_emu: slices must be 0 (automatic) or 1..%d", kMaxSlices);
+  if (m == 0 || n == 0) return GBD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (alpha == 0.0 || k == 0) return scale_c(m, n, beta, C, ldc, s);
+  const int64_t lim = (int64_t)1 << 31;
+  if (m >= lim || n >= lim || k >= lim || (m + 63) / 64 > 65535 || (n + 63) / 64 > 65535)
+    return set_error(GBD_ERR_LIMIT, "dgemm_emu: m, n below 4194240 and k below 2^31 are supported");
+  rc = current_device(nullptr, nullptr);
+  if (rc) return rc;
+
+  const int s_ws = slices ? slices : kMaxSlices;
+  const size_t need = layout(m, n, k, s_ws, nullptr, nullptr);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return set_error(GBD_ERR_WORKSPACE, "dgemm_emu: workspace must be 256-byte aligned and hold %zu bytes", need);
+  Workspace ws;
+  layout(m, n, k, s_ws, workspace, &ws);
+
+  const int ta = trans_code(transa), tb = trans_code(transb);
+  // op(A) rows: A[p*lda + i] when 'N' (rows contiguous), A[i*lda + p] when 'T'
+  // op(B)^T rows (= columns j of op(B)): B[j*ldb + p] when 'N', B[p*ldb + j] when 'T'
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)n, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)n, s)) != cudaSuccess)
+    return cuda_fail(e, "dgemm_emu: workspace initialisation");
+  if ((rc = launch_exponents(A, lda, m, k, ta == 0, ws.sigA, ws.badA, s))) return rc;
+  if ((rc = launch_exponents(B, ldb, n, k, tb != 0, ws.sigB, ws.badB, s))) return rc;
+
+  int s_use = slices;
+  double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
+  if (slices == 0) {
+    if ((e = cudaMemsetAsync(ws.muA, 0, sizeof(float) * (size_t)m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.muB, 0, sizeof(float) * (size_t)n, s)) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu: workspace initialisation");
+    if ((rc = launch_magnitudes(A, lda, m, k, ta == 0, ws.sigA, ws.muA, s))) return rc;
+    if ((rc = launch_magnitudes(B, ldb, n, k, tb != 0, ws.sigB, ws.muB, s))) return rc;
+    if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
+    float st[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(st, ws.stats, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu: reading the magnitude statistics");
+    mu_min = st[0] < 1e38f ? st[0] : 0.0;
+    nu_min = st[1] < 1e38f ? st[1] : 0.0;
+    const double target = tol > 0.0 ? tol : 2.0 * (double)k * kU;
+    s_use = (mu_min > 0.0 && nu_min > 0.0) ? choose_slices(target, mu_min, nu_min, k, &bound) : 1;
+  }
+  if ((rc = launch_split(A, lda, m, k, ta == 0, ws.sigA, s_use, ws.DA, ws.kp, s))) return rc;
+  if ((rc = launch_split(B, ldb, n, k, tb != 0, ws.sigB, s_use, ws.DB, ws.kp, s))) return rc;
+  // the slice tensors are laid out for s_use slices from the start of each region
+  GemmParams gp;
+  gp.m = m; gp.n = n; gp.k = k;
+  gp.slices = s_use;
+  gp.alpha = alpha; gp.beta = beta;
+  gp.C = C; gp.ldc = ldc;
+  gp.sigA = ws.sigA; gp.sigB = ws.sigB; gp.badA = ws.badA; gp.badB = ws.badB;
+  if ((rc = launch_slice_gemm(gp, ws, s))) return rc;
+  if (info) {
+    info->slices = s_use;
+    info->products = s_use * (s_use + 1) / 2;
+    info->mu_min = mu_min;
+    info->nu_min = nu_min;
+    info->bound_est = bound;
+  }
+  return GBD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// emu.cuh -- internal interfaces of the split (Ozaki-scheme) emulation of DGEMM.
+//
+// Method: Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012), in fixed-point digit form:
+//   1. row exponents sigma_i of op(A) and column exponents tau_j of op(B);
+//   2. s digits of kDigitBits bits per entry (truncation of the scaled value);
+//   3. for every level g = 2..s+1 the exact integer sum over the digit pairs
+//      t + u = g, computed on the BF16 tensor cores with FP32 accumulation that is
+//      exact by construction (all partial sums are integers below 2^22);
+//   4. C := beta*C, then C := fma(alpha*2^(sigma_i + tau_j - g*b), P_g, C) from the
+//      smallest level to the largest, in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace gbd {
+namespace emu {
+
+constexpr int kDigitBits = 7;      // digits in [-127, 127]: exact in BF16, products < 2^14
+constexpr int kMaxSlices = 9;      // s * kDigitBits <= 63 bits of the scaled magnitude
+constexpr int kBK = 64;            // k elements per pipeline stage (128 bytes of BF16)
+constexpr int kChunkBlocks = 4;    // k-blocks per exact FP32 chunk: 256 * 127^2 < 2^22
+constexpr int kSegBlocks = 128;    // k-blocks per integer level segment: 9 * 8192 * 127^2 < 2^31
+constexpr int kExpEmpty = (int)0x80808080;  // exponent of a row/column with no non-zero entry
+
+// Layout of the caller's workspace (every array 256-byte aligned).
+struct Workspace {
+  int* sigA;        // [m] row exponents of op(A)
+  int* sigB;        // [n] column exponents of op(B)
+  int* badA;        // [m] non-zero when the row holds Inf/NaN
+  int* badB;        // [n]
+  float* muA;       // [m] sum_p |a_ip| 2^-sigma_i (slice-count selection only)
+  float* muB;       // [n]
+  float* stats;     // [4] min mu, min nu, any bad row, any bad column
+  uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
+  uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
+  int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
+};
+
+// bytes needed for (m, n, k, s) and, when base != nullptr, the pointers into it
+size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws);
+
+// Rows r of op(X) (R rows, K columns): element (r, p) is X[p*ld + r] when rows_contig,
+// X[r*ld + p] otherwise.
+int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig, int* sig,
+                     int* bad, cudaStream_t s);
+int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
+                      const int* sig, float* mu, cudaStream_t s);
+int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, const int* badA,
+                     const int* badB, float* stats, cudaStream_t s);
+int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
+                 const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s);
+
+struct GemmParams {
+  int64_t m, n, k;
+  int slices;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  const int* sigA;
+  const int* sigB;
+  const int* badA;
+  const int* badB;
+};
+int launch_slice_gemm(const GemmParams& p, const Workspace& ws, cudaStream_t s);
+
+}  // namespace emu
+}  // namespace gbd

@@ -1,0 +1,386 @@
+// emu_gemm.cu -- steps 3 and 4 of the split emulation on the 5th-generation
+// tensor cores: the digit-slice products with tcgen05.mma (BF16 x BF16 -> FP32 in
+// Tensor Memory), exact integer level sums, and the FP64 update of C.
+//
+// Persistent, warp-specialised kernel; one 128 x BN output tile at a time per CTA:
+//   warp 0      TMA producer: for each (level g, segment, pair t, k-block) loads the
+//               128 x 64 tile of digit slice t of op(A) and the BN x 64 tile of slice
+//               g-t of op(B)^T (128-byte swizzle) into a kStages-deep ring;
+//   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per k-block into one
+//               of two TMEM accumulators; a chunk of kChunkBlocks k-blocks (256 k) is
+//               accumulated from zero, so every FP32 partial sum is an integer below
+//               2^22 and exact;
+//   warps 2..9  epilogue: drain each finished chunk from TMEM (tcgen05.ld) and add it
+//               exactly into 32-bit integer registers (x + 1.5*2^23 exposes x in the
+//               low mantissa bits), so the MMA runs on while a chunk is drained; at
+//               the end of a level segment, C := fma(alpha 2^(tau_j - g b), P 2^sigma_i, C)
+//               with one FP64 fma per element, coalesced down the columns of C.
+// All waits are bounded (2 s); a wait that gives up sets the device error word and
+// the kernel runs to its end without hanging.
+#include <cstdint>
+#include <cstring>
+
+#include "emu.cuh"
+
+namespace gbd {
+namespace emu {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kStages = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr uint32_t kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
+constexpr float kMagic = 12582912.0f;
+constexpr int kTmemCols = 512;
+
+template <int BN>
+struct SmemLayout {
+  static constexpr int kABytes = kBM * kBK * 2;  // 16 KiB
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kOffA = 0;
+  static constexpr int kOffB = kOffA + kStages * kABytes;
+  static constexpr int kOffBar = kOffB + kStages * kBBytes;
+  static constexpr int kNumBars = 2 * kStages + 5;  // full, empty, acc_full[2], acc_empty[2], done
+  static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
+  static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
+  static constexpr int kBytes = kOffScale + BN * 8;
+  static constexpr int kAlloc = kBytes + 1024;  // slack to align the base to 1024 bytes
+};
+
+struct Args {
+  int64_t m, n, k;
+  int slices;
+  int nkb;      // k-blocks of kBK
+  int tiles_m;  // row tiles
+  int num_tiles;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  const int* sigA;
+  const int* sigB;
+  const int* badA;
+  const int* badB;
+  unsigned int* err;
+};
+
+// --- tcgen05 / TMA wrappers ------------------------------------------------------
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte
+// swizzle: 8-row atoms of 128-byte rows, atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address / 16
+  d |= (uint64_t)1 << 16;                    // leading-dimension byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride-dimension byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive 32-bit columns: register j of lane l = TMEM(lane base + l, col + j)
+__device__ __forceinline__ void tmem_ld_16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+}
+
+// P * 2^sigma as a double, exactly (P is an integer with |P| <= 2^31)
+__device__ __forceinline__ double scaled_int(int32_t P, int sigma) {
+  if (P == 0) return 0.0;
+  const uint32_t a = P < 0 ? 0u - (uint32_t)P : (uint32_t)P;
+  const int msb = 31 - __clz(a);
+  const int ef = 1023 + msb + sigma;
+  if (ef <= 0 || ef >= 2047) return ldexp((double)P, sigma);  // outside the normal range
+  const uint64_t mant = ((uint64_t)a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
+  const uint64_t bits = ((uint64_t)(P < 0) << 63) | ((uint64_t)ef << 52) | mant;
+  return __longlong_as_double((long long)bits);
+}
+
+// number of MMA chunks of level-segment (g, seg0..seg0+segn)
+__device__ __forceinline__ int chunks_of(int g, int segn) {
+  return ((g - 1) * segn + kChunkBlocks - 1) / kChunkBlocks;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+  using L = SmemLayout<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* acc_full = bars + 2 * kStages;
+  uint64_t* acc_empty = bars + 2 * kStages + 2;
+  uint64_t* done = bars + 2 * kStages + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmemSlot);
+  double* colscale = reinterpret_cast<double*>(smem + L::kOffScale);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = p.slices;
+
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 32 * kEpiWarps);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
+      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+        const int m0 = (tile % p.tiles_m) * kBM, n0 = (tile / p.tiles_m) * BN;
+        for (int g = s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, p.nkb - seg0);
+            for (int t = 1; t <= g - 1; ++t)
+              for (int kb = seg0; kb < seg0 + segn; ++kb) {
+                mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
+                mbar_arrive_expect_tx(&full[stage], bytes);
+                tma_load_3d(smem + L::kOffA + stage * L::kABytes, &tmA, &full[stage], kb * kBK, m0, t - 1);
+                tma_load_3d(smem + L::kOffB + stage * L::kBBytes, &tmB, &full[stage], kb * kBK, n0, g - t - 1);
+                if (++stage == kStages) { stage = 0; phase ^= 1u; }
+              }
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer --------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+      uint32_t stage = 0, phase = 0, chunk = 0;
+      const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
+      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+        for (int g = s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, p.nkb - seg0);
+            const int items = (g - 1) * segn;
+            for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
+              const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+              mbar_wait(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
+              tc_fence_after();
+              const uint32_t dtm = tmem_base + buf * BN;
+              const int i1 = min(items, i0 + kChunkBlocks);
+              for (int it = i0; it < i1; ++it) {
+                mbar_wait(&full[stage], phase, p.err, kErrWaitTma);
+                tc_fence_after();
+                const uint64_t da = smem_desc_sw128(a_base + stage * L::kABytes);
+                const uint64_t db = smem_desc_sw128(b_base + stage * L::kBBytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the descriptor
+                  umma_bf16(dtm, da + 2 * kk, db + 2 * kk, idesc, (it > i0 || kk > 0) ? 1u : 0u);
+                umma_commit(&empty[stage]);  // frees the stage when these MMAs have read it
+                if (++stage == kStages) { stage = 0; phase ^= 1u; }
+              }
+              umma_commit(&acc_full[buf]);  // chunk complete in TMEM
+            }
+          }
+      }
+      umma_commit(done);
+      mbar_wait(done, 0, p.err, kErrWaitMma);  // every MMA of this CTA has finished
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------ epilogue ----------------------------------
+    constexpr int kCols = BN / 2;  // columns per thread
+    const int ew = warp - 2;
+    const int quad = warp & 3;     // TMEM lanes 32*quad .. +31 are reachable from this warp
+    const int half = ew >> 2;      // which half of the tile's columns
+    const int row = quad * 32 + lane;
+    const int col0 = half * kCols;
+    uint32_t chunk = 0;
+    uint32_t acc[kCols];
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+      const int64_t m0 = (int64_t)(tile % p.tiles_m) * kBM, n0 = (int64_t)(tile / p.tiles_m) * BN;
+      const int64_t i = m0 + row;
+      const bool row_ok = i < p.m;
+      int sig_i = 0;
+      bool bad_i = false;
+      if (row_ok) {
+        sig_i = p.sigA[i];
+        if (sig_i == kExpEmpty) sig_i = 0;
+        bad_i = p.badA[i] != 0;
+      }
+      bool first = true;
+      for (int g = s + 1; g >= 2; --g)
+        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, p.nkb - seg0);
+          const int nch = chunks_of(g, segn);
+#pragma unroll
+          for (int c = 0; c < kCols; ++c) acc[c] = 0u;
+          for (int ci = 0; ci < nch; ++ci, ++chunk) {
+            const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+            mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + col0;
+#pragma unroll
+            for (int q = 0; q < kCols / 16; ++q) {
+              uint32_t v[16];
+              tmem_ld_16(taddr + q * 16, v);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float_as_uint(__uint_as_float(v[j]) + kMagic);
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+          }
+          // level-segment end: column scales alpha * 2^(tau_j - g b) (NaN for a bad column)
+          epi_bar_sync();  // the previous segment's readers are done with colscale
+          {
+            const int idx = ew * 32 + lane;
+            if (idx < BN) {
+              const int64_t j = n0 + idx;
+              double cs = 0.0;
+              if (j < p.n) {
+                int tau = p.sigB[j];
+                if (tau == kExpEmpty) tau = 0;
+                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - g * kDigitBits);
+              }
+              colscale[idx] = cs;
+            }
+          }
+          epi_bar_sync();
+          const uint32_t bias = (uint32_t)nch * kMagicBits;
+          if (row_ok) {
+            double* cptr = p.C + (n0 + col0) * p.ldc + i;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+              const int64_t j = n0 + col0 + c;
+              if (j < p.n) {
+                const int32_t P = (int32_t)(acc[c] - bias);
+                const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P, sig_i);
+                double w;
+                if (first) w = (p.beta == 0.0) ? 0.0 : p.beta * cptr[(int64_t)c * p.ldc];
+                else w = cptr[(int64_t)c * p.ldc];
+                cptr[(int64_t)c * p.ldc] = fma(colscale[col0 + c], x, w);
+              }
+            }
+          }
+          first = false;
+        }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <int BN>
+int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t stream) {
+  using L = SmemLayout<BN>;
+  CUtensorMap tmA, tmB;
+  memset(&tmA, 0, sizeof(tmA));
+  memset(&tmB, 0, sizeof(tmB));
+  const uint64_t dA[3] = {(uint64_t)gp.k, (uint64_t)gp.m, (uint64_t)gp.slices};
+  const uint64_t pA[2] = {(uint64_t)ws.kp * 2, (uint64_t)gp.m * ws.kp * 2};
+  const uint32_t bA[3] = {(uint32_t)kBK, (uint32_t)kBM, 1};
+  int rc = encode_tmap(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  const uint64_t dB[3] = {(uint64_t)gp.k, (uint64_t)gp.n, (uint64_t)gp.slices};
+  const uint64_t pB[2] = {(uint64_t)ws.kp * 2, (uint64_t)gp.n * ws.kp * 2};
+  const uint32_t bB[3] = {(uint32_t)kBK, (uint32_t)BN, 1};
+  rc = encode_tmap(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+
+  Args a;
+  a.m = gp.m; a.n = gp.n; a.k = gp.k;
+  a.slices = gp.slices;
+  a.nkb = (int)((gp.k + kBK - 1) / kBK);
+  a.tiles_m = (int)((gp.m + kBM - 1) / kBM);
+  const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + BN - 1) / BN);
+  if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
+  a.num_tiles = (int)tiles;
+  a.alpha = gp.alpha; a.beta = gp.beta;
+  a.C = gp.C; a.ldc = gp.ldc;
+  a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
+  a.err = device_error_word();
+
+  auto kern = k_slice_gemm<BN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm)");
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, tmA, tmB);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm launch");
+}
+
+}  // namespace
+
+int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t stream) {
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  if (gp.m == 0 || gp.n == 0) return GBD_OK;
+  const int64_t tiles256 = ((gp.m + kBM - 1) / kBM) * ((gp.n + 255) / 256);
+  if (tiles256 >= sms) return launch_bn<256>(gp, ws, sms, stream);
+  return launch_bn<128>(gp, ws, sms, stream);
+}
+
+}  // namespace emu
+}  // namespace gbd

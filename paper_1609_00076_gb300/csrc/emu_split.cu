@@ -1,0 +1,316 @@
+// emu_split.cu -- steps 1 and 2 of the split emulation: row/column exponents and
+// the digit slices, with integer bit operations only (FP64 arithmetic is a
+// low-rate unit on GB300; none is used here).
+//
+// These kernels are bound by HBM: each reads the operand once (8 bytes per
+// element) and the split writes s BF16 digits (2s bytes per element).
+#include <cstdint>
+
+#include "emu.cuh"
+
+namespace gbd {
+namespace emu {
+namespace {
+
+// frexp exponent e of a finite non-zero double (x = f 2^e, 0.5 <= |f| < 1), from its bits
+__device__ __forceinline__ int exponent_of(uint64_t bits) {
+  const uint32_t E = (uint32_t)(bits >> 52) & 0x7FFu;
+  if (E) return (int)E - 1022;
+  const uint64_t frac = bits & 0xFFFFFFFFFFFFFull;  // subnormal: frac * 2^-1074
+  return (64 - __clzll((long long)frac)) - 1074;
+}
+
+__device__ __forceinline__ bool is_nonfinite(uint64_t bits) {
+  return ((bits >> 52) & 0x7FFu) == 0x7FFu;
+}
+__device__ __forceinline__ bool is_zero(uint64_t bits) { return (bits << 1) == 0; }
+
+template <bool ROWS_CONTIG>
+__device__ __forceinline__ uint64_t load_bits(const double* X, int64_t ld, int64_t r, int64_t p) {
+  const double* a = ROWS_CONTIG ? X + p * ld + r : X + r * ld + p;
+  return (uint64_t)__double_as_longlong(__ldg(a));
+}
+
+constexpr int kRedChunk = 1024;  // k elements per block of the reductions
+
+// sigma_r = max over non-zero finite entries of the frexp exponent; bad_r |= any Inf/NaN
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X, int64_t ld, int64_t R,
+                                                   int64_t K, int* __restrict__ sig, int* __restrict__ bad) {
+  const int64_t p_begin = (int64_t)blockIdx.y * kRedChunk;
+  const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
+  if (ROWS_CONTIG) {
+    // 32 consecutive rows per warp (coalesced), 8 warps split the k range
+    __shared__ int s_max[8][33];
+    __shared__ int s_bad[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
+    int mx = kExpEmpty, bd = 0;
+    if (r < R)
+      for (int64_t p = p_begin + ty; p < p_end; p += 8) {
+        const uint64_t b = load_bits<true>(X, ld, r, p);
+        if (is_nonfinite(b)) bd = 1;
+        else if (!is_zero(b)) mx = max(mx, exponent_of(b));
+      }
+    s_max[ty][tx] = mx;
+    s_bad[ty][tx] = bd;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+      for (int q = 1; q < 8; ++q) {
+        mx = max(mx, s_max[q][tx]);
+        bd |= s_bad[q][tx];
+      }
+      if (mx != kExpEmpty) atomicMax(sig + r, mx);
+      if (bd) atomicOr(bad + r, 1);
+    }
+  } else {
+    // one row per warp, lanes along the contiguous k direction
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 8 + w;
+    if (r >= R) return;
+    int mx = kExpEmpty, bd = 0;
+    for (int64_t p = p_begin + lane; p < p_end; p += 32) {
+      const uint64_t b = load_bits<false>(X, ld, r, p);
+      if (is_nonfinite(b)) bd = 1;
+      else if (!is_zero(b)) mx = max(mx, exponent_of(b));
+    }
+    for (int o = 16; o; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      bd |= __shfl_xor_sync(0xffffffffu, bd, o);
+    }
+    if (lane == 0) {
+      if (mx != kExpEmpty) atomicMax(sig + r, mx);
+      if (bd) atomicOr(bad + r, 1);
+    }
+  }
+}
+
+// |x| * 2^-sigma as a float (truncated mantissa; an estimate for slice selection)
+__device__ __forceinline__ float scaled_magnitude(uint64_t bits, int sigma) {
+  const int E = (int)((bits >> 52) & 0x7FFu);
+  if (E == 0 || E == 0x7FF) return 0.0f;
+  const int fe = E - 1023 - sigma + 127;
+  if (fe <= 0) return 0.0f;
+  if (fe >= 255) return 3.0e38f;
+  const uint32_t fb = ((uint32_t)fe << 23) | (uint32_t)((bits >> 29) & 0x7FFFFFu);
+  return __uint_as_float(fb);
+}
+
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X, int64_t ld, int64_t R,
+                                                    int64_t K, const int* __restrict__ sig,
+                                                    float* __restrict__ mu) {
+  const int64_t p_begin = (int64_t)blockIdx.y * kRedChunk;
+  const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
+  if (ROWS_CONTIG) {
+    __shared__ float s_sum[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
+    float acc = 0.0f;
+    if (r < R) {
+      const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
+      for (int64_t p = p_begin + ty; p < p_end; p += 8) acc += scaled_magnitude(load_bits<true>(X, ld, r, p), sg);
+    }
+    s_sum[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+      for (int q = 1; q < 8; ++q) acc += s_sum[q][tx];
+      atomicAdd(mu + r, acc);
+    }
+  } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 8 + w;
+    if (r >= R) return;
+    const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
+    float acc = 0.0f;
+    for (int64_t p = p_begin + lane; p < p_end; p += 32) acc += scaled_magnitude(load_bits<false>(X, ld, r, p), sg);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicAdd(mu + r, acc);
+  }
+}
+
+// stats = {min over non-empty rows of mu, min over non-empty columns of nu, any bad row, any bad column}
+__global__ void __launch_bounds__(256) k_min_stats(const float* __restrict__ muA, int64_t m,
+                                                   const float* __restrict__ muB, int64_t n,
+                                                   const int* __restrict__ badA, const int* __restrict__ badB,
+                                                   float* __restrict__ stats) {
+  __shared__ float s_min[2][256];
+  __shared__ int s_bad[2][256];
+  float mn[2] = {3.0e38f, 3.0e38f};
+  int bd[2] = {0, 0};
+  for (int64_t i = threadIdx.x; i < m; i += 256) {
+    if (muA[i] > 0.0f) mn[0] = fminf(mn[0], muA[i]);
+    bd[0] |= badA[i];
+  }
+  for (int64_t j = threadIdx.x; j < n; j += 256) {
+    if (muB[j] > 0.0f) mn[1] = fminf(mn[1], muB[j]);
+    bd[1] |= badB[j];
+  }
+  for (int q = 0; q < 2; ++q) {
+    s_min[q][threadIdx.x] = mn[q];
+    s_bad[q][threadIdx.x] = bd[q];
+  }
+  __syncthreads();
+  for (int stride = 128; stride; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+      for (int q = 0; q < 2; ++q) {
+        s_min[q][threadIdx.x] = fminf(s_min[q][threadIdx.x], s_min[q][threadIdx.x + stride]);
+        s_bad[q][threadIdx.x] |= s_bad[q][threadIdx.x + stride];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[0] = s_min[0][0];
+    stats[1] = s_min[1][0];
+    stats[2] = (float)s_bad[0][0];
+    stats[3] = (float)s_bad[1][0];
+  }
+}
+
+// s digits of kDigitBits bits of |x| 2^-sigma, truncated toward zero, with the sign of x:
+// Q = floor(|x| 2^(s*b - sigma)) and digit t is bits [(s-t)b, (s-t+1)b) of Q.
+__device__ __forceinline__ uint64_t scaled_fixed(uint64_t bits, int sigma, int sb) {
+  const uint32_t E = (uint32_t)(bits >> 52) & 0x7FFu;
+  if (E == 0x7FFu) return 0;  // non-finite: the row is flagged, its digits are zero
+  uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+  int e2;  // x = mant * 2^e2
+  if (E) {
+    mant |= 1ull << 52;
+    e2 = (int)E - 1075;
+  } else {
+    e2 = -1074;
+  }
+  const int sh = e2 - sigma + sb;
+  if (sh >= 0) return sh >= 64 ? 0 : (mant << sh);  // |x| < 2^sigma keeps this below 2^sb
+  return (-sh >= 64) ? 0 : (mant >> (-sh));
+}
+
+__device__ __forceinline__ uint32_t bf16_of_digit(int d) {
+  return __float_as_uint((float)d) >> 16;  // |d| <= 127: exact in BF16
+}
+
+constexpr int kTile = 64;
+constexpr int kPerThread = 16;  // k elements per thread in the write phase
+
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) k_split(const double* __restrict__ X, int64_t ld, int64_t R,
+                                               int64_t K, const int* __restrict__ sig, int slices,
+                                               uint16_t* __restrict__ D, int64_t kp) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int64_t p0 = (int64_t)blockIdx.x * kTile, r0 = (int64_t)blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kTile * kTile; idx += 256) {
+    int rr, pp;
+    if (ROWS_CONTIG) { rr = idx % kTile; pp = idx / kTile; }  // coalesced along rows
+    else { pp = idx % kTile; rr = idx / kTile; }              // coalesced along k
+    const int64_t r = r0 + rr, p = p0 + pp;
+    tile[rr][pp] = (r < R && p < K) ? load_bits<ROWS_CONTIG>(X, ld, r, p) : 0ull;
+  }
+  __syncthreads();
+  const int rr = tid >> 2, pp0 = (tid & 3) * kPerThread;
+  const int64_t r = r0 + rr, pbase = p0 + pp0;
+  if (r >= R || pbase >= K) return;
+  const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
+  const int sb = slices * kDigitBits;
+  uint64_t q[kPerThread];
+  uint32_t neg = 0;
+#pragma unroll
+  for (int v = 0; v < kPerThread; ++v) {
+    const uint64_t b = tile[rr][pp0 + v];
+    q[v] = scaled_fixed(b, sg, sb);
+    neg |= (uint32_t)(b >> 63) << v;
+  }
+  const bool full = pbase + kPerThread <= K;
+  for (int t = 0; t < slices; ++t) {
+    const int shift = (slices - 1 - t) * kDigitBits;
+    uint32_t packed[kPerThread / 2];
+#pragma unroll
+    for (int v = 0; v < kPerThread; v += 2) {
+      int d0 = (int)((q[v] >> shift) & 0x7Fu), d1 = (int)((q[v + 1] >> shift) & 0x7Fu);
+      if ((neg >> v) & 1u) d0 = -d0;
+      if ((neg >> (v + 1)) & 1u) d1 = -d1;
+      packed[v / 2] = bf16_of_digit(d0) | (bf16_of_digit(d1) << 16);
+    }
+    uint16_t* row = D + ((int64_t)t * R + r) * kp + pbase;
+    if (full) {
+      uint4* dst = reinterpret_cast<uint4*>(row);  // 16-byte aligned: kp % 8 == 0, pbase % 16 == 0
+      dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    } else {
+      for (int v = 0; v < kPerThread && pbase + v < K; ++v)
+        row[v] = (uint16_t)((packed[v / 2] >> (16 * (v & 1))) & 0xFFFFu);
+    }
+  }
+}
+
+int launch_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, what);
+}
+
+}  // namespace
+
+size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t kp = (k + 7) / 8 * 8;
+  size_t off = 0;
+  const size_t o_sigA = off; off = up(off + sizeof(int) * (size_t)m);
+  const size_t o_sigB = off; off = up(off + sizeof(int) * (size_t)n);
+  const size_t o_badA = off; off = up(off + sizeof(int) * (size_t)m);
+  const size_t o_badB = off; off = up(off + sizeof(int) * (size_t)n);
+  const size_t o_muA = off; off = up(off + sizeof(float) * (size_t)m);
+  const size_t o_muB = off; off = up(off + sizeof(float) * (size_t)n);
+  const size_t o_stats = off; off = up(off + sizeof(float) * 4);
+  const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
+  const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
+  if (base && ws) {
+    char* b = static_cast<char*>(base);
+    ws->sigA = reinterpret_cast<int*>(b + o_sigA);
+    ws->sigB = reinterpret_cast<int*>(b + o_sigB);
+    ws->badA = reinterpret_cast<int*>(b + o_badA);
+    ws->badB = reinterpret_cast<int*>(b + o_badB);
+    ws->muA = reinterpret_cast<float*>(b + o_muA);
+    ws->muB = reinterpret_cast<float*>(b + o_muB);
+    ws->stats = reinterpret_cast<float*>(b + o_stats);
+    ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
+    ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
+    ws->kp = kp;
+  }
+  return off;
+}
+
+int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig, int* sig,
+                     int* bad, cudaStream_t s) {
+  if (R == 0 || K == 0) return GBD_OK;
+  const unsigned gy = (unsigned)((K + kRedChunk - 1) / kRedChunk);
+  if (rows_contig) k_exponents<true><<<dim3((unsigned)((R + 31) / 32), gy), 256, 0, s>>>(X, ld, R, K, sig, bad);
+  else k_exponents<false><<<dim3((unsigned)((R + 7) / 8), gy), 256, 0, s>>>(X, ld, R, K, sig, bad);
+  return launch_check("exponent kernel launch");
+}
+
+int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
+                      const int* sig, float* mu, cudaStream_t s) {
+  if (R == 0 || K == 0) return GBD_OK;
+  const unsigned gy = (unsigned)((K + kRedChunk - 1) / kRedChunk);
+  if (rows_contig) k_magnitudes<true><<<dim3((unsigned)((R + 31) / 32), gy), 256, 0, s>>>(X, ld, R, K, sig, mu);
+  else k_magnitudes<false><<<dim3((unsigned)((R + 7) / 8), gy), 256, 0, s>>>(X, ld, R, K, sig, mu);
+  return launch_check("magnitude kernel launch");
+}
+
+int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, const int* badA,
+                     const int* badB, float* stats, cudaStream_t s) {
+  k_min_stats<<<1, 256, 0, s>>>(muA, m, muB, n, badA, badB, stats);
+  return launch_check("statistics kernel launch");
+}
+
+int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
+                 const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s) {
+  if (R == 0 || K == 0) return GBD_OK;
+  dim3 grid((unsigned)((K + kTile - 1) / kTile), (unsigned)((R + kTile - 1) / kTile));
+  if (rows_contig) k_split<true><<<grid, 256, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
+  else k_split<false><<<grid, 256, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
+  return launch_check("split kernel launch");
+}
+
+}  // namespace emu
+}  // namespace gbd

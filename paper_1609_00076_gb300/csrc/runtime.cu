@@ -110,9 +110,9 @@ unsigned int* device_error_word() {
   return g_err_ptr[dev];
 }
 
-int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
-                   uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer,
-                   CUtensorMapSwizzle swizzle) {
+int encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const void* base,
+                const uint64_t* dims, const uint64_t* pitches_bytes, const uint32_t* box,
+                CUtensorMapSwizzle swizzle) {
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_encode) {
@@ -125,18 +125,31 @@ int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base
       g_encode = reinterpret_cast<EncodeTiledFn>(fn);
     }
   }
-  const cuuint64_t dims[2] = {inner, outer};
-  const cuuint64_t strides[1] = {pitch_bytes};
-  const cuuint32_t box[2] = {box_inner, box_outer};
-  const cuuint32_t estride[2] = {1, 1};
-  CUresult r = g_encode(out, dtype, 2, const_cast<void*>(base), dims, strides, box, estride,
+  if (rank < 1 || rank > 5) return set_error(GBD_ERR_ARG, "tensor map rank %d", rank);
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) st[i] = pitches_bytes[i];
+  }
+  CUresult r = g_encode(out, dtype, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
-    return set_error(GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d): dims %llu x %llu pitch %llu box %u x %u",
-                     (int)r, (unsigned long long)inner, (unsigned long long)outer,
-                     (unsigned long long)pitch_bytes, box_inner, box_outer);
+    return set_error(GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d): rank %d dims %llu x %llu box %u x %u",
+                     (int)r, rank, (unsigned long long)dims[0], (unsigned long long)dims[1], box[0], box[1]);
   return GBD_OK;
+}
+
+int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
+                   uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer,
+                   CUtensorMapSwizzle swizzle) {
+  const uint64_t dims[2] = {inner, outer};
+  const uint64_t pitches[1] = {pitch_bytes};
+  const uint32_t box[2] = {box_inner, box_outer};
+  return encode_tmap(out, dtype, 2, base, dims, pitches, box, swizzle);
 }
 
 int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t stream) {

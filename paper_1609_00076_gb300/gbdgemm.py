@@ -73,8 +73,23 @@ def _declare(lib):
             f.restype = rest
 
 
+class GbdEmuInfo(ctypes.Structure):
+    """Mirror of gbd_emu_info."""
+    _fields_ = [("slices", ctypes.c_int), ("digit_bits", ctypes.c_int), ("products", ctypes.c_int),
+                ("mu_min", ctypes.c_double), ("nu_min", ctypes.c_double), ("bound_est", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_c, _i64, _d, _i, _vp, _sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_size_t)
 # (name, argtypes, restype) of the entry points declared further down the header
-_EXTRA_DECLS: list = []
+_EXTRA_DECLS: list = [
+    ("gbd_dgemm_emu_workspace_size", [_i64, _i64, _i64, _i], _sz),
+    ("gbd_dgemm_emu", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
+                       ctypes.POINTER(GbdEmuInfo), _vp], _i),
+]
 
 
 def header_functions() -> list[str]:
@@ -133,6 +148,21 @@ def gbd_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stre
     return load().gbd_dgemm(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
                             int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc),
                             _stream(stream))
+
+
+def gbd_dgemm_emu_workspace_size(m, n, k, slices=0) -> int:
+    """Device workspace bytes of gbd_dgemm_emu (slices 0 = automatic, sized for 9)."""
+    return int(load().gbd_dgemm_emu_workspace_size(int(m), int(n), int(k), int(slices)))
+
+
+def gbd_dgemm_emu(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, tol, workspace,
+                  workspace_bytes, info=None, stream=None) -> int:
+    """C := alpha*op(A)*op(B) + beta*C by split emulation on the BF16 tensor cores; returns the
+    status.  ``info`` may be a GbdEmuInfo to receive the report."""
+    return load().gbd_dgemm_emu(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                                int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
+                                float(tol), _addr(workspace), int(workspace_bytes),
+                                ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
 def gbd_check_device_error(stream=None) -> int:
