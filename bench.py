@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 DGEMM library: C := alpha*op(A)*op(B) + beta*C.
 
-Metric: DGEMM TFLOP/s (useful flops 2mnk per call) against the FP64 peak, for
-the native FP64-MMA path, on the large square workload m = n = k = 8192
-(FP64 operands uniform on [-1, 1), N,N, alpha = 1, beta = 0; every input is
-larger than L2, so no flush is needed between timed calls).
+Metric: DGEMM TFLOP/s (useful flops 2mnk per call) of the split emulation at
+FP64 accuracy (automatic slice count for the componentwise FP64 bound), with the
+native FP64-MMA path measured beside it on the same inputs, on the large square
+workload m = n = k = 8192 (FP64 operands uniform on [-1, 1), N,N, alpha = 1,
+beta = 0; every input is larger than L2, so no flush is needed between timed
+calls).  The dominant kernel's roofline is the BF16 tensor peak (slice flops =
+products x 2mnk); the native path's is the FP64 peak.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one DGEMM call on device-resident inputs.  Timing: W untimed
+One step = one emulated DGEMM call on device-resident inputs.  Timing: W untimed
 warm-up steps, then K steps between CUDA events on the launching stream, with a
 barrier and a device synchronisation on both sides; the max over ranks is taken.
 Multi-GPU runs are independent replicas (each rank its own problem, no
@@ -46,7 +49,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture of this
 # workload; None until captured for the current kernel
-TRAFFIC_PER_LAUNCH = {"native": None}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": None}
 
 
 def load_peaks():
@@ -212,10 +215,15 @@ def run_reference(args, world, rank, pg):
 # ------------------------------------------------------------------------------
 # GPU legs
 # ------------------------------------------------------------------------------
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
-    from paper_1609_00076_gb300 import gbdgemm, synth
+    from paper_1609_00076_gb300 import gbdgemm
     gbdgemm.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -225,17 +233,24 @@ def run_ours(args, world, rank, local, pg):
     A = torch.from_numpy(A_h).to(dev)
     B = torch.from_numpy(B_h).to(dev)
     C = torch.zeros(M * N, dtype=torch.float64, device=dev)
+    wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     flops = 2.0 * M * N * K
+    info = gbdgemm.GbdEmuInfo()
 
-    def step(s):
-        rc = gbdgemm.gbd_dgemm("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, stream=s)
-        if rc != 0:
-            raise gbdgemm.GbdError(rc, gbdgemm.gbd_last_error())
+    def emu_step(s, record=False):
+        info.record_phases = 1 if record else 0
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
+                                            info, stream=s))
 
+    def native_step(s):
+        gbdgemm.check(gbdgemm.gbd_dgemm("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, stream=s))
+
+    # ---- emulated path (the timed steps): automatic slices at the FP64 bound ----
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step(stream)
+            emu_step(stream)
     torch.cuda.synchronize()
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
 
@@ -243,65 +258,127 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     torch.cuda.synchronize()
     sampler.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = _events(args.steps + 1)
+    gemm_ms, prep_ms = [], []
     ev[0].record(stream)
     for i in range(args.steps):
-        step(stream)
+        emu_step(stream, record=True)
+        gemm_ms.append(info.gemm_ms)
+        prep_ms.append(info.prep_ms)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier(pg)
     clocks = sampler.stop()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     total_ms = max_over_ranks(pg, total_ms, dev)
     value = world * flops * args.steps / (total_ms / 1000.0) / 1e12
+    slices = info.slices
+    products = info.products
 
-    # --- end to end through the C ABI with host buffers (pinned), copies inside the region ---
+    # ---- native path on the same inputs ----
+    nat_calls = 2
+    with torch.cuda.stream(stream):
+        native_step(stream)
+        torch.cuda.synchronize()
+        nev = _events(nat_calls + 1)
+        nev[0].record(stream)
+        for i in range(nat_calls):
+            native_step(stream)
+            nev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    nat_ms = statistics.mean(nev[i].elapsed_time(nev[i + 1]) for i in range(nat_calls))
+    nat_tflops = flops / (nat_ms / 1000.0) / 1e12
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region ----
     A_p = torch.from_numpy(A_h).pin_memory()
     B_p = torch.from_numpy(B_h).pin_memory()
     C_p = torch.empty(M * N, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     with torch.cuda.stream(stream):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        e0, e1 = _events(2)
         e0.record(stream)
         for _ in range(e2e_steps):
             A.copy_(A_p, non_blocking=True)
             B.copy_(B_p, non_blocking=True)
-            step(stream)
+            emu_step(stream)
             C_p.copy_(C, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
     e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
     e2e_val = world * flops * e2e_steps / (e2e_ms / 1000.0) / 1e12
 
+    # ---- latency of small calls (256^3, the latency configuration) ----
+    lat = small_call_latency(dev, stream)
+
     if rank != 0:
         return 0
     peaks, src = load_peaks()
+    bf16_sust = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64 / NOMINAL_BF16
-    kernel_ms = statistics.mean(per)
-    achieved = flops / (kernel_ms / 1000.0) / 1e12
-    cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=12.0)
+    g_ms = statistics.mean(gemm_ms)
+    slice_flops = products * flops
+    achieved = slice_flops / (g_ms / 1000.0) / 1e12
+    cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=8.0)
+    launches_per_step = 8  # exponents x2, magnitudes x2, statistics, split x2, slice product
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(), "path": "native (mma.sync f64)", "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)",
+        "config": {"workload": workload_name(), "path": "emulated (split digits on tcgen05 BF16, FP64 bound)",
+                   "slices": slices, "products": products, "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": TRAFFIC_PER_LAUNCH["native"],
-                     "peak_source": f"{src} bf16 {peaks['bf16_tflops']} x nominal fp64/bf16 "
-                                    f"{NOMINAL_FP64}/{NOMINAL_BF16}"},
+        "native": {"value": nat_tflops, "unit": "TFLOP/s", "ms_per_call": nat_ms, "frac_of_fp64_peak": nat_tflops / fp64_peak,
+                   "fp64_peak": fp64_peak},
+        "emulated_over_native": value / nat_tflops,
+        "phases_ms": {"prep": statistics.mean(prep_ms), "slice_gemm": g_ms},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                     "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
+                     "kernel": "k_slice_gemm (tcgen05 kind::f16, BF16 -> FP32)",
+                     "peak_source": f"{src} bf16_tflops_sustained"},
+        "latency": lat,
         "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
                 "d2h_bytes_per_step": M * N * 8},
-        "gpu_launches": args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def small_call_latency(dev, stream, calls: int = 200):
+    """p50/p99 device latency of 256^3 native and emulated calls (one call per event pair)."""
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm, synth
+    m = n = k = 256
+    A = torch.from_numpy(synth.matrix("uniform", m, k, m, 1, pad=0.0)).to(dev)
+    B = torch.from_numpy(synth.matrix("uniform", k, n, k, 2, pad=0.0)).to(dev)
+    C = torch.zeros(m * n, dtype=torch.float64, device=dev)
+    slices = 7
+    wsb = gbdgemm.gbd_dgemm_emu_workspace_size(m, n, k, slices)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("native", lambda s: gbdgemm.gbd_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, stream=s)),
+                     ("emulated", lambda s: gbdgemm.gbd_dgemm_emu("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m,
+                                                                 slices, 0.0, ws, wsb, None, stream=s))):
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                gbdgemm.check(fn(stream))
+            torch.cuda.synchronize()
+            ev = _events(2 * calls)
+            for i in range(calls):
+                ev[2 * i].record(stream)
+                gbdgemm.check(fn(stream))
+                ev[2 * i + 1].record(stream)
+            torch.cuda.synchronize()
+        t = sorted(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(calls))
+        out[name] = {"p50_ms": t[len(t) // 2], "p99_ms": t[min(len(t) - 1, int(0.99 * len(t)))]}
+    out["config"] = "256^3 N,N alpha=1 beta=0, uniform[-1,1); emulated with 7 slices; device time per call"
+    return out
 
 
 def main():

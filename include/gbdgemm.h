@@ -81,12 +81,16 @@ GBD_API int gbd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k,
  * Report of one emulated call (filled when the `info` argument is not NULL).
  */
 typedef struct gbd_emu_info {
+  int record_phases; /* input: non-zero to time the phases with CUDA events on `stream`
+                        (the call then waits for its own completion before returning) */
   int slices;       /* digit slices per operand that were used */
   int digit_bits;   /* bits per digit (7) */
   int products;     /* slice products computed: slices*(slices+1)/2 */
   double mu_min;    /* automatic mode: min over rows i of sum_p |a_ip| 2^-sigma_i (else 0) */
   double nu_min;    /* automatic mode: min over columns j of sum_p |b_pj| 2^-tau_j (else 0) */
   double bound_est; /* automatic mode: estimated componentwise relative error bound (else 0) */
+  double prep_ms;   /* record_phases: device time of the exponent, statistics and split kernels */
+  double gemm_ms;   /* record_phases: device time of the slice-product kernel */
 } gbd_emu_info;
 
 /*
@@ -118,7 +122,7 @@ GBD_API size_t gbd_dgemm_emu_workspace_size(int64_t m, int64_t n, int64_t k, int
  *   slices) bytes, 256-byte aligned, owned by the caller; its contents on entry
  *   do not matter and it must not be reused until the call has completed on
  *   `stream`.
- * info: optional report (may be NULL).
+ * info: optional report (may be NULL); its record_phases field is read on entry.
  * Rows of op(A) or columns of op(B) holding Inf or NaN give NaN in the matching
  * rows/columns of C.  Supported sizes: m, n < 4194240, k < 2^31.
  * Returns 0, a BLAS argument index, or GBD_ERR_* (GBD_ERR_WORKSPACE when the

@@ -56,7 +56,10 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   using namespace gbd::emu;
   int rc = check_dgemm_args(transa, transb, m, n, k, lda, ldb, ldc);
   if (rc) return rc;
+  const bool timing = info && info->record_phases;
   if (info) {
+    info->prep_ms = 0.0;
+    info->gemm_ms = 0.0;
     info->slices = 0;
     info->digit_bits = kDigitBits;
     info->products = 0;
@@ -83,6 +86,20 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   layout(m, n, k, s_ws, workspace, &ws);
 
   const int ta = trans_code(transa), tb = trans_code(transb);
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  struct EventGuard {
+    cudaEvent_t* e;
+    ~EventGuard() {
+      for (int i = 0; i < 3; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  if (timing) {
+    cudaError_t ee;
+    for (int i = 0; i < 3; ++i)
+      if ((ee = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(ee, "dgemm_emu: cudaEventCreate");
+    if ((ee = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(ee, "dgemm_emu: cudaEventRecord");
+  }
   // op(A) rows: A[p*lda + i] when 'N' (rows contiguous), A[i*lda + p] when 'T'
   // op(B)^T rows (= columns j of op(B)): B[j*ldb + p] when 'N', B[p*ldb + j] when 'T'
   cudaError_t e;
@@ -121,7 +138,17 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   gp.alpha = alpha; gp.beta = beta;
   gp.C = C; gp.ldc = ldc;
   gp.sigA = ws.sigA; gp.sigB = ws.sigB; gp.badA = ws.badA; gp.badB = ws.badB;
+  if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu: cudaEventRecord");
   if ((rc = launch_slice_gemm(gp, ws, s))) return rc;
+  if (timing) {
+    float t0 = 0.f, t1 = 0.f;
+    if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[2])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t0, ev[0], ev[1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t1, ev[1], ev[2])) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu: phase timing");
+    info->prep_ms = t0;
+    info->gemm_ms = t1;
+  }
   if (info) {
     info->slices = s_use;
     info->products = s_use * (s_use + 1) / 2;

@@ -75,8 +75,9 @@ def _declare(lib):
 
 class GbdEmuInfo(ctypes.Structure):
     """Mirror of gbd_emu_info."""
-    _fields_ = [("slices", ctypes.c_int), ("digit_bits", ctypes.c_int), ("products", ctypes.c_int),
-                ("mu_min", ctypes.c_double), ("nu_min", ctypes.c_double), ("bound_est", ctypes.c_double)]
+    _fields_ = [("record_phases", ctypes.c_int), ("slices", ctypes.c_int), ("digit_bits", ctypes.c_int),
+                ("products", ctypes.c_int), ("mu_min", ctypes.c_double), ("nu_min", ctypes.c_double),
+                ("bound_est", ctypes.c_double), ("prep_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
