@@ -7,7 +7,7 @@
 //   2. s digits of kDigitBits bits per entry (truncation of the scaled value);
 //   3. for every level g = 2..s+1 the exact integer sum over the digit pairs
 //      t + u = g, computed on the BF16 tensor cores with FP32 accumulation that is
-//      exact by construction (all partial sums are integers below 2^22);
+//      exact by construction (all partial sums are integers below 2^24);
 //   4. C := beta*C, then C := fma(alpha*2^(sigma_i + tau_j - g*b), P_g, C) from the
 //      smallest level to the largest, in FP64.
 #pragma once
@@ -24,7 +24,7 @@ namespace emu {
 constexpr int kDigitBits = 7;      // digits in [-127, 127]: exact in BF16, products < 2^14
 constexpr int kMaxSlices = 9;      // s * kDigitBits <= 63 bits of the scaled magnitude
 constexpr int kBK = 64;            // k elements per pipeline stage (128 bytes of BF16)
-constexpr int kChunkBlocks = 4;    // k-blocks per exact FP32 chunk: 256 * 127^2 < 2^22
+constexpr int kChunkBlocks = 16;   // k-blocks per exact FP32 chunk: 1024 * 127^2 < 2^24
 constexpr int kSegBlocks = 128;    // k-blocks per integer level segment: 9 * 8192 * 127^2 < 2^31
 constexpr int kExpEmpty = (int)0x80808080;  // exponent of a row/column with no non-zero entry
 
@@ -39,8 +39,12 @@ struct Workspace {
   float* stats;     // [4] min mu, min nu, any bad row, any bad column
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
+  double* scratch;  // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
+  int scratch_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
 };
+
+constexpr int kMaxPairCtas = 256;  // scratch slots reserved for the two-SM kernel (128 pairs)
 
 // bytes needed for (m, n, k, s) and, when base != nullptr, the pointers into it
 size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws);

@@ -7,17 +7,18 @@
 //               128 x 64 tile of digit slice t of op(A) and the BN x 64 tile of slice
 //               g-t of op(B)^T (128-byte swizzle) into a kStages-deep ring;
 //   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per k-block into one
-//               of two TMEM accumulators; a chunk of kChunkBlocks k-blocks (256 k) is
+//               of two TMEM accumulators; a chunk of kChunkBlocks k-blocks (1024 k) is
 //               accumulated from zero, so every FP32 partial sum is an integer below
-//               2^22 and exact;
+//               2^24 and exact;
 //   warps 2..9  epilogue: drain each finished chunk from TMEM (tcgen05.ld) and add it
-//               exactly into 32-bit integer registers (x + 1.5*2^23 exposes x in the
-//               low mantissa bits), so the MMA runs on while a chunk is drained; at
+//               exactly into 32-bit integer registers (cvt.rni.s32.f32 of an exact
+//               integer), so the MMA runs on while a chunk is drained; at
 //               the end of a level segment, C := fma(alpha 2^(tau_j - g b), P 2^sigma_i, C)
 //               with one FP64 fma per element, coalesced down the columns of C.
 // All waits are bounded (2 s); a wait that gives up sets the device error word and
 // the kernel runs to its end without hanging.
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "emu.cuh"
@@ -30,8 +31,6 @@ constexpr int kBM = 128;
 constexpr int kStages = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr uint32_t kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
-constexpr float kMagic = 12582912.0f;
 constexpr int kTmemCols = 512;
 
 template <int BN>
@@ -54,6 +53,7 @@ struct Args {
   int nkb;      // k-blocks of kBK
   int tiles_m;  // row tiles
   int num_tiles;
+  int group_m;  // rasterisation: consecutive tiles walk group_m row tiles, then the next column
   double alpha, beta;
   double* C;
   int64_t ldc;
@@ -61,6 +61,7 @@ struct Args {
   const int* sigB;
   const int* badA;
   const int* badB;
+  double* scratch;  // two-SM kernel: one 128 x 256 FP64 slot per CTA
   unsigned int* err;
 };
 
@@ -136,6 +137,28 @@ __device__ __forceinline__ double scaled_int(int32_t P, int sigma) {
   return __longlong_as_double((long long)bits);
 }
 
+// Tile order: the CTAs that run at the same time take consecutive tile indices;
+// grouping group_m row tiles per column makes that set a near-square block, so the
+// slices of A and B it streams are shared in L2 instead of re-read from HBM.
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int group_m, int num_tiles, int& tm, int& tn) {
+  const int tiles_n = num_tiles / tiles_m;
+  const int group = tile / (group_m * tiles_n);
+  const int first_m = group * group_m;
+  const int gm = min(tiles_m - first_m, group_m);
+  const int local = tile - group * group_m * tiles_n;
+  tm = first_m + local % gm;
+  tn = local / gm;
+}
+
+// Row tiles per raster group: the `concurrent` tiles in flight cover about
+// group x concurrent/group tiles of bm x bn, near-square when group*bm ~ (concurrent/group)*bn.
+int group_rows(int concurrent, int bm, int bn, int tiles_m) {
+  int g = 1;
+  while ((2 * g) * (2 * g) * bm <= concurrent * bn) g *= 2;  // g ~ sqrt(concurrent * bn / bm), a power of two
+  if (g > tiles_m) g = tiles_m;
+  return g < 1 ? 1 : g;
+}
+
 // number of MMA chunks of level-segment (g, seg0..seg0+segn)
 __device__ __forceinline__ int chunks_of(int g, int segn) {
   return ((g - 1) * segn + kChunkBlocks - 1) / kChunkBlocks;
@@ -190,7 +213,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
       for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-        const int m0 = (tile % p.tiles_m) * kBM, n0 = (tile / p.tiles_m) * BN;
+        int tm, tn;
+        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        const int m0 = tm * kBM, n0 = tn * BN;
         for (int g = s + 1; g >= 2; --g)
           for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
             const int segn = min(kSegBlocks, p.nkb - seg0);
@@ -253,7 +278,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t chunk = 0;
     uint32_t acc[kCols];
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-      const int64_t m0 = (int64_t)(tile % p.tiles_m) * kBM, n0 = (int64_t)(tile / p.tiles_m) * BN;
+      int tm, tn;
+      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+      const int64_t m0 = (int64_t)tm * kBM, n0 = (int64_t)tn * BN;
       const int64_t i = m0 + row;
       const bool row_ok = i < p.m;
       int sig_i = 0;
@@ -280,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t v[16];
               tmem_ld_16(taddr + q * 16, v);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float_as_uint(__uint_as_float(v[j]) + kMagic);
+              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
@@ -301,14 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           epi_bar_sync();
-          const uint32_t bias = (uint32_t)nch * kMagicBits;
           if (row_ok) {
             double* cptr = p.C + (n0 + col0) * p.ldc + i;
 #pragma unroll
             for (int c = 0; c < kCols; ++c) {
               const int64_t j = n0 + col0 + c;
               if (j < p.n) {
-                const int32_t P = (int32_t)(acc[c] - bias);
+                const int32_t P = (int32_t)acc[c];
                 const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P, sig_i);
                 double w;
                 if (first) w = (p.beta == 0.0) ? 0.0 : p.beta * cptr[(int64_t)c * p.ldc];
@@ -329,6 +355,349 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTmemCols)
                  : "memory");
   }
+}
+
+// =====================================================================================
+// Two-SM variant (tcgen05 cta_group::2): a CTA pair computes a 256 x 256 tile, each
+// SM holding 128 rows x 256 columns in its TMEM (two accumulators of 256 columns).
+// Each CTA loads its own 128 rows of the A slice and 128 of the 256 rows of the B
+// slice; the leader's MMA reads both CTAs' shared memory.  Between level
+// segments the FP64 running sum of each CTA's 128 x 256 block lives in a private
+// scratch slot of the workspace, laid out so that every warp access is 256
+// contiguous bytes and each warp sweeps 32 KiB in order; C itself is read once
+// (beta*C0) and written once per tile.
+// =====================================================================================
+constexpr int k2Stages = 6;
+constexpr int k2BM = 256;  // pair tile rows (128 per CTA)
+constexpr int k2BN = 256;  // pair tile columns (128 rows of op(B)^T loaded per CTA)
+constexpr int k2ColsPerThread = 128;
+
+struct Smem2 {
+  static constexpr int kABytes = 128 * kBK * 2;  // 16 KiB
+  static constexpr int kBBytes = 128 * kBK * 2;  // 16 KiB
+  static constexpr int kOffA = 0;
+  static constexpr int kOffB = kOffA + k2Stages * kABytes;
+  static constexpr int kOffBar = kOffB + k2Stages * kBBytes;
+  static constexpr int kNumBars = 2 * k2Stages + 5;
+  static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
+  static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
+  static constexpr int kBytes = kOffScale + k2BN * 8;
+  static constexpr int kAlloc = kBytes + 1024;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait with cluster-scope acquire (arrivals may come from the peer CTA)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, unsigned int* err,
+                                                  unsigned int code) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+      if (err) atomicOr(err, code);
+      return false;
+    }
+  }
+}
+// TMA load into this CTA's shared memory, completion counted on a barrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* tm, uint32_t bar_cluster_addr, int x,
+                                                 int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
+      "%4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar_cluster_addr), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive (once) on the barrier at this offset in both CTAs of the pair when the issued MMAs complete
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_slice_gemm_pair(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+  using L = Smem2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + k2Stages;
+  uint64_t* acc_full = bars + 2 * k2Stages;
+  uint64_t* acc_empty = bars + 2 * k2Stages + 2;
+  uint64_t* done = bars + 2 * k2Stages + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmemSlot);
+  double* colscale = reinterpret_cast<double*>(smem + L::kOffScale);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int s = p.slices;
+  const int num_pairs = gridDim.x / 2, pair_id = blockIdx.x / 2;
+
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    for (int i = 0; i < k2Stages; ++i) {
+      mbar_init(&full[i], 1);   // the leader's producer arrives (with both CTAs' bytes)
+      mbar_init(&empty[i], 1);  // one commit per phase, multicast to both CTAs
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 2 * 32 * kEpiWarps);  // every epilogue thread of both CTAs
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // the peer's barriers are initialised and its TMEM is allocated
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer (both CTAs) ------------------------------
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
+      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
+        int tm, tn;
+        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        const int m0 = tm * k2BM + (int)rank * 128;
+        const int nb0 = tn * k2BN + (int)rank * 128;
+        for (int g = s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, p.nkb - seg0);
+            for (int t = 1; t <= g - 1; ++t)
+              for (int kb = seg0; kb < seg0 + segn; ++kb) {
+                mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
+                if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
+                const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
+                tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, t - 1);
+                tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, g - t - 1);
+                if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
+              }
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer (leader CTA) ------------------------------
+    if (leader && lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(k2BM, k2BN);
+      uint32_t stage = 0, phase = 0, chunk = 0;
+      const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
+      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
+        for (int g = s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, p.nkb - seg0);
+            const int items = (g - 1) * segn;
+            for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
+              const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+              mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
+              tc_fence_after();
+              const uint32_t dtm = tmem_base + buf * k2BN;
+              const int i1 = min(items, i0 + kChunkBlocks);
+              for (int it = i0; it < i1; ++it) {
+                mbar_wait_cluster(&full[stage], phase, p.err, kErrWaitTma);
+                tc_fence_after();
+                const uint64_t da = smem_desc_sw128(a_base + stage * L::kABytes);
+                const uint64_t db = smem_desc_sw128(b_base + stage * L::kBBytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                  umma_bf16_pair(dtm, da + 2 * kk, db + 2 * kk, idesc, (it > i0 || kk > 0) ? 1u : 0u);
+                umma_commit_pair(&empty[stage]);  // frees this stage in both CTAs
+                if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
+              }
+              umma_commit_pair(&acc_full[buf]);  // chunk complete in both CTAs' TMEM
+            }
+          }
+      }
+      umma_commit_pair(done);
+      mbar_wait_cluster(done, 0, p.err, kErrWaitMma);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------ epilogue (both CTAs) ------------------------------
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const int row = quad * 32 + lane;
+    const int col0 = half * k2ColsPerThread;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    // this thread's column sweep in the CTA's scratch slot: 256 contiguous bytes per warp per column
+    double* scr = p.scratch + (int64_t)blockIdx.x * (128 * k2BN) + (int64_t)((half * 4 + quad) * k2ColsPerThread) * 32 +
+                  lane;
+    uint32_t chunk = 0;
+    uint32_t acc[k2ColsPerThread];
+    uint32_t empty_remote[2];
+    empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
+    empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
+    for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
+      int tm, tn;
+      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+      const int64_t m0 = (int64_t)tm * k2BM + rank * 128;
+      const int64_t n0 = (int64_t)tn * k2BN;
+      const int64_t i = m0 + row;
+      const bool row_ok = i < p.m;
+      int sig_i = 0;
+      bool bad_i = false;
+      if (row_ok) {
+        sig_i = p.sigA[i];
+        if (sig_i == kExpEmpty) sig_i = 0;
+        bad_i = p.badA[i] != 0;
+      }
+      bool first = true;
+      for (int g = s + 1; g >= 2; --g)
+        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, p.nkb - seg0);
+          const int nch = chunks_of(g, segn);
+          const bool last = (g == 2) && (seg0 + kSegBlocks >= p.nkb);
+#pragma unroll
+          for (int c = 0; c < k2ColsPerThread; ++c) acc[c] = 0u;
+          for (int ci = 0; ci < nch; ++ci, ++chunk) {
+            const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+            mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + lane_base + buf * k2BN + col0;
+#pragma unroll
+            for (int q = 0; q < k2ColsPerThread / 16; ++q) {
+              uint32_t v[16];
+              tmem_ld_16(taddr + q * 16, v);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
+            }
+            tc_fence_before();
+            mbar_arrive_remote(empty_remote[buf]);
+          }
+          // level-segment end: column scales, then W := fma(scale_j, P 2^sigma_i, W)
+          epi_bar_sync();
+          {
+            const int idx = ew * 32 + lane;
+            if (idx < k2BN) {
+              const int64_t j = n0 + idx;
+              double cs = 0.0;
+              if (j < p.n) {
+                int tau = p.sigB[j];
+                if (tau == kExpEmpty) tau = 0;
+                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - g * kDigitBits);
+              }
+              colscale[idx] = cs;
+            }
+          }
+          epi_bar_sync();
+          double* crow = p.C + (n0 + col0) * p.ldc + i;
+#pragma unroll
+          for (int c = 0; c < k2ColsPerThread; ++c) {
+            const bool col_ok = row_ok && n0 + col0 + c < p.n;
+            double w;
+            if (first) w = (p.beta != 0.0 && col_ok) ? p.beta * crow[(int64_t)c * p.ldc] : 0.0;
+            else w = scr[c * 32];
+            const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int((int32_t)acc[c], sig_i);
+            const double r = fma(colscale[col0 + c], x, w);
+            if (last) {
+              if (col_ok) crow[(int64_t)c * p.ldc] = r;
+            } else {
+              scr[c * 32] = r;
+            }
+          }
+          first = false;
+        }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // neither CTA leaves while the pair still uses its shared memory
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTmemCols)
+                 : "memory");
+  }
+}
+
+int launch_pair(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t stream) {
+  using L = Smem2;
+  CUtensorMap tmA, tmB;
+  memset(&tmA, 0, sizeof(tmA));
+  memset(&tmB, 0, sizeof(tmB));
+  const uint64_t dA[3] = {(uint64_t)gp.k, (uint64_t)gp.m, (uint64_t)gp.slices};
+  const uint64_t pA[2] = {(uint64_t)ws.kp * 2, (uint64_t)gp.m * ws.kp * 2};
+  const uint32_t bA[3] = {(uint32_t)kBK, 128u, 1u};
+  int rc = encode_tmap(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  const uint64_t dB[3] = {(uint64_t)gp.k, (uint64_t)gp.n, (uint64_t)gp.slices};
+  const uint64_t pB[2] = {(uint64_t)ws.kp * 2, (uint64_t)gp.n * ws.kp * 2};
+  const uint32_t bB[3] = {(uint32_t)kBK, 128u, 1u};
+  rc = encode_tmap(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+
+  Args a;
+  a.m = gp.m; a.n = gp.n; a.k = gp.k;
+  a.slices = gp.slices;
+  a.nkb = (int)((gp.k + kBK - 1) / kBK);
+  a.tiles_m = (int)((gp.m + k2BM - 1) / k2BM);
+  const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + k2BN - 1) / k2BN);
+  if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
+  a.num_tiles = (int)tiles;
+  int64_t pairs = tiles < sms / 2 ? tiles : sms / 2;
+  if (pairs > ws.scratch_ctas / 2) pairs = ws.scratch_ctas / 2;
+  if (pairs < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the two-SM kernel");
+  a.group_m = group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
+  a.alpha = gp.alpha; a.beta = gp.beta;
+  a.C = gp.C; a.ldc = gp.ldc;
+  a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
+  a.scratch = ws.scratch;
+  a.err = device_error_word();
+
+  cudaError_t e = cudaFuncSetAttribute(k_slice_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm pair)");
+  k_slice_gemm_pair<<<(unsigned)(2 * pairs), kThreads, L::kAlloc, stream>>>(a, tmA, tmB);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm pair launch");
 }
 
 template <int BN>
@@ -356,6 +725,7 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + BN - 1) / BN);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
+  a.group_m = group_rows(sms, kBM, BN, a.tiles_m);
   a.alpha = gp.alpha; a.beta = gp.beta;
   a.C = gp.C; a.ldc = gp.ldc;
   a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
@@ -377,6 +747,13 @@ int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t st
   int rc = current_device(nullptr, &sms);
   if (rc) return rc;
   if (gp.m == 0 || gp.n == 0) return GBD_OK;
+  // GBD_EMU_KERNEL=pair|single overrides the choice below (tests and tuning)
+  const char* force = getenv("GBD_EMU_KERNEL");
+  if (force && force[0] == 'p') return launch_pair(gp, ws, sms, stream);
+  const bool single = force && force[0] == 's';
+  // enough 256 x 128 pair tiles to occupy every SM pair: the two-SM kernel
+  const int64_t pair_tiles = ((gp.m + k2BM - 1) / k2BM) * ((gp.n + k2BN - 1) / k2BN);
+  if (!single && pair_tiles >= sms / 2) return launch_pair(gp, ws, sms, stream);
   const int64_t tiles256 = ((gp.m + kBM - 1) / kBM) * ((gp.n + 255) / 256);
   if (tiles256 >= sms) return launch_bn<256>(gp, ws, sms, stream);
   return launch_bn<128>(gp, ws, sms, stream);

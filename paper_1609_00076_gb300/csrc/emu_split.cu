@@ -263,6 +263,10 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws)
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
+  // one 128 x 256 FP64 slot per CTA of the two-SM kernel (at most one pair per 256 x 256 tile)
+  const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
+  const int scratch_ctas = (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas);
+  const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -274,6 +278,8 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws)
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
+    ws->scratch = reinterpret_cast<double*>(b + o_scr);
+    ws->scratch_ctas = scratch_ctas;
     ws->kp = kp;
   }
   return off;

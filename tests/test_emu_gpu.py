@@ -91,8 +91,15 @@ def test_tiles_integers_bit_exact(oracle_mod, m, n, k):
 
 
 # --- bit-exact against the CPU model of the method ---
+@pytest.fixture(params=["single", "pair"])
+def kernel(request, monkeypatch):
+    """Runs the test once with the one-SM slice kernel and once with the two-SM (cta_group::2) one."""
+    monkeypatch.setenv("GBD_EMU_KERNEL", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("slices", [1, 2, 3, 5, 7, 9])
-def test_model_parity_slices(oracle_mod, slices):
+def test_model_parity_slices(oracle_mod, slices, kernel):
     m, n, k = 200, 300, 333
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "scaled", 10 + slices, pads=(3, 1, 2), e=6)
     out, info = run_emu("N", "N", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, slices=slices)
@@ -101,7 +108,7 @@ def test_model_parity_slices(oracle_mod, slices):
 
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
-def test_model_parity_transposes(oracle_mod, ta, tb):
+def test_model_parity_transposes(oracle_mod, ta, tb, kernel):
     m, n, k = 257, 129, 515
     A, lda, B, ldb, C, ldc = _problem(ta, tb, m, n, k, "uniform", 40, pads=(8, 8, 8))
     out, _ = run_emu(ta, tb, m, n, k, -1.25, A, lda, B, ldb, 0.75, C, ldc, slices=6)
@@ -110,13 +117,13 @@ def test_model_parity_transposes(oracle_mod, ta, tb):
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 3, 7), (127, 129, 63), (129, 255, 65), (64, 700, 1000),
                                    (1000, 33, 129)])
-def test_model_parity_fringes(oracle_mod, m, n, k):
+def test_model_parity_fringes(oracle_mod, m, n, k, kernel):
     A, lda, B, ldb, C, ldc = _problem("T", "N", m, n, k, "uniform", m * 3 + n + k, pads=(1, 3, 5))
     out, _ = run_emu("T", "N", m, n, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, slices=4)
     check_model(oracle_mod, "T", "N", m, n, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, out, 4)
 
 
-def test_model_parity_two_k_segments(oracle_mod):
+def test_model_parity_two_k_segments(oracle_mod, kernel):
     # k > 8192: every level is summed in two integer segments
     m, n, k = 130, 140, 8192 + 200
     A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "uniform", 77)
@@ -124,11 +131,11 @@ def test_model_parity_two_k_segments(oracle_mod):
     check_model(oracle_mod, "N", "T", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, out, 3)
 
 
-def test_adversarial_exact_accumulation(oracle_mod):
-    # every digit of every entry is +127 or -127, one sign per half of k: the FP32 chunk sums reach
-    # 256 * 127^2 = 4129024 (< 2^22), the largest the method allows; any inexact tensor-core
-    # accumulation shows as a mismatch with the exact model
-    m, n, k = 128, 256, 1024
+def test_adversarial_exact_accumulation(oracle_mod, kernel):
+    # every digit of every entry is +127 or -127, one sign per half of k: each 1024-deep FP32 chunk
+    # sums to 1024 * 127^2 = 16516096 (< 2^24), the largest the method allows; any inexact
+    # tensor-core accumulation shows as a mismatch with the exact model
+    m, n, k = 128, 256, 2048
     x = 1.0 - 2.0 ** -53  # binary 0.111...1: every 7-bit digit is 127
     A = np.full(m * k, x)
     A[: m * k // 2] = -x
@@ -145,7 +152,7 @@ def test_adversarial_exact_accumulation(oracle_mod):
     check_bound(oracle_mod, "N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, out, exact=True)
 
 
-def test_nonfinite_rows_and_columns(oracle_mod):
+def test_nonfinite_rows_and_columns(oracle_mod, kernel):
     m, n, k = 140, 150, 90
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "uniform", 9)
     A[5 * lda + 7] = np.inf     # row 7 of op(A)
@@ -234,6 +241,16 @@ def test_quick_returns_and_errors():
     assert gbdgemm.gbd_dgemm_emu("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, 10, 0.0, ws, wsb) == \
         gbdgemm.GBD_ERR_ARG
     assert gbdgemm.gbd_dgemm_emu("N", "N", m, n, k, 1.0, dA, m - 1, dB, k, 0.0, dC, m, 3, 0.0, ws, wsb) == 8
+
+
+def test_pair_and_single_kernels_agree(monkeypatch):
+    m, n, k = 700, 900, 1300
+    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "scaled", 8, e=20)
+    monkeypatch.setenv("GBD_EMU_KERNEL", "single")
+    o1, _ = run_emu("N", "T", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, slices=8)
+    monkeypatch.setenv("GBD_EMU_KERNEL", "pair")
+    o2, _ = run_emu("N", "T", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, slices=8)
+    assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64))
 
 
 def test_deterministic():
