@@ -39,7 +39,8 @@ struct Workspace {
   float* stats;     // [4] min mu, min nu, any bad row, any bad column
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
-  double* scratch;  // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
+  double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
+  int32_t* scratch_p;  // [scratch_ctas][128 * 256] parked integer level sums of the two-SM kernel
   int scratch_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
 };

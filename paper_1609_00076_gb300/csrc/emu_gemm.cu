@@ -61,7 +61,8 @@ struct Args {
   const int* sigB;
   const int* badA;
   const int* badB;
-  double* scratch;  // two-SM kernel: one 128 x 256 FP64 slot per CTA
+  double* scratch;     // two-SM kernel: one 128 x 256 FP64 slot per CTA (running sums)
+  int32_t* scratch_p;  // two-SM kernel: one 128 x 256 int32 slot per CTA (pending level sums)
   unsigned int* err;
 };
 
@@ -381,7 +382,7 @@ struct Smem2 {
   static constexpr int kNumBars = 2 * k2Stages + 5;
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
   static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
-  static constexpr int kBytes = kOffScale + k2BN * 8;
+  static constexpr int kBytes = kOffScale + 2 * k2BN * 8;  // two colscale buffers
   static constexpr int kAlloc = kBytes + 1024;
 };
 
@@ -562,20 +563,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------ epilogue (both CTAs) ------------------------------
+    // The FP64 update of a finished level segment is deferred: its integer sums are
+    // parked in scratch and folded into the running sums a few columns at a time
+    // while the next segment's chunks are drained, so the MMA never waits for it.
     const int ew = warp - 2;
     const int quad = warp & 3;
     const int half = ew >> 2;
     const int row = quad * 32 + lane;
     const int col0 = half * k2ColsPerThread;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    // this thread's column sweep in the CTA's scratch slot: 256 contiguous bytes per warp per column
-    double* scr = p.scratch + (int64_t)blockIdx.x * (128 * k2BN) + (int64_t)((half * 4 + quad) * k2ColsPerThread) * 32 +
-                  lane;
+    // this thread's column sweep in the CTA's scratch slots: 256 (or 128) contiguous bytes per warp per column
+    const int64_t slot = (int64_t)blockIdx.x * (128 * k2BN) + (int64_t)((half * 4 + quad) * k2ColsPerThread) * 32 + lane;
+    double* scrW = p.scratch + slot;
+    int32_t* scrP = p.scratch_p + slot;
     uint32_t chunk = 0;
     uint32_t acc[k2ColsPerThread];
     uint32_t empty_remote[2];
     empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
     empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
+    // the pending update
+    bool pd_active = false, pd_first = false, pd_last = false, pd_bad = false, pd_row_ok = false;
+    int pd_done = 0, pd_sig = 0, pd_buf = 0, cs_next = 0;
+    double* pd_crow = nullptr;
+    int64_t pd_cols_left = 0;  // columns of the pending tile inside C (n - n0 - col0, clamped)
+    auto advance = [&](int ncols) {
+      const int c1 = min(pd_done + ncols, k2ColsPerThread);
+      const double* cs = colscale + pd_buf * k2BN + col0;
+      for (int c = pd_done; c < c1; ++c) {
+        const bool col_ok = pd_row_ok && c < pd_cols_left;
+        double w;
+        if (pd_first) w = (p.beta != 0.0 && col_ok) ? p.beta * pd_crow[(int64_t)c * p.ldc] : 0.0;
+        else w = scrW[c * 32];
+        const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(scrP[c * 32], pd_sig);
+        const double r = fma(cs[c], x, w);
+        if (pd_last) {
+          if (col_ok) pd_crow[(int64_t)c * p.ldc] = r;
+        } else {
+          scrW[c * 32] = r;
+        }
+      }
+      pd_done = c1;
+      if (pd_done >= k2ColsPerThread) pd_active = false;
+    };
     for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
       int tm, tn;
       tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
@@ -596,6 +625,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           const int segn = min(kSegBlocks, p.nkb - seg0);
           const int nch = chunks_of(g, segn);
           const bool last = (g == 2) && (seg0 + kSegBlocks >= p.nkb);
+          const int portion = (k2ColsPerThread + nch - 1) / nch;  // spread the pending update over this segment
 #pragma unroll
           for (int c = 0; c < k2ColsPerThread; ++c) acc[c] = 0u;
           for (int ci = 0; ci < nch; ++ci, ++chunk) {
@@ -612,9 +642,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             mbar_arrive_remote(empty_remote[buf]);
+            if (pd_active) advance(portion);
           }
-          // level-segment end: column scales, then W := fma(scale_j, P 2^sigma_i, W)
-          epi_bar_sync();
+          // segment end: finish the previous pending update, then park this one
+          if (pd_active) advance(k2ColsPerThread);
+          epi_bar_sync();  // nobody reads the colscale buffer about to be rewritten
           {
             const int idx = ew * 32 + lane;
             if (idx < k2BN) {
@@ -625,28 +657,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 if (tau == kExpEmpty) tau = 0;
                 cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - g * kDigitBits);
               }
-              colscale[idx] = cs;
+              colscale[cs_next * k2BN + idx] = cs;
             }
           }
           epi_bar_sync();
-          double* crow = p.C + (n0 + col0) * p.ldc + i;
 #pragma unroll
-          for (int c = 0; c < k2ColsPerThread; ++c) {
-            const bool col_ok = row_ok && n0 + col0 + c < p.n;
-            double w;
-            if (first) w = (p.beta != 0.0 && col_ok) ? p.beta * crow[(int64_t)c * p.ldc] : 0.0;
-            else w = scr[c * 32];
-            const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int((int32_t)acc[c], sig_i);
-            const double r = fma(colscale[col0 + c], x, w);
-            if (last) {
-              if (col_ok) crow[(int64_t)c * p.ldc] = r;
-            } else {
-              scr[c * 32] = r;
-            }
-          }
+          for (int c = 0; c < k2ColsPerThread; ++c) scrP[c * 32] = (int32_t)acc[c];
+          pd_active = true;
+          pd_done = 0;
+          pd_first = first;
+          pd_last = last;
+          pd_bad = bad_i;
+          pd_row_ok = row_ok;
+          pd_sig = sig_i;
+          pd_buf = cs_next;
+          pd_crow = p.C + (n0 + col0) * p.ldc + i;
+          pd_cols_left = p.n - n0 - col0;
+          cs_next ^= 1;
           first = false;
         }
     }
+    if (pd_active) advance(k2ColsPerThread);  // the last level of the last tile
   }
 
   tc_fence_before();
@@ -691,6 +722,7 @@ int launch_pair(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t
   a.C = gp.C; a.ldc = gp.ldc;
   a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
   a.scratch = ws.scratch;
+  a.scratch_p = ws.scratch_p;
   a.err = device_error_word();
 
   cudaError_t e = cudaFuncSetAttribute(k_slice_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);

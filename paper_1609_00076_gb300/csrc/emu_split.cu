@@ -267,6 +267,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws)
   const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
   const int scratch_ctas = (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas);
   const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
+  const size_t o_scp = off; off = up(off + sizeof(int32_t) * 128 * 256 * (size_t)scratch_ctas);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -279,6 +280,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws)
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);
+    ws->scratch_p = reinterpret_cast<int32_t*>(b + o_scp);
     ws->scratch_ctas = scratch_ctas;
     ws->kp = kp;
   }
