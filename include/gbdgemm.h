@@ -133,6 +133,75 @@ GBD_API int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_
                           double* C, int64_t ldc, int slices, double tol, void* workspace,
                           size_t workspace_bytes, gbd_emu_info* info, void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Grouped calls: many independent problems per launch                       */
+/* ------------------------------------------------------------------------- */
+#define GBD_MODE_NATIVE 0    /* FP64 mma.sync, as gbd_dgemm */
+#define GBD_MODE_EMULATED 1  /* split digits on tcgen05, as gbd_dgemm_emu */
+
+/* One problem of a grouped call: the dgemm argument list of Section 1.2 plus how
+ * to compute it.  Pointers are device pointers owned by the caller; problems must
+ * not write overlapping parts of C. */
+typedef struct gbd_problem {
+  char transa, transb;
+  int32_t mode;    /* GBD_MODE_NATIVE or GBD_MODE_EMULATED */
+  int32_t slices;  /* emulated: 1..9, or 0 = automatic (chosen when the plan is created) */
+  int32_t tile;    /* native: CTA tile edge 32 or 64, or 0 = library default (autotuner hook) */
+  int64_t m, n, k;
+  double alpha, beta;
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+  double tol;      /* emulated, automatic slices: target relative error (<= 0: 2 k 2^-53) */
+} gbd_problem;
+
+/* Opaque host-side plan of a grouped call (problem tables live in the workspace). */
+typedef struct gbd_plan gbd_plan;
+
+/*
+ * Bytes of device workspace for a grouped call over `probs` (host-only; needs no
+ * GPU).  Emulated problems with slices == 0 are sized for 9 slices.
+ */
+GBD_API size_t gbd_dgemm_grouped_workspace_size(const gbd_problem* probs, int count);
+
+/*
+ * Builds a plan: validates every problem, lays out `workspace` (caller-owned,
+ * 256-byte aligned, at least gbd_dgemm_grouped_workspace_size bytes), chooses
+ * automatic slice counts from the data present now (synchronising `stream`), and
+ * copies the problem tables to the device.  Native problems are ordered longest
+ * tile first for the atomic tile counter; emulated ones by decreasing tile cost.
+ * slices_used: optional array of `count` ints, receives each emulated problem's
+ * slice count (0 for native problems and quick returns).
+ * Returns 0, GBD_ERR_ARG (gbd_last_error names the problem and the BLAS argument
+ * index), GBD_ERR_WORKSPACE, GBD_ERR_LIMIT or GBD_ERR_CUDA.  Waits for `stream`.
+ */
+GBD_API int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace,
+                                    size_t workspace_bytes, int* slices_used, void* stream,
+                                    gbd_plan** plan);
+
+/*
+ * Runs a plan on `stream`: for emulated problems their exponent and split kernels
+ * and one persistent slice-product launch over all their tiles; for native
+ * problems (and every quick return) one persistent FP64-MMA launch whose CTAs take
+ * tiles from an atomic counter.  Only kernel launches and memsets are issued, so
+ * the call may be captured in a CUDA graph and replayed while the plan, the
+ * workspace and the problems' buffers stay alive; each run reads A, B, C afresh.
+ * A problem's result is bit-identical to the single-problem call with the same
+ * arguments (and, when emulated, the same slice count).  Asynchronous.
+ */
+GBD_API int gbd_grouped_plan_run(gbd_plan* plan, void* stream);
+
+/* Frees the host side of a plan (never the workspace). */
+GBD_API void gbd_grouped_plan_destroy(gbd_plan* plan);
+
+/* Create, run and destroy a plan in one call (synchronises `stream` while the
+ * plan is created). */
+GBD_API int gbd_dgemm_grouped(const gbd_problem* probs, int count, void* workspace,
+                              size_t workspace_bytes, int* slices_used, void* stream);
+
 /*
  * Reads and clears the device error word of the current device that the
  * kernels set when a bounded wait gives up.  Synchronises `stream` first.

@@ -48,7 +48,9 @@ struct Workspace {
 constexpr int kMaxPairCtas = 256;  // scratch slots reserved for the two-SM kernel (128 pairs)
 
 // bytes needed for (m, n, k, s) and, when base != nullptr, the pointers into it
-size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws);
+size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws, bool pair_scratch = true);
+// smallest slice count whose estimated componentwise relative bound is <= tol
+int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* bound);
 
 // Rows r of op(X) (R rows, K columns): element (r, p) is X[p*ld + r] when rows_contig,
 // X[r*ld + p] otherwise.
@@ -73,6 +75,27 @@ struct GemmParams {
   const int* badB;
 };
 int launch_slice_gemm(const GemmParams& p, const Workspace& ws, cudaStream_t s);
+
+// One problem of a grouped launch of the one-SM slice kernel (device table entry).
+struct EmuTableEntry {  // CUtensorMap members keep it 64-byte aligned
+  CUtensorMap tmA;  // digit slices of op(A): dims {k, m, s}, box {64, 128, 1}
+  CUtensorMap tmB;  // digit slices of op(B)^T: dims {k, n, s}, box {64, BN, 1}
+  int64_t m, n, k, ldc;
+  double alpha, beta;
+  double* C;
+  const int* sigA;
+  const int* sigB;
+  const int* badA;
+  const int* badB;
+  int64_t tile_begin;  // first index of this problem in the grouped tile sequence
+  int slices, nkb, tiles_m, group_m, num_tiles, pad;
+};
+constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
+
+// tensor maps of one problem's slices for the grouped kernel
+int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
+// one launch over all problems of a device table (entries sorted by decreasing tile cost)
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t s);
 
 }  // namespace emu
 }  // namespace gbd

@@ -165,9 +165,56 @@ __device__ __forceinline__ int chunks_of(int g, int segn) {
   return ((g - 1) * segn + kChunkBlocks - 1) / kChunkBlocks;
 }
 
-template <int BN>
+// One output tile's view of its problem: the single-problem launch takes it from the
+// kernel arguments, the grouped launch from a table in global memory.
+struct Job {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  int m0, n0;
+  int s, nkb;
+  int64_t m, n, ldc;
+  double alpha, beta;
+  double* C;
+  const int* sigA;
+  const int* sigB;
+  const int* badA;
+  const int* badB;
+};
+
+template <int BN, bool TABLE>
+__device__ __forceinline__ void get_job(const Args& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                        const EmuTableEntry* table, int count, int tile, Job& j) {
+  int tm, tn;
+  if (!TABLE) {
+    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    j.tmA = tmA; j.tmB = tmB;
+    j.s = p.slices; j.nkb = p.nkb;
+    j.m = p.m; j.n = p.n; j.ldc = p.ldc;
+    j.alpha = p.alpha; j.beta = p.beta; j.C = p.C;
+    j.sigA = p.sigA; j.sigB = p.sigB; j.badA = p.badA; j.badB = p.badB;
+  } else {
+    int lo = 0, hi = count - 1;  // last entry whose first tile is <= tile
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (table[mid].tile_begin <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    const EmuTableEntry& e = table[lo];
+    tile_coords((int)(tile - e.tile_begin), e.tiles_m, e.group_m, e.num_tiles, tm, tn);
+    j.tmA = &e.tmA; j.tmB = &e.tmB;
+    j.s = e.slices; j.nkb = e.nkb;
+    j.m = e.m; j.n = e.n; j.ldc = e.ldc;
+    j.alpha = e.alpha; j.beta = e.beta; j.C = e.C;
+    j.sigA = e.sigA; j.sigB = e.sigB; j.badA = e.badA; j.badB = e.badB;
+  }
+  j.m0 = tm * kBM;
+  j.n0 = tn * BN;
+}
+
+template <int BN, bool TABLE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const EmuTableEntry* __restrict__ table, int count, int total_tiles) {
   using L = SmemLayout<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -181,11 +228,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   double* colscale = reinterpret_cast<double*>(smem + L::kOffScale);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = p.slices;
+  const int ntiles = TABLE ? total_tiles : p.num_tiles;
 
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+    if (!TABLE) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+    }
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
@@ -213,19 +262,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
-      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-        int tm, tn;
-        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-        const int m0 = tm * kBM, n0 = tn * BN;
-        for (int g = s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-            const int segn = min(kSegBlocks, p.nkb - seg0);
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        Job j;
+        get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+        if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tmA) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tmB) : "memory");
+        }
+        const int m0 = j.m0, n0 = j.n0;
+        for (int g = j.s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, j.nkb - seg0);
             for (int t = 1; t <= g - 1; ++t)
               for (int kb = seg0; kb < seg0 + segn; ++kb) {
                 mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
                 mbar_arrive_expect_tx(&full[stage], bytes);
-                tma_load_3d(smem + L::kOffA + stage * L::kABytes, &tmA, &full[stage], kb * kBK, m0, t - 1);
-                tma_load_3d(smem + L::kOffB + stage * L::kBBytes, &tmB, &full[stage], kb * kBK, n0, g - t - 1);
+                tma_load_3d(smem + L::kOffA + stage * L::kABytes, j.tmA, &full[stage], kb * kBK, m0, t - 1);
+                tma_load_3d(smem + L::kOffB + stage * L::kBBytes, j.tmB, &full[stage], kb * kBK, n0, g - t - 1);
                 if (++stage == kStages) { stage = 0; phase ^= 1u; }
               }
           }
@@ -238,10 +291,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-        for (int g = s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-            const int segn = min(kSegBlocks, p.nkb - seg0);
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        Job j;
+        get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+        for (int g = j.s + 1; g >= 2; --g)
+          for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+            const int segn = min(kSegBlocks, j.nkb - seg0);
             const int items = (g - 1) * segn;
             for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
               const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
@@ -278,23 +333,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int col0 = half * kCols;
     uint32_t chunk = 0;
     uint32_t acc[kCols];
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-      int tm, tn;
-      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-      const int64_t m0 = (int64_t)tm * kBM, n0 = (int64_t)tn * BN;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      Job j;
+      get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+      const int64_t m0 = j.m0, n0 = j.n0;
       const int64_t i = m0 + row;
-      const bool row_ok = i < p.m;
+      const bool row_ok = i < j.m;
       int sig_i = 0;
       bool bad_i = false;
       if (row_ok) {
-        sig_i = p.sigA[i];
+        sig_i = j.sigA[i];
         if (sig_i == kExpEmpty) sig_i = 0;
-        bad_i = p.badA[i] != 0;
+        bad_i = j.badA[i] != 0;
       }
       bool first = true;
-      for (int g = s + 1; g >= 2; --g)
-        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-          const int segn = min(kSegBlocks, p.nkb - seg0);
+      for (int g = j.s + 1; g >= 2; --g)
+        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, j.nkb - seg0);
           const int nch = chunks_of(g, segn);
 #pragma unroll
           for (int c = 0; c < kCols; ++c) acc[c] = 0u;
@@ -318,29 +373,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           {
             const int idx = ew * 32 + lane;
             if (idx < BN) {
-              const int64_t j = n0 + idx;
+              const int64_t jc = n0 + idx;
               double cs = 0.0;
-              if (j < p.n) {
-                int tau = p.sigB[j];
+              if (jc < j.n) {
+                int tau = j.sigB[jc];
                 if (tau == kExpEmpty) tau = 0;
-                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - g * kDigitBits);
+                cs = j.badB[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - g * kDigitBits);
               }
               colscale[idx] = cs;
             }
           }
           epi_bar_sync();
           if (row_ok) {
-            double* cptr = p.C + (n0 + col0) * p.ldc + i;
+            double* cptr = j.C + (n0 + col0) * j.ldc + i;
 #pragma unroll
             for (int c = 0; c < kCols; ++c) {
-              const int64_t j = n0 + col0 + c;
-              if (j < p.n) {
+              if (n0 + col0 + c < j.n) {
                 const int32_t P = (int32_t)acc[c];
                 const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P, sig_i);
                 double w;
-                if (first) w = (p.beta == 0.0) ? 0.0 : p.beta * cptr[(int64_t)c * p.ldc];
-                else w = cptr[(int64_t)c * p.ldc];
-                cptr[(int64_t)c * p.ldc] = fma(colscale[col0 + c], x, w);
+                if (first) w = (j.beta == 0.0) ? 0.0 : j.beta * cptr[(int64_t)c * j.ldc];
+                else w = cptr[(int64_t)c * j.ldc];
+                cptr[(int64_t)c * j.ldc] = fma(colscale[col0 + c], x, w);
               }
             }
           }
@@ -763,16 +817,48 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
   a.err = device_error_word();
 
-  auto kern = k_slice_gemm<BN>;
+  auto kern = k_slice_gemm<BN, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm)");
   const int grid = (int)(tiles < sms ? tiles : sms);
-  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, tmA, tmB);
+  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm launch");
 }
 
 }  // namespace
+
+int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e) {
+  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, (uint64_t)slices};
+  const uint64_t pA[2] = {(uint64_t)ws.kp * 2, (uint64_t)m * ws.kp * 2};
+  const uint32_t bA[3] = {(uint32_t)kBK, (uint32_t)kBM, 1u};
+  int rc = encode_tmap(&e->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, (uint64_t)slices};
+  const uint64_t pB[2] = {(uint64_t)ws.kp * 2, (uint64_t)n * ws.kp * 2};
+  const uint32_t bB[3] = {(uint32_t)kBK, (uint32_t)kGroupedBN, 1u};
+  return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream) {
+  using L = SmemLayout<kGroupedBN>;
+  if (count <= 0 || total_tiles <= 0) return GBD_OK;
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  Args a;
+  memset(&a, 0, sizeof(a));
+  a.err = device_error_word();
+  auto kern = k_slice_gemm<kGroupedBN, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped slice gemm)");
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm launch");
+}
 
 int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t stream) {
   int sms = 0;

@@ -250,7 +250,7 @@ int launch_check(const char* what) {
 
 }  // namespace
 
-size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws) {
+size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws, bool pair_scratch) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int64_t kp = (k + 7) / 8 * 8;
   size_t off = 0;
@@ -265,7 +265,8 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws)
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
   // one 128 x 256 FP64 slot per CTA of the two-SM kernel (at most one pair per 256 x 256 tile)
   const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
-  const int scratch_ctas = (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas);
+  const int scratch_ctas =
+      pair_scratch ? (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas) : 0;
   const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
   const size_t o_scp = off; off = up(off + sizeof(int32_t) * 128 * 256 * (size_t)scratch_ctas);
   if (base && ws) {

@@ -1,0 +1,375 @@
+// grouped.cu -- many independent DGEMMs (native and emulated) in one launch each.
+//
+// A plan turns a host array of problems into device tables in the caller's
+// workspace:
+//  * native problems (and every problem's BLAS quick path) go to a persistent
+//    FP64-MMA kernel whose CTAs take tiles from one atomic counter over the
+//    concatenated tile space, longest tiles (largest k) first;
+//  * emulated problems get their exponent and split kernels, then one persistent
+//    launch of the table-driven one-SM tcgen05 slice kernel over all their tiles,
+//    ordered by decreasing tile cost.
+// Every tile computes exactly what the single-problem call computes (same k
+// order, same epilogue), so a problem's result is the same bits alone and in any
+// batch.  Running a plan issues only kernel launches and memsets on the stream,
+// so it can be captured in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "emu.cuh"
+#include "native_tile.cuh"
+
+static_assert(sizeof(gbd_problem) == 112 && offsetof(gbd_problem, m) == 16 && offsetof(gbd_problem, A) == 56 &&
+                  offsetof(gbd_problem, tol) == 104,
+              "gbd_problem layout is part of the ABI");
+
+namespace gbd {
+namespace {
+
+struct NativeTableEntry {
+  NativeArgs a;
+  int64_t tile_begin;
+  int32_t ta, tb, tile, tiles_m;
+};
+
+__global__ void __launch_bounds__(kNativeThreads)
+    k_grouped_native(const NativeTableEntry* __restrict__ table, int count, int64_t total_tiles,
+                     unsigned long long* __restrict__ counter) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ long long s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();  // every thread has read s_tile
+    if (tile >= total_tiles) break;
+    int lo = 0, hi = count - 1;  // last entry whose first tile is <= tile
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (table[mid].tile_begin <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    const NativeTableEntry& e = table[lo];
+    const NativeArgs a = e.a;
+    const int64_t local = tile - e.tile_begin;
+    const int64_t tm = local % e.tiles_m, tn = local / e.tiles_m;
+    const int code = (e.ta << 2) | (e.tb << 1) | (e.tile == 32 ? 1 : 0);
+    switch (code) {
+      case 0: native_tile<false, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
+      case 1: native_tile<false, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
+      case 2: native_tile<false, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
+      case 3: native_tile<false, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
+      case 4: native_tile<true, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
+      case 5: native_tile<true, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
+      case 6: native_tile<true, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
+      default: native_tile<true, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
+    }
+  }
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int default_tile(int64_t m, int64_t n) {
+  // 32 x 32 tiles waste less on small or ragged problems; 64 x 64 carry more
+  // independent MMAs per warp.  The autotuner may override per problem.
+  return (m <= 96 || n <= 96) ? 32 : 64;
+}
+
+}  // namespace
+}  // namespace gbd
+
+struct gbd_plan {
+  // native part
+  std::vector<gbd::NativeTableEntry> native;
+  int64_t native_tiles = 0;
+  gbd::NativeTableEntry* native_dev = nullptr;
+  unsigned long long* counter_dev = nullptr;
+  // emulated part
+  struct Emu {
+    gbd_problem p;
+    int slices;
+    gbd::emu::Workspace ws;
+  };
+  std::vector<Emu> emu;
+  std::vector<gbd::emu::EmuTableEntry> emu_table;
+  gbd::emu::EmuTableEntry* emu_dev = nullptr;
+  int64_t emu_tiles = 0;
+};
+
+namespace gbd {
+namespace {
+
+// Layout of the grouped workspace; with base == nullptr only the size is computed.
+size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_override, void* base, gbd_plan* plan) {
+  size_t off = 256;  // tile counter
+  const size_t o_native = off;
+  int nnat = 0, nemu = 0;
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_EMULATED && !quick) ++nemu;
+    else ++nnat;
+  }
+  off = up256(off + sizeof(NativeTableEntry) * (size_t)nnat);
+  const size_t o_emu = off;
+  off = up256(off + sizeof(emu::EmuTableEntry) * (size_t)nemu);
+  int ei = 0;
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+    if (p.mode != GBD_MODE_EMULATED || quick) continue;
+    int s = slices_override ? slices_override[i] : p.slices;
+    if (s <= 0) s = emu::kMaxSlices;
+    const size_t need = emu::layout(p.m, p.n, p.k, s, nullptr, nullptr, false);
+    if (base && plan) emu::layout(p.m, p.n, p.k, s, static_cast<char*>(base) + off, &plan->emu[ei].ws, false);
+    off = up256(off + need);
+    ++ei;
+  }
+  if (base && plan) {
+    plan->counter_dev = reinterpret_cast<unsigned long long*>(base);
+    plan->native_dev = reinterpret_cast<NativeTableEntry*>(static_cast<char*>(base) + o_native);
+    plan->emu_dev = reinterpret_cast<emu::EmuTableEntry*>(static_cast<char*>(base) + o_emu);
+  }
+  return off;
+}
+
+int validate(const gbd_problem* probs, int count) {
+  if (count < 0 || (count > 0 && !probs)) return set_error(GBD_ERR_ARG, "grouped: bad problem array");
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const int bad = check_dgemm_args(p.transa, p.transb, p.m, p.n, p.k, p.lda, p.ldb, p.ldc);
+    if (bad) return set_error(GBD_ERR_ARG, "grouped problem %d: parameter %d had an illegal value", i, bad);
+    if (p.mode != GBD_MODE_NATIVE && p.mode != GBD_MODE_EMULATED)
+      return set_error(GBD_ERR_ARG, "grouped problem %d: mode %d", i, p.mode);
+    if (p.mode == GBD_MODE_EMULATED && (p.slices < 0 || p.slices > emu::kMaxSlices))
+      return set_error(GBD_ERR_ARG, "grouped problem %d: slices %d", i, p.slices);
+    if (p.tile != 0 && p.tile != 32 && p.tile != 64)
+      return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0, 32 or 64)", i, p.tile);
+    const int64_t lim = (int64_t)1 << 31;
+    if (p.m >= lim || p.n >= lim || p.k >= lim || (p.m + 63) / 64 > 65535 || (p.n + 63) / 64 > 65535)
+      return set_error(GBD_ERR_LIMIT, "grouped problem %d: size beyond the supported range", i);
+  }
+  return GBD_OK;
+}
+
+}  // namespace
+}  // namespace gbd
+
+extern "C" {
+
+size_t gbd_dgemm_grouped_workspace_size(const gbd_problem* probs, int count) {
+  if (count <= 0 || !probs) return 256;
+  return gbd::grouped_layout(probs, count, nullptr, nullptr, nullptr);
+}
+
+int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace, size_t workspace_bytes,
+                            int* slices_used, void* stream, gbd_plan** out) {
+  using namespace gbd;
+  if (!out) return set_error(GBD_ERR_ARG, "grouped: plan pointer is NULL");
+  *out = nullptr;
+  int rc = validate(probs, count);
+  if (rc) return rc;
+  rc = current_device(nullptr, nullptr);
+  if (rc) return rc;
+  const size_t need = gbd_dgemm_grouped_workspace_size(probs, count);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return set_error(GBD_ERR_WORKSPACE, "grouped: workspace must be 256-byte aligned and hold %zu bytes", need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gbd_plan* plan = new (std::nothrow) gbd_plan();
+  if (!plan) return set_error(GBD_ERR_WORKSPACE, "grouped: host allocation failed");
+  struct Guard {
+    gbd_plan** keep;
+    gbd_plan* p;
+    ~Guard() {
+      if (!*keep) delete p;
+    }
+  } guard{out, plan};
+
+  // split problems; quick paths (alpha == 0 or k == 0) of both modes become k = 0 native tiles
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    if (slices_used) slices_used[i] = 0;
+    if (p.m == 0 || p.n == 0) continue;
+    const bool quick = p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_EMULATED && !quick) {
+      gbd_plan::Emu e;
+      e.p = p;
+      e.slices = p.slices;
+      plan->emu.push_back(e);
+      continue;
+    }
+    if (quick && p.beta == 1.0) continue;  // nothing to do
+    NativeTableEntry t;
+    memset(&t, 0, sizeof(t));
+    NativeArgs& a = t.a;
+    a.m = p.m; a.n = p.n; a.k = quick ? 0 : p.k;
+    a.alpha = quick ? 0.0 : p.alpha; a.beta = p.beta;
+    a.A = p.A; a.lda = p.lda; a.B = p.B; a.ldb = p.ldb; a.C = p.C; a.ldc = p.ldc;
+    a.err = device_error_word();
+    a.vec_c = ((reinterpret_cast<uintptr_t>(p.C) & 15u) == 0 && (p.ldc & 1) == 0) ? 1 : 0;
+    t.ta = trans_code(p.transa);
+    t.tb = trans_code(p.transb);
+    t.tile = p.tile ? p.tile : default_tile(p.m, p.n);
+    t.tiles_m = (int32_t)((p.m + t.tile - 1) / t.tile);
+    plan->native.push_back(t);
+  }
+  // the workspace holds one slice region per emulated problem (sized for the given or maximal slices)
+  std::vector<int> s_override(count, 0);
+  for (int i = 0; i < count; ++i) s_override[i] = probs[i].slices;
+  grouped_layout(probs, count, s_override.data(), workspace, plan);
+
+  // automatic slice counts: exponents and magnitude statistics now, one read-back for all
+  cudaError_t e;
+  bool any_auto = false;
+  for (auto& em : plan->emu) {
+    if (em.slices != 0) continue;
+    any_auto = true;
+    const gbd_problem& p = em.p;
+    const emu::Workspace& ws = em.ws;
+    const int ta = trans_code(p.transa), tb = trans_code(p.transb);
+    if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.muA, 0, sizeof(float) * (size_t)p.m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.muB, 0, sizeof(float) * (size_t)p.n, s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: workspace initialisation");
+    if ((rc = emu::launch_exponents(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.badA, s))) return rc;
+    if ((rc = emu::launch_exponents(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.badB, s))) return rc;
+    if ((rc = emu::launch_magnitudes(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.muA, s))) return rc;
+    if ((rc = emu::launch_magnitudes(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.muB, s))) return rc;
+    if ((rc = emu::launch_min_stats(ws.muA, p.m, ws.muB, p.n, ws.badA, ws.badB, ws.stats, s))) return rc;
+  }
+  if (any_auto) {
+    std::vector<float> st(4 * plan->emu.size(), 0.0f);
+    for (size_t q = 0; q < plan->emu.size(); ++q)
+      if (plan->emu[q].slices == 0 &&
+          (e = cudaMemcpyAsync(&st[4 * q], plan->emu[q].ws.stats, 4 * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+              cudaSuccess)
+        return cuda_fail(e, "grouped: reading statistics");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "grouped: reading statistics");
+    for (size_t q = 0; q < plan->emu.size(); ++q) {
+      auto& em = plan->emu[q];
+      if (em.slices != 0) continue;
+      const double mu = st[4 * q] < 1e38f ? st[4 * q] : 0.0, nu = st[4 * q + 1] < 1e38f ? st[4 * q + 1] : 0.0;
+      const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * 1.1102230246251565e-16;
+      em.slices = (mu > 0.0 && nu > 0.0) ? emu::choose_slices(target, mu, nu, em.p.k, nullptr) : 1;
+    }
+  }
+  // emulated table: tensor maps and tile counts, longest tiles first
+  std::vector<int> order(plan->emu.size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+  auto cost = [&](int q) {
+    const auto& em = plan->emu[q];
+    return (int64_t)em.slices * (em.slices + 1) / 2 * ((em.p.k + emu::kBK - 1) / emu::kBK);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  plan->emu_table.resize(plan->emu.size());
+  int64_t tiles = 0;
+  for (size_t r = 0; r < order.size(); ++r) {
+    const auto& em = plan->emu[order[r]];
+    emu::EmuTableEntry& t = plan->emu_table[r];
+    memset(&t, 0, sizeof(t));
+    if ((rc = emu::encode_slice_maps(em.ws, em.p.m, em.p.n, em.p.k, em.slices, &t))) return rc;
+    t.m = em.p.m; t.n = em.p.n; t.k = em.p.k; t.ldc = em.p.ldc;
+    t.alpha = em.p.alpha; t.beta = em.p.beta; t.C = em.p.C;
+    t.sigA = em.ws.sigA; t.sigB = em.ws.sigB; t.badA = em.ws.badA; t.badB = em.ws.badB;
+    t.slices = em.slices;
+    t.nkb = (int)((em.p.k + emu::kBK - 1) / emu::kBK);
+    t.tiles_m = (int)((em.p.m + 127) / 128);
+    t.num_tiles = t.tiles_m * (int)((em.p.n + emu::kGroupedBN - 1) / emu::kGroupedBN);
+    t.group_m = t.tiles_m;  // within one problem the tiles walk down the rows
+    t.tile_begin = tiles;
+    tiles += t.num_tiles;
+  }
+  plan->emu_tiles = tiles;
+  if (slices_used)
+    for (int i = 0, q = 0; i < count; ++i) {
+      const gbd_problem& p = probs[i];
+      const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+      if (p.mode == GBD_MODE_EMULATED && !quick) slices_used[i] = plan->emu[q++].slices;
+    }
+  // native table: longest tiles (largest k) first
+  std::stable_sort(plan->native.begin(), plan->native.end(),
+                   [](const NativeTableEntry& a, const NativeTableEntry& b) { return a.a.k > b.a.k; });
+  int64_t nt = 0;
+  for (auto& t : plan->native) {
+    t.tile_begin = nt;
+    nt += (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
+  }
+  plan->native_tiles = nt;
+  // tables to the device (pageable copies are staged before the call returns)
+  if (!plan->native.empty() &&
+      (e = cudaMemcpyAsync(plan->native_dev, plan->native.data(), sizeof(NativeTableEntry) * plan->native.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped: native table copy");
+  if (!plan->emu_table.empty() &&
+      (e = cudaMemcpyAsync(plan->emu_dev, plan->emu_table.data(), sizeof(emu::EmuTableEntry) * plan->emu_table.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped: emulated table copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "grouped: plan set-up");
+  *out = plan;
+  return GBD_OK;
+}
+
+int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
+  using namespace gbd;
+  if (!plan) return set_error(GBD_ERR_ARG, "grouped: plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  cudaError_t e;
+  // emulated: exponents and digit slices of every problem, then one slice-product launch
+  for (auto& em : plan->emu) {
+    const gbd_problem& p = em.p;
+    const emu::Workspace& ws = em.ws;
+    const int ta = trans_code(p.transa), tb = trans_code(p.transb);
+    if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)p.n, s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: workspace initialisation");
+    if ((rc = emu::launch_exponents(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.badA, s))) return rc;
+    if ((rc = emu::launch_exponents(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.badB, s))) return rc;
+    if ((rc = emu::launch_split(p.A, p.lda, p.m, p.k, ta == 0, em.ws.sigA, em.slices, em.ws.DA, em.ws.kp, s))) return rc;
+    if ((rc = emu::launch_split(p.B, p.ldb, p.n, p.k, tb != 0, em.ws.sigB, em.slices, em.ws.DB, em.ws.kp, s))) return rc;
+  }
+  if (plan->emu_tiles > 0 &&
+      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles, s)))
+    return rc;
+  // native: one persistent launch over all tiles
+  if (plan->native_tiles > 0) {
+    if ((e = cudaMemsetAsync(plan->counter_dev, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: counter reset");
+    constexpr size_t smem = native_smem_bytes<64, 64>();
+    e = cudaFuncSetAttribute(k_grouped_native, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped native)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grouped_native, kNativeThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > plan->native_tiles) grid = plan->native_tiles;
+    k_grouped_native<<<(unsigned)grid, kNativeThreads, smem, s>>>(plan->native_dev, (int)plan->native.size(),
+                                                                 plan->native_tiles, plan->counter_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped native launch");
+  }
+  return GBD_OK;
+}
+
+void gbd_grouped_plan_destroy(gbd_plan* plan) { delete plan; }
+
+int gbd_dgemm_grouped(const gbd_problem* probs, int count, void* workspace, size_t workspace_bytes,
+                      int* slices_used, void* stream) {
+  gbd_plan* plan = nullptr;
+  int rc = gbd_grouped_plan_create(probs, count, workspace, workspace_bytes, slices_used, stream, &plan);
+  if (rc) return rc;
+  rc = gbd_grouped_plan_run(plan, stream);
+  gbd_grouped_plan_destroy(plan);
+  return rc;
+}
+
+}  // extern "C"

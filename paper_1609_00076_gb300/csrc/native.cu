@@ -24,185 +24,17 @@
 #include <cstdint>
 #include <cstring>
 
-#include "common.cuh"
+#include "native_tile.cuh"
 
 namespace gbd {
 namespace {
 
-struct NativeArgs {
-  int64_t m, n, k;
-  double alpha, beta;
-  const double* A;
-  int64_t lda;
-  const double* B;
-  int64_t ldb;
-  double* C;
-  int64_t ldc;
-  unsigned int* err;
-  int vec_c;  // C and ldc allow 16-byte stores at even rows
-};
-
-constexpr int kThreads = 128;
-constexpr int kBK = 16;
-constexpr int kStages = 4;
-
-template <int BM, int BN>
-constexpr size_t native_smem_bytes() {
-  return (size_t)kStages * (BM * kBK + kBK * BN) * sizeof(double) + kStages * sizeof(uint64_t);
-}
-
 template <bool TA, bool TB, int BM, int BN, bool USE_TMA>
-__global__ void __launch_bounds__(kThreads) k_native_dgemm(const NativeArgs p,
+__global__ void __launch_bounds__(kNativeThreads) k_native_dgemm(const NativeArgs p,
                                                            const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB) {
-  constexpr int A_EL = BM * kBK, B_EL = kBK * BN;
-  constexpr int WM = BM / 2, WN = BN / 2, MI = WM / 16, NI = WN / 8;
-  static_assert(MI >= 1 && NI >= 1, "warp tile too small");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* sA = reinterpret_cast<double*>(smem_raw);  // [kStages][A_EL]
-  double* sB = sA + kStages * A_EL;                  // [kStages][B_EL]
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * B_EL);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-  const int nkb = (int)((p.k + kBK - 1) / kBK);
-  const int wm0 = (warp >> 1) * WM, wn0 = (warp & 1) * WN;
-
-  if (USE_TMA && tid == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  // stage kb of the k loop into ring slot kb % kStages
-  auto issue = [&](int kb) {
-    const int s = kb % kStages;
-    const int64_t k0 = (int64_t)kb * kBK;
-    if (USE_TMA) {
-      if (tid == 0 && kb < nkb) {
-        mbar_arrive_expect_tx(&full[s], (uint32_t)((A_EL + B_EL) * sizeof(double)));
-        if (!TA) tma_load_2d(sA + s * A_EL, &tmA, &full[s], (int)m0, (int)k0);
-        else tma_load_2d(sA + s * A_EL, &tmA, &full[s], (int)k0, (int)m0);
-        if (!TB) tma_load_2d(sB + s * B_EL, &tmB, &full[s], (int)k0, (int)n0);
-        else tma_load_2d(sB + s * B_EL, &tmB, &full[s], (int)n0, (int)k0);
-      }
-    } else {
-      if (kb < nkb) {
-        double* a_s = sA + s * A_EL;
-        double* b_s = sB + s * B_EL;
-        for (int idx = tid; idx < A_EL; idx += kThreads) {
-          int i, pk;
-          if (!TA) { i = idx % BM; pk = idx / BM; }  // smem [BK][BM]
-          else { pk = idx % kBK; i = idx / kBK; }    // smem [BM][BK]
-          const int64_t gi = m0 + i, gp = k0 + pk;
-          const bool ok = gi < p.m && gp < p.k;
-          const double* src = ok ? (TA ? p.A + gi * p.lda + gp : p.A + gp * p.lda + gi) : p.A;
-          cp_async_8(a_s + idx, src, ok);
-        }
-        for (int idx = tid; idx < B_EL; idx += kThreads) {
-          int j, pk;
-          if (!TB) { pk = idx % kBK; j = idx / kBK; }  // smem [BN][BK]
-          else { j = idx % BN; pk = idx / BN; }        // smem [BK][BN]
-          const int64_t gj = n0 + j, gp = k0 + pk;
-          const bool ok = gj < p.n && gp < p.k;
-          const double* src = ok ? (TB ? p.B + gp * p.ldb + gj : p.B + gj * p.ldb + gp) : p.B;
-          cp_async_8(b_s + idx, src, ok);
-        }
-      }
-      cp_async_commit();  // one group per stage, empty past the end, keeps the count uniform
-    }
-  };
-
-  double acc[MI][NI][4];
-#pragma unroll
-  for (int mi = 0; mi < MI; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < NI; ++ni)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.0;
-
-  for (int kb = 0; kb < kStages - 1; ++kb) issue(kb);
-
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int s = kb % kStages;
-    if (USE_TMA) mbar_wait(&full[s], (uint32_t)((kb / kStages) & 1), p.err, kErrWaitTma);
-    else cp_async_wait<kStages - 2>();
-    __syncthreads();  // tile kb visible to all; slot (kb-1) % kStages no longer read
-    issue(kb + kStages - 1);
-
-    const double* a_s = sA + s * A_EL;
-    const double* b_s = sB + s * B_EL;
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      double af[MI][8], bf[NI][4];
-#pragma unroll
-      for (int mi = 0; mi < MI; ++mi)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int i = wm0 + mi * 16 + g + 8 * (q & 1);
-          const int pk = kk + t + 4 * (q >> 1);
-          af[mi][q] = TA ? a_s[i * kBK + pk] : a_s[pk * BM + i];
-        }
-#pragma unroll
-      for (int ni = 0; ni < NI; ++ni)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = wn0 + ni * 8 + g;
-          const int pk = kk + t + 4 * q;
-          bf[ni][q] = TB ? b_s[pk * BN + j] : b_s[j * kBK + pk];
-        }
-#pragma unroll
-      for (int mi = 0; mi < MI; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < NI; ++ni) dmma_16x8x16(acc[mi][ni], af[mi], bf[ni]);
-    }
-  }
-
-  // ---- fused epilogue through shared memory, column by column ----
-  __syncthreads();  // every load was consumed; the ring is free
-  constexpr int LDS = BM + 2;
-  double* sC = reinterpret_cast<double*>(smem_raw);  // [BN][LDS], column-major tile
-#pragma unroll
-  for (int mi = 0; mi < MI; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < NI; ++ni) {
-      const int r = wm0 + mi * 16 + g, c = wn0 + ni * 8 + 2 * t;
-      sC[c * LDS + r] = acc[mi][ni][0];
-      sC[(c + 1) * LDS + r] = acc[mi][ni][1];
-      sC[c * LDS + r + 8] = acc[mi][ni][2];
-      sC[(c + 1) * LDS + r + 8] = acc[mi][ni][3];
-    }
-  __syncthreads();
-  const double alpha = p.alpha, beta = p.beta;
-  for (int jj = warp; jj < BN; jj += kThreads / 32) {
-    const int64_t j = n0 + jj;
-    if (j >= p.n) break;
-    double* ccol = p.C + j * p.ldc;
-    for (int ii = 2 * lane; ii < BM; ii += 64) {
-      const int64_t i = m0 + ii;
-      if (i >= p.m) break;
-      const double v0 = sC[jj * LDS + ii], v1 = sC[jj * LDS + ii + 1];
-      if (p.vec_c && i + 1 < p.m) {
-        double2* dst = reinterpret_cast<double2*>(ccol + i);
-        double2 out;
-        if (beta == 0.0) {
-          out.x = alpha * v0;
-          out.y = alpha * v1;
-        } else {
-          const double2 c0 = *dst;
-          out.x = fma(alpha, v0, beta * c0.x);
-          out.y = fma(alpha, v1, beta * c0.y);
-        }
-        *dst = out;
-      } else {
-        ccol[i] = (beta == 0.0) ? alpha * v0 : fma(alpha, v0, beta * ccol[i]);
-        if (i + 1 < p.m) ccol[i + 1] = (beta == 0.0) ? alpha * v1 : fma(alpha, v1, beta * ccol[i + 1]);
-      }
-    }
-  }
+  native_tile<TA, TB, BM, BN, USE_TMA>(p, &tmA, &tmB, (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN, smem_raw);
 }
 
 template <bool TA, bool TB, int BM, int BN, bool USE_TMA>
@@ -213,11 +45,11 @@ int launch_native(const NativeArgs& a, cudaStream_t stream) {
   if (USE_TMA) {
     int rc;
     // A stored m x k ('N') or k x m ('T'); B stored k x n ('N') or n x k ('T')
-    if (!TA) rc = encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.A, a.m, a.k, a.lda * 8, BM, kBK, CU_TENSOR_MAP_SWIZZLE_NONE);
-    else rc = encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.A, a.k, a.m, a.lda * 8, kBK, BM, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!TA) rc = encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.A, a.m, a.k, a.lda * 8, BM, kNativeBK, CU_TENSOR_MAP_SWIZZLE_NONE);
+    else rc = encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.A, a.k, a.m, a.lda * 8, kNativeBK, BM, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (rc) return rc;
-    if (!TB) rc = encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.B, a.k, a.n, a.ldb * 8, kBK, BN, CU_TENSOR_MAP_SWIZZLE_NONE);
-    else rc = encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.B, a.n, a.k, a.ldb * 8, BN, kBK, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!TB) rc = encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.B, a.k, a.n, a.ldb * 8, kNativeBK, BN, CU_TENSOR_MAP_SWIZZLE_NONE);
+    else rc = encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, a.B, a.n, a.k, a.ldb * 8, BN, kNativeBK, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (rc) return rc;
   }
   constexpr size_t smem = native_smem_bytes<BM, BN>();
@@ -226,7 +58,7 @@ int launch_native(const NativeArgs& a, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(native)");
   dim3 grid((unsigned)((a.m + BM - 1) / BM), (unsigned)((a.n + BN - 1) / BN));
-  kern<<<grid, kThreads, smem, stream>>>(a, tmA, tmB);
+  kern<<<grid, kNativeThreads, smem, stream>>>(a, tmA, tmB);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "native dgemm launch");
 }

@@ -85,11 +85,28 @@ class GbdEmuInfo(ctypes.Structure):
 
 _c, _i64, _d, _i, _vp, _sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                               ctypes.c_size_t)
+
+GBD_MODE_NATIVE = 0
+GBD_MODE_EMULATED = 1
+
+
+class GbdProblem(ctypes.Structure):
+    """Mirror of gbd_problem (one problem of a grouped call)."""
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char), ("mode", ctypes.c_int32),
+                ("slices", ctypes.c_int32), ("tile", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("A", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p),
+                ("ldc", ctypes.c_int64), ("tol", ctypes.c_double)]
 # (name, argtypes, restype) of the entry points declared further down the header
 _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_workspace_size", [_i64, _i64, _i64, _i], _sz),
     ("gbd_dgemm_emu", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                        ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_dgemm_grouped_workspace_size", [_vp, _i], _sz),
+    ("gbd_grouped_plan_create", [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)], _i),
+    ("gbd_grouped_plan_run", [_vp, _vp], _i),
+    ("gbd_grouped_plan_destroy", [_vp], None),
+    ("gbd_dgemm_grouped", [_vp, _i, _vp, _sz, _vp, _vp], _i),
 ]
 
 
@@ -164,6 +181,54 @@ def gbd_dgemm_emu(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 
                                 int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
                                 float(tol), _addr(workspace), int(workspace_bytes),
                                 ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def problem_array(problems) -> ctypes.Array:
+    """A ctypes array of GbdProblem from GbdProblem objects or dicts of its fields."""
+    arr = (GbdProblem * max(1, len(problems)))()
+    for i, p in enumerate(problems):
+        if isinstance(p, GbdProblem):
+            arr[i] = p
+            continue
+        q = GbdProblem()
+        for key, val in p.items():
+            if key in ("A", "B", "C"):
+                val = _addr(val)
+            elif key in ("transa", "transb"):
+                val = _t(val)
+            setattr(q, key, val)
+        arr[i] = q
+    return arr
+
+
+def gbd_dgemm_grouped_workspace_size(problems) -> int:
+    arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
+    return int(load().gbd_dgemm_grouped_workspace_size(ctypes.cast(arr, _vp), len(arr) if problems else 0))
+
+
+def gbd_grouped_plan_create(problems, workspace, workspace_bytes, slices_used=None, stream=None):
+    """Returns (status, plan handle); slices_used may be a ctypes int array of len(problems)."""
+    arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
+    plan = _vp()
+    rc = load().gbd_grouped_plan_create(ctypes.cast(arr, _vp), len(problems), _addr(workspace), int(workspace_bytes),
+                                        ctypes.cast(slices_used, _vp) if slices_used is not None else None,
+                                        _stream(stream), ctypes.byref(plan))
+    return rc, plan
+
+
+def gbd_grouped_plan_run(plan, stream=None) -> int:
+    return load().gbd_grouped_plan_run(plan, _stream(stream))
+
+
+def gbd_grouped_plan_destroy(plan) -> None:
+    load().gbd_grouped_plan_destroy(plan)
+
+
+def gbd_dgemm_grouped(problems, workspace, workspace_bytes, slices_used=None, stream=None) -> int:
+    arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
+    return load().gbd_dgemm_grouped(ctypes.cast(arr, _vp), len(problems), _addr(workspace), int(workspace_bytes),
+                                    ctypes.cast(slices_used, _vp) if slices_used is not None else None,
+                                    _stream(stream))
 
 
 def gbd_check_device_error(stream=None) -> int:

@@ -45,3 +45,32 @@ def test_empty_problem_is_a_no_op(lib):
     # m == 0 or n == 0 returns before any device work
     assert gbdgemm.gbd_dgemm("N", "N", 0, 5, 5, 1.0, 0, 1, 0, 5, 0.0, 0, 1, stream=0) == 0
     assert gbdgemm.gbd_dgemm("T", "T", 5, 0, 5, 1.0, 0, 5, 0, 1, 0.0, 0, 5, stream=0) == 0
+
+
+def test_problem_struct_layout(lib):
+    # the C side asserts the same size and offsets (grouped.cu)
+    import ctypes
+    P = gbdgemm.GbdProblem
+    assert ctypes.sizeof(P) == 112
+    assert P.m.offset == 16 and P.A.offset == 56 and P.tol.offset == 104
+
+
+def test_grouped_argument_errors_without_gpu(lib):
+    bad = [dict(transa="N", transb="N", mode=0, m=4, n=4, k=4, alpha=1.0, beta=0.0, A=0, lda=2, B=0, ldb=4,
+                C=0, ldc=4)]
+    ws = gbdgemm.gbd_dgemm_grouped_workspace_size(bad)
+    assert ws >= 256
+    rc, plan = gbdgemm.gbd_grouped_plan_create(bad, 0, ws, stream=0)
+    assert rc == gbdgemm.GBD_ERR_ARG
+    assert "problem 0: parameter 8" in gbdgemm.gbd_last_error()
+    bad[0]["lda"] = 4
+    bad[0]["mode"] = 7
+    rc, _ = gbdgemm.gbd_grouped_plan_create(bad, 0, ws, stream=0)
+    assert rc == gbdgemm.GBD_ERR_ARG and "mode 7" in gbdgemm.gbd_last_error()
+
+
+def test_emu_workspace_size_is_host_only(lib):
+    small = gbdgemm.gbd_dgemm_emu_workspace_size(100, 200, 300, 3)
+    big = gbdgemm.gbd_dgemm_emu_workspace_size(100, 200, 300, 0)
+    assert 0 < small < big
+    assert gbdgemm.gbd_dgemm_emu_workspace_size(-1, 2, 3, 1) == 0
