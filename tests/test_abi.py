@@ -74,3 +74,16 @@ def test_emu_workspace_size_is_host_only(lib):
     big = gbdgemm.gbd_dgemm_emu_workspace_size(100, 200, 300, 0)
     assert 0 < small < big
     assert gbdgemm.gbd_dgemm_emu_workspace_size(-1, 2, 3, 1) == 0
+
+
+def test_request_stream_is_seeded_and_poisson():
+    from paper_1609_00076_gb300 import serving
+    a = serving.request_stream(3, 2000, rate=500.0)
+    b = serving.request_stream(3, 2000, rate=500.0)
+    assert [(r.arrival, r.m, r.n, r.k, r.mode) for r in a] == [(r.arrival, r.m, r.n, r.k, r.mode) for r in b]
+    gaps = [y.arrival - x.arrival for x, y in zip(a, a[1:])]
+    assert abs(sum(gaps) / len(gaps) - 1 / 500.0) < 0.1 / 500.0          # mean gap of a Poisson process
+    big = sum(r.m == 4096 for r in a) / len(a)
+    emu = sum(r.mode == serving.EMULATED for r in a) / len(a)
+    assert 0.07 < big < 0.13 and 0.45 < emu < 0.55
+    assert all(32 <= r.m <= 4096 and 32 <= r.k <= 4096 for r in a)
