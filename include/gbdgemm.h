@@ -133,6 +133,38 @@ GBD_API int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_
                           double* C, int64_t ldc, int slices, double tol, void* workspace,
                           size_t workspace_bytes, gbd_emu_info* info, void* stream);
 
+/*
+ * gbd_dgemm_emu for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment convenience of this library.
+ *
+ * Some callers must not call cudaMalloc (or any allocator) while they run: code
+ * in a latency-critical loop where an allocation can block or fail at an
+ * arbitrary moment, plug-ins whose host application owns all device memory, or
+ * code that runs while an allocator lock is held.  This entry point takes the
+ * same arguments as gbd_dgemm_emu except the workspace and computes the same
+ * result (the same bits for the same slice count), using a scratch area built
+ * into the library instead: a 64 MiB device array that every GPU loading the
+ * library keeps until the process exits.  It allocates nothing.
+ *
+ * Limit: problems whose gbd_dgemm_emu_workspace_size(m, n, k, slices) exceeds
+ * 64 MiB (67108864 bytes) are rejected with GBD_ERR_LIMIT; for example every
+ * square problem up to 1024 fits with automatic slices.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture on the device.
+ * Sharing: all calls on a device use the same array, which keeps the previous
+ * call's contents; the parts that must start at zero are cleared by every call.
+ * Calls whose work overlaps on the GPU (other streams, other host threads) race
+ * on the array and corrupt each other's results: serialise them.
+ * info: optional; its record_phases field is ignored (timing would allocate events).
+ * Returns 0, a BLAS argument index, or GBD_ERR_* (GBD_ERR_LIMIT for a problem
+ * above the scratch size).
+ */
+GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                  double alpha, const double* A, int64_t lda, const double* B,
+                                  int64_t ldb, double beta, double* C, int64_t ldc, int slices,
+                                  double tol, gbd_emu_info* info, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Grouped calls: many independent problems per launch                       */
 /* ------------------------------------------------------------------------- */

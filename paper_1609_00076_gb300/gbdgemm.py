@@ -102,6 +102,8 @@ _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_workspace_size", [_i64, _i64, _i64, _i], _sz),
     ("gbd_dgemm_emu", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                        ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_dgemm_emu_noalloc", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d,
+                               ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_grouped_workspace_size", [_vp, _i], _sz),
     ("gbd_grouped_plan_create", [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)], _i),
     ("gbd_grouped_plan_run", [_vp, _vp], _i),
@@ -181,6 +183,14 @@ def gbd_dgemm_emu(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 
                                 int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
                                 float(tol), _addr(workspace), int(workspace_bytes),
                                 ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_dgemm_emu_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, tol, info=None,
+                          stream=None) -> int:
+    """gbd_dgemm_emu without a caller workspace (built-in 64 MiB scratch); returns the status."""
+    return load().gbd_dgemm_emu_noalloc(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                                        int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
+                                        float(tol), ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
 def problem_array(problems) -> ctypes.Array:
