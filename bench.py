@@ -47,8 +47,9 @@ def workload_name():
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to FP64
 NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
-# dram bytes (read + write) per launch of the dominant kernel from one ncu capture of this
-# workload; None until captured for the current kernel
+# dram bytes (read + write) per launch of the dominant kernel, from one single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload; None until captured
+# for the current kernel
 TRAFFIC_PER_LAUNCH = {"native": None, "emu": None}
 
 
@@ -78,7 +79,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -118,7 +119,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend: str | None = None):
+    """Replicas: one process per GPU, joined only for the start/stop barrier and the
+    max-over-ranks time (NCCL on GPUs, gloo when there are none)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -127,10 +130,18 @@ def dist_setup(args):
         import torch
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        torch.cuda.set_device(local)
-        dist.init_process_group(backend="nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
+
+
+def replica_value(world: int, flops_per_step: float, steps: int, max_ms: float) -> float:
+    """Whole-job TFLOP/s: every rank's useful flops over the slowest rank's time."""
+    return world * flops_per_step * steps / (max_ms / 1000.0) / 1e12
 
 
 def barrier(pg):
@@ -272,7 +283,7 @@ def run_ours(args, world, rank, local, pg):
     total_ms = ev[0].elapsed_time(ev[-1])
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     total_ms = max_over_ranks(pg, total_ms, dev)
-    value = world * flops * args.steps / (total_ms / 1000.0) / 1e12
+    value = replica_value(world, flops, args.steps, total_ms)
     slices = info.slices
     products = info.products
 
@@ -307,10 +318,13 @@ def run_ours(args, world, rank, local, pg):
         e1.record(stream)
         torch.cuda.synchronize()
     e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
-    e2e_val = world * flops * e2e_steps / (e2e_ms / 1000.0) / 1e12
+    e2e_val = replica_value(world, flops, e2e_steps, e2e_ms)
 
     # ---- latency of small calls (256^3, the latency configuration) ----
     lat = small_call_latency(dev, stream)
+    # ---- grouped batch of 512 uneven problems, and the serving loop (rank 0, default size only) ----
+    grouped = grouped_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
+    serving_rep = serving_measure() if (rank == 0 and not args.no_extras) else None
 
     if rank != 0:
         return 0
@@ -338,6 +352,8 @@ def run_ours(args, world, rank, local, pg):
                      "kernel": "k_slice_gemm (tcgen05 kind::f16, BF16 -> FP32)",
                      "peak_source": f"{src} bf16_tflops_sustained"},
         "latency": lat,
+        "grouped": grouped,
+        "serving": serving_rep,
         "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
@@ -347,6 +363,74 @@ def run_ours(args, world, rank, local, pg):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
+    """512 problems, m, n, k each log-uniform on [32, 2048], random transposes, uniform[-1,1):
+    one grouped plan per mode (native; emulated at the FP64 bound), TFLOP/s of plan runs."""
+    import ctypes
+
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm, synth
+    sizes = synth.log_uniform_sizes(seed, count, 32, 2048)
+    flips = synth.coin(seed + 1, 2 * count)
+    keep, base = [], []
+    for i in range(count):
+        m, n, k = (int(x) for x in sizes[i])
+        ta, tb = ("T" if flips[2 * i] else "N"), ("T" if flips[2 * i + 1] else "N")
+        ra, ca = (k, m) if ta == "T" else (m, k)
+        rb, cb = (n, k) if tb == "T" else (k, n)
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed * 7919 + i)
+        A = torch.empty(ra * ca, dtype=torch.float64, device=dev).uniform_(-1, 1, generator=g)
+        B = torch.empty(rb * cb, dtype=torch.float64, device=dev).uniform_(-1, 1, generator=g)
+        C = torch.zeros(m * n, dtype=torch.float64, device=dev)
+        keep += [A, B, C]
+        base.append(dict(transa=ta, transb=tb, m=m, n=n, k=k, alpha=1.0, beta=0.0, A=A, lda=ra, B=B, ldb=rb,
+                         C=C, ldc=m, slices=0, tile=0, tol=0.0))
+    flops = sum(2.0 * p["m"] * p["n"] * p["k"] for p in base)
+    out = {"problems": count, "flops_per_batch": flops}
+    for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("emulated", gbdgemm.GBD_MODE_EMULATED)):
+        arr = gbdgemm.problem_array([dict(p, mode=mode) for p in base])
+        wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        used = (ctypes.c_int * count)()
+        torch.cuda.synchronize()
+        rc, plan = gbdgemm.gbd_grouped_plan_create(arr, ws, wsb, slices_used=used, stream=stream)
+        gbdgemm.check(rc)
+        try:
+            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = _events(2)
+                e0.record(stream)
+                gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        finally:
+            gbdgemm.gbd_grouped_plan_destroy(plan)
+        d = {"ms": best, "tflops": flops / (best / 1e3) / 1e12}
+        if mode == gbdgemm.GBD_MODE_EMULATED:
+            d["mean_slices"] = float(sum(used) / count)
+        out[name] = d
+        del ws
+    return out
+
+
+def serving_measure(requests: int = 300, seed: int = 5000):
+    """Saturated rate of the mixed request stream, then a Poisson stream at 0.8 of it."""
+    from paper_1609_00076_gb300 import serving
+    srv = serving.Server(budget_bytes=40e9, slots=3)
+    srv.run(serving.request_stream(seed - 1, 16, 0.0, big_fraction=0.0))
+    sat = srv.run(serving.request_stream(seed, requests, 0.0))
+    rate = 0.8 * sat.requests_per_s
+    rep = srv.run(serving.request_stream(seed + 1, requests, rate))
+    return {"requests": requests, "saturated_requests_per_s": sat.requests_per_s,
+            "saturated_tflops": sat.throughput_tflops, "rate_per_s": rate, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
+            "throughput_tflops": rep.throughput_tflops,
+            "mix": "90% m,n,k log-uniform [32,2048], 10% 4096^3; half native, half emulated at 1e-14; 40 GB budget"}
 
 
 def small_call_latency(dev, stream, calls: int = 200):
@@ -384,9 +468,11 @@ def small_call_latency(dev, stream, calls: int = 200):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the grouped-batch and serving measurements (profiling runs)")
     ap.add_argument("--size", type=int, default=8192,
                     help="m = n = k of the square workload (8192 is the benchmark; smaller sizes are for profiling)")
     args = ap.parse_args()

@@ -235,6 +235,15 @@ GBD_API int gbd_dgemm_grouped(const gbd_problem* probs, int count, void* workspa
                               size_t workspace_bytes, int* slices_used, void* stream);
 
 /*
+ * Exercises the watchdog: launches one thread that waits on a barrier nothing
+ * completes, gives up after `limit_ms` milliseconds (1..10000), sets the device
+ * error word exactly as a kernel whose wait ran out would, and ends normally (no
+ * fault, no hang; the context stays usable).  A following gbd_check_device_error
+ * returns GBD_ERR_TIMEOUT.  Asynchronous on `stream`.
+ */
+GBD_API int gbd_watchdog_selftest(int limit_ms, void* stream);
+
+/*
  * Reads and clears the device error word of the current device that the
  * kernels set when a bounded wait gives up.  Synchronises `stream` first.
  * Returns 0 when no wait gave up since the last call, GBD_ERR_TIMEOUT when one

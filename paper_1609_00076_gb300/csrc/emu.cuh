@@ -40,8 +40,9 @@ struct Workspace {
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
-  int32_t* scratch_p;  // [scratch_ctas][128 * 256] parked integer level sums of the two-SM kernel
+  int32_t* scratch_p;  // [scratch_p_ctas][128 * 256] parked integer level sums of the slice kernels
   int scratch_ctas;
+  int scratch_p_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
 };
 
@@ -62,6 +63,29 @@ int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, c
                      const int* badB, float* stats, cudaStream_t s);
 int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
                  const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s);
+
+// One operand side of one problem for the batched preparation kernels (grouped calls).
+struct PrepJob {
+  const double* X;
+  int64_t ld, R, K;  // rows r of the operand as in launch_split
+  int* sig;
+  int* bad;
+  float* mu;  // magnitude sums (automatic slice counts), or null
+  uint16_t* D;
+  int64_t kp;
+  int rows_contig, slices;
+  int64_t exp_begin, split_begin;  // first block of this job in the batched launches
+  int exp_gx, split_gx;            // blocks along the first grid dimension of each launch
+};
+// fills j's block ranges, advancing the running block counts of both launches
+void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks);
+// exponents: initialise, then one launch for every job; split: one launch for every job
+int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
+                        bool exponents, bool split, cudaStream_t s);
+// exponents and magnitude statistics of every problem (jobs 2q, 2q+1 = op(A), op(B)^T of
+// problem q) into stats_dev[4q .. 4q+3] = {min mu, min nu, bad row, bad column}
+int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
+                         cudaStream_t s);
 
 struct GemmParams {
   int64_t m, n, k;
@@ -95,7 +119,9 @@ constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
 // tensor maps of one problem's slices for the grouped kernel
 int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
 // one launch over all problems of a device table (entries sorted by decreasing tile cost)
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t s);
+// scratch_p: max_ctas slots of 128 x kGroupedBN int32 (parked level sums); the grid is capped at max_ctas
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int32_t* scratch_p,
+                              int max_ctas, cudaStream_t s);
 
 }  // namespace emu
 }  // namespace gbd

@@ -43,7 +43,7 @@ struct SmemLayout {
   static constexpr int kNumBars = 2 * kStages + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
   static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
-  static constexpr int kBytes = kOffScale + BN * 8;
+  static constexpr int kBytes = kOffScale + 2 * BN * 8;  // two colscale buffers
   static constexpr int kAlloc = kBytes + 1024;  // slack to align the base to 1024 bytes
 };
 
@@ -325,14 +325,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------ epilogue ----------------------------------
+    // A finished level segment's integer sums are parked in this CTA's scratch slot
+    // and folded into C a few columns per drained chunk of the next segment (the
+    // last segment of a tile during the next tile), so the MMA does not wait.
     constexpr int kCols = BN / 2;  // columns per thread
     const int ew = warp - 2;
     const int quad = warp & 3;     // TMEM lanes 32*quad .. +31 are reachable from this warp
     const int half = ew >> 2;      // which half of the tile's columns
     const int row = quad * 32 + lane;
     const int col0 = half * kCols;
+    int32_t* scrP = p.scratch_p + (int64_t)blockIdx.x * (128 * BN) + (int64_t)((half * 4 + quad) * kCols) * 32 + lane;
     uint32_t chunk = 0;
     uint32_t acc[kCols];
+    bool pd_active = false, pd_first = false, pd_bad = false, pd_row_ok = false;
+    int pd_done = 0, pd_sig = 0, pd_buf = 0, cs_next = 0;
+    double pd_beta = 0.0;
+    double* pd_crow = nullptr;
+    int64_t pd_ldc = 0, pd_cols_left = 0;
+    // eight columns per step: all their loads are issued before any is used
+    auto advance = [&](int ncols) {
+      const int c1 = min(pd_done + ncols, kCols);
+      const double* cs = colscale + pd_buf * BN + col0;
+      for (int c = pd_done; c < c1; c += 8) {
+        double w[8];
+        int32_t P[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool ok = c + u < c1 && pd_row_ok && c + u < pd_cols_left;
+          const double* cp = pd_crow + (int64_t)(c + u) * pd_ldc;
+          w[u] = (ok && !(pd_first && pd_beta == 0.0)) ? *cp : 0.0;
+          P[u] = (c + u < c1) ? scrP[(c + u) * 32] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (c + u < c1 && pd_row_ok && c + u < pd_cols_left) {
+            const double wp = pd_first ? (pd_beta == 0.0 ? 0.0 : pd_beta * w[u]) : w[u];
+            const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P[u], pd_sig);
+            pd_crow[(int64_t)(c + u) * pd_ldc] = fma(cs[c + u], x, wp);
+          }
+        }
+      }
+      pd_done = c1;
+      if (pd_done >= kCols) pd_active = false;
+    };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       Job j;
       get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
@@ -351,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
           const int segn = min(kSegBlocks, j.nkb - seg0);
           const int nch = chunks_of(g, segn);
+          const int portion = (kCols + nch - 1) / nch;  // spread the pending update over this segment
 #pragma unroll
           for (int c = 0; c < kCols; ++c) acc[c] = 0u;
           for (int ci = 0; ci < nch; ++ci, ++chunk) {
@@ -363,13 +399,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t v[16];
               tmem_ld_16(taddr + q * 16, v);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
+              for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += (uint32_t)__float2int_rn(__uint_as_float(v[jj]));
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
+            if (pd_active) advance(portion);
           }
-          // level-segment end: column scales alpha * 2^(tau_j - g b) (NaN for a bad column)
-          epi_bar_sync();  // the previous segment's readers are done with colscale
+          // segment end: finish the previous pending update, then park this one
+          if (pd_active) advance(kCols);
+          epi_bar_sync();  // nobody reads the colscale buffer about to be rewritten
           {
             const int idx = ew * 32 + lane;
             if (idx < BN) {
@@ -380,27 +418,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (tau == kExpEmpty) tau = 0;
                 cs = j.badB[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - g * kDigitBits);
               }
-              colscale[idx] = cs;
+              colscale[cs_next * BN + idx] = cs;
             }
           }
           epi_bar_sync();
-          if (row_ok) {
-            double* cptr = j.C + (n0 + col0) * j.ldc + i;
 #pragma unroll
-            for (int c = 0; c < kCols; ++c) {
-              if (n0 + col0 + c < j.n) {
-                const int32_t P = (int32_t)acc[c];
-                const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P, sig_i);
-                double w;
-                if (first) w = (j.beta == 0.0) ? 0.0 : j.beta * cptr[(int64_t)c * j.ldc];
-                else w = cptr[(int64_t)c * j.ldc];
-                cptr[(int64_t)c * j.ldc] = fma(colscale[col0 + c], x, w);
-              }
-            }
-          }
+          for (int c = 0; c < kCols; ++c) scrP[c * 32] = (int32_t)acc[c];
+          pd_active = true;
+          pd_done = 0;
+          pd_first = first;
+          pd_beta = j.beta;
+          pd_bad = bad_i;
+          pd_row_ok = row_ok;
+          pd_sig = sig_i;
+          pd_buf = cs_next;
+          pd_crow = j.C + (n0 + col0) * j.ldc + i;
+          pd_ldc = j.ldc;
+          pd_cols_left = j.n - n0 - col0;
+          cs_next ^= 1;
           first = false;
         }
     }
+    if (pd_active) advance(kCols);  // the last level of the last tile
   }
 
   tc_fence_before();
@@ -640,20 +679,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     int pd_done = 0, pd_sig = 0, pd_buf = 0, cs_next = 0;
     double* pd_crow = nullptr;
     int64_t pd_cols_left = 0;  // columns of the pending tile inside C (n - n0 - col0, clamped)
+    // eight columns per step: all their loads are issued before any is used
     auto advance = [&](int ncols) {
       const int c1 = min(pd_done + ncols, k2ColsPerThread);
       const double* cs = colscale + pd_buf * k2BN + col0;
-      for (int c = pd_done; c < c1; ++c) {
-        const bool col_ok = pd_row_ok && c < pd_cols_left;
-        double w;
-        if (pd_first) w = (p.beta != 0.0 && col_ok) ? p.beta * pd_crow[(int64_t)c * p.ldc] : 0.0;
-        else w = scrW[c * 32];
-        const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(scrP[c * 32], pd_sig);
-        const double r = fma(cs[c], x, w);
-        if (pd_last) {
-          if (col_ok) pd_crow[(int64_t)c * p.ldc] = r;
-        } else {
-          scrW[c * 32] = r;
+      for (int c = pd_done; c < c1; c += 8) {
+        double w[8];
+        int32_t P[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool in = c + u < c1;
+          const bool col_ok = in && pd_row_ok && c + u < pd_cols_left;
+          if (pd_first) w[u] = (p.beta != 0.0 && col_ok) ? pd_crow[(int64_t)(c + u) * p.ldc] : 0.0;
+          else w[u] = in ? scrW[(c + u) * 32] : 0.0;
+          P[u] = in ? scrP[(c + u) * 32] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (c + u >= c1) continue;
+          const bool col_ok = pd_row_ok && c + u < pd_cols_left;
+          const double wp = pd_first ? (p.beta != 0.0 && col_ok ? p.beta * w[u] : 0.0) : w[u];
+          const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P[u], pd_sig);
+          const double r = fma(cs[c + u], x, wp);
+          if (pd_last) {
+            if (col_ok) pd_crow[(int64_t)(c + u) * p.ldc] = r;
+          } else {
+            scrW[(c + u) * 32] = r;
+          }
         }
       }
       pd_done = c1;
@@ -811,16 +863,20 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + BN - 1) / BN);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
-  a.group_m = group_rows(sms, kBM, BN, a.tiles_m);
+  int grid = (int)(tiles < sms ? tiles : sms);
+  if (grid > ws.scratch_p_ctas) grid = ws.scratch_p_ctas;
+  if (grid < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the slice kernel");
+  a.group_m = group_rows(grid, kBM, BN, a.tiles_m);
   a.alpha = gp.alpha; a.beta = gp.beta;
   a.C = gp.C; a.ldc = gp.ldc;
   a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
+  a.scratch = nullptr;
+  a.scratch_p = ws.scratch_p;
   a.err = device_error_word();
 
   auto kern = k_slice_gemm<BN, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm)");
-  const int grid = (int)(tiles < sms ? tiles : sms);
   kern<<<grid, kThreads, L::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm launch");
@@ -840,7 +896,8 @@ int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int 
   return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream) {
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int32_t* scratch_p,
+                              int max_ctas, cudaStream_t stream) {
   using L = SmemLayout<kGroupedBN>;
   if (count <= 0 || total_tiles <= 0) return GBD_OK;
   int sms = 0;
@@ -851,10 +908,13 @@ int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int tot
   Args a;
   memset(&a, 0, sizeof(a));
   a.err = device_error_word();
+  a.scratch_p = scratch_p;
   auto kern = k_slice_gemm<kGroupedBN, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped slice gemm)");
-  const int grid = total_tiles < sms ? total_tiles : sms;
+  int grid = total_tiles < sms ? total_tiles : sms;
+  if (grid > max_ctas) grid = max_ctas;
+  if (grid < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the grouped slice kernel");
   kern<<<grid, kThreads, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm launch");

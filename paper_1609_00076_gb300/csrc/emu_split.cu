@@ -33,20 +33,21 @@ __device__ __forceinline__ uint64_t load_bits(const double* X, int64_t ld, int64
 
 constexpr int kRedChunk = 1024;  // k elements per block of the reductions
 
-// sigma_r = max over non-zero finite entries of the frexp exponent; bad_r |= any Inf/NaN
+// sigma_r = max over non-zero finite entries of the frexp exponent; bad_r |= any Inf/NaN.
+// Block (bx, by) covers 32 rows (ROWS_CONTIG) or 8 rows x 1024 k.
 template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X, int64_t ld, int64_t R,
-                                                   int64_t K, int* __restrict__ sig, int* __restrict__ bad) {
-  const int64_t p_begin = (int64_t)blockIdx.y * kRedChunk;
+__device__ __forceinline__ void exponents_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                                               int* __restrict__ sig, int* __restrict__ bad, int64_t bx, int64_t by,
+                                               int (*s_max)[33], int (*s_bad)[33]) {
+  const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
     // 32 consecutive rows per warp (coalesced), 8 warps split the k range
-    __shared__ int s_max[8][33];
-    __shared__ int s_bad[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t r = bx * 32 + tx;
     int mx = kExpEmpty, bd = 0;
     if (r < R)
+#pragma unroll 4
       for (int64_t p = p_begin + ty; p < p_end; p += 8) {
         const uint64_t b = load_bits<true>(X, ld, r, p);
         if (is_nonfinite(b)) bd = 1;
@@ -66,9 +67,10 @@ __global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X,
   } else {
     // one row per warp, lanes along the contiguous k direction
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * 8 + w;
+    const int64_t r = bx * 8 + w;
     if (r >= R) return;
     int mx = kExpEmpty, bd = 0;
+#pragma unroll 4
     for (int64_t p = p_begin + lane; p < p_end; p += 32) {
       const uint64_t b = load_bits<false>(X, ld, r, p);
       if (is_nonfinite(b)) bd = 1;
@@ -85,6 +87,14 @@ __global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X,
   }
 }
 
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X, int64_t ld, int64_t R,
+                                                   int64_t K, int* __restrict__ sig, int* __restrict__ bad) {
+  __shared__ int s_max[8][33];
+  __shared__ int s_bad[8][33];
+  exponents_body<ROWS_CONTIG>(X, ld, R, K, sig, bad, blockIdx.x, blockIdx.y, s_max, s_bad);
+}
+
 // |x| * 2^-sigma as a float (truncated mantissa; an estimate for slice selection)
 __device__ __forceinline__ float scaled_magnitude(uint64_t bits, int sigma) {
   const int E = (int)((bits >> 52) & 0x7FFu);
@@ -97,15 +107,14 @@ __device__ __forceinline__ float scaled_magnitude(uint64_t bits, int sigma) {
 }
 
 template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X, int64_t ld, int64_t R,
-                                                    int64_t K, const int* __restrict__ sig,
-                                                    float* __restrict__ mu) {
-  const int64_t p_begin = (int64_t)blockIdx.y * kRedChunk;
+__device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                                                const int* __restrict__ sig, float* __restrict__ mu, int64_t bx,
+                                                int64_t by, float (*s_sum)[33]) {
+  const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
-    __shared__ float s_sum[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t r = bx * 32 + tx;
     float acc = 0.0f;
     if (r < R) {
       const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
@@ -119,7 +128,7 @@ __global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X
     }
   } else {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * 8 + w;
+    const int64_t r = bx * 8 + w;
     if (r >= R) return;
     const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
     float acc = 0.0f;
@@ -129,13 +138,19 @@ __global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X
   }
 }
 
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X, int64_t ld, int64_t R,
+                                                    int64_t K, const int* __restrict__ sig,
+                                                    float* __restrict__ mu) {
+  __shared__ float s_sum[8][33];
+  magnitudes_body<ROWS_CONTIG>(X, ld, R, K, sig, mu, blockIdx.x, blockIdx.y, s_sum);
+}
+
 // stats = {min over non-empty rows of mu, min over non-empty columns of nu, any bad row, any bad column}
-__global__ void __launch_bounds__(256) k_min_stats(const float* __restrict__ muA, int64_t m,
-                                                   const float* __restrict__ muB, int64_t n,
-                                                   const int* __restrict__ badA, const int* __restrict__ badB,
-                                                   float* __restrict__ stats) {
-  __shared__ float s_min[2][256];
-  __shared__ int s_bad[2][256];
+__device__ __forceinline__ void min_stats_body(const float* __restrict__ muA, int64_t m, const float* __restrict__ muB,
+                                               int64_t n, const int* __restrict__ badA,
+                                               const int* __restrict__ badB, float* __restrict__ stats,
+                                               float (*s_min)[256], int (*s_bad)[256]) {
   float mn[2] = {3.0e38f, 3.0e38f};
   int bd[2] = {0, 0};
   for (int64_t i = threadIdx.x; i < m; i += 256) {
@@ -167,6 +182,15 @@ __global__ void __launch_bounds__(256) k_min_stats(const float* __restrict__ muA
   }
 }
 
+__global__ void __launch_bounds__(256) k_min_stats(const float* __restrict__ muA, int64_t m,
+                                                   const float* __restrict__ muB, int64_t n,
+                                                   const int* __restrict__ badA, const int* __restrict__ badB,
+                                                   float* __restrict__ stats) {
+  __shared__ float s_min[2][256];
+  __shared__ int s_bad[2][256];
+  min_stats_body(muA, m, muB, n, badA, badB, stats, s_min, s_bad);
+}
+
 // s digits of kDigitBits bits of |x| 2^-sigma, truncated toward zero, with the sign of x:
 // Q = floor(|x| 2^(s*b - sigma)) and digit t is bits [(s-t)b, (s-t+1)b) of Q.
 __device__ __forceinline__ uint64_t scaled_fixed(uint64_t bits, int sigma, int sb) {
@@ -190,35 +214,21 @@ __device__ __forceinline__ uint32_t bf16_of_digit(int d) {
 }
 
 constexpr int kTile = 64;
-constexpr int kPerThread = 16;  // k elements per thread in the write phase
+constexpr int kPerThread = 8;       // k elements per thread: one 16-byte store per slice
+constexpr int kSplitThreads = 512;  // 64 rows x 8 groups of 8 k per 64 x 64 tile
 
-template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(256) k_split(const double* __restrict__ X, int64_t ld, int64_t R,
-                                               int64_t K, const int* __restrict__ sig, int slices,
-                                               uint16_t* __restrict__ D, int64_t kp) {
-  __shared__ uint64_t tile[kTile][kTile + 1];
-  const int64_t p0 = (int64_t)blockIdx.x * kTile, r0 = (int64_t)blockIdx.y * kTile;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < kTile * kTile; idx += 256) {
-    int rr, pp;
-    if (ROWS_CONTIG) { rr = idx % kTile; pp = idx / kTile; }  // coalesced along rows
-    else { pp = idx % kTile; rr = idx / kTile; }              // coalesced along k
-    const int64_t r = r0 + rr, p = p0 + pp;
-    tile[rr][pp] = (r < R && p < K) ? load_bits<ROWS_CONTIG>(X, ld, r, p) : 0ull;
-  }
-  __syncthreads();
-  const int rr = tid >> 2, pp0 = (tid & 3) * kPerThread;
-  const int64_t r = r0 + rr, pbase = p0 + pp0;
-  if (r >= R || pbase >= K) return;
-  const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
+// digits of the 8 values x[0..7] (bits) of row r at k positions pbase..pbase+7, written to
+// every slice; 16-byte vector stores when all 8 are inside k (kp % 8 == 0, pbase % 8 == 0)
+__device__ __forceinline__ void write_digits(const uint64_t (&x)[kPerThread], int sg, int slices, int64_t R,
+                                             int64_t K, int64_t r, int64_t pbase, uint16_t* __restrict__ D,
+                                             int64_t kp) {
   const int sb = slices * kDigitBits;
   uint64_t q[kPerThread];
   uint32_t neg = 0;
 #pragma unroll
   for (int v = 0; v < kPerThread; ++v) {
-    const uint64_t b = tile[rr][pp0 + v];
-    q[v] = scaled_fixed(b, sg, sb);
-    neg |= (uint32_t)(b >> 63) << v;
+    q[v] = scaled_fixed(x[v], sg, sb);
+    neg |= (uint32_t)(x[v] >> 63) << v;
   }
   const bool full = pbase + kPerThread <= K;
   for (int t = 0; t < slices; ++t) {
@@ -233,14 +243,130 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ X, int
     }
     uint16_t* row = D + ((int64_t)t * R + r) * kp + pbase;
     if (full) {
-      uint4* dst = reinterpret_cast<uint4*>(row);  // 16-byte aligned: kp % 8 == 0, pbase % 16 == 0
-      dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-      dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      *reinterpret_cast<uint4*>(row) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     } else {
       for (int v = 0; v < kPerThread && pbase + v < K; ++v)
         row[v] = (uint16_t)((packed[v / 2] >> (16 * (v & 1))) & 0xFFFFu);
     }
   }
+}
+
+// Block (bx, by) writes the digits of the 64 x 64 (row, k) tile at (by*64, bx*64).
+// k contiguous in memory: each thread reads its 8 values directly (vector loads when
+// 16-byte aligned), a warp sweeps 2 KiB of one row.  Rows contiguous: the tile is
+// transposed through shared memory.
+template <bool ROWS_CONTIG>
+__device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                                           const int* __restrict__ sig, int slices, uint16_t* __restrict__ D,
+                                           int64_t kp, int64_t bx, int64_t by, uint64_t (*tile)[kTile + 1]) {
+  const int64_t p0 = bx * kTile, r0 = by * kTile;
+  const int tid = threadIdx.x;
+  const int rr = tid >> 3, pp0 = (tid & 7) * kPerThread;
+  const int64_t r = r0 + rr, pbase = p0 + pp0;
+  uint64_t x[kPerThread];
+  if (ROWS_CONTIG) {
+    // column pi of a tile row is stored at (pi & ~7) | ((pi ^ (pi >> 3)) & 7): the eight
+    // threads that read the same v of eight consecutive groups then hit eight banks
+#pragma unroll
+    for (int it = 0; it < kTile * kTile / kSplitThreads; ++it) {
+      const int idx = tid + it * kSplitThreads;
+      const int ri = idx % kTile, pi = idx / kTile;  // coalesced along rows
+      const int64_t rg = r0 + ri, pg = p0 + pi;
+      tile[ri][(pi & ~7) | ((pi ^ (pi >> 3)) & 7)] = (rg < R && pg < K) ? load_bits<true>(X, ld, rg, pg) : 0ull;
+    }
+    __syncthreads();
+    if (r >= R || pbase >= K) return;
+    const int grp = pp0 >> 3;
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) x[v] = tile[rr][pp0 + (v ^ grp)];
+  } else {
+    if (r >= R || pbase >= K) return;
+    const double* src = X + r * ld + pbase;
+    if (pbase + kPerThread <= K && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+      const longlong2* s2 = reinterpret_cast<const longlong2*>(src);
+#pragma unroll
+      for (int v = 0; v < kPerThread / 2; ++v) {
+        const longlong2 w = __ldg(s2 + v);
+        x[2 * v] = (uint64_t)w.x;
+        x[2 * v + 1] = (uint64_t)w.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < kPerThread; ++v)
+        x[v] = (pbase + v < K) ? (uint64_t)__double_as_longlong(__ldg(src + v)) : 0ull;
+    }
+  }
+  const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
+  write_digits(x, sg, slices, R, K, r, pbase, D, kp);
+}
+
+template <bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kSplitThreads) k_split(const double* __restrict__ X, int64_t ld, int64_t R,
+                                               int64_t K, const int* __restrict__ sig, int slices,
+                                               uint16_t* __restrict__ D, int64_t kp) {
+  __shared__ uint64_t tile[ROWS_CONTIG ? kTile : 1][kTile + 1];  // the transpose tile, when one is needed
+  split_body<ROWS_CONTIG>(X, ld, R, K, sig, slices, D, kp, blockIdx.x, blockIdx.y, tile);
+}
+
+// ---- batched forms over a job table (one operand side of one problem per job) ----
+__device__ __forceinline__ int find_job(const PrepJob* __restrict__ jobs, int njobs, int64_t b, bool split) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((split ? jobs[mid].split_begin : jobs[mid].exp_begin) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_prep_init_batched(const PrepJob* __restrict__ jobs) {
+  const PrepJob& j = jobs[blockIdx.x];
+  for (int64_t r = threadIdx.x; r < j.R; r += blockDim.x) {
+    j.sig[r] = kExpEmpty;
+    j.bad[r] = 0;
+    if (j.mu) j.mu[r] = 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_magnitudes_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ float s_sum[8][33];
+  const int ji = find_job(jobs, njobs, blockIdx.x, false);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig) magnitudes_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum);
+  else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum);
+}
+
+// block q: problem q, whose operand sides are jobs 2q (op(A)) and 2q+1 (op(B)^T)
+__global__ void __launch_bounds__(256) k_min_stats_batched(const PrepJob* __restrict__ jobs,
+                                                           float* __restrict__ stats) {
+  __shared__ float s_min[2][256];
+  __shared__ int s_bad[2][256];
+  const PrepJob& a = jobs[2 * blockIdx.x];
+  const PrepJob& b = jobs[2 * blockIdx.x + 1];
+  min_stats_body(a.mu, a.R, b.mu, b.R, a.bad, b.bad, stats + 4 * blockIdx.x, s_min, s_bad);
+}
+
+__global__ void __launch_bounds__(256) k_exponents_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ int s_max[8][33];
+  __shared__ int s_bad[8][33];
+  const int ji = find_job(jobs, njobs, blockIdx.x, false);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig) exponents_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.bad, bx, by, s_max, s_bad);
+  else exponents_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.bad, bx, by, s_max, s_bad);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
 }
 
 int launch_check(const char* what) {
@@ -263,12 +389,16 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
-  // one 128 x 256 FP64 slot per CTA of the two-SM kernel (at most one pair per 256 x 256 tile)
+  // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile);
+  // both slice kernels: one 128 x 256 int32 slot per CTA for the parked level sums
   const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
+  const int64_t single_tiles = ((m + 127) / 128) * ((n + 127) / 128);
   const int scratch_ctas =
       pair_scratch ? (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas) : 0;
+  const int single_ctas = pair_scratch ? (int)(single_tiles < kMaxPairCtas ? single_tiles : kMaxPairCtas) : 0;
+  const int p_ctas = scratch_ctas > single_ctas ? scratch_ctas : single_ctas;
   const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
-  const size_t o_scp = off; off = up(off + sizeof(int32_t) * 128 * 256 * (size_t)scratch_ctas);
+  const size_t o_scp = off; off = up(off + sizeof(int32_t) * 128 * 256 * (size_t)p_ctas);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -282,6 +412,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);
     ws->scratch_p = reinterpret_cast<int32_t*>(b + o_scp);
+    ws->scratch_p_ctas = p_ctas;
     ws->scratch_ctas = scratch_ctas;
     ws->kp = kp;
   }
@@ -312,12 +443,56 @@ int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, c
   return launch_check("statistics kernel launch");
 }
 
+void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks) {
+  const int64_t gy = (j.K + kRedChunk - 1) / kRedChunk;
+  j.exp_gx = (int)(j.rows_contig ? (j.R + 31) / 32 : (j.R + 7) / 8);
+  j.exp_begin = exp_blocks;
+  exp_blocks += (j.R > 0 && j.K > 0) ? (int64_t)j.exp_gx * gy : 0;
+  j.split_gx = (int)((j.K + kTile - 1) / kTile);
+  j.split_begin = split_blocks;
+  split_blocks += (j.R > 0 && j.K > 0) ? (int64_t)j.split_gx * ((j.R + kTile - 1) / kTile) : 0;
+}
+
+int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
+                        bool exponents, bool split, cudaStream_t s) {
+  if (njobs <= 0) return GBD_OK;
+  if (exponents) {
+    k_prep_init_batched<<<njobs, 256, 0, s>>>(jobs_dev);
+    int rc = launch_check("batched init launch");
+    if (rc) return rc;
+    if (exp_blocks > 0) {
+      if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many exponent blocks");
+      k_exponents_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
+      if ((rc = launch_check("batched exponent launch"))) return rc;
+    }
+  }
+  if (split && split_blocks > 0) {
+    if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+    k_split_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    return launch_check("batched split launch");
+  }
+  return GBD_OK;
+}
+
+int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
+                         cudaStream_t s) {
+  if (njobs <= 0) return GBD_OK;
+  int rc = launch_prep_batched(jobs_dev, njobs, exp_blocks, 0, true, false, s);
+  if (rc) return rc;
+  if (exp_blocks > 0) {
+    k_magnitudes_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
+    if ((rc = launch_check("batched magnitude launch"))) return rc;
+  }
+  k_min_stats_batched<<<njobs / 2, 256, 0, s>>>(jobs_dev, stats_dev);
+  return launch_check("batched statistics launch");
+}
+
 int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
                  const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s) {
   if (R == 0 || K == 0) return GBD_OK;
   dim3 grid((unsigned)((K + kTile - 1) / kTile), (unsigned)((R + kTile - 1) / kTile));
-  if (rows_contig) k_split<true><<<grid, 256, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
-  else k_split<false><<<grid, 256, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
+  if (rows_contig) k_split<true><<<grid, kSplitThreads, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
+  else k_split<false><<<grid, kSplitThreads, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
   return launch_check("split kernel launch");
 }
 

@@ -98,6 +98,13 @@ struct gbd_plan {
   std::vector<gbd::emu::EmuTableEntry> emu_table;
   gbd::emu::EmuTableEntry* emu_dev = nullptr;
   int64_t emu_tiles = 0;
+  // batched preparation: jobs 2q, 2q+1 are op(A) and op(B)^T of emulated problem q
+  std::vector<gbd::emu::PrepJob> jobs;
+  gbd::emu::PrepJob* jobs_dev = nullptr;
+  float* stats_dev = nullptr;
+  int64_t exp_blocks = 0, split_blocks = 0;
+  int32_t* scratch_p = nullptr;  // parked level sums of the grouped slice kernel
+  int scratch_p_ctas = 0;
 };
 
 namespace gbd {
@@ -117,6 +124,21 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(NativeTableEntry) * (size_t)nnat);
   const size_t o_emu = off;
   off = up256(off + sizeof(emu::EmuTableEntry) * (size_t)nemu);
+  const size_t o_jobs = off;
+  off = up256(off + sizeof(emu::PrepJob) * 2 * (size_t)nemu);
+  const size_t o_stats = off;
+  off = up256(off + sizeof(float) * 4 * (size_t)nemu);
+  // parked level sums of the grouped slice kernel: one 128 x kGroupedBN int32 slot per CTA
+  int64_t emu_tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_EMULATED && !quick)
+      emu_tiles += ((p.m + 127) / 128) * ((p.n + emu::kGroupedBN - 1) / emu::kGroupedBN);
+  }
+  const int p_ctas = (int)(emu_tiles < emu::kMaxPairCtas ? emu_tiles : emu::kMaxPairCtas);
+  const size_t o_scp = off;
+  off = up256(off + sizeof(int32_t) * 128 * emu::kGroupedBN * (size_t)p_ctas);
   int ei = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];
@@ -133,6 +155,10 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     plan->counter_dev = reinterpret_cast<unsigned long long*>(base);
     plan->native_dev = reinterpret_cast<NativeTableEntry*>(static_cast<char*>(base) + o_native);
     plan->emu_dev = reinterpret_cast<emu::EmuTableEntry*>(static_cast<char*>(base) + o_emu);
+    plan->jobs_dev = reinterpret_cast<emu::PrepJob*>(static_cast<char*>(base) + o_jobs);
+    plan->stats_dev = reinterpret_cast<float*>(static_cast<char*>(base) + o_stats);
+    plan->scratch_p = reinterpret_cast<int32_t*>(static_cast<char*>(base) + o_scp);
+    plan->scratch_p_ctas = p_ctas;
   }
   return off;
 }
@@ -222,36 +248,39 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   for (int i = 0; i < count; ++i) s_override[i] = probs[i].slices;
   grouped_layout(probs, count, s_override.data(), workspace, plan);
 
-  // automatic slice counts: exponents and magnitude statistics now, one read-back for all
+  // preparation jobs: op(A) and op(B)^T of every emulated problem
   cudaError_t e;
+  plan->jobs.resize(2 * plan->emu.size());
   bool any_auto = false;
-  for (auto& em : plan->emu) {
-    if (em.slices != 0) continue;
-    any_auto = true;
+  for (size_t q = 0; q < plan->emu.size(); ++q) {
+    const auto& em = plan->emu[q];
     const gbd_problem& p = em.p;
     const emu::Workspace& ws = em.ws;
-    const int ta = trans_code(p.transa), tb = trans_code(p.transb);
-    if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.muA, 0, sizeof(float) * (size_t)p.m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.muB, 0, sizeof(float) * (size_t)p.n, s)) != cudaSuccess)
-      return cuda_fail(e, "grouped: workspace initialisation");
-    if ((rc = emu::launch_exponents(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.badA, s))) return rc;
-    if ((rc = emu::launch_exponents(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.badB, s))) return rc;
-    if ((rc = emu::launch_magnitudes(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.muA, s))) return rc;
-    if ((rc = emu::launch_magnitudes(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.muB, s))) return rc;
-    if ((rc = emu::launch_min_stats(ws.muA, p.m, ws.muB, p.n, ws.badA, ws.badB, ws.stats, s))) return rc;
+    any_auto = any_auto || em.slices == 0;
+    emu::PrepJob& ja = plan->jobs[2 * q];
+    emu::PrepJob& jb = plan->jobs[2 * q + 1];
+    memset(&ja, 0, sizeof(ja));
+    memset(&jb, 0, sizeof(jb));
+    // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
+    ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
+    ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp;
+    jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
+    jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp;
+    emu::prep_job_blocks(ja, plan->exp_blocks, plan->split_blocks);
+    emu::prep_job_blocks(jb, plan->exp_blocks, plan->split_blocks);
   }
+  // automatic slice counts: batched exponents and magnitude statistics, one read-back for all
   if (any_auto) {
+    if ((e = cudaMemcpyAsync(plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: job table copy");
+    if ((rc = emu::launch_stats_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->stats_dev, s)))
+      return rc;
     std::vector<float> st(4 * plan->emu.size(), 0.0f);
-    for (size_t q = 0; q < plan->emu.size(); ++q)
-      if (plan->emu[q].slices == 0 &&
-          (e = cudaMemcpyAsync(&st[4 * q], plan->emu[q].ws.stats, 4 * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
-              cudaSuccess)
-        return cuda_fail(e, "grouped: reading statistics");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "grouped: reading statistics");
+    if ((e = cudaMemcpyAsync(st.data(), plan->stats_dev, sizeof(float) * st.size(), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: reading statistics");
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       auto& em = plan->emu[q];
       if (em.slices != 0) continue;
@@ -259,6 +288,12 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * 1.1102230246251565e-16;
       em.slices = (mu > 0.0 && nu > 0.0) ? emu::choose_slices(target, mu, nu, em.p.k, nullptr) : 1;
     }
+  }
+  for (size_t q = 0; q < plan->emu.size(); ++q) {
+    plan->jobs[2 * q].slices = plan->emu[q].slices;
+    plan->jobs[2 * q + 1].slices = plan->emu[q].slices;
+    plan->jobs[2 * q].mu = nullptr;  // runs need no magnitude sums
+    plan->jobs[2 * q + 1].mu = nullptr;
   }
   // emulated table: tensor maps and tile counts, longest tiles first
   std::vector<int> order(plan->emu.size());
@@ -311,6 +346,10 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       (e = cudaMemcpyAsync(plan->emu_dev, plan->emu_table.data(), sizeof(emu::EmuTableEntry) * plan->emu_table.size(),
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e, "grouped: emulated table copy");
+  if (!plan->jobs.empty() &&
+      (e = cudaMemcpyAsync(plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped: job table copy");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "grouped: plan set-up");
   *out = plan;
   return GBD_OK;
@@ -324,23 +363,14 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
   int rc = current_device(nullptr, &sms);
   if (rc) return rc;
   cudaError_t e;
-  // emulated: exponents and digit slices of every problem, then one slice-product launch
-  for (auto& em : plan->emu) {
-    const gbd_problem& p = em.p;
-    const emu::Workspace& ws = em.ws;
-    const int ta = trans_code(p.transa), tb = trans_code(p.transb);
-    if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)p.n, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)p.m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)p.n, s)) != cudaSuccess)
-      return cuda_fail(e, "grouped: workspace initialisation");
-    if ((rc = emu::launch_exponents(p.A, p.lda, p.m, p.k, ta == 0, ws.sigA, ws.badA, s))) return rc;
-    if ((rc = emu::launch_exponents(p.B, p.ldb, p.n, p.k, tb != 0, ws.sigB, ws.badB, s))) return rc;
-    if ((rc = emu::launch_split(p.A, p.lda, p.m, p.k, ta == 0, em.ws.sigA, em.slices, em.ws.DA, em.ws.kp, s))) return rc;
-    if ((rc = emu::launch_split(p.B, p.ldb, p.n, p.k, tb != 0, em.ws.sigB, em.slices, em.ws.DB, em.ws.kp, s))) return rc;
-  }
+  // emulated: exponents and digit slices of every problem (three launches), then one slice-product launch
+  if (!plan->jobs.empty() &&
+      (rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->split_blocks,
+                                     true, true, s)))
+    return rc;
   if (plan->emu_tiles > 0 &&
-      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles, s)))
+      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles,
+                                           plan->scratch_p, plan->scratch_p_ctas, s)))
     return rc;
   // native: one persistent launch over all tiles
   if (plan->native_tiles > 0) {

@@ -28,6 +28,24 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
 
+// A bounded wait that nothing completes: the watchdog path of every kernel, exercised
+// on purpose.  One thread waits on a fresh mbarrier's first phase for limit_ns, gives up,
+// sets kErrWaitTma in the error word and the kernel ends normally.
+__global__ void k_watchdog_selftest(unsigned int* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(&bar, 0)) return;  // never: no thread arrives
+    if ((it & 255u) == 0u && global_ns() - t0 > limit_ns) {
+      atomicOr(err, kErrWaitTma);
+      return;
+    }
+  }
+}
+
 __global__ void k_scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc) {
   const int64_t total = m * n;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -172,6 +190,17 @@ extern "C" {
 int gbd_version(void) { return 100; }  // 0.1.0
 
 const char* gbd_last_error(void) { return gbd::g_msg; }
+
+int gbd_watchdog_selftest(int limit_ms, void* stream) {
+  if (limit_ms < 1 || limit_ms > 10000) return gbd::set_error(GBD_ERR_ARG, "watchdog: limit_ms must be in 1..10000");
+  int rc = gbd::current_device(nullptr, nullptr);
+  if (rc) return rc;
+  unsigned int* err = gbd::device_error_word();
+  if (!err) return gbd::set_error(GBD_ERR_CUDA, "device error word not reachable");
+  gbd::k_watchdog_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(err, (unsigned long long)limit_ms * 1000000ull);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : gbd::cuda_fail(e, "watchdog self-test launch");
+}
 
 int gbd_check_device_error(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);

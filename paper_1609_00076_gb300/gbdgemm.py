@@ -104,6 +104,7 @@ _EXTRA_DECLS: list = [
                        ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_noalloc", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d,
                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_watchdog_selftest", [_i, _vp], _i),
     ("gbd_dgemm_grouped_workspace_size", [_vp, _i], _sz),
     ("gbd_grouped_plan_create", [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)], _i),
     ("gbd_grouped_plan_run", [_vp, _vp], _i),
@@ -239,6 +240,10 @@ def gbd_dgemm_grouped(problems, workspace, workspace_bytes, slices_used=None, st
     return load().gbd_dgemm_grouped(ctypes.cast(arr, _vp), len(problems), _addr(workspace), int(workspace_bytes),
                                     ctypes.cast(slices_used, _vp) if slices_used is not None else None,
                                     _stream(stream))
+
+
+def gbd_watchdog_selftest(limit_ms: int, stream=None) -> int:
+    return load().gbd_watchdog_selftest(int(limit_ms), _stream(stream))
 
 
 def gbd_check_device_error(stream=None) -> int:
