@@ -50,7 +50,7 @@ NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
 # dram bytes (read + write) per launch of the dominant kernel, from one single-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload; None until captured
 # for the current kernel
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": None}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 45.4e9}
 
 
 def load_peaks():
@@ -471,6 +471,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--only", choices=["grouped", "serving"],
+                    help="run only the grouped-batch or the serving measurement and print it (profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the grouped-batch and serving measurements (profiling runs)")
     ap.add_argument("--size", type=int, default=8192,
@@ -480,6 +482,15 @@ def main():
     M = N = K = args.size
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.only:
+        import torch
+
+        from paper_1609_00076_gb300 import gbdgemm
+        gbdgemm.load()
+        dev = torch.device("cuda", 0)
+        res = grouped_measure(dev, torch.cuda.Stream(device=dev), reps=1) if args.only == "grouped" else serving_measure()
+        print(json.dumps(res), flush=True)
+        return 0
     world, rank, local, pg = dist_setup(args)
     try:
         if args.impl == "reference":
