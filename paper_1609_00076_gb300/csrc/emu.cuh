@@ -8,8 +8,11 @@
 //   3. for every level g = 2..s+1 the exact integer sum over the digit pairs
 //      t + u = g, computed on the BF16 tensor cores with FP32 accumulation that is
 //      exact by construction (all partial sums are integers below 2^24);
-//   4. C := beta*C, then C := fma(alpha*2^(sigma_i + tau_j - g*b), P_g, C) from the
-//      smallest level to the largest, in FP64.
+//   4. C := beta*C; then, segment by segment of the inner dimension, the levels are
+//      taken from the smallest in groups of up to kGroupLevels consecutive levels
+//      whose sums are combined exactly in 64-bit integers,
+//          Y = sum_{g in group} P_g 2^(b (h - g))   (h the group's smallest level),
+//      and C := fma(alpha*2^(sigma_i + tau_j - h*b), Y, C) in FP64, once per group.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +29,8 @@ constexpr int kMaxSlices = 9;      // s * kDigitBits <= 63 bits of the scaled ma
 constexpr int kBK = 64;            // k elements per pipeline stage (128 bytes of BF16)
 constexpr int kChunkBlocks = 16;   // k-blocks per exact FP32 chunk: 1024 * 127^2 < 2^24
 constexpr int kSegBlocks = 128;    // k-blocks per integer level segment: 9 * 8192 * 127^2 < 2^31
+constexpr int kGroupLevels = 4;    // levels per exact group: 2^30.2 * (1 + 2^7 + 2^14 + 2^21) < 2^52
+constexpr int kParkSlots = 2 * kGroupLevels;  // parked level sums: the group being drained + the pending one
 constexpr int kExpEmpty = (int)0x80808080;  // exponent of a row/column with no non-zero entry
 
 // Layout of the caller's workspace (every array 256-byte aligned).
@@ -40,7 +45,7 @@ struct Workspace {
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
-  int32_t* scratch_p;  // [scratch_p_ctas][128 * 256] parked integer level sums of the slice kernels
+  int32_t* scratch_p;  // [scratch_p_ctas][kParkSlots][128 * 256] parked integer level sums of the slice kernels
   int scratch_ctas;
   int scratch_p_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
@@ -119,7 +124,7 @@ constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
 // tensor maps of one problem's slices for the grouped kernel
 int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
 // one launch over all problems of a device table (entries sorted by decreasing tile cost)
-// scratch_p: max_ctas slots of 128 x kGroupedBN int32 (parked level sums); the grid is capped at max_ctas
+// scratch_p: max_ctas x kParkSlots slots of 128 x kGroupedBN int32 (parked level sums); the grid is capped at max_ctas
 int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int32_t* scratch_p,
                               int max_ctas, cudaStream_t s);
 

@@ -3,7 +3,7 @@
 // Tensor Memory), exact integer level sums, and the FP64 update of C.
 //
 // Persistent, warp-specialised kernel; one 128 x BN output tile at a time per CTA:
-//   warp 0      TMA producer: for each (level g, segment, pair t, k-block) loads the
+//   warp 0      TMA producer: for each (segment, level g, pair t, k-block) loads the
 //               128 x 64 tile of digit slice t of op(A) and the BN x 64 tile of slice
 //               g-t of op(B)^T (128-byte swizzle) into a kStages-deep ring;
 //   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per k-block into one
@@ -12,9 +12,12 @@
 //               2^24 and exact;
 //   warps 2..9  epilogue: drain each finished chunk from TMEM (tcgen05.ld) and add it
 //               exactly into 32-bit integer registers (cvt.rni.s32.f32 of an exact
-//               integer), so the MMA runs on while a chunk is drained; at
-//               the end of a level segment, C := fma(alpha 2^(tau_j - g b), P 2^sigma_i, C)
-//               with one FP64 fma per element, coalesced down the columns of C.
+//               integer), so the MMA runs on while a chunk is drained.  A finished
+//               level's sums are parked in scratch; at the end of a group of up to
+//               kGroupLevels levels (smallest level h) they are combined exactly into
+//               Y = sum_g P_g 2^(b (h - g)) in 64-bit integers and
+//               C := fma(alpha 2^(tau_j - h b), Y 2^sigma_i, C), one FP64 fma per
+//               element and group, coalesced down the columns of C.
 // All waits are bounded (2 s); a wait that gives up sets the device error word and
 // the kernel runs to its end without hanging.
 #include <cstdint>
@@ -126,17 +129,29 @@ __device__ __forceinline__ void epi_bar_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
 }
 
-// P * 2^sigma as a double, exactly (P is an integer with |P| <= 2^31)
-__device__ __forceinline__ double scaled_int(int32_t P, int sigma) {
-  if (P == 0) return 0.0;
-  const uint32_t a = P < 0 ? 0u - (uint32_t)P : (uint32_t)P;
-  const int msb = 31 - __clz(a);
+// Y * 2^sigma as a double, exactly (Y is an integer with |Y| < 2^53)
+__device__ __forceinline__ double scaled_i64(int64_t Y, int sigma) {
+  if (Y == 0) return 0.0;
+  const uint64_t a = Y < 0 ? 0ull - (uint64_t)Y : (uint64_t)Y;
+  const int msb = 63 - __clzll((long long)a);
   const int ef = 1023 + msb + sigma;
-  if (ef <= 0 || ef >= 2047) return ldexp((double)P, sigma);  // outside the normal range
-  const uint64_t mant = ((uint64_t)a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
-  const uint64_t bits = ((uint64_t)(P < 0) << 63) | ((uint64_t)ef << 52) | mant;
+  if (ef <= 0 || ef >= 2047) return ldexp((double)Y, sigma);  // outside the normal range
+  const uint64_t mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
+  const uint64_t bits = ((uint64_t)(Y < 0) << 63) | ((uint64_t)ef << 52) | mant;
   return __longlong_as_double((long long)bits);
 }
+
+// Parked sums P_l (l = h - g, level g of the group whose smallest level is h) combined
+// exactly: Y = sum_l P_l 2^(b l); levels the group does not have are zero.
+__device__ __forceinline__ int64_t combine_levels(const int32_t (&P)[kGroupLevels]) {
+  int64_t Y = P[kGroupLevels - 1];
+#pragma unroll
+  for (int l = kGroupLevels - 2; l >= 0; --l) Y = Y * (1 << kDigitBits) + P[l];
+  return Y;
+}
+
+// largest level of the group whose smallest level is h (levels h, h-1, ..., down to 2)
+__device__ __forceinline__ int group_high(int h) { return max(2, h - kGroupLevels + 1); }
 
 // Tile order: the CTAs that run at the same time take consecutive tile indices;
 // grouping group_m row tiles per column makes that set a near-square block, so the
@@ -270,18 +285,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tmB) : "memory");
         }
         const int m0 = j.m0, n0 = j.n0;
-        for (int g = j.s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
-            const int segn = min(kSegBlocks, j.nkb - seg0);
-            for (int t = 1; t <= g - 1; ++t)
-              for (int kb = seg0; kb < seg0 + segn; ++kb) {
-                mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
-                mbar_arrive_expect_tx(&full[stage], bytes);
-                tma_load_3d(smem + L::kOffA + stage * L::kABytes, j.tmA, &full[stage], kb * kBK, m0, t - 1);
-                tma_load_3d(smem + L::kOffB + stage * L::kBBytes, j.tmB, &full[stage], kb * kBK, n0, g - t - 1);
-                if (++stage == kStages) { stage = 0; phase ^= 1u; }
-              }
-          }
+        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, j.nkb - seg0);
+          for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
+            for (int g = h; g >= group_high(h); --g)
+              for (int t = 1; t <= g - 1; ++t)
+                for (int kb = seg0; kb < seg0 + segn; ++kb) {
+                  mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
+                  mbar_arrive_expect_tx(&full[stage], bytes);
+                  tma_load_3d(smem + L::kOffA + stage * L::kABytes, j.tmA, &full[stage], kb * kBK, m0, t - 1);
+                  tma_load_3d(smem + L::kOffB + stage * L::kBBytes, j.tmB, &full[stage], kb * kBK, n0, g - t - 1);
+                  if (++stage == kStages) { stage = 0; phase ^= 1u; }
+                }
+        }
       }
     }
     __syncwarp();
@@ -294,8 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Job j;
         get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
-        for (int g = j.s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks)
+          for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
+          for (int g = h; g >= group_high(h); --g) {
             const int segn = min(kSegBlocks, j.nkb - seg0);
             const int items = (g - 1) * segn;
             for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
@@ -325,42 +342,50 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------ epilogue ----------------------------------
-    // A finished level segment's integer sums are parked in this CTA's scratch slot
-    // and folded into C a few columns per drained chunk of the next segment (the
-    // last segment of a tile during the next tile), so the MMA does not wait.
+    // Each finished level's integer sums are parked in one of this CTA's scratch
+    // slots.  A finished group is folded into C a few columns per drained chunk of
+    // the next group (the last group of a tile during the next tile), so the MMA does
+    // not wait; two sets of slots hold the group being drained and the pending one.
     constexpr int kCols = BN / 2;  // columns per thread
+    constexpr int kStep = 4;       // columns per step of the pending update
+    constexpr int64_t kSlot = (int64_t)128 * BN;  // one parked level of the tile
     const int ew = warp - 2;
     const int quad = warp & 3;     // TMEM lanes 32*quad .. +31 are reachable from this warp
     const int half = ew >> 2;      // which half of the tile's columns
     const int row = quad * 32 + lane;
     const int col0 = half * kCols;
-    int32_t* scrP = p.scratch_p + (int64_t)blockIdx.x * (128 * BN) + (int64_t)((half * 4 + quad) * kCols) * 32 + lane;
+    int32_t* scrP = p.scratch_p + (int64_t)blockIdx.x * (kParkSlots * kSlot) +
+                    (int64_t)((half * 4 + quad) * kCols) * 32 + lane;
     uint32_t chunk = 0;
     uint32_t acc[kCols];
     bool pd_active = false, pd_first = false, pd_bad = false, pd_row_ok = false;
-    int pd_done = 0, pd_sig = 0, pd_buf = 0, cs_next = 0;
+    int pd_done = 0, pd_sig = 0, pd_buf = 0, pd_set = 0, pd_nlev = 0, cs_next = 0, park_set = 0;
     double pd_beta = 0.0;
     double* pd_crow = nullptr;
     int64_t pd_ldc = 0, pd_cols_left = 0;
-    // eight columns per step: all their loads are issued before any is used
+    // kStep columns per step: all their loads are issued before any is used
     auto advance = [&](int ncols) {
       const int c1 = min(pd_done + ncols, kCols);
       const double* cs = colscale + pd_buf * BN + col0;
-      for (int c = pd_done; c < c1; c += 8) {
-        double w[8];
-        int32_t P[8];
+      const int32_t* pk = scrP + (int64_t)pd_set * kGroupLevels * kSlot;
+      for (int c = pd_done; c < c1; c += kStep) {
+        double w[kStep];
+        int32_t P[kStep][kGroupLevels];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStep; ++u) {
           const bool ok = c + u < c1 && pd_row_ok && c + u < pd_cols_left;
           const double* cp = pd_crow + (int64_t)(c + u) * pd_ldc;
           w[u] = (ok && !(pd_first && pd_beta == 0.0)) ? *cp : 0.0;
-          P[u] = (c + u < c1) ? scrP[(c + u) * 32] : 0;
+#pragma unroll
+          for (int l = 0; l < kGroupLevels; ++l)
+            P[u][l] = (c + u < c1 && l < pd_nlev) ? pk[l * kSlot + (c + u) * 32] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStep; ++u) {
           if (c + u < c1 && pd_row_ok && c + u < pd_cols_left) {
             const double wp = pd_first ? (pd_beta == 0.0 ? 0.0 : pd_beta * w[u]) : w[u];
-            const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P[u], pd_sig);
+            const double x =
+                pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(combine_levels(P[u]), pd_sig);
             pd_crow[(int64_t)(c + u) * pd_ldc] = fma(cs[c + u], x, wp);
           }
         }
@@ -382,30 +407,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         bad_i = j.badA[i] != 0;
       }
       bool first = true;
-      for (int g = j.s + 1; g >= 2; --g)
-        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
-          const int segn = min(kSegBlocks, j.nkb - seg0);
-          const int nch = chunks_of(g, segn);
-          const int portion = (kCols + nch - 1) / nch;  // spread the pending update over this segment
+      for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+        const int segn = min(kSegBlocks, j.nkb - seg0);
+        for (int h = j.s + 1; h >= 2; h -= kGroupLevels) {
+          const int glo = group_high(h);
+          int gch = 0;  // chunks of this group: the pending update is spread over them
+          for (int g = h; g >= glo; --g) gch += chunks_of(g, segn);
+          const int portion = ((kCols + gch - 1) / gch + kStep - 1) / kStep * kStep;
+          for (int g = h; g >= glo; --g) {
+            const int nch = chunks_of(g, segn);
 #pragma unroll
-          for (int c = 0; c < kCols; ++c) acc[c] = 0u;
-          for (int ci = 0; ci < nch; ++ci, ++chunk) {
-            const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-            mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
-            tc_fence_after();
-            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + col0;
+            for (int c = 0; c < kCols; ++c) acc[c] = 0u;
+            for (int ci = 0; ci < nch; ++ci, ++chunk) {
+              const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+              mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+              tc_fence_after();
+              const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + col0;
 #pragma unroll
-            for (int q = 0; q < kCols / 16; ++q) {
-              uint32_t v[16];
-              tmem_ld_16(taddr + q * 16, v);
+              for (int q = 0; q < kCols / 16; ++q) {
+                uint32_t v[16];
+                tmem_ld_16(taddr + q * 16, v);
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += (uint32_t)__float2int_rn(__uint_as_float(v[jj]));
+                for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += (uint32_t)__float2int_rn(__uint_as_float(v[jj]));
+              }
+              tc_fence_before();
+              mbar_arrive(&acc_empty[buf]);
+              if (pd_active) advance(portion);
             }
-            tc_fence_before();
-            mbar_arrive(&acc_empty[buf]);
-            if (pd_active) advance(portion);
+            int32_t* dst = scrP + (int64_t)(park_set * kGroupLevels + (h - g)) * kSlot;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) dst[c * 32] = (int32_t)acc[c];
           }
-          // segment end: finish the previous pending update, then park this one
+          // group end: finish the previous pending update, then make this group pending
           if (pd_active) advance(kCols);
           epi_bar_sync();  // nobody reads the colscale buffer about to be rewritten
           {
@@ -416,14 +449,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (jc < j.n) {
                 int tau = j.sigB[jc];
                 if (tau == kExpEmpty) tau = 0;
-                cs = j.badB[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - g * kDigitBits);
+                cs = j.badB[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - h * kDigitBits);
               }
               colscale[cs_next * BN + idx] = cs;
             }
           }
           epi_bar_sync();
-#pragma unroll
-          for (int c = 0; c < kCols; ++c) scrP[c * 32] = (int32_t)acc[c];
           pd_active = true;
           pd_done = 0;
           pd_first = first;
@@ -432,14 +463,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           pd_row_ok = row_ok;
           pd_sig = sig_i;
           pd_buf = cs_next;
+          pd_set = park_set;
+          pd_nlev = h - glo + 1;
           pd_crow = j.C + (n0 + col0) * j.ldc + i;
           pd_ldc = j.ldc;
           pd_cols_left = j.n - n0 - col0;
           cs_next ^= 1;
+          park_set ^= 1;
           first = false;
         }
+      }
     }
-    if (pd_active) advance(kCols);  // the last level of the last tile
+    if (pd_active) advance(kCols);  // the last group of the last tile
   }
 
   tc_fence_before();
@@ -456,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // SM holding 128 rows x 256 columns in its TMEM (two accumulators of 256 columns).
 // Each CTA loads its own 128 rows of the A slice and 128 of the 256 rows of the B
 // slice; the leader's MMA reads both CTAs' shared memory.  Between level
-// segments the FP64 running sum of each CTA's 128 x 256 block lives in a private
+// groups the FP64 running sum of each CTA's 128 x 256 block lives in a private
 // scratch slot of the workspace, laid out so that every warp access is 256
 // contiguous bytes and each warp sweeps 32 KiB in order; C itself is read once
 // (beta*C0) and written once per tile.
@@ -602,19 +637,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
         const int m0 = tm * k2BM + (int)rank * 128;
         const int nb0 = tn * k2BN + (int)rank * 128;
-        for (int g = s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-            const int segn = min(kSegBlocks, p.nkb - seg0);
-            for (int t = 1; t <= g - 1; ++t)
-              for (int kb = seg0; kb < seg0 + segn; ++kb) {
-                mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
-                if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
-                const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
-                tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, t - 1);
-                tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, g - t - 1);
-                if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
-              }
-          }
+        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, p.nkb - seg0);
+          for (int h = s + 1; h >= 2; h -= kGroupLevels)
+            for (int g = h; g >= group_high(h); --g)
+              for (int t = 1; t <= g - 1; ++t)
+                for (int kb = seg0; kb < seg0 + segn; ++kb) {
+                  mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
+                  if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
+                  const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
+                  tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, t - 1);
+                  tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, g - t - 1);
+                  if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
+                }
+        }
       }
     }
     __syncwarp();
@@ -625,8 +661,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
       for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
-        for (int g = s + 1; g >= 2; --g)
-          for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks)
+          for (int h = s + 1; h >= 2; h -= kGroupLevels)
+          for (int g = h; g >= group_high(h); --g) {
             const int segn = min(kSegBlocks, p.nkb - seg0);
             const int items = (g - 1) * segn;
             for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
@@ -656,9 +693,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------ epilogue (both CTAs) ------------------------------
-    // The FP64 update of a finished level segment is deferred: its integer sums are
-    // parked in scratch and folded into the running sums a few columns at a time
-    // while the next segment's chunks are drained, so the MMA never waits for it.
+    // Each finished level's integer sums are parked in scratch; the FP64 update of a
+    // finished group of levels is deferred and folded into the running sums a few
+    // columns at a time while the next group's chunks are drained, so the MMA never
+    // waits for it.  Two sets of park slots hold the group being drained and the
+    // pending one.
+    constexpr int kStep = 4;  // columns per step of the pending update
+    constexpr int64_t kSlot = (int64_t)128 * k2BN;  // one parked level of the CTA's block
     const int ew = warp - 2;
     const int quad = warp & 3;
     const int half = ew >> 2;
@@ -666,9 +707,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int col0 = half * k2ColsPerThread;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     // this thread's column sweep in the CTA's scratch slots: 256 (or 128) contiguous bytes per warp per column
-    const int64_t slot = (int64_t)blockIdx.x * (128 * k2BN) + (int64_t)((half * 4 + quad) * k2ColsPerThread) * 32 + lane;
-    double* scrW = p.scratch + slot;
-    int32_t* scrP = p.scratch_p + slot;
+    const int64_t within = (int64_t)((half * 4 + quad) * k2ColsPerThread) * 32 + lane;
+    double* scrW = p.scratch + (int64_t)blockIdx.x * kSlot + within;
+    int32_t* scrP = p.scratch_p + (int64_t)blockIdx.x * (kParkSlots * kSlot) + within;
     uint32_t chunk = 0;
     uint32_t acc[k2ColsPerThread];
     uint32_t empty_remote[2];
@@ -676,30 +717,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
     // the pending update
     bool pd_active = false, pd_first = false, pd_last = false, pd_bad = false, pd_row_ok = false;
-    int pd_done = 0, pd_sig = 0, pd_buf = 0, cs_next = 0;
+    int pd_done = 0, pd_sig = 0, pd_buf = 0, pd_set = 0, pd_nlev = 0, cs_next = 0, park_set = 0;
     double* pd_crow = nullptr;
     int64_t pd_cols_left = 0;  // columns of the pending tile inside C (n - n0 - col0, clamped)
-    // eight columns per step: all their loads are issued before any is used
+    // kStep columns per step: all their loads are issued before any is used
     auto advance = [&](int ncols) {
       const int c1 = min(pd_done + ncols, k2ColsPerThread);
       const double* cs = colscale + pd_buf * k2BN + col0;
-      for (int c = pd_done; c < c1; c += 8) {
-        double w[8];
-        int32_t P[8];
+      const int32_t* pk = scrP + (int64_t)pd_set * kGroupLevels * kSlot;
+      for (int c = pd_done; c < c1; c += kStep) {
+        double w[kStep];
+        int32_t P[kStep][kGroupLevels];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStep; ++u) {
           const bool in = c + u < c1;
           const bool col_ok = in && pd_row_ok && c + u < pd_cols_left;
           if (pd_first) w[u] = (p.beta != 0.0 && col_ok) ? pd_crow[(int64_t)(c + u) * p.ldc] : 0.0;
           else w[u] = in ? scrW[(c + u) * 32] : 0.0;
-          P[u] = in ? scrP[(c + u) * 32] : 0;
+#pragma unroll
+          for (int l = 0; l < kGroupLevels; ++l) P[u][l] = (in && l < pd_nlev) ? pk[l * kSlot + (c + u) * 32] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStep; ++u) {
           if (c + u >= c1) continue;
           const bool col_ok = pd_row_ok && c + u < pd_cols_left;
           const double wp = pd_first ? (p.beta != 0.0 && col_ok ? p.beta * w[u] : 0.0) : w[u];
-          const double x = pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_int(P[u], pd_sig);
+          const double x =
+              pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(combine_levels(P[u]), pd_sig);
           const double r = fma(cs[c + u], x, wp);
           if (pd_last) {
             if (col_ok) pd_crow[(int64_t)(c + u) * p.ldc] = r;
@@ -726,31 +770,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         bad_i = p.badA[i] != 0;
       }
       bool first = true;
-      for (int g = s + 1; g >= 2; --g)
-        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-          const int segn = min(kSegBlocks, p.nkb - seg0);
-          const int nch = chunks_of(g, segn);
-          const bool last = (g == 2) && (seg0 + kSegBlocks >= p.nkb);
-          const int portion = (k2ColsPerThread + nch - 1) / nch;  // spread the pending update over this segment
+      for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
+        const int segn = min(kSegBlocks, p.nkb - seg0);
+        for (int h = s + 1; h >= 2; h -= kGroupLevels) {
+          const int glo = group_high(h);
+          const bool last = (glo == 2) && (seg0 + kSegBlocks >= p.nkb);
+          int gch = 0;  // chunks of this group: the pending update is spread over them
+          for (int g = h; g >= glo; --g) gch += chunks_of(g, segn);
+          const int portion = ((k2ColsPerThread + gch - 1) / gch + kStep - 1) / kStep * kStep;
+          for (int g = h; g >= glo; --g) {
+            const int nch = chunks_of(g, segn);
 #pragma unroll
-          for (int c = 0; c < k2ColsPerThread; ++c) acc[c] = 0u;
-          for (int ci = 0; ci < nch; ++ci, ++chunk) {
-            const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-            mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
-            tc_fence_after();
-            const uint32_t taddr = tmem_base + lane_base + buf * k2BN + col0;
+            for (int c = 0; c < k2ColsPerThread; ++c) acc[c] = 0u;
+            for (int ci = 0; ci < nch; ++ci, ++chunk) {
+              const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+              mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+              tc_fence_after();
+              const uint32_t taddr = tmem_base + lane_base + buf * k2BN + col0;
 #pragma unroll
-            for (int q = 0; q < k2ColsPerThread / 16; ++q) {
-              uint32_t v[16];
-              tmem_ld_16(taddr + q * 16, v);
+              for (int q = 0; q < k2ColsPerThread / 16; ++q) {
+                uint32_t v[16];
+                tmem_ld_16(taddr + q * 16, v);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
+                for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
+              }
+              tc_fence_before();
+              mbar_arrive_remote(empty_remote[buf]);
+              if (pd_active) advance(portion);
             }
-            tc_fence_before();
-            mbar_arrive_remote(empty_remote[buf]);
-            if (pd_active) advance(portion);
+            int32_t* dst = scrP + (int64_t)(park_set * kGroupLevels + (h - g)) * kSlot;
+#pragma unroll
+            for (int c = 0; c < k2ColsPerThread; ++c) dst[c * 32] = (int32_t)acc[c];
           }
-          // segment end: finish the previous pending update, then park this one
+          // group end: finish the previous pending update, then make this group pending
           if (pd_active) advance(k2ColsPerThread);
           epi_bar_sync();  // nobody reads the colscale buffer about to be rewritten
           {
@@ -761,14 +813,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
               if (j < p.n) {
                 int tau = p.sigB[j];
                 if (tau == kExpEmpty) tau = 0;
-                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - g * kDigitBits);
+                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - h * kDigitBits);
               }
               colscale[cs_next * k2BN + idx] = cs;
             }
           }
           epi_bar_sync();
-#pragma unroll
-          for (int c = 0; c < k2ColsPerThread; ++c) scrP[c * 32] = (int32_t)acc[c];
           pd_active = true;
           pd_done = 0;
           pd_first = first;
@@ -777,13 +827,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           pd_row_ok = row_ok;
           pd_sig = sig_i;
           pd_buf = cs_next;
+          pd_set = park_set;
+          pd_nlev = h - glo + 1;
           pd_crow = p.C + (n0 + col0) * p.ldc + i;
           pd_cols_left = p.n - n0 - col0;
           cs_next ^= 1;
+          park_set ^= 1;
           first = false;
         }
+      }
     }
-    if (pd_active) advance(k2ColsPerThread);  // the last level of the last tile
+    if (pd_active) advance(k2ColsPerThread);  // the last group of the last tile
   }
 
   tc_fence_before();

@@ -128,7 +128,7 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(emu::PrepJob) * 2 * (size_t)nemu);
   const size_t o_stats = off;
   off = up256(off + sizeof(float) * 4 * (size_t)nemu);
-  // parked level sums of the grouped slice kernel: one 128 x kGroupedBN int32 slot per CTA
+  // parked level sums of the grouped slice kernel: kParkSlots 128 x kGroupedBN int32 slots per CTA
   int64_t emu_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];
@@ -138,7 +138,7 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   }
   const int p_ctas = (int)(emu_tiles < emu::kMaxPairCtas ? emu_tiles : emu::kMaxPairCtas);
   const size_t o_scp = off;
-  off = up256(off + sizeof(int32_t) * 128 * emu::kGroupedBN * (size_t)p_ctas);
+  off = up256(off + sizeof(int32_t) * emu::kParkSlots * 128 * emu::kGroupedBN * (size_t)p_ctas);
   int ei = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];

@@ -184,3 +184,28 @@ def test_quick_returns_and_codes(oracle_mod):
         oracle_mod.ozaki_dgemm_rows("N", "N", m, n, k, 1.0, nan, m, nan, k, 0.0, None, m, 10)
     with pytest.raises(ValueError):
         oracle_mod.ozaki_dgemm_rows("N", "N", m, n, k, 1.0, nan, 2, nan, k, 0.0, None, m, 4)
+
+
+def test_one_level_group_rounds_once(oracle_mod):
+    # 14-bit integers with every row/column maximum in [2^13, 2^14) split into exactly two
+    # 7-bit digits, so with three slices no non-zero digit product is dropped and levels
+    # 2..4 form one group.  With one segment the whole product is then summed exactly and
+    # rounded once onto beta*C0 (itself rounded first): the result is
+    # alpha*A*B + fl(beta*C0) correctly rounded.  beta*C0 is of
+    # the size of the result, so rounding after each level (or a wrong scale for the
+    # group) moves some entries by an ulp.
+    m, n, k = 7, 6, 300
+    Ai = synth.small_ints(11, m * k, -(2 ** 14 - 1), 2 ** 14 - 1).reshape(k, m).T.copy()
+    Bi = synth.small_ints(12, k * n, -(2 ** 14 - 1), 2 ** 14 - 1).reshape(n, k).T.copy()
+    Ai[:, 0] = 2.0 ** 13 + 5   # row maxima (exponent 14)
+    Bi[0, :] = -(2.0 ** 13 + 3)  # column maxima
+    C0 = synth.matrix("uniform", m, n, m, 13) * 2.0 ** 37
+    alpha, beta = 0.7, -0.3
+    A = Ai.flatten(order="F")
+    B = Bi.flatten(order="F")
+    out = oracle_mod.ozaki_dgemm_rows("N", "N", m, n, k, alpha, A, m, B, k, beta, C0, m, 3)
+    S = Ai.astype(np.int64) @ Bi.astype(np.int64)
+    for i in range(m):
+        for j in range(n):
+            want = float(Fraction(alpha) * int(S[i, j]) + Fraction(beta * float(C0[j * m + i])))
+            assert out[j * m + i] == want, (i, j)
