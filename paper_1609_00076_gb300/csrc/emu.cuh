@@ -45,9 +45,8 @@ struct Workspace {
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
-  int32_t* scratch_p;  // [scratch_p_ctas][kParkSlots][128 * 256] parked integer level sums of the slice kernels
+  int32_t* scratch_p;  // [scratch_ctas][kParkSlots][128 * 256] parked integer level sums of the two-SM kernel
   int scratch_ctas;
-  int scratch_p_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
 };
 
@@ -124,9 +123,7 @@ constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
 // tensor maps of one problem's slices for the grouped kernel
 int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
 // one launch over all problems of a device table (entries sorted by decreasing tile cost)
-// scratch_p: max_ctas x kParkSlots slots of 128 x kGroupedBN int32 (parked level sums); the grid is capped at max_ctas
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int32_t* scratch_p,
-                              int max_ctas, cudaStream_t s);
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream);
 
 }  // namespace emu
 }  // namespace gbd

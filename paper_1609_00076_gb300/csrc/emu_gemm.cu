@@ -31,7 +31,7 @@ namespace emu {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 512;
@@ -46,8 +46,9 @@ struct SmemLayout {
   static constexpr int kNumBars = 2 * kStages + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
   static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
-  static constexpr int kBytes = kOffScale + 2 * BN * 8;  // two colscale buffers
+  static constexpr int kBytes = kOffScale + BN * 8;  // colscale of the group being finished
   static constexpr int kAlloc = kBytes + 1024;  // slack to align the base to 1024 bytes
+  static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
 
 struct Args {
@@ -65,7 +66,7 @@ struct Args {
   const int* badA;
   const int* badB;
   double* scratch;     // two-SM kernel: one 128 x 256 FP64 slot per CTA (running sums)
-  int32_t* scratch_p;  // two-SM kernel: one 128 x 256 int32 slot per CTA (pending level sums)
+  int32_t* scratch_p;  // two-SM kernel: kParkSlots 128 x 256 int32 slots per CTA (parked level sums)
   unsigned int* err;
 };
 
@@ -125,6 +126,25 @@ __device__ __forceinline__ void tmem_ld_16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 lanes x 8 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld_8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// register j of lane l -> TMEM(lane base + l, col + j), 16 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_st_16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void epi_bar_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
 }
@@ -180,47 +200,32 @@ __device__ __forceinline__ int chunks_of(int g, int segn) {
   return ((g - 1) * segn + kChunkBlocks - 1) / kChunkBlocks;
 }
 
-// One output tile's view of its problem: the single-problem launch takes it from the
-// kernel arguments, the grouped launch from a table in global memory.
+// One output tile's view of its problem.  The single-problem launch reads the
+// problem's fields from the kernel arguments, the grouped launch from the tile's
+// table entry in global memory (JF below); only the entry's address is kept, so the
+// fields are not held in registers across the tile.
 struct Job {
-  const CUtensorMap* tmA;
-  const CUtensorMap* tmB;
+  const EmuTableEntry* e;  // grouped launch: this tile's problem
   int m0, n0;
   int s, nkb;
-  int64_t m, n, ldc;
-  double alpha, beta;
-  double* C;
-  const int* sigA;
-  const int* sigB;
-  const int* badA;
-  const int* badB;
 };
+#define JF(field) (TABLE ? j.e->field : p.field)
 
 template <int BN, bool TABLE>
-__device__ __forceinline__ void get_job(const Args& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
-                                        const EmuTableEntry* table, int count, int tile, Job& j) {
+__device__ __forceinline__ void get_job(const Args& p, const EmuTableEntry* table, int count, int tile, int& cur,
+                                        Job& j) {
   int tm, tn;
   if (!TABLE) {
     tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-    j.tmA = tmA; j.tmB = tmB;
+    j.e = nullptr;
     j.s = p.slices; j.nkb = p.nkb;
-    j.m = p.m; j.n = p.n; j.ldc = p.ldc;
-    j.alpha = p.alpha; j.beta = p.beta; j.C = p.C;
-    j.sigA = p.sigA; j.sigB = p.sigB; j.badA = p.badA; j.badB = p.badB;
   } else {
-    int lo = 0, hi = count - 1;  // last entry whose first tile is <= tile
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (table[mid].tile_begin <= tile) lo = mid;
-      else hi = mid - 1;
-    }
-    const EmuTableEntry& e = table[lo];
+    // last entry whose first tile is <= tile; a CTA's tiles increase, so cur only moves forward
+    while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
+    const EmuTableEntry& e = table[cur];
     tile_coords((int)(tile - e.tile_begin), e.tiles_m, e.group_m, e.num_tiles, tm, tn);
-    j.tmA = &e.tmA; j.tmB = &e.tmB;
+    j.e = &e;
     j.s = e.slices; j.nkb = e.nkb;
-    j.m = e.m; j.n = e.n; j.ldc = e.ldc;
-    j.alpha = e.alpha; j.beta = e.beta; j.C = e.C;
-    j.sigA = e.sigA; j.sigB = e.sigB; j.badA = e.badA; j.badB = e.badB;
   }
   j.m0 = tm * kBM;
   j.n0 = tn * BN;
@@ -231,6 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const EmuTableEntry* __restrict__ table, int count, int total_tiles) {
   using L = SmemLayout<BN>;
+  // TMEM: two FP32 accumulators of BN columns, then the low and high words of the group sum Y
+  static_assert(4 * BN <= kTmemCols, "accumulators and group sums must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
@@ -277,12 +284,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
+      int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Job j;
-        get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+        get_job<BN, TABLE>(p, table, count, tile, cur, j);
+        const CUtensorMap* mapA = TABLE ? &j.e->tmA : &tmA;
+        const CUtensorMap* mapB = TABLE ? &j.e->tmB : &tmB;
         if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tmA) : "memory");
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tmB) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapA) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapB) : "memory");
         }
         const int m0 = j.m0, n0 = j.n0;
         for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
@@ -293,8 +303,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = seg0; kb < seg0 + segn; ++kb) {
                   mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
                   mbar_arrive_expect_tx(&full[stage], bytes);
-                  tma_load_3d(smem + L::kOffA + stage * L::kABytes, j.tmA, &full[stage], kb * kBK, m0, t - 1);
-                  tma_load_3d(smem + L::kOffB + stage * L::kBBytes, j.tmB, &full[stage], kb * kBK, n0, g - t - 1);
+                  tma_load_3d(smem + L::kOffA + stage * L::kABytes, mapA, &full[stage], kb * kBK, m0, t - 1);
+                  tma_load_3d(smem + L::kOffB + stage * L::kBBytes, mapB, &full[stage], kb * kBK, n0, g - t - 1);
                   if (++stage == kStages) { stage = 0; phase ^= 1u; }
                 }
         }
@@ -307,9 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
+      int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Job j;
-        get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+        get_job<BN, TABLE>(p, table, count, tile, cur, j);
         for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks)
           for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
           for (int g = h; g >= group_high(h); --g) {
@@ -342,87 +353,50 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------ epilogue ----------------------------------
-    // Each finished level's integer sums are parked in one of this CTA's scratch
-    // slots.  A finished group is folded into C a few columns per drained chunk of
-    // the next group (the last group of a tile during the next tile), so the MMA does
-    // not wait; two sets of slots hold the group being drained and the pending one.
+    // The exact group sum Y lives in TMEM next to the accumulators, as two 32-bit words
+    // per element: each finished level is folded into it, and the group's last level
+    // turns it into the FP64 update of C.  The MMA runs one chunk ahead meanwhile.
     constexpr int kCols = BN / 2;  // columns per thread
-    constexpr int kStep = 4;       // columns per step of the pending update
-    constexpr int64_t kSlot = (int64_t)128 * BN;  // one parked level of the tile
     const int ew = warp - 2;
     const int quad = warp & 3;     // TMEM lanes 32*quad .. +31 are reachable from this warp
     const int half = ew >> 2;      // which half of the tile's columns
     const int row = quad * 32 + lane;
     const int col0 = half * kCols;
-    int32_t* scrP = p.scratch_p + (int64_t)blockIdx.x * (kParkSlots * kSlot) +
-                    (int64_t)((half * 4 + quad) * kCols) * 32 + lane;
+    const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
+    const uint32_t y_lo = trow + 2 * BN + col0, y_hi = trow + 3 * BN + col0;
     uint32_t chunk = 0;
     uint32_t acc[kCols];
-    bool pd_active = false, pd_first = false, pd_bad = false, pd_row_ok = false;
-    int pd_done = 0, pd_sig = 0, pd_buf = 0, pd_set = 0, pd_nlev = 0, cs_next = 0, park_set = 0;
-    double pd_beta = 0.0;
-    double* pd_crow = nullptr;
-    int64_t pd_ldc = 0, pd_cols_left = 0;
-    // kStep columns per step: all their loads are issued before any is used
-    auto advance = [&](int ncols) {
-      const int c1 = min(pd_done + ncols, kCols);
-      const double* cs = colscale + pd_buf * BN + col0;
-      const int32_t* pk = scrP + (int64_t)pd_set * kGroupLevels * kSlot;
-      for (int c = pd_done; c < c1; c += kStep) {
-        double w[kStep];
-        int32_t P[kStep][kGroupLevels];
-#pragma unroll
-        for (int u = 0; u < kStep; ++u) {
-          const bool ok = c + u < c1 && pd_row_ok && c + u < pd_cols_left;
-          const double* cp = pd_crow + (int64_t)(c + u) * pd_ldc;
-          w[u] = (ok && !(pd_first && pd_beta == 0.0)) ? *cp : 0.0;
-#pragma unroll
-          for (int l = 0; l < kGroupLevels; ++l)
-            P[u][l] = (c + u < c1 && l < pd_nlev) ? pk[l * kSlot + (c + u) * 32] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kStep; ++u) {
-          if (c + u < c1 && pd_row_ok && c + u < pd_cols_left) {
-            const double wp = pd_first ? (pd_beta == 0.0 ? 0.0 : pd_beta * w[u]) : w[u];
-            const double x =
-                pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(combine_levels(P[u]), pd_sig);
-            pd_crow[(int64_t)(c + u) * pd_ldc] = fma(cs[c + u], x, wp);
-          }
-        }
-      }
-      pd_done = c1;
-      if (pd_done >= kCols) pd_active = false;
-    };
+    int cur = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       Job j;
-      get_job<BN, TABLE>(p, &tmA, &tmB, table, count, tile, j);
+      get_job<BN, TABLE>(p, table, count, tile, cur, j);
       const int64_t m0 = j.m0, n0 = j.n0;
       const int64_t i = m0 + row;
-      const bool row_ok = i < j.m;
+      const bool row_ok = i < JF(m);
       int sig_i = 0;
       bool bad_i = false;
       if (row_ok) {
-        sig_i = j.sigA[i];
+        sig_i = JF(sigA)[i];
         if (sig_i == kExpEmpty) sig_i = 0;
-        bad_i = j.badA[i] != 0;
+        bad_i = JF(badA)[i] != 0;
       }
+      double* crow = JF(C) + (n0 + col0) * JF(ldc) + i;
+      const int64_t cols_left = JF(n) - n0 - col0;  // columns of this thread's half inside C
       bool first = true;
       for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
         const int segn = min(kSegBlocks, j.nkb - seg0);
         for (int h = j.s + 1; h >= 2; h -= kGroupLevels) {
           const int glo = group_high(h);
-          int gch = 0;  // chunks of this group: the pending update is spread over them
-          for (int g = h; g >= glo; --g) gch += chunks_of(g, segn);
-          const int portion = ((kCols + gch - 1) / gch + kStep - 1) / kStep * kStep;
           for (int g = h; g >= glo; --g) {
             const int nch = chunks_of(g, segn);
+            const int l = h - g;  // Y holds sum_l P_l 2^(b l)
 #pragma unroll
             for (int c = 0; c < kCols; ++c) acc[c] = 0u;
             for (int ci = 0; ci < nch; ++ci, ++chunk) {
               const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
               mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
               tc_fence_after();
-              const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + col0;
+              const uint32_t taddr = trow + buf * BN + col0;
 #pragma unroll
               for (int q = 0; q < kCols / 16; ++q) {
                 uint32_t v[16];
@@ -432,49 +406,76 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               tc_fence_before();
               mbar_arrive(&acc_empty[buf]);
-              if (pd_active) advance(portion);
             }
-            int32_t* dst = scrP + (int64_t)(park_set * kGroupLevels + (h - g)) * kSlot;
+            if (g != glo) {
+              // fold this level into Y
 #pragma unroll
-            for (int c = 0; c < kCols; ++c) dst[c * 32] = (int32_t)acc[c];
-          }
-          // group end: finish the previous pending update, then make this group pending
-          if (pd_active) advance(kCols);
-          epi_bar_sync();  // nobody reads the colscale buffer about to be rewritten
-          {
-            const int idx = ew * 32 + lane;
-            if (idx < BN) {
-              const int64_t jc = n0 + idx;
-              double cs = 0.0;
-              if (jc < j.n) {
-                int tau = j.sigB[jc];
-                if (tau == kExpEmpty) tau = 0;
-                cs = j.badB[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - h * kDigitBits);
+              for (int q = 0; q < kCols / 16; ++q) {
+                uint32_t lo[16], hi[16];
+                if (l > 0) {
+                  tmem_ld_16(y_lo + q * 16, lo);
+                  tmem_ld_16(y_hi + q * 16, hi);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                  const int64_t add = (int64_t)(int32_t)acc[q * 16 + jj] * ((int64_t)1 << (kDigitBits * l));
+                  const int64_t y = (l > 0 ? (int64_t)(((uint64_t)hi[jj] << 32) | lo[jj]) : 0) + add;
+                  lo[jj] = (uint32_t)y;
+                  hi[jj] = (uint32_t)((uint64_t)y >> 32);
+                }
+                tmem_st_16(y_lo + q * 16, lo);
+                tmem_st_16(y_hi + q * 16, hi);
               }
-              colscale[cs_next * BN + idx] = cs;
+              tmem_wait_st();
+              continue;
             }
+            // group end: C := fma(alpha 2^(tau_j - h b), Y 2^sigma_i, C)
+            epi_bar_sync();  // the previous group's readers of colscale are done
+            {
+              const int idx = ew * 32 + lane;
+              if (idx < BN) {
+                const int64_t jc = n0 + idx;
+                double cs = 0.0;
+                if (jc < JF(n)) {
+                  int tau = JF(sigB)[jc];
+                  if (tau == kExpEmpty) tau = 0;
+                  cs = JF(badB)[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(JF(alpha), tau - h * kDigitBits);
+                }
+                colscale[idx] = cs;
+              }
+            }
+            epi_bar_sync();
+            const double beta = JF(beta);
+            const int64_t ldc = JF(ldc);
+            const bool read_c = !(first && beta == 0.0);
+#pragma unroll
+            for (int q = 0; q < kCols / 8; ++q) {
+              double w[8];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {  // all 8 loads in flight before any use
+                const int c = q * 8 + jj;
+                w[jj] = (read_c && row_ok && c < cols_left) ? crow[(int64_t)c * ldc] : 0.0;
+              }
+              uint32_t lo[8], hi[8];
+              if (l > 0) {
+                tmem_ld_8(y_lo + q * 8, lo);
+                tmem_ld_8(y_hi + q * 8, hi);
+              }
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const int c = q * 8 + jj;
+                const int64_t add = (int64_t)(int32_t)acc[c] * ((int64_t)1 << (kDigitBits * l));
+                const int64_t y = (l > 0 ? (int64_t)(((uint64_t)hi[jj] << 32) | lo[jj]) : 0) + add;
+                const double wp = first ? (beta == 0.0 ? 0.0 : beta * w[jj]) : w[jj];
+                const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(y, sig_i);
+                if (row_ok && c < cols_left) crow[(int64_t)c * ldc] = fma(colscale[col0 + c], x, wp);
+              }
+            }
+            first = false;
           }
-          epi_bar_sync();
-          pd_active = true;
-          pd_done = 0;
-          pd_first = first;
-          pd_beta = j.beta;
-          pd_bad = bad_i;
-          pd_row_ok = row_ok;
-          pd_sig = sig_i;
-          pd_buf = cs_next;
-          pd_set = park_set;
-          pd_nlev = h - glo + 1;
-          pd_crow = j.C + (n0 + col0) * j.ldc + i;
-          pd_ldc = j.ldc;
-          pd_cols_left = j.n - n0 - col0;
-          cs_next ^= 1;
-          park_set ^= 1;
-          first = false;
         }
       }
     }
-    if (pd_active) advance(kCols);  // the last group of the last tile
   }
 
   tc_fence_before();
@@ -917,15 +918,13 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + BN - 1) / BN);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
-  int grid = (int)(tiles < sms ? tiles : sms);
-  if (grid > ws.scratch_p_ctas) grid = ws.scratch_p_ctas;
-  if (grid < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the slice kernel");
+  const int grid = (int)(tiles < sms ? tiles : sms);
   a.group_m = group_rows(grid, kBM, BN, a.tiles_m);
   a.alpha = gp.alpha; a.beta = gp.beta;
   a.C = gp.C; a.ldc = gp.ldc;
   a.sigA = gp.sigA; a.sigB = gp.sigB; a.badA = gp.badA; a.badB = gp.badB;
   a.scratch = nullptr;
-  a.scratch_p = ws.scratch_p;
+  a.scratch_p = nullptr;
   a.err = device_error_word();
 
   auto kern = k_slice_gemm<BN, false>;
@@ -950,8 +949,7 @@ int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int 
   return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int32_t* scratch_p,
-                              int max_ctas, cudaStream_t stream) {
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream) {
   using L = SmemLayout<kGroupedBN>;
   if (count <= 0 || total_tiles <= 0) return GBD_OK;
   int sms = 0;
@@ -962,13 +960,10 @@ int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int tot
   Args a;
   memset(&a, 0, sizeof(a));
   a.err = device_error_word();
-  a.scratch_p = scratch_p;
   auto kern = k_slice_gemm<kGroupedBN, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped slice gemm)");
-  int grid = total_tiles < sms ? total_tiles : sms;
-  if (grid > max_ctas) grid = max_ctas;
-  if (grid < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the grouped slice kernel");
+  const int grid = total_tiles < sms ? total_tiles : sms;
   kern<<<grid, kThreads, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm launch");
@@ -986,8 +981,6 @@ int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t st
   // enough 256 x 128 pair tiles to occupy every SM pair: the two-SM kernel
   const int64_t pair_tiles = ((gp.m + k2BM - 1) / k2BM) * ((gp.n + k2BN - 1) / k2BN);
   if (!single && pair_tiles >= sms / 2) return launch_pair(gp, ws, sms, stream);
-  const int64_t tiles256 = ((gp.m + kBM - 1) / kBM) * ((gp.n + 255) / 256);
-  if (tiles256 >= sms) return launch_bn<256>(gp, ws, sms, stream);
   return launch_bn<128>(gp, ws, sms, stream);
 }
 

@@ -389,16 +389,14 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
-  // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile);
-  // both slice kernels: kParkSlots 128 x 256 int32 slots per CTA for the parked level sums
+  // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile)
+  // and kParkSlots 128 x 256 int32 slots per CTA for the parked level sums; the one-SM kernel
+  // keeps its sums in TMEM
   const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
-  const int64_t single_tiles = ((m + 127) / 128) * ((n + 127) / 128);
   const int scratch_ctas =
       pair_scratch ? (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas) : 0;
-  const int single_ctas = pair_scratch ? (int)(single_tiles < kMaxPairCtas ? single_tiles : kMaxPairCtas) : 0;
-  const int p_ctas = scratch_ctas > single_ctas ? scratch_ctas : single_ctas;
   const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
-  const size_t o_scp = off; off = up(off + sizeof(int32_t) * kParkSlots * 128 * 256 * (size_t)p_ctas);
+  const size_t o_scp = off; off = up(off + sizeof(int32_t) * kParkSlots * 128 * 256 * (size_t)scratch_ctas);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -412,7 +410,6 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);
     ws->scratch_p = reinterpret_cast<int32_t*>(b + o_scp);
-    ws->scratch_p_ctas = p_ctas;
     ws->scratch_ctas = scratch_ctas;
     ws->kp = kp;
   }

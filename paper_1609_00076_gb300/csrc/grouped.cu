@@ -103,8 +103,6 @@ struct gbd_plan {
   gbd::emu::PrepJob* jobs_dev = nullptr;
   float* stats_dev = nullptr;
   int64_t exp_blocks = 0, split_blocks = 0;
-  int32_t* scratch_p = nullptr;  // parked level sums of the grouped slice kernel
-  int scratch_p_ctas = 0;
 };
 
 namespace gbd {
@@ -128,17 +126,6 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(emu::PrepJob) * 2 * (size_t)nemu);
   const size_t o_stats = off;
   off = up256(off + sizeof(float) * 4 * (size_t)nemu);
-  // parked level sums of the grouped slice kernel: kParkSlots 128 x kGroupedBN int32 slots per CTA
-  int64_t emu_tiles = 0;
-  for (int i = 0; i < count; ++i) {
-    const gbd_problem& p = probs[i];
-    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
-    if (p.mode == GBD_MODE_EMULATED && !quick)
-      emu_tiles += ((p.m + 127) / 128) * ((p.n + emu::kGroupedBN - 1) / emu::kGroupedBN);
-  }
-  const int p_ctas = (int)(emu_tiles < emu::kMaxPairCtas ? emu_tiles : emu::kMaxPairCtas);
-  const size_t o_scp = off;
-  off = up256(off + sizeof(int32_t) * emu::kParkSlots * 128 * emu::kGroupedBN * (size_t)p_ctas);
   int ei = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];
@@ -157,8 +144,6 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     plan->emu_dev = reinterpret_cast<emu::EmuTableEntry*>(static_cast<char*>(base) + o_emu);
     plan->jobs_dev = reinterpret_cast<emu::PrepJob*>(static_cast<char*>(base) + o_jobs);
     plan->stats_dev = reinterpret_cast<float*>(static_cast<char*>(base) + o_stats);
-    plan->scratch_p = reinterpret_cast<int32_t*>(static_cast<char*>(base) + o_scp);
-    plan->scratch_p_ctas = p_ctas;
   }
   return off;
 }
@@ -369,8 +354,7 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
                                      true, true, s)))
     return rc;
   if (plan->emu_tiles > 0 &&
-      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles,
-                                           plan->scratch_p, plan->scratch_p_ctas, s)))
+      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles, s)))
     return rc;
   // native: one persistent launch over all tiles
   if (plan->native_tiles > 0) {
