@@ -122,8 +122,10 @@ constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
 
 // tensor maps of one problem's slices for the grouped kernel
 int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
-// one launch over all problems of a device table (entries sorted by decreasing tile cost)
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream);
+// one launch over `count` problems of a device table that all use `slices` slices (entries
+// sorted by decreasing tile cost, tile_begin counted from the first of them)
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
+                              cudaStream_t stream);
 
 }  // namespace emu
 }  // namespace gbd

@@ -32,8 +32,10 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kStages = 6;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 8;                     // two-SM kernel: 2 x 4 warps over 128 lanes x 256 columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiWarps1 = 16;                   // one-SM kernel: 4 x 4 warps over 128 lanes x 128 columns
+constexpr int kThreads1 = 64 + 32 * kEpiWarps1;
 constexpr int kTmemCols = 512;
 
 template <int BN>
@@ -134,20 +136,23 @@ __device__ __forceinline__ void tmem_ld_8(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// register j of lane l -> TMEM(lane base + l, col + j), 16 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_st_16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
+// register j of lane l -> TMEM(lane base + l, col + j), 8 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_st_8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// named barrier 1 over the epilogue warps only
+template <int WARPS = kEpiWarps>
 __device__ __forceinline__ void epi_bar_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * WARPS) : "memory");
 }
+
+// x * 2^e for the rare results outside the normal range, out of line so that its code
+// takes no registers in the unrolled epilogue loops
+__device__ __noinline__ double ldexp_rare(double x, int e) { return ldexp(x, e); }
 
 // Y * 2^sigma as a double, exactly (Y is an integer with |Y| < 2^53)
 __device__ __forceinline__ double scaled_i64(int64_t Y, int sigma) {
@@ -155,7 +160,7 @@ __device__ __forceinline__ double scaled_i64(int64_t Y, int sigma) {
   const uint64_t a = Y < 0 ? 0ull - (uint64_t)Y : (uint64_t)Y;
   const int msb = 63 - __clzll((long long)a);
   const int ef = 1023 + msb + sigma;
-  if (ef <= 0 || ef >= 2047) return ldexp((double)Y, sigma);  // outside the normal range
+  if (ef <= 0 || ef >= 2047) return ldexp_rare((double)Y, sigma);  // outside the normal range
   const uint64_t mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
   const uint64_t bits = ((uint64_t)(Y < 0) << 63) | ((uint64_t)ef << 52) | mant;
   return __longlong_as_double((long long)bits);
@@ -225,14 +230,15 @@ __device__ __forceinline__ void get_job(const Args& p, const EmuTableEntry* tabl
     const EmuTableEntry& e = table[cur];
     tile_coords((int)(tile - e.tile_begin), e.tiles_m, e.group_m, e.num_tiles, tm, tn);
     j.e = &e;
-    j.s = e.slices; j.nkb = e.nkb;
+    j.s = p.slices;  // one launch per slice count: a launch constant keeps the loop control uniform
+    j.nkb = e.nkb;
   }
   j.m0 = tm * kBM;
   j.n0 = tn * BN;
 }
 
 template <int BN, bool TABLE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads1, 1)
     k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const EmuTableEntry* __restrict__ table, int count, int total_tiles) {
   using L = SmemLayout<BN>;
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 32 * kEpiWarps);
+      mbar_init(&acc_empty[i], 32 * kEpiWarps1);
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -356,12 +362,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // The exact group sum Y lives in TMEM next to the accumulators, as two 32-bit words
     // per element: each finished level is folded into it, and the group's last level
     // turns it into the FP64 update of C.  The MMA runs one chunk ahead meanwhile.
-    constexpr int kCols = BN / 2;  // columns per thread
+    constexpr int kParts = kEpiWarps1 / 4;  // warps that share one quarter of the TMEM lanes
+    constexpr int kCols = BN / kParts;      // columns per thread
     const int ew = warp - 2;
     const int quad = warp & 3;     // TMEM lanes 32*quad .. +31 are reachable from this warp
-    const int half = ew >> 2;      // which half of the tile's columns
+    const int part = ew >> 2;      // which part of the tile's columns
     const int row = quad * 32 + lane;
-    const int col0 = half * kCols;
+    const int col0 = part * kCols;
     const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
     const uint32_t y_lo = trow + 2 * BN + col0, y_hi = trow + 3 * BN + col0;
     uint32_t chunk = 0;
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bad_i = JF(badA)[i] != 0;
       }
       double* crow = JF(C) + (n0 + col0) * JF(ldc) + i;
-      const int64_t cols_left = JF(n) - n0 - col0;  // columns of this thread's half inside C
+      const int64_t cols_left = JF(n) - n0 - col0;  // columns of this thread's part inside C
       bool first = true;
       for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
         const int segn = min(kSegBlocks, j.nkb - seg0);
@@ -408,29 +415,27 @@ __global__ void __launch_bounds__(kThreads, 1)
               mbar_arrive(&acc_empty[buf]);
             }
             if (g != glo) {
-              // fold this level into Y
+              // fold this level into Y (the loads are unconditional: no branch around warp-wide TMEM access)
 #pragma unroll
-              for (int q = 0; q < kCols / 16; ++q) {
-                uint32_t lo[16], hi[16];
-                if (l > 0) {
-                  tmem_ld_16(y_lo + q * 16, lo);
-                  tmem_ld_16(y_hi + q * 16, hi);
-                }
+              for (int q = 0; q < kCols / 8; ++q) {
+                uint32_t lo[8], hi[8];
+                tmem_ld_8(y_lo + q * 8, lo);
+                tmem_ld_8(y_hi + q * 8, hi);
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                  const int64_t add = (int64_t)(int32_t)acc[q * 16 + jj] * ((int64_t)1 << (kDigitBits * l));
+                for (int jj = 0; jj < 8; ++jj) {
+                  const int64_t add = (int64_t)(int32_t)acc[q * 8 + jj] * ((int64_t)1 << (kDigitBits * l));
                   const int64_t y = (l > 0 ? (int64_t)(((uint64_t)hi[jj] << 32) | lo[jj]) : 0) + add;
                   lo[jj] = (uint32_t)y;
                   hi[jj] = (uint32_t)((uint64_t)y >> 32);
                 }
-                tmem_st_16(y_lo + q * 16, lo);
-                tmem_st_16(y_hi + q * 16, hi);
+                tmem_st_8(y_lo + q * 8, lo);
+                tmem_st_8(y_hi + q * 8, hi);
               }
               tmem_wait_st();
               continue;
             }
             // group end: C := fma(alpha 2^(tau_j - h b), Y 2^sigma_i, C)
-            epi_bar_sync();  // the previous group's readers of colscale are done
+            epi_bar_sync<kEpiWarps1>();  // the previous group's readers of colscale are done
             {
               const int idx = ew * 32 + lane;
               if (idx < BN) {
@@ -444,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 colscale[idx] = cs;
               }
             }
-            epi_bar_sync();
+            epi_bar_sync<kEpiWarps1>();
             const double beta = JF(beta);
             const int64_t ldc = JF(ldc);
             const bool read_c = !(first && beta == 0.0);
@@ -457,10 +462,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 w[jj] = (read_c && row_ok && c < cols_left) ? crow[(int64_t)c * ldc] : 0.0;
               }
               uint32_t lo[8], hi[8];
-              if (l > 0) {
-                tmem_ld_8(y_lo + q * 8, lo);
-                tmem_ld_8(y_hi + q * 8, hi);
-              }
+              tmem_ld_8(y_lo + q * 8, lo);
+              tmem_ld_8(y_hi + q * 8, hi);
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) {
                 const int c = q * 8 + jj;
@@ -930,7 +933,7 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   auto kern = k_slice_gemm<BN, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm)");
-  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, 0);
+  kern<<<grid, kThreads1, L::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm launch");
 }
@@ -949,7 +952,8 @@ int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int 
   return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, cudaStream_t stream) {
+int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
+                              cudaStream_t stream) {
   using L = SmemLayout<kGroupedBN>;
   if (count <= 0 || total_tiles <= 0) return GBD_OK;
   int sms = 0;
@@ -960,11 +964,12 @@ int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int tot
   Args a;
   memset(&a, 0, sizeof(a));
   a.err = device_error_word();
+  a.slices = slices;
   auto kern = k_slice_gemm<kGroupedBN, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped slice gemm)");
   const int grid = total_tiles < sms ? total_tiles : sms;
-  kern<<<grid, kThreads, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
+  kern<<<grid, kThreads1, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm launch");
 }

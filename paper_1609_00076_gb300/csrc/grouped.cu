@@ -98,6 +98,12 @@ struct gbd_plan {
   std::vector<gbd::emu::EmuTableEntry> emu_table;
   gbd::emu::EmuTableEntry* emu_dev = nullptr;
   int64_t emu_tiles = 0;
+  // one slice-product launch per slice count: table entries [first, first + count), `tiles` tiles
+  struct Segment {
+    int first, count, slices;
+    int64_t tiles;
+  };
+  std::vector<Segment> segments;
   // batched preparation: jobs 2q, 2q+1 are op(A) and op(B)^T of emulated problem q
   std::vector<gbd::emu::PrepJob> jobs;
   gbd::emu::PrepJob* jobs_dev = nullptr;
@@ -280,18 +286,27 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     plan->jobs[2 * q].mu = nullptr;  // runs need no magnitude sums
     plan->jobs[2 * q + 1].mu = nullptr;
   }
-  // emulated table: tensor maps and tile counts, longest tiles first
+  // emulated table: tensor maps and tile counts; problems with the same slice count are
+  // contiguous (one launch each, most slices first) and longest tiles come first within them
   std::vector<int> order(plan->emu.size());
   for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
   auto cost = [&](int q) {
     const auto& em = plan->emu[q];
     return (int64_t)em.slices * (em.slices + 1) / 2 * ((em.p.k + emu::kBK - 1) / emu::kBK);
   };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int sa = plan->emu[a].slices, sb = plan->emu[b].slices;
+    return sa != sb ? sa > sb : cost(a) > cost(b);
+  });
   plan->emu_table.resize(plan->emu.size());
-  int64_t tiles = 0;
+  plan->segments.clear();
+  int64_t tiles = 0, seg_tiles = 0;
   for (size_t r = 0; r < order.size(); ++r) {
     const auto& em = plan->emu[order[r]];
+    if (plan->segments.empty() || plan->segments.back().slices != em.slices) {
+      plan->segments.push_back({(int)r, 0, em.slices, 0});
+      seg_tiles = 0;
+    }
     emu::EmuTableEntry& t = plan->emu_table[r];
     memset(&t, 0, sizeof(t));
     if ((rc = emu::encode_slice_maps(em.ws, em.p.m, em.p.n, em.p.k, em.slices, &t))) return rc;
@@ -303,8 +318,11 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     t.tiles_m = (int)((em.p.m + 127) / 128);
     t.num_tiles = t.tiles_m * (int)((em.p.n + emu::kGroupedBN - 1) / emu::kGroupedBN);
     t.group_m = t.tiles_m;  // within one problem the tiles walk down the rows
-    t.tile_begin = tiles;
+    t.tile_begin = seg_tiles;  // counted from the first tile of its launch
+    seg_tiles += t.num_tiles;
     tiles += t.num_tiles;
+    plan->segments.back().count += 1;
+    plan->segments.back().tiles = seg_tiles;
   }
   plan->emu_tiles = tiles;
   if (slices_used)
@@ -348,14 +366,16 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
   int rc = current_device(nullptr, &sms);
   if (rc) return rc;
   cudaError_t e;
-  // emulated: exponents and digit slices of every problem (three launches), then one slice-product launch
+  // emulated: exponents and digit slices of every problem (three launches), then one slice-product
+  // launch per slice count
   if (!plan->jobs.empty() &&
       (rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->split_blocks,
                                      true, true, s)))
     return rc;
-  if (plan->emu_tiles > 0 &&
-      (rc = emu::launch_slice_gemm_grouped(plan->emu_dev, (int)plan->emu_table.size(), (int)plan->emu_tiles, s)))
-    return rc;
+  for (const auto& sg : plan->segments)
+    if (sg.tiles > 0 &&
+        (rc = emu::launch_slice_gemm_grouped(plan->emu_dev + sg.first, sg.count, (int)sg.tiles, sg.slices, s)))
+      return rc;
   // native: one persistent launch over all tiles
   if (plan->native_tiles > 0) {
     if ((e = cudaMemsetAsync(plan->counter_dev, 0, sizeof(unsigned long long), s)) != cudaSuccess)
