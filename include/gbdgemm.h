@@ -108,10 +108,12 @@ GBD_API size_t gbd_dgemm_emu_workspace_size(int64_t m, int64_t n, int64_t k, int
  *
  * Steps: per-row exponents sigma_i of op(A) and per-column exponents tau_j of
  * op(B); `slices` digits of 7 bits per entry (truncation of a_ip 2^-sigma_i);
- * for each level g = 2..slices+1 the exact integer sum of the digit products
- * with t + u = g, on tcgen05.mma with FP32 accumulation over chunks of 256 that
- * is exact by construction; then C := beta*C and, from the smallest level to
- * the largest, C := fma(alpha 2^(sigma_i + tau_j - 7g), P_g, C) in FP64.
+ * for each level g = 2..slices+1 the exact integer sum P_g of the digit
+ * products with t + u = g, on tcgen05.mma with FP32 accumulation over chunks of
+ * 1024 that is exact by construction; then C := beta*C and, for each segment of
+ * 8192 of the inner dimension, the levels from the smallest in groups of up to
+ * four: Y = sum_g P_g 2^(7(h-g)) exactly in 64-bit integers (h the group's
+ * smallest level) and C := fma(alpha 2^(sigma_i + tau_j - 7h), Y, C) in FP64.
  *
  * slices: 1..9, or 0 to choose the smallest count whose estimated componentwise
  *   error stays below `tol` (relative to |alpha||op(A)||op(B)|; tol <= 0 means
@@ -164,6 +166,36 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
                                   double alpha, const double* A, int64_t lda, const double* B,
                                   int64_t ldb, double beta, double* C, int64_t ldc, int slices,
                                   double tol, gbd_emu_info* info, void* stream);
+
+/*
+ * gbd_dgemm_emu with A, B and C in HOST memory.  The paper's dgemm works on
+ * operands in the caller's memory (Section 1.2); this entry point gives that
+ * interface to a caller whose matrices are on the host, with the GPU transfers
+ * inside the call.  On `stream`, in order: op(A)'s storage (rows x cols with
+ * leading dimension lda, rows = m or k as for gbd_dgemm) and B's are copied into
+ * `device_buffer` (packed, leading dimension = rows), and C too when beta != 0;
+ * gbd_dgemm_emu runs on the copies; the m x n result is copied back into C
+ * (leading dimension ldc).  Elements of A, B, C outside the matrices (the
+ * leading-dimension padding) are neither read nor written.
+ *
+ * Host memory: page-locked (cudaHostAlloc / cudaHostRegister) for asynchronous
+ *   transfers; pageable memory works, but then the copies synchronise the host.
+ *   The host buffers must stay valid, and C unread, until `stream` has reached
+ *   the end of the call.
+ * device_buffer: device memory of at least gbd_dgemm_emu_host_buffer_size(...)
+ *   bytes, 256-byte aligned, owned by the caller, not reused until the call has
+ *   completed on `stream`.  Two buffers used on two streams let consecutive
+ *   calls overlap one call's transfers with the other's computation.
+ * slices, tol, info and the automatic-mode synchronisation: as gbd_dgemm_emu.
+ * Returns 0, a BLAS argument index, or GBD_ERR_* (GBD_ERR_WORKSPACE when the
+ * buffer is missing, small or misaligned).
+ */
+GBD_API size_t gbd_dgemm_emu_host_buffer_size(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                              int slices);
+GBD_API int gbd_dgemm_emu_host(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                               const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                               double* C, int64_t ldc, int slices, double tol, void* device_buffer,
+                               size_t buffer_bytes, gbd_emu_info* info, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Grouped calls: many independent problems per launch                       */

@@ -104,6 +104,9 @@ _EXTRA_DECLS: list = [
                        ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_noalloc", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d,
                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_dgemm_emu_host_buffer_size", [_c, _c, _i64, _i64, _i64, _i], _sz),
+    ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
+                            ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_watchdog_selftest", [_i, _vp], _i),
     ("gbd_dgemm_grouped_workspace_size", [_vp, _i], _sz),
     ("gbd_grouped_plan_create", [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)], _i),
@@ -126,8 +129,10 @@ def _addr(x) -> int | None:
         return None
     if isinstance(x, int):
         return x
-    if hasattr(x, "data_ptr"):
+    if hasattr(x, "data_ptr"):  # torch tensor (device or host)
         return int(x.data_ptr())
+    if hasattr(x, "ctypes"):  # numpy array (host)
+        return int(x.ctypes.data)
     raise TypeError(f"expected a device tensor or address, got {type(x)!r}")
 
 
@@ -192,6 +197,21 @@ def gbd_dgemm_emu_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, 
     return load().gbd_dgemm_emu_noalloc(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
                                         int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
                                         float(tol), ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_dgemm_emu_host_buffer_size(transa, transb, m, n, k, slices=0) -> int:
+    """Device buffer bytes of gbd_dgemm_emu_host (packed A, B, C and the workspace)."""
+    return int(load().gbd_dgemm_emu_host_buffer_size(_t(transa), _t(transb), int(m), int(n), int(k), int(slices)))
+
+
+def gbd_dgemm_emu_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, tol, buffer,
+                       buffer_bytes, info=None, stream=None) -> int:
+    """gbd_dgemm_emu with A, B and C in host memory (numpy arrays or host tensors; page-locked
+    for asynchronous transfers) and a caller-owned device buffer; returns the status."""
+    return load().gbd_dgemm_emu_host(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                                     int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
+                                     float(tol), _addr(buffer), int(buffer_bytes),
+                                     ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
 def problem_array(problems) -> ctypes.Array:

@@ -76,6 +76,24 @@ def test_emu_workspace_size_is_host_only(lib):
     assert gbdgemm.gbd_dgemm_emu_workspace_size(-1, 2, 3, 1) == 0
 
 
+def test_emu_host_buffer_size_and_argument_codes_without_gpu(lib):
+    import numpy as np
+    ws = gbdgemm.gbd_dgemm_emu_workspace_size(100, 200, 300, 3)
+    size = gbdgemm.gbd_dgemm_emu_host_buffer_size("T", "N", 100, 200, 300, 3)
+    # packed A (300 x 100), B (300 x 200) and C (100 x 200), each 256-byte aligned, then the workspace
+    assert size >= ws + 8 * (300 * 100 + 300 * 200 + 100 * 200)
+    assert size <= ws + 8 * (300 * 100 + 300 * 200 + 100 * 200) + 4 * 256
+    assert gbdgemm.gbd_dgemm_emu_host_buffer_size("N", "N", -1, 2, 3, 1) == 0
+    a = np.zeros(4)
+    # argument checks come before any device work
+    assert gbdgemm.gbd_dgemm_emu_host("X", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 1
+    assert gbdgemm.gbd_dgemm_emu_host("N", "N", 2, 2, 2, 1.0, a, 1, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 8
+    assert gbdgemm.gbd_dgemm_emu_host("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 1, 0, 0.0, None, 0, stream=0) == 13
+    assert gbdgemm.gbd_dgemm_emu_host("N", "N", 0, 2, 2, 1.0, a, 1, a, 2, 0.0, a, 1, 0, 0.0, None, 0, stream=0) == 0
+    assert gbdgemm.gbd_dgemm_emu_host("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 12, 0.0, None, 0, stream=0) == \
+        gbdgemm.GBD_ERR_ARG
+
+
 def test_request_stream_is_seeded_and_poisson():
     from paper_1609_00076_gb300 import serving
     a = serving.request_stream(3, 2000, rate=500.0)
