@@ -118,7 +118,13 @@ struct EmuTableEntry {  // CUtensorMap members keep it 64-byte aligned
   int64_t tile_begin;  // first index of this problem in the grouped tile sequence
   int slices, nkb, tiles_m, group_m, num_tiles, pad;
 };
-constexpr int kGroupedBN = 128;  // column tile of the grouped slice kernel
+constexpr int kGroupedBN = 128;  // column tile of the grouped one-SM slice kernel
+// grouped problems with m, n >= kGroupedPairMinMN and k >= kGroupedPairMinK use the two-SM 256 x 256
+// kernel.  Measured per SM, it needs k >= 1024 to amortise its deferred FP64 update and is about
+// 1.5x the one-SM kernel from k = 2048; in a batch its separate launch and the 256 x 256 padding
+// have to be paid for as well, so only large problems qualify
+constexpr int kGroupedPairMinMN = 1024;
+constexpr int kGroupedPairMinK = 2048;
 
 // tensor maps of one problem's slices for the grouped kernel
 int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int slices, EmuTableEntry* e);
@@ -126,6 +132,10 @@ int encode_slice_maps(const Workspace& ws, int64_t m, int64_t n, int64_t k, int 
 // sorted by decreasing tile cost, tile_begin counted from the first of them)
 int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
                               cudaStream_t stream);
+// the same with the two-SM kernel on 256 x 256 tiles (entries tiled by 256 x 256); scratch and
+// scratch_p hold max_ctas running-sum slots and max_ctas x kParkSlots park slots of 128 x 256
+int launch_slice_gemm_grouped_pair(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
+                                   double* scratch, int32_t* scratch_p, int max_ctas, cudaStream_t stream);
 
 }  // namespace emu
 }  // namespace gbd

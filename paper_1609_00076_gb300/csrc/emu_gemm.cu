@@ -216,7 +216,7 @@ struct Job {
 };
 #define JF(field) (TABLE ? j.e->field : p.field)
 
-template <int BN, bool TABLE>
+template <int BM, int BN, bool TABLE>
 __device__ __forceinline__ void get_job(const Args& p, const EmuTableEntry* table, int count, int tile, int& cur,
                                         Job& j) {
   int tm, tn;
@@ -233,7 +233,7 @@ __device__ __forceinline__ void get_job(const Args& p, const EmuTableEntry* tabl
     j.s = p.slices;  // one launch per slice count: a launch constant keeps the loop control uniform
     j.nkb = e.nkb;
   }
-  j.m0 = tm * kBM;
+  j.m0 = tm * BM;
   j.n0 = tn * BN;
 }
 
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kThreads1, 1)
       int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Job j;
-        get_job<BN, TABLE>(p, table, count, tile, cur, j);
+        get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
         const CUtensorMap* mapA = TABLE ? &j.e->tmA : &tmA;
         const CUtensorMap* mapB = TABLE ? &j.e->tmB : &tmB;
         if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreads1, 1)
       int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         Job j;
-        get_job<BN, TABLE>(p, table, count, tile, cur, j);
+        get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
         for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks)
           for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
           for (int g = h; g >= group_high(h); --g) {
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kThreads1, 1)
     int cur = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       Job j;
-      get_job<BN, TABLE>(p, table, count, tile, cur, j);
+      get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
       const int64_t m0 = j.m0, n0 = j.n0;
       const int64_t i = m0 + row;
       const bool row_ok = i < JF(m);
@@ -585,8 +585,10 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
       "h"((uint16_t)3)
       : "memory");
 }
+template <bool TABLE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    k_slice_gemm_pair(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    k_slice_gemm_pair(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const EmuTableEntry* __restrict__ table, int count, int total_tiles) {
   using L = Smem2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -602,12 +604,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
-  const int s = p.slices;
+  const int s = p.slices;  // one launch per slice count, also for a table of problems
   const int num_pairs = gridDim.x / 2, pair_id = blockIdx.x / 2;
+  const int ntiles = TABLE ? total_tiles : p.num_tiles;
 
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+    if (!TABLE) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+    }
     for (int i = 0; i < k2Stages; ++i) {
       mbar_init(&full[i], 1);   // the leader's producer arrives (with both CTAs' bytes)
       mbar_init(&empty[i], 1);  // one commit per phase, multicast to both CTAs
@@ -636,13 +641,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
-      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
-        int tm, tn;
-        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-        const int m0 = tm * k2BM + (int)rank * 128;
-        const int nb0 = tn * k2BN + (int)rank * 128;
-        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-          const int segn = min(kSegBlocks, p.nkb - seg0);
+      int cur = 0;
+      for (int tile = pair_id; tile < ntiles; tile += num_pairs) {
+        Job j;
+        get_job<k2BM, k2BN, TABLE>(p, table, count, tile, cur, j);
+        const CUtensorMap* mapA = TABLE ? &j.e->tmA : &tmA;
+        const CUtensorMap* mapB = TABLE ? &j.e->tmB : &tmB;
+        if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapA) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapB) : "memory");
+        }
+        const int m0 = j.m0 + (int)rank * 128;
+        const int nb0 = j.n0 + (int)rank * 128;
+        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, j.nkb - seg0);
           for (int h = s + 1; h >= 2; h -= kGroupLevels)
             for (int g = h; g >= group_high(h); --g)
               for (int t = 1; t <= g - 1; ++t)
@@ -650,8 +662,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                   mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
                   if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
                   const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
-                  tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, t - 1);
-                  tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, g - t - 1);
+                  tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, mapA, fbar, kb * kBK, m0, t - 1);
+                  tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, mapB, fbar, kb * kBK, nb0, g - t - 1);
                   if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
                 }
         }
@@ -664,11 +676,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16(k2BM, k2BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
-        for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks)
+      int cur = 0;
+      for (int tile = pair_id; tile < ntiles; tile += num_pairs) {
+        Job j;
+        get_job<k2BM, k2BN, TABLE>(p, table, count, tile, cur, j);
+        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks)
           for (int h = s + 1; h >= 2; h -= kGroupLevels)
           for (int g = h; g >= group_high(h); --g) {
-            const int segn = min(kSegBlocks, p.nkb - seg0);
+            const int segn = min(kSegBlocks, j.nkb - seg0);
             const int items = (g - 1) * segn;
             for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
               const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
@@ -722,8 +737,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     // the pending update
     bool pd_active = false, pd_first = false, pd_last = false, pd_bad = false, pd_row_ok = false;
     int pd_done = 0, pd_sig = 0, pd_buf = 0, pd_set = 0, pd_nlev = 0, cs_next = 0, park_set = 0;
+    double pd_beta = 0.0;
     double* pd_crow = nullptr;
-    int64_t pd_cols_left = 0;  // columns of the pending tile inside C (n - n0 - col0, clamped)
+    int64_t pd_ldc = 0, pd_cols_left = 0;  // columns of the pending tile inside C (n - n0 - col0, clamped)
     // kStep columns per step: all their loads are issued before any is used
     auto advance = [&](int ncols) {
       const int c1 = min(pd_done + ncols, k2ColsPerThread);
@@ -736,7 +752,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         for (int u = 0; u < kStep; ++u) {
           const bool in = c + u < c1;
           const bool col_ok = in && pd_row_ok && c + u < pd_cols_left;
-          if (pd_first) w[u] = (p.beta != 0.0 && col_ok) ? pd_crow[(int64_t)(c + u) * p.ldc] : 0.0;
+          if (pd_first) w[u] = (pd_beta != 0.0 && col_ok) ? pd_crow[(int64_t)(c + u) * pd_ldc] : 0.0;
           else w[u] = in ? scrW[(c + u) * 32] : 0.0;
 #pragma unroll
           for (int l = 0; l < kGroupLevels; ++l) P[u][l] = (in && l < pd_nlev) ? pk[l * kSlot + (c + u) * 32] : 0;
@@ -745,12 +761,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         for (int u = 0; u < kStep; ++u) {
           if (c + u >= c1) continue;
           const bool col_ok = pd_row_ok && c + u < pd_cols_left;
-          const double wp = pd_first ? (p.beta != 0.0 && col_ok ? p.beta * w[u] : 0.0) : w[u];
+          const double wp = pd_first ? (pd_beta != 0.0 && col_ok ? pd_beta * w[u] : 0.0) : w[u];
           const double x =
               pd_bad ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(combine_levels(P[u]), pd_sig);
           const double r = fma(cs[c + u], x, wp);
           if (pd_last) {
-            if (col_ok) pd_crow[(int64_t)(c + u) * p.ldc] = r;
+            if (col_ok) pd_crow[(int64_t)(c + u) * pd_ldc] = r;
           } else {
             scrW[(c + u) * 32] = r;
           }
@@ -759,26 +775,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       pd_done = c1;
       if (pd_done >= k2ColsPerThread) pd_active = false;
     };
-    for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
-      int tm, tn;
-      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-      const int64_t m0 = (int64_t)tm * k2BM + rank * 128;
-      const int64_t n0 = (int64_t)tn * k2BN;
+    int cur = 0;
+    for (int tile = pair_id; tile < ntiles; tile += num_pairs) {
+      Job j;
+      get_job<k2BM, k2BN, TABLE>(p, table, count, tile, cur, j);
+      const int64_t m0 = (int64_t)j.m0 + rank * 128;
+      const int64_t n0 = j.n0;
       const int64_t i = m0 + row;
-      const bool row_ok = i < p.m;
+      const bool row_ok = i < JF(m);
       int sig_i = 0;
       bool bad_i = false;
       if (row_ok) {
-        sig_i = p.sigA[i];
+        sig_i = JF(sigA)[i];
         if (sig_i == kExpEmpty) sig_i = 0;
-        bad_i = p.badA[i] != 0;
+        bad_i = JF(badA)[i] != 0;
       }
       bool first = true;
-      for (int seg0 = 0; seg0 < p.nkb; seg0 += kSegBlocks) {
-        const int segn = min(kSegBlocks, p.nkb - seg0);
+      for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
+        const int segn = min(kSegBlocks, j.nkb - seg0);
         for (int h = s + 1; h >= 2; h -= kGroupLevels) {
           const int glo = group_high(h);
-          const bool last = (glo == 2) && (seg0 + kSegBlocks >= p.nkb);
+          const bool last = (glo == 2) && (seg0 + kSegBlocks >= j.nkb);
           int gch = 0;  // chunks of this group: the pending update is spread over them
           for (int g = h; g >= glo; --g) gch += chunks_of(g, segn);
           const int portion = ((k2ColsPerThread + gch - 1) / gch + kStep - 1) / kStep * kStep;
@@ -812,12 +829,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           {
             const int idx = ew * 32 + lane;
             if (idx < k2BN) {
-              const int64_t j = n0 + idx;
+              const int64_t jc = n0 + idx;
               double cs = 0.0;
-              if (j < p.n) {
-                int tau = p.sigB[j];
+              if (jc < JF(n)) {
+                int tau = JF(sigB)[jc];
                 if (tau == kExpEmpty) tau = 0;
-                cs = p.badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(p.alpha, tau - h * kDigitBits);
+                cs = JF(badB)[jc] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(JF(alpha), tau - h * kDigitBits);
               }
               colscale[cs_next * k2BN + idx] = cs;
             }
@@ -833,8 +850,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           pd_buf = cs_next;
           pd_set = park_set;
           pd_nlev = h - glo + 1;
-          pd_crow = p.C + (n0 + col0) * p.ldc + i;
-          pd_cols_left = p.n - n0 - col0;
+          pd_beta = JF(beta);
+          pd_ldc = JF(ldc);
+          pd_crow = JF(C) + (n0 + col0) * pd_ldc + i;
+          pd_cols_left = JF(n) - n0 - col0;
           cs_next ^= 1;
           park_set ^= 1;
           first = false;
@@ -889,9 +908,10 @@ int launch_pair(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t
   a.scratch_p = ws.scratch_p;
   a.err = device_error_word();
 
-  cudaError_t e = cudaFuncSetAttribute(k_slice_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_slice_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(slice gemm pair)");
-  k_slice_gemm_pair<<<(unsigned)(2 * pairs), kThreads, L::kAlloc, stream>>>(a, tmA, tmB);
+  k_slice_gemm_pair<false><<<(unsigned)(2 * pairs), kThreads, L::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "slice gemm pair launch");
 }
@@ -972,6 +992,33 @@ int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int tot
   kern<<<grid, kThreads1, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count, total_tiles);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm launch");
+}
+
+int launch_slice_gemm_grouped_pair(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
+                                   double* scratch, int32_t* scratch_p, int max_ctas, cudaStream_t stream) {
+  using L = Smem2;
+  if (count <= 0 || total_tiles <= 0) return GBD_OK;
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  Args a;
+  memset(&a, 0, sizeof(a));
+  a.err = device_error_word();
+  a.slices = slices;
+  a.scratch = scratch;
+  a.scratch_p = scratch_p;
+  int pairs = total_tiles < sms / 2 ? total_tiles : sms / 2;
+  if (pairs > max_ctas / 2) pairs = max_ctas / 2;
+  if (pairs < 1) return set_error(GBD_ERR_WORKSPACE, "no scratch slot for the grouped two-SM kernel");
+  cudaError_t e =
+      cudaFuncSetAttribute(k_slice_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped slice gemm pair)");
+  k_slice_gemm_pair<true><<<(unsigned)(2 * pairs), kThreads, L::kAlloc, stream>>>(a, dummy, dummy, table_dev, count,
+                                                                                  total_tiles);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm pair launch");
 }
 
 int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t stream) {

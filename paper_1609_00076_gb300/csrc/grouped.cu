@@ -98,12 +98,18 @@ struct gbd_plan {
   std::vector<gbd::emu::EmuTableEntry> emu_table;
   gbd::emu::EmuTableEntry* emu_dev = nullptr;
   int64_t emu_tiles = 0;
-  // one slice-product launch per slice count: table entries [first, first + count), `tiles` tiles
+  // one slice-product launch per kernel and slice count: table entries [first, first + count),
+  // `tiles` tiles of 256 x 256 (pair) or 128 x 128
   struct Segment {
     int first, count, slices;
+    bool pair;
     int64_t tiles;
   };
   std::vector<Segment> segments;
+  // two-SM kernel scratch: FP64 running sums and parked level sums, per CTA
+  double* pair_scratch = nullptr;
+  int32_t* pair_scratch_p = nullptr;
+  int pair_ctas = 0;
   // batched preparation: jobs 2q, 2q+1 are op(A) and op(B)^T of emulated problem q
   std::vector<gbd::emu::PrepJob> jobs;
   gbd::emu::PrepJob* jobs_dev = nullptr;
@@ -113,6 +119,11 @@ struct gbd_plan {
 
 namespace gbd {
 namespace {
+
+// Emulated problems large enough for the two-SM 256 x 256 kernel
+bool pair_class(const gbd_problem& p) {
+  return p.m >= emu::kGroupedPairMinMN && p.n >= emu::kGroupedPairMinMN && p.k >= emu::kGroupedPairMinK;
+}
 
 // Layout of the grouped workspace; with base == nullptr only the size is computed.
 size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_override, void* base, gbd_plan* plan) {
@@ -132,6 +143,18 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(emu::PrepJob) * 2 * (size_t)nemu);
   const size_t o_stats = off;
   off = up256(off + sizeof(float) * 4 * (size_t)nemu);
+  // two-SM kernel scratch for the large emulated problems (at most one CTA pair per 256 x 256 tile)
+  int64_t pair_tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_EMULATED && !quick && pair_class(p)) pair_tiles += ((p.m + 255) / 256) * ((p.n + 255) / 256);
+  }
+  const int pair_ctas = (int)(2 * pair_tiles < emu::kMaxPairCtas ? 2 * pair_tiles : emu::kMaxPairCtas);
+  const size_t o_pscr = off;
+  off = up256(off + sizeof(double) * 128 * 256 * (size_t)pair_ctas);
+  const size_t o_pscp = off;
+  off = up256(off + sizeof(int32_t) * emu::kParkSlots * 128 * 256 * (size_t)pair_ctas);
   int ei = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];
@@ -150,6 +173,9 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     plan->emu_dev = reinterpret_cast<emu::EmuTableEntry*>(static_cast<char*>(base) + o_emu);
     plan->jobs_dev = reinterpret_cast<emu::PrepJob*>(static_cast<char*>(base) + o_jobs);
     plan->stats_dev = reinterpret_cast<float*>(static_cast<char*>(base) + o_stats);
+    plan->pair_scratch = reinterpret_cast<double*>(static_cast<char*>(base) + o_pscr);
+    plan->pair_scratch_p = reinterpret_cast<int32_t*>(static_cast<char*>(base) + o_pscp);
+    plan->pair_ctas = pair_ctas;
   }
   return off;
 }
@@ -286,8 +312,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     plan->jobs[2 * q].mu = nullptr;  // runs need no magnitude sums
     plan->jobs[2 * q + 1].mu = nullptr;
   }
-  // emulated table: tensor maps and tile counts; problems with the same slice count are
-  // contiguous (one launch each, most slices first) and longest tiles come first within them
+  // emulated table: tensor maps and tile counts.  Problems of the same kernel (two-SM for the large
+  // ones) and slice count are contiguous (one launch each, most slices first), and the longest
+  // tiles come first within them.
   std::vector<int> order(plan->emu.size());
   for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
   auto cost = [&](int q) {
@@ -295,7 +322,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     return (int64_t)em.slices * (em.slices + 1) / 2 * ((em.p.k + emu::kBK - 1) / emu::kBK);
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const bool pa = pair_class(plan->emu[a].p), pb = pair_class(plan->emu[b].p);
     const int sa = plan->emu[a].slices, sb = plan->emu[b].slices;
+    if (pa != pb) return pa;
     return sa != sb ? sa > sb : cost(a) > cost(b);
   });
   plan->emu_table.resize(plan->emu.size());
@@ -303,8 +332,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   int64_t tiles = 0, seg_tiles = 0;
   for (size_t r = 0; r < order.size(); ++r) {
     const auto& em = plan->emu[order[r]];
-    if (plan->segments.empty() || plan->segments.back().slices != em.slices) {
-      plan->segments.push_back({(int)r, 0, em.slices, 0});
+    const bool pair = pair_class(em.p);
+    if (plan->segments.empty() || plan->segments.back().slices != em.slices || plan->segments.back().pair != pair) {
+      plan->segments.push_back({(int)r, 0, em.slices, pair, 0});
       seg_tiles = 0;
     }
     emu::EmuTableEntry& t = plan->emu_table[r];
@@ -315,8 +345,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     t.sigA = em.ws.sigA; t.sigB = em.ws.sigB; t.badA = em.ws.badA; t.badB = em.ws.badB;
     t.slices = em.slices;
     t.nkb = (int)((em.p.k + emu::kBK - 1) / emu::kBK);
-    t.tiles_m = (int)((em.p.m + 127) / 128);
-    t.num_tiles = t.tiles_m * (int)((em.p.n + emu::kGroupedBN - 1) / emu::kGroupedBN);
+    const int bm = pair ? 256 : 128, bn = pair ? 256 : emu::kGroupedBN;
+    t.tiles_m = (int)((em.p.m + bm - 1) / bm);
+    t.num_tiles = t.tiles_m * (int)((em.p.n + bn - 1) / bn);
     t.group_m = t.tiles_m;  // within one problem the tiles walk down the rows
     t.tile_begin = seg_tiles;  // counted from the first tile of its launch
     seg_tiles += t.num_tiles;
@@ -372,10 +403,13 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
       (rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->split_blocks,
                                      true, true, s)))
     return rc;
-  for (const auto& sg : plan->segments)
-    if (sg.tiles > 0 &&
-        (rc = emu::launch_slice_gemm_grouped(plan->emu_dev + sg.first, sg.count, (int)sg.tiles, sg.slices, s)))
-      return rc;
+  for (const auto& sg : plan->segments) {
+    if (sg.tiles <= 0) continue;
+    rc = sg.pair ? emu::launch_slice_gemm_grouped_pair(plan->emu_dev + sg.first, sg.count, (int)sg.tiles, sg.slices,
+                                                       plan->pair_scratch, plan->pair_scratch_p, plan->pair_ctas, s)
+                 : emu::launch_slice_gemm_grouped(plan->emu_dev + sg.first, sg.count, (int)sg.tiles, sg.slices, s);
+    if (rc) return rc;
+  }
   // native: one persistent launch over all tiles
   if (plan->native_tiles > 0) {
     if ((e = cudaMemsetAsync(plan->counter_dev, 0, sizeof(unsigned long long), s)) != cudaSuccess)

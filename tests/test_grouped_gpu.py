@@ -137,6 +137,29 @@ def test_emulated_batch_matches_single_calls_and_model(oracle_mod):
         assert first_mismatch(got, ref, None, m) is None
 
 
+def test_emulated_two_kernel_classes(oracle_mod):
+    # m, n >= 1024 with k >= 2048 go to the two-SM 256 x 256 kernel, the others to the one-SM kernel;
+    # ragged sizes, transposes and several slice counts (one launch per kernel and slice count)
+    probs = make_batch(23, 8, 120, 700, modes=("emu",), slices=(3, 5, 9), alpha_beta=(-0.75, 1.25))
+    for i, (m, n, k, ta, tb, s) in enumerate([(1030, 1100, 2100, "N", "T", 3), (1100, 1030, 2049, "T", "N", 4)]):
+        ra, ca = (k, m) if ta == "T" else (m, k)
+        rb, cb = (n, k) if tb == "T" else (k, n)
+        probs.append(dict(ta=ta, tb=tb, m=m, n=n, k=k, lda=ra + 1, ldb=rb, ldc=m + 1, mode="emu", slices=s,
+                          alpha=-0.75, beta=1.25, A=synth.matrix("uniform", ra, ca, ra + 1, 7000 + i, pad=0.0),
+                          B=synth.matrix("uniform", rb, cb, rb, 7100 + i, pad=0.0),
+                          C=synth.matrix("uniform", m, n, m + 1, 7200 + i, pad=0.0)))
+    to_device(probs)
+    outs, used = run_grouped(probs)
+    for p, out, s in zip(probs, outs, used):
+        assert s == p["slices"]
+        m, n, k = p["m"], p["n"], p["k"]
+        ref = oracle_mod.ozaki_dgemm_rows(p["ta"], p["tb"], m, n, k, p["alpha"], p["A"], p["lda"], p["B"], p["ldb"],
+                                          p["beta"], p["C"], p["ldc"], s)
+        got = synth.view(out, m, n, p["ldc"]).flatten(order="F")
+        assert first_mismatch(got, ref, None, m) is None, (m, n, k, s)
+        assert bits_equal(out, run_single(p, s))
+
+
 def test_emulated_automatic_slices_within_bound(oracle_mod):
     probs = make_batch(22, 10, 48, 500, modes=("emu",), slices=(0,), kinds=("uniform", "scaled"))
     to_device(probs)
