@@ -1030,9 +1030,11 @@ int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t st
   const char* force = getenv("GBD_EMU_KERNEL");
   if (force && force[0] == 'p') return launch_pair(gp, ws, sms, stream);
   const bool single = force && force[0] == 's';
-  // enough 256 x 128 pair tiles to occupy every SM pair: the two-SM kernel
+  // enough 256 x 256 pair tiles to occupy every SM pair and an inner dimension deep enough to
+  // amortise the two-SM kernel's deferred FP64 update (measured per SM: even at k = 512, ahead
+  // from k = 1024): the two-SM kernel
   const int64_t pair_tiles = ((gp.m + k2BM - 1) / k2BM) * ((gp.n + k2BN - 1) / k2BN);
-  if (!single && pair_tiles >= sms / 2) return launch_pair(gp, ws, sms, stream);
+  if (!single && pair_tiles >= sms / 2 && gp.k >= 1024) return launch_pair(gp, ws, sms, stream);
   return launch_bn<128>(gp, ws, sms, stream);
 }
 
