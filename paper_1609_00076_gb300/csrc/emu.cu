@@ -114,8 +114,8 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   int s_use = slices;
   double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
   if (slices == 0) {
-    if ((e = cudaMemsetAsync(ws.muA, 0, sizeof(float) * (size_t)m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.muB, 0, sizeof(float) * (size_t)n, s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ws.muA, 0, sizeof(unsigned long long) * (size_t)m, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.muB, 0, sizeof(unsigned long long) * (size_t)n, s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu: workspace initialisation");
     if ((rc = launch_magnitudes(A, lda, m, k, ta == 0, ws.sigA, ws.muA, s))) return rc;
     if ((rc = launch_magnitudes(B, ldb, n, k, tb != 0, ws.sigB, ws.muB, s))) return rc;

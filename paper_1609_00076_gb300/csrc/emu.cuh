@@ -39,8 +39,8 @@ struct Workspace {
   int* sigB;        // [n] column exponents of op(B)
   int* badA;        // [m] non-zero when the row holds Inf/NaN
   int* badB;        // [n]
-  float* muA;       // [m] sum_p |a_ip| 2^-sigma_i (slice-count selection only)
-  float* muB;       // [n]
+  unsigned long long* muA;  // [m] sum_p |a_ip| 2^-sigma_i in 32.32 fixed point (slice-count selection only)
+  unsigned long long* muB;  // [n]
   float* stats;     // [4] min mu, min nu, any bad row, any bad column
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
@@ -62,9 +62,9 @@ int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* b
 int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig, int* sig,
                      int* bad, cudaStream_t s);
 int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                      const int* sig, float* mu, cudaStream_t s);
-int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, const int* badA,
-                     const int* badB, float* stats, cudaStream_t s);
+                      const int* sig, unsigned long long* mu, cudaStream_t s);
+int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned long long* muB, int64_t n,
+                     const int* badA, const int* badB, float* stats, cudaStream_t s);
 int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
                  const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s);
 
@@ -74,7 +74,7 @@ struct PrepJob {
   int64_t ld, R, K;  // rows r of the operand as in launch_split
   int* sig;
   int* bad;
-  float* mu;  // magnitude sums (automatic slice counts), or null
+  unsigned long long* mu;  // magnitude sums in 32.32 fixed point (automatic slice counts), or null
   uint16_t* D;
   int64_t kp;
   int rows_contig, slices;

@@ -106,10 +106,17 @@ __device__ __forceinline__ float scaled_magnitude(uint64_t bits, int sigma) {
   return __uint_as_float(fb);
 }
 
+// A block's partial magnitude sum (< 2^31) in 32.32 fixed point.  Partial sums are formed in
+// a fixed order inside a block and added across blocks as integers, so the total does not
+// depend on the order in which blocks run.
+__device__ __forceinline__ unsigned long long magnitude_fixed(float partial) {
+  return __float2ull_rz(partial * 4294967296.0f);
+}
+
 template <bool ROWS_CONTIG>
 __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
-                                                const int* __restrict__ sig, float* __restrict__ mu, int64_t bx,
-                                                int64_t by, float (*s_sum)[33]) {
+                                                const int* __restrict__ sig, unsigned long long* __restrict__ mu,
+                                                int64_t bx, int64_t by, float (*s_sum)[33]) {
   const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
@@ -124,7 +131,7 @@ __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, in
     __syncthreads();
     if (ty == 0 && r < R) {
       for (int q = 1; q < 8; ++q) acc += s_sum[q][tx];
-      atomicAdd(mu + r, acc);
+      atomicAdd(mu + r, magnitude_fixed(acc));
     }
   } else {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -134,31 +141,35 @@ __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, in
     float acc = 0.0f;
     for (int64_t p = p_begin + lane; p < p_end; p += 32) acc += scaled_magnitude(load_bits<false>(X, ld, r, p), sg);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomicAdd(mu + r, acc);
+    if (lane == 0) atomicAdd(mu + r, magnitude_fixed(acc));
   }
 }
 
 template <bool ROWS_CONTIG>
 __global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X, int64_t ld, int64_t R,
                                                     int64_t K, const int* __restrict__ sig,
-                                                    float* __restrict__ mu) {
+                                                    unsigned long long* __restrict__ mu) {
   __shared__ float s_sum[8][33];
   magnitudes_body<ROWS_CONTIG>(X, ld, R, K, sig, mu, blockIdx.x, blockIdx.y, s_sum);
 }
 
 // stats = {min over non-empty rows of mu, min over non-empty columns of nu, any bad row, any bad column}
-__device__ __forceinline__ void min_stats_body(const float* __restrict__ muA, int64_t m, const float* __restrict__ muB,
-                                               int64_t n, const int* __restrict__ badA,
+// a magnitude sum back from 32.32 fixed point
+__device__ __forceinline__ float magnitude_value(unsigned long long q) { return (float)((double)q * 0x1p-32); }
+
+__device__ __forceinline__ void min_stats_body(const unsigned long long* __restrict__ muA, int64_t m,
+                                               const unsigned long long* __restrict__ muB, int64_t n,
+                                               const int* __restrict__ badA,
                                                const int* __restrict__ badB, float* __restrict__ stats,
                                                float (*s_min)[256], int (*s_bad)[256]) {
   float mn[2] = {3.0e38f, 3.0e38f};
   int bd[2] = {0, 0};
   for (int64_t i = threadIdx.x; i < m; i += 256) {
-    if (muA[i] > 0.0f) mn[0] = fminf(mn[0], muA[i]);
+    if (muA[i] > 0ull) mn[0] = fminf(mn[0], magnitude_value(muA[i]));
     bd[0] |= badA[i];
   }
   for (int64_t j = threadIdx.x; j < n; j += 256) {
-    if (muB[j] > 0.0f) mn[1] = fminf(mn[1], muB[j]);
+    if (muB[j] > 0ull) mn[1] = fminf(mn[1], magnitude_value(muB[j]));
     bd[1] |= badB[j];
   }
   for (int q = 0; q < 2; ++q) {
@@ -182,8 +193,8 @@ __device__ __forceinline__ void min_stats_body(const float* __restrict__ muA, in
   }
 }
 
-__global__ void __launch_bounds__(256) k_min_stats(const float* __restrict__ muA, int64_t m,
-                                                   const float* __restrict__ muB, int64_t n,
+__global__ void __launch_bounds__(256) k_min_stats(const unsigned long long* __restrict__ muA, int64_t m,
+                                                   const unsigned long long* __restrict__ muB, int64_t n,
                                                    const int* __restrict__ badA, const int* __restrict__ badB,
                                                    float* __restrict__ stats) {
   __shared__ float s_min[2][256];
@@ -324,7 +335,7 @@ __global__ void __launch_bounds__(256) k_prep_init_batched(const PrepJob* __rest
   for (int64_t r = threadIdx.x; r < j.R; r += blockDim.x) {
     j.sig[r] = kExpEmpty;
     j.bad[r] = 0;
-    if (j.mu) j.mu[r] = 0.0f;
+    if (j.mu) j.mu[r] = 0ull;
   }
 }
 
@@ -384,8 +395,8 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_sigB = off; off = up(off + sizeof(int) * (size_t)n);
   const size_t o_badA = off; off = up(off + sizeof(int) * (size_t)m);
   const size_t o_badB = off; off = up(off + sizeof(int) * (size_t)n);
-  const size_t o_muA = off; off = up(off + sizeof(float) * (size_t)m);
-  const size_t o_muB = off; off = up(off + sizeof(float) * (size_t)n);
+  const size_t o_muA = off; off = up(off + sizeof(unsigned long long) * (size_t)m);
+  const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
@@ -403,8 +414,8 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->sigB = reinterpret_cast<int*>(b + o_sigB);
     ws->badA = reinterpret_cast<int*>(b + o_badA);
     ws->badB = reinterpret_cast<int*>(b + o_badB);
-    ws->muA = reinterpret_cast<float*>(b + o_muA);
-    ws->muB = reinterpret_cast<float*>(b + o_muB);
+    ws->muA = reinterpret_cast<unsigned long long*>(b + o_muA);
+    ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -426,7 +437,7 @@ int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool row
 }
 
 int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                      const int* sig, float* mu, cudaStream_t s) {
+                      const int* sig, unsigned long long* mu, cudaStream_t s) {
   if (R == 0 || K == 0) return GBD_OK;
   const unsigned gy = (unsigned)((K + kRedChunk - 1) / kRedChunk);
   if (rows_contig) k_magnitudes<true><<<dim3((unsigned)((R + 31) / 32), gy), 256, 0, s>>>(X, ld, R, K, sig, mu);
@@ -434,8 +445,8 @@ int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool ro
   return launch_check("magnitude kernel launch");
 }
 
-int launch_min_stats(const float* muA, int64_t m, const float* muB, int64_t n, const int* badA,
-                     const int* badB, float* stats, cudaStream_t s) {
+int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned long long* muB, int64_t n,
+                     const int* badA, const int* badB, float* stats, cudaStream_t s) {
   k_min_stats<<<1, 256, 0, s>>>(muA, m, muB, n, badA, badB, stats);
   return launch_check("statistics kernel launch");
 }

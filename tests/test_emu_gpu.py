@@ -259,3 +259,13 @@ def test_deterministic():
     o1, _ = run_emu("T", "T", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, slices=8)
     o2, _ = run_emu("T", "T", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, slices=8)
     assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64))
+
+
+def test_automatic_statistics_do_not_depend_on_block_order():
+    # k > 1024: every row's magnitude sum adds several blocks' partial sums; they are added as
+    # fixed-point integers, so the statistics behind the automatic slice count repeat exactly
+    m, n, k = 300, 260, 5000
+    for ta, tb in (("N", "N"), ("T", "T")):
+        A, lda, B, ldb, C, ldc = _problem(ta, tb, m, n, k, "scaled", 5, e=4)
+        infos = [run_emu(ta, tb, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, slices=0)[1] for _ in range(4)]
+        assert len({(i.mu_min, i.nu_min, i.bound_est, i.slices) for i in infos}) == 1
