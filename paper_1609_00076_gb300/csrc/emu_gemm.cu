@@ -20,6 +20,7 @@
 //               element and group, coalesced down the columns of C.
 // All waits are bounded (2 s); a wait that gives up sets the device error word and
 // the kernel runs to its end without hanging.
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -1021,6 +1022,20 @@ int launch_slice_gemm_grouped_pair(const EmuTableEntry* table_dev, int count, in
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped slice gemm pair launch");
 }
 
+// Throughput per SM of the two-SM 256 x 256 kernel relative to the one-SM 128 x 128 kernel, as
+// a function of k, measured on GB300 with every SM busy (2048 x 2048 outputs, 8 slices).  The
+// two-SM kernel moves half the operand bytes per flop but pays for its deferred FP64 update
+// per tile, which only a deep inner dimension amortises.
+double pair_gain(int64_t k) {
+  static const double lk[] = {7, 8, 9, 10, 11, 12, 13};                    // log2 k
+  static const double gain[] = {0.42, 0.51, 0.69, 0.98, 1.29, 1.56, 1.80};  // 8192: from the 8192^3 runs
+  const double x = log2((double)(k > 1 ? k : 1));
+  if (x <= lk[0]) return gain[0];
+  for (int i = 1; i < 7; ++i)
+    if (x <= lk[i]) return gain[i - 1] + (gain[i] - gain[i - 1]) * (x - lk[i - 1]) / (lk[i] - lk[i - 1]);
+  return gain[6];
+}
+
 int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t stream) {
   int sms = 0;
   int rc = current_device(nullptr, &sms);
@@ -1030,11 +1045,14 @@ int launch_slice_gemm(const GemmParams& gp, const Workspace& ws, cudaStream_t st
   const char* force = getenv("GBD_EMU_KERNEL");
   if (force && force[0] == 'p') return launch_pair(gp, ws, sms, stream);
   const bool single = force && force[0] == 's';
-  // enough 256 x 256 pair tiles to occupy every SM pair and an inner dimension deep enough to
-  // amortise the two-SM kernel's deferred FP64 update (measured per SM: even at k = 512, ahead
-  // from k = 1024): the two-SM kernel
+  // Expected time of each kernel in units of one 128 x 128 tile on one SM: whole waves of tiles
+  // over the SMs (or SM pairs), a 256 x 256 tile being four units on two SMs at pair_gain(k).
+  const int64_t tiles = ((gp.m + kBM - 1) / kBM) * ((gp.n + kBM - 1) / kBM);
   const int64_t pair_tiles = ((gp.m + k2BM - 1) / k2BM) * ((gp.n + k2BN - 1) / k2BN);
-  if (!single && pair_tiles >= sms / 2 && gp.k >= 1024) return launch_pair(gp, ws, sms, stream);
+  const int64_t pairs = sms / 2 > 0 ? sms / 2 : 1;
+  const double t_one = (double)((tiles + sms - 1) / sms);
+  const double t_pair = (double)((pair_tiles + pairs - 1) / pairs) * 2.0 / pair_gain(gp.k);
+  if (!single && t_pair < t_one) return launch_pair(gp, ws, sms, stream);
   return launch_bn<128>(gp, ws, sms, stream);
 }
 
