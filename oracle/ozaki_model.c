@@ -32,10 +32,13 @@
  *     smallest level is h sums its levels exactly as one integer,
  *         Y = sum_{g in group} P_{g,S} 2^(b (h - g)),
  *     and adds it with one rounding,
- *         W = fma(alpha * 2^(sigma_i + tau_j - h*b), Y, W).
+ *         W = fma(alpha * 2^(tau_j - h*b), Y * 2^sigma_i, W),
+ *     the power of two split between the two factors as written (each factor is
+ *     formed with ldexp, so the result stays a single rounding of the exact value
+ *     while both factors are normal numbers, and results near the underflow range
+ *     do not lose bits to an intermediate underflow of 2^(sigma_i + tau_j - h*b)).
  *     The result is W.  |P_{g,S}| <= 9 * kseg * (2^b - 1)^2 < 2^30.2 for the
- *     kseg = 8192, b = 7 of the GPU path, so |Y| < 2^51.2 and Y is exact in FP64;
- *     alpha * 2^e is exact while it stays a normal number.
+ *     kseg = 8192, b = 7 of the GPU path, so |Y| < 2^51.2 and Y is exact in FP64.
  *
  * Pairs with t + u > s + 1 are dropped; the truncation and the dropped pairs
  * bound the error by |alpha| 2^(sigma_i + tau_j - s*b) (mu_i + nu_j + (s-1)(1+2^-b) N)
@@ -149,7 +152,7 @@ static void* oz_run(void* arg) {
             }
             Y += P * ((int64_t)1 << (b * (h - g)));
           }
-          W = fma(ldexp(J->alpha, J->rsig[r] + tau - h * b), (double)Y, W);
+          W = fma(ldexp(J->alpha, tau - h * b), ldexp((double)Y, J->rsig[r]), W);
         }
       }
       J->out[j * J->ldo + r] = W;

@@ -152,6 +152,30 @@ def test_adversarial_exact_accumulation(oracle_mod, kernel):
     check_bound(oracle_mod, "N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, out, exact=True)
 
 
+@pytest.mark.parametrize("case", ["near_underflow", "subnormal_results", "subnormal_inputs", "overflow"])
+def test_model_parity_extreme_exponents(oracle_mod, kernel, case):
+    # The level scale is applied as alpha 2^(tau_j - 7h) times Y 2^sigma_i, on both sides; these
+    # ranges put results near the underflow threshold, below it, inputs below it, and results
+    # past the overflow threshold (Inf).
+    m, n, k = 150, 140, 300
+    scale_a, scale_b, kind, slices = {
+        "near_underflow": (2.0 ** -510, 2.0 ** -510, "int8", 3),
+        "subnormal_results": (2.0 ** -530, 2.0 ** -505, "uniform", 9),
+        "subnormal_inputs": (2.0 ** -1060, 2.0 ** -10, "uniform", 9),
+        "overflow": (2.0 ** 520, 2.0 ** 510, "uniform", 5),
+    }[case]
+    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, kind, 77, pads=(1, 0, 2))
+    A = A * scale_a
+    B = B * scale_b
+    out, _ = run_emu("N", "T", m, n, k, 0.7, A, lda, B, ldb, 0.0, C, ldc, slices=slices)
+    check_model(oracle_mod, "N", "T", m, n, k, 0.7, A, lda, B, ldb, 0.0, C, ldc, out, slices)
+    got = synth.view(out, m, n, ldc)
+    if case == "overflow":
+        assert np.isinf(got).any()
+    if case in ("subnormal_results", "subnormal_inputs"):
+        assert ((got != 0) & (np.abs(got) < 2.0 ** -1022)).any()
+
+
 def test_nonfinite_rows_and_columns(oracle_mod, kernel):
     m, n, k = 140, 150, 90
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "uniform", 9)

@@ -209,3 +209,24 @@ def test_one_level_group_rounds_once(oracle_mod):
         for j in range(n):
             want = float(Fraction(alpha) * int(S[i, j]) + Fraction(beta * float(C0[j * m + i])))
             assert out[j * m + i] == want, (i, j)
+
+
+def test_scale_split_keeps_results_near_underflow_exact(oracle_mod):
+    # Integers up to 8 in magnitude scaled by 2^-510: one 7-bit digit holds them exactly, and the
+    # result alpha x (integer product) x 2^-1020 is a normal number, so the method gives it
+    # correctly rounded.  alpha 2^(sigma_i + tau_j - 14) = 0.7 x 2^-1026 would be subnormal and
+    # lose bits of alpha, so the power of two has to be split between alpha 2^(tau_j - 14) and
+    # P 2^sigma_i.
+    m, n, k = 9, 7, 200
+    alpha = 0.7
+    A = synth.matrix("int8", m, k, m, 31) * 2.0 ** -510
+    B = synth.matrix("int8", k, n, k, 32) * 2.0 ** -510
+    Ai = np.rint(synth.view(A, m, k, m) * 2.0 ** 510).astype(np.int64)
+    Bi = np.rint(synth.view(B, k, n, k) * 2.0 ** 510).astype(np.int64)
+    S = Ai @ Bi
+    assert np.abs(S).max() < 2 ** 53 and np.all(np.abs(S[S != 0]) >= 2)
+    out = oracle_mod.ozaki_dgemm_rows("N", "N", m, n, k, alpha, A, m, B, k, 0.0, None, m, 1)
+    for i in range(m):
+        for j in range(n):
+            want = float(Fraction(alpha) * int(S[i, j]) * Fraction(1, 2 ** 1020))
+            assert out[j * m + i] == want, (i, j)
