@@ -3,7 +3,7 @@
 // Tensor Memory), exact integer level sums, and the FP64 update of C.
 //
 // Persistent, warp-specialised kernel; one 128 x BN output tile at a time per CTA:
-//   warp 0      TMA producer: for each (segment, level g, pair t, k-block) loads the
+//   warp 0      TMA producer: for each (segment, level g, k-block, pair t) loads the
 //               128 x 64 tile of digit slice t of op(A) and the BN x 64 tile of slice
 //               g-t of op(B)^T (128-byte swizzle) into a kStages-deep ring;
 //   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per k-block into one
@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kThreads1, 1)
           const int segn = min(kSegBlocks, j.nkb - seg0);
           for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
             for (int g = h; g >= group_high(h); --g)
-              for (int t = 1; t <= g - 1; ++t)
-                for (int kb = seg0; kb < seg0 + segn; ++kb) {
+              for (int kb = seg0; kb < seg0 + segn; ++kb)  // k-major: tiles in flight share a narrow k window in L2
+                for (int t = 1; t <= g - 1; ++t) {
                   mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
                   mbar_arrive_expect_tx(&full[stage], bytes);
                   tma_load_3d(smem + L::kOffA + stage * L::kABytes, mapA, &full[stage], kb * kBK, m0, t - 1);
@@ -658,8 +658,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           const int segn = min(kSegBlocks, j.nkb - seg0);
           for (int h = s + 1; h >= 2; h -= kGroupLevels)
             for (int g = h; g >= group_high(h); --g)
-              for (int t = 1; t <= g - 1; ++t)
-                for (int kb = seg0; kb < seg0 + segn; ++kb) {
+              for (int kb = seg0; kb < seg0 + segn; ++kb)  // k-major: tiles in flight share a narrow k window in L2
+                for (int t = 1; t <= g - 1; ++t) {
                   mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
                   if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
                   const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
