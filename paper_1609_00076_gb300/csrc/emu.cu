@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdint>
 
+#include <cstring>
+
 #include "emu.cuh"
 
 namespace gbd {
@@ -103,22 +105,23 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   // op(A) rows: A[p*lda + i] when 'N' (rows contiguous), A[i*lda + p] when 'T'
   // op(B)^T rows (= columns j of op(B)): B[j*ldb + p] when 'N', B[p*ldb + j] when 'T'
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.sigA, 0x80, sizeof(int) * (size_t)m, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(ws.sigB, 0x80, sizeof(int) * (size_t)n, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(ws.badA, 0, sizeof(int) * (size_t)m, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(ws.badB, 0, sizeof(int) * (size_t)n, s)) != cudaSuccess)
-    return cuda_fail(e, "dgemm_emu: workspace initialisation");
-  if ((rc = launch_exponents(A, lda, m, k, ta == 0, ws.sigA, ws.badA, s))) return rc;
-  if ((rc = launch_exponents(B, ldb, n, k, tb != 0, ws.sigB, ws.badB, s))) return rc;
+  // both operand sides in one launch per step: op(A) (m rows of k) and op(B)^T (n rows of k)
+  PrepPair pp;
+  memset(&pp, 0, sizeof(pp));
+  PrepJob& ja = pp.j[0];
+  PrepJob& jb = pp.j[1];
+  ja.X = A; ja.ld = lda; ja.R = m; ja.K = k; ja.rows_contig = ta == 0;
+  ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = slices == 0 ? ws.muA : nullptr; ja.D = ws.DA; ja.kp = ws.kp;
+  jb.X = B; jb.ld = ldb; jb.R = n; jb.K = k; jb.rows_contig = tb != 0;
+  jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = slices == 0 ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
+  int64_t exp_blocks = 0, split_blocks = 0;
+  prep_pair_blocks(pp, exp_blocks, split_blocks);
+  if ((rc = launch_exponents_pair(pp, exp_blocks, s))) return rc;
 
   int s_use = slices;
   double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
   if (slices == 0) {
-    if ((e = cudaMemsetAsync(ws.muA, 0, sizeof(unsigned long long) * (size_t)m, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.muB, 0, sizeof(unsigned long long) * (size_t)n, s)) != cudaSuccess)
-      return cuda_fail(e, "dgemm_emu: workspace initialisation");
-    if ((rc = launch_magnitudes(A, lda, m, k, ta == 0, ws.sigA, ws.muA, s))) return rc;
-    if ((rc = launch_magnitudes(B, ldb, n, k, tb != 0, ws.sigB, ws.muB, s))) return rc;
+    if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
     if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
     float st[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(st, ws.stats, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -129,8 +132,9 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
     const double target = tol > 0.0 ? tol : 2.0 * (double)k * kU;
     s_use = (mu_min > 0.0 && nu_min > 0.0) ? choose_slices(target, mu_min, nu_min, k, &bound) : 1;
   }
-  if ((rc = launch_split(A, lda, m, k, ta == 0, ws.sigA, s_use, ws.DA, ws.kp, s))) return rc;
-  if ((rc = launch_split(B, ldb, n, k, tb != 0, ws.sigB, s_use, ws.DB, ws.kp, s))) return rc;
+  ja.slices = s_use;
+  jb.slices = s_use;
+  if ((rc = launch_split_pair(pp, split_blocks, s))) return rc;
   // the slice tensors are laid out for s_use slices from the start of each region
   GemmParams gp;
   gp.m = m; gp.n = n; gp.k = k;

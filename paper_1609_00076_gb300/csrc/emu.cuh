@@ -57,21 +57,15 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
 // smallest slice count whose estimated componentwise relative bound is <= tol
 int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* bound);
 
-// Rows r of op(X) (R rows, K columns): element (r, p) is X[p*ld + r] when rows_contig,
-// X[r*ld + p] otherwise.
-int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig, int* sig,
-                     int* bad, cudaStream_t s);
-int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                      const int* sig, unsigned long long* mu, cudaStream_t s);
+// min over rows of muA, over columns of muB, any bad row, any bad column -> stats[0..3]
 int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned long long* muB, int64_t n,
                      const int* badA, const int* badB, float* stats, cudaStream_t s);
-int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                 const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s);
 
-// One operand side of one problem for the batched preparation kernels (grouped calls).
+// One operand side of one problem for the preparation kernels.  Rows r of op(X) (R rows, K
+// columns): element (r, p) is X[p*ld + r] when rows_contig, X[r*ld + p] otherwise.
 struct PrepJob {
   const double* X;
-  int64_t ld, R, K;  // rows r of the operand as in launch_split
+  int64_t ld, R, K;
   int* sig;
   int* bad;
   unsigned long long* mu;  // magnitude sums in 32.32 fixed point (automatic slice counts), or null
@@ -83,6 +77,18 @@ struct PrepJob {
 };
 // fills j's block ranges, advancing the running block counts of both launches
 void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks);
+
+// Both operand sides of one problem (j[0] = op(A), j[1] = op(B)^T), passed to the kernels by
+// value: a single call prepares them with one launch per step.
+struct PrepPair {
+  PrepJob j[2];
+};
+void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks);
+// exponents (and, when the jobs carry magnitude arrays, their zeroing) of both sides; with
+// K <= 1024 every row has one block, which stores its result and needs no initialisation
+int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
+int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
+int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
 int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
                         bool exponents, bool split, cudaStream_t s);

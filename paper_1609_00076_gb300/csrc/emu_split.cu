@@ -35,10 +35,12 @@ constexpr int kRedChunk = 1024;  // k elements per block of the reductions
 
 // sigma_r = max over non-zero finite entries of the frexp exponent; bad_r |= any Inf/NaN.
 // Block (bx, by) covers 32 rows (ROWS_CONTIG) or 8 rows x 1024 k.
+// direct: this block is the only one covering its rows (K <= kRedChunk), so the results are
+// stored, with no initialisation of sig and bad needed; otherwise they are merged atomically.
 template <bool ROWS_CONTIG>
 __device__ __forceinline__ void exponents_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
                                                int* __restrict__ sig, int* __restrict__ bad, int64_t bx, int64_t by,
-                                               int (*s_max)[33], int (*s_bad)[33]) {
+                                               int (*s_max)[33], int (*s_bad)[33], bool direct = false) {
   const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
@@ -61,8 +63,13 @@ __device__ __forceinline__ void exponents_body(const double* __restrict__ X, int
         mx = max(mx, s_max[q][tx]);
         bd |= s_bad[q][tx];
       }
-      if (mx != kExpEmpty) atomicMax(sig + r, mx);
-      if (bd) atomicOr(bad + r, 1);
+      if (direct) {
+        sig[r] = mx;
+        bad[r] = bd;
+      } else {
+        if (mx != kExpEmpty) atomicMax(sig + r, mx);
+        if (bd) atomicOr(bad + r, 1);
+      }
     }
   } else {
     // one row per warp, lanes along the contiguous k direction
@@ -81,18 +88,15 @@ __device__ __forceinline__ void exponents_body(const double* __restrict__ X, int
       bd |= __shfl_xor_sync(0xffffffffu, bd, o);
     }
     if (lane == 0) {
-      if (mx != kExpEmpty) atomicMax(sig + r, mx);
-      if (bd) atomicOr(bad + r, 1);
+      if (direct) {
+        sig[r] = mx;
+        bad[r] = bd;
+      } else {
+        if (mx != kExpEmpty) atomicMax(sig + r, mx);
+        if (bd) atomicOr(bad + r, 1);
+      }
     }
   }
-}
-
-template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(256) k_exponents(const double* __restrict__ X, int64_t ld, int64_t R,
-                                                   int64_t K, int* __restrict__ sig, int* __restrict__ bad) {
-  __shared__ int s_max[8][33];
-  __shared__ int s_bad[8][33];
-  exponents_body<ROWS_CONTIG>(X, ld, R, K, sig, bad, blockIdx.x, blockIdx.y, s_max, s_bad);
 }
 
 // |x| * 2^-sigma as a float (truncated mantissa; an estimate for slice selection)
@@ -116,7 +120,7 @@ __device__ __forceinline__ unsigned long long magnitude_fixed(float partial) {
 template <bool ROWS_CONTIG>
 __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
                                                 const int* __restrict__ sig, unsigned long long* __restrict__ mu,
-                                                int64_t bx, int64_t by, float (*s_sum)[33]) {
+                                                int64_t bx, int64_t by, float (*s_sum)[33], bool direct = false) {
   const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
@@ -131,7 +135,8 @@ __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, in
     __syncthreads();
     if (ty == 0 && r < R) {
       for (int q = 1; q < 8; ++q) acc += s_sum[q][tx];
-      atomicAdd(mu + r, magnitude_fixed(acc));
+      if (direct) mu[r] = magnitude_fixed(acc);
+      else atomicAdd(mu + r, magnitude_fixed(acc));
     }
   } else {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -141,19 +146,13 @@ __device__ __forceinline__ void magnitudes_body(const double* __restrict__ X, in
     float acc = 0.0f;
     for (int64_t p = p_begin + lane; p < p_end; p += 32) acc += scaled_magnitude(load_bits<false>(X, ld, r, p), sg);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomicAdd(mu + r, magnitude_fixed(acc));
+    if (lane == 0) {
+      if (direct) mu[r] = magnitude_fixed(acc);
+      else atomicAdd(mu + r, magnitude_fixed(acc));
+    }
   }
 }
 
-template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(256) k_magnitudes(const double* __restrict__ X, int64_t ld, int64_t R,
-                                                    int64_t K, const int* __restrict__ sig,
-                                                    unsigned long long* __restrict__ mu) {
-  __shared__ float s_sum[8][33];
-  magnitudes_body<ROWS_CONTIG>(X, ld, R, K, sig, mu, blockIdx.x, blockIdx.y, s_sum);
-}
-
-// stats = {min over non-empty rows of mu, min over non-empty columns of nu, any bad row, any bad column}
 // a magnitude sum back from 32.32 fixed point
 __device__ __forceinline__ float magnitude_value(unsigned long long q) { return (float)((double)q * 0x1p-32); }
 
@@ -311,14 +310,6 @@ __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t
   write_digits(x, sg, slices, R, K, r, pbase, D, kp);
 }
 
-template <bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kSplitThreads) k_split(const double* __restrict__ X, int64_t ld, int64_t R,
-                                               int64_t K, const int* __restrict__ sig, int slices,
-                                               uint16_t* __restrict__ D, int64_t kp) {
-  __shared__ uint64_t tile[ROWS_CONTIG ? kTile : 1][kTile + 1];  // the transpose tile, when one is needed
-  split_body<ROWS_CONTIG>(X, ld, R, K, sig, slices, D, kp, blockIdx.x, blockIdx.y, tile);
-}
-
 // ---- batched forms over a job table (one operand side of one problem per job) ----
 __device__ __forceinline__ int find_job(const PrepJob* __restrict__ jobs, int njobs, int64_t b, bool split) {
   int lo = 0, hi = njobs - 1;
@@ -380,6 +371,49 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
 }
 
+// ---- both operand sides of one problem in one launch (single calls) ----
+// job 0 is op(A), job 1 op(B)^T; their blocks are numbered by prep_job_blocks.  The jobs are
+// kernel arguments, so no job table has to be copied to the device.
+__global__ void __launch_bounds__(256) k_prep_init_pair(const __grid_constant__ PrepPair pp) {
+  const PrepJob& j = pp.j[blockIdx.y];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
+    j.sig[r] = kExpEmpty;
+    j.bad[r] = 0;
+    if (j.mu) j.mu[r] = 0ull;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_exponents_pair(const __grid_constant__ PrepPair pp, bool direct) {
+  __shared__ int s_max[8][33];
+  __shared__ int s_bad[8][33];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig) exponents_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.bad, bx, by, s_max, s_bad, direct);
+  else exponents_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.bad, bx, by, s_max, s_bad, direct);
+}
+
+__global__ void __launch_bounds__(256) k_magnitudes_pair(const __grid_constant__ PrepPair pp, bool direct) {
+  __shared__ float s_sum[8][33];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig) magnitudes_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum, direct);
+  else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum, direct);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_pair(const __grid_constant__ PrepPair pp) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
+}
+
 int launch_check(const char* what) {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, what);
@@ -425,24 +459,6 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->kp = kp;
   }
   return off;
-}
-
-int launch_exponents(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig, int* sig,
-                     int* bad, cudaStream_t s) {
-  if (R == 0 || K == 0) return GBD_OK;
-  const unsigned gy = (unsigned)((K + kRedChunk - 1) / kRedChunk);
-  if (rows_contig) k_exponents<true><<<dim3((unsigned)((R + 31) / 32), gy), 256, 0, s>>>(X, ld, R, K, sig, bad);
-  else k_exponents<false><<<dim3((unsigned)((R + 7) / 8), gy), 256, 0, s>>>(X, ld, R, K, sig, bad);
-  return launch_check("exponent kernel launch");
-}
-
-int launch_magnitudes(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                      const int* sig, unsigned long long* mu, cudaStream_t s) {
-  if (R == 0 || K == 0) return GBD_OK;
-  const unsigned gy = (unsigned)((K + kRedChunk - 1) / kRedChunk);
-  if (rows_contig) k_magnitudes<true><<<dim3((unsigned)((R + 31) / 32), gy), 256, 0, s>>>(X, ld, R, K, sig, mu);
-  else k_magnitudes<false><<<dim3((unsigned)((R + 7) / 8), gy), 256, 0, s>>>(X, ld, R, K, sig, mu);
-  return launch_check("magnitude kernel launch");
 }
 
 int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned long long* muB, int64_t n,
@@ -495,14 +511,41 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
   return launch_check("batched statistics launch");
 }
 
-int launch_split(const double* X, int64_t ld, int64_t R, int64_t K, bool rows_contig,
-                 const int* sig, int slices, uint16_t* D, int64_t kp, cudaStream_t s) {
-  if (R == 0 || K == 0) return GBD_OK;
-  dim3 grid((unsigned)((K + kTile - 1) / kTile), (unsigned)((R + kTile - 1) / kTile));
-  if (rows_contig) k_split<true><<<grid, kSplitThreads, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
-  else k_split<false><<<grid, kSplitThreads, 0, s>>>(X, ld, R, K, sig, slices, D, kp);
-  return launch_check("split kernel launch");
+void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks) {
+  exp_blocks = 0;
+  split_blocks = 0;
+  prep_job_blocks(pp.j[0], exp_blocks, split_blocks);
+  prep_job_blocks(pp.j[1], exp_blocks, split_blocks);
 }
+
+int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s) {
+  if (exp_blocks <= 0) return GBD_OK;
+  if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many exponent blocks");
+  const bool direct = pp.j[0].K <= kRedChunk;  // both sides share K: one block per row
+  if (!direct) {  // several blocks per row merge atomically into zeroed arrays
+    const int64_t rmax = pp.j[0].R > pp.j[1].R ? pp.j[0].R : pp.j[1].R;
+    const unsigned gx = (unsigned)((rmax + 255) / 256 < 1024 ? (rmax + 255) / 256 : 1024);
+    k_prep_init_pair<<<dim3(gx > 0 ? gx : 1, 2), 256, 0, s>>>(pp);
+    int rc = launch_check("exponent initialisation launch");
+    if (rc) return rc;
+  }
+  k_exponents_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, direct);
+  return launch_check("exponent launch");
+}
+
+int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s) {
+  if (exp_blocks <= 0) return GBD_OK;
+  k_magnitudes_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, pp.j[0].K <= kRedChunk);
+  return launch_check("magnitude launch");
+}
+
+int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s) {
+  if (split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
+  k_split_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp);
+  return launch_check("split launch");
+}
+
 
 }  // namespace emu
 }  // namespace gbd
