@@ -116,7 +116,7 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = slices == 0 ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
-  if ((rc = launch_exponents_pair(pp, exp_blocks, s))) return rc;
+  if ((rc = launch_exponents_pair(pp, exp_blocks, ws.ysum, ws.zero_bytes, s))) return rc;
 
   int s_use = slices;
   double bound = 0.0, mu_min = 0.0, nu_min = 0.0;

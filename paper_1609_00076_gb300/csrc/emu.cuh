@@ -48,9 +48,22 @@ struct Workspace {
   int32_t* scratch_p;  // [scratch_ctas][kParkSlots][128 * 256] parked integer level sums of the two-SM kernel
   int scratch_ctas;
   int64_t kp;       // k rounded up to 8 (16-byte rows for the tensor maps)
+  // one-SM kernel with a split inner dimension (small m x n, deep k; see split_count)
+  int splits;                  // sub-ranges per k segment, 1 = no split
+  unsigned long long* ysum;    // [tiles][segments][groups][128 x 128] exact group sums
+  unsigned int* tile_done;     // [tiles] finished items
+  size_t zero_bytes;           // ysum and tile_done are contiguous and zeroed before each call
 };
 
 constexpr int kMaxPairCtas = 256;  // scratch slots reserved for the two-SM kernel (128 pairs)
+
+// Sub-ranges per k segment for the one-SM kernel on a single problem.  Few output tiles
+// leave most SMs idle; cutting each 8192-deep segment of a tile into sub-ranges (at least two
+// k-blocks each) gives about kSplitTargetItems work items.  The items' group sums are added
+// as exact integers, so the result does not depend on the count, which is a function of the
+// sizes alone (the workspace size needs no device).
+constexpr int kSplitTargetItems = 152;
+int split_count(int64_t m, int64_t n, int64_t k);
 
 // bytes needed for (m, n, k, s) and, when base != nullptr, the pointers into it
 size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws, bool pair_scratch = true);
@@ -86,7 +99,7 @@ struct PrepPair {
 void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks);
 // exponents (and, when the jobs carry magnitude arrays, their zeroing) of both sides; with
 // K <= 1024 every row has one block, which stores its result and needs no initialisation
-int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
+int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s);
 int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job

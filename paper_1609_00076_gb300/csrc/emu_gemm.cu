@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kStages = 6;
+constexpr int kMaxGroups = (kMaxSlices + kGroupLevels - 1) / kGroupLevels;  // level groups per segment
 constexpr int kEpiWarps = 8;                     // two-SM kernel: 2 x 4 warps over 128 lanes x 256 columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpiWarps1 = 16;                   // one-SM kernel: 4 x 4 warps over 128 lanes x 128 columns
@@ -49,7 +50,7 @@ struct SmemLayout {
   static constexpr int kNumBars = 2 * kStages + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
   static constexpr int kOffScale = (kOffTmemSlot + 16 + 15) / 16 * 16;
-  static constexpr int kBytes = kOffScale + BN * 8;  // colscale of the group being finished
+  static constexpr int kBytes = kOffScale + kMaxGroups * BN * 8 + 16;  // colscale per level group, a flag
   static constexpr int kAlloc = kBytes + 1024;  // slack to align the base to 1024 bytes
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
@@ -71,6 +72,13 @@ struct Args {
   double* scratch;     // two-SM kernel: one 128 x 256 FP64 slot per CTA (running sums)
   int32_t* scratch_p;  // two-SM kernel: kParkSlots 128 x 256 int32 slots per CTA (parked level sums)
   unsigned int* err;
+  // one-SM kernel, split inner dimension: each k segment of a tile is cut into `splits`
+  // sub-ranges, one work item each; the items add their exact group sums into ysum
+  // [tile][segment][group][128 x 128] (column-major) and the tile's last item applies them
+  int splits;               // 1: a CTA takes whole tiles
+  int nsegs, ngroups;       // k segments per tile, level groups per segment
+  unsigned long long* ysum;  // zeroed before the launch
+  unsigned int* tile_done;   // items finished per tile, zeroed before the launch
 };
 
 // --- tcgen05 / TMA wrappers ------------------------------------------------------
@@ -238,6 +246,36 @@ __device__ __forceinline__ void get_job(const Args& p, const EmuTableEntry* tabl
   j.n0 = tn * BN;
 }
 
+// Work item of the one-SM kernel: a whole tile, or with a split inner dimension one
+// sub-range of one k segment of a tile (the items of a tile are consecutive).
+template <bool TABLE>
+__device__ __forceinline__ void item_coords(const Args& p, int item, int& tile, int& seg, int& sub) {
+  if (!TABLE && p.splits > 1) {
+    const int per = p.nsegs * p.splits;
+    tile = item / per;
+    const int r = item - tile * per;
+    seg = r / p.splits;
+    sub = r - seg * p.splits;
+  } else {
+    tile = item;
+    seg = 0;
+    sub = 0;
+  }
+}
+// k-block range [kb0, kb1) of an item (the whole inner dimension without a split)
+template <bool TABLE>
+__device__ __forceinline__ void item_range(const Args& p, int nkb, int seg, int sub, int& kb0, int& kb1) {
+  if (!TABLE && p.splits > 1) {
+    const int s0 = seg * kSegBlocks;
+    const int len = min(kSegBlocks, nkb - s0);
+    kb0 = s0 + (int)((int64_t)sub * len / p.splits);
+    kb1 = s0 + (int)((int64_t)(sub + 1) * len / p.splits);
+  } else {
+    kb0 = 0;
+    kb1 = nkb;
+  }
+}
+
 template <int BN, bool TABLE>
 __global__ void __launch_bounds__(kThreads1, 1)
     k_slice_gemm(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -257,7 +295,8 @@ __global__ void __launch_bounds__(kThreads1, 1)
   double* colscale = reinterpret_cast<double*>(smem + L::kOffScale);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = TABLE ? total_tiles : p.num_tiles;
+  const bool split = !TABLE && p.splits > 1;
+  const int nitems = TABLE ? total_tiles : (split ? p.num_tiles * p.nsegs * p.splits : p.num_tiles);
 
   if (warp == 0 && lane == 0) {
     if (!TABLE) {
@@ -292,9 +331,12 @@ __global__ void __launch_bounds__(kThreads1, 1)
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
       int cur = 0;
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int tile, seg, sub, kb0, kb1;
+        item_coords<TABLE>(p, item, tile, seg, sub);
         Job j;
         get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
+        item_range<TABLE>(p, j.nkb, seg, sub, kb0, kb1);
         const CUtensorMap* mapA = TABLE ? &j.e->tmA : &tmA;
         const CUtensorMap* mapB = TABLE ? &j.e->tmB : &tmB;
         if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
@@ -302,8 +344,8 @@ __global__ void __launch_bounds__(kThreads1, 1)
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapB) : "memory");
         }
         const int m0 = j.m0, n0 = j.n0;
-        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
-          const int segn = min(kSegBlocks, j.nkb - seg0);
+        for (int seg0 = kb0; seg0 < kb1; seg0 += kSegBlocks) {
+          const int segn = min(kSegBlocks, kb1 - seg0);
           for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
             for (int g = h; g >= group_high(h); --g)
               for (int kb = seg0; kb < seg0 + segn; ++kb)  // k-major: tiles in flight share a narrow k window in L2
@@ -325,13 +367,16 @@ __global__ void __launch_bounds__(kThreads1, 1)
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
       int cur = 0;
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int tile, seg, sub, kb0, kb1;
+        item_coords<TABLE>(p, item, tile, seg, sub);
         Job j;
         get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
-        for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks)
+        item_range<TABLE>(p, j.nkb, seg, sub, kb0, kb1);
+        for (int seg0 = kb0; seg0 < kb1; seg0 += kSegBlocks)
           for (int h = j.s + 1; h >= 2; h -= kGroupLevels)
           for (int g = h; g >= group_high(h); --g) {
-            const int segn = min(kSegBlocks, j.nkb - seg0);
+            const int segn = min(kSegBlocks, kb1 - seg0);
             const int items = (g - 1) * segn;
             for (int i0 = 0; i0 < items; i0 += kChunkBlocks, ++chunk) {
               const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
@@ -374,10 +419,14 @@ __global__ void __launch_bounds__(kThreads1, 1)
     const uint32_t y_lo = trow + 2 * BN + col0, y_hi = trow + 3 * BN + col0;
     uint32_t chunk = 0;
     uint32_t acc[kCols];
+    int* last_flag = reinterpret_cast<int*>(colscale + kMaxGroups * BN);
     int cur = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+      int tile, seg, sub, kb0, kb1;
+      item_coords<TABLE>(p, item, tile, seg, sub);
       Job j;
       get_job<kBM, BN, TABLE>(p, table, count, tile, cur, j);
+      item_range<TABLE>(p, j.nkb, seg, sub, kb0, kb1);
       const int64_t m0 = j.m0, n0 = j.n0;
       const int64_t i = m0 + row;
       const bool row_ok = i < JF(m);
@@ -390,9 +439,13 @@ __global__ void __launch_bounds__(kThreads1, 1)
       }
       double* crow = JF(C) + (n0 + col0) * JF(ldc) + i;
       const int64_t cols_left = JF(n) - n0 - col0;  // columns of this thread's part inside C
+      // split items: this thread's elements of the tile's group sums for the item's segment
+      unsigned long long* ysum_seg =
+          split ? p.ysum + ((int64_t)tile * p.nsegs + seg) * p.ngroups * (kBM * BN) + (int64_t)col0 * kBM + row
+                : nullptr;
       bool first = true;
-      for (int seg0 = 0; seg0 < j.nkb; seg0 += kSegBlocks) {
-        const int segn = min(kSegBlocks, j.nkb - seg0);
+      for (int seg0 = kb0; seg0 < kb1; seg0 += kSegBlocks) {
+        const int segn = min(kSegBlocks, kb1 - seg0);
         for (int h = j.s + 1; h >= 2; h -= kGroupLevels) {
           const int glo = group_high(h);
           for (int g = h; g >= glo; --g) {
@@ -433,6 +486,24 @@ __global__ void __launch_bounds__(kThreads1, 1)
                 tmem_st_8(y_hi + q * 8, hi);
               }
               tmem_wait_st();
+              continue;
+            }
+            if (split) {
+              // group end of a split item: add this sub-range's exact group sums into the tile's
+              // (64-bit integer additions: the total does not depend on the order of the items)
+              unsigned long long* yg = ysum_seg + (int64_t)((j.s + 1 - h) / kGroupLevels) * (kBM * BN);
+#pragma unroll
+              for (int q = 0; q < kCols / 8; ++q) {
+                uint32_t lo[8], hi[8];
+                tmem_ld_8(y_lo + q * 8, lo);
+                tmem_ld_8(y_hi + q * 8, hi);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                  const int64_t add = (int64_t)(int32_t)acc[q * 8 + jj] * ((int64_t)1 << (kDigitBits * l));
+                  const int64_t y = (l > 0 ? (int64_t)(((uint64_t)hi[jj] << 32) | lo[jj]) : 0) + add;
+                  atomicAdd(yg + (int64_t)(q * 8 + jj) * kBM, (unsigned long long)y);
+                }
+              }
               continue;
             }
             // group end: C := fma(alpha 2^(tau_j - h b), Y 2^sigma_i, C)
@@ -479,6 +550,65 @@ __global__ void __launch_bounds__(kThreads1, 1)
           }
         }
       }
+      if (!split) continue;
+      // ---- split item done: the tile's last item applies the summed groups to C ----
+      __threadfence();  // this item's additions are visible before it is counted
+      epi_bar_sync<kEpiWarps1>();
+      if (ew == 0 && lane == 0)
+        *last_flag = atomicAdd(p.tile_done + tile, 1u) == (unsigned)(p.nsegs * p.splits - 1) ? 1 : 0;
+      epi_bar_sync<kEpiWarps1>();
+      if (!*last_flag) continue;
+      __threadfence();
+      {
+        const int idx = ew * 32 + lane;  // colscale of every group: alpha 2^(tau_j - 7h)
+        if (idx < BN) {
+          const int64_t jc = n0 + idx;
+          int tau = 0;
+          bool badc = false;
+          if (jc < p.n) {
+            tau = p.sigB[jc] == kExpEmpty ? 0 : p.sigB[jc];
+            badc = p.badB[jc] != 0;
+          }
+          for (int gi = 0; gi < p.ngroups; ++gi) {
+            const int h = j.s + 1 - gi * kGroupLevels;
+            colscale[gi * BN + idx] = jc >= p.n ? 0.0
+                                      : badc   ? __longlong_as_double(0x7FF8000000000000ll)
+                                               : ldexp(p.alpha, tau - h * kDigitBits);
+          }
+        }
+      }
+      epi_bar_sync<kEpiWarps1>();
+      // W := beta*C0, then W := fma(alpha 2^(tau_j - 7h), Y 2^sigma_i, W) for every segment and
+      // group in order, as an unsplit tile does
+      const unsigned long long* ytile = p.ysum + (int64_t)tile * p.nsegs * p.ngroups * (kBM * BN) +
+                                        (int64_t)col0 * kBM + row;
+#pragma unroll 1
+      for (int q = 0; q < kCols / 8; ++q) {
+        double w[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int c = q * 8 + jj;
+          w[jj] = (p.beta != 0.0 && row_ok && c < cols_left) ? p.beta * crow[(int64_t)c * p.ldc] : 0.0;
+        }
+        for (int sg = 0; sg < p.nsegs; ++sg)
+          for (int gi = 0; gi < p.ngroups; ++gi) {
+            const unsigned long long* yg = ytile + (int64_t)(sg * p.ngroups + gi) * (kBM * BN) + (int64_t)q * 8 * kBM;
+            int64_t y[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) y[jj] = (int64_t)__ldcg(yg + (int64_t)jj * kBM);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const double x = bad_i ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64(y[jj], sig_i);
+              w[jj] = fma(colscale[gi * BN + col0 + q * 8 + jj], x, w[jj]);
+            }
+          }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int c = q * 8 + jj;
+          if (row_ok && c < cols_left) crow[(int64_t)c * p.ldc] = w[jj];
+        }
+      }
+      epi_bar_sync<kEpiWarps1>();  // colscale and the flag are rewritten by the next item
     }
   }
 
@@ -891,6 +1021,7 @@ int launch_pair(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t
   if (rc) return rc;
 
   Args a;
+  memset(&a, 0, sizeof(a));
   a.m = gp.m; a.n = gp.n; a.k = gp.k;
   a.slices = gp.slices;
   a.nkb = (int)((gp.k + kBK - 1) / kBK);
@@ -935,6 +1066,7 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   if (rc) return rc;
 
   Args a;
+  memset(&a, 0, sizeof(a));
   a.m = gp.m; a.n = gp.n; a.k = gp.k;
   a.slices = gp.slices;
   a.nkb = (int)((gp.k + kBK - 1) / kBK);
@@ -942,7 +1074,7 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   const int64_t tiles = (int64_t)a.tiles_m * ((gp.n + BN - 1) / BN);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
-  const int grid = (int)(tiles < sms ? tiles : sms);
+  int grid = (int)(tiles < sms ? tiles : sms);
   a.group_m = group_rows(grid, kBM, BN, a.tiles_m);
   a.alpha = gp.alpha; a.beta = gp.beta;
   a.C = gp.C; a.ldc = gp.ldc;
@@ -950,6 +1082,16 @@ int launch_bn(const GemmParams& gp, const Workspace& ws, int sms, cudaStream_t s
   a.scratch = nullptr;
   a.scratch_p = nullptr;
   a.err = device_error_word();
+  // split inner dimension for few tiles (the workspace holds the sums; see split_count)
+  a.splits = ws.splits;
+  a.nsegs = (a.nkb + kSegBlocks - 1) / kSegBlocks;
+  a.ngroups = (gp.slices + kGroupLevels - 1) / kGroupLevels;
+  a.ysum = ws.ysum;
+  a.tile_done = ws.tile_done;
+  if (a.splits > 1) {
+    const int64_t items = tiles * a.nsegs * a.splits;
+    grid = (int)(items < sms ? items : sms);
+  }
 
   auto kern = k_slice_gemm<BN, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);

@@ -383,9 +383,13 @@ __global__ void __launch_bounds__(256) k_prep_init_pair(const __grid_constant__ 
   }
 }
 
-__global__ void __launch_bounds__(256) k_exponents_pair(const __grid_constant__ PrepPair pp, bool direct) {
+__global__ void __launch_bounds__(256) k_exponents_pair(const __grid_constant__ PrepPair pp, bool direct,
+                                                        uint4* __restrict__ zero, int64_t zero_vecs) {
   __shared__ int s_max[8][33];
   __shared__ int s_bad[8][33];
+  // clears the slice kernel's accumulation area on the way (16-byte stores over the grid)
+  for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < zero_vecs; z += (int64_t)gridDim.x * blockDim.x)
+    zero[z] = make_uint4(0u, 0u, 0u, 0u);
   const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
@@ -421,6 +425,18 @@ int launch_check(const char* what) {
 
 }  // namespace
 
+int split_count(int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 1;
+  const int64_t tiles = ((m + 127) / 128) * ((n + 127) / 128);
+  const int64_t nkb = (k + kBK - 1) / kBK;
+  const int64_t nsegs = (nkb + kSegBlocks - 1) / kSegBlocks;
+  if (tiles * nsegs * 2 > kSplitTargetItems) return 1;
+  int64_t sp = kSplitTargetItems / (tiles * nsegs);
+  const int64_t seg_len = nkb < kSegBlocks ? nkb : kSegBlocks;
+  if (sp > seg_len / 2) sp = seg_len / 2;  // at least two k-blocks per sub-range
+  return sp < 1 ? 1 : (int)sp;
+}
+
 size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws, bool pair_scratch) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int64_t kp = (k + 7) / 8 * 8;
@@ -442,6 +458,16 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
       pair_scratch ? (int)(2 * pair_tiles < kMaxPairCtas ? 2 * pair_tiles : kMaxPairCtas) : 0;
   const size_t o_scr = off; off = up(off + sizeof(double) * 128 * 256 * (size_t)scratch_ctas);
   const size_t o_scp = off; off = up(off + sizeof(int32_t) * kParkSlots * 128 * 256 * (size_t)scratch_ctas);
+  // single calls: exact group sums of the split one-SM kernel and its per-tile counters
+  const int splits = pair_scratch ? split_count(m, n, k) : 1;
+  const int64_t tiles128 = ((m + 127) / 128) * ((n + 127) / 128);
+  const int64_t nsegs = ((k + kBK - 1) / kBK + kSegBlocks - 1) / kSegBlocks;
+  const int64_t ngroups = (s + kGroupLevels - 1) / kGroupLevels;
+  const size_t ysum_bytes =
+      splits > 1 ? sizeof(unsigned long long) * 128 * 128 * (size_t)(tiles128 * nsegs * ngroups) : 0;
+  const size_t done_bytes = splits > 1 ? sizeof(unsigned int) * (size_t)tiles128 : 0;
+  const size_t o_ysum = off;
+  off = up(off + ysum_bytes + done_bytes);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -457,6 +483,10 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->scratch_p = reinterpret_cast<int32_t*>(b + o_scp);
     ws->scratch_ctas = scratch_ctas;
     ws->kp = kp;
+    ws->splits = splits;
+    ws->ysum = reinterpret_cast<unsigned long long*>(b + o_ysum);
+    ws->tile_done = reinterpret_cast<unsigned int*>(b + o_ysum + ysum_bytes);
+    ws->zero_bytes = up(ysum_bytes + done_bytes);
   }
   return off;
 }
@@ -518,7 +548,7 @@ void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks) 
   prep_job_blocks(pp.j[1], exp_blocks, split_blocks);
 }
 
-int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s) {
+int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s) {
   if (exp_blocks <= 0) return GBD_OK;
   if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many exponent blocks");
   const bool direct = pp.j[0].K <= kRedChunk;  // both sides share K: one block per row
@@ -529,7 +559,8 @@ int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s
     int rc = launch_check("exponent initialisation launch");
     if (rc) return rc;
   }
-  k_exponents_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, direct);
+  k_exponents_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, direct, static_cast<uint4*>(zero),
+                                                        (int64_t)(zero_bytes / sizeof(uint4)));
   return launch_check("exponent launch");
 }
 

@@ -176,6 +176,16 @@ def test_model_parity_extreme_exponents(oracle_mod, kernel, case):
         assert ((got != 0) & (np.abs(got) < 2.0 ** -1022)).any()
 
 
+@pytest.mark.parametrize("m,n,k", [(200, 150, 20000), (130, 96, 8192 + 130), (64, 64, 1000)])
+def test_split_inner_dimension_matches_model(oracle_mod, m, n, k):
+    # few output tiles and a deep inner dimension: the one-SM kernel cuts each 8192-deep segment
+    # of a tile into sub-ranges whose exact group sums are added as integers; the result must be
+    # the model's bits (several segments, a short last segment, uneven sub-ranges)
+    A, lda, B, ldb, C, ldc = _problem("T", "N", m, n, k, "scaled", 91, pads=(1, 2, 3), e=5)
+    out, info = run_emu("T", "N", m, n, k, -1.25, A, lda, B, ldb, 0.5, C, ldc, slices=7)
+    check_model(oracle_mod, "T", "N", m, n, k, -1.25, A, lda, B, ldb, 0.5, C, ldc, out, 7)
+
+
 def test_nonfinite_rows_and_columns(oracle_mod, kernel):
     m, n, k = 140, 150, 90
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "uniform", 9)
