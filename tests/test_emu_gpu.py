@@ -287,6 +287,49 @@ def test_pair_and_single_kernels_agree(monkeypatch):
     assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64))
 
 
+def test_concurrent_host_threads_and_streams():
+    # two host threads, each with its own stream, workspace and output, calling the emulated
+    # entry point at the same time (ctypes releases the interpreter lock during the call)
+    import threading
+
+    import torch
+    jobs = []
+    for i, (m, n, k) in enumerate([(300, 200, 700), (257, 333, 1500)]):
+        A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "uniform", 60 + i)
+        ref, _ = run_emu("N", "T", m, n, k, 1.0, A, lda, B, ldb, 0.5, C, ldc, slices=0)
+        dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        wsb = gbdgemm.gbd_dgemm_emu_workspace_size(m, n, k, 0)
+        jobs.append(dict(args=(m, n, k, dA, lda, dB, ldb, C, ldc), ref=ref, wsb=wsb,
+                         ws=torch.empty(wsb, dtype=torch.uint8, device="cuda"), stream=torch.cuda.Stream()))
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(jb):
+        m, n, k, dA, lda, dB, ldb, C, ldc = jb["args"]
+        try:
+            for _ in range(20):
+                dC = torch.from_numpy(C).cuda()
+                rc = gbdgemm.gbd_dgemm_emu("N", "T", m, n, k, 1.0, dA, lda, dB, ldb, 0.5, dC, ldc, 0, 0.0, jb["ws"],
+                                           jb["wsb"], None, stream=jb["stream"])
+                if rc != 0:
+                    errors.append(gbdgemm.gbd_last_error())
+                    return
+                jb["stream"].synchronize()
+                if not np.array_equal(dC.cpu().numpy().view(np.uint64), jb["ref"].view(np.uint64)):
+                    errors.append("result differs from the single-threaded call")
+                    return
+        except Exception as exc:  # noqa: BLE001 -- reported to the main thread
+            errors.append(repr(exc))
+
+    threads = [threading.Thread(target=worker, args=(jb,)) for jb in jobs]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert gbdgemm.gbd_check_device_error() == 0
+
+
 def test_deterministic():
     m, n, k = 600, 500, 700
     A, lda, B, ldb, C, ldc = _problem("T", "T", m, n, k, "scaled", 3, e=8)
