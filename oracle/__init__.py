@@ -14,6 +14,9 @@ Contents
 * ``ozaki_dgemm_rows``: a plain CPU model of the split emulation (ozaki_model.c),
   same digits, same level order, same segment order as the GPU emulation but
   written independently (floating-point digit recursion instead of bit fields).
+* ``ozmod_dgemm_rows``: a plain CPU model of the modular emulation (Ozaki scheme II,
+  ozaki_mod_model.c): rounded scaled integers and their exact 128-bit product, where
+  the GPU path goes through residues and the Chinese remainder theorem.
 
 Matrices are passed as 1-D float64 numpy arrays in column-major order with an
 explicit leading dimension, exactly as in the BLAS statement (Section 2.1:
@@ -29,7 +32,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_SOURCES = ["oracle.c", "ozaki_model.c"]
+_SOURCES = ["oracle.c", "ozaki_model.c", "ozaki_mod_model.c"]
 _lib = None
 
 
@@ -70,6 +73,11 @@ def _load():
     lib.oracle_ozaki_exponent.restype = i
     lib.oracle_ozaki_split.argtypes = [d, i, i, i, vp]
     lib.oracle_ozaki_split.restype = None
+    lib.oracle_ozmod_dgemm_rows.argtypes = [c, c, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64,
+                                            i, vp, i64, vp, i64, i]
+    lib.oracle_ozmod_dgemm_rows.restype = i
+    lib.oracle_ozmod_i128_to_double.argtypes = [i64, ctypes.c_uint64]
+    lib.oracle_ozmod_i128_to_double.restype = d
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = i
     _lib = lib
@@ -156,6 +164,30 @@ def ozaki_dgemm_rows(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, l
     if rc != 0:
         raise ValueError(f"oracle_ozaki_dgemm_rows: status {rc}")
     return out[: nr * n]
+
+
+def ozmod_dgemm_rows(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc, bits, rows=None,
+                     nthreads=0):
+    """Rows of the modular emulation (model of the GPU path) with ``bits`` integer bits."""
+    lib = _load()
+    r, nr = _rows_arg(rows, m)
+    out = np.empty(max(1, nr) * max(1, n), dtype=np.float64)
+    rc = lib.oracle_ozmod_dgemm_rows(transa.encode(), transb.encode(), m, n, k, float(alpha),
+                                     _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, float(beta),
+                                     _ptr(_as_f64(C0)), ldc, int(bits), _ptr(r), nr, out.ctypes.data,
+                                     max(1, nr), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_ozmod_dgemm_rows: status {rc}")
+    return out[: nr * n]
+
+
+def ozmod_i128_to_double(v: int) -> float:
+    """The model's conversion of a 128-bit integer to double."""
+    u = v & ((1 << 128) - 1)
+    hi = u >> 64
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return _load().oracle_ozmod_i128_to_double(hi, u & ((1 << 64) - 1))
 
 
 def ozaki_exponent(x: float) -> int:
