@@ -26,10 +26,13 @@
 #include <cstring>
 
 #include "emu.cuh"
+#include "tcgen05.cuh"
 
 namespace gbd {
 namespace emu {
 namespace {
+
+using namespace tc;
 
 constexpr int kBM = 128;
 constexpr int kStages = 6;
@@ -81,82 +84,10 @@ struct Args {
   unsigned int* tile_done;   // items finished per tile, zeroed before the launch
 };
 
-// --- tcgen05 / TMA wrappers ------------------------------------------------------
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte
-// swizzle: 8-row atoms of 128-byte rows, atoms 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address / 16
-  d |= (uint64_t)1 << 16;                    // leading-dimension byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride-dimension byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 16 consecutive 32-bit columns: register j of lane l = TMEM(lane base + l, col + j)
-__device__ __forceinline__ void tmem_ld_16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// 32 lanes x 8 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_ld_8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// register j of lane l -> TMEM(lane base + l, col + j), 8 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_st_8(uint32_t taddr, const uint32_t (&v)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// named barrier 1 over the epilogue warps only
+// named barrier 1 over the epilogue warps only (the two-SM kernel's by default)
 template <int WARPS = kEpiWarps>
 __device__ __forceinline__ void epi_bar_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * WARPS) : "memory");
+  epi_barrier<WARPS>();
 }
 
 // x * 2^e for the rare results outside the normal range, out of line so that its code
@@ -186,28 +117,6 @@ __device__ __forceinline__ int64_t combine_levels(const int32_t (&P)[kGroupLevel
 
 // largest level of the group whose smallest level is h (levels h, h-1, ..., down to 2)
 __device__ __forceinline__ int group_high(int h) { return max(2, h - kGroupLevels + 1); }
-
-// Tile order: the CTAs that run at the same time take consecutive tile indices;
-// grouping group_m row tiles per column makes that set a near-square block, so the
-// slices of A and B it streams are shared in L2 instead of re-read from HBM.
-__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int group_m, int num_tiles, int& tm, int& tn) {
-  const int tiles_n = num_tiles / tiles_m;
-  const int group = tile / (group_m * tiles_n);
-  const int first_m = group * group_m;
-  const int gm = min(tiles_m - first_m, group_m);
-  const int local = tile - group * group_m * tiles_n;
-  tm = first_m + local % gm;
-  tn = local / gm;
-}
-
-// Row tiles per raster group: the `concurrent` tiles in flight cover about
-// group x concurrent/group tiles of bm x bn, near-square when group*bm ~ (concurrent/group)*bn.
-int group_rows(int concurrent, int bm, int bn, int tiles_m) {
-  int g = 1;
-  while ((2 * g) * (2 * g) * bm <= concurrent * bn) g *= 2;  // g ~ sqrt(concurrent * bn / bm), a power of two
-  if (g > tiles_m) g = tiles_m;
-  return g < 1 ? 1 : g;
-}
 
 // number of MMA chunks of level-segment (g, seg0..seg0+segn)
 __device__ __forceinline__ int chunks_of(int g, int segn) {
@@ -649,73 +558,6 @@ struct Smem2 {
   static constexpr int kAlloc = kBytes + 1024;
 };
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// shared::cluster address of the same shared variable in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait with cluster-scope acquire (arrivals may come from the peer CTA)
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, unsigned int* err,
-                                                  unsigned int code) {
-  if (mbar_try_wait_cluster(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) {
-      if (err) atomicOr(err, code);
-      return false;
-    }
-  }
-}
-// TMA load into this CTA's shared memory, completion counted on a barrier of either CTA of the pair
-__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* tm, uint32_t bar_cluster_addr, int x,
-                                                 int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
-      "%4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar_cluster_addr), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                               uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// arrive (once) on the barrier at this offset in both CTAs of the pair when the issued MMAs complete
-__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"((uint16_t)3)
-      : "memory");
-}
 template <bool TABLE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_slice_gemm_pair(const Args p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
