@@ -168,6 +168,43 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
                                   double tol, gbd_emu_info* info, void* stream);
 
 /*
+ * Double-precision GEMM emulated with the integer modular technique of Ozaki, Uchino
+ * and Imamura ("Ozaki Scheme II", 2025); the operation and the argument list are those
+ * of gbd_dgemm (Section 1.2 of the paper).
+ *
+ * Steps: the exponents sigma_i, tau_j of gbd_dgemm_emu; the integers
+ * A' = rint(a_ip 2^(t - sigma_i)) and B' = rint(b_pj 2^(t - tau_j)) (ties to even,
+ * |.| <= 2^t); their residues modulo the first n of the pairwise coprime moduli
+ * 256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, with
+ * n the fewest whose product M exceeds 2 k 2^(2t); one BF16 tcgen05 product per modulus
+ * (exact FP32 chunks, int32 sums); the Chinese remainder reconstruction of the exact
+ * integer C' = A'B'; and C := fma(alpha 2^(tau_j - 2t), fl(C') 2^sigma_i, beta C) with fl
+ * correctly rounded.  The products number n (13 at 44 bits and k = 8192) where the split
+ * emulation needs s(s+1)/2.
+ *
+ * bits: t in 1..62, or 0 to choose the smallest t whose estimated componentwise error
+ *   stays below `tol` (as for gbd_dgemm_emu; tol <= 0 means 2 k 2^-53).  Automatic mode
+ *   reads 16 bytes back and so synchronises `stream`.  When t (given or chosen) needs
+ *   more than 16 moduli at this k the call returns GBD_ERR_LIMIT (gbd_dgemm_emu covers
+ *   any target).
+ * workspace: at least gbd_dgemm_emu_mod_workspace_size(m, n, k, bits) bytes, 256-byte
+ *   aligned (bits = 0 sizes it for 16 moduli); as for gbd_dgemm_emu.
+ * info: optional; slices and products report n, digit_bits reports t.
+ * Returns 0, a BLAS argument index, or GBD_ERR_*.
+ */
+GBD_API size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits);
+/*
+ * The moduli gbd_dgemm_emu_mod uses for t = bits integer bits at inner dimension k (host
+ * only): writes them to moduli[0..n) when moduli is not NULL (room for 16) and returns n,
+ * or 0 when 16 moduli are not enough (or bits < 1, k < 1).
+ */
+GBD_API int gbd_dgemm_emu_mod_moduli(int bits, int64_t k, int* moduli);
+GBD_API int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                              const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                              double* C, int64_t ldc, int bits, double tol, void* workspace,
+                              size_t workspace_bytes, gbd_emu_info* info, void* stream);
+
+/*
  * gbd_dgemm_emu with A, B and C in HOST memory.  The paper's dgemm works on
  * operands in the caller's memory (Section 1.2); this entry point gives that
  * interface to a caller whose matrices are on the host, with the GPU transfers

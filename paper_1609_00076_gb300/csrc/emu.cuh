@@ -102,6 +102,23 @@ void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks);
 int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s);
 int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
+
+// ---- modular emulation (Ozaki scheme II) ----
+constexpr int kMaxModuli = 16;  // the product of the moduli stays below 2^126
+// pairwise coprime moduli up to 256 (greedily from 256 down), so that every symmetric
+// residue is at most 128 in magnitude: exact in BF16, products at most 2^14
+constexpr int kModuli[kMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
+                                     229, 227, 223, 217, 211, 199, 197, 193};
+// residue split parameters: t integer bits (<= 62), the first n moduli, 1/p, and 256^d mod p
+// for d = 0..3 (wlo) and 4..7 (whi) packed one byte per d
+struct ModSplit {
+  int n, t;
+  int p[kMaxModuli];
+  float inv[kMaxModuli];
+  uint32_t wlo[kMaxModuli], whi[kMaxModuli];
+};
+// residue slices D[i][r][kp] of both sides (slices = n) from the rounded scaled integers
+int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_blocks, cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
 int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
                         bool exponents, bool split, cudaStream_t s);

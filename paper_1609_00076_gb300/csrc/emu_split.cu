@@ -265,10 +265,102 @@ __device__ __forceinline__ void write_digits(const uint64_t (&x)[kPerThread], in
 // k contiguous in memory: each thread reads its 8 values directly (vector loads when
 // 16-byte aligned), a warp sweeps 2 KiB of one row.  Rows contiguous: the tile is
 // transposed through shared memory.
-template <bool ROWS_CONTIG>
+// the digits of the split emulation (writer of split_body)
+struct DigitWriter {
+  int slices;
+  int64_t R, K;
+  uint16_t* D;
+  int64_t kp;
+  __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
+                                             int64_t pbase) const {
+    write_digits(x, sg, slices, R, K, r, pbase, D, kp);
+  }
+};
+
+// rint(x 2^(t - sigma)) of a double given by its bits, ties to even, from integer operations
+// (|x| < 2^sigma keeps the result within 2^t); 0 for a non-finite x (its row is flagged)
+__device__ __forceinline__ int64_t rounded_scaled(uint64_t bits, int sigma, int t) {
+  const uint32_t E = (uint32_t)(bits >> 52) & 0x7FFu;
+  if (E == 0x7FFu) return 0;
+  uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+  int e2;  // |x| = mant * 2^e2
+  if (E) {
+    mant |= 1ull << 52;
+    e2 = (int)E - 1075;
+  } else {
+    e2 = -1074;
+  }
+  const int sh = e2 - sigma + t;
+  uint64_t q;
+  if (sh >= 0) {
+    q = mant << sh;
+  } else if (-sh >= 64) {
+    q = 0;  // below a quarter of a unit
+  } else {
+    const int s = -sh;
+    q = mant >> s;
+    const uint64_t rem = mant & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (bits >> 63) ? -(int64_t)q : (int64_t)q;
+}
+
+// the residues of the modular emulation (writer of split_body): for each modulus p, the
+// symmetric residue of A' = rint(x 2^(t - sigma)) as a BF16 value (|residue| <= 128)
+struct ResidueWriter {
+  const ModSplit* mp;  // in the kernel's parameter space
+  int64_t R, K;
+  uint16_t* D;
+  int64_t kp;
+  __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
+                                             int64_t pbase) const {
+    uint32_t lo[kPerThread], hi[kPerThread];  // the bytes of |A'|: 0..3 and 4..7
+    uint32_t neg = 0;
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) {
+      const int64_t q = rounded_scaled(x[v], sg, mp->t);
+      const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
+      lo[v] = (uint32_t)a;
+      hi[v] = (uint32_t)(a >> 32);
+      neg |= (uint32_t)(q < 0) << v;
+    }
+    const bool full = pbase + kPerThread <= K;
+    for (int i = 0; i < mp->n; ++i) {
+      const int p = mp->p[i];
+      const float inv = mp->inv[i];
+      const uint32_t wl = mp->wlo[i], wh = mp->whi[i];  // 256^d mod p, one byte per d
+      uint32_t packed[kPerThread / 2];
+#pragma unroll
+      for (int v = 0; v < kPerThread; v += 2) {
+        int res[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          // |A'| mod p = (sum_d byte_d (256^d mod p)) mod p; the sum is below 2^20
+          const uint32_t sum = __dp4a(lo[v + u], wl, 0u) + __dp4a(hi[v + u], wh, 0u);
+          int rr = (int)sum - p * (int)floorf((float)sum * inv);
+          rr += rr < 0 ? p : 0;
+          rr -= rr >= p ? p : 0;
+          if (2 * rr >= p) rr -= p;       // symmetric: [-p/2, p/2)
+          if ((neg >> (v + u)) & 1u) rr = -rr;
+          res[u] = rr;
+        }
+        packed[v / 2] = bf16_of_digit(res[0]) | (bf16_of_digit(res[1]) << 16);
+      }
+      uint16_t* row = D + ((int64_t)i * R + r) * kp + pbase;
+      if (full) {
+        *reinterpret_cast<uint4*>(row) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      } else {
+        for (int v = 0; v < kPerThread && pbase + v < K; ++v)
+          row[v] = (uint16_t)((packed[v / 2] >> (16 * (v & 1))) & 0xFFFFu);
+      }
+    }
+  }
+};
+
+template <bool ROWS_CONTIG, class Writer>
 __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
-                                           const int* __restrict__ sig, int slices, uint16_t* __restrict__ D,
-                                           int64_t kp, int64_t bx, int64_t by, uint64_t (*tile)[kTile + 1]) {
+                                           const int* __restrict__ sig, int64_t bx, int64_t by,
+                                           uint64_t (*tile)[kTile + 1], const Writer& write) {
   const int64_t p0 = bx * kTile, r0 = by * kTile;
   const int tid = threadIdx.x;
   const int rr = tid >> 3, pp0 = (tid & 7) * kPerThread;
@@ -307,7 +399,7 @@ __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t
     }
   }
   const int sg = sig[r] == kExpEmpty ? 0 : sig[r];
-  write_digits(x, sg, slices, R, K, r, pbase, D, kp);
+  write(x, sg, r, pbase);
 }
 
 // ---- batched forms over a job table (one operand side of one problem per job) ----
@@ -367,8 +459,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
   const PrepJob& j = jobs[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
-  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
+  const DigitWriter w{j.slices, j.R, j.K, j.D, j.kp};
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
 // ---- both operand sides of one problem in one launch (single calls) ----
@@ -414,8 +507,21 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_pair(const __grid_const
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
-  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.slices, j.D, j.kp, bx, by, tile);
+  const DigitWriter w{j.slices, j.R, j.K, j.D, j.kp};
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_residue_pair(const __grid_constant__ PrepPair pp,
+                                                                const __grid_constant__ ModSplit mp) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  const ResidueWriter w{&mp, j.R, j.K, j.D, j.kp};
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
 int launch_check(const char* what) {
@@ -568,6 +674,13 @@ int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t 
   if (exp_blocks <= 0) return GBD_OK;
   k_magnitudes_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, pp.j[0].K <= kRedChunk);
   return launch_check("magnitude launch");
+}
+
+int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_blocks, cudaStream_t s) {
+  if (split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
+  k_residue_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, mp);
+  return launch_check("residue launch");
 }
 
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s) {

@@ -104,6 +104,10 @@ _EXTRA_DECLS: list = [
                        ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_noalloc", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d,
                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_dgemm_emu_mod_workspace_size", [_i64, _i64, _i64, _i], _sz),
+    ("gbd_dgemm_emu_mod_moduli", [_i, _i64, ctypes.POINTER(ctypes.c_int)], _i),
+    ("gbd_dgemm_emu_mod", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
+                           ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_host_buffer_size", [_c, _c, _i64, _i64, _i64, _i], _sz),
     ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                             ctypes.POINTER(GbdEmuInfo), _vp], _i),
@@ -197,6 +201,29 @@ def gbd_dgemm_emu_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, 
     return load().gbd_dgemm_emu_noalloc(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
                                         int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
                                         float(tol), ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_dgemm_emu_mod_workspace_size(m, n, k, bits=0) -> int:
+    """Device workspace bytes of gbd_dgemm_emu_mod (bits 0 = automatic, sized for 16 moduli)."""
+    return int(load().gbd_dgemm_emu_mod_workspace_size(int(m), int(n), int(k), int(bits)))
+
+
+def gbd_dgemm_emu_mod_moduli(bits, k) -> list:
+    """The moduli of the modular emulation for `bits` integer bits at inner dimension k ([] if 16
+    are not enough)."""
+    out = (ctypes.c_int * 16)()
+    n = int(load().gbd_dgemm_emu_mod_moduli(int(bits), int(k), out))
+    return [int(out[i]) for i in range(n)]
+
+
+def gbd_dgemm_emu_mod(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bits, tol, workspace,
+                      workspace_bytes, info=None, stream=None) -> int:
+    """C := alpha*op(A)*op(B) + beta*C by the modular emulation (residue products and the Chinese
+    remainder theorem) on the BF16 tensor cores; returns the status."""
+    return load().gbd_dgemm_emu_mod(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                                    int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(bits),
+                                    float(tol), _addr(workspace), int(workspace_bytes),
+                                    ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
 def gbd_dgemm_emu_host_buffer_size(transa, transb, m, n, k, slices=0) -> int:

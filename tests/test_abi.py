@@ -105,3 +105,39 @@ def test_request_stream_is_seeded_and_poisson():
     emu = sum(r.mode == serving.EMULATED for r in a) / len(a)
     assert 0.07 < big < 0.13 and 0.45 < emu < 0.55
     assert all(32 <= r.m <= 4096 and 32 <= r.k <= 4096 for r in a)
+
+
+def test_emu_mod_moduli_are_coprime_minimal_and_enough(lib):
+    import math
+    all16 = gbdgemm.gbd_dgemm_emu_mod_moduli(62, 1)  # 2 2^124 = 2^125 needs all of them
+    assert len(all16) == 16 and 2 ** 125 < math.prod(all16) < 2 ** 126
+    assert all(2 <= p <= 256 for p in all16)  # symmetric residues within 128: exact in BF16
+    assert all(math.gcd(a, b) == 1 for i, a in enumerate(all16) for b in all16[i + 1:])
+    for k in (1, 2, 3, 1000, 8192, 65537, 2 ** 31 - 1):
+        for t in range(1, 63):
+            mods = gbdgemm.gbd_dgemm_emu_mod_moduli(t, k)
+            need = 2 * k * 2 ** (2 * t)  # 2 max |A'B'| for |A'|, |B'| <= 2^t
+            if not mods:
+                assert math.prod(all16) <= need, (t, k)
+                continue
+            assert mods == all16[:len(mods)]
+            assert math.prod(mods) > need and math.prod(mods[:-1]) <= need, (t, k)
+    assert len(gbdgemm.gbd_dgemm_emu_mod_moduli(44, 8192)) == 13  # 2 8192 2^88 = 2^102
+    assert gbdgemm.gbd_dgemm_emu_mod_moduli(0, 10) == [] and gbdgemm.gbd_dgemm_emu_mod_moduli(10, 0) == []
+
+
+def test_emu_mod_workspace_and_argument_codes_without_gpu(lib):
+    import numpy as np
+    few = gbdgemm.gbd_dgemm_emu_mod_workspace_size(100, 200, 300, 10)
+    auto = gbdgemm.gbd_dgemm_emu_mod_workspace_size(100, 200, 300, 0)
+    n10 = len(gbdgemm.gbd_dgemm_emu_mod_moduli(10, 300))
+    # residues of both sides (2 bytes, k padded to 8) and one byte per result element, per modulus
+    assert few >= n10 * (2 * 304 * (100 + 200) + 100 * 200)
+    assert few < auto and gbdgemm.gbd_dgemm_emu_mod_workspace_size(-1, 2, 3, 0) == 0
+    a = np.zeros(4)
+    call = gbdgemm.gbd_dgemm_emu_mod
+    assert call("X", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 1
+    assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 1, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 10
+    assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 63, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
+    assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, -1, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
+    assert call("N", "N", 2, 0, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 0
