@@ -4,14 +4,15 @@
 //
 //   1. sigma_i, tau_j: the row and column exponents of the split emulation (emu_split.cu).
 //   2. A' = rint(a 2^(t - sigma_i)), B' = rint(b 2^(t - tau_j)) (integers, |.| <= 2^t), and
-//      their symmetric residues modulo n pairwise coprime moduli p_l <= 256, written as BF16
-//      slices (emu_split.cu, k_residue_pair).
+//      their residues modulo n pairwise coprime moduli p_l <= 256, written as BF16 slices
+//      (emu_split.cu, k_residue_pair).
 //   3. For every modulus: the residue product on tcgen05.mma with 1024-deep exact FP32
-//      chunks drained into int32, reduced modulo p_l; the epilogue stores one byte per
-//      element, u_l = (residue x c_l) mod p_l with c_l = (M/p_l)^-1 mod p_l.
-//   4. k_crt: C' = sum_l u_l (M/p_l) mod M, the unique integer of (-M/2, M/2] congruent to
-//      the products; it equals A'B' because M > 2 k 2^(2t) >= 2 max|A'B'|.  Then
-//      C := fma(alpha 2^(tau_j - 2t), fl(C') 2^sigma_i, beta C0), fl correctly rounded.
+//      chunks drained into int32, reduced modulo p_l; the epilogue parks one byte per
+//      element, u_l = (residue x c_l) mod p_l with c_l = (M/p_l)^-1 mod p_l, in a per-CTA slot.
+//   4. In the same epilogue, while the next tile's products run: C' = sum_l u_l (M/p_l) mod M,
+//      the unique integer of (-M/2, M/2] congruent to the products; it equals A'B' because
+//      M > 2 k 2^(2t) >= 2 max|A'B'|.  Then C := fma(alpha 2^(tau_j - 2t), fl(C') 2^sigma_i,
+//      beta C0), fl correctly rounded.
 // There is no FP64 arithmetic in the products: n GEMMs replace the s(s+1)/2 of the split
 // emulation.  All waits are bounded (2 s) and set the device error word when they give up.
 #include <cstdint>
@@ -27,13 +28,247 @@ namespace {
 
 using namespace tc;
 
+constexpr int kReduceChunks = 63;  // 63 chunks of 1024 k (each below 2^24) plus a residue stay below 2^30
+// parked residue bytes: per CTA two slots (the tile being multiplied and the one being
+// reconstructed) of [modulus][column / 4][128 rows][4 columns] bytes, sized for the widest tile:
+// a thread moves four columns in one 32-bit word and a warp 128 contiguous bytes
+constexpr int kSlotCols = 256;
+constexpr int64_t kLStride = (int64_t)kSlotCols * 128;
+constexpr int64_t kSlotBytes = (int64_t)kMaxModuli * kLStride;
+constexpr int kMaxModCtas = 256;
+
+struct ModArgs {
+  int64_t m, n, ldc;
+  int nkb, nmod;
+  int tiles_m, num_tiles, group_m;
+  int p[kMaxModuli];            // moduli
+  int c[kMaxModuli];            // (M/p_l)^-1 mod p_l
+  uint32_t bar[kMaxModuli];     // floor(2^32 / p_l), for Barrett reduction
+  uint32_t rq[kMaxModuli];      // ceil(2^24 / p_l)
+  uint32_t mpl[kMaxModuli][4];  // M/p_l in 32-bit limbs, least significant first
+  uint64_t M_lo, M_hi, half_lo, half_hi;  // M and floor(M/2)
+  double beta;
+  double* C;
+  const int* sigA;
+  const int* badA;
+  const double* cs;  // [n] alpha 2^(tau_j - 2t); NaN for a column with a non-finite entry
+  uint8_t* scr;      // [CTA][2][kMaxModuli][kSlotCols / 4][128][4] parked u_l
+  unsigned int* err;
+};
+
+// x mod p for 0 <= x < 2^32 (Barrett: with b = floor(2^32/p), floor(x b / 2^32) is floor(x/p) or
+// one less)
+__device__ __forceinline__ uint32_t mod_barrett(uint32_t x, uint32_t p, uint32_t b) {
+  uint32_t r = x - __umulhi(x, b) * p;
+  return r >= p ? r - p : r;
+}
+// v mod p in [0, p) for |v| < 2^30 (shifted by p 2^23, which lies in [2^30, 2^31], into [0, 2^32))
+__device__ __forceinline__ int mod_nonneg(int v, uint32_t p, uint32_t b) {
+  return (int)mod_barrett((uint32_t)v + (p << 23), p, b);
+}
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 make_u128(uint64_t hi, uint64_t lo) { return ((u128)hi << 64) | lo; }
+
+// C' from its parked bytes u_l = (C' mod p_l) c_l mod p_l: sum_l u_l (M/p_l) = (C' mod M) + q M
+// with q = floor(sum_l u_l / p_l).  Returns the representative of (-M/2, M/2] in two's
+// complement 128 bits.
+__device__ __forceinline__ u128 crt_combine(const uint32_t (&u)[kMaxModuli], const ModArgs& p) {
+  uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // limb sums, each below 16 * 255 * 2^32 < 2^44
+  uint32_t qfix = 0;                         // sum_l u_l ceil(2^24/p_l) < 2^29
+#pragma unroll
+  for (int l = 0; l < kMaxModuli; ++l) {
+    if (l < p.nmod) {
+      a0 += (uint64_t)u[l] * p.mpl[l][0];
+      a1 += (uint64_t)u[l] * p.mpl[l][1];
+      a2 += (uint64_t)u[l] * p.mpl[l][2];
+      a3 += (uint64_t)u[l] * p.mpl[l][3];
+      qfix += u[l] * p.rq[l];
+    }
+  }
+  const u128 s = (u128)a0 + ((u128)a1 << 32) + ((u128)a2 << 64) + ((u128)a3 << 96);  // modulo 2^128
+  // qfix / 2^24 exceeds sum_l u_l/p_l by less than 16 * 255 / 2^24, so its floor is q or q + 1
+  const u128 M = make_u128(p.M_hi, p.M_lo);
+  u128 cu = s - (u128)(qfix >> 24) * M;
+  if ((uint64_t)(cu >> 127)) cu += M;  // the estimate was one too large
+  else if (cu >= M) cu -= M;
+  const u128 half = make_u128(p.half_hi, p.half_lo);
+  return cu > half ? cu - M : cu;
+}
+
+// fl(v) 2^sig for a two's complement 128-bit v: fl rounds to nearest (ties to even); the
+// scaling rounds again only where the result leaves the normal range (as ldexp).  The common
+// case builds the double from integers.
+__device__ __forceinline__ double scaled_double(u128 v, int sig) {
+  const bool neg = (uint64_t)(v >> 127) != 0;
+  const u128 a = neg ? (u128)0 - v : v;
+  const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
+  if ((hi | lo) == 0ull) return 0.0;
+  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  uint64_t mant = lo;
+  int e = 0;
+  if (nbits > 53) {
+    const int shift = nbits - 53;
+    mant = (uint64_t)(a >> shift);
+    const u128 rem = a & (((u128)1 << shift) - 1), hf = (u128)1 << (shift - 1);
+    e = shift;
+    if (rem > hf || (rem == hf && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++e;
+      }
+    }
+  }
+  // |v| rounded = mant 2^e with mant < 2^53
+  const int L = 64 - __clzll((long long)mant);
+  const int E = e + sig + L - 1;  // exponent of the scaled value
+  if (E >= -1022 && E <= 1023) {
+    const uint64_t bits = ((uint64_t)(E + 1023) << 52) | ((mant << (53 - L)) & 0xFFFFFFFFFFFFFull) |
+                          (neg ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
+  }
+  const double y = ldexp(ldexp((double)mant, e), sig);  // the first ldexp is exact
+  return neg ? -y : y;
+}
+
+// The epilogue of both product kernels.  Each thread owns one TMEM lane (a row of the CTA's
+// 128) and COLS columns of the TBN-wide tile.  Per modulus: drain the chunks into int32 sums,
+// park u_l; at each modulus boundary (sums dead), reconstruct a few groups of four columns of
+// the previous tile from its parked bytes and write them to C.  All loads of a group are
+// issued before its arithmetic, so a group waits for memory once.
+template <int EPI_WARPS, int TBN, bool PAIR>
+__device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_base, uint64_t* acc_full,
+                                             uint64_t* acc_empty, int warp, int lane, int tile0, int tile_step,
+                                             int tbm, int row_off) {
+  constexpr int COLS = TBN / (EPI_WARPS / 4);
+  const int ew = warp - 2;
+  const int quad = warp & 3;
+  const int part = ew >> 2;
+  const int row = quad * 32 + lane;
+  const int col0 = part * COLS;
+  const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
+  uint32_t empty_remote[2] = {0u, 0u};
+  if (PAIR) {
+    empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
+    empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
+  }
+  uint8_t* const scr_cta = p.scr + (int64_t)blockIdx.x * 2 * kSlotBytes + (int64_t)(col0 / 4) * 512 + row * 4;
+  constexpr int kGroups = COLS / 4;
+  const int per_boundary = (kGroups + p.nmod - 1) / p.nmod;  // groups of four columns
+
+  // the pending reconstruction: this thread's row and columns of the previous tile
+  bool pd_active = false, pd_bad = false;
+  int pd_done = 0, pd_slot = 0, pd_sig = 0, pd_cols = 0;
+  double* pd_c = nullptr;
+  const double* pd_cs = nullptr;
+  auto advance = [&](int ngroups) {
+    const int g1 = min(pd_done + ngroups, kGroups);
+    const uint8_t* ub = scr_cta + (int64_t)pd_slot * kSlotBytes;
+    for (int g = pd_done; g < g1; ++g) {
+      const int c0 = 4 * g;
+      if (c0 >= pd_cols) break;
+      uint32_t w4[kMaxModuli];  // the bytes of columns c0..c0+3, one word per modulus
+#pragma unroll
+      for (int l = 0; l < kMaxModuli; ++l)
+        w4[l] = l < p.nmod ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
+      double c0v[4], csv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool in = c0 + q < pd_cols;
+        c0v[q] = (in && p.beta != 0.0) ? pd_c[(int64_t)(c0 + q) * p.ldc] : 0.0;
+        csv[q] = in ? pd_cs[c0 + q] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (c0 + q >= pd_cols) break;
+        uint32_t u[kMaxModuli];
+#pragma unroll
+        for (int l = 0; l < kMaxModuli; ++l) u[l] = (w4[l] >> (8 * q)) & 0xFFu;
+        const double w0 = p.beta != 0.0 ? p.beta * c0v[q] : 0.0;
+        double w;
+        if (pd_bad || csv[q] != csv[q]) w = __longlong_as_double(0x7FF8000000000000ll);
+        else w = fma(csv[q], scaled_double(crt_combine(u, p), pd_sig), w0);
+        pd_c[(int64_t)(c0 + q) * p.ldc] = w;
+      }
+    }
+    pd_done = g1;
+    if (pd_done >= kGroups) pd_active = false;
+  };
+
+  uint32_t chunk = 0;
+  int acc[COLS];
+  int tcount = 0;
+  for (int tile = tile0; tile < p.num_tiles; tile += tile_step, ++tcount) {
+    int tm, tn;
+    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    const int64_t i = (int64_t)tm * tbm + row_off + row;
+    const int64_t jc0 = (int64_t)tn * TBN + col0;
+    const int slot = tcount & 1;
+    uint8_t* const ub = scr_cta + (int64_t)slot * kSlotBytes;
+    for (int l = 0; l < p.nmod; ++l) {
+      const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) acc[c] = 0;
+      int nch = 0;
+      for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+        const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+        mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+        tc_fence_after();
+        const uint32_t taddr = trow + buf * TBN + col0;
+#pragma unroll
+        for (int q = 0; q < COLS / 16; ++q) {
+          uint32_t v[16];
+          tmem_ld_16(taddr + q * 16, v);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
+        }
+        tc_fence_before();
+        if (PAIR) mbar_arrive_remote(empty_remote[buf]);
+        else mbar_arrive(&acc_empty[buf]);
+        if (++nch == kReduceChunks) {  // keep the running sums below 2^30 in magnitude
+          nch = 0;
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
+        }
+      }
+      const uint32_t cl = (uint32_t)p.c[l];
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        uint32_t w = 0u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          w |= mod_barrett((uint32_t)mod_nonneg(acc[4 * g + b], pm, bm) * cl, pm, bm) << (8 * b);
+        *reinterpret_cast<uint32_t*>(ub + l * kLStride + g * 512) = w;
+      }
+      if (pd_active) advance(l + 1 == p.nmod ? kGroups : per_boundary);
+    }
+    // this tile's residues are complete: it becomes the pending reconstruction
+    const bool row_ok = i < p.m;
+    pd_active = true;
+    pd_done = 0;
+    pd_slot = slot;
+    pd_cols = row_ok && jc0 < p.n ? (int)min((int64_t)COLS, p.n - jc0) : 0;
+    pd_sig = 0;
+    pd_bad = false;
+    if (row_ok) {
+      const int sg = p.sigA[i];
+      pd_sig = sg == kExpEmpty ? 0 : sg;
+      pd_bad = p.badA[i] != 0;
+    }
+    pd_c = p.C + jc0 * p.ldc + i;  // dereferenced only for the pd_cols columns inside C
+    pd_cs = p.cs + jc0;
+  }
+  if (pd_active) advance(kGroups);
+}
+
+// ---- the one-SM form: 128 x 128 tiles ----
 constexpr int kBM = 128, kBN = 128;
 constexpr int kStages = 6;
 constexpr int kEpiWarps = 16;  // 4 x 4 warps over 128 TMEM lanes x 128 columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kCols = kBN / (kEpiWarps / 4);  // columns per epilogue thread
-constexpr int kTmemCols = 2 * kBN;             // two accumulators
-constexpr int kReduceChunks = 64;              // int32 stays exact for 64 chunks of 1024 k
+constexpr int kTmemCols = 2 * kBN;  // two accumulators
 
 struct Smem {
   static constexpr int kABytes = kBM * kBK * 2;
@@ -48,24 +283,9 @@ struct Smem {
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
 
-struct ModArgs {
-  int64_t m, n;
-  int nkb, nmod;
-  int tiles_m, num_tiles, group_m;
-  int p[kMaxModuli];  // moduli
-  int c[kMaxModuli];  // (M/p_l)^-1 mod p_l
-  uint8_t* U;         // [nmod][n][m] bytes u_l
-  unsigned int* err;
-};
-
-// v mod p in [0, p) for a 32-bit integer of either sign
-__device__ __forceinline__ int mod_nonneg(int v, int p) {
-  int r = v % p;
-  return r < 0 ? r + p : r;
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
-    k_mod_gemm(const ModArgs p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    k_mod_gemm(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
+               const __grid_constant__ CUtensorMap tmB) {
   using L = Smem;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -154,56 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // ------------------------------ epilogue ----------------------------------
-    // each modulus: exact int32 sums of the drained chunks, then one residue byte
-    const int ew = warp - 2;
-    const int quad = warp & 3;
-    const int part = ew >> 2;
-    const int row = quad * 32 + lane;
-    const int col0 = part * kCols;
-    const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const int64_t plane = p.m * p.n;
-    uint32_t chunk = 0;
-    int acc[kCols];
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-      int tm, tn;
-      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-      const int64_t i = (int64_t)tm * kBM + row;
-      const int64_t jc0 = (int64_t)tn * kBN + col0;
-      for (int l = 0; l < p.nmod; ++l) {
-        const int pm = p.p[l];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[c] = 0;
-        int nch = 0;
-        for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
-          const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-          mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
-          tc_fence_after();
-          const uint32_t taddr = trow + buf * kBN + col0;
-#pragma unroll
-          for (int q = 0; q < kCols / 16; ++q) {
-            uint32_t v[16];
-            tmem_ld_16(taddr + q * 16, v);
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
-          }
-          tc_fence_before();
-          mbar_arrive(&acc_empty[buf]);
-          if (++nch == kReduceChunks) {  // keep the running sums inside int32
-            nch = 0;
-#pragma unroll
-            for (int c = 0; c < kCols; ++c) acc[c] = mod_nonneg(acc[c], pm);
-          }
-        }
-        const int cl = p.c[l];
-        uint8_t* u = p.U + (int64_t)l * plane + jc0 * p.m + i;
-        if (i < p.m) {
-#pragma unroll
-          for (int c = 0; c < kCols; ++c)
-            if (jc0 + c < p.n) u[(int64_t)c * p.m] = (uint8_t)((mod_nonneg(acc[c], pm) * cl) % pm);
-        }
-      }
-    }
+    mod_epilogue<kEpiWarps, kBN, false>(p, tmem_base, acc_full, acc_empty, warp, lane, blockIdx.x, gridDim.x, kBM,
+                                        0);
   }
 
   tc_fence_before();
@@ -223,8 +395,8 @@ constexpr int k2BM = 256, k2BN = 256;
 constexpr int k2Stages = 6;
 constexpr int k2EpiWarps = 16;  // 4 x 4 warps over 128 TMEM lanes x 256 columns
 constexpr int k2Threads = 64 + 32 * k2EpiWarps;
-constexpr int k2Cols = k2BN / (k2EpiWarps / 4);
 constexpr int k2TmemCols = 2 * k2BN;
+static_assert(k2BN <= kSlotCols && kBN <= kSlotCols, "parked bytes of a tile fit one slot");
 
 struct Smem2 {
   static constexpr int kABytes = 128 * kBK * 2;
@@ -240,7 +412,7 @@ struct Smem2 {
 };
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
-    k_mod_gemm_pair(const ModArgs p, const __grid_constant__ CUtensorMap tmA,
+    k_mod_gemm_pair(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB) {
   using L = Smem2;
   extern __shared__ uint8_t smem_raw[];
@@ -337,58 +509,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     __syncwarp();
   } else {
-    // ------------------------------ epilogue (both CTAs) ------------------------------
-    const int ew = warp - 2;
-    const int quad = warp & 3;
-    const int part = ew >> 2;
-    const int row = quad * 32 + lane;
-    const int col0 = part * k2Cols;
-    const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const int64_t plane = p.m * p.n;
-    uint32_t empty_remote[2];
-    empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
-    empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
-    uint32_t chunk = 0;
-    int acc[k2Cols];
-    for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
-      int tm, tn;
-      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-      const int64_t i = (int64_t)tm * k2BM + rank * 128 + row;
-      const int64_t jc0 = (int64_t)tn * k2BN + col0;
-      for (int l = 0; l < p.nmod; ++l) {
-        const int pm = p.p[l];
-#pragma unroll
-        for (int c = 0; c < k2Cols; ++c) acc[c] = 0;
-        int nch = 0;
-        for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
-          const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-          mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
-          tc_fence_after();
-          const uint32_t taddr = trow + buf * k2BN + col0;
-#pragma unroll
-          for (int q = 0; q < k2Cols / 16; ++q) {
-            uint32_t v[16];
-            tmem_ld_16(taddr + q * 16, v);
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
-          }
-          tc_fence_before();
-          mbar_arrive_remote(empty_remote[buf]);
-          if (++nch == kReduceChunks) {  // keep the running sums inside int32
-            nch = 0;
-#pragma unroll
-            for (int c = 0; c < k2Cols; ++c) acc[c] = mod_nonneg(acc[c], pm);
-          }
-        }
-        const int cl = p.c[l];
-        uint8_t* u = p.U + (int64_t)l * plane + jc0 * p.m + i;
-        if (i < p.m) {
-#pragma unroll
-          for (int c = 0; c < k2Cols; ++c)
-            if (jc0 + c < p.n) u[(int64_t)c * p.m] = (uint8_t)((mod_nonneg(acc[c], pm) * cl) % pm);
-        }
-      }
-    }
+    mod_epilogue<k2EpiWarps, k2BN, true>(p, tmem_base, acc_full, acc_empty, warp, lane, pair_id, num_pairs, k2BM,
+                                         (int)rank * 128);
   }
 
   tc_fence_before();
@@ -401,80 +523,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
   }
 }
 
-// ---- Chinese remainder reconstruction and the FP64 result ----
-struct CrtArgs {
-  int64_t m, n, ldc;
-  int nmod, t;
-  uint64_t mp_lo[kMaxModuli], mp_hi[kMaxModuli];  // M / p_l
-  float inv[kMaxModuli];                          // 1 / p_l
-  uint64_t M_lo, M_hi, half_lo, half_hi;          // M and floor(M/2)
-  double alpha, beta;
-  double* C;
-  const int* sigA;
-  const int* sigB;
-  const int* badA;
-  const int* badB;
-  const uint8_t* U;
-};
-
-typedef unsigned __int128 u128;
-
-__device__ __forceinline__ u128 make_u128(uint64_t hi, uint64_t lo) { return ((u128)hi << 64) | lo; }
-
-// a 128-bit integer of either sign as the nearest double (ties to even)
-__device__ __forceinline__ double i128_to_double(u128 v) {
-  const bool neg = (uint64_t)(v >> 127) != 0;
-  const u128 a = neg ? (u128)0 - v : v;
-  const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
-  if (hi == 0 && lo < (1ull << 53)) {
-    const double d = (double)lo;
-    return neg ? -d : d;
-  }
-  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-  const int shift = nbits - 53;  // >= 1
-  uint64_t mant = (uint64_t)(a >> shift);
-  const u128 rem = a & (((u128)1 << shift) - 1), half = (u128)1 << (shift - 1);
-  int e = shift;
-  if (rem > half || (rem == half && (mant & 1ull))) {
-    ++mant;
-    if (mant == (1ull << 53)) {
-      mant >>= 1;
-      ++e;
-    }
-  }
-  const double d = ldexp((double)mant, e);  // mant < 2^53, e < 128: exact
-  return neg ? -d : d;
-}
-
-__global__ void __launch_bounds__(256) k_crt(const __grid_constant__ CrtArgs a) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= a.m) return;
-  const int sig = a.sigA[row] == kExpEmpty ? 0 : a.sigA[row];
-  const bool bad_r = a.badA[row] != 0;
-  const u128 M = make_u128(a.M_hi, a.M_lo), half = make_u128(a.half_hi, a.half_lo);
-  const int64_t plane = a.m * a.n;
-  for (int64_t col = blockIdx.y; col < a.n; col += gridDim.y) {
-    const int64_t e = col * a.m + row;
-    u128 s = 0;
-    float qf = 0.0f;
-    for (int l = 0; l < a.nmod; ++l) {
-      const uint32_t u = a.U[(int64_t)l * plane + e];
-      s += (u128)u * make_u128(a.mp_hi[l], a.mp_lo[l]);  // modulo 2^128
-      qf += (float)u * a.inv[l];
-    }
-    // sum_l u_l (M/p_l) = C'_u + q M with q = floor(sum_l u_l/p_l); the float estimate of q
-    // is off by at most one, which the range of the difference reveals
-    u128 cu = s - (u128)(uint64_t)floorf(qf) * M;
-    if ((uint64_t)(cu >> 127)) cu += M;  // q was one too large
-    else if (cu >= M) cu -= M;           // one too small
-    const u128 v = cu > half ? cu - M : cu;  // the symmetric representative
-    const double x = i128_to_double(v);
-    const int tau = a.sigB[col] == kExpEmpty ? 0 : a.sigB[col];
-    double w = a.beta != 0.0 ? a.beta * a.C[col * a.ldc + row] : 0.0;
-    if (bad_r || a.badB[col]) w = __longlong_as_double(0x7FF8000000000000ll);
-    else w = fma(ldexp(a.alpha, tau - 2 * a.t), ldexp(x, sig), w);
-    a.C[col * a.ldc + row] = w;
-  }
+// alpha 2^(tau_j - 2t) for every column (NaN for a column with a non-finite entry)
+__global__ void __launch_bounds__(256) k_mod_colscale(const int* __restrict__ sigB, const int* __restrict__ badB,
+                                                      int64_t n, double alpha, int t, double* __restrict__ cs) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int tau = sigB[j] == kExpEmpty ? 0 : sigB[j];
+  cs[j] = badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(alpha, tau - 2 * t);
 }
 
 // ---- host side ----
@@ -486,15 +541,22 @@ struct ModWorkspace {
   unsigned long long* muA;
   unsigned long long* muB;
   float* stats;
+  double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
   uint16_t* DB;  // [nmod][n][kp]
-  uint8_t* U;    // [nmod][n][m]
+  uint8_t* scr;  // [scr_ctas][2][kSlotBytes]
+  int scr_ctas;
   int64_t kp;
 };
 
 size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWorkspace* ws) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int64_t kp = (k + 7) / 8 * 8;
+  // one CTA per 128 x 128 tile (one-SM form) or two per 256 x 256 tile (two-SM form), at most kMaxModCtas
+  const int64_t tiles1 = ((m + 127) / 128) * ((n + 127) / 128);
+  const int64_t tiles2 = ((m + 255) / 256) * ((n + 255) / 256);
+  int64_t ctas = tiles1 > 2 * tiles2 ? tiles1 : 2 * tiles2;
+  if (ctas > kMaxModCtas) ctas = kMaxModCtas;
   size_t off = 0;
   const size_t o_sigA = off; off = up(off + sizeof(int) * (size_t)m);
   const size_t o_sigB = off; off = up(off + sizeof(int) * (size_t)n);
@@ -503,9 +565,10 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_muA = off; off = up(off + sizeof(unsigned long long) * (size_t)m);
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
+  const size_t o_cs = off; off = up(off + sizeof(double) * (size_t)n);
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
-  const size_t o_U = off; off = up(off + (size_t)nmod * (size_t)m * (size_t)n);
+  const size_t o_scr = off; off = up(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -515,9 +578,11 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->muA = reinterpret_cast<unsigned long long*>(b + o_muA);
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
+    ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
-    ws->U = reinterpret_cast<uint8_t*>(b + o_U);
+    ws->scr = reinterpret_cast<uint8_t*>(b + o_scr);
+    ws->scr_ctas = (int)ctas;
     ws->kp = kp;
   }
   return off;
@@ -577,48 +642,40 @@ int choose_bits(double tol, double mu_min, double nu_min, int64_t k, double* bou
 // Relative throughput per SM of the two-SM form over the one-SM form when both fill the GPU
 constexpr double kModPairGain = 1.2;
 
-int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod, const int* pc, const ModWorkspace& ws, int sms,
+// the product kernel of one call; `a` carries everything but the tile geometry
+int launch_mod_gemm(int64_t m, int64_t n, int64_t k, ModArgs& a, const ModWorkspace& ws, int sms,
                     cudaStream_t stream) {
   // GBD_EMU_KERNEL=pair|single overrides the choice (tests and tuning).  Otherwise the expected
   // time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs (or SM
   // pairs), a 256 x 256 tile being four units on two SMs at kModPairGain.
   const char* force = getenv("GBD_EMU_KERNEL");
+  const int cta_cap = sms < ws.scr_ctas ? sms : ws.scr_ctas;
   const int64_t tiles1 = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
   const int64_t tiles2 = ((m + k2BM - 1) / k2BM) * ((n + k2BN - 1) / k2BN);
-  const int64_t pairs_avail = sms / 2 > 0 ? sms / 2 : 1;
-  const double t_one = (double)((tiles1 + sms - 1) / sms);
+  const int64_t pairs_avail = cta_cap / 2 > 0 ? cta_cap / 2 : 1;
+  const double t_one = (double)((tiles1 + cta_cap - 1) / cta_cap);
   const double t_pair = (double)((tiles2 + pairs_avail - 1) / pairs_avail) * 2.0 / kModPairGain;
-  const bool pair = force ? force[0] == 'p' : t_pair < t_one;
-  const int bm = pair ? 128 : kBM;  // rows of A (and of op(B)^T) one CTA stages
+  const bool pair = (force ? force[0] == 'p' : t_pair < t_one) && cta_cap >= 2;
+  const uint32_t brows = pair ? 128u : (uint32_t)kBM;  // rows of A (and of op(B)^T) one CTA stages
   CUtensorMap tmA, tmB;
   memset(&tmA, 0, sizeof(tmA));
   memset(&tmB, 0, sizeof(tmB));
-  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, (uint64_t)nmod};
+  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, (uint64_t)a.nmod};
   const uint64_t pA[2] = {(uint64_t)ws.kp * 2, (uint64_t)m * ws.kp * 2};
-  const uint32_t bA[3] = {(uint32_t)kBK, (uint32_t)bm, 1u};
+  const uint32_t bA[3] = {(uint32_t)kBK, brows, 1u};
   int rc = encode_tmap(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
-  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, (uint64_t)nmod};
+  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, (uint64_t)a.nmod};
   const uint64_t pB[2] = {(uint64_t)ws.kp * 2, (uint64_t)n * ws.kp * 2};
-  const uint32_t bB[3] = {(uint32_t)kBK, (uint32_t)(pair ? 128 : kBN), 1u};
+  const uint32_t bB[3] = {(uint32_t)kBK, brows, 1u};
   rc = encode_tmap(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
-  ModArgs a;
-  memset(&a, 0, sizeof(a));
-  a.m = m; a.n = n;
   a.nkb = (int)((k + kBK - 1) / kBK);
-  a.nmod = nmod;
   const int tbm = pair ? k2BM : kBM, tbn = pair ? k2BN : kBN;
   a.tiles_m = (int)((m + tbm - 1) / tbm);
   const int64_t tiles = (int64_t)a.tiles_m * ((n + tbn - 1) / tbn);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
-  for (int l = 0; l < nmod; ++l) {
-    a.p[l] = kModuli[l];
-    a.c[l] = pc[l];
-  }
-  a.U = ws.U;
-  a.err = device_error_word();
   cudaError_t e;
   if (pair) {
     const int pairs = (int)(tiles < pairs_avail ? tiles : pairs_avail);
@@ -627,7 +684,7 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod, const int* pc, co
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm pair)");
     k_mod_gemm_pair<<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
   } else {
-    const int grid = (int)(tiles < sms ? tiles : sms);
+    const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);
     e = cudaFuncSetAttribute(k_mod_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm)");
@@ -694,6 +751,21 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
                      need);
   ModWorkspace ws;
   mod_layout(m, n, k, nmod_ws, workspace, &ws);
+  const bool timing = info && info->record_phases;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  struct EventGuard {
+    cudaEvent_t* e;
+    ~EventGuard() {
+      for (int i = 0; i < 3; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  cudaError_t e;
+  if (timing) {
+    for (int i = 0; i < 3; ++i)
+      if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventCreate");
+    if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
+  }
   const int ta = (transa == 'N' || transa == 'n') ? 0 : 1, tb = (transb == 'N' || transb == 'n') ? 0 : 1;
 
   // exponents (and, in automatic mode, the magnitude statistics) of both sides
@@ -710,7 +782,6 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) return rc;
   int t = bits;
   double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
-  cudaError_t e;
   if (bits == 0) {
     if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
     if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
@@ -749,31 +820,43 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     ms.whi[l] = hi;
   }
   if ((rc = launch_residue_pair(pp, ms, split_blocks, s))) return rc;
+  k_mod_colscale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.sigB, ws.badB, n, alpha, t, ws.cs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "column scale launch");
 
-  // products modulo each modulus, then the reconstruction
+  // products modulo each modulus and the reconstruction
+  ModArgs a;
+  memset(&a, 0, sizeof(a));
   const hu128 M = moduli_product(nmod);
-  int pc[kMaxModuli];
-  CrtArgs ca;
-  memset(&ca, 0, sizeof(ca));
   for (int l = 0; l < nmod; ++l) {
     const hu128 Mp = M / (hu128)kModuli[l];
-    pc[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
-    ca.mp_lo[l] = (uint64_t)Mp;
-    ca.mp_hi[l] = (uint64_t)(Mp >> 64);
-    ca.inv[l] = 1.0f / (float)kModuli[l];
+    a.p[l] = kModuli[l];
+    a.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
+    a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
+    a.rq[l] = ((1u << 24) + (uint32_t)kModuli[l] - 1u) / (uint32_t)kModuli[l];
+    for (int w = 0; w < 4; ++w) a.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
   }
-  if ((rc = launch_mod_gemm(m, n, k, nmod, pc, ws, sms, s))) return rc;
-  ca.m = m; ca.n = n; ca.ldc = ldc;
-  ca.nmod = nmod; ca.t = t;
-  ca.M_lo = (uint64_t)M; ca.M_hi = (uint64_t)(M >> 64);
+  a.m = m; a.n = n; a.ldc = ldc;
+  a.nmod = nmod;
+  a.M_lo = (uint64_t)M; a.M_hi = (uint64_t)(M >> 64);
   const hu128 half = M / 2;
-  ca.half_lo = (uint64_t)half; ca.half_hi = (uint64_t)(half >> 64);
-  ca.alpha = alpha; ca.beta = beta; ca.C = C;
-  ca.sigA = ws.sigA; ca.sigB = ws.sigB; ca.badA = ws.badA; ca.badB = ws.badB;
-  ca.U = ws.U;
-  const unsigned gy = (unsigned)(n < 65535 ? n : 65535);
-  k_crt<<<dim3((unsigned)((m + 255) / 256), gy), 256, 0, s>>>(ca);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "reconstruction launch");
+  a.half_lo = (uint64_t)half; a.half_hi = (uint64_t)(half >> 64);
+  a.beta = beta;
+  a.C = C;
+  a.sigA = ws.sigA; a.badA = ws.badA;
+  a.cs = ws.cs;
+  a.scr = ws.scr;
+  a.err = device_error_word();
+  if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
+  if ((rc = launch_mod_gemm(m, n, k, a, ws, sms, s))) return rc;
+  if (timing) {
+    float t0 = 0.f, t1 = 0.f;
+    if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[2])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t0, ev[0], ev[1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t1, ev[1], ev[2])) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu_mod: phase timing");
+    info->prep_ms = t0;
+    info->gemm_ms = t1;
+  }
   if (info) {
     info->slices = nmod;
     info->digit_bits = t;

@@ -159,22 +159,20 @@ def test_auto_large_square_sampled_rows(oracle_mod):
 
 def test_errors_and_quick_returns():
     import torch
-    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(4, 4, 4, 0)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     z = torch.zeros(64, dtype=torch.float64, device="cuda")
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 63, 0.0, ws, 1 << 20) == \
-        gbdgemm.GBD_ERR_ARG
+    call = gbdgemm.gbd_dgemm_emu_mod
+    assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 63, 0.0, ws, wsb) == gbdgemm.GBD_ERR_ARG
     # 2 k 2^(2t) = 2^127 at t = 62, k = 4: more than 16 moduli
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 62, 0.0, ws, 1 << 20) == \
-        gbdgemm.GBD_ERR_LIMIT
+    assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 62, 0.0, ws, wsb) == gbdgemm.GBD_ERR_LIMIT
     # an accuracy target beyond 16 moduli in automatic mode
     o = torch.ones(64, dtype=torch.float64, device="cuda")
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 4, 1.0, o, 4, o, 4, 0.0, z, 4, 0, 1e-40, ws, 1 << 20) == \
-        gbdgemm.GBD_ERR_LIMIT
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 10, 0.0, ws, 64) == \
-        gbdgemm.GBD_ERR_WORKSPACE
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 4, 1.0, z, 3, z, 4, 0.0, z, 4, 10, 0.0, ws, 1 << 20) == 8
+    assert call("N", "N", 4, 4, 4, 1.0, o, 4, o, 4, 0.0, z, 4, 0, 1e-40, ws, wsb) == gbdgemm.GBD_ERR_LIMIT
+    assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 10, 0.0, ws, 64) == gbdgemm.GBD_ERR_WORKSPACE
+    assert call("N", "N", 4, 4, 4, 1.0, z, 3, z, 4, 0.0, z, 4, 10, 0.0, ws, wsb) == 8
     C = torch.arange(16, dtype=torch.float64, device="cuda")
-    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", 4, 4, 0, 1.0, z, 4, z, 1, 3.0, C, 4, 0, 0.0, ws, 1 << 20) == 0
+    assert call("N", "N", 4, 4, 0, 1.0, z, 4, z, 1, 3.0, C, 4, 0, 0.0, ws, wsb) == 0
     torch.cuda.synchronize()
     assert torch.equal(C, 3.0 * torch.arange(16, dtype=torch.float64, device="cuda"))
 
