@@ -109,11 +109,11 @@ constexpr int kMaxModuli = 16;  // the product of the moduli stays below 2^126
 // residue is at most 128 in magnitude: exact in BF16, products at most 2^14
 constexpr int kModuli[kMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
                                      229, 227, 223, 217, 211, 199, 197, 193};
-// residue split parameters: t integer bits (<= 62), the first n moduli, 1/p, and 256^d mod p
-// for d = 0..3 (wlo) and 4..7 (whi) packed one byte per d
+// residue split parameters: t integer bits (<= 62), the first n moduli (as float), 1/p, and
+// 256^d mod p for d = 0..3 (wlo) and 4..7 (whi) packed one byte per d
 struct ModSplit {
   int n, t;
-  int p[kMaxModuli];
+  float pf[kMaxModuli];
   float inv[kMaxModuli];
   uint32_t wlo[kMaxModuli], whi[kMaxModuli];
 };

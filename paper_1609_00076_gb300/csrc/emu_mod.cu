@@ -808,7 +808,7 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   ms.t = t;
   for (int l = 0; l < nmod; ++l) {
     const int pm = kModuli[l];
-    ms.p[l] = pm;
+    ms.pf[l] = (float)pm;
     ms.inv[l] = 1.0f / (float)pm;
     uint32_t w = 1, lo = 0, hi = 0;  // 256^d mod p
     for (int d = 0; d < 8; ++d) {

@@ -305,8 +305,11 @@ __device__ __forceinline__ int64_t rounded_scaled(uint64_t bits, int sigma, int 
   return (bits >> 63) ? -(int64_t)q : (int64_t)q;
 }
 
-// the residues of the modular emulation (writer of split_body): for each modulus p, the
-// symmetric residue of A' = rint(x 2^(t - sigma)) as a BF16 value (|residue| <= 128)
+// the residues of the modular emulation (writer of split_body): for each modulus p, a residue
+// of A' = rint(x 2^(t - sigma)) of magnitude at most 128 (exact in BF16).  |A'| mod p is
+// reduced from s = sum_d byte_d (256^d mod p) < 2^20 as r = s - p rint(s/p) in FP32, exact: the
+// rounded quotient errs by less than 2^-11, so |r| <= p/2 + p 2^-11, that is |r| <= 128.  The
+// sign of A' is then set on its bits.
 struct ResidueWriter {
   const ModSplit* mp;  // in the kernel's parameter space
   int64_t R, K;
@@ -314,38 +317,31 @@ struct ResidueWriter {
   int64_t kp;
   __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
                                              int64_t pbase) const {
-    uint32_t lo[kPerThread], hi[kPerThread];  // the bytes of |A'|: 0..3 and 4..7
-    uint32_t neg = 0;
+    uint32_t lo[kPerThread], hi[kPerThread], sgn[kPerThread];  // the bytes of |A'| (0..3, 4..7), its sign
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
       const int64_t q = rounded_scaled(x[v], sg, mp->t);
       const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
       lo[v] = (uint32_t)a;
       hi[v] = (uint32_t)(a >> 32);
-      neg |= (uint32_t)(q < 0) << v;
+      sgn[v] = q < 0 ? 0x80000000u : 0u;
     }
     const bool full = pbase + kPerThread <= K;
     for (int i = 0; i < mp->n; ++i) {
-      const int p = mp->p[i];
-      const float inv = mp->inv[i];
+      const float pf = mp->pf[i], inv = mp->inv[i];
       const uint32_t wl = mp->wlo[i], wh = mp->whi[i];  // 256^d mod p, one byte per d
-      uint32_t packed[kPerThread / 2];
+      uint32_t bits[kPerThread];
 #pragma unroll
-      for (int v = 0; v < kPerThread; v += 2) {
-        int res[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          // |A'| mod p = (sum_d byte_d (256^d mod p)) mod p; the sum is below 2^20
-          const uint32_t sum = __dp4a(lo[v + u], wl, 0u) + __dp4a(hi[v + u], wh, 0u);
-          int rr = (int)sum - p * (int)floorf((float)sum * inv);
-          rr += rr < 0 ? p : 0;
-          rr -= rr >= p ? p : 0;
-          if (2 * rr >= p) rr -= p;       // symmetric: [-p/2, p/2)
-          if ((neg >> (v + u)) & 1u) rr = -rr;
-          res[u] = rr;
-        }
-        packed[v / 2] = bf16_of_digit(res[0]) | (bf16_of_digit(res[1]) << 16);
+      for (int v = 0; v < kPerThread; ++v) {
+        const uint32_t s = __dp4a(lo[v], wl, __dp4a(hi[v], wh, 0u));
+        const float sf = __uint_as_float(s | 0x4B000000u) - 8388608.0f;  // s exactly (s < 2^23)
+        const float qf = fmaf(sf, inv, 12582912.0f) - 12582912.0f;          // rint(s/p)
+        const float rf = fmaf(-pf, qf, sf);                                  // exact
+        bits[v] = __float_as_uint(rf) ^ sgn[v];
       }
+      uint32_t packed[kPerThread / 2];  // BF16 pairs: the upper halves of the FP32 bits (exact here)
+#pragma unroll
+      for (int v = 0; v < kPerThread; v += 2) packed[v / 2] = __byte_perm(bits[v], bits[v + 1], 0x7632);
       uint16_t* row = D + ((int64_t)i * R + r) * kp + pbase;
       if (full) {
         *reinterpret_cast<uint4*>(row) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
