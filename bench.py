@@ -3,7 +3,8 @@
 
 Metric: DGEMM TFLOP/s (useful flops 2mnk per call) of the split emulation at
 FP64 accuracy (automatic slice count for the componentwise FP64 bound), with the
-native FP64-MMA path measured beside it on the same inputs, on the large square
+native FP64-MMA path and the modular emulation (Ozaki scheme II, automatic
+integer bits for the same bound) measured beside it on the same inputs, on the large square
 workload m = n = k = 8192 (FP64 operands uniform on [-1, 1), N,N, alpha = 1,
 beta = 0; every input is larger than L2, so no flush is needed between timed
 calls).  The dominant kernel's roofline is the BF16 tensor peak (slice flops =
@@ -50,7 +51,7 @@ NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
 # dram bytes (read + write) per launch of the dominant kernel, from one single-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload; None until captured
 # for the current kernel
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.1e9}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.1e9, "mod": None}
 
 
 def load_peaks():
@@ -301,6 +302,9 @@ def run_ours(args, world, rank, local, pg):
     nat_ms = statistics.mean(nev[i].elapsed_time(nev[i + 1]) for i in range(nat_calls))
     nat_tflops = flops / (nat_ms / 1000.0) / 1e12
 
+    # ---- the modular emulation (Ozaki scheme II) on the same inputs, automatic bits at the FP64 bound ----
+    mod = modular_measure(dev, stream, A, B, C, steps=max(3, args.steps), warmup=max(3, args.warmup))
+
     # ---- end to end through the host-buffer C-ABI call (pinned host memory), copies inside the region ----
     # Each step is one gbd_dgemm_emu_host call: upload of A and B, the emulated product, download of C.
     # Serial: one call at a time.  Overlapped (the reported value): two calls in flight on two streams
@@ -364,6 +368,18 @@ def run_ours(args, world, rank, local, pg):
     slice_flops = products * flops
     achieved = slice_flops / (g_ms / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=8.0)
+    mod_achieved = mod["moduli"] * flops / (mod["products_ms"] / 1000.0) / 1e12
+    modular = {
+        "value": mod["value"], "unit": "TFLOP/s", "ms_per_call": mod["ms"], "steps": mod["steps"],
+        "path": "emulated (Ozaki scheme II: residues modulo coprime moduli <= 256 on tcgen05 BF16, CRT; FP64 bound)",
+        "moduli": mod["moduli"], "integer_bits": mod["bits"], "bound_est": mod["bound_est"],
+        "phases_ms": {"prep": mod["prep_ms"], "products_and_reconstruction": mod["products_ms"]},
+        "over_split": mod["value"] / value, "over_native": mod["value"] / nat_tflops,
+        "roofline": {"bound": "tensor", "achieved": mod_achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                     "frac": mod_achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
+                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT)",
+                     "peak_source": f"{src} bf16_tflops_sustained"},
+    }
     launches_per_step = 8  # exponents x2, magnitudes x2, statistics, split x2, slice product
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -375,6 +391,7 @@ def run_ours(args, world, rank, local, pg):
         "native": {"value": nat_tflops, "unit": "TFLOP/s", "ms_per_call": nat_ms, "frac_of_fp64_peak": nat_tflops / fp64_peak,
                    "fp64_peak": fp64_peak},
         "emulated_over_native": value / nat_tflops,
+        "modular": modular,
         "phases_ms": {"prep": statistics.mean(prep_ms), "slice_gemm": g_ms},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
@@ -395,6 +412,43 @@ def run_ours(args, world, rank, local, pg):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def modular_measure(dev, stream, A, B, C, steps: int, warmup: int):
+    """Device time of gbd_dgemm_emu_mod on the headline inputs (automatic integer bits for the FP64
+    bound), its phases, and the rate of its product kernel."""
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, 0)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    info = gbdgemm.GbdEmuInfo()
+
+    def step(record):
+        info.record_phases = 1 if record else 0
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
+                                                info, stream=stream))
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step(False)
+    torch.cuda.synchronize()
+    ev = _events(steps + 1)
+    prep, prod = [], []
+    ev[0].record(stream)
+    for i in range(steps):
+        step(True)
+        prep.append(info.prep_ms)
+        prod.append(info.gemm_ms)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+    ms = ev[0].elapsed_time(ev[-1]) / steps
+    del ws
+    flops = 2.0 * M * N * K
+    return {"ms": ms, "value": flops / (ms / 1000.0) / 1e12, "moduli": info.products, "bits": info.digit_bits,
+            "bound_est": info.bound_est, "prep_ms": statistics.mean(prep), "products_ms": statistics.mean(prod),
+            "steps": steps}
 
 
 def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
