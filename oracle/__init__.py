@@ -17,6 +17,9 @@ Contents
 * ``ozmod_dgemm_rows``: a plain CPU model of the modular emulation (Ozaki scheme II,
   ozaki_mod_model.c): rounded scaled integers and their exact 128-bit product, where
   the GPU path goes through residues and the Chinese remainder theorem.
+* ``dsyrk`` / ``dtrmm`` / ``dtrsm``: the GEMM-based level-3 operations by their plain
+  definitions (level3.c): Dot2 inner products on the referenced triangle, and
+  substitution with Dot2 numerators for the triangular solve.
 
 Matrices are passed as 1-D float64 numpy arrays in column-major order with an
 explicit leading dimension, exactly as in the BLAS statement (Section 2.1:
@@ -32,7 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_SOURCES = ["oracle.c", "ozaki_model.c", "ozaki_mod_model.c"]
+_SOURCES = ["oracle.c", "ozaki_model.c", "ozaki_mod_model.c", "level3.c"]
 _lib = None
 
 
@@ -78,6 +81,12 @@ def _load():
     lib.oracle_ozmod_dgemm_rows.restype = i
     lib.oracle_ozmod_i128_to_double.argtypes = [i64, ctypes.c_uint64]
     lib.oracle_ozmod_i128_to_double.restype = d
+    lib.oracle_dsyrk.argtypes = [c, c, i64, i64, d, vp, i64, d, vp, i64, i]
+    lib.oracle_dsyrk.restype = i
+    lib.oracle_dtrmm.argtypes = [c, c, c, c, i64, i64, d, vp, i64, vp, i64, i]
+    lib.oracle_dtrmm.restype = i
+    lib.oracle_dtrsm.argtypes = lib.oracle_dtrmm.argtypes
+    lib.oracle_dtrsm.restype = i
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = i
     _lib = lib
@@ -188,6 +197,25 @@ def ozmod_i128_to_double(v: int) -> float:
     if hi >= 1 << 63:
         hi -= 1 << 64
     return _load().oracle_ozmod_i128_to_double(hi, u & ((1 << 64) - 1))
+
+
+def dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, nthreads=0):
+    """In place on the `uplo` triangle of C: C := alpha op(A) op(A)^T + beta C.  Returns the
+    BLAS status."""
+    return _load().oracle_dsyrk(uplo.encode(), trans.encode(), n, k, float(alpha), _ptr(_as_f64(A)), lda,
+                                float(beta), _ptr(_as_f64(C)), ldc, int(nthreads))
+
+
+def dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, nthreads=0):
+    """In place: B := alpha op(A) B (side 'L') or alpha B op(A) (side 'R'), A triangular."""
+    return _load().oracle_dtrmm(side.encode(), uplo.encode(), transa.encode(), diag.encode(), m, n,
+                                float(alpha), _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, int(nthreads))
+
+
+def dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, nthreads=0):
+    """In place: B := X with op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R')."""
+    return _load().oracle_dtrsm(side.encode(), uplo.encode(), transa.encode(), diag.encode(), m, n,
+                                float(alpha), _ptr(_as_f64(A)), lda, _ptr(_as_f64(B)), ldb, int(nthreads))
 
 
 def ozaki_exponent(x: float) -> int:
