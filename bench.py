@@ -51,7 +51,7 @@ NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
 # dram bytes (read + write) per launch of the dominant kernel, from one single-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload; None until captured
 # for the current kernel
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.1e9, "mod": None}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 38.97e9, "mod": 21.25e9}
 
 
 def load_peaks():
