@@ -320,6 +320,46 @@ GBD_API int gbd_watchdog_selftest(int limit_ms, void* stream);
  */
 GBD_API int gbd_check_device_error(void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* GEMM-based level-3 BLAS (the paper's "Poorman's BLAS", Section 3.1)        */
+/* ------------------------------------------------------------------------- */
+/*
+ * DSYRK, DTRMM and DTRSM cast in terms of this library's GEMM, after Kagstrom, Ling and
+ * Van Loan (TOMS 24(3), 1998), the work the paper cites for building every level-3
+ * operation from matrix-matrix products of submatrices.  Argument lists, meanings and
+ * return codes are those of reference BLAS; column-major storage with leading dimensions
+ * (Section 2.1); device pointers owned by the caller; asynchronous on `stream`.
+ *
+ * mode: GBD_MODE_NATIVE (products by gbd_dgemm) or GBD_MODE_EMULATED (products by
+ *   gbd_dgemm_emu with automatic slices for `tol`, tol <= 0 meaning each product's FP64
+ *   bound; each product then synchronises `stream` once).  Any other value: GBD_ERR_ARG.
+ * workspace: at least the matching *_workspace_size bytes, 256-byte aligned (may be NULL
+ *   when that size is 0).  Its contents are scratch.
+ *
+ * gbd_dsyrk: C := alpha op(A) op(A)^T + beta C on the `uplo` ('U'/'L') triangle of the
+ *   n x n matrix C; op(A) = A (n x k) for trans 'N', A^T (A is k x n) for 'T'/'C'.  The
+ *   other triangle is neither read for the result nor written.  beta = 0: C is not read.
+ *   Codes: 1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc.
+ * gbd_dtrmm: B := alpha op(A) B (side 'L', A m x m) or alpha B op(A) (side 'R', A n x n),
+ *   A triangular: only its `uplo` triangle is read; diag 'U' means a unit diagonal, not
+ *   read.  alpha = 0: B := 0 without reading A.
+ * gbd_dtrsm: B := X solving op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R'),
+ *   same conventions.  No test for singularity is made (as in BLAS).
+ *   Codes (both): 1 side, 2 uplo, 3 transa, 4 diag, 5 m, 6 n, 9 lda, 11 ldb.
+ */
+GBD_API size_t gbd_dsyrk_workspace_size(int64_t n, int64_t k, int mode);
+GBD_API size_t gbd_dtrmm_workspace_size(char side, int64_t m, int64_t n, int mode);
+GBD_API size_t gbd_dtrsm_workspace_size(char side, int64_t m, int64_t n, int mode);
+GBD_API int gbd_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double* A,
+                      int64_t lda, double beta, double* C, int64_t ldc, int mode, double tol,
+                      void* workspace, size_t workspace_bytes, void* stream);
+GBD_API int gbd_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                      double alpha, const double* A, int64_t lda, double* B, int64_t ldb, int mode,
+                      double tol, void* workspace, size_t workspace_bytes, void* stream);
+GBD_API int gbd_dtrsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                      double alpha, const double* A, int64_t lda, double* B, int64_t ldb, int mode,
+                      double tol, void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,12 @@ _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_mod_moduli", [_i, _i64, ctypes.POINTER(ctypes.c_int)], _i),
     ("gbd_dgemm_emu_mod", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                            ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_dsyrk_workspace_size", [_i64, _i64, _i], _sz),
+    ("gbd_dtrmm_workspace_size", [_c, _i64, _i64, _i], _sz),
+    ("gbd_dtrsm_workspace_size", [_c, _i64, _i64, _i], _sz),
+    ("gbd_dsyrk", [_c, _c, _i64, _i64, _d, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz, _vp], _i),
+    ("gbd_dtrmm", [_c, _c, _c, _c, _i64, _i64, _d, _vp, _i64, _vp, _i64, _i, _d, _vp, _sz, _vp], _i),
+    ("gbd_dtrsm", [_c, _c, _c, _c, _i64, _i64, _d, _vp, _i64, _vp, _i64, _i, _d, _vp, _sz, _vp], _i),
     ("gbd_dgemm_emu_host_buffer_size", [_c, _c, _i64, _i64, _i64, _i], _sz),
     ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                             ctypes.POINTER(GbdEmuInfo), _vp], _i),
@@ -224,6 +230,45 @@ def gbd_dgemm_emu_mod(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, l
                                     int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(bits),
                                     float(tol), _addr(workspace), int(workspace_bytes),
                                     ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_dsyrk_workspace_size(n, k, mode) -> int:
+    """Device workspace bytes of gbd_dsyrk."""
+    return int(load().gbd_dsyrk_workspace_size(int(n), int(k), int(mode)))
+
+
+def gbd_dtrmm_workspace_size(side, m, n, mode) -> int:
+    """Device workspace bytes of gbd_dtrmm."""
+    return int(load().gbd_dtrmm_workspace_size(_t(side), int(m), int(n), int(mode)))
+
+
+def gbd_dtrsm_workspace_size(side, m, n, mode) -> int:
+    """Device workspace bytes of gbd_dtrsm."""
+    return int(load().gbd_dtrsm_workspace_size(_t(side), int(m), int(n), int(mode)))
+
+
+def gbd_dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, mode, tol, workspace, workspace_bytes,
+              stream=None) -> int:
+    """C := alpha op(A) op(A)^T + beta C on one triangle (GEMM-based); returns the status."""
+    return load().gbd_dsyrk(_t(uplo), _t(trans), int(n), int(k), float(alpha), _addr(A), int(lda), float(beta),
+                            _addr(C), int(ldc), int(mode), float(tol), _addr(workspace), int(workspace_bytes),
+                            _stream(stream))
+
+
+def gbd_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, mode, tol, workspace, workspace_bytes,
+              stream=None) -> int:
+    """B := alpha op(A) B or alpha B op(A), A triangular (GEMM-based); returns the status."""
+    return load().gbd_dtrmm(_t(side), _t(uplo), _t(transa), _t(diag), int(m), int(n), float(alpha), _addr(A),
+                            int(lda), _addr(B), int(ldb), int(mode), float(tol), _addr(workspace),
+                            int(workspace_bytes), _stream(stream))
+
+
+def gbd_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, mode, tol, workspace, workspace_bytes,
+              stream=None) -> int:
+    """B := X with op(A) X = alpha B or X op(A) = alpha B (GEMM-based); returns the status."""
+    return load().gbd_dtrsm(_t(side), _t(uplo), _t(transa), _t(diag), int(m), int(n), float(alpha), _addr(A),
+                            int(lda), _addr(B), int(ldb), int(mode), float(tol), _addr(workspace),
+                            int(workspace_bytes), _stream(stream))
 
 
 def gbd_dgemm_emu_host_buffer_size(transa, transb, m, n, k, slices=0) -> int:

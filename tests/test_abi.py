@@ -141,3 +141,37 @@ def test_emu_mod_workspace_and_argument_codes_without_gpu(lib):
     assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 63, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
     assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, -1, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
     assert call("N", "N", 2, 0, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 0
+
+
+def test_level3_workspace_sizes_and_codes_without_gpu(lib):
+    import numpy as np
+    nat, emu = gbdgemm.GBD_MODE_NATIVE, gbdgemm.GBD_MODE_EMULATED
+    # the native triangular solve needs no workspace; the others hold scratch and, emulated, GEMM workspace
+    assert gbdgemm.gbd_dtrsm_workspace_size("L", 1000, 300, nat) == 0
+    # the top split of 1000 is 512 + 488: both triangles' coupling products fit
+    for shape in ((300, 488, 512), (300, 512, 488)):
+        assert gbdgemm.gbd_dtrsm_workspace_size("R", 300, 1000, emu) >= gbdgemm.gbd_dgemm_emu_workspace_size(*shape, 0)
+    assert 0 < gbdgemm.gbd_dtrmm_workspace_size("L", 1000, 300, nat) < gbdgemm.gbd_dtrmm_workspace_size("L", 1000, 300, emu)
+    assert gbdgemm.gbd_dsyrk_workspace_size(700, 300, nat) == 512 * 512 * 8
+    assert gbdgemm.gbd_dsyrk_workspace_size(700, 300, emu) > 512 * 512 * 8
+    assert gbdgemm.gbd_dtrmm_workspace_size("X", 10, 10, nat) == 0
+    a = np.zeros(16)
+    s = dict(stream=0)
+    assert gbdgemm.gbd_dsyrk("X", "N", 2, 2, 1.0, a, 2, 0.0, a, 2, nat, 0.0, None, 0, **s) == 1
+    assert gbdgemm.gbd_dsyrk("L", "X", 2, 2, 1.0, a, 2, 0.0, a, 2, nat, 0.0, None, 0, **s) == 2
+    assert gbdgemm.gbd_dsyrk("L", "N", -1, 2, 1.0, a, 2, 0.0, a, 2, nat, 0.0, None, 0, **s) == 3
+    assert gbdgemm.gbd_dsyrk("L", "N", 2, -1, 1.0, a, 2, 0.0, a, 2, nat, 0.0, None, 0, **s) == 4
+    assert gbdgemm.gbd_dsyrk("L", "T", 2, 3, 1.0, a, 2, 0.0, a, 2, nat, 0.0, None, 0, **s) == 7
+    assert gbdgemm.gbd_dsyrk("L", "N", 3, 2, 1.0, a, 3, 0.0, a, 2, nat, 0.0, None, 0, **s) == 10
+    assert gbdgemm.gbd_dsyrk("L", "N", 0, 2, 1.0, a, 1, 0.0, a, 1, nat, 0.0, None, 0, **s) == 0
+    for f in (gbdgemm.gbd_dtrmm, gbdgemm.gbd_dtrsm):
+        assert f("X", "L", "N", "N", 2, 2, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 1
+        assert f("L", "X", "N", "N", 2, 2, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 2
+        assert f("L", "L", "X", "N", 2, 2, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 3
+        assert f("L", "L", "N", "X", 2, 2, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 4
+        assert f("L", "L", "N", "N", -1, 2, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 5
+        assert f("L", "L", "N", "N", 2, -1, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 6
+        assert f("R", "L", "N", "N", 2, 3, 1.0, a, 2, a, 2, nat, 0.0, None, 0, **s) == 9
+        assert f("L", "L", "N", "N", 3, 2, 1.0, a, 3, a, 2, nat, 0.0, None, 0, **s) == 11
+        assert f("L", "L", "N", "N", 3, 0, 1.0, a, 3, a, 3, nat, 0.0, None, 0, **s) == 0
+        assert f("L", "L", "N", "N", 2, 2, 1.0, a, 2, a, 2, 5, 0.0, None, 0, **s) == gbdgemm.GBD_ERR_ARG
