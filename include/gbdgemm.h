@@ -330,9 +330,13 @@ GBD_API int gbd_check_device_error(void* stream);
  * return codes are those of reference BLAS; column-major storage with leading dimensions
  * (Section 2.1); device pointers owned by the caller; asynchronous on `stream`.
  *
- * mode: GBD_MODE_NATIVE (products by gbd_dgemm) or GBD_MODE_EMULATED (products by
- *   gbd_dgemm_emu with automatic slices for `tol`, tol <= 0 meaning each product's FP64
- *   bound; each product then synchronises `stream` once).  Any other value: GBD_ERR_ARG.
+ * mode: GBD_MODE_NATIVE (products by gbd_dgemm) or GBD_MODE_EMULATED: each product by the
+ *   fastest path that meets `tol` (tol <= 0: each product's FP64 bound): gbd_dgemm below
+ *   1e8 flops; gbd_dgemm_emu_mod for at least 2.5e6 outputs, or gbd_dgemm_emu when 16
+ *   moduli cannot reach `tol`; gbd_dgemm_emu otherwise.  Each emulated product synchronises
+ *   `stream` once.  Any other mode: GBD_ERR_ARG.  The environment variables
+ *   GBD_L3_NATIVE_FLOPS and GBD_L3_MODULAR_OUTPUTS override the two thresholds (read at
+ *   every call; for tests and tuning).
  * workspace: at least the matching *_workspace_size bytes, 256-byte aligned (may be NULL
  *   when that size is 0).  Its contents are scratch.
  *

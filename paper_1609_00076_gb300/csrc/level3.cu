@@ -15,9 +15,15 @@
 //          (beta = alpha folds the scaling in), the trailing half solved with alpha = 1.  A
 //          diagonal block of at most 64 is solved by substitution in k_trsm_base: one thread
 //          per right-hand side, the triangle in shared memory (read as a broadcast).
-// All work is stream-ordered on the caller's stream.  In emulated mode the GEMMs are
-// gbd_dgemm_emu calls with automatic slices for `tol` (each synchronises the stream once).
+// All work is stream-ordered on the caller's stream.  In emulated mode each product takes the
+// fastest path that meets `tol`: products under 1e8 flops run natively (a native call is then
+// faster than the emulation's fixed cost, and at least as accurate); products with at least
+// 2.5e6 outputs (enough 128 x 128 tiles for every SM) use the modular emulation, and the split
+// emulation when 16 moduli cannot reach `tol`; the rest use the split emulation, whose
+// split inner dimension serves few output tiles.  Each emulated product synchronises the
+// stream once (automatic mode).
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -29,6 +35,17 @@ constexpr int64_t kSyrkBase = 512;  // diagonal blocks of DSYRK
 constexpr int64_t kTrmmBase = 512;  // diagonal blocks of DTRMM
 constexpr int64_t kTrsmBase = 64;   // diagonal blocks of DTRSM (substitution kernel)
 constexpr int kTrsmVecs = 64;       // right-hand sides per CTA of the substitution kernel
+constexpr double kNativeFlops = 1e8;    // emulated mode: smaller products run natively
+constexpr double kModularOutputs = 2.5e6;  // emulated mode: larger outputs use the modular emulation
+
+// the two thresholds, overridable by GBD_L3_NATIVE_FLOPS and GBD_L3_MODULAR_OUTPUTS (tests, tuning)
+double threshold(const char* env, double dflt) {
+  const char* v = getenv(env);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const double x = strtod(v, &end);
+  return end && end != v ? x : dflt;
+}
 
 int64_t split_point(int64_t r0, int64_t r1) {
   const int64_t half = (r1 - r0) / 2;
@@ -140,18 +157,34 @@ struct Ctx {
   double* scr;  // level-3 scratch (W, D, T)
   bool dry;
   size_t need;
+  double native_flops = kNativeFlops, modular_outputs = kModularOutputs;
+  void thresholds() {
+    native_flops = threshold("GBD_L3_NATIVE_FLOPS", kNativeFlops);
+    modular_outputs = threshold("GBD_L3_MODULAR_OUTPUTS", kModularOutputs);
+  }
 
   int gemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
            const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
     if (m == 0 || n == 0) return GBD_OK;
+    const bool native = mode == GBD_MODE_NATIVE || 2.0 * (double)m * (double)n * (double)k <= native_flops;
+    const bool modular = !native && (double)m * (double)n >= modular_outputs;
     if (dry) {
-      if (mode == GBD_MODE_EMULATED) {
-        const size_t w = gbd_dgemm_emu_workspace_size(m, n, k, 0);
+      if (!native) {
+        size_t w = gbd_dgemm_emu_workspace_size(m, n, k, 0);
+        if (modular) {
+          const size_t wm = gbd_dgemm_emu_mod_workspace_size(m, n, k, 0);
+          if (wm > w) w = wm;
+        }
         if (w > need) need = w;
       }
       return GBD_OK;
     }
-    if (mode == GBD_MODE_NATIVE) return gbd_dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    if (native) return gbd_dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    if (modular) {
+      const int rc = gbd_dgemm_emu_mod(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0, tol, gws, gwsb,
+                                       nullptr, s);
+      if (rc != GBD_ERR_LIMIT) return rc;  // GBD_ERR_LIMIT: the target needs more than 16 moduli; C untouched
+    }
     return gbd_dgemm_emu(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0, tol, gws, gwsb, nullptr, s);
   }
   int check(const char* what) {
@@ -346,6 +379,7 @@ size_t tri_workspace(bool solve, int side, int64_t m, int64_t n, int mode) {
   Ctx c;
   memset(&c, 0, sizeof(c));
   c.mode = mode;
+  c.thresholds();
   c.dry = true;
   Tri t;
   memset(&t, 0, sizeof(t));
@@ -388,6 +422,7 @@ int tri_call(bool solve, char side, char uplo, char transa, char diag, int64_t m
   const size_t scr = solve ? 0 : trmm_scratch(sd, m, n);
   Ctx c;
   c.mode = mode;
+  c.thresholds();
   c.tol = tol;
   c.s = s;
   c.scr = static_cast<double*>(workspace);
@@ -422,6 +457,7 @@ size_t gbd_dsyrk_workspace_size(int64_t n, int64_t k, int mode) {
   Ctx c;
   memset(&c, 0, sizeof(c));
   c.mode = mode;
+  c.thresholds();
   c.dry = true;
   Syrk y;
   memset(&y, 0, sizeof(y));
@@ -475,6 +511,7 @@ int gbd_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const d
   const size_t scr = syrk_scratch(n);
   Ctx c;
   c.mode = mode;
+  c.thresholds();
   c.tol = tol;
   c.s = s;
   c.scr = static_cast<double*>(workspace);

@@ -153,7 +153,10 @@ def test_level3_workspace_sizes_and_codes_without_gpu(lib):
         assert gbdgemm.gbd_dtrsm_workspace_size("R", 300, 1000, emu) >= gbdgemm.gbd_dgemm_emu_workspace_size(*shape, 0)
     assert 0 < gbdgemm.gbd_dtrmm_workspace_size("L", 1000, 300, nat) < gbdgemm.gbd_dtrmm_workspace_size("L", 1000, 300, emu)
     assert gbdgemm.gbd_dsyrk_workspace_size(700, 300, nat) == 512 * 512 * 8
-    assert gbdgemm.gbd_dsyrk_workspace_size(700, 300, emu) > 512 * 512 * 8
+    # 700 x 300 products are all below 1e8 flops (native); at 4096 x 256 the coupling block is modular
+    assert gbdgemm.gbd_dsyrk_workspace_size(700, 300, emu) == 512 * 512 * 8
+    assert gbdgemm.gbd_dsyrk_workspace_size(4096, 256, emu) >= 512 * 512 * 8 + \
+        gbdgemm.gbd_dgemm_emu_mod_workspace_size(2048, 2048, 256, 0)
     assert gbdgemm.gbd_dtrmm_workspace_size("X", 10, 10, nat) == 0
     a = np.zeros(16)
     s = dict(stream=0)

@@ -1,7 +1,8 @@
 """GPU parity of the GEMM-based level-3 BLAS (gbd_dsyrk, gbd_dtrmm, gbd_dtrsm) with the oracle.
 
-Both modes (native FP64 products, emulated products) run every side/uplo/trans/diag case
-at sizes that recurse at least once.  Unreferenced triangles and unit diagonals hold NaN,
+Three product paths (native FP64; emulated mode forced to the split emulation; emulated mode
+forced to the modular emulation) run every side/uplo/trans/diag case at sizes that recurse
+at least once.  Unreferenced triangles and unit diagonals hold NaN,
 so reading them would show.  Tolerances:
   DSYRK  each element is one GEMM element: 2 k u G, G = |alpha||op(A)||op(A)^T| + |beta||C0|
          (the benchmark spec's bound of the product);
@@ -22,7 +23,23 @@ from conftest import U, DeviceBuf
 from paper_1609_00076_gb300 import gbdgemm, synth
 
 pytestmark = pytest.mark.gpu
-MODES = {"native": gbdgemm.GBD_MODE_NATIVE, "emulated": gbdgemm.GBD_MODE_EMULATED}
+MODES = {"native": gbdgemm.GBD_MODE_NATIVE, "emulated": gbdgemm.GBD_MODE_EMULATED,
+         "modular": gbdgemm.GBD_MODE_EMULATED}
+
+
+@pytest.fixture
+def products(monkeypatch):
+    """Forces the product path of emulated mode at these small sizes: "emulated" sends every
+    product to the split emulation, "modular" to the modular one (split where 16 moduli
+    cannot reach the target)."""
+    def force(mode):
+        if mode == "emulated":
+            monkeypatch.setenv("GBD_L3_NATIVE_FLOPS", "0")
+            monkeypatch.setenv("GBD_L3_MODULAR_OUTPUTS", "1e300")
+        elif mode == "modular":
+            monkeypatch.setenv("GBD_L3_NATIVE_FLOPS", "0")
+            monkeypatch.setenv("GBD_L3_MODULAR_OUTPUTS", "0")
+    return force
 
 
 def _ws(nbytes):
@@ -65,7 +82,8 @@ def _tri(order, uplo, diag, seed, kind="uniform"):
 # ---------------------------------------------------------------------------------- DSYRK
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
-def test_syrk_within_bound(oracle_mod, mode, uplo, trans):
+def test_syrk_within_bound(oracle_mod, products, mode, uplo, trans):
+    products(mode)
     n, k = 700, 300
     ra, ca = (n, k) if trans == "N" else (k, n)
     lda, ldc = ra + 2, n + 1
@@ -93,6 +111,27 @@ def test_syrk_within_bound(oracle_mod, mode, uplo, trans):
     assert np.all(err <= 2 * k * U * G[tri]), float(np.max(err / (2 * k * U * G[tri])))
 
 
+def test_syrk_large_emulated_within_bound(oracle_mod):
+    # the 2048 x 2048 coupling block (4.2e6 outputs) goes to the modular emulation
+    n, k = 4096, 256
+    A = synth.matrix("uniform", n, k, n, 13)
+    C0 = synth.matrix("uniform", n, n, n, 14)
+    ref = C0.copy()
+    assert oracle_mod.dsyrk("L", "N", n, k, 1.0, A, n, 1.0, ref, n) == 0
+    dA, dC = DeviceBuf(A), DeviceBuf(C0)
+    wsb = gbdgemm.gbd_dsyrk_workspace_size(n, k, 1)
+    assert wsb >= gbdgemm.gbd_dgemm_emu_mod_workspace_size(2048, 2048, k, 0)
+    ws = _ws(wsb)
+    assert gbdgemm.gbd_dsyrk("L", "N", n, k, 1.0, dA.ptr, n, 1.0, dC.ptr, n, 1, 0.0, ws, wsb) == 0
+    _sync_ok()
+    got = synth.view(dC.host(), n, n, n)
+    Av = synth.view(A, n, k, n)
+    G = np.abs(Av) @ np.abs(Av).T + np.abs(synth.view(C0, n, n, n))
+    low = np.tril(np.ones((n, n), bool))
+    err = np.abs(got - synth.view(ref, n, n, n))[low]
+    assert np.all(err <= 2 * k * U * G[low]), float(np.max(err / (2 * k * U * G[low])))
+
+
 def test_syrk_integer_exact_native():
     n, k = 600, 257
     A = synth.matrix("int8", n, k, n, 21)
@@ -113,7 +152,8 @@ def test_syrk_integer_exact_native():
 # ---------------------------------------------------------------------------------- DTRMM
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("side,uplo,trans,diag", list(itertools.product("LR", "LU", "NT", "NU")))
-def test_trmm_within_bound(oracle_mod, mode, side, uplo, trans, diag):
+def test_trmm_within_bound(oracle_mod, products, mode, side, uplo, trans, diag):
+    products(mode)
     order, other = 600, 150
     m, n = (order, other) if side == "L" else (other, order)
     A, lda, tri = _tri(order, uplo, diag, 31 + ord(side) + 2 * ord(uplo))
@@ -140,7 +180,8 @@ def test_trmm_within_bound(oracle_mod, mode, side, uplo, trans, diag):
 # ---------------------------------------------------------------------------------- DTRSM
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("side,uplo,trans,diag", list(itertools.product("LR", "LU", "NT", "NU")))
-def test_trsm_residual_and_forward(oracle_mod, mode, side, uplo, trans, diag):
+def test_trsm_residual_and_forward(oracle_mod, products, mode, side, uplo, trans, diag):
+    products(mode)
     order, other = 333, 130
     m, n = (order, other) if side == "L" else (other, order)
     A, lda, tri = _tri(order, uplo, diag, 41 + ord(side) + 2 * ord(trans))
