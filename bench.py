@@ -358,6 +358,7 @@ def run_ours(args, world, rank, local, pg):
     # ---- grouped batch of 512 uneven problems, and the serving loop (rank 0, default size only) ----
     grouped = grouped_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
     serving_rep = serving_measure() if (rank == 0 and not args.no_extras) else None
+    level3 = level3_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
 
     if rank != 0:
         return 0
@@ -400,6 +401,7 @@ def run_ours(args, world, rank, local, pg):
         "latency": lat,
         "grouped": grouped,
         "serving": serving_rep,
+        "level3": level3,
         "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
@@ -449,6 +451,54 @@ def modular_measure(dev, stream, A, B, C, steps: int, warmup: int):
     return {"ms": ms, "value": flops / (ms / 1000.0) / 1e12, "moduli": info.products, "bits": info.digit_bits,
             "bound_est": info.bound_est, "prep_ms": statistics.mean(prep), "products_ms": statistics.mean(prod),
             "steps": steps}
+
+
+def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
+    """Device time of the GEMM-based DSYRK, DTRMM and DTRSM (side L, lower, N, non-unit) at n,
+    native and emulated (each product at its FP64 bound), on well-conditioned triangles."""
+    import numpy as np
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm, synth
+    A = torch.from_numpy(synth.uniform_pm1(seed, n * n) / n).to(dev)
+    A.view(n, n).diagonal().add_(1.5)
+    B0 = torch.from_numpy(synth.uniform_pm1(seed + 1, n * n)).to(dev)
+    B = torch.empty_like(B0)
+    C = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    out = {"n": n, "config": "dsyrk L,N n=k; dtrmm/dtrsm side L, lower, N, non-unit, m=n; A/n + 1.5 I, B uniform[-1,1)",
+           "flops": {"dsyrk": float(n) * n * n, "dtrmm": float(n) * n * n, "dtrsm": float(n) * n * n}}
+    for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("emulated", gbdgemm.GBD_MODE_EMULATED)):
+        wsb = max(gbdgemm.gbd_dsyrk_workspace_size(n, n, mode), gbdgemm.gbd_dtrmm_workspace_size("L", n, n, mode),
+                  gbdgemm.gbd_dtrsm_workspace_size("L", n, n, mode))
+        ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+        calls = {
+            "dsyrk": lambda: gbdgemm.gbd_dsyrk("L", "N", n, n, 1.0, A, n, 0.0, C, n, mode, 0.0, ws, wsb, stream=stream),
+            "dtrmm": lambda: gbdgemm.gbd_dtrmm("L", "L", "N", "N", n, n, 1.0, A, n, B, n, mode, 0.0, ws, wsb,
+                                               stream=stream),
+            "dtrsm": lambda: gbdgemm.gbd_dtrsm("L", "L", "N", "N", n, n, 1.0, A, n, B, n, mode, 0.0, ws, wsb,
+                                               stream=stream),
+        }
+        res = {}
+        for op, fn in calls.items():
+            reps = 1 if mode == gbdgemm.GBD_MODE_NATIVE else 3
+            with torch.cuda.stream(stream):
+                B.copy_(B0)
+                gbdgemm.check(fn())  # warm-up
+                ev = _events(2 * reps)
+                for r in range(reps):
+                    B.copy_(B0)  # the triangular calls overwrite B: time each call alone
+                    ev[2 * r].record(stream)
+                    gbdgemm.check(fn())
+                    ev[2 * r + 1].record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.mean(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(reps))
+            res[op] = {"ms": ms, "tflops": out["flops"][op] / (ms / 1000.0) / 1e12}
+        gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+        out[name] = res
+        del ws
+    for op in ("dsyrk", "dtrmm", "dtrsm"):
+        out[op + "_emulated_over_native"] = out["emulated"][op]["tflops"] / out["native"][op]["tflops"]
+    return out
 
 
 def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
