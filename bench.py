@@ -1,14 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 DGEMM library: C := alpha*op(A)*op(B) + beta*C.
 
-Metric: DGEMM TFLOP/s (useful flops 2mnk per call) of the split emulation at
-FP64 accuracy (automatic slice count for the componentwise FP64 bound), with the
-native FP64-MMA path and the modular emulation (Ozaki scheme II, automatic
-integer bits for the same bound) measured beside it on the same inputs, on the large square
-workload m = n = k = 8192 (FP64 operands uniform on [-1, 1), N,N, alpha = 1,
-beta = 0; every input is larger than L2, so no flush is needed between timed
-calls).  The dominant kernel's roofline is the BF16 tensor peak (slice flops =
-products x 2mnk); the native path's is the FP64 peak.
+Metric: DGEMM TFLOP/s (useful flops 2mnk per call) of the emulated DGEMM at FP64
+accuracy -- the modular emulation (Ozaki scheme II: residues modulo coprime moduli,
+automatic integer bits for the componentwise FP64 bound) -- with the split emulation
+(automatic slices for the same bound) and the native FP64-MMA path measured beside it on
+the same inputs, on the large square workload m = n = k = 8192 (FP64 operands uniform on
+[-1, 1), N,N, alpha = 1, beta = 0; every input is larger than L2, so no flush is needed
+between timed calls).  The dominant kernel's roofline is the BF16 tensor peak (residue
+or slice products x 2mnk); the native path's is the FP64 peak.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -245,24 +245,22 @@ def run_ours(args, world, rank, local, pg):
     A = torch.from_numpy(A_h).to(dev)
     B = torch.from_numpy(B_h).to(dev)
     C = torch.zeros(M * N, dtype=torch.float64, device=dev)
-    wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
-    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     flops = 2.0 * M * N * K
+
+    # ---- the headline: the modular emulation, automatic integer bits at the FP64 bound ----
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, 0)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     info = gbdgemm.GbdEmuInfo()
 
-    def emu_step(s, record=False):
+    def mod_step(s, record=False):
         info.record_phases = 1 if record else 0
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
-                                            info, stream=s))
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
+                                                info, stream=s))
 
-    def native_step(s):
-        gbdgemm.check(gbdgemm.gbd_dgemm("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, stream=s))
-
-    # ---- emulated path (the timed steps): automatic slices at the FP64 bound ----
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            emu_step(stream)
+            mod_step(stream)
     torch.cuda.synchronize()
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
 
@@ -274,7 +272,7 @@ def run_ours(args, world, rank, local, pg):
     gemm_ms, prep_ms = [], []
     ev[0].record(stream)
     for i in range(args.steps):
-        emu_step(stream, record=True)
+        mod_step(stream, record=True)
         gemm_ms.append(info.gemm_ms)
         prep_ms.append(info.prep_ms)
         ev[i + 1].record(stream)
@@ -285,10 +283,16 @@ def run_ours(args, world, rank, local, pg):
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     total_ms = max_over_ranks(pg, total_ms, dev)
     value = replica_value(world, flops, args.steps, total_ms)
-    slices = info.slices
-    products = info.products
+    moduli, bits, bound_est = info.products, info.digit_bits, info.bound_est
+    del ws
+
+    # ---- the split emulation on the same inputs (automatic slices at the same bound) ----
+    split = split_measure(dev, stream, A, B, C, steps=max(3, min(args.steps, 10)), warmup=max(3, args.warmup))
 
     # ---- native path on the same inputs ----
+    def native_step(s):
+        gbdgemm.check(gbdgemm.gbd_dgemm("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, stream=s))
+
     nat_calls = 2
     with torch.cuda.stream(stream):
         native_step(stream)
@@ -302,26 +306,24 @@ def run_ours(args, world, rank, local, pg):
     nat_ms = statistics.mean(nev[i].elapsed_time(nev[i + 1]) for i in range(nat_calls))
     nat_tflops = flops / (nat_ms / 1000.0) / 1e12
 
-    # ---- the modular emulation (Ozaki scheme II) on the same inputs, automatic bits at the FP64 bound ----
-    mod = modular_measure(dev, stream, A, B, C, steps=max(3, args.steps), warmup=max(3, args.warmup))
-
     # ---- end to end through the host-buffer C-ABI call (pinned host memory), copies inside the region ----
-    # Each step is one gbd_dgemm_emu_host call: upload of A and B, the emulated product, download of C.
-    # Serial: one call at a time.  Overlapped (the reported value): two calls in flight on two streams
-    # with two device buffers, so one call's transfers run under the other's products.
+    # Each step is one gbd_dgemm_emu_mod_host call: upload of A and B, the emulated product, download of C.
+    # Serial: one call at a time.  Overlapped (the reported value): two host threads, each driving its own
+    # stream and device buffer, so one call's transfers run under the other's products (the automatic
+    # mode's statistics read-back blocks only the calling thread).
     A_p = torch.from_numpy(A_h).pin_memory()
     B_p = torch.from_numpy(B_h).pin_memory()
     C_p = [torch.empty(M * N, dtype=torch.float64).pin_memory() for _ in range(2)]
-    hsize = gbdgemm.gbd_dgemm_emu_host_buffer_size("N", "N", M, N, K, 0)
-    del ws  # the device-side workspace is not needed any more
+    hsize = gbdgemm.gbd_dgemm_emu_mod_host_buffer_size("N", "N", M, N, K, 0)
     hbufs = [torch.empty(hsize, dtype=torch.uint8, device=dev) for _ in range(2)]
     hstreams = [stream, torch.cuda.Stream(device=dev)]
-    hinfo = gbdgemm.GbdEmuInfo()
-    e2e_steps = max(2, min(args.steps, 6))
+    hinfo = [gbdgemm.GbdEmuInfo(), gbdgemm.GbdEmuInfo()]  # one per stream (and host thread)
+    # enough calls that the first upload and the last download, which nothing hides, weigh little
+    e2e_steps = max(4, min(args.steps, 16))
 
     def host_call(i):
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[i % 2], M, 0, 0.0,
-                                                 hbufs[i % 2], hsize, hinfo, stream=hstreams[i % 2]))
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[i % 2], M, 0,
+                                                     0.0, hbufs[i % 2], hsize, hinfo[i % 2], stream=hstreams[i % 2]))
 
     host_call(0)  # untimed warm-up of both buffers and streams (first use of the pinned memory)
     host_call(1)
@@ -340,8 +342,22 @@ def run_ours(args, world, rank, local, pg):
     e0, e1, last1 = _events(3)
     e0.record(hstreams[0])
     hstreams[1].wait_event(e0)
-    for i in range(e2e_steps):
-        host_call(i)
+    errors = []
+
+    def driver(t):
+        try:
+            for i in range(t, e2e_steps, 2):
+                host_call(i)
+        except Exception as exc:  # re-raised below, on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=driver, args=(t,)) for t in (0, 1)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    if errors:
+        raise errors[0]
     last1.record(hstreams[1])
     hstreams[0].wait_event(last1)
     e1.record(hstreams[0])
@@ -355,7 +371,7 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- latency of small calls (256^3, the latency configuration) ----
     lat = small_call_latency(dev, stream)
-    # ---- grouped batch of 512 uneven problems, and the serving loop (rank 0, default size only) ----
+    # ---- grouped batch of 512 uneven problems, the serving loop, level-3 BLAS (rank 0, default size only) ----
     grouped = grouped_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
     serving_rep = serving_measure() if (rank == 0 and not args.no_extras) else None
     level3 = level3_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
@@ -366,38 +382,39 @@ def run_ours(args, world, rank, local, pg):
     bf16_sust = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64 / NOMINAL_BF16
     g_ms = statistics.mean(gemm_ms)
-    slice_flops = products * flops
-    achieved = slice_flops / (g_ms / 1000.0) / 1e12
+    achieved = moduli * flops / (g_ms / 1000.0) / 1e12
+    s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=8.0)
-    mod_achieved = mod["moduli"] * flops / (mod["products_ms"] / 1000.0) / 1e12
-    modular = {
-        "value": mod["value"], "unit": "TFLOP/s", "ms_per_call": mod["ms"], "steps": mod["steps"],
-        "path": "emulated (Ozaki scheme II: residues modulo coprime moduli <= 256 on tcgen05 BF16, CRT; FP64 bound)",
-        "moduli": mod["moduli"], "integer_bits": mod["bits"], "bound_est": mod["bound_est"],
-        "phases_ms": {"prep": mod["prep_ms"], "products_and_reconstruction": mod["products_ms"]},
-        "over_split": mod["value"] / value, "over_native": mod["value"] / nat_tflops,
-        "roofline": {"bound": "tensor", "achieved": mod_achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                     "frac": mod_achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
-                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT)",
-                     "peak_source": f"{src} bf16_tflops_sustained"},
-    }
-    launches_per_step = 8  # exponents x2, magnitudes x2, statistics, split x2, slice product
+    # prep init, exponents, magnitudes, statistics, residues, column scales, residue products (+ CRT)
+    launches_per_step = 7
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(), "path": "emulated (split digits on tcgen05 BF16, FP64 bound)",
-                   "slices": slices, "products": products, "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)",
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": workload_name(),
+                   "path": "emulated at the FP64 bound: modular (Ozaki scheme II: residues modulo coprime moduli "
+                           "<= 256 on tcgen05 BF16, Chinese remainder reconstruction)",
+                   "moduli": moduli, "integer_bits": bits, "bound_est": bound_est,
+                   "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)", "parallelism": f"replicas x{world}"},
         "native": {"value": nat_tflops, "unit": "TFLOP/s", "ms_per_call": nat_ms, "frac_of_fp64_peak": nat_tflops / fp64_peak,
                    "fp64_peak": fp64_peak},
         "emulated_over_native": value / nat_tflops,
-        "modular": modular,
-        "phases_ms": {"prep": statistics.mean(prep_ms), "slice_gemm": g_ms},
+        "phases_ms": {"prep": statistics.mean(prep_ms), "products_and_reconstruction": g_ms},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                     "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
-                     "kernel": "k_slice_gemm (tcgen05 kind::f16, BF16 -> FP32)",
+                     "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
+                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT)",
                      "peak_source": f"{src} bf16_tflops_sustained"},
+        "split": {
+            "value": split["value"], "unit": "TFLOP/s", "ms_per_call": split["ms"], "steps": split["steps"],
+            "path": "emulated (split digits on tcgen05 BF16, FP64 bound)", "slices": split["slices"],
+            "products": split["products"], "over_native": split["value"] / nat_tflops,
+            "modular_over_split": value / split["value"],
+            "phases_ms": {"prep": split["prep_ms"], "slice_gemm": split["gemm_ms"]},
+            "roofline": {"bound": "tensor", "achieved": s_achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                         "frac": s_achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
+                         "kernel": "k_slice_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32)",
+                         "peak_source": f"{src} bf16_tflops_sustained"},
+        },
         "latency": lat,
         "grouped": grouped,
         "serving": serving_rep,
@@ -406,7 +423,7 @@ def run_ours(args, world, rank, local, pg):
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
                 "d2h_bytes_per_step": M * N * 8, "steps": e2e_steps,
-                "call": "gbd_dgemm_emu_host, pinned host A, B, C; two calls in flight on two streams",
+                "call": "gbd_dgemm_emu_mod_host, pinned host A, B, C; two host threads, one stream and buffer each",
                 "ms_per_step": e2e_ms / e2e_steps,
                 "serial": {"value": e2e_serial, "ms_per_step": serial_ms / e2e_steps}, "clocks": e2e_clocks},
         "gpu_launches": launches_per_step * args.steps,
@@ -416,20 +433,20 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
-def modular_measure(dev, stream, A, B, C, steps: int, warmup: int):
-    """Device time of gbd_dgemm_emu_mod on the headline inputs (automatic integer bits for the FP64
-    bound), its phases, and the rate of its product kernel."""
+def split_measure(dev, stream, A, B, C, steps: int, warmup: int):
+    """Device time of gbd_dgemm_emu (the split emulation) on the headline inputs (automatic slices
+    for the FP64 bound), and its phases."""
     import torch
 
     from paper_1609_00076_gb300 import gbdgemm
-    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, 0)
+    wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     info = gbdgemm.GbdEmuInfo()
 
     def step(record):
         info.record_phases = 1 if record else 0
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
-                                                info, stream=stream))
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
+                                            info, stream=stream))
 
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -447,9 +464,8 @@ def modular_measure(dev, stream, A, B, C, steps: int, warmup: int):
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     ms = ev[0].elapsed_time(ev[-1]) / steps
     del ws
-    flops = 2.0 * M * N * K
-    return {"ms": ms, "value": flops / (ms / 1000.0) / 1e12, "moduli": info.products, "bits": info.digit_bits,
-            "bound_est": info.bound_est, "prep_ms": statistics.mean(prep), "products_ms": statistics.mean(prod),
+    return {"ms": ms, "value": 2.0 * M * N * K / (ms / 1000.0) / 1e12, "slices": info.slices,
+            "products": info.products, "prep_ms": statistics.mean(prep), "gemm_ms": statistics.mean(prod),
             "steps": steps}
 
 
@@ -607,8 +623,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["grouped", "serving"],
-                    help="run only the grouped-batch or the serving measurement and print it (profiling)")
+    ap.add_argument("--only", choices=["grouped", "serving", "level3"],
+                    help="run only the grouped-batch, serving or level-3 measurement and print it (profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the grouped-batch and serving measurements (profiling runs)")
     ap.add_argument("--size", type=int, default=8192,
@@ -624,7 +640,13 @@ def main():
         from paper_1609_00076_gb300 import gbdgemm
         gbdgemm.load()
         dev = torch.device("cuda", 0)
-        res = grouped_measure(dev, torch.cuda.Stream(device=dev), reps=1) if args.only == "grouped" else serving_measure()
+        stream = torch.cuda.Stream(device=dev)
+        if args.only == "grouped":
+            res = grouped_measure(dev, stream, reps=1)
+        elif args.only == "level3":
+            res = level3_measure(dev, stream, n=args.size)
+        else:
+            res = serving_measure()
         print(json.dumps(res), flush=True)
         return 0
     world, rank, local, pg = dist_setup(args)

@@ -233,6 +233,18 @@ GBD_API int gbd_dgemm_emu_host(char transa, char transb, int64_t m, int64_t n, i
                                const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                                double* C, int64_t ldc, int slices, double tol, void* device_buffer,
                                size_t buffer_bytes, gbd_emu_info* info, void* stream);
+/*
+ * The same with the modular emulation (gbd_dgemm_emu_mod) on the device copies: `bits`,
+ * `tol`, `info` and the automatic-mode synchronisation as gbd_dgemm_emu_mod; the buffer
+ * as above, sized by gbd_dgemm_emu_mod_host_buffer_size.
+ */
+GBD_API size_t gbd_dgemm_emu_mod_host_buffer_size(char transa, char transb, int64_t m, int64_t n,
+                                                  int64_t k, int bits);
+GBD_API int gbd_dgemm_emu_mod_host(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                   double alpha, const double* A, int64_t lda, const double* B,
+                                   int64_t ldb, double beta, double* C, int64_t ldc, int bits,
+                                   double tol, void* device_buffer, size_t buffer_bytes,
+                                   gbd_emu_info* info, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Grouped calls: many independent problems per launch                       */

@@ -115,6 +115,9 @@ _EXTRA_DECLS: list = [
     ("gbd_dtrmm", [_c, _c, _c, _c, _i64, _i64, _d, _vp, _i64, _vp, _i64, _i, _d, _vp, _sz, _vp], _i),
     ("gbd_dtrsm", [_c, _c, _c, _c, _i64, _i64, _d, _vp, _i64, _vp, _i64, _i, _d, _vp, _sz, _vp], _i),
     ("gbd_dgemm_emu_host_buffer_size", [_c, _c, _i64, _i64, _i64, _i], _sz),
+    ("gbd_dgemm_emu_mod_host_buffer_size", [_c, _c, _i64, _i64, _i64, _i], _sz),
+    ("gbd_dgemm_emu_mod_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
+                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                             ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_watchdog_selftest", [_i, _vp], _i),
@@ -284,6 +287,21 @@ def gbd_dgemm_emu_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, 
                                      int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(slices),
                                      float(tol), _addr(buffer), int(buffer_bytes),
                                      ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_dgemm_emu_mod_host_buffer_size(transa, transb, m, n, k, bits=0) -> int:
+    """Device buffer bytes of gbd_dgemm_emu_mod_host (packed A, B, C and the modular workspace)."""
+    return int(load().gbd_dgemm_emu_mod_host_buffer_size(_t(transa), _t(transb), int(m), int(n), int(k),
+                                                         int(bits)))
+
+
+def gbd_dgemm_emu_mod_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bits, tol, buffer,
+                           buffer_bytes, info=None, stream=None) -> int:
+    """gbd_dgemm_emu_mod with A, B and C in host memory and a caller-owned device buffer."""
+    return load().gbd_dgemm_emu_mod_host(_t(transa), _t(transb), int(m), int(n), int(k), float(alpha), _addr(A),
+                                         int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(bits),
+                                         float(tol), _addr(buffer), int(buffer_bytes),
+                                         ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
 def problem_array(problems) -> ctypes.Array:

@@ -117,3 +117,35 @@ def test_two_streams_in_flight():
     for A, lda, B, ldb, C0, ldc, Ct in jobs:
         ref = _device_reference("N", "T", m, n, k, 1.0, A, lda, B, ldb, 0.5, C0, ldc, 6)
         assert np.array_equal(synth.view(Ct.numpy(), m, n, ldc).view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("m,n,k,ta,tb,alpha,beta,bits,pinned", [
+    (300, 257, 199, "N", "N", 1.5, -0.5, 0, True),
+    (129, 400, 1000, "T", "N", -1.0, 0.0, 40, False),
+    (200, 133, 517, "N", "T", 0.75, 2.0, 0, False),
+])
+def test_modular_host_call_matches_the_model(oracle_mod, m, n, k, ta, tb, alpha, beta, bits, pinned):
+    import torch
+    A, lda, B, ldb, C0, ldc = _operands(950 + m, m, n, k, ta, tb, pad=3)
+    C = C0.copy()
+    hA, hB, hC = (torch.from_numpy(x) for x in (A, B, C))
+    if pinned:
+        hA, hB, hC = hA.pin_memory(), hB.pin_memory(), hC.pin_memory()
+    size = gbdgemm.gbd_dgemm_emu_mod_host_buffer_size(ta, tb, m, n, k, bits)
+    buf = torch.empty(size, dtype=torch.uint8, device="cuda")
+    info = gbdgemm.GbdEmuInfo()
+    rc = gbdgemm.gbd_dgemm_emu_mod_host(ta, tb, m, n, k, alpha, hA, lda, hB, ldb, beta, hC, ldc, bits, 0.0, buf, size,
+                                        info)
+    assert rc == 0, gbdgemm.gbd_last_error()
+    torch.cuda.synchronize()
+    out = hC.numpy()
+    assert padding_intact(out, m, n, ldc)
+    assert bits == 0 or info.digit_bits == bits
+    ref = oracle_mod.ozmod_dgemm_rows(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc, info.digit_bits)
+    assert first_mismatch(synth.view(out, m, n, ldc).flatten(order="F"), ref, None, m) is None
+    if bits == 0:
+        G = oracle_mod.abs_bound_rows(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc)
+        want = oracle_mod.dgemm_rows(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc)
+        assert first_mismatch(synth.view(out, m, n, ldc).flatten(order="F"), want, 2 * k * U * G, m) is None
+    assert gbdgemm.gbd_dgemm_emu_mod_host(ta, tb, m, n, k, alpha, hA, lda, hB, ldb, beta, hC, ldc, bits, 0.0, buf,
+                                          64) == gbdgemm.GBD_ERR_WORKSPACE
