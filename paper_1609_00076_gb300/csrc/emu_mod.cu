@@ -621,11 +621,14 @@ int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
   return t < 0 ? t + p : t;
 }
 
-// Estimated componentwise relative error of t integer bits, from the magnitude statistics
-// (as the slice count of the split emulation): 2^(-t-1) (2k + k 2^(-t-1)) / (mu nu / (8k)).
+// Estimated componentwise relative error of t integer bits, from the magnitude statistics:
+// the rounding error 2^(sigma_i + tau_j - t - 1) (mu_i + nu_j + k 2^(-t-1)) over the estimate
+// 2^(sigma_i + tau_j) mu_i nu_j / (8k) of (|A||B|)_ij (a safety factor of 8, as the slice count
+// of the split emulation), maximised over i, j by the smallest mu and nu:
+// 2^(-t-1) 8k (1/nu + 1/mu + k 2^(-t-1) / (mu nu)).
 double mod_relative_bound(int t, double mu_min, double nu_min, int64_t k) {
   const double kd = (double)k;
-  return ldexp(1.0, -t - 1) * (2.0 * kd + kd * ldexp(1.0, -t - 1)) / (mu_min * nu_min / kd / 8.0);
+  return ldexp(1.0, -t - 1) * 8.0 * kd * (1.0 / nu_min + 1.0 / mu_min + kd * ldexp(1.0, -t - 1) / (mu_min * nu_min));
 }
 
 int choose_bits(double tol, double mu_min, double nu_min, int64_t k, double* bound) {
