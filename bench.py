@@ -248,15 +248,16 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     flops = 2.0 * M * N * K
 
-    # ---- the headline: the modular emulation, automatic integer bits at the FP64 bound ----
-    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, 0)
+    # ---- the headline: the modular emulation, integer bits chosen on the device for the FP64 bound ----
+    # (bits = -1: no host round trip inside a call; the timed steps pass no info, so nothing synchronises)
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, -1)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     info = gbdgemm.GbdEmuInfo()
 
-    def mod_step(s, record=False):
-        info.record_phases = 1 if record else 0
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
-                                                info, stream=s))
+    def mod_step(s, report=False):
+        info.record_phases = 1 if report else 0
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, -1, 0.0, ws, wsb,
+                                                info if report else None, stream=s))
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -269,12 +270,9 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     sampler.start()
     ev = _events(args.steps + 1)
-    gemm_ms, prep_ms = [], []
     ev[0].record(stream)
     for i in range(args.steps):
-        mod_step(stream, record=True)
-        gemm_ms.append(info.gemm_ms)
-        prep_ms.append(info.prep_ms)
+        mod_step(stream)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier(pg)
@@ -283,6 +281,12 @@ def run_ours(args, world, rank, local, pg):
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     total_ms = max_over_ranks(pg, total_ms, dev)
     value = replica_value(world, flops, args.steps, total_ms)
+    # phases and the device's choice, from three further calls that read them back (untimed above)
+    gemm_ms, prep_ms = [], []
+    for _ in range(3):
+        mod_step(stream, report=True)
+        gemm_ms.append(info.gemm_ms)
+        prep_ms.append(info.prep_ms)
     moduli, bits, bound_est = info.products, info.digit_bits, info.bound_est
     del ws
 
@@ -309,21 +313,19 @@ def run_ours(args, world, rank, local, pg):
     # ---- end to end through the host-buffer C-ABI call (pinned host memory), copies inside the region ----
     # Each step is one gbd_dgemm_emu_mod_host call: upload of A and B, the emulated product, download of C.
     # Serial: one call at a time.  Overlapped (the reported value): two host threads, each driving its own
-    # stream and device buffer, so one call's transfers run under the other's products (the automatic
-    # mode's statistics read-back blocks only the calling thread).
+    # stream and device buffer, so one call's transfers run under the other's products.
     A_p = torch.from_numpy(A_h).pin_memory()
     B_p = torch.from_numpy(B_h).pin_memory()
     C_p = [torch.empty(M * N, dtype=torch.float64).pin_memory() for _ in range(2)]
-    hsize = gbdgemm.gbd_dgemm_emu_mod_host_buffer_size("N", "N", M, N, K, 0)
+    hsize = gbdgemm.gbd_dgemm_emu_mod_host_buffer_size("N", "N", M, N, K, -1)
     hbufs = [torch.empty(hsize, dtype=torch.uint8, device=dev) for _ in range(2)]
     hstreams = [stream, torch.cuda.Stream(device=dev)]
-    hinfo = [gbdgemm.GbdEmuInfo(), gbdgemm.GbdEmuInfo()]  # one per stream (and host thread)
     # enough calls that the first upload and the last download, which nothing hides, weigh little
     e2e_steps = max(4, min(args.steps, 16))
 
     def host_call(i):
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[i % 2], M, 0,
-                                                     0.0, hbufs[i % 2], hsize, hinfo[i % 2], stream=hstreams[i % 2]))
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[i % 2], M, -1,
+                                                     0.0, hbufs[i % 2], hsize, None, stream=hstreams[i % 2]))
 
     host_call(0)  # untimed warm-up of both buffers and streams (first use of the pinned memory)
     host_call(1)
@@ -385,15 +387,15 @@ def run_ours(args, world, rank, local, pg):
     achieved = moduli * flops / (g_ms / 1000.0) / 1e12
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=8.0)
-    # prep init, exponents, magnitudes, statistics, residues, column scales, residue products (+ CRT)
-    launches_per_step = 7
+    # prep init, exponents, magnitudes, statistics, plan, residues, column scales, residue products (+ CRT)
+    launches_per_step = 8
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(),
                    "path": "emulated at the FP64 bound: modular (Ozaki scheme II: residues modulo coprime moduli "
-                           "<= 256 on tcgen05 BF16, Chinese remainder reconstruction)",
+                           "<= 256 on tcgen05 BF16, Chinese remainder reconstruction; bits chosen on the device)",
                    "moduli": moduli, "integer_bits": bits, "bound_est": bound_est,
                    "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)", "parallelism": f"replicas x{world}"},
         "native": {"value": nat_tflops, "unit": "TFLOP/s", "ms_per_call": nat_ms, "frac_of_fp64_peak": nat_tflops / fp64_peak,
@@ -423,7 +425,8 @@ def run_ours(args, world, rank, local, pg):
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
                 "d2h_bytes_per_step": M * N * 8, "steps": e2e_steps,
-                "call": "gbd_dgemm_emu_mod_host, pinned host A, B, C; two host threads, one stream and buffer each",
+                "call": "gbd_dgemm_emu_mod_host (bits = -1), pinned host A, B, C; two host threads, one stream and "
+                        "buffer each",
                 "ms_per_step": e2e_ms / e2e_steps,
                 "serial": {"value": e2e_serial, "ms_per_step": serial_ms / e2e_steps}, "clocks": e2e_clocks},
         "gpu_launches": launches_per_step * args.steps,

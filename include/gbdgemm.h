@@ -182,14 +182,22 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
  * correctly rounded.  The products number n (13 at 44 bits and k = 8192) where the split
  * emulation needs s(s+1)/2.
  *
- * bits: t in 1..62, or 0 to choose the smallest t whose estimated componentwise error
- *   stays below `tol` (as for gbd_dgemm_emu; tol <= 0 means 2 k 2^-53).  Automatic mode
- *   reads 16 bytes back and so synchronises `stream`.  When t (given or chosen) needs
- *   more than 16 moduli at this k the call returns GBD_ERR_LIMIT (gbd_dgemm_emu covers
- *   any target).
+ * bits: t in 1..62, or automatic: the smallest t whose estimated componentwise error
+ *   stays below `tol` (tol <= 0 means 2 k 2^-53), chosen on the device from the row and
+ *   column magnitude sums, the same way in both automatic forms:
+ *     0: the choice is read back (the call synchronises `stream` once); when it needs more
+ *        than 16 moduli at this k the call returns GBD_ERR_LIMIT before touching C
+ *        (gbd_dgemm_emu covers any target);
+ *    -1: nothing is read back and the call never synchronises; an unreachable target fills
+ *        C with NaN and sets the device error word, which gbd_check_device_error reports
+ *        as GBD_ERR_LIMIT.
+ *   Given t that needs more than 16 moduli returns GBD_ERR_LIMIT.
  * workspace: at least gbd_dgemm_emu_mod_workspace_size(m, n, k, bits) bytes, 256-byte
- *   aligned (bits = 0 sizes it for 16 moduli); as for gbd_dgemm_emu.
- * info: optional; slices and products report n, digit_bits reports t.
+ *   aligned (bits <= 0 sizes it for 16 moduli); as for gbd_dgemm_emu.
+ * info: optional; slices and products report n, digit_bits reports t, bound_est the
+ *   estimate (automatic modes); with bits = -1 a non-NULL info is filled by reading the
+ *   choice back, which synchronises `stream`.  record_phases times the preparation
+ *   (prep_ms) and the products with the reconstruction (gemm_ms).
  * Returns 0, a BLAS argument index, or GBD_ERR_*.
  */
 GBD_API size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits);
@@ -326,9 +334,11 @@ GBD_API int gbd_watchdog_selftest(int limit_ms, void* stream);
 
 /*
  * Reads and clears the device error word of the current device that the
- * kernels set when a bounded wait gives up.  Synchronises `stream` first.
- * Returns 0 when no wait gave up since the last call, GBD_ERR_TIMEOUT when one
- * did, or GBD_ERR_CUDA.
+ * kernels set when a bounded wait gives up (or when a gbd_dgemm_emu_mod call in
+ * device-side automatic mode, bits = -1, met an unreachable target).  Synchronises
+ * `stream` first.  Returns 0 when nothing was recorded since the last call,
+ * GBD_ERR_LIMIT when only such a modular call was, GBD_ERR_TIMEOUT when a wait gave
+ * up, or GBD_ERR_CUDA.
  */
 GBD_API int gbd_check_device_error(void* stream);
 

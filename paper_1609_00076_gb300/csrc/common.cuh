@@ -47,6 +47,7 @@ constexpr unsigned int kErrWaitMma = 2u;     // a wait for MMA completion gave u
 constexpr unsigned int kErrWaitEpi = 4u;     // a wait for the epilogue gave up
 constexpr unsigned int kErrWaitSlot = 8u;    // a producer wait for a free stage gave up
 constexpr unsigned int kErrTmemAlloc = 16u;  // TMEM allocation was not granted
+constexpr unsigned int kErrModRange = 32u;   // a device-side automatic modular call needed more than 16 moduli
 
 // time limit of every device-side wait, in nanoseconds of %globaltimer
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s

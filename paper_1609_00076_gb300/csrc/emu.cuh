@@ -109,13 +109,22 @@ constexpr int kMaxModuli = 16;  // the product of the moduli stays below 2^126
 // residue is at most 128 in magnitude: exact in BF16, products at most 2^14
 constexpr int kModuli[kMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
                                      229, 227, 223, 217, 211, 199, 197, 193};
-// residue split parameters: t integer bits (<= 62), the first n moduli (as float), 1/p, and
-// 256^d mod p for d = 0..3 (wlo) and 4..7 (whi) packed one byte per d
+// The modular emulation's choice for one call, written on the device (so that the automatic
+// mode needs no host round trip) and read by every later kernel of the call.
+struct ModPlan {
+  int t;         // integer bits
+  int n;         // moduli used (1 when infeasible)
+  int feasible;  // 0: the target needs more than kMaxModuli moduli; the call writes NaN
+  int pad;
+  double mu, nu, bound;  // the magnitude statistics and the estimated bound (automatic mode)
+};
+// residue split parameters: all kMaxModuli moduli (as float), 1/p, and 256^d mod p for
+// d = 0..3 (wlo) and 4..7 (whi) packed one byte per d; t and n come from the plan
 struct ModSplit {
-  int n, t;
   float pf[kMaxModuli];
   float inv[kMaxModuli];
   uint32_t wlo[kMaxModuli], whi[kMaxModuli];
+  const ModPlan* plan;
 };
 // residue slices D[i][r][kp] of both sides (slices = n) from the rounded scaled integers
 int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_blocks, cudaStream_t s);

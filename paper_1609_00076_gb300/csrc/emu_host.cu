@@ -52,9 +52,8 @@ int host_call(bool modular, char transa, char transb, int64_t m, int64_t n, int6
   const char* name = modular ? "dgemm_emu_mod_host" : "dgemm_emu_host";
   int rc = gbd::check_dgemm_args(transa, transb, m, n, k, lda, ldb, ldc);
   if (rc) return rc;
-  if (modular ? (digits < 0 || digits > 62) : (digits < 0 || digits > gbd::emu::kMaxSlices))
-    return gbd::set_error(GBD_ERR_ARG, "%s: %s must be 0 (automatic) or 1..%d", name, modular ? "bits" : "slices",
-                          modular ? 62 : gbd::emu::kMaxSlices);
+  if (modular ? (digits < -1 || digits > 62) : (digits < 0 || digits > gbd::emu::kMaxSlices))
+    return gbd::set_error(GBD_ERR_ARG, "%s: %s out of range", name, modular ? "bits" : "slices");
   if (m == 0 || n == 0) return GBD_OK;  // nothing to compute or copy
   const HostLayout L = host_layout(transa, transb, m, n, k, digits, modular);
   if (!device_buffer || buffer_bytes < L.total || (reinterpret_cast<uintptr_t>(device_buffer) & (kAlign - 1)))

@@ -37,16 +37,22 @@ constexpr int64_t kLStride = (int64_t)kSlotCols * 128;
 constexpr int64_t kSlotBytes = (int64_t)kMaxModuli * kLStride;
 constexpr int kMaxModCtas = 256;
 
-struct ModArgs {
-  int64_t m, n, ldc;
-  int nkb, nmod;
-  int tiles_m, num_tiles, group_m;
-  int p[kMaxModuli];            // moduli
+// the reconstruction constants of the first n moduli (M = p_0 ... p_(n-1))
+struct CrtSet {
   int c[kMaxModuli];            // (M/p_l)^-1 mod p_l
-  uint32_t bar[kMaxModuli];     // floor(2^32 / p_l), for Barrett reduction
-  uint32_t rq[kMaxModuli];      // ceil(2^24 / p_l)
   uint32_t mpl[kMaxModuli][4];  // M/p_l in 32-bit limbs, least significant first
   uint64_t M_lo, M_hi, half_lo, half_hi;  // M and floor(M/2)
+};
+
+struct ModArgs {
+  int64_t m, n, ldc;
+  int nkb;
+  int tiles_m, num_tiles, group_m;
+  int p[kMaxModuli];         // moduli
+  uint32_t bar[kMaxModuli];  // floor(2^32 / p_l), for Barrett reduction
+  uint32_t rq[kMaxModuli];   // ceil(2^24 / p_l)
+  CrtSet set[kMaxModuli];    // set[n - 1]: the constants for the first n moduli
+  const ModPlan* plan;       // the call's n (and whether the target was reachable)
   double beta;
   double* C;
   const int* sigA;
@@ -74,26 +80,27 @@ __device__ __forceinline__ u128 make_u128(uint64_t hi, uint64_t lo) { return ((u
 // C' from its parked bytes u_l = (C' mod p_l) c_l mod p_l: sum_l u_l (M/p_l) = (C' mod M) + q M
 // with q = floor(sum_l u_l / p_l).  Returns the representative of (-M/2, M/2] in two's
 // complement 128 bits.
-__device__ __forceinline__ u128 crt_combine(const uint32_t (&u)[kMaxModuli], const ModArgs& p) {
+__device__ __forceinline__ u128 crt_combine(const uint32_t (&u)[kMaxModuli], const ModArgs& p, const CrtSet& cs,
+                                            int nmod) {
   uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // limb sums, each below 16 * 255 * 2^32 < 2^44
   uint32_t qfix = 0;                         // sum_l u_l ceil(2^24/p_l) < 2^29
 #pragma unroll
   for (int l = 0; l < kMaxModuli; ++l) {
-    if (l < p.nmod) {
-      a0 += (uint64_t)u[l] * p.mpl[l][0];
-      a1 += (uint64_t)u[l] * p.mpl[l][1];
-      a2 += (uint64_t)u[l] * p.mpl[l][2];
-      a3 += (uint64_t)u[l] * p.mpl[l][3];
+    if (l < nmod) {
+      a0 += (uint64_t)u[l] * cs.mpl[l][0];
+      a1 += (uint64_t)u[l] * cs.mpl[l][1];
+      a2 += (uint64_t)u[l] * cs.mpl[l][2];
+      a3 += (uint64_t)u[l] * cs.mpl[l][3];
       qfix += u[l] * p.rq[l];
     }
   }
   const u128 s = (u128)a0 + ((u128)a1 << 32) + ((u128)a2 << 64) + ((u128)a3 << 96);  // modulo 2^128
   // qfix / 2^24 exceeds sum_l u_l/p_l by less than 16 * 255 / 2^24, so its floor is q or q + 1
-  const u128 M = make_u128(p.M_hi, p.M_lo);
+  const u128 M = make_u128(cs.M_hi, cs.M_lo);
   u128 cu = s - (u128)(qfix >> 24) * M;
   if ((uint64_t)(cu >> 127)) cu += M;  // the estimate was one too large
   else if (cu >= M) cu -= M;
-  const u128 half = make_u128(p.half_hi, p.half_lo);
+  const u128 half = make_u128(cs.half_hi, cs.half_lo);
   return cu > half ? cu - M : cu;
 }
 
@@ -137,11 +144,13 @@ __device__ __forceinline__ double scaled_double(u128 v, int sig) {
 // 128) and COLS columns of the TBN-wide tile.  Per modulus: drain the chunks into int32 sums,
 // park u_l; at each modulus boundary (sums dead), reconstruct a few groups of four columns of
 // the previous tile from its parked bytes and write them to C.  All loads of a group are
-// issued before its arithmetic, so a group waits for memory once.
+// issued before its arithmetic, so a group waits for memory once.  nan_out: the plan found the
+// target unreachable; every result is NaN.
 template <int EPI_WARPS, int TBN, bool PAIR>
-__device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_base, uint64_t* acc_full,
-                                             uint64_t* acc_empty, int warp, int lane, int tile0, int tile_step,
-                                             int tbm, int row_off) {
+__device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool nan_out, uint32_t tmem_base,
+                                             uint64_t* acc_full, uint64_t* acc_empty, int warp, int lane, int tile0,
+                                             int tile_step, int tbm, int row_off) {
+  const CrtSet& cset = p.set[nmod - 1];
   constexpr int COLS = TBN / (EPI_WARPS / 4);
   const int ew = warp - 2;
   const int quad = warp & 3;
@@ -156,7 +165,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
   }
   uint8_t* const scr_cta = p.scr + (int64_t)blockIdx.x * 2 * kSlotBytes + (int64_t)(col0 / 4) * 512 + row * 4;
   constexpr int kGroups = COLS / 4;
-  const int per_boundary = (kGroups + p.nmod - 1) / p.nmod;  // groups of four columns
+  const int per_boundary = (kGroups + nmod - 1) / nmod;  // groups of four columns
 
   // the pending reconstruction: this thread's row and columns of the previous tile
   bool pd_active = false, pd_bad = false;
@@ -172,7 +181,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
       uint32_t w4[kMaxModuli];  // the bytes of columns c0..c0+3, one word per modulus
 #pragma unroll
       for (int l = 0; l < kMaxModuli; ++l)
-        w4[l] = l < p.nmod ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
+        w4[l] = l < nmod ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
       double c0v[4], csv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -188,8 +197,8 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
         for (int l = 0; l < kMaxModuli; ++l) u[l] = (w4[l] >> (8 * q)) & 0xFFu;
         const double w0 = p.beta != 0.0 ? p.beta * c0v[q] : 0.0;
         double w;
-        if (pd_bad || csv[q] != csv[q]) w = __longlong_as_double(0x7FF8000000000000ll);
-        else w = fma(csv[q], scaled_double(crt_combine(u, p), pd_sig), w0);
+        if (nan_out || pd_bad || csv[q] != csv[q]) w = __longlong_as_double(0x7FF8000000000000ll);
+        else w = fma(csv[q], scaled_double(crt_combine(u, p, cset, nmod), pd_sig), w0);
         pd_c[(int64_t)(c0 + q) * p.ldc] = w;
       }
     }
@@ -207,7 +216,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
     const int64_t jc0 = (int64_t)tn * TBN + col0;
     const int slot = tcount & 1;
     uint8_t* const ub = scr_cta + (int64_t)slot * kSlotBytes;
-    for (int l = 0; l < p.nmod; ++l) {
+    for (int l = 0; l < nmod; ++l) {
       const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
 #pragma unroll
       for (int c = 0; c < COLS; ++c) acc[c] = 0;
@@ -233,7 +242,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
           for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
         }
       }
-      const uint32_t cl = (uint32_t)p.c[l];
+      const uint32_t cl = (uint32_t)cset.c[l];
 #pragma unroll
       for (int g = 0; g < kGroups; ++g) {
         uint32_t w = 0u;
@@ -242,7 +251,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, uint32_t tmem_bas
           w |= mod_barrett((uint32_t)mod_nonneg(acc[4 * g + b], pm, bm) * cl, pm, bm) << (8 * b);
         *reinterpret_cast<uint32_t*>(ub + l * kLStride + g * 512) = w;
       }
-      if (pd_active) advance(l + 1 == p.nmod ? kGroups : per_boundary);
+      if (pd_active) advance(l + 1 == nmod ? kGroups : per_boundary);
     }
     // this tile's residues are complete: it becomes the pending reconstruction
     const bool row_ok = i < p.m;
@@ -322,6 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
+  const int nmod = plan.n;
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
         int tm, tn;
         tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-        for (int l = 0; l < p.nmod; ++l)
+        for (int l = 0; l < nmod; ++l)
           for (int kb = 0; kb < p.nkb; ++kb) {
             mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             mbar_arrive_expect_tx(&full[stage], bytes);
@@ -349,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
       for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-        for (int l = 0; l < p.nmod; ++l)
+        for (int l = 0; l < nmod; ++l)
           for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
             const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
             mbar_wait(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
@@ -374,8 +385,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    mod_epilogue<kEpiWarps, kBN, false>(p, tmem_base, acc_full, acc_empty, warp, lane, blockIdx.x, gridDim.x, kBM,
-                                        0);
+    mod_epilogue<kEpiWarps, kBN, false>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, warp, lane,
+                                        blockIdx.x, gridDim.x, kBM, 0);
   }
 
   tc_fence_before();
@@ -454,6 +465,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
   cluster_sync_all();  // the peer's barriers are initialised and its TMEM is allocated
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
+  const int nmod = plan.n;
 
   if (warp == 0) {
     // ------------------------------ TMA producer (both CTAs) ------------------------------
@@ -465,7 +478,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
         tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
         const int m0 = tm * k2BM + (int)rank * 128;
         const int nb0 = tn * k2BN + (int)rank * 128;
-        for (int l = 0; l < p.nmod; ++l)
+        for (int l = 0; l < nmod; ++l)
           for (int kb = 0; kb < p.nkb; ++kb) {
             mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
@@ -484,7 +497,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
       for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs)
-        for (int l = 0; l < p.nmod; ++l)
+        for (int l = 0; l < nmod; ++l)
           for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
             const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
             mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
@@ -509,8 +522,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     __syncwarp();
   } else {
-    mod_epilogue<k2EpiWarps, k2BN, true>(p, tmem_base, acc_full, acc_empty, warp, lane, pair_id, num_pairs, k2BM,
-                                         (int)rank * 128);
+    mod_epilogue<k2EpiWarps, k2BN, true>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, warp, lane,
+                                         pair_id, num_pairs, k2BM, (int)rank * 128);
   }
 
   tc_fence_before();
@@ -525,11 +538,83 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
 
 // alpha 2^(tau_j - 2t) for every column (NaN for a column with a non-finite entry)
 __global__ void __launch_bounds__(256) k_mod_colscale(const int* __restrict__ sigB, const int* __restrict__ badB,
-                                                      int64_t n, double alpha, int t, double* __restrict__ cs) {
+                                                      int64_t n, double alpha, const ModPlan* __restrict__ plan,
+                                                      double* __restrict__ cs) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
+  const int t = plan->t;
   const int tau = sigB[j] == kExpEmpty ? 0 : sigB[j];
   cs[j] = badB[j] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(alpha, tau - 2 * t);
+}
+
+typedef unsigned __int128 hu128;
+
+// products of the first n moduli, n = 1..kMaxModuli
+struct ModProducts {
+  uint64_t lo[kMaxModuli], hi[kMaxModuli];
+};
+
+// fewest moduli whose product exceeds 2 k 2^(2t) >= 2 max |A'B'|; 0 when none is enough
+__host__ __device__ int moduli_for_products(int t, int64_t k, const ModProducts& mp) {
+  if (t < 1 || k < 1) return 0;
+  // k > 2^(kb-1): from 2t + kb >= 126 on, 2 k 2^(2t) > 2^126 exceeds every product;
+  // below it, 2 k 2^(2t) < 2^127 is computed exactly
+  int kb = 0;
+  while (((int64_t)1 << kb) < k) ++kb;
+  if (2 * t + kb >= 126) return 0;
+  const hu128 need = ((hu128)2 * (hu128)k) << (2 * t);
+  for (int n = 1; n <= kMaxModuli; ++n)
+    if ((((hu128)mp.hi[n - 1] << 64) | mp.lo[n - 1]) > need) return n;
+  return 0;
+}
+
+// Estimated componentwise relative error of t integer bits, from the magnitude statistics:
+// the rounding error 2^(sigma_i + tau_j - t - 1) (mu_i + nu_j + k 2^(-t-1)) over the estimate
+// 2^(sigma_i + tau_j) mu_i nu_j / (8k) of (|A||B|)_ij (a safety factor of 8, as the slice count
+// of the split emulation), maximised over i, j by the smallest mu and nu:
+// 2^(-t-1) 8k (1/nu + 1/mu + k 2^(-t-1) / (mu nu)).
+__host__ __device__ double mod_relative_bound(int t, double mu_min, double nu_min, int64_t k) {
+  const double kd = (double)k;
+  return ldexp(1.0, -t - 1) * 8.0 * kd * (1.0 / nu_min + 1.0 / mu_min + kd * ldexp(1.0, -t - 1) / (mu_min * nu_min));
+}
+
+// The call's plan, on one thread: t given (fixed_t > 0), or the smallest t whose estimated
+// bound meets `tol` from the magnitude statistics; then n.  When no n <= kMaxModuli suffices
+// the plan is marked infeasible (n = 1, t = 1: the kernels then write NaN) and, for the
+// device-side automatic mode (`flag`), the device error word records it.
+__global__ void k_mod_plan(const float* __restrict__ stats, int64_t k, double tol, int fixed_t,
+                           const __grid_constant__ ModProducts mp, ModPlan* __restrict__ plan, unsigned int* err,
+                           int flag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mu = 0.0, nu = 0.0, bound = 0.0;
+  int t = fixed_t;
+  if (fixed_t <= 0) {
+    mu = stats[0] < 1e38f ? stats[0] : 0.0;
+    nu = stats[1] < 1e38f ? stats[1] : 0.0;
+    t = 1;
+    if (mu > 0.0 && nu > 0.0) {
+      t = 63;
+      for (int tt = 1; tt <= 62; ++tt) {
+        const double b = mod_relative_bound(tt, mu, nu, k);
+        if (b <= tol) {
+          t = tt;
+          bound = b;
+          break;
+        }
+      }
+    }
+  }
+  const int n = moduli_for_products(t, k, mp);
+  ModPlan pl;
+  pl.t = n ? t : 1;
+  pl.n = n ? n : 1;
+  pl.feasible = n != 0;
+  pl.pad = t;  // the bits the target asked for (also when infeasible)
+  pl.mu = mu;
+  pl.nu = nu;
+  pl.bound = bound;
+  *plan = pl;
+  if (!n && flag) atomicOr(err, kErrModRange);
 }
 
 // ---- host side ----
@@ -541,6 +626,7 @@ struct ModWorkspace {
   unsigned long long* muA;
   unsigned long long* muB;
   float* stats;
+  ModPlan* plan;
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
   uint16_t* DB;  // [nmod][n][kp]
@@ -565,6 +651,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_muA = off; off = up(off + sizeof(unsigned long long) * (size_t)m);
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
+  const size_t o_plan = off; off = up(off + sizeof(ModPlan));
   const size_t o_cs = off; off = up(off + sizeof(double) * (size_t)n);
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
@@ -578,6 +665,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->muA = reinterpret_cast<unsigned long long*>(b + o_muA);
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
+    ws->plan = reinterpret_cast<ModPlan*>(b + o_plan);
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -588,28 +676,19 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   return off;
 }
 
-typedef unsigned __int128 hu128;
-
-// product of the first n moduli
-hu128 moduli_product(int n) {
+// products of the first n moduli
+ModProducts moduli_products() {
+  ModProducts mp;
   hu128 M = 1;
-  for (int l = 0; l < n; ++l) M *= (hu128)kModuli[l];
-  return M;
+  for (int l = 0; l < kMaxModuli; ++l) {
+    M *= (hu128)kModuli[l];
+    mp.lo[l] = (uint64_t)M;
+    mp.hi[l] = (uint64_t)(M >> 64);
+  }
+  return mp;
 }
 
-// fewest moduli whose product exceeds 2 k 2^(2t) >= 2 max |A'B'|; 0 when none is enough
-int moduli_for(int t, int64_t k) {
-  if (t < 1 || k < 1) return 0;
-  // k > 2^(kb-1): from 2t + kb >= 126 on, 2 k 2^(2t) > 2^126 exceeds every product;
-  // below it, 2 k 2^(2t) < 2^127 is computed exactly
-  int kb = 0;
-  while (((int64_t)1 << kb) < k) ++kb;
-  if (2 * t + kb >= 126) return 0;
-  const hu128 need = ((hu128)2 * (hu128)k) << (2 * t);
-  for (int n = 1; n <= kMaxModuli; ++n)
-    if (moduli_product(n) > need) return n;
-  return 0;
-}
+int moduli_for(int t, int64_t k) { return moduli_for_products(t, k, moduli_products()); }
 
 int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
   int64_t t = 0, nt = 1, r = p, nr = ((a % p) + p) % p;
@@ -621,32 +700,12 @@ int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
   return t < 0 ? t + p : t;
 }
 
-// Estimated componentwise relative error of t integer bits, from the magnitude statistics:
-// the rounding error 2^(sigma_i + tau_j - t - 1) (mu_i + nu_j + k 2^(-t-1)) over the estimate
-// 2^(sigma_i + tau_j) mu_i nu_j / (8k) of (|A||B|)_ij (a safety factor of 8, as the slice count
-// of the split emulation), maximised over i, j by the smallest mu and nu:
-// 2^(-t-1) 8k (1/nu + 1/mu + k 2^(-t-1) / (mu nu)).
-double mod_relative_bound(int t, double mu_min, double nu_min, int64_t k) {
-  const double kd = (double)k;
-  return ldexp(1.0, -t - 1) * 8.0 * kd * (1.0 / nu_min + 1.0 / mu_min + kd * ldexp(1.0, -t - 1) / (mu_min * nu_min));
-}
-
-int choose_bits(double tol, double mu_min, double nu_min, int64_t k, double* bound) {
-  for (int t = 1; t <= 62; ++t) {
-    const double b = mod_relative_bound(t, mu_min, nu_min, k);
-    if (b <= tol) {
-      if (bound) *bound = b;
-      return t;
-    }
-  }
-  return 63;
-}
-
 // Relative throughput per SM of the two-SM form over the one-SM form when both fill the GPU
 constexpr double kModPairGain = 1.2;
 
-// the product kernel of one call; `a` carries everything but the tile geometry
-int launch_mod_gemm(int64_t m, int64_t n, int64_t k, ModArgs& a, const ModWorkspace& ws, int sms,
+// the product kernel of one call; `a` carries everything but the tile geometry; the residue
+// planes hold up to nmod_ws moduli (the plan's n is at most that)
+int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, const ModWorkspace& ws, int sms,
                     cudaStream_t stream) {
   // GBD_EMU_KERNEL=pair|single overrides the choice (tests and tuning).  Otherwise the expected
   // time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs (or SM
@@ -663,12 +722,12 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, ModArgs& a, const ModWorksp
   CUtensorMap tmA, tmB;
   memset(&tmA, 0, sizeof(tmA));
   memset(&tmB, 0, sizeof(tmB));
-  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, (uint64_t)a.nmod};
+  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, (uint64_t)nmod_ws};
   const uint64_t pA[2] = {(uint64_t)ws.kp * 2, (uint64_t)m * ws.kp * 2};
   const uint32_t bA[3] = {(uint32_t)kBK, brows, 1u};
   int rc = encode_tmap(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
-  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, (uint64_t)a.nmod};
+  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, (uint64_t)nmod_ws};
   const uint64_t pB[2] = {(uint64_t)ws.kp * 2, (uint64_t)n * ws.kp * 2};
   const uint32_t bB[3] = {(uint32_t)kBK, brows, 1u};
   rc = encode_tmap(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -732,7 +791,8 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     memset(info, 0, sizeof(*info));
     info->record_phases = rp;
   }
-  if (bits < 0 || bits > 62) return set_error(GBD_ERR_ARG, "dgemm_emu_mod: bits must be 0 (automatic) or 1..62");
+  if (bits < -1 || bits > 62)
+    return set_error(GBD_ERR_ARG, "dgemm_emu_mod: bits must be -1 or 0 (automatic) or 1..62");
   if (m == 0 || n == 0) return GBD_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (alpha == 0.0 || k == 0) return scale_c(m, n, beta, C, ldc, s);
@@ -741,9 +801,10 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     return set_error(GBD_ERR_LIMIT, "dgemm_emu_mod: m, n and k below 2^31 are supported");
   int sms = 0;
   if ((rc = current_device(nullptr, &sms))) return rc;
+  const ModProducts prods = moduli_products();
   int nmod_ws = kMaxModuli;
   if (bits > 0) {
-    nmod_ws = moduli_for(bits, k);
+    nmod_ws = moduli_for_products(bits, k, prods);
     if (nmod_ws == 0)
       return set_error(GBD_ERR_LIMIT, "dgemm_emu_mod: %d bits need more than %d moduli at k = %lld", bits,
                        kMaxModuli, (long long)k);
@@ -770,6 +831,7 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
   }
   const int ta = (transa == 'N' || transa == 'n') ? 0 : 1, tb = (transb == 'N' || transb == 'n') ? 0 : 1;
+  const bool automatic = bits <= 0;
 
   // exponents (and, in automatic mode, the magnitude statistics) of both sides
   PrepPair pp;
@@ -777,39 +839,38 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   PrepJob& ja = pp.j[0];
   PrepJob& jb = pp.j[1];
   ja.X = A; ja.ld = lda; ja.R = m; ja.K = k; ja.rows_contig = ta == 0;
-  ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = bits == 0 ? ws.muA : nullptr; ja.D = ws.DA; ja.kp = ws.kp;
+  ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = automatic ? ws.muA : nullptr; ja.D = ws.DA; ja.kp = ws.kp;
   jb.X = B; jb.ld = ldb; jb.R = n; jb.K = k; jb.rows_contig = tb != 0;
-  jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = bits == 0 ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
+  jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = automatic ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) return rc;
-  int t = bits;
-  double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
-  if (bits == 0) {
+  if (automatic) {
     if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
     if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
-    float st[4] = {0, 0, 0, 0};
-    if ((e = cudaMemcpyAsync(st, ws.stats, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_fail(e, "dgemm_emu_mod: reading statistics");
-    mu_min = st[0] < 1e38f ? st[0] : 0.0;
-    nu_min = st[1] < 1e38f ? st[1] : 0.0;
-    const double target = tol > 0.0 ? tol : 2.0 * (double)k * 1.1102230246251565e-16;
-    t = (mu_min > 0.0 && nu_min > 0.0) ? choose_bits(target, mu_min, nu_min, k, &bound) : 1;
   }
-  const int nmod = moduli_for(t, k);
-  if (nmod == 0)
-    return set_error(GBD_ERR_LIMIT,
-                     "dgemm_emu_mod: the accuracy target needs %d integer bits, beyond %d moduli at k = %lld "
-                     "(gbd_dgemm_emu covers it)",
-                     t, kMaxModuli, (long long)k);
+  // the plan: t and n, on the device
+  const double target = tol > 0.0 ? tol : 2.0 * (double)k * 1.1102230246251565e-16;
+  k_mod_plan<<<1, 32, 0, s>>>(ws.stats, k, target, automatic ? 0 : bits, prods, ws.plan, device_error_word(),
+                              bits == -1 ? 1 : 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan launch");
+  ModPlan host_plan;
+  memset(&host_plan, 0, sizeof(host_plan));
+  if (bits == 0) {  // read the plan back: an unreachable target is refused before C is touched
+    if ((e = cudaMemcpyAsync(&host_plan, ws.plan, sizeof(host_plan), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu_mod: reading the plan");
+    if (!host_plan.feasible)
+      return set_error(GBD_ERR_LIMIT,
+                       "dgemm_emu_mod: the accuracy target needs %d integer bits, beyond %d moduli at k = %lld "
+                       "(gbd_dgemm_emu covers it)",
+                       host_plan.pad, kMaxModuli, (long long)k);
+  }
 
-  // residues of both sides
+  // residues of both sides (the first n of the kMaxModuli, t bits, from the plan)
   ModSplit ms;
   memset(&ms, 0, sizeof(ms));
-  ms.n = nmod;
-  ms.t = t;
-  for (int l = 0; l < nmod; ++l) {
+  for (int l = 0; l < kMaxModuli; ++l) {
     const int pm = kModuli[l];
     ms.pf[l] = (float)pm;
     ms.inv[l] = 1.0f / (float)pm;
@@ -822,27 +883,33 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     ms.wlo[l] = lo;
     ms.whi[l] = hi;
   }
+  ms.plan = ws.plan;
   if ((rc = launch_residue_pair(pp, ms, split_blocks, s))) return rc;
-  k_mod_colscale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.sigB, ws.badB, n, alpha, t, ws.cs);
+  k_mod_colscale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.sigB, ws.badB, n, alpha, ws.plan, ws.cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "column scale launch");
 
-  // products modulo each modulus and the reconstruction
+  // products modulo each modulus and the reconstruction; the constants of every n ride along
   ModArgs a;
   memset(&a, 0, sizeof(a));
-  const hu128 M = moduli_product(nmod);
-  for (int l = 0; l < nmod; ++l) {
-    const hu128 Mp = M / (hu128)kModuli[l];
+  for (int l = 0; l < kMaxModuli; ++l) {
     a.p[l] = kModuli[l];
-    a.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
     a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
     a.rq[l] = ((1u << 24) + (uint32_t)kModuli[l] - 1u) / (uint32_t)kModuli[l];
-    for (int w = 0; w < 4; ++w) a.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
+  }
+  for (int nn = 1; nn <= kMaxModuli; ++nn) {
+    CrtSet& cs = a.set[nn - 1];
+    const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
+    for (int l = 0; l < nn; ++l) {
+      const hu128 Mp = M / (hu128)kModuli[l];
+      cs.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
+      for (int w = 0; w < 4; ++w) cs.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
+    }
+    cs.M_lo = (uint64_t)M; cs.M_hi = (uint64_t)(M >> 64);
+    const hu128 half = M / 2;
+    cs.half_lo = (uint64_t)half; cs.half_hi = (uint64_t)(half >> 64);
   }
   a.m = m; a.n = n; a.ldc = ldc;
-  a.nmod = nmod;
-  a.M_lo = (uint64_t)M; a.M_hi = (uint64_t)(M >> 64);
-  const hu128 half = M / 2;
-  a.half_lo = (uint64_t)half; a.half_hi = (uint64_t)(half >> 64);
+  a.plan = ws.plan;
   a.beta = beta;
   a.C = C;
   a.sigA = ws.sigA; a.badA = ws.badA;
@@ -850,7 +917,7 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   a.scr = ws.scr;
   a.err = device_error_word();
   if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
-  if ((rc = launch_mod_gemm(m, n, k, a, ws, sms, s))) return rc;
+  if ((rc = launch_mod_gemm(m, n, k, nmod_ws, a, ws, sms, s))) return rc;
   if (timing) {
     float t0 = 0.f, t1 = 0.f;
     if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[2])) != cudaSuccess ||
@@ -861,12 +928,20 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     info->gemm_ms = t1;
   }
   if (info) {
-    info->slices = nmod;
-    info->digit_bits = t;
-    info->products = nmod;
-    info->mu_min = mu_min;
-    info->nu_min = nu_min;
-    info->bound_est = bound;
+    if (bits > 0) {
+      host_plan.t = bits;
+      host_plan.n = nmod_ws;
+    } else if (bits == -1) {  // the device-side choice: read it back (this synchronises `stream`)
+      if ((e = cudaMemcpyAsync(&host_plan, ws.plan, sizeof(host_plan), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "dgemm_emu_mod: reading the plan");
+    }
+    info->slices = host_plan.n;
+    info->digit_bits = host_plan.t;
+    info->products = host_plan.n;
+    info->mu_min = host_plan.mu;
+    info->nu_min = host_plan.nu;
+    info->bound_est = host_plan.bound;
   }
   return GBD_OK;
 }

@@ -312,6 +312,7 @@ __device__ __forceinline__ int64_t rounded_scaled(uint64_t bits, int sigma, int 
 // sign of A' is then set on its bits.
 struct ResidueWriter {
   const ModSplit* mp;  // in the kernel's parameter space
+  int n, t;            // from the call's plan
   int64_t R, K;
   uint16_t* D;
   int64_t kp;
@@ -320,14 +321,14 @@ struct ResidueWriter {
     uint32_t lo[kPerThread], hi[kPerThread], sgn[kPerThread];  // the bytes of |A'| (0..3, 4..7), its sign
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
-      const int64_t q = rounded_scaled(x[v], sg, mp->t);
+      const int64_t q = rounded_scaled(x[v], sg, t);
       const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
       lo[v] = (uint32_t)a;
       hi[v] = (uint32_t)(a >> 32);
       sgn[v] = q < 0 ? 0x80000000u : 0u;
     }
     const bool full = pbase + kPerThread <= K;
-    for (int i = 0; i < mp->n; ++i) {
+    for (int i = 0; i < n; ++i) {
       const float pf = mp->pf[i], inv = mp->inv[i];
       const uint32_t wl = mp->wlo[i], wh = mp->whi[i];  // 256^d mod p, one byte per d
       uint32_t bits[kPerThread];
@@ -515,7 +516,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_residue_pair(const __grid_con
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  const ResidueWriter w{&mp, j.R, j.K, j.D, j.kp};
+  const ModPlan pl = *mp.plan;
+  const ResidueWriter w{&mp, pl.n, pl.t, j.R, j.K, j.D, j.kp};
   if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }

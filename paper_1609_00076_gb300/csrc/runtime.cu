@@ -214,6 +214,9 @@ int gbd_check_device_error(void* stream) {
   if (v == 0) return GBD_OK;
   if ((e = cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice)) != cudaSuccess)
     return gbd::cuda_fail(e, "clear device error word");
+  if (v == gbd::kErrModRange)
+    return gbd::set_error(GBD_ERR_LIMIT,
+                          "a modular call in device-side automatic mode needed more than 16 moduli (its C is NaN)");
   return gbd::set_error(GBD_ERR_TIMEOUT, "a bounded device wait gave up (error bits 0x%x)", v);
 }
 

@@ -139,7 +139,7 @@ def test_emu_mod_workspace_and_argument_codes_without_gpu(lib):
     assert call("X", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 1
     assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 1, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 10
     assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 63, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
-    assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, -1, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
+    assert call("N", "N", 2, 2, 2, 1.0, a, 2, a, 2, 0.0, a, 2, -2, 0.0, None, 0, stream=0) == gbdgemm.GBD_ERR_ARG
     assert call("N", "N", 2, 0, 2, 1.0, a, 2, a, 2, 0.0, a, 2, 0, 0.0, None, 0, stream=0) == 0
 
 

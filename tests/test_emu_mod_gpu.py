@@ -164,6 +164,7 @@ def test_errors_and_quick_returns():
     z = torch.zeros(64, dtype=torch.float64, device="cuda")
     call = gbdgemm.gbd_dgemm_emu_mod
     assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 63, 0.0, ws, wsb) == gbdgemm.GBD_ERR_ARG
+    assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, -2, 0.0, ws, wsb) == gbdgemm.GBD_ERR_ARG
     # 2 k 2^(2t) = 2^127 at t = 62, k = 4: more than 16 moduli
     assert call("N", "N", 4, 4, 4, 1.0, z, 4, z, 4, 0.0, z, 4, 62, 0.0, ws, wsb) == gbdgemm.GBD_ERR_LIMIT
     # an accuracy target beyond 16 moduli in automatic mode
@@ -183,3 +184,36 @@ def test_deterministic():
     o1, i1 = run_mod("N", "N", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, 0)
     o2, i2 = run_mod("N", "N", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, 0)
     assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64)) and i1.digit_bits == i2.digit_bits
+
+
+@pytest.mark.parametrize("e", [0, 8])
+def test_device_side_automatic_mode_matches_the_synchronising_one(oracle_mod, e):
+    # bits = -1 chooses on the device exactly as bits = 0 does, without any read-back
+    m, n, k = 400, 300, 900
+    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "scaled", 60 + e, pads=(1, 2, 3), e=e)
+    out0, info0 = run_mod("N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, 0)
+    out1, info1 = run_mod("N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, -1)
+    assert np.array_equal(out0.view(np.uint64), out1.view(np.uint64))
+    assert (info1.digit_bits, info1.products, info1.bound_est) == (info0.digit_bits, info0.products, info0.bound_est)
+    check_model(oracle_mod, "N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, out1, info1.digit_bits)
+
+
+def test_device_side_automatic_mode_unreachable_target():
+    # a target beyond 16 moduli: C becomes NaN, the device error word reports GBD_ERR_LIMIT,
+    # and the synchronising form refuses before touching C
+    import torch
+    m = n = k = 64
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(m, n, k, 0)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    A = torch.ones(m * k, dtype=torch.float64, device="cuda")
+    C = torch.zeros(m * n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert gbdgemm.gbd_check_device_error() == 0
+    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", m, n, k, 1.0, A, m, A, k, 0.0, C, m, 0, 1e-40, ws, wsb) == \
+        gbdgemm.GBD_ERR_LIMIT
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(C).item() == 0 and gbdgemm.gbd_check_device_error() == 0
+    assert gbdgemm.gbd_dgemm_emu_mod("N", "N", m, n, k, 1.0, A, m, A, k, 0.0, C, m, -1, 1e-40, ws, wsb) == 0
+    assert gbdgemm.gbd_check_device_error() == gbdgemm.GBD_ERR_LIMIT
+    assert torch.isnan(C).all().item()
+    assert gbdgemm.gbd_check_device_error() == 0  # read and cleared
