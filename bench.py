@@ -600,10 +600,14 @@ def small_call_latency(dev, stream, calls: int = 200):
     slices = 7
     wsb = gbdgemm.gbd_dgemm_emu_workspace_size(m, n, k, slices)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    wsm_b = gbdgemm.gbd_dgemm_emu_mod_workspace_size(m, n, k, -1)
+    wsm = torch.empty(wsm_b, dtype=torch.uint8, device=dev)
     out = {}
     for name, fn in (("native", lambda s: gbdgemm.gbd_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, stream=s)),
                      ("emulated", lambda s: gbdgemm.gbd_dgemm_emu("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m,
-                                                                 slices, 0.0, ws, wsb, None, stream=s))):
+                                                                 slices, 0.0, ws, wsb, None, stream=s)),
+                     ("modular", lambda s: gbdgemm.gbd_dgemm_emu_mod("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m,
+                                                                    -1, 0.0, wsm, wsm_b, None, stream=s))):
         with torch.cuda.stream(stream):
             for _ in range(5):
                 gbdgemm.check(fn(stream))
@@ -616,7 +620,8 @@ def small_call_latency(dev, stream, calls: int = 200):
             torch.cuda.synchronize()
         t = sorted(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(calls))
         out[name] = {"p50_ms": t[len(t) // 2], "p99_ms": t[min(len(t) - 1, int(0.99 * len(t)))]}
-    out["config"] = "256^3 N,N alpha=1 beta=0, uniform[-1,1); emulated with 7 slices; device time per call"
+    out["config"] = ("256^3 N,N alpha=1 beta=0, uniform[-1,1); emulated with 7 slices; modular with its bits "
+                     "chosen on the device; device time per call")
     return out
 
 
