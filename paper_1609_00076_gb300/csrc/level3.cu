@@ -12,9 +12,12 @@
 //          at most 512: the triangle packed with zeros (and a unit diagonal), one GEMM into
 //          scratch, copied back.
 //   DTRSM  the leading half solved, the trailing right-hand sides updated by one GEMM
-//          (beta = alpha folds the scaling in), the trailing half solved with alpha = 1.  A
-//          diagonal block of at most 64 is solved by substitution in k_trsm_base: one thread
-//          per right-hand side, the triangle in shared memory (read as a broadcast).
+//          (beta = alpha folds the scaling in), the trailing half solved with alpha = 1.  The
+//          diagonal blocks of at most 64 are inverted together in one launch before the
+//          recursion (k_trsm_invert, substitution on the identity); each is then applied as a
+//          dense triangular product, one thread per element of the solution (k_trsm_apply).
+//          On GB300's narrow FP64 pipe this beats substitution on the right-hand sides, which
+//          leaves the pipe idle (one thread per right-hand side) or wastes it (one warp).
 // All work is stream-ordered on the caller's stream.  In emulated mode each product takes the
 // fastest path that meets `tol`: products under 1e8 flops run natively (a native call is then
 // faster than the emulation's fixed cost, and at least as accurate); products with at least
@@ -22,9 +25,11 @@
 // emulation when 16 moduli cannot reach `tol`; the rest use the split emulation, whose
 // split inner dimension serves few output tiles.  Each emulated product synchronises the
 // stream once (automatic mode).
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -34,7 +39,7 @@ namespace {
 constexpr int64_t kSyrkBase = 512;  // diagonal blocks of DSYRK
 constexpr int64_t kTrmmBase = 512;  // diagonal blocks of DTRMM
 constexpr int64_t kTrsmBase = 64;   // diagonal blocks of DTRSM (substitution kernel)
-constexpr int kTrsmVecs = 64;       // right-hand sides per CTA of the substitution kernel
+constexpr int kTrsmVecs = 16;       // right-hand sides per CTA of the diagonal-block product
 constexpr double kNativeFlops = 1e8;    // emulated mode: smaller products run natively
 constexpr double kModularOutputs = 2.5e6;  // emulated mode: larger outputs use the modular emulation
 
@@ -90,56 +95,95 @@ __global__ void __launch_bounds__(256) k_tri_pack(const double* __restrict__ a, 
   D[j * ldd + i] = v;
 }
 
-// Substitution for the diagonal block: E x = alpha v for nvec right-hand sides v, where E is
-// the b x b block of A at `a` (b <= 64) or its transpose (teff), restricted to its stored
-// triangle (unit diagonal if `unit`).  Element q of right-hand side u lives at
-// B[q * sq + u * su]; x overwrites it.  E is lower (forward substitution) when the stored
-// triangle is lower xor teff.
-constexpr int kTrsmSmem = (64 * 64 + 64 * kTrsmVecs) * 8;
-__global__ void __launch_bounds__(kTrsmVecs) k_trsm_base(const double* __restrict__ a, int64_t lda, int b, int upper,
-                                                         int unit, int teff, double* __restrict__ B, int64_t sq,
-                                                         int64_t su, int64_t nvec, double alpha) {
+// The diagonal blocks of the solve, inverted once per call: block q covers rows
+// [r0[q], r0[q] + b[q]) (b <= 64) of the stored A; E is that block's stored triangle (unit
+// diagonal if `unit`) or its transpose (teff), and Dinv[q] = E^-1, row-major 64 x 64.  Thread c
+// solves E y = e_c by substitution (E^-1 is triangular like E) with E in shared memory.
+struct TrsmBlock {
+  int64_t r0;
+  int b;
+  int pad;
+};
+
+constexpr int kTrsmInvSmem = 2 * 64 * 64 * 8;
+__global__ void __launch_bounds__(64) k_trsm_invert(const double* __restrict__ A, int64_t lda,
+                                                    const TrsmBlock* __restrict__ blocks, int upper, int unit,
+                                                    int teff, double* __restrict__ Dinv) {
   extern __shared__ double sm[];
-  double (*E)[64] = reinterpret_cast<double (*)[64]>(sm);                       // E[r][s], read as broadcasts
-  double (*X)[kTrsmVecs] = reinterpret_cast<double (*)[kTrsmVecs]>(sm + 64 * 64);  // X[q][vector]
-  const int t = threadIdx.x;
-  const int64_t u0 = (int64_t)blockIdx.x * kTrsmVecs;
-  const int nv = (int)min((int64_t)kTrsmVecs, nvec - u0);
-  for (int idx = t; idx < b * b; idx += blockDim.x) {
-    const int r = idx % b, s = idx / b;  // stored element (r, s) of the block, r fastest
+  double (*E)[64] = reinterpret_cast<double (*)[64]>(sm);            // E[s][t] (a row read by all threads)
+  double (*Y)[64] = reinterpret_cast<double (*)[64]>(sm + 64 * 64);  // Y[s][c]: column c of E^-1
+  const TrsmBlock blk = blocks[blockIdx.x];
+  const int b = blk.b;
+  const double* a = A + blk.r0 * lda + blk.r0;
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    const int i = idx % b, j = idx / b;  // stored element (i, j), i fastest (contiguous)
     double v = 0.0;
-    if (r == s) v = unit ? 1.0 : a[(int64_t)s * lda + r];
-    else if (upper ? r < s : r > s) v = a[(int64_t)s * lda + r];
-    if (teff) E[s][r] = v;
-    else E[r][s] = v;
-  }
-  // right-hand sides, in the order that makes global accesses contiguous
-  const bool q_fast = sq == 1;
-  for (int idx = t; idx < b * nv; idx += blockDim.x) {
-    const int q = q_fast ? idx % b : idx / nv, u = q_fast ? idx / b : idx % nv;
-    X[q][u] = B[(int64_t)q * sq + (u0 + u) * su];
+    if (i == j) v = unit ? 1.0 : a[(int64_t)j * lda + i];
+    else if (upper ? i < j : i > j) v = a[(int64_t)j * lda + i];
+    if (teff) E[j][i] = v;
+    else E[i][j] = v;
   }
   __syncthreads();
-  if (t < nv) {
-    const bool lower = (upper == 0) != (teff != 0);
+  const int c = threadIdx.x;
+  const bool lower = (upper == 0) != (teff != 0);
+  if (c < b) {
     for (int step = 0; step < b; ++step) {
-      const int r = lower ? step : b - 1 - step;
-      double acc0 = 0.0, acc1 = 0.0;
-      const int s0 = lower ? 0 : r + 1, s1 = lower ? r : b;
-      int s = s0;
-      for (; s + 1 < s1; s += 2) {
-        acc0 = fma(E[r][s], X[s][t], acc0);
-        acc1 = fma(E[r][s + 1], X[s + 1][t], acc1);
+      const int s = lower ? step : b - 1 - step;
+      double y = 0.0;
+      if (lower ? s >= c : s <= c) {
+        double acc = s == c ? 1.0 : 0.0;
+        const int t0 = lower ? c : s + 1, t1 = lower ? s : c + 1;
+        for (int t = t0; t < t1; ++t) acc = fma(-E[s][t], Y[t][c], acc);
+        y = unit ? acc : acc / E[s][s];
       }
-      if (s < s1) acc0 = fma(E[r][s], X[s][t], acc0);
-      const double num = fma(alpha, X[r][t], -(acc0 + acc1));
-      X[r][t] = unit ? num : num / E[r][r];
+      Y[s][c] = y;
     }
   }
   __syncthreads();
-  for (int idx = t; idx < b * nv; idx += blockDim.x) {
-    const int q = q_fast ? idx % b : idx / nv, u = q_fast ? idx / b : idx % nv;
-    B[(int64_t)q * sq + (u0 + u) * su] = X[q][u];
+  double* out = Dinv + (int64_t)blockIdx.x * 64 * 64;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+    const int s = idx / 64, t = idx % 64;
+    out[idx] = (s < b && t < b) ? Y[s][t] : 0.0;
+  }
+}
+
+// X := E^-1 (alpha V) for nvec right-hand sides of the b x b diagonal block whose inverse is
+// Dinv (row-major 64 x 64); element q of right-hand side u lives at B[q * sq + u * su].  A CTA
+// takes 16 right-hand sides: the inverse and the scaled right-hand sides are staged in shared
+// memory, then thread (s, v) forms row s of solution v.
+__global__ void __launch_bounds__(64 * kTrsmVecs) k_trsm_apply(const double* __restrict__ Dinv, int b, int lower,
+                                                               double* __restrict__ B, int64_t sq, int64_t su,
+                                                               int64_t nvec, double alpha) {
+  __shared__ double Di[64][65];
+  __shared__ double R[64][kTrsmVecs];  // R[t][v]
+  const int64_t u0 = (int64_t)blockIdx.x * kTrsmVecs;
+  const int nv = (int)min((int64_t)kTrsmVecs, nvec - u0);
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) Di[idx / 64][idx % 64] = Dinv[idx];
+  const bool q_fast = sq == 1;
+  for (int idx = threadIdx.x; idx < b * nv; idx += blockDim.x) {
+    const int q = q_fast ? idx % b : idx / nv, v = q_fast ? idx / b : idx % nv;
+    R[q][v] = alpha * B[(int64_t)q * sq + (u0 + v) * su];
+  }
+  __syncthreads();
+  const int s = threadIdx.x % 64, v = threadIdx.x / 64;
+  double x = 0.0;
+  if (s < b && v < nv) {
+    const int t0 = lower ? 0 : s, t1 = lower ? s + 1 : b;
+    double x1 = 0.0;
+    int t = t0;
+    for (; t + 1 < t1; t += 2) {
+      x = fma(Di[s][t], R[t][v], x);
+      x1 = fma(Di[s][t + 1], R[t + 1][v], x1);
+    }
+    if (t < t1) x = fma(Di[s][t], R[t][v], x);
+    x += x1;
+  }
+  __syncthreads();
+  if (s < b && v < nv) R[s][v] = x;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < b * nv; idx += blockDim.x) {
+    const int q = q_fast ? idx % b : idx / nv, vv = q_fast ? idx / b : idx % nv;
+    B[(int64_t)q * sq + (u0 + vv) * su] = R[q][vv];
   }
 }
 
@@ -157,6 +201,18 @@ struct Ctx {
   double* scr;  // level-3 scratch (W, D, T)
   bool dry;
   size_t need;
+  std::vector<TrsmBlock>* blocks = nullptr;  // DTRSM: the diagonal blocks (sorted by first row for use)
+  double* dinv = nullptr;                    // DTRSM: their inverses, 64 x 64 each, in that order
+  // the inverse of the diagonal block starting at row r0
+  const double* inverse_at(int64_t r0) const {
+    size_t lo = 0, hi = blocks->size();
+    while (hi - lo > 1) {
+      const size_t mid = (lo + hi) / 2;
+      if ((*blocks)[mid].r0 <= r0) lo = mid;
+      else hi = mid;
+    }
+    return dinv + (int64_t)lo * 64 * 64;
+  }
   double native_flops = kNativeFlops, modular_outputs = kModularOutputs;
   void thresholds() {
     native_flops = threshold("GBD_L3_NATIVE_FLOPS", kNativeFlops);
@@ -305,17 +361,19 @@ struct Tri {
     const int64_t b = r1 - r0;
     int rc;
     if (b <= kTrsmBase) {
-      if (c->dry) return GBD_OK;
+      if (c->dry) {
+        if (c->blocks) c->blocks->push_back(TrsmBlock{r0, (int)b, 0});
+        return GBD_OK;
+      }
       // side L: E = op(D), right-hand sides are the columns of B[r0:r1, :];
       // side R: X op(D) = alpha B  <=>  op(D)^T X^T = alpha B^T, right-hand sides are rows
       const int teff = side == 0 ? tr : !tr;
+      const int lowerE = (upper == 0) != (teff != 0);
       const int64_t nvec = side == 0 ? n : m;
       double* base = side == 0 ? Brow(r0) : Bcol(r0);
       const int64_t sq = side == 0 ? 1 : ldb, su = side == 0 ? ldb : 1;
-      const cudaError_t e = cudaFuncSetAttribute(k_trsm_base, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(triangular solve)");
-      k_trsm_base<<<(unsigned)((nvec + kTrsmVecs - 1) / kTrsmVecs), kTrsmVecs, kTrsmSmem, c->s>>>(
-          A + r0 * lda + r0, lda, (int)b, upper, unit, teff, base, sq, su, nvec, alpha);
+      k_trsm_apply<<<(unsigned)((nvec + kTrsmVecs - 1) / kTrsmVecs), 64 * kTrsmVecs, 0, c->s>>>(
+          c->inverse_at(r0), (int)b, lowerE, base, sq, su, nvec, alpha);
       return c->check("triangular solve launch");
     }
     const int64_t h = split_point(r0, r1);
@@ -373,9 +431,18 @@ int check_tri_args(char side, char uplo, char transa, char diag, int64_t m, int6
   return 0;
 }
 
-// workspace of one DTRMM/DTRSM call: level-3 scratch, then the emulated GEMM workspace
-size_t tri_workspace(bool solve, int side, int64_t m, int64_t n, int mode) {
+// DTRSM scratch: the diagonal blocks' list and their 64 x 64 inverses
+size_t trsm_scratch(size_t nblocks) {
+  return up256(sizeof(TrsmBlock) * nblocks) + up256(sizeof(double) * 64 * 64 * nblocks);
+}
+
+// workspace of one DTRMM/DTRSM call: level-3 scratch, then the emulated GEMM workspace; for
+// DTRSM `blocks` (if given) receives the diagonal blocks in the order the recursion visits them
+size_t tri_workspace(bool solve, int side, int64_t m, int64_t n, int mode, std::vector<TrsmBlock>* blocks = nullptr) {
   if (m <= 0 || n <= 0) return 0;
+  std::vector<TrsmBlock> local;
+  if (!blocks) blocks = &local;
+  blocks->clear();
   Ctx c;
   memset(&c, 0, sizeof(c));
   c.mode = mode;
@@ -390,13 +457,15 @@ size_t tri_workspace(bool solve, int side, int64_t m, int64_t n, int mode) {
   t.lda = side == 0 ? m : n;
   t.ldb = m;
   const int64_t order = side == 0 ? m : n;
-  // the two triangle orientations issue transposed GEMM shapes: size for both
+  // the two triangle orientations issue transposed GEMM shapes: size for both (the diagonal
+  // blocks are the same for both; they are listed once)
   for (int up = 0; up < 2; ++up) {
     t.upper = up;
+    c.blocks = up == 0 ? blocks : nullptr;
     if (solve) t.trsm(0, order, 1.0);
     else t.trmm(0, order, 1.0);
   }
-  const size_t scr = solve ? 0 : trmm_scratch(side, m, n);
+  const size_t scr = solve ? trsm_scratch(blocks->size()) : trmm_scratch(side, m, n);
   return scr + up256(c.need);
 }
 
@@ -415,11 +484,12 @@ int tri_call(bool solve, char side, char uplo, char transa, char diag, int64_t m
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "level-3: zeroing B");
   }
   const int sd = side_code(side);
-  const size_t need = tri_workspace(solve, sd, m, n, mode);
+  std::vector<TrsmBlock> blocks;
+  const size_t need = tri_workspace(solve, sd, m, n, mode, &blocks);
   if (need > 0 && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)))
     return set_error(GBD_ERR_WORKSPACE, "%s: workspace must be 256-byte aligned and hold %zu bytes",
                      solve ? "dtrsm" : "dtrmm", need);
-  const size_t scr = solve ? 0 : trmm_scratch(sd, m, n);
+  const size_t scr = solve ? trsm_scratch(blocks.size()) : trmm_scratch(sd, m, n);
   Ctx c;
   c.mode = mode;
   c.thresholds();
@@ -443,6 +513,21 @@ int tri_call(bool solve, char side, char uplo, char transa, char diag, int64_t m
   t.B = B;
   t.ldb = ldb;
   const int64_t order = sd == 0 ? m : n;
+  if (solve) {  // invert every diagonal block first, all in one launch
+    // the dry pass lists them in its recursion's order, which depends on the side: sort by row
+    std::sort(blocks.begin(), blocks.end(), [](const TrsmBlock& x, const TrsmBlock& y) { return x.r0 < y.r0; });
+    const size_t nb = blocks.size();
+    TrsmBlock* dblocks = static_cast<TrsmBlock*>(workspace);
+    c.dinv = reinterpret_cast<double*>(static_cast<char*>(workspace) + up256(sizeof(TrsmBlock) * nb));
+    c.blocks = &blocks;
+    cudaError_t e = cudaMemcpyAsync(dblocks, blocks.data(), sizeof(TrsmBlock) * nb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dtrsm: the diagonal blocks' list");
+    const int teff = sd == 0 ? t.tr : !t.tr;
+    e = cudaFuncSetAttribute(k_trsm_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmInvSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(diagonal inversion)");
+    k_trsm_invert<<<(unsigned)nb, 64, kTrsmInvSmem, s>>>(A, lda, dblocks, t.upper, t.unit, teff, c.dinv);
+    if ((rc = c.check("diagonal inversion launch"))) return rc;
+  }
   return solve ? t.trsm(0, order, alpha) : t.trmm(0, order, alpha);
 }
 

@@ -146,8 +146,9 @@ def test_emu_mod_workspace_and_argument_codes_without_gpu(lib):
 def test_level3_workspace_sizes_and_codes_without_gpu(lib):
     import numpy as np
     nat, emu = gbdgemm.GBD_MODE_NATIVE, gbdgemm.GBD_MODE_EMULATED
-    # the native triangular solve needs no workspace; the others hold scratch and, emulated, GEMM workspace
-    assert gbdgemm.gbd_dtrsm_workspace_size("L", 1000, 300, nat) == 0
+    # every call holds level-3 scratch (the solve: its diagonal blocks' inverses), emulated ones also
+    # GEMM workspace
+    assert 0 < gbdgemm.gbd_dtrsm_workspace_size("L", 1000, 300, nat) < gbdgemm.gbd_dtrsm_workspace_size("L", 1000, 300, emu)
     # the top split of 1000 is 512 + 488: both triangles' coupling products fit
     for shape in ((300, 488, 512), (300, 512, 488)):
         assert gbdgemm.gbd_dtrsm_workspace_size("R", 300, 1000, emu) >= gbdgemm.gbd_dgemm_emu_workspace_size(*shape, 0)
