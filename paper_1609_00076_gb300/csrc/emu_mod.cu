@@ -36,6 +36,9 @@ constexpr int kSlotCols = 256;
 constexpr int64_t kLStride = (int64_t)kSlotCols * 128;
 constexpr int64_t kSlotBytes = (int64_t)kMaxModuli * kLStride;
 constexpr int kMaxModCtas = 256;
+// few-tile problems split each 128 x 128 tile's moduli over several CTAs (at most this many tiles)
+constexpr int kSplitMaxTiles = 64;
+constexpr int64_t kTileSlotBytes = (int64_t)kMaxModuli * (128 / 4) * 128 * 4;  // one tile's parked bytes
 
 // the reconstruction constants of the first n moduli (M = p_0 ... p_(n-1))
 struct CrtSet {
@@ -59,8 +62,18 @@ struct ModArgs {
   const int* badA;
   const double* cs;  // [n] alpha 2^(tau_j - 2t); NaN for a column with a non-finite entry
   uint8_t* scr;      // [CTA][2][kMaxModuli][kSlotCols / 4][128][4] parked u_l
+  // split over moduli (one-SM form, few tiles): each tile's moduli in `groups` work units
+  int groups;
+  uint8_t* tslot;            // [tile][kMaxModuli][kBN / 4][128][4] parked u_l of every unit of the tile
+  unsigned int* tile_done;   // [tile] finished units (zero at launch)
   unsigned int* err;
 };
+
+// the moduli [l0, l1) of work unit g of `groups` (at most nmod units per tile)
+__device__ __forceinline__ void unit_range(int g, int groups, int nmod, int& l0, int& l1) {
+  l0 = (int)((int64_t)g * nmod / groups);
+  l1 = (int)((int64_t)(g + 1) * nmod / groups);
+}
 
 // x mod p for 0 <= x < 2^32 (Barrett: with b = floor(2^32/p), floor(x b / 2^32) is floor(x/p) or
 // one less)
@@ -272,6 +285,112 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
   if (pd_active) advance(kGroups);
 }
 
+// The epilogue of the split form (one-SM kernel, 128 x 128 tiles, few of them): the moduli
+// of a tile are spread over `groups` work units on different CTAs.  Each unit drains its
+// moduli and parks their bytes in the tile's global slot; after a barrier of the epilogue
+// warps one thread publishes the unit (fence, then a counter per tile); the CTA that
+// finishes the tile's last unit rebuilds the whole tile from the slot, immediately.
+template <int EPI_WARPS, int TBN>
+__device__ __forceinline__ void mod_epilogue_split(const ModArgs& p, int nmod, bool nan_out, uint32_t tmem_base,
+                                                   uint64_t* acc_full, uint64_t* acc_empty, int* last_flag, int warp,
+                                                   int lane) {
+  constexpr int COLS = TBN / (EPI_WARPS / 4);
+  constexpr int kGroups = COLS / 4;
+  constexpr int64_t kTileStride = (int64_t)TBN / 4 * 128 * 4;  // one modulus of one tile
+  const CrtSet& cset = p.set[nmod - 1];
+  const int ew = warp - 2;
+  const int quad = warp & 3;
+  const int part = ew >> 2;
+  const int row = quad * 32 + lane;
+  const int col0 = part * COLS;
+  const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
+  const int groups = min(p.groups, nmod);
+  const int units = p.num_tiles * groups;
+  uint32_t chunk = 0;
+  int acc[COLS];
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int tile = u / groups;
+    int l0, l1;
+    unit_range(u % groups, groups, nmod, l0, l1);
+    uint8_t* const ub = p.tslot + (int64_t)tile * kMaxModuli * kTileStride + (int64_t)(col0 / 4) * 512 + row * 4;
+    for (int l = l0; l < l1; ++l) {
+      const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) acc[c] = 0;
+      int nch = 0;
+      for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+        const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+        mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+        tc_fence_after();
+        const uint32_t taddr = trow + buf * TBN + col0;
+#pragma unroll
+        for (int q = 0; q < COLS / 16; ++q) {
+          uint32_t v[16];
+          tmem_ld_16(taddr + q * 16, v);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        if (++nch == kReduceChunks) {
+          nch = 0;
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
+        }
+      }
+      const uint32_t cl = (uint32_t)cset.c[l];
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        uint32_t w = 0u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          w |= mod_barrett((uint32_t)mod_nonneg(acc[4 * g + b], pm, bm) * cl, pm, bm) << (8 * b);
+        *reinterpret_cast<uint32_t*>(ub + l * kTileStride + g * 512) = w;
+      }
+    }
+    // publish the unit; the last of the tile's units rebuilds it
+    epi_barrier<EPI_WARPS>();
+    if (warp == 2 && lane == 0) {
+      __threadfence();
+      const unsigned int prev = atomicAdd(p.tile_done + tile, 1u);
+      *last_flag = prev + 1u == (unsigned int)groups;
+    }
+    epi_barrier<EPI_WARPS>();
+    if (!*last_flag) continue;
+    __threadfence();  // the other units' bytes, published before their counts
+    int tm, tn;
+    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    const int64_t i = (int64_t)tm * 128 + row;
+    const int64_t jc0 = (int64_t)tn * TBN + col0;
+    if (i >= p.m || jc0 >= p.n) continue;
+    const int cols = (int)min((int64_t)COLS, p.n - jc0);
+    const int sg = p.sigA[i];
+    const int sig = sg == kExpEmpty ? 0 : sg;
+    const bool bad = p.badA[i] != 0;
+    double* crow = p.C + jc0 * p.ldc + i;
+    for (int g = 0; g * 4 < cols; ++g) {
+      uint32_t w4[kMaxModuli];
+#pragma unroll
+      for (int l = 0; l < kMaxModuli; ++l)
+        w4[l] = l < nmod ? __ldcg(reinterpret_cast<const unsigned int*>(ub + l * kTileStride + g * 512)) : 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 4 * g + q;
+        if (c >= cols) break;
+        uint32_t uu[kMaxModuli];
+#pragma unroll
+        for (int l = 0; l < kMaxModuli; ++l) uu[l] = (w4[l] >> (8 * q)) & 0xFFu;
+        const double csv = p.cs[jc0 + c];
+        const double w0 = p.beta != 0.0 ? p.beta * crow[(int64_t)c * p.ldc] : 0.0;
+        double w;
+        if (nan_out || bad || csv != csv) w = __longlong_as_double(0x7FF8000000000000ll);
+        else w = fma(csv, scaled_double(crt_combine(uu, p, cset, nmod), sig), w0);
+        crow[(int64_t)c * p.ldc] = w;
+      }
+    }
+  }
+}
+
 // ---- the one-SM form: 128 x 128 tiles ----
 constexpr int kBM = 128, kBN = 128;
 constexpr int kStages = 6;
@@ -292,6 +411,8 @@ struct Smem {
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
 
+// SPLIT: the work units are (tile, group of moduli) instead of tiles (few-tile problems)
+template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mod_gemm(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB) {
@@ -305,6 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_empty = bars + 2 * kStages + 2;
   uint64_t* done = bars + 2 * kStages + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmemSlot);
+  int* last_flag = reinterpret_cast<int*>(smem + L::kOffTmemSlot + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0 && lane == 0) {
@@ -333,16 +455,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *tmem_slot;
   const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
   const int nmod = plan.n;
+  // work units: tiles, or (tile, group of moduli) with at most nmod groups per tile
+  const int groups = SPLIT ? min(p.groups, nmod) : 1;
+  const int units = p.num_tiles * groups;
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
-      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int tile = u / groups;
+        int l0 = 0, l1 = nmod;
+        if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
         int tm, tn;
         tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-        for (int l = 0; l < nmod; ++l)
+        for (int l = l0; l < l1; ++l)
           for (int kb = 0; kb < p.nkb; ++kb) {
             mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             mbar_arrive_expect_tx(&full[stage], bytes);
@@ -359,8 +487,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-        for (int l = 0; l < nmod; ++l)
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int l0 = 0, l1 = nmod;
+        if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
+        for (int l = l0; l < l1; ++l)
           for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
             const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
             mbar_wait(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
@@ -380,10 +510,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             umma_commit(&acc_full[buf]);
           }
-      umma_commit(done);
-      mbar_wait(done, 0, p.err, kErrWaitMma);
+      }
+      if (chunk > 0) {  // a CTA without a unit issued nothing and has nothing to wait for
+        umma_commit(done);
+        mbar_wait(done, 0, p.err, kErrWaitMma);
+      }
     }
     __syncwarp();
+  } else if (SPLIT) {
+    mod_epilogue_split<kEpiWarps, kBN>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, last_flag, warp,
+                                       lane);
   } else {
     mod_epilogue<kEpiWarps, kBN, false>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, warp, lane,
                                         blockIdx.x, gridDim.x, kBM, 0);
@@ -632,6 +768,8 @@ struct ModWorkspace {
   uint16_t* DB;  // [nmod][n][kp]
   uint8_t* scr;  // [scr_ctas][2][kSlotBytes]
   int scr_ctas;
+  uint8_t* tslot;            // [tiles][kTileSlotBytes] when the split form may run, else null
+  unsigned int* tile_done;   // [tiles]
   int64_t kp;
 };
 
@@ -656,6 +794,9 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
   const size_t o_scr = off; off = up(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
+  const int64_t split_tiles = tiles1 <= kSplitMaxTiles ? tiles1 : 0;
+  const size_t o_tslot = off; off = up(off + (size_t)kTileSlotBytes * (size_t)split_tiles);
+  const size_t o_tdone = off; off = up(off + sizeof(unsigned int) * (size_t)split_tiles);
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -671,6 +812,8 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scr = reinterpret_cast<uint8_t*>(b + o_scr);
     ws->scr_ctas = (int)ctas;
+    ws->tslot = split_tiles ? reinterpret_cast<uint8_t*>(b + o_tslot) : nullptr;
+    ws->tile_done = split_tiles ? reinterpret_cast<unsigned int*>(b + o_tdone) : nullptr;
     ws->kp = kp;
   }
   return off;
@@ -707,10 +850,16 @@ constexpr double kModPairGain = 1.2;
 // planes hold up to nmod_ws moduli (the plan's n is at most that)
 int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, const ModWorkspace& ws, int sms,
                     cudaStream_t stream) {
-  // GBD_EMU_KERNEL=pair|single overrides the choice (tests and tuning).  Otherwise the expected
-  // time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs (or SM
-  // pairs), a 256 x 256 tile being four units on two SMs at kModPairGain.
+  // GBD_EMU_KERNEL=pair|single|split overrides the choice (tests and tuning).  Otherwise the
+  // expected time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs
+  // (or SM pairs), a 256 x 256 tile being four units on two SMs at kModPairGain; and the one-SM
+  // form splits the moduli of each tile over several CTAs for at most 8 tiles, or for fewer
+  // tiles than half the SMs with a deep inner dimension (k >= 2048); measured at 256^3 (4
+  // tiles) 0.145 against 0.169 ms, 256^2 x 4096 0.25 against 0.47 ms, but 512^3 (16 tiles) 0.22
+  // against 0.20 ms and 1024^3 (64 tiles) 0.34 against 0.30 ms.
   const char* force = getenv("GBD_EMU_KERNEL");
+  const bool force_split = force && strcmp(force, "split") == 0;
+  if (force_split) force = nullptr;
   const int cta_cap = sms < ws.scr_ctas ? sms : ws.scr_ctas;
   const int64_t tiles1 = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
   const int64_t tiles2 = ((m + k2BM - 1) / k2BM) * ((n + k2BN - 1) / k2BN);
@@ -739,7 +888,23 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
   cudaError_t e;
-  if (pair) {
+  const bool split = !pair && ws.tslot != nullptr &&
+                     (force_split || (!force && (tiles <= 8 || (2 * tiles < sms && k >= 2048))));
+  if (split) {
+    int groups = (int)((sms + tiles - 1) / tiles);  // the kernel keeps at most nmod of them
+    if (groups > kMaxModuli) groups = kMaxModuli;
+    a.groups = groups;
+    a.tslot = ws.tslot;
+    a.tile_done = ws.tile_done;
+    a.group_m = 1;
+    const int64_t units = tiles * groups;
+    const int grid = (int)(units < sms ? units : sms);
+    if ((e = cudaMemsetAsync(ws.tile_done, 0, sizeof(unsigned int) * (size_t)tiles, stream)) != cudaSuccess)
+      return cuda_fail(e, "modular gemm: clearing the tile counters");
+    e = cudaFuncSetAttribute(k_mod_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm split)");
+    k_mod_gemm<true><<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
+  } else if (pair) {
     const int pairs = (int)(tiles < pairs_avail ? tiles : pairs_avail);
     a.group_m = group_rows(pairs, k2BM, k2BN, a.tiles_m);
     e = cudaFuncSetAttribute(k_mod_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
@@ -748,9 +913,9 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   } else {
     const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);
-    e = cudaFuncSetAttribute(k_mod_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
+    e = cudaFuncSetAttribute(k_mod_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm)");
-    k_mod_gemm<<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
+    k_mod_gemm<false><<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "modular gemm launch");

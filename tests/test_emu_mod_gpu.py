@@ -63,17 +63,19 @@ def test_model_parity_bits(oracle_mod, bits):
     check_model(oracle_mod, "N", "N", m, n, k, 1.5, A, lda, B, ldb, -0.5, C, ldc, out, bits)
 
 
-@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("kernel", ["single", "pair", "split"])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 def test_model_parity_transposes(oracle_mod, monkeypatch, kernel, ta, tb):
-    monkeypatch.setenv("GBD_EMU_KERNEL", kernel)  # the one-SM and the two-SM product kernels
+    # the one-SM kernel, the two-SM kernel, and the one-SM kernel with each tile's moduli split
+    # over several CTAs (the last to finish rebuilds the tile)
+    monkeypatch.setenv("GBD_EMU_KERNEL", kernel)
     m, n, k = 260, 190, 515
     A, lda, B, ldb, C, ldc = _problem(ta, tb, m, n, k, "uniform", 40, pads=(2, 5, 1))
     out, _ = run_mod(ta, tb, m, n, k, -0.75, A, lda, B, ldb, 2.0, C, ldc, 40)
     check_model(oracle_mod, ta, tb, m, n, k, -0.75, A, lda, B, ldb, 2.0, C, ldc, out, 40)
 
 
-@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("kernel", ["single", "pair", "split"])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (127, 129, 63), (129, 1, 1025), (33, 257, 65), (5, 3, 70001),
                                    (600, 520, 300)])
 def test_model_parity_fringes(oracle_mod, monkeypatch, kernel, m, n, k):
@@ -217,3 +219,26 @@ def test_device_side_automatic_mode_unreachable_target():
     assert gbdgemm.gbd_check_device_error() == gbdgemm.GBD_ERR_LIMIT
     assert torch.isnan(C).all().item()
     assert gbdgemm.gbd_check_device_error() == 0  # read and cleared
+
+
+@pytest.mark.parametrize("bits", [0, -1])
+def test_split_form_repeated_calls_reuse_counters(oracle_mod, monkeypatch, bits):
+    # the split form's per-tile counters are cleared by every call: three calls on one workspace agree
+    import torch
+    monkeypatch.setenv("GBD_EMU_KERNEL", "split")
+    m, n, k = 300, 260, 700
+    A, lda, B, ldb, C, ldc = _problem("T", "T", m, n, k, "uniform", 88, pads=(1, 1, 1))
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(m, n, k, bits)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    outs = []
+    for _ in range(3):
+        dC = torch.from_numpy(C).cuda()
+        info = gbdgemm.GbdEmuInfo()
+        assert gbdgemm.gbd_dgemm_emu_mod("T", "T", m, n, k, 0.5, dA, lda, dB, ldb, 1.5, dC, ldc, bits, 0.0, ws, wsb,
+                                         info) == 0
+        torch.cuda.synchronize()
+        assert gbdgemm.gbd_check_device_error() == 0
+        outs.append(dC.cpu().numpy())
+    assert all(np.array_equal(outs[0].view(np.uint64), o.view(np.uint64)) for o in outs[1:])
+    check_model(oracle_mod, "T", "T", m, n, k, 0.5, A, lda, B, ldb, 1.5, C, ldc, outs[0], info.digit_bits)
