@@ -174,8 +174,9 @@ def host_inputs(seed: int):
     return _HOST_INPUTS[seed]
 
 
-def oracle_sample(target_s: float, seed: int = 2000):
-    """Times the CPU oracle on rows of the workload; returns (TFLOP/s, seconds, rows, threads)."""
+def oracle_sample(target_s: float, seed: int = 2000, want_rows: bool = False):
+    """Times the CPU oracle on rows of the workload; returns (TFLOP/s, seconds, rows, threads), and
+    with want_rows also the sampled row indices and the oracle's values there (nrows x N, column-major)."""
     import numpy as np
 
     import oracle
@@ -191,10 +192,28 @@ def oracle_sample(target_s: float, seed: int = 2000):
     nrows = int(max(1, min(M, target_s / max(per_row, 1e-6))))
     rows = [int(r) for r in (np.arange(nrows) * (M // max(nrows, 1))) % M]
     t0 = time.perf_counter()
-    oracle.dgemm_rows("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, None, M, rows=rows, nthreads=threads)
+    ref = oracle.dgemm_rows("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, None, M, rows=rows, nthreads=threads)
     dt = time.perf_counter() - t0
     flops = 2.0 * len(rows) * N * K
+    if want_rows:
+        return flops / dt / 1e12, dt, len(rows), threads, rows, ref
     return flops / dt / 1e12, dt, len(rows), threads
+
+
+def accuracy_report(results: dict, rows, ref, seed: int = 2000) -> dict:
+    """Error of each path's result against the oracle on the sampled rows: the largest |C - C_oracle|
+    and its largest ratio to the componentwise bound 2 k 2^-53 (|A||B|)_ij."""
+    import numpy as np
+    A, B = host_inputs(seed)
+    Ar = np.abs(A.reshape(K, M).T[rows, :])        # sampled rows of |A| (row-major)
+    G = Ar @ np.abs(B.reshape(N, K).T)              # (nrows x N) of |A||B|
+    Rv = ref.reshape(N, len(rows)).T                # oracle values, (nrows x N)
+    out = {"rows": len(rows), "bound": "2 k 2^-53 (|A||B|)_ij"}
+    for name, C in results.items():
+        Cv = C.reshape(N, M).T[rows, :]
+        err = np.abs(Cv - Rv)
+        out[name] = {"max_abs_err": float(err.max()), "max_err_over_bound": float((err / (2 * K * 2.0 ** -53 * G)).max())}
+    return out
 
 
 def run_reference(args, world, rank, pg):
@@ -245,6 +264,11 @@ def run_ours(args, world, rank, local, pg):
     A = torch.from_numpy(A_h).to(dev)
     B = torch.from_numpy(B_h).to(dev)
     C = torch.zeros(M * N, dtype=torch.float64, device=dev)
+    # the split path's workspace, allocated before the headline's: the split slice kernel's DRAM traffic
+    # depends on where its slices land (36-39 GB per launch as the process's first large allocation,
+    # 88-114 GB inside memory the modular workspace used)
+    split_wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
+    split_ws = torch.empty(split_wsb, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     flops = 2.0 * M * N * K
 
@@ -289,13 +313,14 @@ def run_ours(args, world, rank, local, pg):
         prep_ms.append(info.prep_ms)
     moduli, bits, bound_est = info.products, info.digit_bits, info.bound_est
     del ws
-    # give the freed workspace back to the driver: the split path's own workspace is then a fresh
-    # allocation, as it is for a caller running only that path (placed inside the freed block it
-    # measured 6 % slower, with three times the DRAM reads)
-    torch.cuda.empty_cache()
+    results = {"modular": C.cpu().numpy()} if rank == 0 else {}  # for the accuracy report (untimed)
 
     # ---- the split emulation on the same inputs (automatic slices at the same bound) ----
-    split = split_measure(dev, stream, A, B, C, steps=max(3, min(args.steps, 10)), warmup=max(3, args.warmup))
+    split = split_measure(dev, stream, A, B, C, split_ws, split_wsb, steps=max(3, min(args.steps, 10)),
+                          warmup=max(3, args.warmup))
+    del split_ws
+    if rank == 0:
+        results["split"] = C.cpu().numpy()
 
     # ---- native path on the same inputs ----
     def native_step(s):
@@ -313,6 +338,8 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     nat_ms = statistics.mean(nev[i].elapsed_time(nev[i + 1]) for i in range(nat_calls))
     nat_tflops = flops / (nat_ms / 1000.0) / 1e12
+    if rank == 0:
+        results["native"] = C.cpu().numpy()
 
     # ---- end to end through the host-buffer C-ABI call (pinned host memory), copies inside the region ----
     # Each step is one gbd_dgemm_emu_mod_host call: upload of A and B, the emulated product, download of C.
@@ -390,7 +417,8 @@ def run_ours(args, world, rank, local, pg):
     g_ms = statistics.mean(gemm_ms)
     achieved = moduli * flops / (g_ms / 1000.0) / 1e12
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
-    cpu_v, cpu_dt, cpu_rows, cpu_threads = oracle_sample(target_s=8.0)
+    cpu_v, cpu_dt, cpu_rows, cpu_threads, rows, ref = oracle_sample(target_s=8.0, want_rows=True)
+    accuracy = accuracy_report(results, rows, ref)
     # prep init, exponents, magnitudes, statistics, plan, residues, column scales, residue products (+ CRT)
     launches_per_step = 8
     line = {
@@ -427,6 +455,7 @@ def run_ours(args, world, rank, local, pg):
         "level3": level3,
         "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_rows} rows x {N} columns of the {M}^3 product ({cpu_dt:.1f} s)"},
+        "accuracy": accuracy,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
                 "d2h_bytes_per_step": M * N * 8, "steps": e2e_steps,
                 "call": "gbd_dgemm_emu_mod_host (bits = -1), pinned host A, B, C; two host threads, one stream and "
@@ -440,14 +469,12 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
-def split_measure(dev, stream, A, B, C, steps: int, warmup: int):
+def split_measure(dev, stream, A, B, C, ws, wsb, steps: int, warmup: int):
     """Device time of gbd_dgemm_emu (the split emulation) on the headline inputs (automatic slices
-    for the FP64 bound), and its phases."""
+    for the FP64 bound), and its phases, on the workspace `ws` of `wsb` bytes."""
     import torch
 
     from paper_1609_00076_gb300 import gbdgemm
-    wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
-    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     info = gbdgemm.GbdEmuInfo()
 
     def step(record):
@@ -470,7 +497,6 @@ def split_measure(dev, stream, A, B, C, steps: int, warmup: int):
     torch.cuda.synchronize()
     gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
     ms = ev[0].elapsed_time(ev[-1]) / steps
-    del ws
     return {"ms": ms, "value": 2.0 * M * N * K / (ms / 1000.0) / 1e12, "slices": info.slices,
             "products": info.products, "prep_ms": statistics.mean(prep), "gemm_ms": statistics.mean(prod),
             "steps": steps}
