@@ -101,6 +101,17 @@ void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks);
 // K <= 1024 every row has one block, which stores its result and needs no initialisation
 int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s);
 int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
+// Exponents and magnitude sums of both sides in one pass over the operands: per row and
+// k-block the largest exponent, a non-finite flag and the magnitude sum relative to that
+// exponent (partials [row][nkr]); then per row sig, bad and mu (32.32 fixed point) from the
+// partials in a fixed order.  Writes what launch_exponents_pair + launch_magnitudes_pair do.
+struct ExpMagParts {
+  int* e[2];
+  float* s[2];
+  int* b[2];
+  int nkr;  // k-blocks of kRedChunk per row
+};
+int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
 
 // ---- modular emulation (Ozaki scheme II) ----

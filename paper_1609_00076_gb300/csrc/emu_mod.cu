@@ -763,6 +763,7 @@ struct ModWorkspace {
   unsigned long long* muB;
   float* stats;
   ModPlan* plan;
+  ExpMagParts parts;  // automatic mode: per row and k-block exponents, flags and magnitude sums
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
   uint16_t* DB;  // [nmod][n][kp]
@@ -790,6 +791,13 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_plan = off; off = up(off + sizeof(ModPlan));
+  const int64_t nkr = (k + 1023) / 1024;  // k-blocks of the exponent and magnitude pass
+  size_t o_part[2][3];
+  for (int side = 0; side < 2; ++side)
+    for (int f = 0; f < 3; ++f) {
+      o_part[side][f] = off;
+      off = up(off + 4 * (size_t)(side == 0 ? m : n) * (size_t)nkr);
+    }
   const size_t o_cs = off; off = up(off + sizeof(double) * (size_t)n);
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
@@ -807,6 +815,12 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->plan = reinterpret_cast<ModPlan*>(b + o_plan);
+    for (int side = 0; side < 2; ++side) {
+      ws->parts.e[side] = reinterpret_cast<int*>(b + o_part[side][0]);
+      ws->parts.s[side] = reinterpret_cast<float*>(b + o_part[side][1]);
+      ws->parts.b[side] = reinterpret_cast<int*>(b + o_part[side][2]);
+    }
+    ws->parts.nkr = (int)nkr;
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -1009,10 +1023,11 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = automatic ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
-  if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) return rc;
-  if (automatic) {
-    if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
+  if (automatic) {  // exponents and magnitude sums in one pass over the operands
+    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
     if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
+  } else if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) {
+    return rc;
   }
   // the plan: t and n, on the device
   const double target = tol > 0.0 ? tol : 2.0 * (double)k * 1.1102230246251565e-16;

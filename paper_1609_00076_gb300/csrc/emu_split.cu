@@ -498,6 +498,141 @@ __global__ void __launch_bounds__(256) k_magnitudes_pair(const __grid_constant__
   else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum, direct);
 }
 
+// ---- exponents and magnitudes in one pass (the modular emulation's automatic mode) ----
+// 2^d for d <= 0 as a float (0 below 2^-126)
+__device__ __forceinline__ float pow2f_nonpos(int d) { return d < -126 ? 0.0f : __int_as_float((127 + d) << 23); }
+
+// folds element bits b into a running (largest exponent E, sum acc of |x| 2^-E, non-finite flag)
+__device__ __forceinline__ void expmag_add(uint64_t b, int& E, float& acc, int& bad) {
+  if (is_nonfinite(b)) {
+    bad = 1;
+    return;
+  }
+  if (is_zero(b)) return;
+  const int e = exponent_of(b);
+  if (e > E) {
+    acc = E == kExpEmpty ? 0.0f : acc * pow2f_nonpos(E - e);
+    E = e;
+  }
+  acc += scaled_magnitude(b, E);
+}
+// (E, acc) := (E, acc) + (E2, acc2), both relative to their own largest exponent
+__device__ __forceinline__ void expmag_merge(int& E, float& acc, int E2, float acc2) {
+  if (E2 == kExpEmpty) return;
+  if (E == kExpEmpty) {
+    E = E2;
+    acc = acc2;
+    return;
+  }
+  if (E2 > E) {
+    acc = acc * pow2f_nonpos(E - E2) + acc2;
+    E = E2;
+  } else {
+    acc += acc2 * pow2f_nonpos(E2 - E);
+  }
+}
+
+template <bool ROWS_CONTIG>
+__device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K, int nkr,
+                                            int* __restrict__ pe, float* __restrict__ ps, int* __restrict__ pb,
+                                            int64_t bx, int64_t by, int (*s_e)[33], float (*s_s)[33],
+                                            int (*s_b)[33]) {
+  const int64_t p_begin = by * kRedChunk;
+  const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
+  if (ROWS_CONTIG) {
+    // 32 consecutive rows per warp (coalesced), 8 warps split the k range
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r = bx * 32 + tx;
+    int E = kExpEmpty, bd = 0;
+    float acc = 0.0f;
+    if (r < R)
+#pragma unroll 4
+      for (int64_t p = p_begin + ty; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, bd);
+    s_e[ty][tx] = E;
+    s_s[ty][tx] = acc;
+    s_b[ty][tx] = bd;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+      for (int q = 1; q < 8; ++q) {
+        expmag_merge(E, acc, s_e[q][tx], s_s[q][tx]);
+        bd |= s_b[q][tx];
+      }
+      pe[r * nkr + by] = E;
+      ps[r * nkr + by] = acc;
+      pb[r * nkr + by] = bd;
+    }
+  } else {
+    // one row per warp, lanes along the contiguous k direction
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r = bx * 8 + w;
+    if (r >= R) return;
+    int E = kExpEmpty, bd = 0;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int64_t p = p_begin + lane; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, bd);
+    for (int o = 16; o; o >>= 1) {  // a fixed butterfly: deterministic
+      const int E2 = __shfl_xor_sync(0xffffffffu, E, o);
+      const float a2 = __shfl_xor_sync(0xffffffffu, acc, o);
+      bd |= __shfl_xor_sync(0xffffffffu, bd, o);
+      // both partners merge the same pair, lower lane first, so they agree bit for bit
+      if (lane & o) {
+        int El = E2;
+        float al = a2;
+        expmag_merge(El, al, E, acc);
+        E = El;
+        acc = al;
+      } else {
+        expmag_merge(E, acc, E2, a2);
+      }
+    }
+    if (lane == 0) {
+      pe[r * nkr + by] = E;
+      ps[r * nkr + by] = acc;
+      pb[r * nkr + by] = bd;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ PrepPair pp,
+                                                     const __grid_constant__ ExpMagParts parts) {
+  __shared__ int s_e[8][33];
+  __shared__ float s_s[8][33];
+  __shared__ int s_b[8][33];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig)
+    expmag_body<true>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.b[ji], bx, by, s_e, s_s, s_b);
+  else
+    expmag_body<false>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.b[ji], bx, by, s_e, s_s, s_b);
+}
+
+// per row of both sides: sig = the largest block exponent, bad = any flag, mu = the blocks'
+// sums rescaled to sig and added in block order (32.32 fixed point, as the magnitude pass)
+__global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp,
+                                                       const __grid_constant__ ExpMagParts parts) {
+  const int ji = blockIdx.y;
+  const PrepJob& j = pp.j[ji];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
+    const int* pe = parts.e[ji] + r * parts.nkr;
+    const float* ps = parts.s[ji] + r * parts.nkr;
+    const int* pb = parts.b[ji] + r * parts.nkr;
+    int E = kExpEmpty, bd = 0;
+    for (int q = 0; q < parts.nkr; ++q) {
+      E = max(E, pe[q]);
+      bd |= pb[q];
+    }
+    float mu = 0.0f;
+    if (E != kExpEmpty)
+      for (int q = 0; q < parts.nkr; ++q)
+        if (pe[q] != kExpEmpty) mu += ps[q] * pow2f_nonpos(pe[q] - E);
+    j.sig[r] = E;
+    j.bad[r] = bd;
+    if (j.mu) j.mu[r] = magnitude_fixed(mu);
+  }
+}
+
 __global__ void __launch_bounds__(kSplitThreads) k_split_pair(const __grid_constant__ PrepPair pp) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
@@ -672,6 +807,18 @@ int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t 
   if (exp_blocks <= 0) return GBD_OK;
   k_magnitudes_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, pp.j[0].K <= kRedChunk);
   return launch_check("magnitude launch");
+}
+
+int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s) {
+  if (exp_blocks <= 0) return GBD_OK;
+  if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many exponent blocks");
+  k_expmag_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, parts);
+  int rc = launch_check("exponent and magnitude launch");
+  if (rc) return rc;
+  const int64_t rmax = pp.j[0].R > pp.j[1].R ? pp.j[0].R : pp.j[1].R;
+  const unsigned gx = (unsigned)((rmax + 255) / 256 < 4096 ? (rmax + 255) / 256 : 4096);
+  k_rowstats_pair<<<dim3(gx > 0 ? gx : 1, 2), 256, 0, s>>>(pp, parts);
+  return launch_check("row statistics launch");
 }
 
 int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_blocks, cudaStream_t s) {
