@@ -135,6 +135,7 @@ struct ModSplit {
   float pf[kMaxModuli];
   float inv[kMaxModuli];
   uint32_t wlo[kMaxModuli], whi[kMaxModuli];
+  uint32_t wbias[kMaxModuli];  // 0x4B000000 + (-2^23 mod p): the byte sum read as 2^23 + s in FP32
   const ModPlan* plan;
 };
 // residue slices D[i][r][kp] of both sides (slices = n) from the rounded scaled integers

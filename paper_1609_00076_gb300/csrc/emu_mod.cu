@@ -1062,6 +1062,7 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     }
     ms.wlo[l] = lo;
     ms.whi[l] = hi;
+    ms.wbias[l] = 0x4B000000u + ((uint32_t)pm - (8388608u % (uint32_t)pm)) % (uint32_t)pm;
   }
   ms.plan = ws.plan;
   if ((rc = launch_residue_pair(pp, ms, split_blocks, s))) return rc;

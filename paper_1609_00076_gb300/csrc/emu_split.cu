@@ -306,10 +306,11 @@ __device__ __forceinline__ int64_t rounded_scaled(uint64_t bits, int sigma, int 
 }
 
 // the residues of the modular emulation (writer of split_body): for each modulus p, a residue
-// of A' = rint(x 2^(t - sigma)) of magnitude at most 128 (exact in BF16).  |A'| mod p is
-// reduced from s = sum_d byte_d (256^d mod p) < 2^20 as r = s - p rint(s/p) in FP32, exact: the
-// rounded quotient errs by less than 2^-11, so |r| <= p/2 + p 2^-11, that is |r| <= 128.  The
-// sign of A' is then set on its bits.
+// of A' = rint(x 2^(t - sigma)) of magnitude at most 128 (exact in BF16).  The bytes of |A'|
+// weighted by 256^d mod p sum, with the start value wbias = 0x4B000000 + c (c = -2^23 mod p),
+// to the FP32 bits of x = 2^23 + s' with s' < 2^20 + p, so x = |A'| (mod p).  One fma gives
+// q = rint(x * fl(1/p)), within 1/p of x/p, so r = x - p q (exact in one fma) has |r| <= p/2 + 1,
+// that is |r| <= 128 for every modulus; the sign of A' is then set on the BF16 pair.
 struct ResidueWriter {
   const ModSplit* mp;  // in the kernel's parameter space
   int n, t;            // from the call's plan
@@ -318,31 +319,31 @@ struct ResidueWriter {
   int64_t kp;
   __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
                                              int64_t pbase) const {
-    uint32_t lo[kPerThread], hi[kPerThread], sgn[kPerThread];  // the bytes of |A'| (0..3, 4..7), its sign
+    uint32_t lo[kPerThread], hi[kPerThread];  // the bytes of |A'| (0..3, 4..7)
+    uint32_t sgn[kPerThread / 2];             // sign bits 15 and 31 of each BF16 pair
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
       const int64_t q = rounded_scaled(x[v], sg, t);
       const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
       lo[v] = (uint32_t)a;
       hi[v] = (uint32_t)(a >> 32);
-      sgn[v] = q < 0 ? 0x80000000u : 0u;
+      if (v & 1) sgn[v / 2] |= q < 0 ? 0x80000000u : 0u;
+      else sgn[v / 2] = q < 0 ? 0x00008000u : 0u;
     }
     const bool full = pbase + kPerThread <= K;
     for (int i = 0; i < n; ++i) {
       const float pf = mp->pf[i], inv = mp->inv[i];
-      const uint32_t wl = mp->wlo[i], wh = mp->whi[i];  // 256^d mod p, one byte per d
+      const uint32_t wl = mp->wlo[i], wh = mp->whi[i], wb = mp->wbias[i];  // 256^d mod p, one byte per d
       uint32_t bits[kPerThread];
 #pragma unroll
       for (int v = 0; v < kPerThread; ++v) {
-        const uint32_t s = __dp4a(lo[v], wl, __dp4a(hi[v], wh, 0u));
-        const float sf = __uint_as_float(s | 0x4B000000u) - 8388608.0f;  // s exactly (s < 2^23)
-        const float qf = fmaf(sf, inv, 12582912.0f) - 12582912.0f;          // rint(s/p)
-        const float rf = fmaf(-pf, qf, sf);                                  // exact
-        bits[v] = __float_as_uint(rf) ^ sgn[v];
+        const float xf = __uint_as_float(__dp4a(lo[v], wl, __dp4a(hi[v], wh, wb)));  // 2^23 + s'
+        const float qf = fmaf(xf, inv, 12582912.0f) - 12582912.0f;                 // rint(x/p), to 1/p
+        bits[v] = __float_as_uint(fmaf(-pf, qf, xf));                               // r, exact
       }
       uint32_t packed[kPerThread / 2];  // BF16 pairs: the upper halves of the FP32 bits (exact here)
 #pragma unroll
-      for (int v = 0; v < kPerThread; v += 2) packed[v / 2] = __byte_perm(bits[v], bits[v + 1], 0x7632);
+      for (int v = 0; v < kPerThread; v += 2) packed[v / 2] = __byte_perm(bits[v], bits[v + 1], 0x7632) ^ sgn[v / 2];
       uint16_t* row = D + ((int64_t)i * R + r) * kp + pbase;
       if (full) {
         *reinterpret_cast<uint4*>(row) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ P
   }
 }
 
-__global__ void __launch_bounds__(kSplitThreads) k_split_pair(const __grid_constant__ PrepPair pp) {
+__global__ void __launch_bounds__(kSplitThreads, 3) k_split_pair(const __grid_constant__ PrepPair pp) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_pair(const __grid_const
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
-__global__ void __launch_bounds__(kSplitThreads) k_residue_pair(const __grid_constant__ PrepPair pp,
+__global__ void __launch_bounds__(kSplitThreads, 3) k_residue_pair(const __grid_constant__ PrepPair pp,
                                                                 const __grid_constant__ ModSplit mp) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
