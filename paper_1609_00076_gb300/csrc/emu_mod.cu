@@ -51,6 +51,11 @@ struct ModArgs {
   int64_t m, n, ldc;
   int nkb;
   int tiles_m, num_tiles, group_m;
+  int tile_end;  // the two-SM form computes tiles [0, tile_end) of its num_tiles
+  // a one-SM launch over the tail of a two-SM raster (tail_from >= 0): its tile u is quadrant
+  // u % 4 of the 256 x 256 tile tail_from + u / 4 of that raster (tail_tiles_m, tail_group_m,
+  // tail_num as tiles_m, group_m and num_tiles of the two-SM launch)
+  int tail_from, tail_tiles_m, tail_group_m, tail_num;
   int p[kMaxModuli];         // moduli
   uint32_t bar[kMaxModuli];  // floor(2^32 / p_l), for Barrett reduction
   uint32_t rq[kMaxModuli];   // ceil(2^24 / p_l)
@@ -68,6 +73,18 @@ struct ModArgs {
   unsigned int* tile_done;   // [tile] finished units (zero at launch)
   unsigned int* err;
 };
+
+// the coordinates, in 128 x 128 tiles, of tile `tile` of a one-SM launch
+__device__ __forceinline__ void tile128_coords(const ModArgs& p, int tile, int& tm, int& tn) {
+  if (p.tail_from < 0) {
+    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    return;
+  }
+  int tm2, tn2;
+  tile_coords(p.tail_from + tile / 4, p.tail_tiles_m, p.tail_group_m, p.tail_num, tm2, tn2);
+  tm = 2 * tm2 + (tile & 1);
+  tn = 2 * tn2 + ((tile >> 1) & 1);
+}
 
 // the moduli [l0, l1) of work unit g of `groups` (at most nmod units per tile)
 __device__ __forceinline__ void unit_range(int g, int groups, int nmod, int& l0, int& l1) {
@@ -222,9 +239,11 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
   uint32_t chunk = 0;
   int acc[COLS];
   int tcount = 0;
-  for (int tile = tile0; tile < p.num_tiles; tile += tile_step, ++tcount) {
+  const int tile_end = PAIR ? p.tile_end : p.num_tiles;
+  for (int tile = tile0; tile < tile_end; tile += tile_step, ++tcount) {
     int tm, tn;
-    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    if (PAIR) tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    else tile128_coords(p, tile, tm, tn);
     const int64_t i = (int64_t)tm * tbm + row_off + row;
     const int64_t jc0 = (int64_t)tn * TBN + col0;
     const int slot = tcount & 1;
@@ -469,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int l0 = 0, l1 = nmod;
         if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
         int tm, tn;
-        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        tile128_coords(p, tile, tm, tn);
         for (int l = l0; l < l1; ++l)
           for (int kb = 0; kb < p.nkb; ++kb) {
             mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
@@ -609,7 +628,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
-      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs) {
+      for (int tile = pair_id; tile < p.tile_end; tile += num_pairs) {
         int tm, tn;
         tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
         const int m0 = tm * k2BM + (int)rank * 128;
@@ -632,7 +651,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
       constexpr uint32_t idesc = idesc_bf16(k2BM, k2BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = pair_id; tile < p.num_tiles; tile += num_pairs)
+      for (int tile = pair_id; tile < p.tile_end; tile += num_pairs)
         for (int l = 0; l < nmod; ++l)
           for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
             const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
@@ -866,7 +885,8 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
                     cudaStream_t stream) {
   // GBD_EMU_KERNEL=pair|single|split overrides the choice (tests and tuning).  Otherwise the
   // expected time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs
-  // (or SM pairs), a 256 x 256 tile being four units on two SMs at kModPairGain; and the one-SM
+  // (or SM pairs), a 256 x 256 tile being four units on two SMs at kModPairGain, a last wave
+  // that leaves pairs idle going to one-SM CTAs when its quarters fit one wave; and the one-SM
   // form splits the moduli of each tile over several CTAs for at most 8 tiles, or for fewer
   // tiles than half the SMs with a deep inner dimension (k >= 2048); measured at 256^3 (4
   // tiles) 0.145 against 0.169 ms, 256^2 x 4096 0.25 against 0.47 ms, but 512^3 (16 tiles) 0.22
@@ -878,8 +898,13 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const int64_t tiles1 = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
   const int64_t tiles2 = ((m + k2BM - 1) / k2BM) * ((n + k2BN - 1) / k2BN);
   const int64_t pairs_avail = cta_cap / 2 > 0 ? cta_cap / 2 : 1;
+  const int64_t pairs = tiles2 < pairs_avail ? tiles2 : pairs_avail;
+  const int64_t waves2 = (tiles2 + pairs - 1) / pairs;
+  const int64_t last = tiles2 - (waves2 - 1) * pairs;  // tiles of the last two-SM wave
+  const char* tail_env = getenv("GBD_EMU_TAIL");       // GBD_EMU_TAIL=0 keeps the last wave on the pairs
+  const bool tail = waves2 > 1 && last < pairs && 4 * last <= cta_cap && !(tail_env && tail_env[0] == '0');
   const double t_one = (double)((tiles1 + cta_cap - 1) / cta_cap);
-  const double t_pair = (double)((tiles2 + pairs_avail - 1) / pairs_avail) * 2.0 / kModPairGain;
+  const double t_pair = tail ? (double)(waves2 - 1) * 2.0 / kModPairGain + 1.0 : (double)waves2 * 2.0 / kModPairGain;
   const bool pair = (force ? force[0] == 'p' : t_pair < t_one) && cta_cap >= 2;
   const uint32_t brows = pair ? 128u : (uint32_t)kBM;  // rows of A (and of op(B)^T) one CTA stages
   CUtensorMap tmA, tmB;
@@ -901,6 +926,9 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const int64_t tiles = (int64_t)a.tiles_m * ((n + tbn - 1) / tbn);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
+  a.tile_end = (int)tiles;
+  a.tail_from = -1;
+  a.tail_tiles_m = a.tail_group_m = a.tail_num = 0;
   cudaError_t e;
   const bool split = !pair && ws.tslot != nullptr &&
                      (force_split || (!force && (tiles <= 8 || (2 * tiles < sms && k >= 2048))));
@@ -919,11 +947,28 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm split)");
     k_mod_gemm<true><<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
   } else if (pair) {
-    const int pairs = (int)(tiles < pairs_avail ? tiles : pairs_avail);
-    a.group_m = group_rows(pairs, k2BM, k2BN, a.tiles_m);
+    a.group_m = group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
+    // a last wave that would leave SM pairs idle goes to one-SM CTAs instead, as four 128 x 128
+    // tiles per 256 x 256 tile, when they fill at most one wave of SMs: it then takes about
+    // kModPairGain / 2 of a two-SM wave
+    if (tail) a.tile_end = (int)(tiles - last);
     e = cudaFuncSetAttribute(k_mod_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm pair)");
     k_mod_gemm_pair<<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
+    if (tail) {
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "modular gemm pair launch");
+      ModArgs b = a;
+      b.tail_from = a.tile_end;
+      b.tail_tiles_m = a.tiles_m;
+      b.tail_group_m = a.group_m;
+      b.tail_num = a.num_tiles;
+      b.tiles_m = 0;
+      b.group_m = 1;
+      b.num_tiles = b.tile_end = (int)(4 * last);
+      e = cudaFuncSetAttribute(k_mod_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm)");
+      k_mod_gemm<false><<<(unsigned)(4 * last), kThreads, Smem::kAlloc, stream>>>(b, tmA, tmB);
+    }
   } else {
     const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);

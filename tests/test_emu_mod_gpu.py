@@ -86,6 +86,18 @@ def test_model_parity_fringes(oracle_mod, monkeypatch, kernel, m, n, k):
     check_model(oracle_mod, "T", "N", m, n, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, out, 30)
 
 
+@pytest.mark.parametrize("tail", ["1", "0"])
+def test_model_parity_pair_with_tail_wave(oracle_mod, monkeypatch, tail):
+    # 9 x 10 tiles of 256 x 256 over the SM pairs leave a partial last wave; by default its
+    # tiles run as 128 x 128 quarters on one-SM CTAs after the two-SM launch (ragged in m, n, k)
+    monkeypatch.setenv("GBD_EMU_KERNEL", "pair")
+    monkeypatch.setenv("GBD_EMU_TAIL", tail)
+    m, n, k = 2300, 2310, 100
+    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "uniform", 77, pads=(1, 2, 3))
+    out, _ = run_mod("N", "T", m, n, k, 0.5, A, lda, B, ldb, -1.5, C, ldc, 36)
+    check_model(oracle_mod, "N", "T", m, n, k, 0.5, A, lda, B, ldb, -1.5, C, ldc, out, 36)
+
+
 def test_integer_inputs_bit_exact(oracle_mod):
     m, n, k = 150, 170, 900
     A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "int8", 7, pads=(1, 1, 1))
