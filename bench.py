@@ -516,29 +516,38 @@ def split_measure(dev, stream, A, B, C, ws, wsb, steps: int, warmup: int):
 
 def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
     """Device time of the GEMM-based DSYRK, DTRMM and DTRSM (side L, lower, N, non-unit) at n,
-    native and emulated (each product at its FP64 bound), on well-conditioned triangles."""
+    native and emulated (each product at its FP64 bound): DSYRK on uniform[-1,1) A (the GEMM's
+    inputs), the triangular operations on the well-conditioned A/n + 1.5 I; emulated DSYRK also
+    on that diagonally dominant A ("dsyrk_dominant"), whose rows need more than 16 moduli at the
+    FP64 bound, so that its products fall back to the split emulation."""
     import numpy as np
     import torch
 
     from paper_1609_00076_gb300 import gbdgemm, synth
     A = torch.from_numpy(synth.uniform_pm1(seed, n * n) / n).to(dev)
     A.view(n, n).diagonal().add_(1.5)
+    Au = torch.from_numpy(synth.uniform_pm1(seed + 2, n * n)).to(dev)
     B0 = torch.from_numpy(synth.uniform_pm1(seed + 1, n * n)).to(dev)
     B = torch.empty_like(B0)
     C = torch.zeros(n * n, dtype=torch.float64, device=dev)
-    out = {"n": n, "config": "dsyrk L,N n=k; dtrmm/dtrsm side L, lower, N, non-unit, m=n; A/n + 1.5 I, B uniform[-1,1)",
-           "flops": {"dsyrk": float(n) * n * n, "dtrmm": float(n) * n * n, "dtrsm": float(n) * n * n}}
+    out = {"n": n, "config": "dsyrk L,N n=k, A uniform[-1,1) (dsyrk_dominant: A/n + 1.5 I); dtrmm/dtrsm side L, "
+                             "lower, N, non-unit, m=n, A/n + 1.5 I, B uniform[-1,1)",
+           "flops": {"dsyrk": float(n) * n * n, "dtrmm": float(n) * n * n, "dtrsm": float(n) * n * n,
+                     "dsyrk_dominant": float(n) * n * n}}
     for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("emulated", gbdgemm.GBD_MODE_EMULATED)):
         wsb = max(gbdgemm.gbd_dsyrk_workspace_size(n, n, mode), gbdgemm.gbd_dtrmm_workspace_size("L", n, n, mode),
                   gbdgemm.gbd_dtrsm_workspace_size("L", n, n, mode))
         ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
         calls = {
-            "dsyrk": lambda: gbdgemm.gbd_dsyrk("L", "N", n, n, 1.0, A, n, 0.0, C, n, mode, 0.0, ws, wsb, stream=stream),
+            "dsyrk": lambda: gbdgemm.gbd_dsyrk("L", "N", n, n, 1.0, Au, n, 0.0, C, n, mode, 0.0, ws, wsb, stream=stream),
             "dtrmm": lambda: gbdgemm.gbd_dtrmm("L", "L", "N", "N", n, n, 1.0, A, n, B, n, mode, 0.0, ws, wsb,
                                                stream=stream),
             "dtrsm": lambda: gbdgemm.gbd_dtrsm("L", "L", "N", "N", n, n, 1.0, A, n, B, n, mode, 0.0, ws, wsb,
                                                stream=stream),
         }
+        if mode == gbdgemm.GBD_MODE_EMULATED:
+            calls["dsyrk_dominant"] = lambda: gbdgemm.gbd_dsyrk("L", "N", n, n, 1.0, A, n, 0.0, C, n, mode, 0.0, ws, wsb,
+                                                                stream=stream)
         res = {}
         for op, fn in calls.items():
             reps = 1 if mode == gbdgemm.GBD_MODE_NATIVE else 3

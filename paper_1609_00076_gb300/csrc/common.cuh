@@ -40,6 +40,13 @@ int encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const voi
                 CUtensorMapSwizzle swizzle);
 // launches the C := beta*C quick path (alpha == 0 or k == 0)
 int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t stream);
+// (emu_mod.cu) C := alpha op(A) op(B) + beta C on the lower (upper != 0: upper) triangle of the
+// n x n C only, by the modular emulation in automatic mode (bits chosen on the host, which
+// synchronises `stream`): tiles off the triangle are skipped, elements off it neither read nor
+// written.  alpha != 0, k > 0.  GBD_ERR_LIMIT (C untouched) when 16 moduli cannot reach `tol`.
+int dgemm_emu_mod_tri(char transa, char transb, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int upper, double tol,
+                      void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 // error-word bits
 constexpr unsigned int kErrWaitTma = 1u;     // a wait for a TMA tile gave up

@@ -52,6 +52,9 @@ struct ModArgs {
   int nkb;
   int tiles_m, num_tiles, group_m;
   int tile_end;  // the two-SM form computes tiles [0, tile_end) of its num_tiles
+  int tri;       // 0: all of C; 1: only its lower triangle (i >= j), 2: its upper one (m = n): the
+                 // tiles are those that meet the triangle, and elements outside it are neither
+                 // read nor written
   // a one-SM launch over the tail of a two-SM raster (tail_from >= 0): its tile u is quadrant
   // u % 4 of the 256 x 256 tile tail_from + u / 4 of that raster (tail_tiles_m, tail_group_m,
   // tail_num as tiles_m, group_m and num_tiles of the two-SM launch)
@@ -74,14 +77,37 @@ struct ModArgs {
   unsigned int* err;
 };
 
+// tile t of a triangle of tiles, by rows: (r, c) with c <= r, t = r (r + 1) / 2 + c
+__device__ __forceinline__ void tri_tile(int t, int& r, int& c) {
+  int q = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // corrected below
+  while ((int64_t)(q + 1) * (q + 2) / 2 <= t) ++q;
+  while (q > 0 && (int64_t)q * (q + 1) / 2 > t) --q;
+  r = q;
+  c = t - (int)((int64_t)q * (q + 1) / 2);
+}
+
+// the coordinates of tile `tile` of a launch: group-M rows over all tiles, or, for a triangular
+// output, the tiles that meet the triangle, by rows
+__device__ __forceinline__ void raster_coords(int tri, int tile, int tiles_m, int group_m, int num_tiles, int& tm,
+                                              int& tn) {
+  if (tri == 0) {
+    tile_coords(tile, tiles_m, group_m, num_tiles, tm, tn);
+    return;
+  }
+  int r, c;
+  tri_tile(tile, r, c);
+  tm = tri == 1 ? r : c;
+  tn = tri == 1 ? c : r;
+}
+
 // the coordinates, in 128 x 128 tiles, of tile `tile` of a one-SM launch
 __device__ __forceinline__ void tile128_coords(const ModArgs& p, int tile, int& tm, int& tn) {
   if (p.tail_from < 0) {
-    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
     return;
   }
   int tm2, tn2;
-  tile_coords(p.tail_from + tile / 4, p.tail_tiles_m, p.tail_group_m, p.tail_num, tm2, tn2);
+  raster_coords(p.tri, p.tail_from + tile / 4, p.tail_tiles_m, p.tail_group_m, p.tail_num, tm2, tn2);
   tm = 2 * tm2 + (tile & 1);
   tn = 2 * tn2 + ((tile >> 1) & 1);
 }
@@ -199,7 +225,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
 
   // the pending reconstruction: this thread's row and columns of the previous tile
   bool pd_active = false, pd_bad = false;
-  int pd_done = 0, pd_slot = 0, pd_sig = 0, pd_cols = 0;
+  int pd_done = 0, pd_slot = 0, pd_sig = 0, pd_cols = 0, pd_first = 0;  // columns [pd_first, pd_cols) are written
   double* pd_c = nullptr;
   const double* pd_cs = nullptr;
   auto advance = [&](int ngroups) {
@@ -208,6 +234,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
     for (int g = pd_done; g < g1; ++g) {
       const int c0 = 4 * g;
       if (c0 >= pd_cols) break;
+      if (c0 + 4 <= pd_first) continue;
       uint32_t w4[kMaxModuli];  // the bytes of columns c0..c0+3, one word per modulus
 #pragma unroll
       for (int l = 0; l < kMaxModuli; ++l)
@@ -215,13 +242,14 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
       double c0v[4], csv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const bool in = c0 + q < pd_cols;
+        const bool in = c0 + q < pd_cols && c0 + q >= pd_first;
         c0v[q] = (in && p.beta != 0.0) ? pd_c[(int64_t)(c0 + q) * p.ldc] : 0.0;
         csv[q] = in ? pd_cs[c0 + q] : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (c0 + q >= pd_cols) break;
+        if (c0 + q < pd_first) continue;
         uint32_t u[kMaxModuli];
 #pragma unroll
         for (int l = 0; l < kMaxModuli; ++l) u[l] = (w4[l] >> (8 * q)) & 0xFFu;
@@ -242,7 +270,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
   const int tile_end = PAIR ? p.tile_end : p.num_tiles;
   for (int tile = tile0; tile < tile_end; tile += tile_step, ++tcount) {
     int tm, tn;
-    if (PAIR) tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    if (PAIR) raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
     else tile128_coords(p, tile, tm, tn);
     const int64_t i = (int64_t)tm * tbm + row_off + row;
     const int64_t jc0 = (int64_t)tn * TBN + col0;
@@ -291,6 +319,9 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
     pd_done = 0;
     pd_slot = slot;
     pd_cols = row_ok && jc0 < p.n ? (int)min((int64_t)COLS, p.n - jc0) : 0;
+    pd_first = 0;
+    if (p.tri == 1) pd_cols = (int)max((int64_t)0, min((int64_t)pd_cols, i - jc0 + 1));  // j <= i
+    else if (p.tri == 2) pd_first = (int)max((int64_t)0, i - jc0);                      // j >= i
     pd_sig = 0;
     pd_bad = false;
     if (row_ok) {
@@ -630,7 +661,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
       const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
       for (int tile = pair_id; tile < p.tile_end; tile += num_pairs) {
         int tm, tn;
-        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
         const int m0 = tm * k2BM + (int)rank * 128;
         const int nb0 = tn * k2BN + (int)rank * 128;
         for (int l = 0; l < nmod; ++l)
@@ -895,8 +926,13 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const bool force_split = force && strcmp(force, "split") == 0;
   if (force_split) force = nullptr;
   const int cta_cap = sms < ws.scr_ctas ? sms : ws.scr_ctas;
-  const int64_t tiles1 = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
-  const int64_t tiles2 = ((m + k2BM - 1) / k2BM) * ((n + k2BN - 1) / k2BN);
+  // a triangular output (m = n) covers the tiles that meet its triangle
+  auto count = [&](int64_t bm, int64_t bn) {
+    const int64_t tm = (m + bm - 1) / bm, tn = (n + bn - 1) / bn;
+    return a.tri ? tm * (tm + 1) / 2 : tm * tn;
+  };
+  const int64_t tiles1 = count(kBM, kBN);
+  const int64_t tiles2 = count(k2BM, k2BN);
   const int64_t pairs_avail = cta_cap / 2 > 0 ? cta_cap / 2 : 1;
   const int64_t pairs = tiles2 < pairs_avail ? tiles2 : pairs_avail;
   const int64_t waves2 = (tiles2 + pairs - 1) / pairs;
@@ -923,14 +959,14 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   a.nkb = (int)((k + kBK - 1) / kBK);
   const int tbm = pair ? k2BM : kBM, tbn = pair ? k2BN : kBN;
   a.tiles_m = (int)((m + tbm - 1) / tbm);
-  const int64_t tiles = (int64_t)a.tiles_m * ((n + tbn - 1) / tbn);
+  const int64_t tiles = count(tbm, tbn);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
   a.tile_end = (int)tiles;
   a.tail_from = -1;
   a.tail_tiles_m = a.tail_group_m = a.tail_num = 0;
   cudaError_t e;
-  const bool split = !pair && ws.tslot != nullptr &&
+  const bool split = !pair && ws.tslot != nullptr && a.tri == 0 &&
                      (force_split || (!force && (tiles <= 8 || (2 * tiles < sms && k >= 2048))));
   if (split) {
     int groups = (int)((sms + tiles - 1) / tiles);  // the kernel keeps at most nmod of them
@@ -984,30 +1020,15 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
 }  // namespace emu
 }  // namespace gbd
 
-extern "C" {
+namespace gbd {
+namespace emu {
 
-size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits) {
-  if (m < 0 || n < 0 || k < 0) return 0;
-  int nmod = gbd::emu::kMaxModuli;
-  if (bits > 0) {
-    const int nm = gbd::emu::moduli_for(bits, k > 0 ? k : 1);
-    if (nm > 0) nmod = nm;
-  }
-  return gbd::emu::mod_layout(m, n, k, nmod, nullptr, nullptr);
-}
-
-int gbd_dgemm_emu_mod_moduli(int bits, int64_t k, int* moduli) {
-  const int n = gbd::emu::moduli_for(bits, k);
-  if (moduli)
-    for (int l = 0; l < n; ++l) moduli[l] = gbd::emu::kModuli[l];
-  return n;
-}
-
-int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
-                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int bits,
-                      double tol, void* workspace, size_t workspace_bytes, gbd_emu_info* info, void* stream) {
-  using namespace gbd;
-  using namespace gbd::emu;
+// gbd_dgemm_emu_mod, and the triangular-output form of DSYRK (tri = 1 lower, 2 upper; m = n,
+// alpha != 0, k > 0): only the elements of C on that triangle are read and written
+int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int bits,
+                       double tol, void* workspace, size_t workspace_bytes, gbd_emu_info* info, void* stream,
+                       int tri) {
   int rc = check_dgemm_args(transa, transb, m, n, k, lda, ldb, ldc);
   if (rc) return rc;
   if (info) {
@@ -1019,6 +1040,8 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     return set_error(GBD_ERR_ARG, "dgemm_emu_mod: bits must be -1 or 0 (automatic) or 1..62");
   if (m == 0 || n == 0) return GBD_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (tri && (m != n || alpha == 0.0 || k == 0))
+    return set_error(GBD_ERR_ARG, "dgemm_emu_mod: a triangular output needs m = n, alpha != 0 and k > 0");
   if (alpha == 0.0 || k == 0) return scale_c(m, n, beta, C, ldc, s);
   const int64_t lim = (int64_t)1 << 31;
   if (m >= lim || n >= lim || k >= lim)
@@ -1117,6 +1140,7 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
   // products modulo each modulus and the reconstruction; the constants of every n ride along
   ModArgs a;
   memset(&a, 0, sizeof(a));
+  a.tri = tri;
   for (int l = 0; l < kMaxModuli; ++l) {
     a.p[l] = kModuli[l];
     a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
@@ -1170,6 +1194,46 @@ int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k,
     info->bound_est = host_plan.bound;
   }
   return GBD_OK;
+}
+
+}  // namespace emu
+}  // namespace gbd
+
+namespace gbd {
+
+int dgemm_emu_mod_tri(char transa, char transb, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int upper, double tol,
+                      void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  return emu::dgemm_emu_mod_impl(transa, transb, n, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0, tol, workspace,
+                                 workspace_bytes, nullptr, stream, upper ? 2 : 1);
+}
+
+}  // namespace gbd
+
+extern "C" {
+
+size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits) {
+  if (m < 0 || n < 0 || k < 0) return 0;
+  int nmod = gbd::emu::kMaxModuli;
+  if (bits > 0) {
+    const int nm = gbd::emu::moduli_for(bits, k > 0 ? k : 1);
+    if (nm > 0) nmod = nm;
+  }
+  return gbd::emu::mod_layout(m, n, k, nmod, nullptr, nullptr);
+}
+
+int gbd_dgemm_emu_mod_moduli(int bits, int64_t k, int* moduli) {
+  const int n = gbd::emu::moduli_for(bits, k);
+  if (moduli)
+    for (int l = 0; l < n; ++l) moduli[l] = gbd::emu::kModuli[l];
+  return n;
+}
+
+int gbd_dgemm_emu_mod(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int bits,
+                      double tol, void* workspace, size_t workspace_bytes, gbd_emu_info* info, void* stream) {
+  return gbd::emu::dgemm_emu_mod_impl(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bits, tol,
+                                      workspace, workspace_bytes, info, stream, 0);
 }
 
 }  // extern "C"

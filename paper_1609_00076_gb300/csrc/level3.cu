@@ -6,7 +6,10 @@
 //
 // Each operation recurses on halves of its triangle (split points on multiples of 64):
 //   DSYRK  C11 := syrk(A1); C21 (or C12) := GEMM; C22 := syrk(A2).  A diagonal block of at
-//          most 512 is one GEMM into scratch followed by a copy of its triangle.
+//          most 512 is one GEMM into scratch followed by a copy of its triangle.  In emulated
+//          mode, when the whole triangle would go to the modular emulation, it is instead one
+//          modular product whose tiles cover only the triangle (the recursion's products are
+//          smaller, and each pays the emulation's fixed costs).
 //   DTRMM  one half through the recursion, the coupling block as one GEMM with beta = 1,
 //          ordered so every GEMM reads only blocks not yet overwritten.  A diagonal block of
 //          at most 512: the triangle packed with zeros (and a unit diagonal), one GEMM into
@@ -217,6 +220,11 @@ struct Ctx {
   void thresholds() {
     native_flops = threshold("GBD_L3_NATIVE_FLOPS", kNativeFlops);
     modular_outputs = threshold("GBD_L3_MODULAR_OUTPUTS", kModularOutputs);
+  }
+  // DSYRK in emulated mode: the whole n x n triangle as one modular product
+  bool syrk_modular(int64_t n, int64_t k) const {
+    return mode != GBD_MODE_NATIVE && (double)n * (double)n * (double)k > native_flops &&
+           0.5 * (double)n * (double)n >= modular_outputs;
   }
 
   int gemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
@@ -555,6 +563,10 @@ size_t gbd_dsyrk_workspace_size(int64_t n, int64_t k, int mode) {
     y.upper = up;
     y.run(0, n);
   }
+  if (c.syrk_modular(n, k)) {
+    const size_t w = gbd_dgemm_emu_mod_workspace_size(n, n, k, 0);
+    if (w > c.need) c.need = w;
+  }
   return syrk_scratch(n) + up256(c.need);
 }
 
@@ -615,6 +627,11 @@ int gbd_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const d
   y.lda = lda;
   y.C = C;
   y.ldc = ldc;
+  if (c.syrk_modular(n, k)) {  // one product over the triangle; the recursion when 16 moduli fall short
+    rc = dgemm_emu_mod_tri(tr ? 'T' : 'N', tr ? 'N' : 'T', n, k, alpha, A, lda, A, lda, beta, C, ldc, up, tol, c.gws,
+                           c.gwsb, s);
+    if (rc != GBD_ERR_LIMIT) return rc;
+  }
   return y.run(0, n);
 }
 

@@ -111,6 +111,41 @@ def test_syrk_within_bound(oracle_mod, products, mode, uplo, trans):
     assert np.all(err <= 2 * k * U * G[tri]), float(np.max(err / (2 * k * U * G[tri])))
 
 
+@pytest.mark.parametrize("kernel,n", [("single", 700), ("pair", 700), ("pair", 3022)])
+@pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
+def test_syrk_modular_triangle(oracle_mod, products, monkeypatch, kernel, n, uplo, trans):
+    # emulated DSYRK as one modular product over the tiles that meet the triangle, on the one-SM
+    # and two-SM kernels; at n = 3022 the 78 tiles of 256 x 256 leave a last wave of 2 tiles,
+    # which runs as one-SM quarters
+    products("modular")
+    monkeypatch.setenv("GBD_EMU_KERNEL", kernel)
+    k = 300 if n < 1000 else 64
+    ra, ca = (n, k) if trans == "N" else (k, n)
+    lda, ldc = ra + 1, n + 3
+    A = synth.matrix("uniform", ra, ca, lda, 15)
+    C0 = synth.matrix("uniform", n, n, ldc, 16)
+    other = ~np.tril(np.ones((n, n), bool)) if uplo == "L" else ~np.triu(np.ones((n, n), bool))
+    C0v = synth.view(C0, n, n, ldc)
+    C0v[other] = np.nan
+    ref = C0.copy()
+    assert oracle_mod.dsyrk(uplo, trans, n, k, -0.5, A, lda, 2.0, ref, ldc) == 0
+    dA, dC = DeviceBuf(A), DeviceBuf(C0)
+    wsb = gbdgemm.gbd_dsyrk_workspace_size(n, k, 1)
+    assert wsb >= gbdgemm.gbd_dgemm_emu_mod_workspace_size(n, n, k, 0)
+    ws = _ws(wsb)
+    assert gbdgemm.gbd_dsyrk(uplo, trans, n, k, -0.5, dA.ptr, lda, 2.0, dC.ptr, ldc, 1, 0.0, ws, wsb) == 0
+    _sync_ok()
+    assert dA.guards_intact() and dC.guards_intact()
+    got = synth.view(dC.host(), n, n, ldc)
+    op = synth.view(A, ra, ca, lda)
+    op = op if trans == "N" else op.T
+    G = 0.5 * np.abs(op) @ np.abs(op).T + 2.0 * np.abs(np.nan_to_num(C0v))
+    tri = ~other
+    assert np.all(np.isnan(got[other]))
+    err = np.abs(got[tri] - synth.view(ref, n, n, ldc)[tri])
+    assert np.all(err <= 2 * k * U * G[tri]), float(np.max(err / (2 * k * U * G[tri])))
+
+
 def test_syrk_large_emulated_within_bound(oracle_mod):
     # the 2048 x 2048 coupling block (4.2e6 outputs) goes to the modular emulation
     n, k = 4096, 256
