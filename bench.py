@@ -48,10 +48,11 @@ def workload_name():
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to FP64
 NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
-# dram bytes (read + write) per launch of the dominant kernel, from one single-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload; None until captured
-# for the current kernel
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 106.9e9, "mod": 23.15e9}
+# dram bytes (read + write) of the product phase of one call, from one single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload: the split slice kernel's
+# launch (its workspace the process's first large allocation), and the modular pair launch plus its
+# one-SM launch for the last wave (18.34 + 0.76 GB); None until captured for the current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.25e9, "mod": 19.10e9}
 
 
 def load_peaks():
@@ -429,10 +430,10 @@ def run_ours(args, world, rank, local, pg):
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads, rows, ref = oracle_sample(target_s=8.0, want_rows=True)
     accuracy = accuracy_report(results, rows, ref)
-    # prep init, exponents and magnitudes, row statistics, statistics, plan, residues, column scales,
-    # residue products (+ CRT) on SM pairs, and the products of a partial last wave of 256 x 256
-    # tiles on one-SM CTAs when their 128 x 128 quarters fit one wave of SMs
-    launches_per_step = 8 + mod_tail_launches(M, N, torch.cuda.get_device_properties(dev).multi_processor_count)
+    # exponents and magnitudes, row statistics, their minima, plan, residues, column scales, residue
+    # products (+ CRT) on SM pairs, and the products of a partial last wave of 256 x 256 tiles on
+    # one-SM CTAs when their 128 x 128 quarters fit one wave of SMs
+    launches_per_step = 7 + mod_tail_launches(M, N, torch.cuda.get_device_properties(dev).multi_processor_count)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -448,7 +449,8 @@ def run_ours(args, world, rank, local, pg):
         "phases_ms": {"prep": statistics.mean(prep_ms), "products_and_reconstruction": g_ms},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
-                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT)",
+                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT), with "
+                               "k_mod_gemm<0> for the last wave's tiles (cta_group::1)",
                      "peak_source": f"{src} bf16_tflops_sustained"},
         "split": {
             "value": split["value"], "unit": "TFLOP/s", "ms_per_call": split["ms"], "steps": split["steps"],
