@@ -109,7 +109,8 @@ struct ExpMagParts {
   int* e[2];
   float* s[2];
   int* b[2];
-  int nkr;  // k-blocks of kRedChunk per row
+  int nkr;       // k-blocks of kRedChunk per row
+  float* stats;  // {min mu over rows, min nu over columns, any bad row, any bad column}
 };
 int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);

@@ -764,14 +764,15 @@ __host__ __device__ double mod_relative_bound(int t, double mu_min, double nu_mi
   return ldexp(1.0, -t - 1) * 8.0 * kd * (1.0 / nu_min + 1.0 / mu_min + kd * ldexp(1.0, -t - 1) / (mu_min * nu_min));
 }
 
-// The call's plan, on one thread: t given (fixed_t > 0), or the smallest t whose estimated
+// The call's plan, on one warp: t given (fixed_t > 0), or the smallest t whose estimated
 // bound meets `tol` from the magnitude statistics; then n.  When no n <= kMaxModuli suffices
 // the plan is marked infeasible (n = 1, t = 1: the kernels then write NaN) and, for the
 // device-side automatic mode (`flag`), the device error word records it.
-__global__ void k_mod_plan(const float* __restrict__ stats, int64_t k, double tol, int fixed_t,
-                           const __grid_constant__ ModProducts mp, ModPlan* __restrict__ plan, unsigned int* err,
-                           int flag) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(32) k_mod_plan(const float* __restrict__ stats, int64_t k, double tol, int fixed_t,
+                                                  const __grid_constant__ ModProducts mp, ModPlan* __restrict__ plan,
+                                                  unsigned int* err, int flag) {
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
   double mu = 0.0, nu = 0.0, bound = 0.0;
   int t = fixed_t;
   if (fixed_t <= 0) {
@@ -779,17 +780,23 @@ __global__ void k_mod_plan(const float* __restrict__ stats, int64_t k, double to
     nu = stats[1] < 1e38f ? stats[1] : 0.0;
     t = 1;
     if (mu > 0.0 && nu > 0.0) {
+      // the warp's lanes try t = lane + 1 and t = lane + 33 at once; the smallest t that meets
+      // the target wins (63 when none of 1..62 does)
       t = 63;
-      for (int tt = 1; tt <= 62; ++tt) {
-        const double b = mod_relative_bound(tt, mu, nu, k);
-        if (b <= tol) {
-          t = tt;
-          bound = b;
+      for (int base = 1; base <= 62; base += 32) {
+        const int tt = base + lane;
+        const double b = tt <= 62 ? mod_relative_bound(tt, mu, nu, k) : 0.0;
+        const unsigned ok = __ballot_sync(0xffffffffu, tt <= 62 && b <= tol);
+        if (ok) {
+          const int first = __ffs(ok) - 1;
+          t = base + first;
+          bound = __shfl_sync(0xffffffffu, b, first);
           break;
         }
       }
     }
   }
+  if (lane != 0) return;
   const int n = moduli_for_products(t, k, mp);
   ModPlan pl;
   pl.t = n ? t : 1;
@@ -871,6 +878,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
       ws->parts.b[side] = reinterpret_cast<int*>(b + o_part[side][2]);
     }
     ws->parts.nkr = (int)nkr;
+    ws->parts.stats = ws->stats;
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -1092,8 +1100,7 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if (automatic) {  // exponents and magnitude sums in one pass over the operands
-    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
-    if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
+    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;  // and their minima
   } else if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) {
     return rc;
   }

@@ -546,9 +546,18 @@ __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_
     const int64_t r = bx * 32 + tx;
     int E = kExpEmpty, bd = 0;
     float acc = 0.0f;
-    if (r < R)
-#pragma unroll 4
-      for (int64_t p = p_begin + ty; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, bd);
+    if (r < R) {
+      // eight loads in flight per thread, then their folds in the same order
+      int64_t p = p_begin + ty;
+      for (; p + 56 < p_end; p += 64) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = load_bits<true>(X, ld, r, p + 8 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, bd);
+      }
+      for (; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, bd);
+    }
     s_e[ty][tx] = E;
     s_s[ty][tx] = acc;
     s_b[ty][tx] = bd;
@@ -569,8 +578,15 @@ __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_
     if (r >= R) return;
     int E = kExpEmpty, bd = 0;
     float acc = 0.0f;
-#pragma unroll 4
-    for (int64_t p = p_begin + lane; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, bd);
+    int64_t p = p_begin + lane;
+    for (; p + 224 < p_end; p += 256) {  // eight loads in flight per lane, then their folds in order
+      uint64_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = load_bits<false>(X, ld, r, p + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, bd);
+    }
+    for (; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, bd);
     for (int o = 16; o; o >>= 1) {  // a fixed butterfly: deterministic
       const int E2 = __shfl_xor_sync(0xffffffffu, E, o);
       const float a2 = __shfl_xor_sync(0xffffffffu, acc, o);
@@ -599,6 +615,12 @@ __global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ Pre
   __shared__ int s_e[8][33];
   __shared__ float s_s[8][33];
   __shared__ int s_b[8][33];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the minima start empty (k_rowstats_pair runs after this grid)
+    parts.stats[0] = 3.0e38f;
+    parts.stats[1] = 3.0e38f;
+    parts.stats[2] = 0.0f;
+    parts.stats[3] = 0.0f;
+  }
   const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
@@ -610,11 +632,17 @@ __global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ Pre
 }
 
 // per row of both sides: sig = the largest block exponent, bad = any flag, mu = the blocks'
-// sums rescaled to sig and added in block order (32.32 fixed point, as the magnitude pass)
+// sums rescaled to sig and added in block order (32.32 fixed point, as the magnitude pass);
+// then the side's minimum of the non-zero mu and its any-bad flag into stats (a minimum and an
+// OR: the same values in any order)
 __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp,
                                                        const __grid_constant__ ExpMagParts parts) {
+  __shared__ float s_mn[8];
+  __shared__ int s_bd[8];
   const int ji = blockIdx.y;
   const PrepJob& j = pp.j[ji];
+  float mn = 3.0e38f;
+  int any_bad = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
     const int* pe = parts.e[ji] + r * parts.nkr;
     const float* ps = parts.s[ji] + r * parts.nkr;
@@ -630,7 +658,29 @@ __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ P
         if (pe[q] != kExpEmpty) mu += ps[q] * pow2f_nonpos(pe[q] - E);
     j.sig[r] = E;
     j.bad[r] = bd;
-    if (j.mu) j.mu[r] = magnitude_fixed(mu);
+    const unsigned long long mq = magnitude_fixed(mu);
+    if (j.mu) j.mu[r] = mq;
+    if (mq > 0ull) mn = fminf(mn, magnitude_value(mq));
+    any_bad |= bd;
+  }
+  for (int o = 16; o; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    any_bad |= __shfl_xor_sync(0xffffffffu, any_bad, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_mn[w] = mn;
+    s_bd[w] = any_bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      mn = fminf(mn, s_mn[q]);
+      any_bad |= s_bd[q];
+    }
+    // non-negative floats order as their bit patterns
+    if (mn < 3.0e38f) atomicMin(reinterpret_cast<int*>(parts.stats + ji), __float_as_int(mn));
+    if (any_bad) atomicOr(reinterpret_cast<int*>(parts.stats + 2 + ji), __float_as_int(1.0f));
   }
 }
 

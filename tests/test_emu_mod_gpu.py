@@ -200,6 +200,41 @@ def test_deterministic():
     assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64)) and i1.digit_bits == i2.digit_bits
 
 
+@pytest.mark.parametrize("m,n,k", [(2048, 2048, 256), (4096, 4096, 256)])
+def test_kernel_launches_per_call(m, n, k):
+    # one call with the bits chosen on the device launches the kernels that the benchmark's
+    # launch count claims: six, plus one when the last two-SM wave runs on one-SM CTAs
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    import bench
+    A = torch.rand(m * k, dtype=torch.float64, device="cuda") - 0.5
+    B = torch.rand(k * n, dtype=torch.float64, device="cuda") - 0.5
+    C = torch.zeros(m * n, dtype=torch.float64, device="cuda")
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(m, n, k, -1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+
+    def call():
+        rc = gbdgemm.gbd_dgemm_emu_mod("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, -1, 0.0, ws, wsb, None)
+        assert rc == 0, gbdgemm.gbd_last_error()
+
+    call()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]):  # the profiler's own first use
+        C.add_(0.0)
+        torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        call()
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+    kernels = [x for x in names if "k_" in x and ("emu::" in x or "gbd::" in x)]
+    if not names:
+        pytest.skip("the profiler recorded no device activity here")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(kernels) == 6 + bench.mod_tail_launches(m, n, sms), kernels
+    assert gbdgemm.gbd_check_device_error() == 0
+
+
 @pytest.mark.parametrize("e", [0, 8])
 def test_device_side_automatic_mode_matches_the_synchronising_one(oracle_mod, e):
     # bits = -1 chooses on the device exactly as bits = 0 does, without any read-back
