@@ -18,7 +18,7 @@
 //          (beta = alpha folds the scaling in), the trailing half solved with alpha = 1.  The
 //          diagonal blocks of at most 64 are inverted together in one launch before the
 //          recursion (k_trsm_invert, substitution on the identity); each is then applied as a
-//          dense triangular product, one thread per element of the solution (k_trsm_apply).
+//          dense triangular product, one thread per two rows of a solution (k_trsm_apply).
 //          On GB300's narrow FP64 pipe this beats substitution on the right-hand sides, which
 //          leaves the pipe idle (one thread per right-hand side) or wastes it (one warp).
 // All work is stream-ordered on the caller's stream.  In emulated mode each product takes the
@@ -153,12 +153,27 @@ __global__ void __launch_bounds__(64) k_trsm_invert(const double* __restrict__ A
 // X := E^-1 (alpha V) for nvec right-hand sides of the b x b diagonal block whose inverse is
 // Dinv (row-major 64 x 64); element q of right-hand side u lives at B[q * sq + u * su].  A CTA
 // takes 16 right-hand sides: the inverse and the scaled right-hand sides are staged in shared
-// memory, then thread (s, v) forms row s of solution v.
-__global__ void __launch_bounds__(64 * kTrsmVecs) k_trsm_apply(const double* __restrict__ Dinv, int b, int lower,
+// memory, then thread (h, v) forms rows h and b - 1 - h of solution v.  Row s of a triangular
+// E^-1 has s + 1 (lower) or b - s (upper) terms, so each thread's pair has b + 1 and the
+// warp's lanes, which the FP64 pipe charges for whether busy or masked, all work alike.
+__device__ __forceinline__ double tri_row(const double (*Di)[65], const double (*R)[kTrsmVecs + 1], int s, int v, int b,
+                                          bool lower) {
+  const int t0 = lower ? 0 : s, t1 = lower ? s + 1 : b;
+  double x = 0.0, x1 = 0.0;
+  int t = t0;
+  for (; t + 1 < t1; t += 2) {
+    x = fma(Di[s][t], R[t][v], x);
+    x1 = fma(Di[s][t + 1], R[t + 1][v], x1);
+  }
+  if (t < t1) x = fma(Di[s][t], R[t][v], x);
+  return x + x1;
+}
+
+__global__ void __launch_bounds__(32 * kTrsmVecs) k_trsm_apply(const double* __restrict__ Dinv, int b, int lower,
                                                                double* __restrict__ B, int64_t sq, int64_t su,
                                                                int64_t nvec, double alpha) {
   __shared__ double Di[64][65];
-  __shared__ double R[64][kTrsmVecs];  // R[t][v]
+  __shared__ double R[64][kTrsmVecs + 1];  // R[t][v]; the pad spreads the row-fast staging over banks
   const int64_t u0 = (int64_t)blockIdx.x * kTrsmVecs;
   const int nv = (int)min((int64_t)kTrsmVecs, nvec - u0);
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) Di[idx / 64][idx % 64] = Dinv[idx];
@@ -168,21 +183,19 @@ __global__ void __launch_bounds__(64 * kTrsmVecs) k_trsm_apply(const double* __r
     R[q][v] = alpha * B[(int64_t)q * sq + (u0 + v) * su];
   }
   __syncthreads();
-  const int s = threadIdx.x % 64, v = threadIdx.x / 64;
-  double x = 0.0;
-  if (s < b && v < nv) {
-    const int t0 = lower ? 0 : s, t1 = lower ? s + 1 : b;
-    double x1 = 0.0;
-    int t = t0;
-    for (; t + 1 < t1; t += 2) {
-      x = fma(Di[s][t], R[t][v], x);
-      x1 = fma(Di[s][t + 1], R[t + 1][v], x1);
-    }
-    if (t < t1) x = fma(Di[s][t], R[t][v], x);
-    x += x1;
+  const int h = threadIdx.x % 32, v = threadIdx.x / 32;
+  const int s1 = b - 1 - h;  // the partner row (h itself for the middle row of an odd b)
+  const bool act = v < nv && h <= s1;
+  double x0 = 0.0, x1 = 0.0;
+  if (act) {
+    x0 = tri_row(Di, R, h, v, b, lower != 0);
+    if (s1 != h) x1 = tri_row(Di, R, s1, v, b, lower != 0);
   }
   __syncthreads();
-  if (s < b && v < nv) R[s][v] = x;
+  if (act) {
+    R[h][v] = x0;
+    if (s1 != h) R[s1][v] = x1;
+  }
   __syncthreads();
   for (int idx = threadIdx.x; idx < b * nv; idx += blockDim.x) {
     const int q = q_fast ? idx % b : idx / nv, vv = q_fast ? idx / b : idx % nv;
@@ -380,7 +393,7 @@ struct Tri {
       const int64_t nvec = side == 0 ? n : m;
       double* base = side == 0 ? Brow(r0) : Bcol(r0);
       const int64_t sq = side == 0 ? 1 : ldb, su = side == 0 ? ldb : 1;
-      k_trsm_apply<<<(unsigned)((nvec + kTrsmVecs - 1) / kTrsmVecs), 64 * kTrsmVecs, 0, c->s>>>(
+      k_trsm_apply<<<(unsigned)((nvec + kTrsmVecs - 1) / kTrsmVecs), 32 * kTrsmVecs, 0, c->s>>>(
           c->inverse_at(r0), (int)b, lowerE, base, sq, su, nvec, alpha);
       return c->check("triangular solve launch");
     }
