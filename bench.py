@@ -50,9 +50,10 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
 # dram bytes (read + write) of the product phase of one call, from one single-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload: the split slice kernel's
-# launch (its workspace the process's first large allocation), and the modular pair launch plus its
-# one-SM launch for the last wave (18.34 + 0.76 GB); None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.25e9, "mod": 19.10e9}
+# launch, and the modular pair launch plus its one-SM launch for the last wave (24.79 + 0.77 GB);
+# both vary with where the planes land in physical memory (16.8-23.2 GB read by the pair launch,
+# 36-114 GB by the slice kernel, across captures); None until captured for the current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 78.48e9, "mod": 25.56e9}
 
 
 def load_peaks():
