@@ -68,5 +68,27 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     return LIB
 
 
+CPU_SRC = os.path.join(PKG, "cpu", "gbd_cpu.c")
+CPU_LIB = os.path.join(PKG, "libgbdcpu.so")
+CC = os.environ.get("CC", "gcc")
+
+
+def build_cpu(force: bool = False) -> str:
+    """Compile (if stale) and return the path of libgbdcpu.so, the host DGEMM of the paper's
+    five loops (portable C: no target-specific flags, so x86-64 and aarch64 builds agree)."""
+    deps = [CPU_SRC, os.path.join(INCLUDE, "gbdcpu.h"), __file__]
+    if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(CPU_LIB) for d in deps):
+        return CPU_LIB
+    tmp = CPU_LIB + f".tmp{os.getpid()}"
+    cmd = [CC, "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fvisibility=hidden", "-I" + INCLUDE,
+           "-o", tmp, CPU_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"{CC} failed on gbd_cpu.c:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, CPU_LIB)
+    return CPU_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build_cpu(force="--force" in sys.argv))
