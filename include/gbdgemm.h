@@ -198,6 +198,13 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
  *   estimate (automatic modes); with bits = -1 a non-NULL info is filled by reading the
  *   choice back, which synchronises `stream`.  record_phases times the preparation
  *   (prep_ms) and the products with the reconstruction (gemm_ms).
+ * Kernels: six launches of preparation and the plan, then the products: 256 x 256 tiles on
+ *   SM pairs, or 128 x 128 tiles on single SMs (with each tile's moduli spread over several
+ *   SMs when there are few tiles), by a wave-quantised estimate of their times; a last
+ *   wave of 256 x 256 tiles that would leave SM pairs idle runs as 128 x 128 quarters in
+ *   one more launch when they fit one wave.  The environment variables GBD_EMU_KERNEL
+ *   (pair, single or split) and GBD_EMU_TAIL=0 override the choice (tests and tuning);
+ *   the result is the same bits either way.
  * Returns 0, a BLAS argument index, or GBD_ERR_*.
  */
 GBD_API size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits);
@@ -365,6 +372,9 @@ GBD_API int gbd_check_device_error(void* stream);
  * gbd_dsyrk: C := alpha op(A) op(A)^T + beta C on the `uplo` ('U'/'L') triangle of the
  *   n x n matrix C; op(A) = A (n x k) for trans 'N', A^T (A is k x n) for 'T'/'C'.  The
  *   other triangle is neither read for the result nor written.  beta = 0: C is not read.
+ *   In emulated mode, when the whole triangle meets the modular threshold (n^2 / 2
+ *   outputs), it is one modular product whose tiles are those that meet the triangle;
+ *   when 16 moduli cannot reach `tol` there, the call recurses on halves instead.
  *   Codes: 1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc.
  * gbd_dtrmm: B := alpha op(A) B (side 'L', A m x m) or alpha B op(A) (side 'R', A n x n),
  *   A triangular: only its `uplo` triangle is read; diag 'U' means a unit diagonal, not
