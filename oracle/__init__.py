@@ -17,6 +17,10 @@ Contents
 * ``ozmod_dgemm_rows``: a plain CPU model of the modular emulation (Ozaki scheme II,
   ozaki_mod_model.c): rounded scaled integers and their exact 128-bit product, where
   the GPU path goes through residues and the Chinese remainder theorem.
+* ``certify``: the certified precision choice of both emulations (certify.c): the
+  smallest slice count / integer bit count whose a-priori truncation bound stays within
+  the componentwise target on every element, from the exact |op(A)||op(B)|, or the
+  exactness width when every scaled entry is an integer.
 * ``dsyrk`` / ``dtrmm`` / ``dtrsm``: the GEMM-based level-3 operations by their plain
   definitions (level3.c): Dot2 inner products on the referenced triangle, and
   substitution with Dot2 numerators for the triangular solve.
@@ -35,8 +39,16 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_SOURCES = ["oracle.c", "ozaki_model.c", "ozaki_mod_model.c", "level3.c"]
+_SOURCES = ["oracle.c", "ozaki_model.c", "ozaki_mod_model.c", "level3.c", "certify.c"]
 _lib = None
+
+
+class CertChoice(ctypes.Structure):
+    """Mirror of oracle_cert_t (certify.c)."""
+    _fields_ = [("t_cert", ctypes.c_int), ("t_exact", ctypes.c_int), ("t", ctypes.c_int),
+                ("moduli", ctypes.c_int), ("s_cert", ctypes.c_int), ("s_exact", ctypes.c_int),
+                ("s", ctypes.c_int), ("pad", ctypes.c_int), ("rho", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -87,6 +99,11 @@ def _load():
     lib.oracle_dtrmm.restype = i
     lib.oracle_dtrsm.argtypes = lib.oracle_dtrmm.argtypes
     lib.oracle_dtrsm.restype = i
+    lib.oracle_certify.argtypes = [c, c, i64, i64, i64, vp, i64, vp, i64, d, vp, i64, i,
+                                   ctypes.POINTER(CertChoice)]
+    lib.oracle_certify.restype = i
+    lib.oracle_cert_moduli.argtypes = [i, i64]
+    lib.oracle_cert_moduli.restype = i
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = i
     _lib = lib
@@ -226,3 +243,24 @@ def ozaki_split(x: float, sigma: int, slices: int, bits: int = 7) -> list[int]:
     out = np.zeros(16, dtype=np.int32)
     _load().oracle_ozaki_split(float(x), int(sigma), int(slices), int(bits), out.ctypes.data)
     return [int(v) for v in out[:slices]]
+
+
+def certify(transa, transb, m, n, k, A, lda, B, ldb, tol=0.0, rows=None, nthreads=0) -> dict:
+    """The certified precision choice of both emulations (certify.c) for rows ``rows``
+    (default: all) of op(A) against every column of op(B).  Keys: t_cert, t_exact, t
+    (63: infeasible), moduli (0: infeasible), s_cert, s_exact, s (10: infeasible), rho,
+    gamma."""
+    lib = _load()
+    r, nr = _rows_arg(rows, m)
+    out = CertChoice()
+    rc = lib.oracle_certify(transa.encode(), transb.encode(), m, n, k, _ptr(_as_f64(A)), lda,
+                            _ptr(_as_f64(B)), ldb, float(tol), _ptr(r), nr, int(nthreads),
+                            ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"oracle_certify: status {rc}")
+    return {f: getattr(out, f) for f, _ in CertChoice._fields_ if f != "pad"}
+
+
+def cert_moduli(t: int, k: int) -> int:
+    """Fewest leading moduli whose product exceeds 2 k 2^(2t) (0: more than 16)."""
+    return _load().oracle_cert_moduli(int(t), int(k))

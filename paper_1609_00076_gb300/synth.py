@@ -94,6 +94,23 @@ def matrix(kind: str, rows: int, cols: int, ld: int, seed: int, e: int = 0,
     return colmajor(rows, cols, ld, values(kind, seed, rows * cols, e), pad)
 
 
+def halves_matrix(rows: int, cols: int, ld: int, seed: int, d: int, small_cols_from: int | None = None,
+                  small_rows_below: int | None = None, pad: float = SENTINEL) -> np.ndarray:
+    """Seeded uniform[-1,1) matrix with one part scaled by 2^-d: the columns from
+    ``small_cols_from`` on, or the rows below ``small_rows_below``.  With A (m x k) scaled on
+    its second half of columns and B (k x n) on its first half of rows, every term of
+    (|A||B|)_ij has one factor scaled down, while each row of A and column of B keeps
+    entries near its largest: the case where magnitude sums misjudge |A||B|."""
+    buf = matrix("uniform", rows, cols, ld, seed, pad=pad)
+    v = buf.reshape(max(cols, 1), ld) if rows and cols else None
+    if v is not None:
+        if small_cols_from is not None:
+            v[small_cols_from:, :rows] *= 2.0 ** -d
+        if small_rows_below is not None:
+            v[:, :small_rows_below] *= 2.0 ** -d
+    return buf
+
+
 def view(buf: np.ndarray, rows: int, cols: int, ld: int) -> np.ndarray:
     """The rows x cols matrix inside a column-major buffer, as a 2-D numpy view."""
     return buf[: ld * cols].reshape(cols, ld)[:, :rows].T
