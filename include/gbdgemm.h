@@ -77,20 +77,37 @@ GBD_API int gbd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k,
                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                       double* C, int64_t ldc, void* stream);
 
+/* Which path computed an emulated call (gbd_emu_info.path). */
+#define GBD_PATH_NONE 0     /* a quick return: nothing was multiplied */
+#define GBD_PATH_SPLIT 1    /* digit slices (gbd_dgemm_emu) */
+#define GBD_PATH_MODULAR 2  /* residues (gbd_dgemm_emu_mod) */
+#define GBD_PATH_NATIVE 3   /* gbd_dgemm_emu found the target out of its reach and ran gbd_dgemm */
+
 /*
  * Report of one emulated call (filled when the `info` argument is not NULL).
+ *
+ * In automatic mode the precision is certified, not estimated: with sigma_i, tau_j the
+ * row and column exponents, mu_i = sum_p |a_ip| 2^-sigma_i, nu_j = sum_p |b_pj| 2^-tau_j and
+ * L_ij a guaranteed lower bound of (|op(A)||op(B)|)_ij 2^-(sigma_i + tau_j) computed on the
+ * tensor cores, every element's a-priori truncation bound is at most `bound` times
+ * (|op(A)||op(B)|)_ij, and `bound` plus the allowance for the final roundings stays within
+ * the target.  Elements whose |A||B| terms all have a zero factor carry no error.
  */
 typedef struct gbd_emu_info {
   int record_phases; /* input: non-zero to time the phases with CUDA events on `stream`
                         (the call then waits for its own completion before returning) */
-  int slices;       /* digit slices per operand that were used */
-  int digit_bits;   /* bits per digit (7) */
-  int products;     /* slice products computed: slices*(slices+1)/2 */
-  double mu_min;    /* automatic mode: min over rows i of sum_p |a_ip| 2^-sigma_i (else 0) */
-  double nu_min;    /* automatic mode: min over columns j of sum_p |b_pj| 2^-tau_j (else 0) */
-  double bound_est; /* automatic mode: estimated componentwise relative error bound (else 0) */
-  double prep_ms;   /* record_phases: device time of the exponent, statistics and split kernels */
-  double gemm_ms;   /* record_phases: device time of the slice-product kernel */
+  int slices;       /* split: digit slices per operand; modular: moduli; 0 for the native path */
+  int digit_bits;   /* split: bits per digit (7); modular: integer bits t */
+  int products;     /* tensor-core products: slices*(slices+1)/2 (split), the moduli (modular) */
+  int path;         /* GBD_PATH_* */
+  int exact;        /* automatic mode: 1 when every scaled entry is an integer at the chosen
+                       precision, so the products are exact (integer inputs, for instance) */
+  double rho;       /* automatic mode: max over elements of (mu_i + nu_j) / L_ij */
+  double gamma;     /* automatic mode: max over elements of 1 / L_ij */
+  double bound;     /* automatic mode: the certified componentwise relative bound of the truncation
+                       error at the chosen precision (0 when exact) */
+  double prep_ms;   /* record_phases: device time of the preparation and certification kernels */
+  double gemm_ms;   /* record_phases: device time of the product kernels */
 } gbd_emu_info;
 
 /*
@@ -115,11 +132,15 @@ GBD_API size_t gbd_dgemm_emu_workspace_size(int64_t m, int64_t n, int64_t k, int
  * four: Y = sum_g P_g 2^(7(h-g)) exactly in 64-bit integers (h the group's
  * smallest level) and C := fma(alpha 2^(sigma_i + tau_j - 7h), Y, C) in FP64.
  *
- * slices: 1..9, or 0 to choose the smallest count whose estimated componentwise
- *   error stays below `tol` (relative to |alpha||op(A)||op(B)|; tol <= 0 means
- *   the FP64 bound 2 k 2^-53).  Automatic mode reads 16 bytes back from the
- *   device and therefore synchronises `stream`; with slices > 0 the call is
- *   fully asynchronous.
+ * slices: 1..9, or 0 for the certified automatic choice: the smallest count whose
+ *   a-priori truncation bound, plus the final roundings, stays within `tol` times
+ *   |alpha||op(A)||op(B)| on every element (tol <= 0 means the FP64 bound 2 k 2^-53), with
+ *   (|op(A)||op(B)|)_ij bounded from below by a BF16 product of magnitude planes on the
+ *   tensor cores (see gbd_emu_info); or the count at which the digits are exact.  When no
+ *   count up to 9 can be certified the call computes C with gbd_dgemm instead (info->path =
+ *   GBD_PATH_NATIVE), so the result always meets the target.  Automatic mode reads 16 bytes
+ *   back from the device and therefore synchronises `stream`; with slices > 0 the call is
+ *   fully asynchronous and the caller answers for the accuracy.
  * workspace: device memory of at least gbd_dgemm_emu_workspace_size(m, n, k,
  *   slices) bytes, 256-byte aligned, owned by the caller; its contents on entry
  *   do not matter and it must not be reused until the call has completed on
@@ -134,6 +155,26 @@ GBD_API int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_
                           const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                           double* C, int64_t ldc, int slices, double tol, void* workspace,
                           size_t workspace_bytes, gbd_emu_info* info, void* stream);
+
+/*
+ * A guaranteed lower bound of |op(A)||op(B)|, the magnitude that scales the componentwise
+ * error bound of every GEMM (Section 1.2's operation; the paper states no error analysis):
+ * L_ij <= sum_p |op(A)_ip| |op(B)_pj|, computed on the tensor cores exactly as the automatic
+ * modes of the emulations do to certify their precision.  Per row of op(A) and column of op(B)
+ * the entries are scaled by the power of two of their largest magnitude and rounded toward
+ * zero to BF16 (with a floor of 2^-63 relative to that largest magnitude, so that L_ij = 0
+ * exactly when every term has a zero factor), multiplied with FP32 accumulation, and the
+ * accumulation's possible overshoot and the floors are subtracted with downward rounding.
+ * L (device, m x n, column-major, leading dimension ldl >= max(1, m)) receives L_ij, NaN in
+ * rows of op(A) and columns of op(B) that hold Inf or NaN.  The workspace (256-byte aligned)
+ * holds at least gbd_abs_product_lower_bound_workspace_size(m, n, k) bytes.
+ * Returns 0, a BLAS argument index (1 transa, 2 transb, 3 m, 4 n, 5 k, 8 lda, 10 ldb, 11 ldl)
+ * or GBD_ERR_*.  Asynchronous on stream.
+ */
+GBD_API size_t gbd_abs_product_lower_bound_workspace_size(int64_t m, int64_t n, int64_t k);
+GBD_API int gbd_abs_product_lower_bound(char transa, char transb, int64_t m, int64_t n, int64_t k, const double* A,
+                                        int64_t lda, const double* B, int64_t ldb, double* L, int64_t ldl,
+                                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * gbd_dgemm_emu for callers that cannot allocate device memory.  The paper has
@@ -182,9 +223,11 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
  * correctly rounded.  The products number n (13 at 44 bits and k = 8192) where the split
  * emulation needs s(s+1)/2.
  *
- * bits: t in 1..62, or automatic: the smallest t whose estimated componentwise error
- *   stays below `tol` (tol <= 0 means 2 k 2^-53), chosen on the device from the row and
- *   column magnitude sums, the same way in both automatic forms:
+ * bits: t in 1..62, or automatic: the certified choice (the smallest t whose a-priori
+ *   truncation bound, plus the final roundings, stays within `tol` times
+ *   |alpha||op(A)||op(B)| on every element, tol <= 0 meaning 2 k 2^-53, as for gbd_dgemm_emu;
+ *   or the width at which every scaled entry is an integer), made on the device from a
+ *   tensor-core product of magnitude planes, the same way in both automatic forms:
  *     0: the choice is read back (the call synchronises `stream` once); when it needs more
  *        than 16 moduli at this k the call returns GBD_ERR_LIMIT before touching C
  *        (gbd_dgemm_emu covers any target);
@@ -194,11 +237,13 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
  *   Given t that needs more than 16 moduli returns GBD_ERR_LIMIT.
  * workspace: at least gbd_dgemm_emu_mod_workspace_size(m, n, k, bits) bytes, 256-byte
  *   aligned (bits <= 0 sizes it for 16 moduli); as for gbd_dgemm_emu.
- * info: optional; slices and products report n, digit_bits reports t, bound_est the
- *   estimate (automatic modes); with bits = -1 a non-NULL info is filled by reading the
- *   choice back, which synchronises `stream`.  record_phases times the preparation
- *   (prep_ms) and the products with the reconstruction (gemm_ms).
- * Kernels: six launches of preparation and the plan, then the products: 256 x 256 tiles on
+ * info: optional; slices and products report n, digit_bits reports t, rho, gamma, bound and
+ *   exact the certification (automatic modes); with bits = -1 a non-NULL info is filled by
+ *   reading the choice back, which synchronises `stream`.  record_phases times the
+ *   preparation with the certification (prep_ms) and the products with the reconstruction
+ *   (gemm_ms).
+ * Kernels: the preparation, the certification (magnitude planes and their product) and the
+ *   plan, then the residues and the products: 256 x 256 tiles on
  *   SM pairs, or 128 x 128 tiles on single SMs (with each tile's moduli spread over several
  *   SMs when there are few tiles), by a wave-quantised estimate of their times; a last
  *   wave of 256 x 256 tiles that would leave SM pairs idle runs as 128 x 128 quarters in

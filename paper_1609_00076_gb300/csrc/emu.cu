@@ -1,46 +1,11 @@
-// emu.cu -- host side of the split emulation: workspace sizing, slice-count
-// selection and the launch sequence of gbd_dgemm_emu.
+// emu.cu -- host side of the split emulation: workspace sizing, the certified
+// slice-count choice and the launch sequence of gbd_dgemm_emu.
 #include <cmath>
 #include <cstdint>
 
 #include <cstring>
 
 #include "emu.cuh"
-
-namespace gbd {
-namespace emu {
-namespace {
-
-constexpr double kU = 1.1102230246251565e-16;  // 2^-53
-
-// A-priori relative error of s slices (digits of b bits), as a fraction of
-// |alpha| (|op(A)||op(B)|)_ij, for row/column magnitude sums mu, nu (in units of
-// 2^sigma_i, 2^tau_j) and inner dimension k:
-//   |err_ij| <= |alpha| 2^(sigma_i + tau_j - s b) (mu_i + nu_j + (s-1)(1+2^-b) k)
-// and (|op(A)||op(B)|)_ij is estimated as 2^(sigma_i + tau_j) mu_i nu_j / k, with a
-// safety factor of 8 for the estimate.
-double relative_bound(int s, double mu_min, double nu_min, int64_t k) {
-  const double kk = (double)k;
-  const double trunc = std::ldexp(1.0, -s * kDigitBits) * (2.0 * kk + (s - 1) * (1.0 + std::ldexp(1.0, -kDigitBits)) * kk);
-  const double ab = mu_min * nu_min / kk / 8.0;
-  return ab > 0.0 ? trunc / ab : INFINITY;
-}
-
-}  // namespace
-
-int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* bound) {
-  for (int s = 1; s <= kMaxSlices; ++s) {
-    const double b = relative_bound(s, mu_min, nu_min, k);
-    if (b <= tol || s == kMaxSlices) {
-      if (bound) *bound = b;
-      return s;
-    }
-  }
-  return kMaxSlices;
-}
-
-}  // namespace emu
-}  // namespace gbd
 
 extern "C" {
 
@@ -60,14 +25,10 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   if (rc) return rc;
   const bool timing = info && info->record_phases;
   if (info) {
-    info->prep_ms = 0.0;
-    info->gemm_ms = 0.0;
-    info->slices = 0;
+    const int rp = info->record_phases;
+    memset(info, 0, sizeof(*info));
+    info->record_phases = rp;
     info->digit_bits = kDigitBits;
-    info->products = 0;
-    info->mu_min = 0.0;
-    info->nu_min = 0.0;
-    info->bound_est = 0.0;
   }
   if (slices < 0 || slices > kMaxSlices)
     return set_error(GBD_ERR_ARG, "dgemm_emu: slices must be 0 (automatic) or 1..%d", kMaxSlices);
@@ -77,7 +38,8 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   const int64_t lim = (int64_t)1 << 31;
   if (m >= lim || n >= lim || k >= lim || (m + 63) / 64 > 65535 || (n + 63) / 64 > 65535)
     return set_error(GBD_ERR_LIMIT, "dgemm_emu: m, n below 4194240 and k below 2^31 are supported");
-  rc = current_device(nullptr, nullptr);
+  int sms = 0;
+  rc = current_device(nullptr, &sms);
   if (rc) return rc;
 
   const int s_ws = slices ? slices : kMaxSlices;
@@ -118,19 +80,47 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if ((rc = launch_exponents_pair(pp, exp_blocks, ws.ysum, ws.zero_bytes, s))) return rc;
 
-  int s_use = slices;
-  double bound = 0.0, mu_min = 0.0, nu_min = 0.0;
-  if (slices == 0) {
+  int s_use = slices, exact = 0;
+  double bound = 0.0, rho = 0.0, gamma = 0.0;
+  if (slices == 0) {  // the certified choice: magnitude planes (in the slices' place) and their product
     if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
-    if ((rc = launch_min_stats(ws.muA, m, ws.muB, n, ws.badA, ws.badB, ws.stats, s))) return rc;
-    float st[4] = {0, 0, 0, 0};
-    if ((e = cudaMemcpyAsync(st, ws.stats, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu: clearing the certification words");
+    if ((rc = launch_magplane_pair(pp, plane_scale(k), ws.cert + 2, split_blocks, s))) return rc;
+    if ((rc = launch_cert(m, n, k, ws.DA, ws.DB, ws.kp, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
+                          nullptr, 0, sms, s)))
+      return rc;
+    unsigned int cw[kCertWords] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(cw, ws.cert, sizeof(cw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_fail(e, "dgemm_emu: reading the magnitude statistics");
-    mu_min = st[0] < 1e38f ? st[0] : 0.0;
-    nu_min = st[1] < 1e38f ? st[1] : 0.0;
-    const double target = tol > 0.0 ? tol : 2.0 * (double)k * kU;
-    s_use = (mu_min > 0.0 && nu_min > 0.0) ? choose_slices(target, mu_min, nu_min, k, &bound) : 1;
+      return cuda_fail(e, "dgemm_emu: reading the certification");
+    float fr, fg;
+    memcpy(&fr, &cw[0], 4);
+    memcpy(&fg, &cw[1], 4);
+    rho = fr;
+    gamma = fg;
+    const double target = tol > 0.0 ? tol : 2.0 * (double)k * kUnitRoundoff;
+    s_use = cert_split_slices(rho, gamma, (int)cw[2], (int)cw[3], k, target, &bound, &exact);
+    if (s_use > kMaxSlices) {  // no slice count can be certified: the FP64 tensor-core path
+      if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu: cudaEventRecord");
+      if ((rc = gbd_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream))) return rc;
+      if (info) {
+        info->path = GBD_PATH_NATIVE;
+        info->rho = rho;
+        info->gamma = gamma;
+        info->bound = 0.0;
+        if (timing) {
+          float t0 = 0.f, t1 = 0.f;
+          if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[2])) != cudaSuccess ||
+              (e = cudaEventElapsedTime(&t0, ev[0], ev[1])) != cudaSuccess ||
+              (e = cudaEventElapsedTime(&t1, ev[1], ev[2])) != cudaSuccess)
+            return cuda_fail(e, "dgemm_emu: phase timing");
+          info->prep_ms = t0;
+          info->gemm_ms = t1;
+        }
+      }
+      return GBD_OK;
+    }
   }
   ja.slices = s_use;
   jb.slices = s_use;
@@ -154,11 +144,13 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
     info->gemm_ms = t1;
   }
   if (info) {
+    info->path = GBD_PATH_SPLIT;
     info->slices = s_use;
     info->products = s_use * (s_use + 1) / 2;
-    info->mu_min = mu_min;
-    info->nu_min = nu_min;
-    info->bound_est = bound;
+    info->exact = exact;
+    info->rho = rho;
+    info->gamma = gamma;
+    info->bound = bound;
   }
   return GBD_OK;
 }

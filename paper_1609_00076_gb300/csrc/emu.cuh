@@ -39,9 +39,10 @@ struct Workspace {
   int* sigB;        // [n] column exponents of op(B)
   int* badA;        // [m] non-zero when the row holds Inf/NaN
   int* badB;        // [n]
-  unsigned long long* muA;  // [m] sum_p |a_ip| 2^-sigma_i in 32.32 fixed point (slice-count selection only)
+  unsigned long long* muA;  // [m] sum_p |a_ip| 2^-sigma_i in 32.32 fixed point (automatic slice counts)
   unsigned long long* muB;  // [n]
-  float* stats;     // [4] min mu, min nu, any bad row, any bad column
+  float* stats;     // [4] min mu, min nu, any bad row, any bad column (grouped plans)
+  unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
@@ -67,9 +68,6 @@ int split_count(int64_t m, int64_t n, int64_t k);
 
 // bytes needed for (m, n, k, s) and, when base != nullptr, the pointers into it
 size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws, bool pair_scratch = true);
-// smallest slice count whose estimated componentwise relative bound is <= tol
-int choose_slices(double tol, double mu_min, double nu_min, int64_t k, double* bound);
-
 // min over rows of muA, over columns of muB, any bad row, any bad column -> stats[0..3]
 int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned long long* muB, int64_t n,
                      const int* badA, const int* badB, float* stats, cudaStream_t s);
@@ -127,8 +125,10 @@ struct ModPlan {
   int t;         // integer bits
   int n;         // moduli used (1 when infeasible)
   int feasible;  // 0: the target needs more than kMaxModuli moduli; the call writes NaN
+  int want;      // the bits the target asked for (also when infeasible; 63: none up to 62)
+  int exact;     // automatic mode: 1 when t is the exactness width (no truncation error)
   int pad;
-  double mu, nu, bound;  // the magnitude statistics and the estimated bound (automatic mode)
+  double rho, gamma, bound;  // automatic mode: the certification's maxima and the certified bound
 };
 // residue split parameters: all kMaxModuli moduli (as float), 1/p, and 256^d mod p for
 // d = 0..3 (wlo) and 4..7 (whi) packed one byte per d; t and n come from the plan
@@ -144,10 +144,100 @@ int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_bl
 // exponents: initialise, then one launch for every job; split: one launch for every job
 int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
                         bool exponents, bool split, cudaStream_t s);
+// magnitude sums of every job (after the batched exponents; the jobs' mu arrays zeroed by them)
+int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
 // exponents and magnitude statistics of every problem (jobs 2q, 2q+1 = op(A), op(B)^T of
 // problem q) into stats_dev[4q .. 4q+3] = {min mu, min nu, bad row, bad column}
 int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
                          cudaStream_t s);
+
+// ---- the certified precision choice (emu_cert.cu, emu_split.cu) ----
+// The choice certifies, for every element with a non-zero |A||B| term, that the a-priori
+// truncation bound stays within (tol - r u) (|op(A)||op(B)|)_ij (r u: the final roundings).
+// cert words (device, zeroed before the magnitude planes): [0] max rho, [1] max gamma (float
+// bits), [2] / [3] the exactness widths of op(A) / op(B).
+constexpr int kCertWords = 4;
+// scale exponent S of the magnitude planes at inner dimension k (k 2^(2S) < 2^124)
+int plane_scale(int64_t k);
+// magnitude planes of both sides into their jobs' D (one plane each); widths to tex[0], tex[1]
+int launch_magplane_pair(const PrepPair& pp, int S, unsigned int* tex, int64_t split_blocks, cudaStream_t s);
+// the certification product of the planes PA [m][kp], PB [n][kp]: rho and gamma into words[0..1];
+// Lout (optional, m x n, leading dimension ldl) receives the lower bound of (|A||B|)_ij
+int launch_cert(int64_t m, int64_t n, int64_t k, const uint16_t* PA, const uint16_t* PB, int64_t kp,
+                const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
+                const int* sigA, const int* sigB, unsigned int* words, double* Lout, int64_t ldl, int sms,
+                cudaStream_t stream);
+
+constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
+// exactness width of the modular integers: t at which every scaled entry is an integer (0: both
+// sides zero), from the two side widths
+__host__ __device__ inline int cert_exact_width(int texA, int texB) { return texA > texB ? texA : texB; }
+// Modular emulation: the smallest t in 1..62 with 2^(-t-1) (rho + k 2^(-t-1) gamma) <= tol - 3u,
+// or the exactness width when smaller (and tol >= 2u: an exact product keeps only the rounding
+// of its conversion and of the update); 63 when neither exists.  *bound: the certified
+// relative truncation bound at the choice (0 when exact).
+__host__ __device__ inline int cert_mod_bits(double rho, double gamma, int texA, int texB, int64_t k, double tol,
+                                             double* bound, int* exact) {
+  const double kd = (double)k, tau = tol - 3.0 * kUnitRoundoff;
+  int t = 63;
+  double b = 0.0;
+  if (tau > 0.0)
+    for (int tt = 1; tt <= 62; ++tt) {
+      const double h = ldexp(1.0, -tt - 1);
+      const double bb = h * (rho + kd * h * gamma);
+      if (bb <= tau) {
+        t = tt;
+        b = bb;
+        break;
+      }
+    }
+  int ex = 0;
+  const int tx = cert_exact_width(texA, texB);
+  if (tx <= 62 && tol >= 2.0 * kUnitRoundoff) {
+    const int te = tx < 1 ? 1 : tx;
+    if (te < t) {
+      t = te;
+      b = 0.0;
+      ex = 1;
+    }
+  }
+  if (bound) *bound = b;
+  if (exact) *exact = ex;
+  return t;
+}
+// Split emulation: the smallest s in 1..kMaxSlices with 2^-7s (rho + (s-1)(1+2^-7) k gamma) <=
+// tol - (3g + 3)u, g = ceil(k / 8192) segments, or the slices that make the digits exact and keep
+// every digit product (ceil(tA/7) + ceil(tB/7) - 1) when fewer, if tol covers their g ceil(s/4) + 1
+// roundings; kMaxSlices + 1 when neither exists.
+__host__ __device__ inline int cert_split_slices(double rho, double gamma, int texA, int texB, int64_t k,
+                                                 double tol, double* bound, int* exact) {
+  const double kd = (double)k;
+  const double segs = (double)((k + 8191) / 8192);
+  const double tau = tol - (3.0 * segs + 3.0) * kUnitRoundoff;
+  int s = kMaxSlices + 1;
+  double b = 0.0;
+  if (tau > 0.0)
+    for (int ss = 1; ss <= kMaxSlices; ++ss) {
+      const double bb = ldexp(1.0, -kDigitBits * ss) * (rho + (ss - 1) * (1.0 + ldexp(1.0, -kDigitBits)) * kd * gamma);
+      if (bb <= tau) {
+        s = ss;
+        b = bb;
+        break;
+      }
+    }
+  int ex = 0;
+  const int dA = (texA + kDigitBits - 1) / kDigitBits, dB = (texB + kDigitBits - 1) / kDigitBits;
+  int sx = dA + dB - 1;
+  if (sx < 1) sx = 1;
+  if (sx <= kMaxSlices && sx < s && tol >= (segs * (double)((sx + kGroupLevels - 1) / kGroupLevels) + 1.0) * kUnitRoundoff) {
+    s = sx;
+    b = 0.0;
+    ex = 1;
+  }
+  if (bound) *bound = b;
+  if (exact) *exact = ex;
+  return s;
+}
 
 struct GemmParams {
   int64_t m, n, k;

@@ -754,57 +754,32 @@ __host__ __device__ int moduli_for_products(int t, int64_t k, const ModProducts&
   return 0;
 }
 
-// Estimated componentwise relative error of t integer bits, from the magnitude statistics:
-// the rounding error 2^(sigma_i + tau_j - t - 1) (mu_i + nu_j + k 2^(-t-1)) over the estimate
-// 2^(sigma_i + tau_j) mu_i nu_j / (8k) of (|A||B|)_ij (a safety factor of 8, as the slice count
-// of the split emulation), maximised over i, j by the smallest mu and nu:
-// 2^(-t-1) 8k (1/nu + 1/mu + k 2^(-t-1) / (mu nu)).
-__host__ __device__ double mod_relative_bound(int t, double mu_min, double nu_min, int64_t k) {
-  const double kd = (double)k;
-  return ldexp(1.0, -t - 1) * 8.0 * kd * (1.0 / nu_min + 1.0 / mu_min + kd * ldexp(1.0, -t - 1) / (mu_min * nu_min));
-}
-
-// The call's plan, on one warp: t given (fixed_t > 0), or the smallest t whose estimated
-// bound meets `tol` from the magnitude statistics; then n.  When no n <= kMaxModuli suffices
+// The call's plan, on one warp: t given (fixed_t > 0), or the certified choice from the
+// certification words (cert_mod_bits: the smallest t whose a-priori bound stays within the
+// target on every element, or the exactness width); then n.  When no n <= kMaxModuli suffices
 // the plan is marked infeasible (n = 1, t = 1: the kernels then write NaN) and, for the
 // device-side automatic mode (`flag`), the device error word records it.
-__global__ void __launch_bounds__(32) k_mod_plan(const float* __restrict__ stats, int64_t k, double tol, int fixed_t,
-                                                  const __grid_constant__ ModProducts mp, ModPlan* __restrict__ plan,
-                                                  unsigned int* err, int flag) {
-  if (blockIdx.x != 0) return;
-  const int lane = threadIdx.x;
-  double mu = 0.0, nu = 0.0, bound = 0.0;
-  int t = fixed_t;
+__global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict__ cert, int64_t k, double tol,
+                                                  int fixed_t, const __grid_constant__ ModProducts mp,
+                                                  ModPlan* __restrict__ plan, unsigned int* err, int flag) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double rho = 0.0, gamma = 0.0, bound = 0.0;
+  int t = fixed_t, exact = 0;
   if (fixed_t <= 0) {
-    mu = stats[0] < 1e38f ? stats[0] : 0.0;
-    nu = stats[1] < 1e38f ? stats[1] : 0.0;
-    t = 1;
-    if (mu > 0.0 && nu > 0.0) {
-      // the warp's lanes try t = lane + 1 and t = lane + 33 at once; the smallest t that meets
-      // the target wins (63 when none of 1..62 does)
-      t = 63;
-      for (int base = 1; base <= 62; base += 32) {
-        const int tt = base + lane;
-        const double b = tt <= 62 ? mod_relative_bound(tt, mu, nu, k) : 0.0;
-        const unsigned ok = __ballot_sync(0xffffffffu, tt <= 62 && b <= tol);
-        if (ok) {
-          const int first = __ffs(ok) - 1;
-          t = base + first;
-          bound = __shfl_sync(0xffffffffu, b, first);
-          break;
-        }
-      }
-    }
+    rho = (double)__uint_as_float(cert[0]);
+    gamma = (double)__uint_as_float(cert[1]);
+    t = cert_mod_bits(rho, gamma, (int)cert[2], (int)cert[3], k, tol, &bound, &exact);
   }
-  if (lane != 0) return;
-  const int n = moduli_for_products(t, k, mp);
+  const int n = t <= 62 ? moduli_for_products(t, k, mp) : 0;
   ModPlan pl;
   pl.t = n ? t : 1;
   pl.n = n ? n : 1;
   pl.feasible = n != 0;
-  pl.pad = t;  // the bits the target asked for (also when infeasible)
-  pl.mu = mu;
-  pl.nu = nu;
+  pl.want = t;
+  pl.exact = exact;
+  pl.pad = 0;
+  pl.rho = rho;
+  pl.gamma = gamma;
   pl.bound = bound;
   *plan = pl;
   if (!n && flag) atomicOr(err, kErrModRange);
@@ -820,6 +795,7 @@ struct ModWorkspace {
   unsigned long long* muB;
   float* stats;
   ModPlan* plan;
+  unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
   ExpMagParts parts;  // automatic mode: per row and k-block exponents, flags and magnitude sums
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
@@ -848,6 +824,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_plan = off; off = up(off + sizeof(ModPlan));
+  const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
   const int64_t nkr = (k + 1023) / 1024;  // k-blocks of the exponent and magnitude pass
   size_t o_part[2][3];
   for (int side = 0; side < 2; ++side)
@@ -872,6 +849,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->plan = reinterpret_cast<ModPlan*>(b + o_plan);
+    ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
     for (int side = 0; side < 2; ++side) {
       ws->parts.e[side] = reinterpret_cast<int*>(b + o_part[side][0]);
       ws->parts.s[side] = reinterpret_cast<float*>(b + o_part[side][1]);
@@ -1100,13 +1078,21 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if (automatic) {  // exponents and magnitude sums in one pass over the operands
-    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;  // and their minima
+    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
+    // the certification: magnitude planes (in the residue planes' place, which are written
+    // after the plan) and their product with the reduction of the bound's ratios
+    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
+      return cuda_fail(e, "dgemm_emu_mod: clearing the certification words");
+    if ((rc = launch_magplane_pair(pp, plane_scale(k), ws.cert + 2, split_blocks, s))) return rc;
+    if ((rc = launch_cert(m, n, k, ws.DA, ws.DB, ws.kp, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB,
+                          ws.cert, nullptr, 0, sms, s)))
+      return rc;
   } else if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) {
     return rc;
   }
   // the plan: t and n, on the device
-  const double target = tol > 0.0 ? tol : 2.0 * (double)k * 1.1102230246251565e-16;
-  k_mod_plan<<<1, 32, 0, s>>>(ws.stats, k, target, automatic ? 0 : bits, prods, ws.plan, device_error_word(),
+  const double target = tol > 0.0 ? tol : 2.0 * (double)k * kUnitRoundoff;
+  k_mod_plan<<<1, 32, 0, s>>>(ws.cert, k, target, automatic ? 0 : bits, prods, ws.plan, device_error_word(),
                               bits == -1 ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan launch");
   ModPlan host_plan;
@@ -1117,9 +1103,10 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
       return cuda_fail(e, "dgemm_emu_mod: reading the plan");
     if (!host_plan.feasible)
       return set_error(GBD_ERR_LIMIT,
-                       "dgemm_emu_mod: the accuracy target needs %d integer bits, beyond %d moduli at k = %lld "
-                       "(gbd_dgemm_emu covers it)",
-                       host_plan.pad, kMaxModuli, (long long)k);
+                       "dgemm_emu_mod: the accuracy target cannot be certified within %d moduli at k = %lld (%s; "
+                       "gbd_dgemm_emu covers every target)",
+                       kMaxModuli, (long long)k,
+                       host_plan.want > 62 ? "no bit count up to 62 meets it" : "too many bits");
   }
 
   // residues of both sides (the first n of the kMaxModuli, t bits, from the plan)
@@ -1193,12 +1180,14 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
           (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "dgemm_emu_mod: reading the plan");
     }
+    info->path = GBD_PATH_MODULAR;
     info->slices = host_plan.n;
     info->digit_bits = host_plan.t;
     info->products = host_plan.n;
-    info->mu_min = host_plan.mu;
-    info->nu_min = host_plan.nu;
-    info->bound_est = host_plan.bound;
+    info->exact = host_plan.exact;
+    info->rho = host_plan.rho;
+    info->gamma = host_plan.gamma;
+    info->bound = host_plan.bound;
   }
   return GBD_OK;
 }

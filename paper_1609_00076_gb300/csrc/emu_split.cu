@@ -355,6 +355,62 @@ struct ResidueWriter {
   }
 };
 
+// The magnitude plane of the certified precision choice (writer of split_body): for each entry
+// v = RZ_bf16(max(|x| 2^-sigma, 2^(-63-S)) 2^S) when x is finite and non-zero, else 0.  Rounding
+// toward zero keeps v below |x| 2^(S-sigma) except where the floor raises it; the floor makes the
+// product of two non-zero entries at least 2^-126 (an FP32 normal), so a product of the planes
+// is zero exactly where every term of |A||B| has a zero factor.  With |x| < 2^sigma, v < 2^S.
+// Also the exactness width: the largest sigma - lambda(x) over the side, x = odd 2^lambda(x),
+// so that every x 2^(t - sigma) is an integer once t reaches it (capped at 255).
+struct MagWriter {
+  int S;
+  int64_t R, K;
+  uint16_t* D;
+  int64_t kp;
+  unsigned int* tex;  // the side's exactness width (atomic maximum)
+  __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
+                                             int64_t pbase) const {
+    uint32_t h[kPerThread];
+    int w = 0;
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) {
+      const uint64_t b = x[v];
+      const uint32_t E = (uint32_t)(b >> 52) & 0x7FFu;
+      if (E == 0x7FFu || (b << 1) == 0) {
+        h[v] = 0u;
+        continue;
+      }
+      uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+      int e2;  // |x| = mant 2^e2
+      if (E) {
+        mant |= 1ull << 52;
+        e2 = (int)E - 1075;
+      } else {
+        e2 = -1074;
+      }
+      const int nb = 64 - __clzll((long long)mant);  // bit length, 1..53
+      const int eb = nb - 1 + e2 - sg + S;           // exponent of |x| 2^(S - sigma)
+      if (eb < -63) {
+        h[v] = (uint32_t)(127 - 63) << 7;  // the floor 2^-63
+      } else {
+        const uint32_t m7 = (uint32_t)((nb >= 8 ? (mant >> (nb - 8)) : (mant << (8 - nb))) & 0x7Full);
+        h[v] = ((uint32_t)(eb + 127) << 7) | m7;
+      }
+      w = max(w, min(255, sg - (e2 + __ffsll((long long)mant) - 1)));
+    }
+    const bool full = pbase + kPerThread <= K;
+    uint16_t* row = D + r * kp + pbase;
+    if (full) {
+      *reinterpret_cast<uint4*>(row) =
+          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    } else {
+      for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint16_t)h[v];
+    }
+    // an atomic only when it raises the stored width (a warp's loads of one word merge)
+    if ((unsigned)w > __ldcg(tex)) atomicMax(tex, (unsigned)w);
+  }
+};
+
 template <bool ROWS_CONTIG, class Writer>
 __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
                                            const int* __restrict__ sig, int64_t bx, int64_t by,
@@ -708,6 +764,19 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_pair(const __grid_
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
+// the magnitude planes of both sides (plane scale S): job j writes its D, side j's width to tex[j]
+__global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_pair(const __grid_constant__ PrepPair pp, int S,
+                                                                 unsigned int* tex) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
+  const PrepJob& j = pp.j[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  const MagWriter w{S, j.R, j.K, j.D, j.kp, tex + ji};
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+}
+
 int launch_check(const char* what) {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, what);
@@ -738,6 +807,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_muA = off; off = up(off + sizeof(unsigned long long) * (size_t)m);
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
+  const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
   // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile)
@@ -767,6 +837,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->muA = reinterpret_cast<unsigned long long*>(b + o_muA);
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
+    ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);
@@ -831,6 +902,12 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
   return launch_check("batched statistics launch");
 }
 
+int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s) {
+  if (njobs <= 0 || exp_blocks <= 0) return GBD_OK;
+  k_magnitudes_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
+  return launch_check("batched magnitude launch");
+}
+
 void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks) {
   exp_blocks = 0;
   split_blocks = 0;
@@ -884,6 +961,13 @@ int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s) 
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
   k_split_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp);
   return launch_check("split launch");
+}
+
+int launch_magplane_pair(const PrepPair& pp, int S, unsigned int* tex, int64_t split_blocks, cudaStream_t s) {
+  if (split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
+  k_magplane_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, S, tex);
+  return launch_check("magnitude plane launch");
 }
 
 

@@ -91,6 +91,7 @@ struct gbd_plan {
   // emulated part
   struct Emu {
     gbd_problem p;
+    int index;   // position in the caller's problem array
     int slices;
     gbd::emu::Workspace ws;
   };
@@ -136,7 +137,8 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     if (p.mode == GBD_MODE_EMULATED && !quick) ++nemu;
     else ++nnat;
   }
-  off = up256(off + sizeof(NativeTableEntry) * (size_t)nnat);
+  // room for every problem: emulated ones whose target cannot be certified run natively
+  off = up256(off + sizeof(NativeTableEntry) * (size_t)(nnat + nemu));
   const size_t o_emu = off;
   off = up256(off + sizeof(emu::EmuTableEntry) * (size_t)nemu);
   const size_t o_jobs = off;
@@ -178,6 +180,23 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     plan->pair_ctas = pair_ctas;
   }
   return off;
+}
+
+// the FP64-MMA table entry of a problem (quick: its C := beta C path, as a k = 0 problem)
+NativeTableEntry native_entry(const gbd_problem& p, bool quick) {
+  NativeTableEntry t;
+  memset(&t, 0, sizeof(t));
+  NativeArgs& a = t.a;
+  a.m = p.m; a.n = p.n; a.k = quick ? 0 : p.k;
+  a.alpha = quick ? 0.0 : p.alpha; a.beta = p.beta;
+  a.A = p.A; a.lda = p.lda; a.B = p.B; a.ldb = p.ldb; a.C = p.C; a.ldc = p.ldc;
+  a.err = device_error_word();
+  a.vec_c = ((reinterpret_cast<uintptr_t>(p.C) & 15u) == 0 && (p.ldc & 1) == 0) ? 1 : 0;
+  t.ta = trans_code(p.transa);
+  t.tb = trans_code(p.transb);
+  t.tile = p.tile ? p.tile : default_tile(p.m, p.n);
+  t.tiles_m = (int32_t)((p.m + t.tile - 1) / t.tile);
+  return t;
 }
 
 int validate(const gbd_problem* probs, int count) {
@@ -241,24 +260,13 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     if (p.mode == GBD_MODE_EMULATED && !quick) {
       gbd_plan::Emu e;
       e.p = p;
+      e.index = i;
       e.slices = p.slices;
       plan->emu.push_back(e);
       continue;
     }
     if (quick && p.beta == 1.0) continue;  // nothing to do
-    NativeTableEntry t;
-    memset(&t, 0, sizeof(t));
-    NativeArgs& a = t.a;
-    a.m = p.m; a.n = p.n; a.k = quick ? 0 : p.k;
-    a.alpha = quick ? 0.0 : p.alpha; a.beta = p.beta;
-    a.A = p.A; a.lda = p.lda; a.B = p.B; a.ldb = p.ldb; a.C = p.C; a.ldc = p.ldc;
-    a.err = device_error_word();
-    a.vec_c = ((reinterpret_cast<uintptr_t>(p.C) & 15u) == 0 && (p.ldc & 1) == 0) ? 1 : 0;
-    t.ta = trans_code(p.transa);
-    t.tb = trans_code(p.transb);
-    t.tile = p.tile ? p.tile : default_tile(p.m, p.n);
-    t.tiles_m = (int32_t)((p.m + t.tile - 1) / t.tile);
-    plan->native.push_back(t);
+    plan->native.push_back(native_entry(p, quick));
   }
   // the workspace holds one slice region per emulated problem (sized for the given or maximal slices)
   std::vector<int> s_override(count, 0);
@@ -286,24 +294,67 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     emu::prep_job_blocks(ja, plan->exp_blocks, plan->split_blocks);
     emu::prep_job_blocks(jb, plan->exp_blocks, plan->split_blocks);
   }
-  // automatic slice counts: batched exponents and magnitude statistics, one read-back for all
+  // automatic slice counts, certified per problem: batched exponents and magnitude sums, then each
+  // automatic problem's magnitude planes and certification product, one read-back for all
   if (any_auto) {
+    int sms = 0;
+    if ((rc = current_device(nullptr, &sms))) return rc;
     if ((e = cudaMemcpyAsync(plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "grouped: job table copy");
-    if ((rc = emu::launch_stats_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->stats_dev, s)))
+    if ((rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, 0, true, false, s)))
       return rc;
-    std::vector<float> st(4 * plan->emu.size(), 0.0f);
-    if ((e = cudaMemcpyAsync(st.data(), plan->stats_dev, sizeof(float) * st.size(), cudaMemcpyDeviceToHost, s)) !=
+    if ((rc = emu::launch_magnitudes_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, s))) return rc;
+    unsigned int* words = reinterpret_cast<unsigned int*>(plan->stats_dev);  // kCertWords per emulated problem
+    static_assert(emu::kCertWords == 4, "four certification words per problem fill its statistics slot");
+    if ((e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * emu::kCertWords * plan->emu.size(), s)) != cudaSuccess)
+      return cuda_fail(e, "grouped: clearing the certification words");
+    for (size_t q = 0; q < plan->emu.size(); ++q) {
+      const auto& em = plan->emu[q];
+      if (em.slices != 0) continue;
+      emu::PrepPair pp;
+      pp.j[0] = plan->jobs[2 * q];
+      pp.j[1] = plan->jobs[2 * q + 1];
+      int64_t eb = 0, sb = 0;
+      emu::prep_pair_blocks(pp, eb, sb);
+      unsigned int* w = words + emu::kCertWords * q;
+      if ((rc = emu::launch_magplane_pair(pp, emu::plane_scale(em.p.k), w + 2, sb, s))) return rc;
+      if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, em.ws.DA, em.ws.DB, em.ws.kp, em.ws.muA, em.ws.muB,
+                                 em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, w, nullptr, 0, sms, s)))
+        return rc;
+    }
+    std::vector<unsigned int> cw(emu::kCertWords * plan->emu.size(), 0u);
+    if ((e = cudaMemcpyAsync(cw.data(), words, sizeof(unsigned int) * cw.size(), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_fail(e, "grouped: reading statistics");
+      return cuda_fail(e, "grouped: reading the certification");
+    // problems whose target no slice count can certify move to the FP64 path
+    std::vector<gbd_plan::Emu> kept;
+    std::vector<emu::PrepJob> kept_jobs;
     for (size_t q = 0; q < plan->emu.size(); ++q) {
-      auto& em = plan->emu[q];
-      if (em.slices != 0) continue;
-      const double mu = st[4 * q] < 1e38f ? st[4 * q] : 0.0, nu = st[4 * q + 1] < 1e38f ? st[4 * q + 1] : 0.0;
-      const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * 1.1102230246251565e-16;
-      em.slices = (mu > 0.0 && nu > 0.0) ? emu::choose_slices(target, mu, nu, em.p.k, nullptr) : 1;
+      auto em = plan->emu[q];
+      if (em.slices == 0) {
+        float fr, fg;
+        memcpy(&fr, &cw[emu::kCertWords * q], 4);
+        memcpy(&fg, &cw[emu::kCertWords * q + 1], 4);
+        const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * emu::kUnitRoundoff;
+        em.slices = emu::cert_split_slices(fr, fg, (int)cw[emu::kCertWords * q + 2], (int)cw[emu::kCertWords * q + 3],
+                                           em.p.k, target, nullptr, nullptr);
+      }
+      if (em.slices > emu::kMaxSlices) {
+        plan->native.push_back(native_entry(em.p, false));
+        continue;
+      }
+      kept.push_back(em);
+      kept_jobs.push_back(plan->jobs[2 * q]);
+      kept_jobs.push_back(plan->jobs[2 * q + 1]);
+    }
+    if (kept.size() != plan->emu.size()) {  // renumber the preparation blocks of the remaining jobs
+      plan->emu.swap(kept);
+      plan->jobs.swap(kept_jobs);
+      plan->exp_blocks = 0;
+      plan->split_blocks = 0;
+      for (auto& j : plan->jobs) emu::prep_job_blocks(j, plan->exp_blocks, plan->split_blocks);
     }
   }
   for (size_t q = 0; q < plan->emu.size(); ++q) {
@@ -356,12 +407,14 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     plan->segments.back().tiles = seg_tiles;
   }
   plan->emu_tiles = tiles;
-  if (slices_used)
-    for (int i = 0, q = 0; i < count; ++i) {
+  if (slices_used) {
+    for (int i = 0; i < count; ++i) {
       const gbd_problem& p = probs[i];
       const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
-      if (p.mode == GBD_MODE_EMULATED && !quick) slices_used[i] = plan->emu[q++].slices;
+      if (p.mode == GBD_MODE_EMULATED && !quick) slices_used[i] = -1;  // unless it stayed emulated
     }
+    for (const auto& em : plan->emu) slices_used[em.index] = em.slices;
+  }
   // native table: longest tiles (largest k) first
   std::stable_sort(plan->native.begin(), plan->native.end(),
                    [](const NativeTableEntry& a, const NativeTableEntry& b) { return a.a.k > b.a.k; });

@@ -76,8 +76,9 @@ def _declare(lib):
 class GbdEmuInfo(ctypes.Structure):
     """Mirror of gbd_emu_info."""
     _fields_ = [("record_phases", ctypes.c_int), ("slices", ctypes.c_int), ("digit_bits", ctypes.c_int),
-                ("products", ctypes.c_int), ("mu_min", ctypes.c_double), ("nu_min", ctypes.c_double),
-                ("bound_est", ctypes.c_double), ("prep_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double)]
+                ("products", ctypes.c_int), ("path", ctypes.c_int), ("exact", ctypes.c_int),
+                ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("bound", ctypes.c_double),
+                ("prep_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,6 +89,11 @@ _c, _i64, _d, _i, _vp, _sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ct
 
 GBD_MODE_NATIVE = 0
 GBD_MODE_EMULATED = 1
+
+GBD_PATH_NONE = 0
+GBD_PATH_SPLIT = 1
+GBD_PATH_MODULAR = 2
+GBD_PATH_NATIVE = 3
 
 
 class GbdProblem(ctypes.Structure):
@@ -105,6 +111,8 @@ _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_noalloc", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d,
                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_mod_workspace_size", [_i64, _i64, _i64, _i], _sz),
+    ("gbd_abs_product_lower_bound_workspace_size", [_i64, _i64, _i64], _sz),
+    ("gbd_abs_product_lower_bound", [_c, _c, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], _i),
     ("gbd_dgemm_emu_mod_moduli", [_i, _i64, ctypes.POINTER(ctypes.c_int)], _i),
     ("gbd_dgemm_emu_mod", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                            ctypes.POINTER(GbdEmuInfo), _vp], _i),
@@ -233,6 +241,19 @@ def gbd_dgemm_emu_mod(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, l
                                     int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), int(bits),
                                     float(tol), _addr(workspace), int(workspace_bytes),
                                     ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_abs_product_lower_bound_workspace_size(m, n, k) -> int:
+    """Device workspace bytes of gbd_abs_product_lower_bound."""
+    return int(load().gbd_abs_product_lower_bound_workspace_size(int(m), int(n), int(k)))
+
+
+def gbd_abs_product_lower_bound(transa, transb, m, n, k, A, lda, B, ldb, L, ldl, workspace, workspace_bytes,
+                                stream=None) -> int:
+    """L := a guaranteed lower bound of |op(A)||op(B)| (the certification product); returns the status."""
+    return load().gbd_abs_product_lower_bound(_t(transa), _t(transb), int(m), int(n), int(k), _addr(A), int(lda),
+                                              _addr(B), int(ldb), _addr(L), int(ldl), _addr(workspace),
+                                              int(workspace_bytes), _stream(stream))
 
 
 def gbd_dsyrk_workspace_size(n, k, mode) -> int:

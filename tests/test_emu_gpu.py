@@ -202,7 +202,7 @@ def test_auto_square_256(oracle_mod):
     m = n = k = 256
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "uniform", synth.seed_for(0))
     out, info = run_emu("N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, slices=0)
-    assert 1 <= info.slices <= 9 and info.bound_est <= 2 * k * U
+    assert 1 <= info.slices <= 9 and info.path == gbdgemm.GBD_PATH_SPLIT and info.bound <= 2 * k * U
     check_bound(oracle_mod, "N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, out)
     check_model(oracle_mod, "N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, out, info.slices)
 
@@ -243,6 +243,8 @@ def test_auto_large_square_sampled_rows(oracle_mod, e):
     G = oracle_mod.abs_bound_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, rows=rows)
     msg = first_mismatch(got, ref, 2 * k * U * G, len(rows))
     assert msg is None, f"slices={info.slices}: {msg}"
+    if info.path == gbdgemm.GBD_PATH_NATIVE:  # no slice count certified: computed on the FP64 path
+        return
     # and bit for bit against the model of the method on two of the rows
     mrows = rows[:2]
     mref = oracle_mod.ozaki_dgemm_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, info.slices, rows=mrows)
@@ -345,4 +347,4 @@ def test_automatic_statistics_do_not_depend_on_block_order():
     for ta, tb in (("N", "N"), ("T", "T")):
         A, lda, B, ldb, C, ldc = _problem(ta, tb, m, n, k, "scaled", 5, e=4)
         infos = [run_emu(ta, tb, m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, slices=0)[1] for _ in range(4)]
-        assert len({(i.mu_min, i.nu_min, i.bound_est, i.slices) for i in infos}) == 1
+        assert len({(i.rho, i.gamma, i.bound, i.slices, i.path) for i in infos}) == 1

@@ -203,7 +203,8 @@ def test_deterministic():
 @pytest.mark.parametrize("m,n,k", [(2048, 2048, 256), (4096, 4096, 256)])
 def test_kernel_launches_per_call(m, n, k):
     # one call with the bits chosen on the device launches the kernels that the benchmark's
-    # launch count claims: six, plus one when the last two-SM wave runs on one-SM CTAs
+    # launch count claims: eight (preparation, certification, plan, residues, column scales,
+    # products), plus one when the last two-SM wave runs on one-SM CTAs
     import torch
     from torch.profiler import ProfilerActivity, profile
 
@@ -231,7 +232,7 @@ def test_kernel_launches_per_call(m, n, k):
     if not names:
         pytest.skip("the profiler recorded no device activity here")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert len(kernels) == 6 + bench.mod_tail_launches(m, n, sms), kernels
+    assert len(kernels) == bench.MOD_LAUNCHES + bench.mod_tail_launches(m, n, sms), kernels
     assert gbdgemm.gbd_check_device_error() == 0
 
 
@@ -243,7 +244,7 @@ def test_device_side_automatic_mode_matches_the_synchronising_one(oracle_mod, e)
     out0, info0 = run_mod("N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, 0)
     out1, info1 = run_mod("N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, -1)
     assert np.array_equal(out0.view(np.uint64), out1.view(np.uint64))
-    assert (info1.digit_bits, info1.products, info1.bound_est) == (info0.digit_bits, info0.products, info0.bound_est)
+    assert (info1.digit_bits, info1.products, info1.bound) == (info0.digit_bits, info0.products, info0.bound)
     check_model(oracle_mod, "N", "T", m, n, k, 1.25, A, lda, B, ldb, -0.75, C, ldc, out1, info1.digit_bits)
 
 
