@@ -190,11 +190,19 @@ GBD_API int gbd_abs_product_lower_bound(char transa, char transb, int64_t m, int
  * library keeps until the process exits.  It allocates nothing.
  *
  * Limit: problems whose gbd_dgemm_emu_workspace_size(m, n, k, slices) exceeds
- * 64 MiB (67108864 bytes) are rejected with GBD_ERR_LIMIT; for example every
- * square problem up to 1024 fits with automatic slices.
+ * 64 MiB (67108864 bytes) are rejected with GBD_ERR_LIMIT; with automatic slices every
+ * square problem up to 768 fits (769 needs 79 MiB).  The BLAS quick returns (m, n or k
+ * zero, alpha zero) need no scratch and are never rejected.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture on the device.
+ * (cudaGetSymbolAddress, with that device current).  Under lazy module loading, the
+ * CUDA default, that look-up also loads the library's module holding the array, which
+ * commits its 64 MiB of device memory: the first call on a device can therefore block
+ * or fail with GBD_ERR_CUDA like an allocation.  Make one small call on every device at
+ * set-up time, before the loop that must not allocate and before any stream capture.
+ * Automatic slices (slices = 0) read the certification back from the device, so such a
+ * call synchronises `stream` and cannot be captured; pass an explicit slice count to
+ * avoid both.  When no slice count can be certified the call runs gbd_dgemm, which
+ * needs no scratch either.
  * Sharing: all calls on a device use the same array, which keeps the previous
  * call's contents; the parts that must start at zero are cleared by every call.
  * Calls whose work overlaps on the GPU (other streams, other host threads) race

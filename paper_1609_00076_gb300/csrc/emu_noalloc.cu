@@ -7,8 +7,11 @@
 // unpredictable moment, plug-ins whose host application owns every allocator, or
 // code paths that run while an allocator lock is held.  For them this file keeps
 // a fixed scratch area in the library itself: a file-scope __device__ array that
-// every GPU loading the library holds from load until process exit.  The entry
-// point below calls no cudaMalloc, cudaFree or any other allocating routine.
+// every GPU using the library holds until process exit.  The entry point below
+// calls no cudaMalloc, cudaFree or any other allocating routine.  Under lazy module
+// loading (the CUDA default) the array is committed when this file's module first
+// loads on a device, which the first call's address look-up triggers: that first
+// call is the one that may wait for, or fail for lack of, the array's memory.
 #include <mutex>
 
 #include "emu.cuh"
@@ -55,6 +58,10 @@ int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n, int64_
   if (slices < 0 || slices > gbd::emu::kMaxSlices)
     return gbd::set_error(GBD_ERR_ARG, "dgemm_emu_noalloc: slices must be 0 (automatic) or 1..%d",
                           gbd::emu::kMaxSlices);
+  // the BLAS quick returns need no scratch at all: C := beta C (or nothing) without the array
+  if (m == 0 || n == 0 || alpha == 0.0 || k == 0)
+    return gbd_dgemm_emu(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, tol, nullptr, 0, info,
+                         stream);
   const size_t need = gbd_dgemm_emu_workspace_size(m, n, k, slices);
   if (need > kNoAllocScratchBytes)
     return gbd::set_error(GBD_ERR_LIMIT,

@@ -349,9 +349,10 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       kept_jobs.push_back(plan->jobs[2 * q]);
       kept_jobs.push_back(plan->jobs[2 * q + 1]);
     }
-    if (kept.size() != plan->emu.size()) {  // renumber the preparation blocks of the remaining jobs
-      plan->emu.swap(kept);
-      plan->jobs.swap(kept_jobs);
+    const bool dropped = kept.size() != plan->emu.size();
+    plan->emu.swap(kept);  // the chosen slice counts
+    plan->jobs.swap(kept_jobs);
+    if (dropped) {  // renumber the preparation blocks of the remaining jobs
       plan->exp_blocks = 0;
       plan->split_blocks = 0;
       for (auto& j : plan->jobs) emu::prep_job_blocks(j, plan->exp_blocks, plan->split_blocks);
