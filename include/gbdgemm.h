@@ -165,15 +165,18 @@ GBD_API int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_
  * zero to BF16 (with a floor of 2^-63 relative to that largest magnitude, so that L_ij = 0
  * exactly when every term has a zero factor), multiplied with FP32 accumulation, and the
  * accumulation's possible overshoot and the floors are subtracted with downward rounding.
+ * fp8: 0 for BF16 planes (8 significant bits, within about 2 % of |A||B| on well-scaled data),
+ *   1 for FP8 E5M2 planes (3 significant bits, the emulations' choice: the products run at the
+ *   FP8 tensor-core rate; within about 25 %).
  * L (device, m x n, column-major, leading dimension ldl >= max(1, m)) receives L_ij, NaN in
  * rows of op(A) and columns of op(B) that hold Inf or NaN.  The workspace (256-byte aligned)
  * holds at least gbd_abs_product_lower_bound_workspace_size(m, n, k) bytes.
- * Returns 0, a BLAS argument index (1 transa, 2 transb, 3 m, 4 n, 5 k, 8 lda, 10 ldb, 11 ldl)
- * or GBD_ERR_*.  Asynchronous on stream.
+ * Returns 0, a BLAS argument index (1 transa, 2 transb, 3 m, 4 n, 5 k, 8 lda, 10 ldb, 11 ldl,
+ * 12 fp8) or GBD_ERR_*.  Asynchronous on stream.
  */
 GBD_API size_t gbd_abs_product_lower_bound_workspace_size(int64_t m, int64_t n, int64_t k);
 GBD_API int gbd_abs_product_lower_bound(char transa, char transb, int64_t m, int64_t n, int64_t k, const double* A,
-                                        int64_t lda, const double* B, int64_t ldb, double* L, int64_t ldl,
+                                        int64_t lda, const double* B, int64_t ldb, double* L, int64_t ldl, int fp8,
                                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*

@@ -86,21 +86,18 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
     if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
     if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu: clearing the certification words");
-    if ((rc = launch_magplane_pair(pp, plane_scale(k), ws.cert + 2, split_blocks, s))) return rc;
-    if ((rc = launch_cert(m, n, k, ws.DA, ws.DB, ws.kp, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
+    const int prec = cert_prec_default();
+    if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
+    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
                           nullptr, 0, sms, s)))
       return rc;
-    unsigned int cw[kCertWords] = {0, 0, 0, 0};
+    unsigned int cw[kCertWords] = {};
     if ((e = cudaMemcpyAsync(cw, ws.cert, sizeof(cw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu: reading the certification");
-    float fr, fg;
-    memcpy(&fr, &cw[0], 4);
-    memcpy(&fg, &cw[1], 4);
-    rho = fr;
-    gamma = fg;
+    cert_rho_gamma(cw, &rho, &gamma);
     const double target = tol > 0.0 ? tol : 2.0 * (double)k * kUnitRoundoff;
-    s_use = cert_split_slices(rho, gamma, (int)cw[2], (int)cw[3], k, target, &bound, &exact);
+    s_use = cert_split_slices(rho, gamma, (int)cw[kCertTexA], (int)cw[kCertTexB], k, target, &bound, &exact);
     if (s_use > kMaxSlices) {  // no slice count can be certified: the FP64 tensor-core path
       if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu: cudaEventRecord");
       if ((rc = gbd_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream))) return rc;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -154,16 +155,35 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
 // ---- the certified precision choice (emu_cert.cu, emu_split.cu) ----
 // The choice certifies, for every element with a non-zero |A||B| term, that the a-priori
 // truncation bound stays within (tol - r u) (|op(A)||op(B)|)_ij (r u: the final roundings).
-// cert words (device, zeroed before the magnitude planes): [0] max rho, [1] max gamma (float
-// bits), [2] / [3] the exactness widths of op(A) / op(B).
-constexpr int kCertWords = 4;
+// cert words (device, zeroed before the magnitude planes): rhoA = max_i mu_i / min_j G_ij, rhoB =
+// max_j nu_j / min_i G_ij and gamma = 1 / min G_ij (float bits; G the certified lower bound of
+// (|A||B|)_ij 2^-(sigma_i + tau_j)), and the exactness widths of op(A) and op(B).
+constexpr int kCertRhoA = 0, kCertRhoB = 1, kCertGamma = 2, kCertTexA = 3, kCertTexB = 4;
+constexpr int kCertWords = 8;
+// rho = rhoA + rhoB (rounded up) and gamma from the words
+__host__ __device__ inline void cert_rho_gamma(const unsigned int* w, double* rho, double* gamma) {
+  float a, b, g;
+  memcpy(&a, &w[kCertRhoA], 4);
+  memcpy(&b, &w[kCertRhoB], 4);
+  memcpy(&g, &w[kCertGamma], 4);
+  *rho = ((double)a + (double)b) * (1.0 + 1e-15);
+  *gamma = (double)g;
+}
+// precision of the magnitude planes: BF16 (7 stored fraction bits) or FP8 E5M2 (2 bits, products on
+// the FP8 tensor-core rate)
+constexpr int kCertBF16 = 0;
+constexpr int kCertFP8 = 1;
+// the planes' precision of the emulations' automatic modes: FP8 unless GBD_CERT_DTYPE=bf16
+int cert_prec_default();
 // scale exponent S of the magnitude planes at inner dimension k (k 2^(2S) < 2^124)
-int plane_scale(int64_t k);
+int plane_scale(int64_t k, int prec);
+// row pitch of a plane, in elements (16 bytes at least per row)
+int64_t plane_pitch(int64_t k, int prec);
 // magnitude planes of both sides into their jobs' D (one plane each); widths to tex[0], tex[1]
-int launch_magplane_pair(const PrepPair& pp, int S, unsigned int* tex, int64_t split_blocks, cudaStream_t s);
-// the certification product of the planes PA [m][kp], PB [n][kp]: rho and gamma into words[0..1];
-// Lout (optional, m x n, leading dimension ldl) receives the lower bound of (|A||B|)_ij
-int launch_cert(int64_t m, int64_t n, int64_t k, const uint16_t* PA, const uint16_t* PB, int64_t kp,
+int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s);
+// the certification product of the planes PA [m][pitch], PB [n][pitch]: rho and gamma into
+// words[0..1]; Lout (optional, m x n, leading dimension ldl) receives the lower bound of (|A||B|)_ij
+int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const void* PB,
                 const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
                 const int* sigA, const int* sigB, unsigned int* words, double* Lout, int64_t ldl, int sms,
                 cudaStream_t stream);

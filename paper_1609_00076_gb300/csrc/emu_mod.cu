@@ -766,9 +766,8 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
   double rho = 0.0, gamma = 0.0, bound = 0.0;
   int t = fixed_t, exact = 0;
   if (fixed_t <= 0) {
-    rho = (double)__uint_as_float(cert[0]);
-    gamma = (double)__uint_as_float(cert[1]);
-    t = cert_mod_bits(rho, gamma, (int)cert[2], (int)cert[3], k, tol, &bound, &exact);
+    cert_rho_gamma(cert, &rho, &gamma);
+    t = cert_mod_bits(rho, gamma, (int)cert[kCertTexA], (int)cert[kCertTexB], k, tol, &bound, &exact);
   }
   const int n = t <= 62 ? moduli_for_products(t, k, mp) : 0;
   ModPlan pl;
@@ -1083,9 +1082,10 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
     // after the plan) and their product with the reduction of the bound's ratios
     if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu_mod: clearing the certification words");
-    if ((rc = launch_magplane_pair(pp, plane_scale(k), ws.cert + 2, split_blocks, s))) return rc;
-    if ((rc = launch_cert(m, n, k, ws.DA, ws.DB, ws.kp, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB,
-                          ws.cert, nullptr, 0, sms, s)))
+    const int prec = cert_prec_default();
+    if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
+    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
+                          nullptr, 0, sms, s)))
       return rc;
   } else if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) {
     return rc;

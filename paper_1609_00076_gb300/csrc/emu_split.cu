@@ -4,6 +4,9 @@
 //
 // These kernels are bound by HBM: each reads the operand once (8 bytes per
 // element) and the split writes s BF16 digits (2s bytes per element).
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include <cstdint>
 
 #include "emu.cuh"
@@ -356,20 +359,26 @@ struct ResidueWriter {
 };
 
 // The magnitude plane of the certified precision choice (writer of split_body): for each entry
-// v = RZ_bf16(max(|x| 2^-sigma, 2^(-63-S)) 2^S) when x is finite and non-zero, else 0.  Rounding
-// toward zero keeps v below |x| 2^(S-sigma) except where the floor raises it; the floor makes the
-// product of two non-zero entries at least 2^-126 (an FP32 normal), so a product of the planes
-// is zero exactly where every term of |A||B| has a zero factor.  With |x| < 2^sigma, v < 2^S.
-// Also the exactness width: the largest sigma - lambda(x) over the side, x = odd 2^lambda(x),
-// so that every x 2^(t - sigma) is an integer once t reaches it (capped at 255).
+// v = RZ(max(|x| 2^-sigma, w) 2^S) when x is finite and non-zero, else 0, in BF16 (w = 2^(-63-S)) or
+// in FP8 E5M2 (S = 15, w = 2^-29: the smallest normal E5M2 value, so no subnormal is formed).
+// Rounding toward zero keeps v below |x| 2^(S-sigma) except where the floor raises it; the floor
+// makes the product of two non-zero entries an FP32 normal (at least 2^-126, BF16, or 2^-28,
+// FP8), so a product of the planes is zero exactly where every term of |A||B| has a zero factor.
+// With |x| < 2^sigma, v < 2^S.  Also the exactness width: the largest sigma - lambda(x) over the
+// side, x = odd 2^lambda(x), so that every x 2^(t - sigma) is an integer once t reaches it (capped
+// at 255).  Rows hold kp BF16 values or kp FP8 bytes (16-byte pitches either way).
+template <bool FP8>
 struct MagWriter {
   int S;
   int64_t R, K;
-  uint16_t* D;
+  void* D;
   int64_t kp;
   unsigned int* tex;  // the side's exactness width (atomic maximum)
   __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
                                              int64_t pbase) const {
+    constexpr int kMant = FP8 ? 2 : 7;     // stored fraction bits
+    constexpr int kBias = FP8 ? 15 : 127;  // exponent bias
+    constexpr int kFloor = FP8 ? -14 : -63;  // exponent of the floor in plane units
     uint32_t h[kPerThread];
     int w = 0;
 #pragma unroll
@@ -390,24 +399,38 @@ struct MagWriter {
       }
       const int nb = 64 - __clzll((long long)mant);  // bit length, 1..53
       const int eb = nb - 1 + e2 - sg + S;           // exponent of |x| 2^(S - sigma)
-      if (eb < -63) {
-        h[v] = (uint32_t)(127 - 63) << 7;  // the floor 2^-63
+      if (eb < kFloor) {
+        h[v] = (uint32_t)(kFloor + kBias) << kMant;  // the floor
       } else {
-        const uint32_t m7 = (uint32_t)((nb >= 8 ? (mant >> (nb - 8)) : (mant << (8 - nb))) & 0x7Full);
-        h[v] = ((uint32_t)(eb + 127) << 7) | m7;
+        const uint32_t mf = (uint32_t)((nb >= kMant + 1 ? (mant >> (nb - kMant - 1)) : (mant << (kMant + 1 - nb))) &
+                                       ((1u << kMant) - 1u));
+        h[v] = ((uint32_t)(eb + kBias) << kMant) | mf;
       }
       w = max(w, min(255, sg - (e2 + __ffsll((long long)mant) - 1)));
     }
     const bool full = pbase + kPerThread <= K;
-    uint16_t* row = D + r * kp + pbase;
-    if (full) {
-      *reinterpret_cast<uint4*>(row) =
-          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    if (FP8) {
+      uint8_t* row = static_cast<uint8_t*>(D) + r * kp + pbase;
+      if (full) {
+        *reinterpret_cast<uint2*>(row) = make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
+                                                    h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
+      } else {
+        for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint8_t)h[v];
+      }
     } else {
-      for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint16_t)h[v];
+      uint16_t* row = static_cast<uint16_t*>(D) + r * kp + pbase;
+      if (full) {
+        *reinterpret_cast<uint4*>(row) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      } else {
+        for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint16_t)h[v];
+      }
     }
-    // an atomic only when it raises the stored width (a warp's loads of one word merge)
-    if ((unsigned)w > __ldcg(tex)) atomicMax(tex, (unsigned)w);
+    // the lanes that are here together reduce their widths; one of them raises the stored width
+    namespace cg = cooperative_groups;
+    const cg::coalesced_group g = cg::coalesced_threads();
+    const unsigned wm = cg::reduce(g, (unsigned)w, cg::greater<unsigned>());
+    if (g.thread_rank() == 0 && wm > __ldcg(tex)) atomicMax(tex, wm);
   }
 };
 
@@ -764,15 +787,17 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_pair(const __grid_
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
-// the magnitude planes of both sides (plane scale S): job j writes its D, side j's width to tex[j]
+// the magnitude planes of both sides (plane scale S, rows of kp elements): job j writes its D,
+// side j's width to tex[j]
+template <bool FP8>
 __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_pair(const __grid_constant__ PrepPair pp, int S,
-                                                                 unsigned int* tex) {
+                                                                 int64_t kp, unsigned int* tex) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  const MagWriter w{S, j.R, j.K, j.D, j.kp, tex + ji};
+  const MagWriter<FP8> w{S, j.R, j.K, j.D, kp, tex + ji};
   if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
@@ -963,10 +988,12 @@ int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s) 
   return launch_check("split launch");
 }
 
-int launch_magplane_pair(const PrepPair& pp, int S, unsigned int* tex, int64_t split_blocks, cudaStream_t s) {
+int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s) {
   if (split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
-  k_magplane_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, S, tex);
+  const int64_t K = pp.j[0].K;
+  if (prec == kCertFP8) k_magplane_pair<true><<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex);
+  else k_magplane_pair<false><<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex);
   return launch_check("magnitude plane launch");
 }
 

@@ -143,8 +143,8 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(emu::EmuTableEntry) * (size_t)nemu);
   const size_t o_jobs = off;
   off = up256(off + sizeof(emu::PrepJob) * 2 * (size_t)nemu);
-  const size_t o_stats = off;
-  off = up256(off + sizeof(float) * 4 * (size_t)nemu);
+  const size_t o_stats = off;  // statistics, then the certification words of each emulated problem
+  off = up256(off + sizeof(unsigned int) * emu::kCertWords * (size_t)nemu);
   // two-SM kernel scratch for the large emulated problems (at most one CTA pair per 256 x 256 tile)
   int64_t pair_tiles = 0;
   for (int i = 0; i < count; ++i) {
@@ -306,9 +306,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       return rc;
     if ((rc = emu::launch_magnitudes_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, s))) return rc;
     unsigned int* words = reinterpret_cast<unsigned int*>(plan->stats_dev);  // kCertWords per emulated problem
-    static_assert(emu::kCertWords == 4, "four certification words per problem fill its statistics slot");
     if ((e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * emu::kCertWords * plan->emu.size(), s)) != cudaSuccess)
       return cuda_fail(e, "grouped: clearing the certification words");
+    const int prec = emu::cert_prec_default();
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       const auto& em = plan->emu[q];
       if (em.slices != 0) continue;
@@ -318,8 +318,8 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       int64_t eb = 0, sb = 0;
       emu::prep_pair_blocks(pp, eb, sb);
       unsigned int* w = words + emu::kCertWords * q;
-      if ((rc = emu::launch_magplane_pair(pp, emu::plane_scale(em.p.k), w + 2, sb, s))) return rc;
-      if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, em.ws.DA, em.ws.DB, em.ws.kp, em.ws.muA, em.ws.muB,
+      if ((rc = emu::launch_magplane_pair(pp, prec, w + emu::kCertTexA, sb, s))) return rc;
+      if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, prec, em.ws.DA, em.ws.DB, em.ws.muA, em.ws.muB,
                                  em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, w, nullptr, 0, sms, s)))
         return rc;
     }
@@ -334,12 +334,12 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       auto em = plan->emu[q];
       if (em.slices == 0) {
-        float fr, fg;
-        memcpy(&fr, &cw[emu::kCertWords * q], 4);
-        memcpy(&fg, &cw[emu::kCertWords * q + 1], 4);
+        const unsigned int* w = &cw[emu::kCertWords * q];
+        double rho, gamma;
+        emu::cert_rho_gamma(w, &rho, &gamma);
         const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * emu::kUnitRoundoff;
-        em.slices = emu::cert_split_slices(fr, fg, (int)cw[emu::kCertWords * q + 2], (int)cw[emu::kCertWords * q + 3],
-                                           em.p.k, target, nullptr, nullptr);
+        em.slices = emu::cert_split_slices(rho, gamma, (int)w[emu::kCertTexA], (int)w[emu::kCertTexB], em.p.k, target,
+                                           nullptr, nullptr);
       }
       if (em.slices > emu::kMaxSlices) {
         plan->native.push_back(native_entry(em.p, false));

@@ -112,7 +112,8 @@ _EXTRA_DECLS: list = [
                                ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_dgemm_emu_mod_workspace_size", [_i64, _i64, _i64, _i], _sz),
     ("gbd_abs_product_lower_bound_workspace_size", [_i64, _i64, _i64], _sz),
-    ("gbd_abs_product_lower_bound", [_c, _c, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], _i),
+    ("gbd_abs_product_lower_bound", [_c, _c, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i, _vp, _sz, _vp],
+     _i),
     ("gbd_dgemm_emu_mod_moduli", [_i, _i64, ctypes.POINTER(ctypes.c_int)], _i),
     ("gbd_dgemm_emu_mod", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                            ctypes.POINTER(GbdEmuInfo), _vp], _i),
@@ -248,11 +249,12 @@ def gbd_abs_product_lower_bound_workspace_size(m, n, k) -> int:
     return int(load().gbd_abs_product_lower_bound_workspace_size(int(m), int(n), int(k)))
 
 
-def gbd_abs_product_lower_bound(transa, transb, m, n, k, A, lda, B, ldb, L, ldl, workspace, workspace_bytes,
+def gbd_abs_product_lower_bound(transa, transb, m, n, k, A, lda, B, ldb, L, ldl, fp8, workspace, workspace_bytes,
                                 stream=None) -> int:
-    """L := a guaranteed lower bound of |op(A)||op(B)| (the certification product); returns the status."""
+    """L := a guaranteed lower bound of |op(A)||op(B)| (the certification product, BF16 or FP8 E5M2
+    planes); returns the status."""
     return load().gbd_abs_product_lower_bound(_t(transa), _t(transb), int(m), int(n), int(k), _addr(A), int(lda),
-                                              _addr(B), int(ldb), _addr(L), int(ldl), _addr(workspace),
+                                              _addr(B), int(ldb), _addr(L), int(ldl), int(fp8), _addr(workspace),
                                               int(workspace_bytes), _stream(stream))
 
 

@@ -77,13 +77,13 @@ def _inputs(kind, ta, tb, m, n, k, seed):
     return synth.matrix(vk, ra, ca, ra, seed, e), ra, synth.matrix(vk, rb, cb, rb, seed + 1, e), rb
 
 
-def _lower_bound(ta, tb, m, n, k, A, lda, B, ldb):
+def _lower_bound(ta, tb, m, n, k, A, lda, B, ldb, fp8=0):
     import torch
     dA, dB = DeviceBuf(A), DeviceBuf(B)
     dL = DeviceBuf(None, n=m * n)
     wsb = gbdgemm.gbd_abs_product_lower_bound_workspace_size(m, n, k)
     ws = torch.full((wsb // 8 + 64,), float("nan"), dtype=torch.float64, device="cuda")
-    rc = gbdgemm.gbd_abs_product_lower_bound(ta, tb, m, n, k, dA.ptr, lda, dB.ptr, ldb, dL.ptr, m, ws, wsb)
+    rc = gbdgemm.gbd_abs_product_lower_bound(ta, tb, m, n, k, dA.ptr, lda, dB.ptr, ldb, dL.ptr, m, fp8, ws, wsb)
     assert rc == 0, gbdgemm.gbd_last_error()
     torch.cuda.synchronize()
     assert gbdgemm.gbd_check_device_error() == 0
@@ -91,19 +91,45 @@ def _lower_bound(ta, tb, m, n, k, A, lda, B, ldb):
     return dL.host()
 
 
+@pytest.fixture(params=["single", "pair"])
+def cert_kernel(request, monkeypatch):
+    """Runs the test with the one-SM certification kernel and with the CTA-pair one."""
+    monkeypatch.setenv("GBD_CERT_KERNEL", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("kind", ["uniform", "e8", "e32", "halves30", "sparse", "blocks", "extreme", "int8"])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
-def test_lower_bound_of_abs_product(oracle_mod, kind, ta, tb):
+@pytest.mark.parametrize("fp8", [0, 1])
+def test_lower_bound_of_abs_product(oracle_mod, kind, ta, tb, fp8, cert_kernel):
     m, n, k = 300, 200, 777  # several tiles and ragged edges in every dimension
     A, lda, B, ldb = _inputs(kind, ta, tb, m, n, k, 500 + len(kind))
-    L = _lower_bound(ta, tb, m, n, k, A, lda, B, ldb)
+    L = _lower_bound(ta, tb, m, n, k, A, lda, B, ldb, fp8)
     G = oracle_mod.abs_bound_rows(ta, tb, m, n, k, 1.0, A, lda, B, ldb, 0.0, None, m)
     # the oracle's G is |A||B| to within a few units in the last place (Dot2 of the magnitudes)
     assert np.all(L <= G * (1.0 + 2.0 ** -50)), first_mismatch(L, G, np.zeros_like(G), m)
-    assert np.all((L == 0.0) == (G == 0.0)) or kind == "extreme"
-    if kind in ("uniform", "int8", "blocks", "sparse", "halves30"):
+    assert np.all(L[G == 0.0] == 0.0)  # a zero |A||B| element has a zero bound
+    if not fp8 and kind != "extreme":  # and BF16 planes keep every non-zero one positive
+        assert np.all(L[G > 0.0] > 0.0)
+    # BF16 planes keep 8 significant bits, E5M2 planes 3 (each factor rounded toward zero)
+    tight = {"uniform": (0.97, 0.70), "int8": (0.97, 0.70), "blocks": (0.97, 0.70), "sparse": (0.97, 0.70),
+             "halves30": (0.97, None)}.get(kind)
+    if tight and tight[fp8]:
         pos = G > 0
-        assert np.all(L[pos] >= 0.97 * G[pos]), float(np.min(L[pos] / G[pos]))
+        assert np.all(L[pos] >= tight[fp8] * G[pos]), float(np.min(L[pos] / G[pos]))
+
+
+@pytest.mark.parametrize("k", [16383, 16384 + 64 * 3 + 5])
+def test_lower_bound_chunked_inner_dimension(oracle_mod, k, cert_kernel):
+    # the one-SM form drains 16384-deep chunks and adds them rounding down; the pair form
+    # accumulates the whole inner dimension in TMEM
+    m, n = 140, 260
+    A = synth.matrix("scaled", k, m, k, 41, 4)
+    B = synth.matrix("uniform", k, n, k, 42)
+    for fp8, lo in ((0, 0.9), (1, 0.6)):
+        L = _lower_bound("T", "N", m, n, k, A, k, B, k, fp8)
+        G = oracle_mod.abs_bound_rows("T", "N", m, n, k, 1.0, A, k, B, k, 0.0, None, m)
+        assert np.all(L <= G * (1.0 + 2.0 ** -50)) and np.all(L >= lo * G)
 
 
 def test_lower_bound_nonfinite_rows_and_columns(oracle_mod):
@@ -139,9 +165,16 @@ def _check_bound(oracle_mod, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ld
     assert msg is None, msg
 
 
+@pytest.fixture(params=["fp8", "bf16"])
+def cert_dtype(request, monkeypatch):
+    """Runs the test with the emulations' FP8 magnitude planes and with BF16 ones."""
+    monkeypatch.setenv("GBD_CERT_DTYPE", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("kind", ["uniform", "e8", "e32", "halves4", "halves8", "sparse", "blocks", "int8"])
 @pytest.mark.parametrize("tol", [0.0, 1e-10])
-def test_modular_choice_matches_the_rule(oracle_mod, kind, tol):
+def test_modular_choice_matches_the_rule(oracle_mod, kind, tol, cert_dtype):
     m, n, k = 260, 190, 900
     ta, tb = "T", "N"
     A, lda, B, ldb = _inputs(kind, ta, tb, m, n, k, 600 + len(kind))
@@ -164,7 +197,7 @@ def test_modular_choice_matches_the_rule(oracle_mod, kind, tol):
 
 
 @pytest.mark.parametrize("kind", ["uniform", "e8", "halves4", "sparse", "blocks", "int8"])
-def test_split_choice_matches_the_rule(oracle_mod, kind):
+def test_split_choice_matches_the_rule(oracle_mod, kind, cert_dtype):
     m, n, k = 230, 170, 700
     ta, tb = "N", "T"
     A, lda, B, ldb = _inputs(kind, ta, tb, m, n, k, 700 + len(kind))
