@@ -406,6 +406,54 @@ GBD_API int gbd_watchdog_selftest(int limit_ms, void* stream);
 GBD_API int gbd_check_device_error(void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Context: a device and a pool of library-owned workspaces                   */
+/* ------------------------------------------------------------------------- */
+/*
+ * The calls above take a caller-owned workspace.  A context owns them instead: it is bound
+ * to one device, keeps one workspace per stream that it grows with stream-ordered
+ * allocations (cudaMallocAsync / cudaFreeAsync on that stream, so no call waits for
+ * another and a block is reused only by later calls on the same stream), and makes its
+ * device current for the duration of each call.  Tensor maps and grouped plans are not
+ * cached: both depend on the operands' addresses, and automatic precision on their data.
+ * A context may be used from several host threads; calls that share a stream must be
+ * issued in the order the stream should run them.
+ */
+typedef struct gbd_ctx gbd_ctx;
+
+#define GBD_METHOD_NATIVE 0   /* gbd_dgemm (FP64 tensor-core MMA) */
+#define GBD_METHOD_SPLIT 1    /* gbd_dgemm_emu with the certified slice count */
+#define GBD_METHOD_MODULAR 2  /* gbd_dgemm_emu_mod with the certified bit count (bits = 0) */
+#define GBD_METHOD_AUTO 3     /* modular, or split when 16 moduli cannot certify the target
+                                 (which computes natively when 9 slices cannot either) */
+
+/* Creates a context on `device` (an sm_103 GPU).  Returns 0, GBD_ERR_DEVICE, GBD_ERR_CUDA. */
+GBD_API int gbd_create(gbd_ctx** ctx, int device);
+/* Releases the context and its workspaces (each freed in its stream's order). */
+GBD_API void gbd_destroy(gbd_ctx* ctx);
+/* Bytes of workspace that `method` takes for an m x n x k problem (automatic precision);
+ * host-only: ctx may be NULL.  Returns 0, 3/4/5 for a negative m/n/k, or GBD_ERR_ARG. */
+GBD_API int gbd_workspace_size(const gbd_ctx* ctx, int method, int64_t m, int64_t n, int64_t k, size_t* bytes);
+/*
+ * C := alpha op(A) op(B) + beta C (Section 1.2) by `method`, with the workspace from the
+ * context's pool for `stream`; tol as gbd_dgemm_emu (<= 0: the FP64 bound 2 k 2^-53).  The
+ * emulated methods choose their precision automatically and synchronise `stream` once to
+ * read the choice.  info (optional) reports the path taken.  Returns 0, a BLAS argument
+ * index, or GBD_ERR_* (GBD_ERR_LIMIT from GBD_METHOD_MODULAR when 16 moduli cannot certify
+ * the target; GBD_ERR_WORKSPACE when the pool cannot grow).
+ */
+GBD_API int gbd_ctx_dgemm(gbd_ctx* ctx, int method, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                          double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                          double* C, int64_t ldc, double tol, gbd_emu_info* info, void* stream);
+/* gbd_dgemm_grouped with the workspace from the context's pool for `stream`. */
+GBD_API int gbd_ctx_dgemm_grouped(gbd_ctx* ctx, const gbd_problem* probs, int count, int* slices_used,
+                                  void* stream);
+/* gbd_check_device_error on the context's device: synchronises `stream`, then reads and
+ * clears the device error word (0, GBD_ERR_TIMEOUT, GBD_ERR_LIMIT or GBD_ERR_CUDA). */
+GBD_API int gbd_sync_error(gbd_ctx* ctx, void* stream);
+/* Bytes the context's pool holds now (all streams). */
+GBD_API size_t gbd_ctx_pool_bytes(gbd_ctx* ctx);
+
+/* ------------------------------------------------------------------------- */
 /* GEMM-based level-3 BLAS (the paper's "Poorman's BLAS", Section 3.1)        */
 /* ------------------------------------------------------------------------- */
 /*

@@ -90,6 +90,11 @@ _c, _i64, _d, _i, _vp, _sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ct
 GBD_MODE_NATIVE = 0
 GBD_MODE_EMULATED = 1
 
+GBD_METHOD_NATIVE = 0
+GBD_METHOD_SPLIT = 1
+GBD_METHOD_MODULAR = 2
+GBD_METHOD_AUTO = 3
+
 GBD_PATH_NONE = 0
 GBD_PATH_SPLIT = 1
 GBD_PATH_MODULAR = 2
@@ -130,6 +135,14 @@ _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                             ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_watchdog_selftest", [_i, _vp], _i),
+    ("gbd_create", [ctypes.POINTER(_vp), _i], _i),
+    ("gbd_destroy", [_vp], None),
+    ("gbd_workspace_size", [_vp, _i, _i64, _i64, _i64, ctypes.POINTER(_sz)], _i),
+    ("gbd_ctx_dgemm", [_vp, _i, _c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _d,
+                       ctypes.POINTER(GbdEmuInfo), _vp], _i),
+    ("gbd_ctx_dgemm_grouped", [_vp, _vp, _i, _vp, _vp], _i),
+    ("gbd_sync_error", [_vp, _vp], _i),
+    ("gbd_ctx_pool_bytes", [_vp], _sz),
     ("gbd_dgemm_grouped_workspace_size", [_vp, _i], _sz),
     ("gbd_grouped_plan_create", [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)], _i),
     ("gbd_grouped_plan_run", [_vp, _vp], _i),
@@ -373,6 +386,47 @@ def gbd_dgemm_grouped(problems, workspace, workspace_bytes, slices_used=None, st
     return load().gbd_dgemm_grouped(ctypes.cast(arr, _vp), len(problems), _addr(workspace), int(workspace_bytes),
                                     ctypes.cast(slices_used, _vp) if slices_used is not None else None,
                                     _stream(stream))
+
+
+def gbd_create(device: int = 0):
+    """Returns (status, context handle)."""
+    ctx = _vp()
+    rc = load().gbd_create(ctypes.byref(ctx), int(device))
+    return rc, ctx
+
+
+def gbd_destroy(ctx) -> None:
+    load().gbd_destroy(ctx)
+
+
+def gbd_workspace_size(ctx, method, m, n, k):
+    """Returns (status, bytes) of the workspace `method` takes (ctx may be None)."""
+    out = _sz(0)
+    rc = load().gbd_workspace_size(ctx, int(method), int(m), int(n), int(k), ctypes.byref(out))
+    return rc, int(out.value)
+
+
+def gbd_ctx_dgemm(ctx, method, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tol=0.0, info=None,
+                  stream=None) -> int:
+    """C := alpha*op(A)*op(B) + beta*C by `method` with the context's workspace pool."""
+    return load().gbd_ctx_dgemm(ctx, int(method), _t(transa), _t(transb), int(m), int(n), int(k), float(alpha),
+                                _addr(A), int(lda), _addr(B), int(ldb), float(beta), _addr(C), int(ldc), float(tol),
+                                ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def gbd_ctx_dgemm_grouped(ctx, problems, slices_used=None, stream=None) -> int:
+    arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
+    return load().gbd_ctx_dgemm_grouped(ctx, ctypes.cast(arr, _vp), len(problems),
+                                        ctypes.cast(slices_used, _vp) if slices_used is not None else None,
+                                        _stream(stream))
+
+
+def gbd_sync_error(ctx, stream=None) -> int:
+    return load().gbd_sync_error(ctx, _stream(stream))
+
+
+def gbd_ctx_pool_bytes(ctx) -> int:
+    return int(load().gbd_ctx_pool_bytes(ctx))
 
 
 def gbd_watchdog_selftest(limit_ms: int, stream=None) -> int:

@@ -179,3 +179,33 @@ def test_level3_workspace_sizes_and_codes_without_gpu(lib):
         assert f("L", "L", "N", "N", 3, 2, 1.0, a, 3, a, 2, nat, 0.0, None, 0, **s) == 11
         assert f("L", "L", "N", "N", 3, 0, 1.0, a, 3, a, 3, nat, 0.0, None, 0, **s) == 0
         assert f("L", "L", "N", "N", 2, 2, 1.0, a, 2, a, 2, 5, 0.0, None, 0, **s) == gbdgemm.GBD_ERR_ARG
+
+
+def test_context_workspace_sizes_without_gpu(lib):
+    # the context's sizes are the entry points' own, computed on the host (no context needed)
+    m, n, k = 300, 200, 1000
+    cases = {gbdgemm.GBD_METHOD_NATIVE: 0,
+             gbdgemm.GBD_METHOD_SPLIT: gbdgemm.gbd_dgemm_emu_workspace_size(m, n, k, 0),
+             gbdgemm.GBD_METHOD_MODULAR: gbdgemm.gbd_dgemm_emu_mod_workspace_size(m, n, k, 0)}
+    cases[gbdgemm.GBD_METHOD_AUTO] = max(cases[gbdgemm.GBD_METHOD_SPLIT], cases[gbdgemm.GBD_METHOD_MODULAR])
+    for method, want in cases.items():
+        assert gbdgemm.gbd_workspace_size(None, method, m, n, k) == (0, want)
+    assert gbdgemm.gbd_workspace_size(None, 7, m, n, k)[0] == gbdgemm.GBD_ERR_ARG
+    assert gbdgemm.gbd_workspace_size(None, 1, -1, n, k)[0] == 3
+    assert gbdgemm.gbd_workspace_size(None, 1, m, n, -1)[0] == 5
+
+
+def test_context_calls_refuse_cleanly_without_a_context(lib):
+    assert gbdgemm.gbd_ctx_dgemm(None, 0, "N", "N", 2, 2, 2, 1.0, 0, 2, 0, 2, 0.0, 0, 2, stream=0) == \
+        gbdgemm.GBD_ERR_ARG
+    assert gbdgemm.gbd_sync_error(None, stream=0) == gbdgemm.GBD_ERR_ARG
+    assert gbdgemm.gbd_ctx_pool_bytes(None) == 0
+    gbdgemm.gbd_destroy(None)  # a no-op
+
+
+def test_context_creation_reports_a_missing_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: creation is tested with the GPU tests")
+    rc, ctx = gbdgemm.gbd_create(0)
+    assert rc in (gbdgemm.GBD_ERR_CUDA, gbdgemm.GBD_ERR_DEVICE) and not ctx.value
