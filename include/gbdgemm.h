@@ -322,14 +322,16 @@ GBD_API int gbd_dgemm_emu_mod_host(char transa, char transb, int64_t m, int64_t 
 /* ------------------------------------------------------------------------- */
 #define GBD_MODE_NATIVE 0    /* FP64 mma.sync, as gbd_dgemm */
 #define GBD_MODE_EMULATED 1  /* split digits on tcgen05, as gbd_dgemm_emu */
+#define GBD_MODE_MODULAR 2   /* residues on tcgen05, as gbd_dgemm_emu_mod, planned on the device */
 
 /* One problem of a grouped call: the dgemm argument list of Section 1.2 plus how
  * to compute it.  Pointers are device pointers owned by the caller; problems must
  * not write overlapping parts of C. */
 typedef struct gbd_problem {
   char transa, transb;
-  int32_t mode;    /* GBD_MODE_NATIVE or GBD_MODE_EMULATED */
-  int32_t slices;  /* emulated: 1..9, or 0 = automatic (chosen when the plan is created) */
+  int32_t mode;    /* GBD_MODE_NATIVE, GBD_MODE_EMULATED or GBD_MODE_MODULAR */
+  int32_t slices;  /* emulated: 1..9, or 0 = certified automatically when the plan is created;
+                      modular: integer bits 1..62, or 0 = certified on the device by every run */
   int32_t tile;    /* native: CTA tile edge 32 or 64, or 0 = library default (autotuner hook) */
   int64_t m, n, k;
   double alpha, beta;
@@ -339,7 +341,7 @@ typedef struct gbd_problem {
   int64_t ldb;
   double* C;
   int64_t ldc;
-  double tol;      /* emulated, automatic slices: target relative error (<= 0: 2 k 2^-53) */
+  double tol;      /* emulated and modular, automatic precision: target relative error (<= 0: 2 k 2^-53) */
 } gbd_problem;
 
 /* Opaque host-side plan of a grouped call (problem tables live in the workspace). */
@@ -347,20 +349,28 @@ typedef struct gbd_plan gbd_plan;
 
 /*
  * Bytes of device workspace for a grouped call over `probs` (host-only; needs no
- * GPU).  Emulated problems with slices == 0 are sized for 9 slices.
+ * GPU).  Emulated problems with slices == 0 are sized for 9 slices, modular ones with
+ * bits == 0 for 16 moduli.
  */
 GBD_API size_t gbd_dgemm_grouped_workspace_size(const gbd_problem* probs, int count);
 
 /*
  * Builds a plan: validates every problem, lays out `workspace` (caller-owned,
- * 256-byte aligned, at least gbd_dgemm_grouped_workspace_size bytes), chooses
- * automatic slice counts from the data present now (synchronising `stream`), and
- * copies the problem tables to the device.  Native problems are ordered longest
- * tile first for the atomic tile counter; emulated ones by decreasing tile cost.
+ * 256-byte aligned, at least gbd_dgemm_grouped_workspace_size bytes) and copies the
+ * problem tables to the device through page-locked staging owned by the plan
+ * (stream-ordered copies on `stream`).  Emulated problems with automatic slices are
+ * certified now, from the data present now (the only case that synchronises `stream`);
+ * a problem that no slice count up to 9 certifies joins the FP64 problems.  Modular
+ * problems are certified and planned on the device by every run instead, so a plan
+ * of modular and native problems is made without any synchronisation and its runs
+ * re-certify whatever data the buffers hold.  Native problems are ordered longest tile
+ * first for the atomic tile counter; emulated ones by decreasing tile cost; modular ones
+ * by decreasing k.
  * slices_used: optional array of `count` ints, receives each emulated problem's
- * slice count (0 for native problems and quick returns).
+ * slice count (-1 when it was sent to the FP64 path; 0 for native and modular problems
+ * and quick returns).
  * Returns 0, GBD_ERR_ARG (gbd_last_error names the problem and the BLAS argument
- * index), GBD_ERR_WORKSPACE, GBD_ERR_LIMIT or GBD_ERR_CUDA.  Waits for `stream`.
+ * index), GBD_ERR_WORKSPACE, GBD_ERR_LIMIT or GBD_ERR_CUDA.
  */
 GBD_API int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace,
                                     size_t workspace_bytes, int* slices_used, void* stream,
@@ -368,21 +378,24 @@ GBD_API int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* w
 
 /*
  * Runs a plan on `stream`: for emulated problems their exponent and split kernels
- * and one persistent slice-product launch over all their tiles; for native
- * problems (and every quick return) one persistent FP64-MMA launch whose CTAs take
- * tiles from an atomic counter.  Only kernel launches and memsets are issued, so
- * the call may be captured in a CUDA graph and replayed while the plan, the
- * workspace and the problems' buffers stay alive; each run reads A, B, C afresh.
- * A problem's result is bit-identical to the single-problem call with the same
- * arguments (and, when emulated, the same slice count).  Asynchronous.
+ * and one persistent slice-product launch per slice count over all their tiles; for
+ * modular problems their batched preparation, the certification product (FP8), one
+ * plan per problem, the residues, and one persistent launch of the modular products
+ * over all their tiles; then one persistent FP64-MMA launch for native problems,
+ * every quick return, and each modular problem whose plan found the target out of the
+ * reach of 16 moduli (its tiles in that launch test the plan on the device).  Only
+ * kernel launches and memsets are issued, so the call may be captured in a CUDA graph
+ * and replayed while the plan, the workspace and the problems' buffers stay alive; each
+ * run reads A, B, C afresh.  A problem's result is bit-identical to the single-problem
+ * call with the same arguments (emulated: the same slice count; modular: gbd_dgemm_emu_mod
+ * with bits = -1, or gbd_dgemm when its plan was infeasible).  Asynchronous.
  */
 GBD_API int gbd_grouped_plan_run(gbd_plan* plan, void* stream);
 
 /* Frees the host side of a plan (never the workspace). */
 GBD_API void gbd_grouped_plan_destroy(gbd_plan* plan);
 
-/* Create, run and destroy a plan in one call (synchronises `stream` while the
- * plan is created). */
+/* Create, run and destroy a plan in one call. */
 GBD_API int gbd_dgemm_grouped(const gbd_problem* probs, int count, void* workspace,
                               size_t workspace_bytes, int* slices_used, void* stream);
 

@@ -38,6 +38,12 @@ int encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base
 int encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const void* base,
                 const uint64_t* dims, const uint64_t* pitches_bytes, const uint32_t* box,
                 CUtensorMapSwizzle swizzle);
+// Page-locked staging blocks for host-to-device copies that must not synchronise: a block of at
+// least `bytes` on the current device (reused once the copies recorded by its last staging_put
+// have run; allocated the first time none is free), and its release after the copies from it
+// were issued on `stream`.
+int staging_get(size_t bytes, int* handle, void** ptr);
+int staging_put(int handle, cudaStream_t stream);
 // launches the C := beta*C quick path (alpha == 0 or k == 0)
 int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t stream);
 // (emu_mod.cu) C := alpha op(A) op(B) + beta C on the lower (upper != 0: upper) triangle of the

@@ -19,6 +19,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -86,6 +87,9 @@ struct PrepJob {
   int rows_contig, slices;
   int64_t exp_begin, split_begin;  // first block of this job in the batched launches
   int exp_gx, split_gx;            // blocks along the first grid dimension of each launch
+  // grouped modular problems: the side's exactness-width word and the problem's device plan
+  unsigned int* tex;
+  const struct ModPlan* plan;
 };
 // fills j's block ranges, advancing the running block counts of both launches
 void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks);
@@ -131,6 +135,38 @@ struct ModPlan {
   int pad;
   double rho, gamma, bound;  // automatic mode: the certification's maxima and the certified bound
 };
+// One problem of a grouped launch of the modular products (device table entry; the tensor
+// maps keep it 64-byte aligned).  Its plan is made on the device by every run.
+struct ModTableEntry {
+  CUtensorMap tmA;  // residue planes of op(A): dims {k, m, kMaxModuli}, box {64, 128, 1}
+  CUtensorMap tmB;  // residue planes of op(B)^T: dims {k, n, kMaxModuli}, box {64, 128, 1}
+  int64_t m, n, ldc;
+  double beta;
+  double* C;
+  const int* sigA;
+  const int* badA;
+  const double* cs;     // [n] alpha 2^(tau_j - 2t), from the problem's plan
+  const ModPlan* plan;  // the problem's t, n and feasibility
+  int64_t tile_begin;   // first tile of this problem in the launch
+  int nkb, tiles_m, group_m, num_tiles;
+};
+// the device plan of one problem of a grouped launch, and its column scales
+struct ModPlanJob {
+  const unsigned int* words;  // the problem's certification words
+  ModPlan* plan;
+  int64_t k;
+  double tol;   // the target (already the FP64 bound when the caller gave none)
+  int fixed_t;  // > 0: given bits (no certification)
+  int pad;
+};
+struct ColJob {
+  const int* sigB;
+  const int* badB;
+  double* cs;
+  const ModPlan* plan;
+  double alpha;
+  int64_t n;
+};
 // residue split parameters: all kMaxModuli moduli (as float), 1/p, and 256^d mod p for
 // d = 0..3 (wlo) and 4..7 (whi) packed one byte per d; t and n come from the plan
 struct ModSplit {
@@ -142,6 +178,12 @@ struct ModSplit {
 };
 // residue slices D[i][r][kp] of both sides (slices = n) from the rounded scaled integers
 int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_blocks, cudaStream_t s);
+// grouped modular problems: the magnitude planes (FP8 E5M2) of every job into its D, widths to
+// its tex; then, after the plans, the residues of every job with its problem's plan (nothing for
+// an infeasible plan)
+int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s);
+int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
+                           cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
 int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
                         bool exponents, bool split, cudaStream_t s);
@@ -187,6 +229,37 @@ int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const
                 const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
                 const int* sigA, const int* sigB, unsigned int* words, double* Lout, int64_t ldl, int sms,
                 cudaStream_t stream);
+
+// Arguments of the certification product of one problem (emu_cert.cu)
+struct CertArgs {
+  int64_t m, n;
+  int nkb, chunk_blocks, tiles_m, num_tiles, group_m;
+  float f;         // (1 - delta) 2^-2S, rounded down
+  float slack;     // k (2 w + w^2), rounded up
+  float mu_scale;  // upper-bound factor of the magnitude sums
+  const unsigned long long* muA;  // [m] sum_p |a^_ip| in 32.32 fixed point
+  const unsigned long long* muB;  // [n]
+  const int* badA;
+  const int* badB;
+  const int* sigA;
+  const int* sigB;
+  unsigned int* words;  // the certification words: rhoA, rhoB, gamma (bits of non-negative floats)
+  double* L;            // optional [m x n] output G_ij 2^(sigma_i + tau_j), leading dimension ldl
+  int64_t ldl;
+  unsigned int* err;
+};
+
+// one problem of a grouped certification launch (FP8 planes, one SM per 128 x 128 tile)
+struct CertTableEntry {
+  CUtensorMap tmA;  // the FP8 magnitude plane of op(A): dims {k, m, 1}, box {128, 128, 1}
+  CUtensorMap tmB;
+  CertArgs a;
+  int64_t tile_begin;  // first tile of this problem in the launch
+};
+int make_cert_entry(int64_t m, int64_t n, int64_t k, const void* PA, const void* PB, const unsigned long long* muA,
+                    const unsigned long long* muB, const int* badA, const int* badB, unsigned int* words,
+                    CertTableEntry* e);
+int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int sms, cudaStream_t stream);
 
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 // exactness width of the modular integers: t at which every scaled entry is an integer (0: both
@@ -304,6 +377,40 @@ int launch_slice_gemm_grouped(const EmuTableEntry* table_dev, int count, int tot
 // scratch_p hold max_ctas running-sum slots and max_ctas x kParkSlots park slots of 128 x 256
 int launch_slice_gemm_grouped_pair(const EmuTableEntry* table_dev, int count, int total_tiles, int slices,
                                    double* scratch, int32_t* scratch_p, int max_ctas, cudaStream_t stream);
+
+// ---- grouped modular problems (emu_mod.cu) ----
+// The modular problems of a grouped plan.  Every run certifies and plans each problem on the
+// device (no host round trip), then computes all of them in one persistent launch of the
+// table-driven one-SM product kernel; a problem whose plan is infeasible is skipped there and
+// computed by the grouped FP64 kernel (its fallback entry tests the same plan).
+struct ModGrouped {
+  int count = 0;
+  std::vector<int> index;                  // the caller's position of each problem
+  std::vector<const ModPlan*> plans;       // the device plan of each problem
+  std::vector<PrepJob> jobs;               // op(A), op(B)^T of each problem
+  std::vector<CertTableEntry> cert;
+  std::vector<ModPlanJob> planjobs;
+  std::vector<ColJob> coljobs;
+  std::vector<ModTableEntry> table;        // in launch order (decreasing k)
+  int64_t exp_blocks = 0, split_blocks = 0;
+  int cert_tiles = 0, mod_tiles = 0;
+  // device memory in the grouped workspace
+  PrepJob* jobs_dev = nullptr;
+  CertTableEntry* cert_dev = nullptr;
+  ModPlanJob* planjobs_dev = nullptr;
+  ColJob* coljobs_dev = nullptr;
+  ModTableEntry* table_dev = nullptr;
+  unsigned int* words_dev = nullptr;       // kCertWords per problem
+  uint8_t* scr = nullptr;                  // park slots of the product launch
+  int scr_ctas = 0;
+};
+// Bytes of the grouped modular part for the problems probs[which[q]], q < count (host-only).
+// With base, lays out the workspace from there and builds the host tables into g.
+size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count, void* base, ModGrouped* g, int* rc);
+// copies the tables to the device (asynchronous on s; the host vectors must live until it ran)
+int mod_grouped_upload(const ModGrouped& g, cudaStream_t s);
+// one run: preparation, certification, plans, residues, column scales and the products
+int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s);
 
 }  // namespace emu
 }  // namespace gbd

@@ -68,33 +68,20 @@ struct CertCfg {
 constexpr int kCertChunkBlocks = 256;
 constexpr int64_t kCertPairMaxK = 65536;
 
-struct CertArgs {
-  int64_t m, n;
-  int nkb, chunk_blocks, tiles_m, num_tiles, group_m;
-  float f;         // (1 - delta) 2^-2S, rounded down
-  float slack;     // k (2 w + w^2), rounded up
-  float mu_scale;  // upper-bound factor of the magnitude sums
-  const unsigned long long* muA;  // [m] sum_p |a^_ip| in 32.32 fixed point
-  const unsigned long long* muB;  // [n]
-  const int* badA;
-  const int* badB;
-  const int* sigA;
-  const int* sigB;
-  unsigned int* words;  // the certification words: rhoA, rhoB, gamma (bits of non-negative floats)
-  double* L;            // optional [m x n] output G_ij 2^(sigma_i + tau_j), leading dimension ldl
-  int64_t ldl;
-  unsigned int* err;
-};
 
 // an upper bound of a magnitude sum held in 32.32 fixed point
 __device__ __forceinline__ float mu_upper(unsigned long long q, float scale) {
   return __fmaf_ru((float)((double)q * 0x1p-32), scale, 0x1p-20f);
 }
 
-template <bool PAIR, bool FP8>
+// TABLE (one-SM form): the tiles of several problems, each with its own arguments and maps in a
+// table entry (entries in tile order); the maxima go to each problem's words tile by tile.
+template <bool PAIR, bool FP8, bool TABLE = false>
 __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
     k_cert_gemm(const __grid_constant__ CertArgs p, const __grid_constant__ CUtensorMap tmA,
-                const __grid_constant__ CUtensorMap tmB) {
+                const __grid_constant__ CUtensorMap tmB, const CertTableEntry* __restrict__ table = nullptr,
+                int count = 0, int total_tiles = 0) {
+  static_assert(!(PAIR && TABLE), "grouped certification runs on one SM per tile");
   using L = CertCfg<PAIR, FP8>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -111,9 +98,24 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
   const int unit = PAIR ? (int)(blockIdx.x / 2) : (int)blockIdx.x;   // tile sequence of this CTA (pair)
   const int units = PAIR ? (int)(gridDim.x / 2) : (int)gridDim.x;
 
+  const int num_tiles = TABLE ? total_tiles : p.num_tiles;
+  // the arguments and the tile coordinates of tile `tile` (grouped: of its problem)
+  auto tile_args = [&](int tile, int& cur, int& tm, int& tn) -> const CertArgs* {
+    if (!TABLE) {
+      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+      return &p;  // a __grid_constant__ parameter: its address is that of the parameter itself
+    }
+    while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
+    const CertArgs* q = &table[cur].a;
+    tile_coords(tile - (int)table[cur].tile_begin, q->tiles_m, q->group_m, q->num_tiles, tm, tn);
+    return q;
+  };
+
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+    if (!TABLE) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+    }
     for (int i = 0; i < L::kStages; ++i) {
       mbar_init(&full[i], 1);   // PAIR: the leader's producer arrives with both CTAs' bytes
       mbar_init(&empty[i], 1);  // one commit per phase (multicast to both CTAs of a pair)
@@ -148,22 +150,29 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
-      for (int tile = unit; tile < p.num_tiles; tile += units) {
+      int cur = 0;
+      for (int tile = unit; tile < num_tiles; tile += units) {
         int tm, tn;
-        tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        const CertArgs& q = *tile_args(tile, cur, tm, tn);
+        const CUtensorMap* ma = TABLE ? &table[cur].tmA : &tmA;
+        const CUtensorMap* mb = TABLE ? &table[cur].tmB : &tmB;
+        if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb) : "memory");
+        }
         const int m0 = tm * L::BM + (int)rank * 128, n0 = tn * L::BN + (int)rank * 128;
-        for (int kb = 0; kb < p.nkb; ++kb) {
+        for (int kb = 0; kb < q.nkb; ++kb) {
           if (PAIR) {
             mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             if (leader) mbar_arrive_expect_tx(&full[stage], (uint32_t)(2 * (L::kABytes + L::kBBytes)));
             const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
-            tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * L::kKB, m0, 0);
-            tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * L::kKB, n0, 0);
+            tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, ma, fbar, kb * L::kKB, m0, 0);
+            tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, mb, fbar, kb * L::kKB, n0, 0);
           } else {
             mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             mbar_arrive_expect_tx(&full[stage], (uint32_t)(L::kABytes + L::kBBytes));
-            tma_load_3d(smem + L::kOffA + stage * L::kABytes, &tmA, &full[stage], kb * L::kKB, m0, 0);
-            tma_load_3d(smem + L::kOffB + stage * L::kBBytes, &tmB, &full[stage], kb * L::kKB, n0, 0);
+            tma_load_3d(smem + L::kOffA + stage * L::kABytes, ma, &full[stage], kb * L::kKB, m0, 0);
+            tma_load_3d(smem + L::kOffB + stage * L::kBBytes, mb, &full[stage], kb * L::kKB, n0, 0);
           }
           if (++stage == L::kStages) { stage = 0; phase ^= 1u; }
         }
@@ -176,14 +185,17 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       constexpr uint32_t idesc = FP8 ? idesc_e5m2(L::BM, L::BN) : idesc_bf16(L::BM, L::BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = unit; tile < p.num_tiles; tile += units)
-        for (int i0 = 0; i0 < p.nkb; i0 += p.chunk_blocks, ++chunk) {
+      int cur = 0;
+      for (int tile = unit; tile < num_tiles; tile += units) {
+        int tm, tn;
+        const CertArgs& q = *tile_args(tile, cur, tm, tn);
+        for (int i0 = 0; i0 < q.nkb; i0 += q.chunk_blocks, ++chunk) {
           const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
           if (PAIR) mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
           else mbar_wait(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
           tc_fence_after();
           const uint32_t dtm = tmem_base + buf * L::BN;
-          const int i1 = min(p.nkb, i0 + p.chunk_blocks);
+          const int i1 = min(q.nkb, i0 + q.chunk_blocks);
           for (int it = i0; it < i1; ++it) {
             if (PAIR) mbar_wait_cluster(&full[stage], phase, p.err, kErrWaitTma);
             else mbar_wait(&full[stage], phase, p.err, kErrWaitTma);
@@ -208,6 +220,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
           if (PAIR) umma_commit_pair(&acc_full[buf]);  // the chunk is complete in both CTAs' TMEM
           else umma_commit(&acc_full[buf]);
         }
+      }
       if (chunk > 0) {  // a CTA without a tile issued nothing and has nothing to wait for
         if (PAIR) {
           umma_commit_pair(done);
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
     //   rhoA = max mu_i / min_j G_ij,  rhoB = max nu_j / min_i G_ij,  gamma = 1 / min G_ij,
     // and max (mu_i + nu_j) / G_ij <= rhoA + rhoB.
     float rmaxA = 0.0f, rmaxB = 0.0f, gmin = INFINITY;
-    auto certify = [&](int64_t i, int64_t jc0, const float (&acc)[32]) {
+    auto certify = [&](const CertArgs& p, int64_t i, int64_t jc0, const float (&acc)[32]) {
       const bool row_ok = i < p.m && p.badA[i] == 0;
       const int si = (p.L && i < p.m) ? (p.sigA[i] == kExpEmpty ? 0 : p.sigA[i]) : 0;
       float rowmin = INFINITY, colmin = INFINITY;
@@ -265,10 +278,25 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       if (colmin < INFINITY)
         rmaxB = fmaxf(rmaxB, colmin > 0.0f ? __fdiv_ru(mu_upper(p.muB[jc0 + lane], p.mu_scale), colmin) : INFINITY);
     };
+    // the maxima into a problem's words (grouped: after every tile, the next may be another's)
+    auto flush = [&](unsigned int* words) {
+      const float gmax = gmin < INFINITY ? (gmin > 0.0f ? __frcp_ru(gmin) : INFINITY) : 0.0f;
+      const unsigned ra = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxA));
+      const unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxB));
+      const unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
+      if (lane == 0) {
+        if (ra) atomicMax(words + kCertRhoA, ra);
+        if (rb) atomicMax(words + kCertRhoB, rb);
+        if (gb) atomicMax(words + kCertGamma, gb);
+      }
+      rmaxA = rmaxB = 0.0f;
+      gmin = INFINITY;
+    };
     uint32_t chunk = 0;
-    for (int tile = unit; tile < p.num_tiles; tile += units) {
+    int cur = 0;
+    for (int tile = unit; tile < num_tiles; tile += units) {
       int tm, tn;
-      tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+      const CertArgs& p = *tile_args(tile, cur, tm, tn);
       const int64_t i = (int64_t)tm * L::BM + (int)rank * 128 + row;
       const int64_t jc0 = (int64_t)tn * L::BN + col0;
       if (p.chunk_blocks >= p.nkb) {
@@ -288,7 +316,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] = __uint_as_float(v[jj]);
           }
-          certify(i, jc0 + h, acc);
+          certify(p, i, jc0 + h, acc);
         }
         tc_fence_before();
         if (PAIR) mbar_arrive_remote(empty_remote[buf]);
@@ -315,19 +343,11 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
           tc_fence_before();
           mbar_arrive(&acc_empty[buf]);
         }
-        certify(i, jc0, acc);
+        certify(p, i, jc0, acc);
       }
+      if (TABLE) flush(p.words);
     }
-    // non-negative floats order as their bit patterns
-    const float gmax = gmin < INFINITY ? (gmin > 0.0f ? __frcp_ru(gmin) : INFINITY) : 0.0f;
-    const unsigned ra = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxA));
-    const unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxB));
-    const unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
-    if (lane == 0) {
-      if (ra) atomicMax(p.words + kCertRhoA, ra);
-      if (rb) atomicMax(p.words + kCertRhoB, rb);
-      if (gb) atomicMax(p.words + kCertGamma, gb);
-    }
+    if (!TABLE) flush(p.words);  // non-negative floats order as their bit patterns
   }
 
   tc_fence_before();
@@ -395,7 +415,7 @@ int launch_cert_kernel(const CertArgs& a, const CUtensorMap& tmA, const CUtensor
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = PAIR ? 1 : 0;
-  e = cudaLaunchKernelEx(&cfg, kern, a, tmA, tmB);
+  e = cudaLaunchKernelEx(&cfg, kern, a, tmA, tmB, static_cast<const CertTableEntry*>(nullptr), 0, 0);
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "certification gemm launch");
 }
 
@@ -474,6 +494,57 @@ int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const
   a.group_m = group_rows(grid, bm, bn, a.tiles_m);
   return fp8 ? launch_cert_kernel<false, true>(a, tmA, tmB, grid, stream)
              : launch_cert_kernel<false, false>(a, tmA, tmB, grid, stream);
+}
+
+int make_cert_entry(int64_t m, int64_t n, int64_t k, const void* PA, const void* PB, const unsigned long long* muA,
+                    const unsigned long long* muB, const int* badA, const int* badB, unsigned int* words,
+                    CertTableEntry* e) {
+  memset(e, 0, sizeof(*e));
+  CertArgs& a = e->a;
+  const int S = plane_scale(k, kCertFP8);
+  const int64_t pitch = plane_pitch(k, kCertFP8);
+  a.m = m;
+  a.n = n;
+  a.nkb = (int)((k + 127) / 128);
+  a.chunk_blocks = kCertChunkBlocks * kBK / 128;  // 16384 deep, as the one-SM form of single calls
+  const int64_t chunk_k = (int64_t)a.chunk_blocks * 128 < k ? (int64_t)a.chunk_blocks * 128 : k;
+  a.f = float_down(std::ldexp(1.0 - (double)chunk_k * std::ldexp(1.0, -19), -2 * S));
+  const double w = std::ldexp(1.0, -14 - S);
+  a.slack = float_up((double)k * (2.0 * w + w * w) * (1.0 + std::ldexp(1.0, -40)));
+  a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + (double)((k + 1023) / 1024) * std::ldexp(1.0, -22));
+  a.muA = muA;
+  a.muB = muB;
+  a.badA = badA;
+  a.badB = badB;
+  a.words = words;
+  a.err = device_error_word();
+  a.tiles_m = (int)((m + 127) / 128);
+  a.num_tiles = a.tiles_m * (int)((n + 127) / 128);
+  a.group_m = a.tiles_m;  // within one problem the tiles walk down the rows
+  const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, 1u};
+  const uint64_t pA[2] = {(uint64_t)pitch, (uint64_t)m * pitch};
+  const uint32_t box[3] = {128u, 128u, 1u};
+  int rc = encode_tmap(&e->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, PA, dA, pA, box, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, 1u};
+  const uint64_t pB[2] = {(uint64_t)pitch, (uint64_t)n * pitch};
+  return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, PB, dB, pB, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int sms, cudaStream_t stream) {
+  if (count <= 0 || total_tiles <= 0) return GBD_OK;
+  using L = CertCfg<false, true>;
+  auto kern = k_cert_gemm<false, true, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped certification)");
+  CertArgs dummy_args;
+  memset(&dummy_args, 0, sizeof(dummy_args));
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  kern<<<grid, L::kThreads, L::kAlloc, stream>>>(dummy_args, dummy, dummy, table_dev, count, total_tiles);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped certification launch");
 }
 
 }  // namespace emu

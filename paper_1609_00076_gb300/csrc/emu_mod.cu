@@ -15,6 +15,7 @@
 //      beta C0), fl correctly rounded.
 // There is no FP64 arithmetic in the products: n GEMMs replace the s(s+1)/2 of the split
 // emulation.  All waits are bounded (2 s) and set the device error word when they give up.
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -202,11 +203,15 @@ __device__ __forceinline__ double scaled_double(u128 v, int sig) {
 // the previous tile from its parked bytes and write them to C.  All loads of a group are
 // issued before its arithmetic, so a group waits for memory once.  nan_out: the plan found the
 // target unreachable; every result is NaN.
-template <int EPI_WARPS, int TBN, bool PAIR>
+// TABLE: the tiles belong to the problems of a grouped launch (table entries in tile order); each
+// tile takes its problem's sizes, C, scales and moduli count from its entry, and a tile whose
+// problem's plan is infeasible is skipped (another kernel computes that problem).
+template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE = false>
 __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool nan_out, uint32_t tmem_base,
                                              uint64_t* acc_full, uint64_t* acc_empty, int warp, int lane, int tile0,
-                                             int tile_step, int tbm, int row_off) {
-  const CrtSet& cset = p.set[nmod - 1];
+                                             int tile_step, int tbm, int row_off,
+                                             const ModTableEntry* table = nullptr, int count = 0) {
+  const CrtSet* cset = &p.set[nmod - 1];
   constexpr int COLS = TBN / (EPI_WARPS / 4);
   const int ew = warp - 2;
   const int quad = warp & 3;
@@ -221,13 +226,18 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
   }
   uint8_t* const scr_cta = p.scr + (int64_t)blockIdx.x * 2 * kSlotBytes + (int64_t)(col0 / 4) * 512 + row * 4;
   constexpr int kGroups = COLS / 4;
-  const int per_boundary = (kGroups + nmod - 1) / nmod;  // groups of four columns
+  int per_boundary = (kGroups + nmod - 1) / nmod;  // groups of four columns
 
   // the pending reconstruction: this thread's row and columns of the previous tile
   bool pd_active = false, pd_bad = false;
   int pd_done = 0, pd_slot = 0, pd_sig = 0, pd_cols = 0, pd_first = 0;  // columns [pd_first, pd_cols) are written
   double* pd_c = nullptr;
   const double* pd_cs = nullptr;
+  // grouped: the pending tile's problem (its moduli, beta and leading dimension)
+  int pd_nmod = nmod;
+  const CrtSet* pd_cset = cset;
+  double pd_beta = p.beta;
+  int64_t pd_ldc = p.ldc;
   auto advance = [&](int ngroups) {
     const int g1 = min(pd_done + ngroups, kGroups);
     const uint8_t* ub = scr_cta + (int64_t)pd_slot * kSlotBytes;
@@ -235,15 +245,18 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
       const int c0 = 4 * g;
       if (c0 >= pd_cols) break;
       if (c0 + 4 <= pd_first) continue;
+      const int nm = TABLE ? pd_nmod : nmod;
+      const double beta = TABLE ? pd_beta : p.beta;
+      const int64_t ldc = TABLE ? pd_ldc : p.ldc;
       uint32_t w4[kMaxModuli];  // the bytes of columns c0..c0+3, one word per modulus
 #pragma unroll
       for (int l = 0; l < kMaxModuli; ++l)
-        w4[l] = l < nmod ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
+        w4[l] = l < nm ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
       double c0v[4], csv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const bool in = c0 + q < pd_cols && c0 + q >= pd_first;
-        c0v[q] = (in && p.beta != 0.0) ? pd_c[(int64_t)(c0 + q) * p.ldc] : 0.0;
+        c0v[q] = (in && beta != 0.0) ? pd_c[(int64_t)(c0 + q) * ldc] : 0.0;
         csv[q] = in ? pd_cs[c0 + q] : 0.0;
       }
 #pragma unroll
@@ -253,11 +266,11 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
         uint32_t u[kMaxModuli];
 #pragma unroll
         for (int l = 0; l < kMaxModuli; ++l) u[l] = (w4[l] >> (8 * q)) & 0xFFu;
-        const double w0 = p.beta != 0.0 ? p.beta * c0v[q] : 0.0;
+        const double w0 = beta != 0.0 ? beta * c0v[q] : 0.0;
         double w;
         if (nan_out || pd_bad || csv[q] != csv[q]) w = __longlong_as_double(0x7FF8000000000000ll);
-        else w = fma(csv[q], scaled_double(crt_combine(u, p, cset, nmod), pd_sig), w0);
-        pd_c[(int64_t)(c0 + q) * p.ldc] = w;
+        else w = fma(csv[q], scaled_double(crt_combine(u, p, TABLE ? *pd_cset : *cset, nm), pd_sig), w0);
+        pd_c[(int64_t)(c0 + q) * ldc] = w;
       }
     }
     pd_done = g1;
@@ -268,20 +281,36 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
   int acc[COLS];
   int tcount = 0;
   const int tile_end = PAIR ? p.tile_end : p.num_tiles;
-  for (int tile = tile0; tile < tile_end; tile += tile_step, ++tcount) {
-    int tm, tn;
-    if (PAIR) raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-    else tile128_coords(p, tile, tm, tn);
+  int cur = 0;  // grouped: the table entry of the current tile (a CTA's tiles increase)
+  for (int tile = tile0; tile < tile_end; tile += tile_step) {
+    int tm, tn, nkb = p.nkb;
+    const ModTableEntry* e = nullptr;
+    if (TABLE) {
+      while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
+      e = &table[cur];
+      const ModPlan* pl = e->plan;
+      if (!pl->feasible) continue;  // computed by the FP64 kernel instead
+      nmod = pl->n;
+      nkb = e->nkb;
+      cset = &p.set[nmod - 1];
+      per_boundary = (kGroups + nmod - 1) / nmod;
+      tile_coords(tile - (int)e->tile_begin, e->tiles_m, e->group_m, e->num_tiles, tm, tn);
+    } else if (PAIR) {
+      raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+    } else {
+      tile128_coords(p, tile, tm, tn);
+    }
     const int64_t i = (int64_t)tm * tbm + row_off + row;
     const int64_t jc0 = (int64_t)tn * TBN + col0;
     const int slot = tcount & 1;
+    ++tcount;
     uint8_t* const ub = scr_cta + (int64_t)slot * kSlotBytes;
     for (int l = 0; l < nmod; ++l) {
       const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
 #pragma unroll
       for (int c = 0; c < COLS; ++c) acc[c] = 0;
       int nch = 0;
-      for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+      for (int i0 = 0; i0 < nkb; i0 += kChunkBlocks, ++chunk) {
         const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
         mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
         tc_fence_after();
@@ -302,7 +331,7 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
           for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
         }
       }
-      const uint32_t cl = (uint32_t)cset.c[l];
+      const uint32_t cl = (uint32_t)cset->c[l];
 #pragma unroll
       for (int g = 0; g < kGroups; ++g) {
         uint32_t w = 0u;
@@ -314,23 +343,35 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
       if (pd_active) advance(l + 1 == nmod ? kGroups : per_boundary);
     }
     // this tile's residues are complete: it becomes the pending reconstruction
-    const bool row_ok = i < p.m;
+    const int64_t pm = TABLE ? e->m : p.m, pn = TABLE ? e->n : p.n;
+    const bool row_ok = i < pm;
     pd_active = true;
     pd_done = 0;
     pd_slot = slot;
-    pd_cols = row_ok && jc0 < p.n ? (int)min((int64_t)COLS, p.n - jc0) : 0;
+    pd_cols = row_ok && jc0 < pn ? (int)min((int64_t)COLS, pn - jc0) : 0;
     pd_first = 0;
-    if (p.tri == 1) pd_cols = (int)max((int64_t)0, min((int64_t)pd_cols, i - jc0 + 1));  // j <= i
-    else if (p.tri == 2) pd_first = (int)max((int64_t)0, i - jc0);                      // j >= i
+    if (!TABLE && p.tri == 1) pd_cols = (int)max((int64_t)0, min((int64_t)pd_cols, i - jc0 + 1));  // j <= i
+    else if (!TABLE && p.tri == 2) pd_first = (int)max((int64_t)0, i - jc0);                      // j >= i
     pd_sig = 0;
     pd_bad = false;
+    const int* sigA = TABLE ? e->sigA : p.sigA;
+    const int* badA = TABLE ? e->badA : p.badA;
     if (row_ok) {
-      const int sg = p.sigA[i];
+      const int sg = sigA[i];
       pd_sig = sg == kExpEmpty ? 0 : sg;
-      pd_bad = p.badA[i] != 0;
+      pd_bad = badA[i] != 0;
     }
-    pd_c = p.C + jc0 * p.ldc + i;  // dereferenced only for the pd_cols columns inside C
-    pd_cs = p.cs + jc0;
+    if (TABLE) {
+      pd_nmod = nmod;
+      pd_cset = cset;
+      pd_beta = e->beta;
+      pd_ldc = e->ldc;
+      pd_c = e->C + jc0 * e->ldc + i;  // dereferenced only for the pd_cols columns inside C
+      pd_cs = e->cs + jc0;
+    } else {
+      pd_c = p.C + jc0 * p.ldc + i;
+      pd_cs = p.cs + jc0;
+    }
   }
   if (pd_active) advance(kGroups);
 }
@@ -461,11 +502,15 @@ struct Smem {
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
 
-// SPLIT: the work units are (tile, group of moduli) instead of tiles (few-tile problems)
-template <bool SPLIT>
+// SPLIT: the work units are (tile, group of moduli) instead of tiles (few-tile problems).
+// TABLE: the tiles of several problems (a grouped launch): entries in tile order, each with its
+// problem's residue maps and device plan; tiles of an infeasible plan are skipped.
+template <bool SPLIT, bool TABLE = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mod_gemm(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
-               const __grid_constant__ CUtensorMap tmB) {
+               const __grid_constant__ CUtensorMap tmB, const ModTableEntry* __restrict__ table = nullptr,
+               int count = 0) {
+  static_assert(!(SPLIT && TABLE), "the grouped form has whole tiles as work units");
   using L = Smem;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -503,29 +548,52 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
+  const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream (grouped: the first problem's)
   const int nmod = plan.n;
   // work units: tiles, or (tile, group of moduli) with at most nmod groups per tile
   const int groups = SPLIT ? min(p.groups, nmod) : 1;
   const int units = p.num_tiles * groups;
+  // grouped: the moduli count and k-blocks of unit u's problem (0 moduli: skipped), its maps
+  auto table_unit = [&](int u, int& cur, int& tm, int& tn, int& nm, int& nkb, const CUtensorMap*& ma,
+                        const CUtensorMap*& mb) {
+    while (cur + 1 < count && table[cur + 1].tile_begin <= u) ++cur;
+    const ModTableEntry& e = table[cur];
+    const ModPlan* pl = e.plan;
+    nm = pl->feasible ? pl->n : 0;
+    nkb = e.nkb;
+    tile_coords(u - (int)e.tile_begin, e.tiles_m, e.group_m, e.num_tiles, tm, tn);
+    ma = &e.tmA;
+    mb = &e.tmB;
+  };
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t bytes = (uint32_t)(L::kABytes + L::kBBytes);
+      int cur = 0;
       for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const int tile = u / groups;
-        int l0 = 0, l1 = nmod;
+        int l0 = 0, l1 = nmod, nkb = p.nkb;
         if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
         int tm, tn;
-        tile128_coords(p, tile, tm, tn);
+        const CUtensorMap* ma = &tmA;
+        const CUtensorMap* mb = &tmB;
+        if (TABLE) {
+          table_unit(u, cur, tm, tn, l1, nkb, ma, mb);
+          if (l1 == 0) continue;
+          // maps written into global memory before the launch: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb) : "memory");
+        } else {
+          tile128_coords(p, tile, tm, tn);
+        }
         for (int l = l0; l < l1; ++l)
-          for (int kb = 0; kb < p.nkb; ++kb) {
+          for (int kb = 0; kb < nkb; ++kb) {
             mbar_wait(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
             mbar_arrive_expect_tx(&full[stage], bytes);
-            tma_load_3d(smem + L::kOffA + stage * L::kABytes, &tmA, &full[stage], kb * kBK, tm * kBM, l);
-            tma_load_3d(smem + L::kOffB + stage * L::kBBytes, &tmB, &full[stage], kb * kBK, tn * kBN, l);
+            tma_load_3d(smem + L::kOffA + stage * L::kABytes, ma, &full[stage], kb * kBK, tm * kBM, l);
+            tma_load_3d(smem + L::kOffB + stage * L::kBBytes, mb, &full[stage], kb * kBK, tn * kBN, l);
             if (++stage == kStages) { stage = 0; phase ^= 1u; }
           }
       }
@@ -537,16 +605,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
+      int cur = 0;
       for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        int l0 = 0, l1 = nmod;
+        int l0 = 0, l1 = nmod, nkb = p.nkb;
         if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
+        if (TABLE) {
+          int tm, tn;
+          const CUtensorMap *ma, *mb;
+          table_unit(u, cur, tm, tn, l1, nkb, ma, mb);
+        }
         for (int l = l0; l < l1; ++l)
-          for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+          for (int i0 = 0; i0 < nkb; i0 += kChunkBlocks, ++chunk) {
             const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
             mbar_wait(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
             tc_fence_after();
             const uint32_t dtm = tmem_base + buf * kBN;
-            const int i1 = min(p.nkb, i0 + kChunkBlocks);
+            const int i1 = min(nkb, i0 + kChunkBlocks);
             for (int it = i0; it < i1; ++it) {
               mbar_wait(&full[stage], phase, p.err, kErrWaitTma);
               tc_fence_after();
@@ -571,8 +645,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mod_epilogue_split<kEpiWarps, kBN>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, last_flag, warp,
                                        lane);
   } else {
-    mod_epilogue<kEpiWarps, kBN, false>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, warp, lane,
-                                        blockIdx.x, gridDim.x, kBM, 0);
+    mod_epilogue<kEpiWarps, kBN, false, TABLE>(p, nmod, !TABLE && plan.feasible == 0, tmem_base, acc_full, acc_empty,
+                                               warp, lane, blockIdx.x, gridDim.x, kBM, 0, table, count);
   }
 
   tc_fence_before();
@@ -784,6 +858,44 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
   if (!n && flag) atomicOr(err, kErrModRange);
 }
 
+// the plans of a grouped launch, one thread per problem (as k_mod_plan; an infeasible plan needs no
+// error bit: the grouped FP64 kernel computes that problem)
+__global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __restrict__ jobs, int count,
+                                                          const __grid_constant__ ModProducts mp) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const ModPlanJob j = jobs[q];
+  double rho = 0.0, gamma = 0.0, bound = 0.0;
+  int t = j.fixed_t, exact = 0;
+  if (t <= 0) {
+    cert_rho_gamma(j.words, &rho, &gamma);
+    t = cert_mod_bits(rho, gamma, (int)j.words[kCertTexA], (int)j.words[kCertTexB], j.k, j.tol, &bound, &exact);
+  }
+  const int n = t <= 62 ? moduli_for_products(t, j.k, mp) : 0;
+  ModPlan pl;
+  pl.t = n ? t : 1;
+  pl.n = n ? n : 1;
+  pl.feasible = n != 0;
+  pl.want = t;
+  pl.exact = exact;
+  pl.pad = 0;
+  pl.rho = rho;
+  pl.gamma = gamma;
+  pl.bound = bound;
+  *j.plan = pl;
+}
+
+// the column scales alpha 2^(tau_j - 2t) of a grouped launch, one block per problem
+__global__ void __launch_bounds__(256) k_mod_colscale_batched(const ColJob* __restrict__ jobs) {
+  const ColJob j = jobs[blockIdx.x];
+  const ModPlan pl = *j.plan;
+  if (!pl.feasible) return;
+  for (int64_t c = threadIdx.x; c < j.n; c += blockDim.x) {
+    const int tau = j.sigB[c] == kExpEmpty ? 0 : j.sigB[c];
+    j.cs[c] = j.badB[c] ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(j.alpha, tau - 2 * pl.t);
+  }
+}
+
 // ---- host side ----
 struct ModWorkspace {
   int* sigA;
@@ -806,7 +918,9 @@ struct ModWorkspace {
   int64_t kp;
 };
 
-size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWorkspace* ws) {
+// scratch = false (a problem of a grouped launch): no park slots, no split-form slots; the
+// launch has its own
+size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWorkspace* ws, bool scratch = true) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int64_t kp = (k + 7) / 8 * 8;
   // one CTA per 128 x 128 tile (one-SM form) or two per 256 x 256 tile (two-SM form), at most kMaxModCtas
@@ -814,6 +928,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const int64_t tiles2 = ((m + 255) / 256) * ((n + 255) / 256);
   int64_t ctas = tiles1 > 2 * tiles2 ? tiles1 : 2 * tiles2;
   if (ctas > kMaxModCtas) ctas = kMaxModCtas;
+  if (!scratch) ctas = 0;
   size_t off = 0;
   const size_t o_sigA = off; off = up(off + sizeof(int) * (size_t)m);
   const size_t o_sigB = off; off = up(off + sizeof(int) * (size_t)n);
@@ -835,7 +950,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
   const size_t o_scr = off; off = up(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
-  const int64_t split_tiles = tiles1 <= kSplitMaxTiles ? tiles1 : 0;
+  const int64_t split_tiles = (scratch && tiles1 <= kSplitMaxTiles) ? tiles1 : 0;
   const size_t o_tslot = off; off = up(off + (size_t)kTileSlotBytes * (size_t)split_tiles);
   const size_t o_tdone = off; off = up(off + sizeof(unsigned int) * (size_t)split_tiles);
   if (base && ws) {
@@ -890,6 +1005,48 @@ int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
     x = r - q * nr; r = nr; nr = x;
   }
   return t < 0 ? t + p : t;
+}
+
+// the moduli, their Barrett constants and the reconstruction constants of every n = 1..kMaxModuli;
+// the rest of `a` zeroed
+void mod_constants(ModArgs& a, const ModProducts& prods) {
+  memset(&a, 0, sizeof(a));
+  for (int l = 0; l < kMaxModuli; ++l) {
+    a.p[l] = kModuli[l];
+    a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
+    a.rq[l] = ((1u << 24) + (uint32_t)kModuli[l] - 1u) / (uint32_t)kModuli[l];
+  }
+  for (int nn = 1; nn <= kMaxModuli; ++nn) {
+    CrtSet& cs = a.set[nn - 1];
+    const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
+    for (int l = 0; l < nn; ++l) {
+      const hu128 Mp = M / (hu128)kModuli[l];
+      cs.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
+      for (int w = 0; w < 4; ++w) cs.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
+    }
+    cs.M_lo = (uint64_t)M; cs.M_hi = (uint64_t)(M >> 64);
+    const hu128 half = M / 2;
+    cs.half_lo = (uint64_t)half; cs.half_hi = (uint64_t)(half >> 64);
+  }
+}
+
+// the residue split parameters of every modulus (t and n come from a plan)
+void mod_split_params(ModSplit& ms) {
+  memset(&ms, 0, sizeof(ms));
+  for (int l = 0; l < kMaxModuli; ++l) {
+    const int pm = kModuli[l];
+    ms.pf[l] = (float)pm;
+    ms.inv[l] = 1.0f / (float)pm;
+    uint32_t w = 1, lo = 0, hi = 0;  // 256^d mod p
+    for (int d = 0; d < 8; ++d) {
+      if (d < 4) lo |= (w % (uint32_t)pm) << (8 * d);
+      else hi |= (w % (uint32_t)pm) << (8 * (d - 4));
+      w = (w * 256u) % (uint32_t)pm;
+    }
+    ms.wlo[l] = lo;
+    ms.whi[l] = hi;
+    ms.wbias[l] = 0x4B000000u + ((uint32_t)pm - (8388608u % (uint32_t)pm)) % (uint32_t)pm;
+  }
 }
 
 // Relative throughput per SM of the two-SM form over the one-SM form when both fill the GPU
@@ -1111,21 +1268,7 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
 
   // residues of both sides (the first n of the kMaxModuli, t bits, from the plan)
   ModSplit ms;
-  memset(&ms, 0, sizeof(ms));
-  for (int l = 0; l < kMaxModuli; ++l) {
-    const int pm = kModuli[l];
-    ms.pf[l] = (float)pm;
-    ms.inv[l] = 1.0f / (float)pm;
-    uint32_t w = 1, lo = 0, hi = 0;  // 256^d mod p
-    for (int d = 0; d < 8; ++d) {
-      if (d < 4) lo |= (w % (uint32_t)pm) << (8 * d);
-      else hi |= (w % (uint32_t)pm) << (8 * (d - 4));
-      w = (w * 256u) % (uint32_t)pm;
-    }
-    ms.wlo[l] = lo;
-    ms.whi[l] = hi;
-    ms.wbias[l] = 0x4B000000u + ((uint32_t)pm - (8388608u % (uint32_t)pm)) % (uint32_t)pm;
-  }
+  mod_split_params(ms);
   ms.plan = ws.plan;
   if ((rc = launch_residue_pair(pp, ms, split_blocks, s))) return rc;
   k_mod_colscale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.sigB, ws.badB, n, alpha, ws.plan, ws.cs);
@@ -1133,25 +1276,8 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
 
   // products modulo each modulus and the reconstruction; the constants of every n ride along
   ModArgs a;
-  memset(&a, 0, sizeof(a));
+  mod_constants(a, prods);
   a.tri = tri;
-  for (int l = 0; l < kMaxModuli; ++l) {
-    a.p[l] = kModuli[l];
-    a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
-    a.rq[l] = ((1u << 24) + (uint32_t)kModuli[l] - 1u) / (uint32_t)kModuli[l];
-  }
-  for (int nn = 1; nn <= kMaxModuli; ++nn) {
-    CrtSet& cs = a.set[nn - 1];
-    const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
-    for (int l = 0; l < nn; ++l) {
-      const hu128 Mp = M / (hu128)kModuli[l];
-      cs.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
-      for (int w = 0; w < 4; ++w) cs.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
-    }
-    cs.M_lo = (uint64_t)M; cs.M_hi = (uint64_t)(M >> 64);
-    const hu128 half = M / 2;
-    cs.half_lo = (uint64_t)half; cs.half_hi = (uint64_t)(half >> 64);
-  }
   a.m = m; a.n = n; a.ldc = ldc;
   a.plan = ws.plan;
   a.beta = beta;
@@ -1190,6 +1316,206 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
     info->bound = host_plan.bound;
   }
   return GBD_OK;
+}
+
+// ---- grouped modular problems ----
+namespace {
+constexpr int kGroupedModCtas = 160;  // park slots of the grouped product launch (one CTA per SM)
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count, void* base, ModGrouped* g, int* rc) {
+  *rc = GBD_OK;
+  char* b = static_cast<char*>(base);
+  size_t off = 0;
+  int64_t tiles = 0;
+  for (int q = 0; q < count; ++q) {
+    const gbd_problem& p = probs[which[q]];
+    tiles += ((p.m + kBM - 1) / kBM) * ((p.n + kBN - 1) / kBN);
+  }
+  const int ctas = (int)(tiles < kGroupedModCtas ? (tiles > 0 ? tiles : 1) : kGroupedModCtas);
+  const size_t o_jobs = off; off = up256(off + sizeof(PrepJob) * 2 * (size_t)count);
+  const size_t o_cert = off; off = up256(off + sizeof(CertTableEntry) * (size_t)count);
+  const size_t o_plj = off; off = up256(off + sizeof(ModPlanJob) * (size_t)count);
+  const size_t o_col = off; off = up256(off + sizeof(ColJob) * (size_t)count);
+  const size_t o_tab = off; off = up256(off + sizeof(ModTableEntry) * (size_t)count);
+  const size_t o_words = off; off = up256(off + sizeof(unsigned int) * kCertWords * (size_t)count);
+  const size_t o_scr = off; off = up256(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
+  std::vector<size_t> o_ws(count);
+  std::vector<int> nmod_ws(count);
+  for (int q = 0; q < count; ++q) {
+    const gbd_problem& p = probs[which[q]];
+    int nm = kMaxModuli;
+    if (p.slices > 0) {
+      nm = moduli_for(p.slices, p.k);
+      if (nm == 0) {
+        *rc = set_error(GBD_ERR_LIMIT, "grouped problem %d: %d bits need more than %d moduli at k = %lld", which[q],
+                        p.slices, kMaxModuli, (long long)p.k);
+        nm = kMaxModuli;
+      }
+    }
+    nmod_ws[q] = nm;
+    o_ws[q] = off;
+    off = up256(off + mod_layout(p.m, p.n, p.k, nm, nullptr, nullptr, false));
+  }
+  if (!base || !g || *rc) return off;
+
+  g->count = count;
+  g->index.assign(which, which + count);
+  g->jobs_dev = reinterpret_cast<PrepJob*>(b + o_jobs);
+  g->cert_dev = reinterpret_cast<CertTableEntry*>(b + o_cert);
+  g->planjobs_dev = reinterpret_cast<ModPlanJob*>(b + o_plj);
+  g->coljobs_dev = reinterpret_cast<ColJob*>(b + o_col);
+  g->table_dev = reinterpret_cast<ModTableEntry*>(b + o_tab);
+  g->words_dev = reinterpret_cast<unsigned int*>(b + o_words);
+  g->scr = reinterpret_cast<uint8_t*>(b + o_scr);
+  g->scr_ctas = ctas;
+  g->jobs.assign(2 * (size_t)count, PrepJob{});
+  g->cert.assign(count, CertTableEntry{});
+  g->planjobs.assign(count, ModPlanJob{});
+  g->coljobs.assign(count, ColJob{});
+  g->plans.assign(count, nullptr);
+  std::vector<ModWorkspace> ws(count);
+  g->exp_blocks = 0;
+  g->split_blocks = 0;
+  int64_t cert_tiles = 0;
+  for (int q = 0; q < count; ++q) {
+    const gbd_problem& p = probs[which[q]];
+    mod_layout(p.m, p.n, p.k, nmod_ws[q], b + o_ws[q], &ws[q], false);
+    const ModWorkspace& w = ws[q];
+    unsigned int* words = g->words_dev + (size_t)kCertWords * q;
+    PrepJob& ja = g->jobs[2 * q];
+    PrepJob& jb = g->jobs[2 * q + 1];
+    // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
+    ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
+    ja.sig = w.sigA; ja.bad = w.badA; ja.mu = w.muA; ja.D = w.DA; ja.kp = w.kp;
+    ja.tex = words + kCertTexA; ja.plan = w.plan;
+    jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
+    jb.sig = w.sigB; jb.bad = w.badB; jb.mu = w.muB; jb.D = w.DB; jb.kp = w.kp;
+    jb.tex = words + kCertTexB; jb.plan = w.plan;
+    prep_job_blocks(ja, g->exp_blocks, g->split_blocks);
+    prep_job_blocks(jb, g->exp_blocks, g->split_blocks);
+    CertTableEntry& ce = g->cert[q];
+    if ((*rc = make_cert_entry(p.m, p.n, p.k, w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, words, &ce))) return off;
+    ce.tile_begin = cert_tiles;
+    cert_tiles += ce.a.num_tiles;
+    ModPlanJob& pj = g->planjobs[q];
+    pj.words = words;
+    pj.plan = w.plan;
+    pj.k = p.k;
+    pj.tol = p.tol > 0.0 ? p.tol : 2.0 * (double)p.k * kUnitRoundoff;
+    pj.fixed_t = p.slices > 0 ? p.slices : 0;
+    ColJob& cj = g->coljobs[q];
+    cj.sigB = w.sigB;
+    cj.badB = w.badB;
+    cj.cs = w.cs;
+    cj.plan = w.plan;
+    cj.alpha = p.alpha;
+    cj.n = p.n;
+    g->plans[q] = w.plan;
+  }
+  g->cert_tiles = (int)cert_tiles;
+  // the product table: the deepest problems' tiles first (longest tiles first over the SMs)
+  std::vector<int> order(count);
+  for (int q = 0; q < count; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return probs[which[x]].k > probs[which[y]].k; });
+  g->table.assign(count, ModTableEntry{});
+  int64_t mt = 0;
+  for (int r = 0; r < count; ++r) {
+    const int q = order[r];
+    const gbd_problem& p = probs[which[q]];
+    const ModWorkspace& w = ws[q];
+    ModTableEntry& e = g->table[r];
+    const uint64_t dA[3] = {(uint64_t)p.k, (uint64_t)p.m, (uint64_t)nmod_ws[q]};
+    const uint64_t pA[2] = {(uint64_t)w.kp * 2, (uint64_t)p.m * w.kp * 2};
+    const uint32_t bA[3] = {(uint32_t)kBK, (uint32_t)kBM, 1u};
+    if ((*rc = encode_tmap(&e.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.DA, dA, pA, bA, CU_TENSOR_MAP_SWIZZLE_128B)))
+      return off;
+    const uint64_t dB[3] = {(uint64_t)p.k, (uint64_t)p.n, (uint64_t)nmod_ws[q]};
+    const uint64_t pB[2] = {(uint64_t)w.kp * 2, (uint64_t)p.n * w.kp * 2};
+    const uint32_t bB[3] = {(uint32_t)kBK, (uint32_t)kBN, 1u};
+    if ((*rc = encode_tmap(&e.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B)))
+      return off;
+    e.m = p.m; e.n = p.n; e.ldc = p.ldc;
+    e.beta = p.beta;
+    e.C = p.C;
+    e.sigA = w.sigA; e.badA = w.badA;
+    e.cs = w.cs;
+    e.plan = w.plan;
+    e.nkb = (int)((p.k + kBK - 1) / kBK);
+    e.tiles_m = (int)((p.m + kBM - 1) / kBM);
+    e.num_tiles = e.tiles_m * (int)((p.n + kBN - 1) / kBN);
+    e.group_m = e.tiles_m;  // within one problem the tiles walk down the rows
+    e.tile_begin = mt;
+    mt += e.num_tiles;
+  }
+  g->mod_tiles = (int)mt;
+  if (mt > ((int64_t)1 << 30) || cert_tiles > ((int64_t)1 << 30)) *rc = set_error(GBD_ERR_LIMIT, "grouped: too many tiles");
+  return off;
+}
+
+int mod_grouped_upload(const ModGrouped& g, cudaStream_t s) {
+  if (g.count == 0) return GBD_OK;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(g.jobs_dev, g.jobs.data(), sizeof(PrepJob) * g.jobs.size(), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(g.cert_dev, g.cert.data(), sizeof(CertTableEntry) * g.cert.size(), cudaMemcpyHostToDevice,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(g.planjobs_dev, g.planjobs.data(), sizeof(ModPlanJob) * g.planjobs.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(g.coljobs_dev, g.coljobs.data(), sizeof(ColJob) * g.coljobs.size(), cudaMemcpyHostToDevice,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(g.table_dev, g.table.data(), sizeof(ModTableEntry) * g.table.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped modular: table copies");
+  return GBD_OK;
+}
+
+int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
+  if (g.count == 0) return GBD_OK;
+  cudaError_t e;
+  int rc;
+  const int njobs = (int)g.jobs.size();
+  if ((e = cudaMemsetAsync(g.words_dev, 0, sizeof(unsigned int) * kCertWords * (size_t)g.count, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped modular: clearing the certification words");
+  // exponents, flags and magnitude sums of every side (the sums zeroed by the first launch)
+  if ((rc = launch_prep_batched(g.jobs_dev, njobs, g.exp_blocks, 0, true, false, s))) return rc;
+  if ((rc = launch_magnitudes_batched(g.jobs_dev, njobs, g.exp_blocks, s))) return rc;
+  // the certification: FP8 magnitude planes, their products, the plans
+  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s))) return rc;
+  if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, sms, s))) return rc;
+  k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, moduli_products());
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped plan launch");
+  // residues and column scales with each problem's plan
+  ModSplit ms;
+  mod_split_params(ms);
+  if ((rc = launch_residue_batched(g.jobs_dev, njobs, ms, g.split_blocks, s))) return rc;
+  k_mod_colscale_batched<<<g.count, 256, 0, s>>>(g.coljobs_dev);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped column scale launch");
+  // the products of every feasible problem in one persistent launch
+  if (g.mod_tiles <= 0) return GBD_OK;
+  ModArgs a;
+  mod_constants(a, moduli_products());
+  a.plan = g.plans[0];  // read at kernel start; the tiles use their own problems' plans
+  a.scr = g.scr;
+  a.err = device_error_word();
+  a.num_tiles = g.mod_tiles;
+  a.tile_end = g.mod_tiles;
+  a.tail_from = -1;
+  a.tiles_m = 1;
+  a.group_m = 1;
+  a.nkb = 1;
+  a.groups = 1;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  int grid = g.mod_tiles < sms ? g.mod_tiles : sms;
+  if (grid > g.scr_ctas) grid = g.scr_ctas;
+  e = cudaFuncSetAttribute(k_mod_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped modular gemm)");
+  k_mod_gemm<false, true><<<grid, kThreads, Smem::kAlloc, s>>>(a, dummy, dummy, g.table_dev, g.count);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped modular gemm launch");
 }
 
 }  // namespace emu

@@ -541,6 +541,32 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
+// grouped modular problems: magnitude planes (FP8) and residues over a job table
+__global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  const MagWriter<true> w{15, j.R, j.K, j.D, (j.K + 15) / 16 * 16, j.tex};  // the FP8 plane scale and pitch
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+}
+
+__global__ void __launch_bounds__(kSplitThreads, 3) k_residue_batched(const PrepJob* __restrict__ jobs, int njobs,
+                                                                   const __grid_constant__ ModSplit mp) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const PrepJob& j = jobs[ji];
+  const ModPlan pl = *j.plan;
+  if (!pl.feasible) return;  // the problem is computed by the FP64 kernel
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  const ResidueWriter w{&mp, pl.n, pl.t, j.R, j.K, j.D, j.kp};
+  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+}
+
 // ---- both operand sides of one problem in one launch (single calls) ----
 // job 0 is op(A), job 1 op(B)^T; their blocks are numbered by prep_job_blocks.  The jobs are
 // kernel arguments, so no job table has to be copied to the device.
@@ -912,6 +938,21 @@ int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, 
     return launch_check("batched split launch");
   }
   return GBD_OK;
+}
+
+int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s) {
+  if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+  k_magplane_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+  return launch_check("batched magnitude plane launch");
+}
+
+int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
+                           cudaStream_t s) {
+  if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+  k_residue_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs, mp);
+  return launch_check("batched residue launch");
 }
 
 int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,

@@ -33,6 +33,9 @@ struct NativeTableEntry {
   NativeArgs a;
   int64_t tile_begin;
   int32_t ta, tb, tile, tiles_m;
+  // the FP64 fallback of a modular problem: its tiles run only when the problem's device plan
+  // found the target out of reach (otherwise the modular kernel computes it)
+  const emu::ModPlan* only_if_infeasible;
 };
 
 __global__ void __launch_bounds__(kNativeThreads)
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(kNativeThreads)
       else hi = mid - 1;
     }
     const NativeTableEntry& e = table[lo];
+    if (e.only_if_infeasible && e.only_if_infeasible->feasible) continue;  // uniform over the block
     const NativeArgs a = e.a;
     const int64_t local = tile - e.tile_begin;
     const int64_t tm = local % e.tiles_m, tn = local / e.tiles_m;
@@ -116,6 +120,8 @@ struct gbd_plan {
   gbd::emu::PrepJob* jobs_dev = nullptr;
   float* stats_dev = nullptr;
   int64_t exp_blocks = 0, split_blocks = 0;
+  // modular problems: prepared, certified and planned on the device by every run
+  gbd::emu::ModGrouped mod;
 };
 
 namespace gbd {
@@ -135,7 +141,7 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
     const gbd_problem& p = probs[i];
     const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
     if (p.mode == GBD_MODE_EMULATED && !quick) ++nemu;
-    else ++nnat;
+    else ++nnat;  // native problems, quick returns and modular problems' fallback entries
   }
   // room for every problem: emulated ones whose target cannot be certified run natively
   off = up256(off + sizeof(NativeTableEntry) * (size_t)(nnat + nemu));
@@ -157,6 +163,19 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   off = up256(off + sizeof(double) * 128 * 256 * (size_t)pair_ctas);
   const size_t o_pscp = off;
   off = up256(off + sizeof(int32_t) * emu::kParkSlots * 128 * 256 * (size_t)pair_ctas);
+  // modular problems: their workspaces, tables and the product launch's park slots
+  std::vector<int> mod_which;
+  for (int i = 0; i < count; ++i) {
+    const gbd_problem& p = probs[i];
+    const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_MODULAR && !quick) mod_which.push_back(i);
+  }
+  const size_t o_mod = off;
+  int mrc = GBD_OK;
+  off = up256(off + emu::mod_grouped_layout(probs, mod_which.data(), (int)mod_which.size(),
+                                            (base && plan) ? static_cast<char*>(base) + o_mod : nullptr,
+                                            (base && plan) ? &plan->mod : nullptr, &mrc));
+  if (mrc && plan) plan->mod.count = -1;  // an invalid fixed bit count: reported by the plan
   int ei = 0;
   for (int i = 0; i < count; ++i) {
     const gbd_problem& p = probs[i];
@@ -205,10 +224,12 @@ int validate(const gbd_problem* probs, int count) {
     const gbd_problem& p = probs[i];
     const int bad = check_dgemm_args(p.transa, p.transb, p.m, p.n, p.k, p.lda, p.ldb, p.ldc);
     if (bad) return set_error(GBD_ERR_ARG, "grouped problem %d: parameter %d had an illegal value", i, bad);
-    if (p.mode != GBD_MODE_NATIVE && p.mode != GBD_MODE_EMULATED)
+    if (p.mode != GBD_MODE_NATIVE && p.mode != GBD_MODE_EMULATED && p.mode != GBD_MODE_MODULAR)
       return set_error(GBD_ERR_ARG, "grouped problem %d: mode %d", i, p.mode);
     if (p.mode == GBD_MODE_EMULATED && (p.slices < 0 || p.slices > emu::kMaxSlices))
       return set_error(GBD_ERR_ARG, "grouped problem %d: slices %d", i, p.slices);
+    if (p.mode == GBD_MODE_MODULAR && (p.slices < 0 || p.slices > 62))
+      return set_error(GBD_ERR_ARG, "grouped problem %d: bits %d (0 automatic, or 1..62)", i, p.slices);
     if (p.tile != 0 && p.tile != 32 && p.tile != 64)
       return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0, 32 or 64)", i, p.tile);
     const int64_t lim = (int64_t)1 << 31;
@@ -257,6 +278,7 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     if (slices_used) slices_used[i] = 0;
     if (p.m == 0 || p.n == 0) continue;
     const bool quick = p.alpha == 0.0 || p.k == 0;
+    if (p.mode == GBD_MODE_MODULAR && !quick) continue;  // the modular part (laid out below)
     if (p.mode == GBD_MODE_EMULATED && !quick) {
       gbd_plan::Emu e;
       e.p = p;
@@ -272,6 +294,13 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   std::vector<int> s_override(count, 0);
   for (int i = 0; i < count; ++i) s_override[i] = probs[i].slices;
   grouped_layout(probs, count, s_override.data(), workspace, plan);
+  if (plan->mod.count < 0) return GBD_ERR_LIMIT;  // a fixed bit count beyond 16 moduli (message set)
+  // each modular problem's FP64 fallback, gated by its device plan
+  for (int q = 0; q < plan->mod.count; ++q) {
+    NativeTableEntry t = native_entry(probs[plan->mod.index[q]], false);
+    t.only_if_infeasible = plan->mod.plans[q];
+    plan->native.push_back(t);
+  }
 
   // preparation jobs: op(A) and op(B)^T of every emulated problem
   cudaError_t e;
@@ -425,20 +454,42 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     nt += (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
   }
   plan->native_tiles = nt;
-  // tables to the device (pageable copies are staged before the call returns)
-  if (!plan->native.empty() &&
-      (e = cudaMemcpyAsync(plan->native_dev, plan->native.data(), sizeof(NativeTableEntry) * plan->native.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(e, "grouped: native table copy");
-  if (!plan->emu_table.empty() &&
-      (e = cudaMemcpyAsync(plan->emu_dev, plan->emu_table.data(), sizeof(emu::EmuTableEntry) * plan->emu_table.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(e, "grouped: emulated table copy");
-  if (!plan->jobs.empty() &&
-      (e = cudaMemcpyAsync(plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(e, "grouped: job table copy");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "grouped: plan set-up");
+  // tables to the device, through page-locked staging owned by the plan: the copies are stream-ordered
+  // and need no synchronisation
+  struct Part {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  const Part parts[] = {
+      {plan->native_dev, plan->native.data(), sizeof(NativeTableEntry) * plan->native.size()},
+      {plan->emu_dev, plan->emu_table.data(), sizeof(emu::EmuTableEntry) * plan->emu_table.size()},
+      {plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size()},
+      {plan->mod.jobs_dev, plan->mod.jobs.data(), sizeof(emu::PrepJob) * plan->mod.jobs.size()},
+      {plan->mod.cert_dev, plan->mod.cert.data(), sizeof(emu::CertTableEntry) * plan->mod.cert.size()},
+      {plan->mod.planjobs_dev, plan->mod.planjobs.data(), sizeof(emu::ModPlanJob) * plan->mod.planjobs.size()},
+      {plan->mod.coljobs_dev, plan->mod.coljobs.data(), sizeof(emu::ColJob) * plan->mod.coljobs.size()},
+      {plan->mod.table_dev, plan->mod.table.data(), sizeof(emu::ModTableEntry) * plan->mod.table.size()},
+  };
+  size_t staged = 0;
+  for (const Part& q : parts) staged += up256(q.bytes);
+  if (staged > 0) {
+    int handle = -1;
+    void* pinned = nullptr;
+    if ((rc = staging_get(staged, &handle, &pinned))) return rc;
+    size_t at = 0;
+    for (const Part& q : parts) {
+      if (q.bytes == 0) continue;
+      char* h = static_cast<char*>(pinned) + at;
+      memcpy(h, q.src, q.bytes);
+      if ((e = cudaMemcpyAsync(q.dst, h, q.bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        staging_put(handle, s);
+        return cuda_fail(e, "grouped: table copy");
+      }
+      at += up256(q.bytes);
+    }
+    if ((rc = staging_put(handle, s))) return rc;
+  }
   *out = plan;
   return GBD_OK;
 }
@@ -464,7 +515,10 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
                  : emu::launch_slice_gemm_grouped(plan->emu_dev + sg.first, sg.count, (int)sg.tiles, sg.slices, s);
     if (rc) return rc;
   }
-  // native: one persistent launch over all tiles
+  // modular: preparation, certification and plans on the device, then one persistent product launch
+  if ((rc = emu::mod_grouped_run(plan->mod, sms, s))) return rc;
+  // native (and the fallbacks of modular problems whose plans found no certified bit count): one
+  // persistent launch over all tiles
   if (plan->native_tiles > 0) {
     if ((e = cudaMemsetAsync(plan->counter_dev, 0, sizeof(unsigned long long), s)) != cudaSuccess)
       return cuda_fail(e, "grouped: counter reset");

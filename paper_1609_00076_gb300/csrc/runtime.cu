@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -114,6 +115,62 @@ int current_device(int* device, int* num_sms) {
   if (device) *device = dev;
   if (num_sms) *num_sms = g_sm_count[dev];
   return GBD_OK;
+}
+
+// ---- page-locked staging for host-to-device table copies ----
+namespace {
+struct StagingBlock {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int device = -1;
+  cudaEvent_t ev = nullptr;  // recorded after the block's last copies
+  bool in_use = false;
+};
+std::mutex g_staging_mu;
+std::vector<StagingBlock> g_staging;
+constexpr size_t kStagingMin = (size_t)64 << 10;
+}  // namespace
+
+int staging_get(size_t bytes, int* handle, void** ptr) {
+  *handle = -1;
+  *ptr = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "staging: cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_staging_mu);
+  for (size_t i = 0; i < g_staging.size(); ++i) {
+    StagingBlock& b = g_staging[i];
+    if (b.in_use || b.device != dev || b.bytes < bytes) continue;
+    if (cudaEventQuery(b.ev) != cudaSuccess) continue;  // its copies have not run yet
+    b.in_use = true;
+    *handle = (int)i;
+    *ptr = b.p;
+    return GBD_OK;
+  }
+  StagingBlock b;
+  b.bytes = kStagingMin;
+  while (b.bytes < bytes) b.bytes *= 2;
+  b.device = dev;
+  if ((e = cudaHostAlloc(&b.p, b.bytes, cudaHostAllocDefault)) != cudaSuccess)
+    return cuda_fail(e, "staging: cudaHostAlloc");
+  if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) {
+    cudaFreeHost(b.p);
+    return cuda_fail(e, "staging: cudaEventCreate");
+  }
+  b.in_use = true;
+  g_staging.push_back(b);
+  *handle = (int)g_staging.size() - 1;
+  *ptr = b.p;
+  return GBD_OK;
+}
+
+int staging_put(int handle, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_staging_mu);
+  if (handle < 0 || handle >= (int)g_staging.size()) return GBD_OK;
+  StagingBlock& b = g_staging[handle];
+  cudaError_t e = cudaEventRecord(b.ev, stream);
+  b.in_use = false;
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "staging: cudaEventRecord");
 }
 
 unsigned int* device_error_word() {

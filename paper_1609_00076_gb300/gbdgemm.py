@@ -89,6 +89,7 @@ _c, _i64, _d, _i, _vp, _sz = (ctypes.c_char, ctypes.c_int64, ctypes.c_double, ct
 
 GBD_MODE_NATIVE = 0
 GBD_MODE_EMULATED = 1
+GBD_MODE_MODULAR = 2
 
 GBD_METHOD_NATIVE = 0
 GBD_METHOD_SPLIT = 1
