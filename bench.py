@@ -46,14 +46,9 @@ def workload_name():
 
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to FP64
-NOMINAL_BF16, NOMINAL_FP64 = 2250.0, 1.25
-# dram bytes (read + write) of the product phase of one call, from one single-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of this 8192^3 workload: the split slice kernel's
-# launch, and the modular pair launch plus its one-SM launch for the last wave (24.79 + 0.77 GB);
-# both vary with where the planes land in physical memory (16.8-23.2 GB read by the pair launch,
-# 36-114 GB by the slice kernel, across captures); None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 78.48e9, "mod": 25.56e9}
+# dram bytes (read + write) of the product phase of one call (dram__bytes_read.sum +
+# dram__bytes_write.sum of the product launches), None until captured for the current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": None, "mod": None}
 
 
 def load_peaks():
@@ -177,9 +172,10 @@ def host_inputs(seed: int):
 
 
 # kernels of one modular call with the bits chosen on the device: exponents and magnitudes, row
-# statistics, magnitude planes, the certification product, the plan, residues, column scales and
-# the products (the tail launch comes on top, see mod_tail_launches)
-MOD_LAUNCHES = 8
+# statistics, magnitude planes (FP8), the certification product, the plan, the BF16 retry's planes,
+# product and plan (three launches that return at once when the FP8 plan is feasible), residues,
+# column scales and the products (the tail launch comes on top, see mod_tail_launches)
+MOD_LAUNCHES = 11
 
 
 def mod_tail_launches(m, n, sms):
@@ -330,13 +326,11 @@ def run_ours(args, world, rank, local, pg):
         gemm_ms.append(info.gemm_ms)
         prep_ms.append(info.prep_ms)
     moduli, bits, bound_est = info.products, info.digit_bits, info.bound
-    del ws
     results = {"modular": C.cpu().numpy()} if rank == 0 else {}  # for the accuracy report (untimed)
 
     # ---- the split emulation on the same inputs (automatic slices at the same bound) ----
     split = split_measure(dev, stream, A, B, C, split_ws, split_wsb, steps=max(3, min(args.steps, 10)),
                           warmup=max(3, args.warmup))
-    del split_ws
     if rank == 0:
         results["split"] = C.cpu().numpy()
 
@@ -422,6 +416,12 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- latency of small calls (256^3, the latency configuration) ----
     lat = small_call_latency(dev, stream)
+    # ---- the FP64 tensor-core rate of this GPU (the native path's roofline), measured ----
+    rc_probe, fp64_peak = gbdgemm.gbd_fp64_mma_probe(2000, stream=stream)  # about 0.3 s
+    gbdgemm.check(rc_probe)
+    # ---- configuration 3's wider exponent ranges (rank 0; the headline's inputs are overwritten) ----
+    e_legs = exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb) if rank == 0 else None
+    del ws, split_ws
     # ---- grouped batch of 512 uneven problems, the serving loop, level-3 BLAS (rank 0, default size only) ----
     grouped = grouped_measure(dev, stream) if (rank == 0 and not args.no_extras) else None
     serving_rep = serving_measure() if (rank == 0 and not args.no_extras) else None
@@ -431,8 +431,9 @@ def run_ours(args, world, rank, local, pg):
     if rank != 0:
         return 0
     peaks, src = load_peaks()
-    bf16_sust = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64 / NOMINAL_BF16
+    # the modular call is about 10 ms, its timed region a fraction of a second: the burst peak applies
+    bf16_burst = peaks["bf16_tflops"]
+    bf16_sust = peaks.get("bf16_tflops_sustained", bf16_burst)
     g_ms = statistics.mean(gemm_ms)
     achieved = moduli * flops / (g_ms / 1000.0) / 1e12
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
@@ -452,24 +453,27 @@ def run_ours(args, world, rank, local, pg):
                    "moduli": moduli, "integer_bits": bits, "certified_bound": bound_est,
                    "l2": f"inputs larger than L2 ({M * K * 8 >> 20} MiB each)", "parallelism": f"replicas x{world}"},
         "native": {"value": nat_tflops, "unit": "TFLOP/s", "ms_per_call": nat_ms, "frac_of_fp64_peak": nat_tflops / fp64_peak,
-                   "fp64_peak": fp64_peak},
+                   "fp64_peak": fp64_peak,
+                   "fp64_peak_source": "measured: gbd_fp64_mma_probe (independent mma.sync.m16n8k16.f64 streams)"},
+        "exponent_ranges": e_legs,
         "emulated_over_native": value / nat_tflops,
         "phases_ms": {"prep": statistics.mean(prep_ms), "products_and_reconstruction": g_ms},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                     "frac": achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+                     "frac": achieved / bf16_burst, "frac_of_sustained": achieved / bf16_sust,
+                     "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
                      "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT), with "
                                "k_mod_gemm<0> for the last wave's tiles (cta_group::1)",
-                     "peak_source": f"{src} bf16_tflops_sustained"},
+                     "peak_source": f"{src} bf16_tflops (burst: one call of about 10 ms)"},
         "split": {
             "value": split["value"], "unit": "TFLOP/s", "ms_per_call": split["ms"], "steps": split["steps"],
             "path": "emulated (split digits on tcgen05 BF16, FP64 bound)", "slices": split["slices"],
             "products": split["products"], "over_native": split["value"] / nat_tflops,
             "modular_over_split": value / split["value"],
             "phases_ms": {"prep": split["prep_ms"], "slice_gemm": split["gemm_ms"]},
-            "roofline": {"bound": "tensor", "achieved": s_achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                         "frac": s_achieved / bf16_sust, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
+            "roofline": {"bound": "tensor", "achieved": s_achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+                         "frac": s_achieved / bf16_burst, "traffic": TRAFFIC_PER_LAUNCH.get("emu"),
                          "kernel": "k_slice_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32)",
-                         "peak_source": f"{src} bf16_tflops_sustained"},
+                         "peak_source": f"{src} bf16_tflops (burst)"},
         },
         "latency": lat,
         "grouped": grouped,
@@ -529,8 +533,10 @@ def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
     """Device time of the GEMM-based DSYRK, DTRMM and DTRSM (side L, lower, N, non-unit) at n,
     native and emulated (each product at its FP64 bound): DSYRK on uniform[-1,1) A (the GEMM's
     inputs), the triangular operations on the well-conditioned A/n + 1.5 I; emulated DSYRK also
-    on that diagonally dominant A ("dsyrk_dominant"), whose rows need more than 16 moduli at the
-    FP64 bound, so that its products fall back to the split emulation."""
+    on that diagonally dominant A ("dsyrk_dominant"): the off-diagonal entries of A A^T whose two
+    small factors next to the 1.5 are themselves small need more than 16 moduli and more than 9
+    slices at the FP64 bound (the row scale is set by the 1.5), so every block product of that call
+    is certified onto the FP64 path and the leg runs at the native rate."""
     import numpy as np
     import torch
 
@@ -582,14 +588,84 @@ def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
     return out
 
 
+def exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb, es=(8, 32), seed: int = 2100, calls: int = 3,
+                  sample_rows: int = 16):
+    """Configuration 3's wider exponent ranges: entries uniform[-1,1) * 2^U, U uniform on {-e..e}.
+    Each leg takes the fastest certified path (the modular emulation, else the split one, which
+    computes natively when no slice count is certified), as gbd_ctx_dgemm's automatic method does;
+    reports the path, its precision, the time per call and the error against the oracle on sampled
+    rows.  A, B, C and the workspaces are reused (the headline's inputs are overwritten)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1609_00076_gb300 import gbdgemm, synth
+    out = {}
+    flops = 2.0 * M * N * K
+    for e in es:
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed + e)
+        with torch.cuda.stream(stream):
+            for X in (A, B):
+                u = torch.empty(X.numel(), dtype=torch.float64, device=dev).uniform_(-1.0, 1.0, generator=g)
+                ex = torch.randint(-e, e + 1, (X.numel(),), device=dev, generator=g, dtype=torch.int32)
+                X.copy_(torch.ldexp(u, ex.to(torch.float64)))
+                del u, ex
+        stream.synchronize()
+        info = gbdgemm.GbdEmuInfo()
+
+        def call(report=False):
+            info.record_phases = 0
+            rc = gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, ws, wsb,
+                                           info if report else None, stream=stream)
+            if rc == gbdgemm.GBD_ERR_LIMIT:  # no bit count within 16 moduli: the split emulation
+                rc = gbdgemm.gbd_dgemm_emu("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, 0, 0.0, split_ws, split_wsb,
+                                           info if report else None, stream=stream)
+            gbdgemm.check(rc)
+
+        call(report=True)
+        stream.synchronize()
+        ev = _events(calls + 1)
+        ev[0].record(stream)
+        for i in range(calls):
+            call()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[-1]) / calls
+        gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+        path = {gbdgemm.GBD_PATH_MODULAR: "modular", gbdgemm.GBD_PATH_SPLIT: "split",
+                gbdgemm.GBD_PATH_NATIVE: "native (no certified emulation)"}.get(info.path, str(info.path))
+        leg = {"ms_per_call": ms, "tflops": flops / (ms / 1e3) / 1e12, "path": path}
+        if info.path == gbdgemm.GBD_PATH_MODULAR:
+            leg.update({"moduli": info.slices, "integer_bits": info.digit_bits, "certified_bound": info.bound})
+        elif info.path == gbdgemm.GBD_PATH_SPLIT:
+            leg.update({"slices": info.slices, "products": info.products, "certified_bound": info.bound})
+        # the error against the oracle on sampled rows
+        Ah, Bh, Ch = A.cpu().numpy(), B.cpu().numpy(), C.cpu().numpy()
+        rows = sorted({int(r) for r in synth.splitmix64(seed + 7 * e, sample_rows) % M})
+        ref = oracle.dgemm_rows("N", "N", M, N, K, 1.0, Ah, M, Bh, K, 0.0, None, M, rows=rows)
+        G = oracle.abs_bound_rows("N", "N", M, N, K, 1.0, Ah, M, Bh, K, 0.0, None, M, rows=rows)
+        got = Ch.reshape(N, M)[:, rows].flatten()
+        err = np.abs(got - ref)
+        leg["accuracy"] = {"rows": len(rows), "max_abs_err": float(err.max()),
+                           "max_err_over_bound": float(np.max(err / (2 * K * 2.0 ** -53 * G)))}
+        out[f"e{e}"] = leg
+        del Ah, Bh, Ch
+    return out
+
+
 def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
-    """512 problems, m, n, k each log-uniform on [32, 2048], random transposes, uniform[-1,1):
-    one grouped plan per mode (native; emulated at the FP64 bound), TFLOP/s of plan runs."""
+    """Configuration 4: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
+    uniform[-1,1).  Native problems take the autotuner's tile per size bucket (measured here first);
+    every plan run is captured once in a CUDA graph and replayed.  Modes: native FP64; modular
+    (certified and planned on the device in every replay); split digits (slices certified when the
+    plan is made).  TFLOP/s of graph replays (best of `reps`)."""
     import ctypes
+    import tempfile
 
     import torch
 
-    from paper_1609_00076_gb300 import gbdgemm, synth
+    from paper_1609_00076_gb300 import autotune, gbdgemm, synth
     sizes = synth.log_uniform_sizes(seed, count, 32, 2048)
     flips = synth.coin(seed + 1, 2 * count)
     keep, base = [], []
@@ -607,47 +683,63 @@ def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int =
         base.append(dict(transa=ta, transb=tb, m=m, n=n, k=k, alpha=1.0, beta=0.0, A=A, lda=ra, B=B, ldb=rb,
                          C=C, ldc=m, slices=0, tile=0, tol=0.0))
     flops = sum(2.0 * p["m"] * p["n"] * p["k"] for p in base)
-    out = {"problems": count, "flops_per_batch": flops}
-    for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("emulated", gbdgemm.GBD_MODE_EMULATED)):
-        arr = gbdgemm.problem_array([dict(p, mode=mode) for p in base])
+    # the autotuner: native tile per output-size bucket, measured on this GPU into a fresh cache
+    t0 = time.perf_counter()
+    tuner = autotune.Autotuner(cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"))
+    tuner.tune_native_tiles(per_bucket=8, reps=2)
+    tune_s = time.perf_counter() - t0
+    out = {"problems": count, "flops_per_batch": flops, "graph": True,
+           "autotuner": {"seconds": tune_s, "native_tile_by_bucket": {b: e["tile"] for b, e in tuner.table.items()}}}
+    for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("emulated", gbdgemm.GBD_MODE_MODULAR),
+                       ("emulated_split", gbdgemm.GBD_MODE_EMULATED)):
+        desc = [dict(p, mode=mode) for p in base]
+        tuner.apply(desc)
+        arr = gbdgemm.problem_array(desc)
         wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         used = (ctypes.c_int * count)()
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
         rc, plan = gbdgemm.gbd_grouped_plan_create(arr, ws, wsb, slices_used=used, stream=stream)
         gbdgemm.check(rc)
+        create_ms = (time.perf_counter() - t0) * 1e3
         try:
-            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))  # warm-up
+            stream.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+            graph.replay()
             best = float("inf")
             for _ in range(reps):
                 e0, e1 = _events(2)
                 e0.record(stream)
-                gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+                with torch.cuda.stream(stream):
+                    graph.replay()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 best = min(best, e0.elapsed_time(e1))
+            gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+            del graph
         finally:
             gbdgemm.gbd_grouped_plan_destroy(plan)
-        d = {"ms": best, "tflops": flops / (best / 1e3) / 1e12}
+        d = {"ms": best, "tflops": flops / (best / 1e3) / 1e12, "plan_create_ms": create_ms}
         if mode == gbdgemm.GBD_MODE_EMULATED:
-            d["mean_slices"] = float(sum(used) / count)
+            d["mean_slices"] = float(sum(max(0, u) for u in used) / count)
+            d["fp64_fallbacks"] = int(sum(1 for u in used if u < 0))
         out[name] = d
         del ws
+    out["emulated_over_native"] = out["emulated"]["tflops"] / out["native"]["tflops"]
     return out
 
 
-def serving_measure(requests: int = 300, seed: int = 5000):
-    """Saturated rate of the mixed request stream, then a Poisson stream at 0.8 of it."""
+def serving_measure(requests: int = 2000, seed: int = 5000):
+    """Configuration 5: the saturated rate of the mixed request stream (all requests at once), then
+    Poisson streams of `requests` requests at 0.5, 0.8 and 0.95 of it: p50/p99 latency and TFLOP/s
+    per rate."""
     from paper_1609_00076_gb300 import serving
-    srv = serving.Server(budget_bytes=40e9, slots=3)
-    srv.run(serving.request_stream(seed - 1, 16, 0.0, big_fraction=0.0))
-    sat = srv.run(serving.request_stream(seed, requests, 0.0))
-    rate = 0.8 * sat.requests_per_s
-    rep = srv.run(serving.request_stream(seed + 1, requests, rate))
-    return {"requests": requests, "saturated_requests_per_s": sat.requests_per_s,
-            "saturated_tflops": sat.throughput_tflops, "rate_per_s": rate, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
-            "throughput_tflops": rep.throughput_tflops,
-            "mix": "90% m,n,k log-uniform [32,2048], 10% 4096^3; half native, half emulated at 1e-14; 40 GB budget"}
+    return serving.serving_benchmark(count=requests, fractions=(0.5, 0.8, 0.95), seed=seed, budget_gb=40.0, slots=3,
+                                     saturate_count=requests)
 
 
 def cpu_five_loop_measure(n: int = 4096, seed: int = 7000, reps: int = 2):

@@ -400,6 +400,14 @@ GBD_API int gbd_dgemm_grouped(const gbd_problem* probs, int count, void* workspa
                               size_t workspace_bytes, int* slices_used, void* stream);
 
 /*
+ * Measures the FP64 tensor-core rate of the current device (the native path's roofline):
+ * 4 x (SMs) blocks of 256 threads, each warp issuing iters x 8 independent
+ * mma.sync.m16n8k16.f64 (4096 flops each) on register operands; one warm-up launch, then
+ * one launch timed with CUDA events on `stream` (synchronised).  *tflops receives the rate.
+ */
+GBD_API int gbd_fp64_mma_probe(int64_t iters, double* tflops, void* stream);
+
+/*
  * Exercises the watchdog: launches one thread that waits on a barrier nothing
  * completes, gives up after `limit_ms` milliseconds (1..10000), sets the device
  * error word exactly as a kernel whose wait ran out would, and ends normally (no

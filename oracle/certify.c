@@ -17,7 +17,13 @@
  *     modular, t integer bits:          2^(-t-1) (mu_i + nu_j + k 2^(-t-1))
  *
  * (the rounding of every scaled entry is at most 2^(-t-1), the truncated digit tail below
- * 2^-7s, and the dropped digit pairs are those of levels above s + 1).  The FP64 target is
+ * 2^-7s, and the dropped digit pairs are those of levels above s + 1).  Every one of these
+ * errors vanishes with its entry, and an entry of magnitude at least theta_i (the smallest
+ * non-zero |a^_ip| of row i; phi_j likewise for column j of op(B)) is at least theta_i/|a^_ip|
+ * times smaller than its own term of G^: so the sums over p may be replaced by
+ *     nu_j -> min(nu_j, G^_ij / theta_i),   mu_i -> min(mu_i, G^_ij / phi_j),
+ *     k    -> min(k, G^_ij / (theta_i phi_j))       (the count of p with both entries non-zero),
+ * which is what makes triangular, sparse and block operands certifiable.  The FP64 target is
  * the componentwise bound tol (|alpha| |A||B| + |beta||C0|); the beta term only loosens it,
  * so it is met when the truncation error stays below (tol - r u) G_ij, where r u (u = 2^-53)
  * is set aside for the final roundings: r = 3 for the modular emulation (the conversion of
@@ -52,8 +58,8 @@ typedef struct {
   int s_exact;  /* s with exact digits and every product kept; 10: above 9 */
   int s;        /* the choice (10: infeasible) */
   int pad;
-  double rho;   /* max over the elements of (mu_i + nu_j) / G^_ij */
-  double gamma; /* max over the elements of 1 / G^_ij */
+  double rho;   /* max over the elements of (min(mu_i, G^/phi_j) + min(nu_j, G^/theta_i)) / G^_ij */
+  double gamma; /* max over the elements of min(k, G^/(theta_i phi_j)) / (k G^_ij) */
 } oracle_cert_t;
 
 static const int oc_moduli[16] = {256, 255, 253, 251, 247, 241, 239, 233,
@@ -126,6 +132,7 @@ typedef struct {
   int64_t nrows;
   const double* ra; /* [nrows][k] |a^| of the requested rows */
   const double* rmu;
+  const double* rth; /* [nrows] theta_i: the smallest non-zero |a^_ip| (0 for a zero row) */
   const int* rbad;
   double tau_mod, tau_split;
   int64_t j0, j1;
@@ -167,6 +174,9 @@ static void* oc_run(void* arg) {
       oc_add(&nu, cb[p]);
     }
     const double nuj = nu.hi + nu.lo;
+    double phj = 0.0; /* phi_j: the smallest non-zero |b^_pj| */
+    for (int64_t p = 0; p < k; ++p)
+      if (cb[p] > 0.0 && (phj == 0.0 || cb[p] < phj)) phj = cb[p];
     for (int64_t r = 0; r < J->nrows; ++r) {
       if (J->rbad[r]) continue;
       const double* a = J->ra + r * k;
@@ -174,15 +184,18 @@ static void* oc_run(void* arg) {
       for (int64_t p = 0; p < k; ++p) oc_add_prod(&g, a[p], cb[p]);
       const double G = g.hi + g.lo;
       if (!(G > 0.0)) continue; /* every term has a zero factor: no error */
-      const double mn = J->rmu[r] + nuj;
-      const double rho = mn / G, gam = 1.0 / G;
+      const double th = J->rth[r];
+      /* the error sums over p, each term vanishing with its entry (zero-aware) */
+      const double s1 = fmin(nuj, G / th), s2 = fmin(J->rmu[r], G / phj), s3 = fmin(kd, G / (th * phj));
+      const double mn = s1 + s2;
+      const double rho = mn / G, gam = s3 / (kd * G);
       if (rho > J->rho) J->rho = rho;
       if (gam > J->gamma) J->gamma = gam;
       int t = 1;
-      while (t <= 62 && !(ldexp(1.0, -t - 1) * (mn + kd * ldexp(1.0, -t - 1)) <= J->tau_mod * G)) ++t;
+      while (t <= 62 && !(ldexp(1.0, -t - 1) * (mn + s3 * ldexp(1.0, -t - 1)) <= J->tau_mod * G)) ++t;
       if (t > J->t_cert) J->t_cert = t;
       int s = 1;
-      while (s <= 9 && !(ldexp(1.0, -7 * s) * (mn + (s - 1) * (1.0 + ldexp(1.0, -7)) * kd) <= J->tau_split * G)) ++s;
+      while (s <= 9 && !(ldexp(1.0, -7 * s) * (mn + (s - 1) * (1.0 + ldexp(1.0, -7)) * s3) <= J->tau_split * G)) ++s;
       if (s > J->s_cert) J->s_cert = s;
     }
   }
@@ -259,9 +272,10 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
   /* the scaled magnitudes of the requested rows */
   double* ra = (double*)malloc(sizeof(double) * (size_t)(nrows > 0 ? nrows : 1) * (size_t)(k > 0 ? k : 1));
   double* rmu = (double*)malloc(sizeof(double) * (size_t)(nrows > 0 ? nrows : 1));
+  double* rth = (double*)malloc(sizeof(double) * (size_t)(nrows > 0 ? nrows : 1));
   int* rbad = (int*)malloc(sizeof(int) * (size_t)(nrows > 0 ? nrows : 1));
-  if (!ra || !rmu || !rbad) {
-    free(ra); free(rmu); free(rbad);
+  if (!ra || !rmu || !rth || !rbad) {
+    free(ra); free(rmu); free(rth); free(rbad);
     return -2;
   }
   for (int64_t r = 0; r < nrows; ++r) {
@@ -284,6 +298,10 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
     }
     rmu[r] = mu.hi + mu.lo;
     rbad[r] = bad;
+    double th = 0.0;
+    for (int64_t p = 0; p < k; ++p)
+      if (ra[r * k + p] > 0.0 && (th == 0.0 || ra[r * k + p] < th)) th = ra[r * k + p];
+    rth[r] = th;
   }
 
   int t_cert = 1, s_cert = 1;
@@ -304,7 +322,7 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
       J->m = m; J->n = n; J->k = k;
       J->A = A; J->B = B; J->lda = lda; J->ldb = ldb;
       J->rows = rows; J->nrows = nrows;
-      J->ra = ra; J->rmu = rmu; J->rbad = rbad;
+      J->ra = ra; J->rmu = rmu; J->rth = rth; J->rbad = rbad;
       J->tau_mod = tol - 3.0 * u;
       J->tau_split = tol - (3.0 * (double)segs + 3.0) * u;
       J->j0 = n * w / nthreads;
@@ -327,7 +345,7 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
     free(jobs);
     free(th);
   }
-  free(ra); free(rmu); free(rbad);
+  free(ra); free(rmu); free(rth); free(rbad);
   if (rc) return rc;
 
   const int tx = tA > tB ? tA : tB;

@@ -76,6 +76,8 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = slices == 0 ? ws.muA : nullptr; ja.D = ws.DA; ja.kp = ws.kp;
   jb.X = B; jb.ld = ldb; jb.R = n; jb.K = k; jb.rows_contig = tb != 0;
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = slices == 0 ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
+  ja.emin = slices == 0 ? ws.eminA : nullptr;
+  jb.emin = slices == 0 ? ws.eminB : nullptr;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if ((rc = launch_exponents_pair(pp, exp_blocks, ws.ysum, ws.zero_bytes, s))) return rc;
@@ -84,12 +86,13 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   double bound = 0.0, rho = 0.0, gamma = 0.0;
   if (slices == 0) {  // the certified choice: magnitude planes (in the slices' place) and their product
     if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
-    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu: clearing the certification words");
     const int prec = cert_prec_default();
     if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
-    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
-                          nullptr, 0, sms, s)))
+    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
+                          ws.eminB, ws.cert, nullptr, 0, sms, s)))
       return rc;
     unsigned int cw[kCertWords] = {};
     if ((e = cudaMemcpyAsync(cw, ws.cert, sizeof(cw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -98,6 +101,18 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
     cert_rho_gamma(cw, &rho, &gamma);
     const double target = tol > 0.0 ? tol : 2.0 * (double)k * kUnitRoundoff;
     s_use = cert_split_slices(rho, gamma, (int)cw[kCertTexA], (int)cw[kCertTexB], k, target, &bound, &exact);
+    if (s_use > kMaxSlices && prec == kCertFP8) {  // the FP8 planes' looser bound: certify again with BF16 planes
+      unsigned int* w2 = ws.cert + kCertRetry;
+      if ((rc = launch_magplane_pair(pp, kCertBF16, w2 + kCertTexA, split_blocks, s))) return rc;
+      if ((rc = launch_cert(m, n, k, kCertBF16, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB,
+                            ws.eminA, ws.eminB, w2, nullptr, 0, sms, s)))
+        return rc;
+      if ((e = cudaMemcpyAsync(cw, w2, sizeof(unsigned int) * kCertRetry, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "dgemm_emu: reading the certification");
+      cert_rho_gamma(cw, &rho, &gamma);
+      s_use = cert_split_slices(rho, gamma, (int)cw[kCertTexA], (int)cw[kCertTexB], k, target, &bound, &exact);
+    }
     if (s_use > kMaxSlices) {  // no slice count can be certified: the FP64 tensor-core path
       if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu: cudaEventRecord");
       if ((rc = gbd_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream))) return rc;

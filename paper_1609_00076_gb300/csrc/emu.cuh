@@ -45,6 +45,8 @@ struct Workspace {
   unsigned long long* muB;  // [n]
   float* stats;     // [4] min mu, min nu, any bad row, any bad column (grouped plans)
   unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
+  int* eminA;       // [m] smallest exponent of a row's non-zero entries (the certification)
+  int* eminB;       // [n]
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
@@ -90,7 +92,11 @@ struct PrepJob {
   // grouped modular problems: the side's exactness-width word and the problem's device plan
   unsigned int* tex;
   const struct ModPlan* plan;
+  // the smallest frexp exponent of each row's non-zero finite entries (atomic minimum by the
+  // magnitude planes; kEminNone until then), or null
+  int* emin;
 };
+constexpr int kEminNone = 0x7F7F7F7F;  // a row without a non-zero finite entry (memset byte 0x7F)
 // fills j's block ranges, advancing the running block counts of both launches
 void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks);
 
@@ -119,6 +125,10 @@ int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
 
 // ---- modular emulation (Ozaki scheme II) ----
+// precision of the magnitude planes: BF16 (7 stored fraction bits) or FP8 E5M2 (2 bits, products on
+// the FP8 tensor-core rate)
+constexpr int kCertBF16 = 0;
+constexpr int kCertFP8 = 1;
 constexpr int kMaxModuli = 16;  // the product of the moduli stays below 2^126
 // pairwise coprime moduli up to 256 (greedily from 256 down), so that every symmetric
 // residue is at most 128 in magnitude: exact in BF16, products at most 2^14
@@ -181,7 +191,8 @@ int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_bl
 // grouped modular problems: the magnitude planes (FP8 E5M2) of every job into its D, widths to
 // its tex; then, after the plans, the residues of every job with its problem's plan (nothing for
 // an infeasible plan)
-int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s);
+int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s,
+                            int prec = kCertFP8, bool retry = false);
 int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
                            cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
@@ -201,7 +212,10 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
 // max_j nu_j / min_i G_ij and gamma = 1 / min G_ij (float bits; G the certified lower bound of
 // (|A||B|)_ij 2^-(sigma_i + tau_j)), and the exactness widths of op(A) and op(B).
 constexpr int kCertRhoA = 0, kCertRhoB = 1, kCertGamma = 2, kCertTexA = 3, kCertTexB = 4;
-constexpr int kCertWords = 8;
+// two sets of words: the FP8 certification's, then (kCertRetry on) the BF16 one's, which runs only
+// when the FP8 planes' looser bound leaves the target out of reach
+constexpr int kCertRetry = 8;
+constexpr int kCertWords = 16;
 // rho = rhoA + rhoB (rounded up) and gamma from the words
 __host__ __device__ inline void cert_rho_gamma(const unsigned int* w, double* rho, double* gamma) {
   float a, b, g;
@@ -211,24 +225,22 @@ __host__ __device__ inline void cert_rho_gamma(const unsigned int* w, double* rh
   *rho = ((double)a + (double)b) * (1.0 + 1e-15);
   *gamma = (double)g;
 }
-// precision of the magnitude planes: BF16 (7 stored fraction bits) or FP8 E5M2 (2 bits, products on
-// the FP8 tensor-core rate)
-constexpr int kCertBF16 = 0;
-constexpr int kCertFP8 = 1;
 // the planes' precision of the emulations' automatic modes: FP8 unless GBD_CERT_DTYPE=bf16
 int cert_prec_default();
 // scale exponent S of the magnitude planes at inner dimension k (k 2^(2S) < 2^124)
 int plane_scale(int64_t k, int prec);
 // row pitch of a plane, in elements (16 bytes at least per row)
 int64_t plane_pitch(int64_t k, int prec);
-// magnitude planes of both sides into their jobs' D (one plane each); widths to tex[0], tex[1]
-int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s);
+// magnitude planes of both sides into their jobs' D (one plane each); widths to tex[0], tex[1];
+// with a gate, nothing is done when the gate's plan is feasible (the retry of the certification)
+int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s,
+                         const struct ModPlan* gate = nullptr);
 // the certification product of the planes PA [m][pitch], PB [n][pitch]: rho and gamma into
 // words[0..1]; Lout (optional, m x n, leading dimension ldl) receives the lower bound of (|A||B|)_ij
 int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const void* PB,
                 const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
-                const int* sigA, const int* sigB, unsigned int* words, double* Lout, int64_t ldl, int sms,
-                cudaStream_t stream);
+                const int* sigA, const int* sigB, const int* eminA, const int* eminB, unsigned int* words,
+                double* Lout, int64_t ldl, int sms, cudaStream_t stream, const struct ModPlan* gate = nullptr);
 
 // Arguments of the certification product of one problem (emu_cert.cu)
 struct CertArgs {
@@ -243,6 +255,10 @@ struct CertArgs {
   const int* badB;
   const int* sigA;
   const int* sigB;
+  const int* eminA;     // [m] smallest exponent of each row's non-zero entries (kEminNone: none)
+  const int* eminB;     // [n]
+  float kinv;           // 1/k, rounded up
+  const struct ModPlan* gate;  // the retry: nothing to do when this plan is already feasible
   unsigned int* words;  // the certification words: rhoA, rhoB, gamma (bits of non-negative floats)
   double* L;            // optional [m x n] output G_ij 2^(sigma_i + tau_j), leading dimension ldl
   int64_t ldl;
@@ -256,10 +272,12 @@ struct CertTableEntry {
   CertArgs a;
   int64_t tile_begin;  // first tile of this problem in the launch
 };
-int make_cert_entry(int64_t m, int64_t n, int64_t k, const void* PA, const void* PB, const unsigned long long* muA,
-                    const unsigned long long* muB, const int* badA, const int* badB, unsigned int* words,
-                    CertTableEntry* e);
-int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int sms, cudaStream_t stream);
+int make_cert_entry(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const void* PB,
+                    const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
+                    const int* sigA, const int* sigB, const int* eminA, const int* eminB, unsigned int* words,
+                    const struct ModPlan* gate, CertTableEntry* e);
+int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int prec, int sms,
+                        cudaStream_t stream);
 
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 // exactness width of the modular integers: t at which every scaled entry is an integer (0: both
@@ -388,7 +406,7 @@ struct ModGrouped {
   std::vector<int> index;                  // the caller's position of each problem
   std::vector<const ModPlan*> plans;       // the device plan of each problem
   std::vector<PrepJob> jobs;               // op(A), op(B)^T of each problem
-  std::vector<CertTableEntry> cert;
+  std::vector<CertTableEntry> cert;        // FP8 certification, then its BF16 retry (count each)
   std::vector<ModPlanJob> planjobs;
   std::vector<ColJob> coljobs;
   std::vector<ModTableEntry> table;        // in launch order (decreasing k)

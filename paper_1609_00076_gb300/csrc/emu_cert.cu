@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
                 int count = 0, int total_tiles = 0) {
   static_assert(!(PAIR && TABLE), "grouped certification runs on one SM per tile");
   using L = CertCfg<PAIR, FP8>;
+  if (!TABLE && p.gate && p.gate->feasible) return;  // the retry of a certification that succeeded
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
@@ -110,6 +111,8 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
     tile_coords(tile - (int)table[cur].tile_begin, q->tiles_m, q->group_m, q->num_tiles, tm, tn);
     return q;
   };
+  // grouped retry: the tiles of a problem whose plan is already feasible are skipped by every role
+  auto skipped = [&](const CertArgs& q) { return TABLE && q.gate && q.gate->feasible; };
 
   if (warp == 0 && lane == 0) {
     if (!TABLE) {
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       for (int tile = unit; tile < num_tiles; tile += units) {
         int tm, tn;
         const CertArgs& q = *tile_args(tile, cur, tm, tn);
+        if (skipped(q)) continue;
         const CUtensorMap* ma = TABLE ? &table[cur].tmA : &tmA;
         const CUtensorMap* mb = TABLE ? &table[cur].tmB : &tmB;
         if (TABLE) {  // maps written into global memory before the launch: acquire them for the TMA unit
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       for (int tile = unit; tile < num_tiles; tile += units) {
         int tm, tn;
         const CertArgs& q = *tile_args(tile, cur, tm, tn);
+        if (skipped(q)) continue;
         for (int i0 = 0; i0 < q.nkb; i0 += q.chunk_blocks, ++chunk) {
           const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
           if (PAIR) mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
@@ -245,42 +250,61 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
       empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
     }
-    // Per element only its lower bound G_ij (no constraint: +inf; an unusable bound: 0); per row its
-    // minimum, per column the minimum over the warp's 32 rows (one redux per column).  Then
-    //   rhoA = max mu_i / min_j G_ij,  rhoB = max nu_j / min_i G_ij,  gamma = 1 / min G_ij,
-    // and max (mu_i + nu_j) / G_ij <= rhoA + rhoB.
-    float rmaxA = 0.0f, rmaxB = 0.0f, gmin = INFINITY;
+    // Per element, with G_ij its lower bound and 1/theta_i, 1/phi_j upper bounds of the reciprocal
+    // of the smallest non-zero scaled entry of row i and column j:
+    //   T1 = min(nu_j / G_ij, 1/theta_i),  T2 = min(mu_i / G_ij, 1/phi_j),
+    //   T3 = min(1 / G_ij, 1 / (k theta_i phi_j)),
+    // every term rounded up (without a usable G_ij only the spread terms remain).  The words hold
+    // rhoA = max T2, rhoB = max T1 and gamma = max T3, so that for every element
+    //   (its error bound) / G_ij <= 2^(-t-1) (rhoA + rhoB + k 2^(-t-1) gamma)     (modular).
+    float rmaxA = 0.0f, rmaxB = 0.0f, gmax = 0.0f;
+    // 1/theta as a power of two from the row's exponent sigma and its smallest one (inf above 2^127)
+    auto inv_spread = [](int sig, int em) -> float {
+      if (em == kEminNone) return 0.0f;  // no non-zero entry: no term
+      const int x = (sig == kExpEmpty ? 0 : sig) + 1 - em;
+      return x > 127 ? INFINITY : __int_as_float((127 + x) << 23);
+    };
     auto certify = [&](const CertArgs& p, int64_t i, int64_t jc0, const float (&acc)[32]) {
       const bool row_ok = i < p.m && p.badA[i] == 0;
-      const int si = (p.L && i < p.m) ? (p.sigA[i] == kExpEmpty ? 0 : p.sigA[i]) : 0;
-      float rowmin = INFINITY, colmin = INFINITY;
+      const int si = (i < p.m) ? p.sigA[i] : 0;
+      const float mui = row_ok ? mu_upper(p.muA[i], p.mu_scale) : 0.0f;
+      const float cth = row_ok ? inv_spread(si, p.eminA[i]) : 0.0f;
+      // this lane's column of the 32: its magnitude sum and spread, handed round by shuffles
+      const int64_t jl = jc0 + lane;
+      const bool col_ok = jl < p.n && p.badB[jl] == 0;
+      const float nu_l = col_ok ? mu_upper(p.muB[jl], p.mu_scale) : 0.0f;
+      const float cph_l = col_ok ? inv_spread(p.sigB[jl], p.eminB[jl]) : 0.0f;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {  // fully unrolled: acc stays in registers
         const int64_t j = jc0 + c;
+        const float nuj = __shfl_sync(0xffffffffu, nu_l, c);
+        const float cph = __shfl_sync(0xffffffffu, cph_l, c);
         const bool ok = row_ok && j < p.n && p.badB[j] == 0;
-        float G = INFINITY;
-        if (ok && acc[c] > 0.0f) G = fmaxf(__fsub_rd(__fmul_rd(acc[c], p.f), p.slack), 0.0f);
-        rowmin = fminf(rowmin, G);
-        // non-negative floats (and +inf) order as their bit patterns
-        const unsigned cm = __reduce_min_sync(0xffffffffu, __float_as_uint(G));
-        if (lane == c) colmin = __uint_as_float(cm);
+        float G = 0.0f;
+        if (ok && acc[c] > 0.0f) {
+          G = __fsub_rd(__fmul_rd(acc[c], p.f), p.slack);
+          float t1 = cth, t2 = cph, t3 = __fmul_ru(__fmul_ru(cth, cph), p.kinv);
+          if (G > 0.0f) {
+            const float inv = __frcp_ru(G);
+            t1 = fminf(t1, __fmul_ru(nuj, inv));
+            t2 = fminf(t2, __fmul_ru(mui, inv));
+            t3 = fminf(t3, inv);
+          }
+          rmaxB = fmaxf(rmaxB, t1);
+          rmaxA = fmaxf(rmaxA, t2);
+          gmax = fmaxf(gmax, t3);
+        }
         if (p.L && i < p.m && j < p.n) {
           double out = 0.0;
           if (!ok) out = __longlong_as_double(0x7FF8000000000000ll);  // a NaN row or column: no bound
-          else if (G < INFINITY && G > 0.0f) out = ldexp((double)G, si + (p.sigB[j] == kExpEmpty ? 0 : p.sigB[j]));
+          else if (G > 0.0f) out = ldexp((double)G, (si == kExpEmpty ? 0 : si) +
+                                                        (p.sigB[j] == kExpEmpty ? 0 : p.sigB[j]));
           p.L[i + j * p.ldl] = out;
         }
       }
-      if (rowmin < INFINITY) {
-        gmin = fminf(gmin, rowmin);
-        rmaxA = fmaxf(rmaxA, rowmin > 0.0f ? __fdiv_ru(mu_upper(p.muA[i], p.mu_scale), rowmin) : INFINITY);
-      }
-      if (colmin < INFINITY)
-        rmaxB = fmaxf(rmaxB, colmin > 0.0f ? __fdiv_ru(mu_upper(p.muB[jc0 + lane], p.mu_scale), colmin) : INFINITY);
     };
     // the maxima into a problem's words (grouped: after every tile, the next may be another's)
-    auto flush = [&](unsigned int* words) {
-      const float gmax = gmin < INFINITY ? (gmin > 0.0f ? __frcp_ru(gmin) : INFINITY) : 0.0f;
+    auto flush = [&](unsigned int* words) {  // non-negative floats (and +inf) order as their bits
       const unsigned ra = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxA));
       const unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rmaxB));
       const unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
@@ -289,14 +313,14 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
         if (rb) atomicMax(words + kCertRhoB, rb);
         if (gb) atomicMax(words + kCertGamma, gb);
       }
-      rmaxA = rmaxB = 0.0f;
-      gmin = INFINITY;
+      rmaxA = rmaxB = gmax = 0.0f;
     };
     uint32_t chunk = 0;
     int cur = 0;
     for (int tile = unit; tile < num_tiles; tile += units) {
       int tm, tn;
       const CertArgs& p = *tile_args(tile, cur, tm, tn);
+      if (skipped(p)) continue;
       const int64_t i = (int64_t)tm * L::BM + (int)rank * 128 + row;
       const int64_t jc0 = (int64_t)tn * L::BN + col0;
       if (p.chunk_blocks >= p.nkb) {
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
       }
       if (TABLE) flush(p.words);
     }
-    if (!TABLE) flush(p.words);  // non-negative floats order as their bit patterns
+    if (!TABLE) flush(p.words);
   }
 
   tc_fence_before();
@@ -423,8 +447,8 @@ int launch_cert_kernel(const CertArgs& a, const CUtensorMap& tmA, const CUtensor
 
 int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const void* PB,
                 const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
-                const int* sigA, const int* sigB, unsigned int* words, double* Lout, int64_t ldl, int sms,
-                cudaStream_t stream) {
+                const int* sigA, const int* sigB, const int* eminA, const int* eminB, unsigned int* words,
+                double* Lout, int64_t ldl, int sms, cudaStream_t stream, const ModPlan* gate) {
   if (m <= 0 || n <= 0 || k <= 0) return GBD_OK;
   const bool fp8 = prec == kCertFP8;
   const int S = plane_scale(k, prec);
@@ -446,6 +470,10 @@ int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const
   a.badB = badB;
   a.sigA = sigA;
   a.sigB = sigB;
+  a.eminA = eminA;
+  a.eminB = eminB;
+  a.kinv = float_up(1.0 / (double)k);
+  a.gate = gate;
   a.words = words;
   a.L = Lout;
   a.ldl = ldl;
@@ -496,45 +524,57 @@ int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const
              : launch_cert_kernel<false, false>(a, tmA, tmB, grid, stream);
 }
 
-int make_cert_entry(int64_t m, int64_t n, int64_t k, const void* PA, const void* PB, const unsigned long long* muA,
-                    const unsigned long long* muB, const int* badA, const int* badB, unsigned int* words,
-                    CertTableEntry* e) {
+int make_cert_entry(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const void* PB,
+                    const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
+                    const int* sigA, const int* sigB, const int* eminA, const int* eminB, unsigned int* words,
+                    const ModPlan* gate, CertTableEntry* e) {
   memset(e, 0, sizeof(*e));
   CertArgs& a = e->a;
-  const int S = plane_scale(k, kCertFP8);
-  const int64_t pitch = plane_pitch(k, kCertFP8);
+  const bool fp8 = prec == kCertFP8;
+  const int S = plane_scale(k, prec);
+  const int64_t pitch = plane_pitch(k, prec);
+  const int kkb = fp8 ? 128 : kBK;  // k elements per k-block
+  const uint64_t eb = fp8 ? 1 : 2;
   a.m = m;
   a.n = n;
-  a.nkb = (int)((k + 127) / 128);
-  a.chunk_blocks = kCertChunkBlocks * kBK / 128;  // 16384 deep, as the one-SM form of single calls
-  const int64_t chunk_k = (int64_t)a.chunk_blocks * 128 < k ? (int64_t)a.chunk_blocks * 128 : k;
+  a.nkb = (int)((k + kkb - 1) / kkb);
+  a.chunk_blocks = kCertChunkBlocks * kBK / kkb;  // 16384 deep, as the one-SM form of single calls
+  const int64_t chunk_k = (int64_t)a.chunk_blocks * kkb < k ? (int64_t)a.chunk_blocks * kkb : k;
   a.f = float_down(std::ldexp(1.0 - (double)chunk_k * std::ldexp(1.0, -19), -2 * S));
-  const double w = std::ldexp(1.0, -14 - S);
+  const double w = std::ldexp(1.0, (fp8 ? -14 : -63) - S);
   a.slack = float_up((double)k * (2.0 * w + w * w) * (1.0 + std::ldexp(1.0, -40)));
   a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + (double)((k + 1023) / 1024) * std::ldexp(1.0, -22));
   a.muA = muA;
   a.muB = muB;
   a.badA = badA;
   a.badB = badB;
+  a.sigA = sigA;
+  a.sigB = sigB;
+  a.eminA = eminA;
+  a.eminB = eminB;
+  a.kinv = float_up(1.0 / (double)k);
+  a.gate = gate;
   a.words = words;
   a.err = device_error_word();
   a.tiles_m = (int)((m + 127) / 128);
   a.num_tiles = a.tiles_m * (int)((n + 127) / 128);
   a.group_m = a.tiles_m;  // within one problem the tiles walk down the rows
+  const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint64_t dA[3] = {(uint64_t)k, (uint64_t)m, 1u};
-  const uint64_t pA[2] = {(uint64_t)pitch, (uint64_t)m * pitch};
-  const uint32_t box[3] = {128u, 128u, 1u};
-  int rc = encode_tmap(&e->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, PA, dA, pA, box, CU_TENSOR_MAP_SWIZZLE_128B);
+  const uint64_t pA[2] = {(uint64_t)pitch * eb, (uint64_t)m * pitch * eb};
+  const uint32_t box[3] = {(uint32_t)kkb, 128u, 1u};
+  int rc = encode_tmap(&e->tmA, dt, 3, PA, dA, pA, box, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
   const uint64_t dB[3] = {(uint64_t)k, (uint64_t)n, 1u};
-  const uint64_t pB[2] = {(uint64_t)pitch, (uint64_t)n * pitch};
-  return encode_tmap(&e->tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, PB, dB, pB, box, CU_TENSOR_MAP_SWIZZLE_128B);
+  const uint64_t pB[2] = {(uint64_t)pitch * eb, (uint64_t)n * pitch * eb};
+  return encode_tmap(&e->tmB, dt, 3, PB, dB, pB, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int sms, cudaStream_t stream) {
+int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int prec, int sms,
+                        cudaStream_t stream) {
   if (count <= 0 || total_tiles <= 0) return GBD_OK;
-  using L = CertCfg<false, true>;
-  auto kern = k_cert_gemm<false, true, true>;
+  using L = CertCfg<false, true>;  // the same shared memory and threads in both precisions
+  auto kern = prec == kCertFP8 ? k_cert_gemm<false, true, true> : k_cert_gemm<false, false, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped certification)");
   CertArgs dummy_args;
@@ -584,19 +624,20 @@ int gbd_abs_product_lower_bound(char transa, char transb, int64_t m, int64_t n, 
   PrepJob& ja = pp.j[0];
   PrepJob& jb = pp.j[1];
   ja.X = A; ja.ld = lda; ja.R = m; ja.K = k; ja.rows_contig = trans_code(transa) == 0;
-  ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp;
+  ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp; ja.emin = ws.eminA;
   jb.X = B; jb.ld = ldb; jb.R = n; jb.K = k; jb.rows_contig = trans_code(transb) != 0;
-  jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp;
+  jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp; jb.emin = ws.eminB;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) return rc;
   if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
   cudaError_t e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s);
   if (e != cudaSuccess) return cuda_fail(e, "abs_product_lower_bound: clearing the certification words");
   const int prec = fp8 ? kCertFP8 : kCertBF16;
   if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
-  return launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert, L, ldl,
-                     sms, s);
+  return launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
+                     ws.eminB, ws.cert, L, ldl, sms, s);
 }
 
 }  // extern "C"

@@ -833,10 +833,16 @@ __host__ __device__ int moduli_for_products(int t, int64_t k, const ModProducts&
 // target on every element, or the exactness width); then n.  When no n <= kMaxModuli suffices
 // the plan is marked infeasible (n = 1, t = 1: the kernels then write NaN) and, for the
 // device-side automatic mode (`flag`), the device error word records it.
+// retry: the second plan, from the BF16 certification's words, only when the first was infeasible
 __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict__ cert, int64_t k, double tol,
                                                   int fixed_t, const __grid_constant__ ModProducts mp,
-                                                  ModPlan* __restrict__ plan, unsigned int* err, int flag) {
+                                                  ModPlan* __restrict__ plan, unsigned int* err, int flag,
+                                                  int retry) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (retry) {
+    if (plan->feasible) return;
+    cert += kCertRetry;
+  }
   double rho = 0.0, gamma = 0.0, bound = 0.0;
   int t = fixed_t, exact = 0;
   if (fixed_t <= 0) {
@@ -861,15 +867,17 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
 // the plans of a grouped launch, one thread per problem (as k_mod_plan; an infeasible plan needs no
 // error bit: the grouped FP64 kernel computes that problem)
 __global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __restrict__ jobs, int count,
-                                                          const __grid_constant__ ModProducts mp) {
+                                                          const __grid_constant__ ModProducts mp, int retry) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const ModPlanJob j = jobs[q];
+  if (retry && j.plan->feasible) return;
+  const unsigned int* words = retry ? j.words + kCertRetry : j.words;
   double rho = 0.0, gamma = 0.0, bound = 0.0;
   int t = j.fixed_t, exact = 0;
   if (t <= 0) {
-    cert_rho_gamma(j.words, &rho, &gamma);
-    t = cert_mod_bits(rho, gamma, (int)j.words[kCertTexA], (int)j.words[kCertTexB], j.k, j.tol, &bound, &exact);
+    cert_rho_gamma(words, &rho, &gamma);
+    t = cert_mod_bits(rho, gamma, (int)words[kCertTexA], (int)words[kCertTexB], j.k, j.tol, &bound, &exact);
   }
   const int n = t <= 62 ? moduli_for_products(t, j.k, mp) : 0;
   ModPlan pl;
@@ -907,6 +915,8 @@ struct ModWorkspace {
   float* stats;
   ModPlan* plan;
   unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
+  int* eminA;          // [m] smallest exponent of each row's non-zero entries, then eminB [n]
+  int* eminB;
   ExpMagParts parts;  // automatic mode: per row and k-block exponents, flags and magnitude sums
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
@@ -939,6 +949,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_plan = off; off = up(off + sizeof(ModPlan));
   const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
+  const size_t o_emin = off; off = up(off + sizeof(int) * (size_t)(m + n));
   const int64_t nkr = (k + 1023) / 1024;  // k-blocks of the exponent and magnitude pass
   size_t o_part[2][3];
   for (int side = 0; side < 2; ++side)
@@ -964,6 +975,8 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->plan = reinterpret_cast<ModPlan*>(b + o_plan);
     ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
+    ws->eminA = reinterpret_cast<int*>(b + o_emin);
+    ws->eminB = ws->eminA + m;
     for (int side = 0; side < 2; ++side) {
       ws->parts.e[side] = reinterpret_cast<int*>(b + o_part[side][0]);
       ws->parts.s[side] = reinterpret_cast<float*>(b + o_part[side][1]);
@@ -1231,27 +1244,41 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = automatic ? ws.muA : nullptr; ja.D = ws.DA; ja.kp = ws.kp;
   jb.X = B; jb.ld = ldb; jb.R = n; jb.K = k; jb.rows_contig = tb != 0;
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = automatic ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
+  ja.emin = automatic ? ws.eminA : nullptr;
+  jb.emin = automatic ? ws.eminB : nullptr;
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
+  const int prec = cert_prec_default();
   if (automatic) {  // exponents and magnitude sums in one pass over the operands
     if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
     // the certification: magnitude planes (in the residue planes' place, which are written
     // after the plan) and their product with the reduction of the bound's ratios
-    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu_mod: clearing the certification words");
-    const int prec = cert_prec_default();
     if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
-    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.cert,
-                          nullptr, 0, sms, s)))
+    if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
+                          ws.eminB, ws.cert, nullptr, 0, sms, s)))
       return rc;
   } else if ((rc = launch_exponents_pair(pp, exp_blocks, nullptr, 0, s))) {
     return rc;
   }
-  // the plan: t and n, on the device
+  // the plan: t and n, on the device; after FP8 planes, a plan that finds no feasible t is made
+  // again from a BF16 certification (its kernels return at once when the first plan is feasible)
   const double target = tol > 0.0 ? tol : 2.0 * (double)k * kUnitRoundoff;
+  const bool retry = automatic && prec == kCertFP8;
   k_mod_plan<<<1, 32, 0, s>>>(ws.cert, k, target, automatic ? 0 : bits, prods, ws.plan, device_error_word(),
-                              bits == -1 ? 1 : 0);
+                              (bits == -1 && !retry) ? 1 : 0, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan launch");
+  if (retry) {
+    if ((rc = launch_magplane_pair(pp, kCertBF16, ws.cert + kCertRetry + kCertTexA, split_blocks, s, ws.plan)))
+      return rc;
+    if ((rc = launch_cert(m, n, k, kCertBF16, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB,
+                          ws.eminA, ws.eminB, ws.cert + kCertRetry, nullptr, 0, sms, s, ws.plan)))
+      return rc;
+    k_mod_plan<<<1, 32, 0, s>>>(ws.cert, k, target, 0, prods, ws.plan, device_error_word(), bits == -1 ? 1 : 0, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan launch");
+  }
   ModPlan host_plan;
   memset(&host_plan, 0, sizeof(host_plan));
   if (bits == 0) {  // read the plan back: an unreachable target is refused before C is touched
@@ -1335,7 +1362,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   }
   const int ctas = (int)(tiles < kGroupedModCtas ? (tiles > 0 ? tiles : 1) : kGroupedModCtas);
   const size_t o_jobs = off; off = up256(off + sizeof(PrepJob) * 2 * (size_t)count);
-  const size_t o_cert = off; off = up256(off + sizeof(CertTableEntry) * (size_t)count);
+  const size_t o_cert = off; off = up256(off + sizeof(CertTableEntry) * 2 * (size_t)count);  // FP8, BF16 retry
   const size_t o_plj = off; off = up256(off + sizeof(ModPlanJob) * (size_t)count);
   const size_t o_col = off; off = up256(off + sizeof(ColJob) * (size_t)count);
   const size_t o_tab = off; off = up256(off + sizeof(ModTableEntry) * (size_t)count);
@@ -1371,7 +1398,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   g->scr = reinterpret_cast<uint8_t*>(b + o_scr);
   g->scr_ctas = ctas;
   g->jobs.assign(2 * (size_t)count, PrepJob{});
-  g->cert.assign(count, CertTableEntry{});
+  g->cert.assign(2 * (size_t)count, CertTableEntry{});
   g->planjobs.assign(count, ModPlanJob{});
   g->coljobs.assign(count, ColJob{});
   g->plans.assign(count, nullptr);
@@ -1389,15 +1416,21 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
     ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
     ja.sig = w.sigA; ja.bad = w.badA; ja.mu = w.muA; ja.D = w.DA; ja.kp = w.kp;
-    ja.tex = words + kCertTexA; ja.plan = w.plan;
+    ja.tex = words + kCertTexA; ja.plan = w.plan; ja.emin = w.eminA;
     jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
     jb.sig = w.sigB; jb.bad = w.badB; jb.mu = w.muB; jb.D = w.DB; jb.kp = w.kp;
-    jb.tex = words + kCertTexB; jb.plan = w.plan;
+    jb.tex = words + kCertTexB; jb.plan = w.plan; jb.emin = w.eminB;
     prep_job_blocks(ja, g->exp_blocks, g->split_blocks);
     prep_job_blocks(jb, g->exp_blocks, g->split_blocks);
     CertTableEntry& ce = g->cert[q];
-    if ((*rc = make_cert_entry(p.m, p.n, p.k, w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, words, &ce))) return off;
-    ce.tile_begin = cert_tiles;
+    if ((*rc = make_cert_entry(p.m, p.n, p.k, kCertFP8, w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, w.sigA, w.sigB,
+                               w.eminA, w.eminB, words, nullptr, &ce)))
+      return off;
+    CertTableEntry& cr = g->cert[count + q];  // the BF16 retry, for a plan that found no feasible t
+    if ((*rc = make_cert_entry(p.m, p.n, p.k, kCertBF16, w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, w.sigA, w.sigB,
+                               w.eminA, w.eminB, words + kCertRetry, w.plan, &cr)))
+      return off;
+    ce.tile_begin = cr.tile_begin = cert_tiles;
     cert_tiles += ce.a.num_tiles;
     ModPlanJob& pj = g->planjobs[q];
     pj.words = words;
@@ -1482,11 +1515,21 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   // exponents, flags and magnitude sums of every side (the sums zeroed by the first launch)
   if ((rc = launch_prep_batched(g.jobs_dev, njobs, g.exp_blocks, 0, true, false, s))) return rc;
   if ((rc = launch_magnitudes_batched(g.jobs_dev, njobs, g.exp_blocks, s))) return rc;
-  // the certification: FP8 magnitude planes, their products, the plans
-  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s))) return rc;
-  if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, sms, s))) return rc;
-  k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, moduli_products());
+  // the certification: magnitude planes, their products, the plans (the same precision as the
+  // single call's, so that a problem gets the same plan alone and in a batch)
+  const int prec = cert_prec_default();
+  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec, false))) return rc;
+  if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, prec, sms, s))) return rc;
+  const ModProducts prods = moduli_products();
+  k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped plan launch");
+  if (prec == kCertFP8) {
+    // the BF16 retry of every problem whose plan found no feasible t (the others return at once)
+    if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, kCertBF16, true))) return rc;
+    if ((rc = launch_cert_grouped(g.cert_dev + g.count, g.count, g.cert_tiles, kCertBF16, sms, s))) return rc;
+    k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped plan launch");
+  }
   // residues and column scales with each problem's plan
   ModSplit ms;
   mod_split_params(ms);

@@ -374,13 +374,14 @@ struct MagWriter {
   void* D;
   int64_t kp;
   unsigned int* tex;  // the side's exactness width (atomic maximum)
+  int* emin;          // per row: the smallest frexp exponent of a non-zero entry (atomic minimum)
   __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
                                              int64_t pbase) const {
     constexpr int kMant = FP8 ? 2 : 7;     // stored fraction bits
     constexpr int kBias = FP8 ? 15 : 127;  // exponent bias
     constexpr int kFloor = FP8 ? -14 : -63;  // exponent of the floor in plane units
     uint32_t h[kPerThread];
-    int w = 0;
+    int w = 0, em = kEminNone;
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
       const uint64_t b = x[v];
@@ -407,7 +408,9 @@ struct MagWriter {
         h[v] = ((uint32_t)(eb + kBias) << kMant) | mf;
       }
       w = max(w, min(255, sg - (e2 + __ffsll((long long)mant) - 1)));
+      em = min(em, nb + e2);  // the frexp exponent of x
     }
+    if (emin && em < __ldcg(emin + r)) atomicMin(emin + r, em);
     const bool full = pbase + kPerThread <= K;
     if (FP8) {
       uint8_t* row = static_cast<uint8_t*>(D) + r * kp + pbase;
@@ -496,6 +499,7 @@ __global__ void __launch_bounds__(256) k_prep_init_batched(const PrepJob* __rest
     j.sig[r] = kExpEmpty;
     j.bad[r] = 0;
     if (j.mu) j.mu[r] = 0ull;
+    if (j.emin) j.emin[r] = kEminNone;
   }
 }
 
@@ -542,13 +546,24 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
 }
 
 // grouped modular problems: magnitude planes (FP8) and residues over a job table
+// FP8 planes (the certification), or BF16 planes for its retry: then only the jobs whose problem's
+// plan found no feasible precision, with the widths into the retry's words
+template <bool FP8, bool RETRY>
 __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const PrepJob* __restrict__ jobs, int njobs) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   const int ji = find_job(jobs, njobs, blockIdx.x, true);
   const PrepJob& j = jobs[ji];
+  if (RETRY && j.plan->feasible) return;
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  const MagWriter<true> w{15, j.R, j.K, j.D, (j.K + 15) / 16 * 16, j.tex};  // the FP8 plane scale and pitch
+  int S = 15;  // the E5M2 plane scale; BF16: the largest with K 2^(2S) < 2^124
+  if (!FP8) {
+    int kb = 0;
+    while (((int64_t)1 << kb) < j.K) ++kb;
+    S = (124 - kb) / 2;
+  }
+  const int64_t pitch = FP8 ? (j.K + 15) / 16 * 16 : (j.K + 7) / 8 * 8;
+  const MagWriter<FP8> w{S, j.R, j.K, j.D, pitch, RETRY ? j.tex + kCertRetry : j.tex, j.emin};
   if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
@@ -817,13 +832,14 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_pair(const __grid_
 // side j's width to tex[j]
 template <bool FP8>
 __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_pair(const __grid_constant__ PrepPair pp, int S,
-                                                                 int64_t kp, unsigned int* tex) {
+                                                                 int64_t kp, unsigned int* tex, const ModPlan* gate) {
   __shared__ uint64_t tile[kTile][kTile + 1];
+  if (gate && gate->feasible) return;  // the retry of a certification that already succeeded
   const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  const MagWriter<FP8> w{S, j.R, j.K, j.D, kp, tex + ji};
+  const MagWriter<FP8> w{S, j.R, j.K, j.D, kp, tex + ji, j.emin};
   if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
   else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
@@ -859,6 +875,7 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
+  const size_t o_emin = off; off = up(off + sizeof(int) * (size_t)(m + n));
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
   // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile)
@@ -889,6 +906,8 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
     ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
+    ws->eminA = reinterpret_cast<int*>(b + o_emin);
+    ws->eminB = ws->eminA + m;
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);
@@ -940,10 +959,18 @@ int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, 
   return GBD_OK;
 }
 
-int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s) {
+int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s, int prec,
+                            bool retry) {
   if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
-  k_magplane_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+  const unsigned g = (unsigned)split_blocks;
+  if (prec == kCertFP8) {
+    if (retry) k_magplane_batched<true, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    else k_magplane_batched<true, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+  } else {
+    if (retry) k_magplane_batched<false, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    else k_magplane_batched<false, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+  }
   return launch_check("batched magnitude plane launch");
 }
 
@@ -1029,12 +1056,16 @@ int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s) 
   return launch_check("split launch");
 }
 
-int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s) {
+int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_t split_blocks, cudaStream_t s,
+                         const ModPlan* gate) {
   if (split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
   const int64_t K = pp.j[0].K;
-  if (prec == kCertFP8) k_magplane_pair<true><<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex);
-  else k_magplane_pair<false><<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex);
+  const unsigned g = (unsigned)split_blocks;
+  if (prec == kCertFP8)
+    k_magplane_pair<true><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate);
+  else
+    k_magplane_pair<false><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate);
   return launch_check("magnitude plane launch");
 }
 

@@ -317,9 +317,9 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     memset(&jb, 0, sizeof(jb));
     // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
     ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
-    ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp;
+    ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp; ja.emin = ws.eminA;
     jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
-    jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp;
+    jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp; jb.emin = ws.eminB;
     emu::prep_job_blocks(ja, plan->exp_blocks, plan->split_blocks);
     emu::prep_job_blocks(jb, plan->exp_blocks, plan->split_blocks);
   }
@@ -349,26 +349,59 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       unsigned int* w = words + emu::kCertWords * q;
       if ((rc = emu::launch_magplane_pair(pp, prec, w + emu::kCertTexA, sb, s))) return rc;
       if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, prec, em.ws.DA, em.ws.DB, em.ws.muA, em.ws.muB,
-                                 em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, w, nullptr, 0, sms, s)))
+                                 em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, em.ws.eminA, em.ws.eminB, w,
+                                 nullptr, 0, sms, s)))
         return rc;
     }
     std::vector<unsigned int> cw(emu::kCertWords * plan->emu.size(), 0u);
-    if ((e = cudaMemcpyAsync(cw.data(), words, sizeof(unsigned int) * cw.size(), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_fail(e, "grouped: reading the certification");
+    auto read_words = [&]() -> int {
+      if ((e = cudaMemcpyAsync(cw.data(), words, sizeof(unsigned int) * cw.size(), cudaMemcpyDeviceToHost, s)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "grouped: reading the certification");
+      return GBD_OK;
+    };
+    if ((rc = read_words())) return rc;
+    // the slice count of problem q from its words of set `off` (0: the first certification, kCertRetry)
+    auto slices_of = [&](size_t q, int off) {
+      const auto& em = plan->emu[q];
+      const unsigned int* w = &cw[emu::kCertWords * q + off];
+      double rho, gamma;
+      emu::cert_rho_gamma(w, &rho, &gamma);
+      const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * emu::kUnitRoundoff;
+      return emu::cert_split_slices(rho, gamma, (int)w[emu::kCertTexA], (int)w[emu::kCertTexB], em.p.k, target,
+                                    nullptr, nullptr);
+    };
+    // the FP8 planes' looser bound: the problems it leaves without a slice count, certified again
+    // with BF16 planes
+    if (prec == emu::kCertFP8) {
+      bool again = false;
+      for (size_t q = 0; q < plan->emu.size(); ++q) {
+        const auto& em = plan->emu[q];
+        if (em.slices != 0 || slices_of(q, 0) <= emu::kMaxSlices) continue;
+        emu::PrepPair pp;
+        pp.j[0] = plan->jobs[2 * q];
+        pp.j[1] = plan->jobs[2 * q + 1];
+        int64_t eb = 0, sb = 0;
+        emu::prep_pair_blocks(pp, eb, sb);
+        unsigned int* w = words + emu::kCertWords * q + emu::kCertRetry;
+        if ((rc = emu::launch_magplane_pair(pp, emu::kCertBF16, w + emu::kCertTexA, sb, s))) return rc;
+        if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, emu::kCertBF16, em.ws.DA, em.ws.DB, em.ws.muA, em.ws.muB,
+                                   em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, em.ws.eminA, em.ws.eminB, w,
+                                   nullptr, 0, sms, s)))
+          return rc;
+        again = true;
+      }
+      if (again && (rc = read_words())) return rc;
+    }
     // problems whose target no slice count can certify move to the FP64 path
     std::vector<gbd_plan::Emu> kept;
     std::vector<emu::PrepJob> kept_jobs;
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       auto em = plan->emu[q];
       if (em.slices == 0) {
-        const unsigned int* w = &cw[emu::kCertWords * q];
-        double rho, gamma;
-        emu::cert_rho_gamma(w, &rho, &gamma);
-        const double target = em.p.tol > 0.0 ? em.p.tol : 2.0 * (double)em.p.k * emu::kUnitRoundoff;
-        em.slices = emu::cert_split_slices(rho, gamma, (int)w[emu::kCertTexA], (int)w[emu::kCertTexB], em.p.k, target,
-                                           nullptr, nullptr);
+        em.slices = slices_of(q, 0);
+        if (em.slices > emu::kMaxSlices && prec == emu::kCertFP8) em.slices = slices_of(q, emu::kCertRetry);
       }
       if (em.slices > emu::kMaxSlices) {
         plan->native.push_back(native_entry(em.p, false));
@@ -390,8 +423,10 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   for (size_t q = 0; q < plan->emu.size(); ++q) {
     plan->jobs[2 * q].slices = plan->emu[q].slices;
     plan->jobs[2 * q + 1].slices = plan->emu[q].slices;
-    plan->jobs[2 * q].mu = nullptr;  // runs need no magnitude sums
+    plan->jobs[2 * q].mu = nullptr;  // runs need no magnitude sums or spreads
     plan->jobs[2 * q + 1].mu = nullptr;
+    plan->jobs[2 * q].emin = nullptr;
+    plan->jobs[2 * q + 1].emin = nullptr;
   }
   // emulated table: tensor maps and tile counts.  Problems of the same kernel (two-SM for the large
   // ones) and slice count are contiguous (one launch each, most slices first), and the longest

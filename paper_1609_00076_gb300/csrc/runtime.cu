@@ -47,6 +47,33 @@ __global__ void k_watchdog_selftest(unsigned int* err, unsigned long long limit_
   }
 }
 
+// The FP64 tensor-core rate: every warp runs `iters` rounds of eight independent
+// mma.sync.m16n8k16.f64 on register fragments (4096 flops each); the sums keep the
+// results live.
+__device__ double g_probe_sink;  // written only to keep the probe's products live
+
+__global__ void __launch_bounds__(256) k_fp64_mma_probe(int64_t iters) {
+  double a[8], b[4], d[8][4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = 1.0 + 1e-3 * (threadIdx.x + q);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) b[q] = 1.0 - 1e-3 * (threadIdx.x + q);
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[r][q] = 0.0;
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) dmma_16x8x16(d[r], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += d[r][q];
+  if (s == 1234.5) g_probe_sink = s;  // practically never: only keeps the products alive
+}
+
 __global__ void k_scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc) {
   const int64_t total = m * n;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -247,6 +274,33 @@ extern "C" {
 int gbd_version(void) { return 100; }  // 0.1.0
 
 const char* gbd_last_error(void) { return gbd::g_msg; }
+
+int gbd_fp64_mma_probe(int64_t iters, double* tflops, void* stream) {
+  using namespace gbd;
+  if (iters < 1 || !tflops) return set_error(GBD_ERR_ARG, "fp64_mma_probe: iters >= 1 and a result pointer");
+  int sms = 0;
+  int rc = current_device(nullptr, &sms);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+    return cuda_fail(e, "fp64_mma_probe: cudaEventCreate");
+  const int blocks = 4 * sms, threads = 256;
+  k_fp64_mma_probe<<<blocks, threads, 0, s>>>(iters / 8 + 1);  // warm-up
+  cudaEventRecord(e0, s);
+  k_fp64_mma_probe<<<blocks, threads, 0, s>>>(iters);
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64_mma_probe: timing");
+  const double flops = 4096.0 * 8.0 * (double)iters * (double)(blocks * threads / 32);
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return GBD_OK;
+}
 
 int gbd_watchdog_selftest(int limit_ms, void* stream) {
   if (limit_ms < 1 || limit_ms > 10000) return gbd::set_error(GBD_ERR_ARG, "watchdog: limit_ms must be in 1..10000");

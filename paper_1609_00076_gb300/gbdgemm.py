@@ -136,6 +136,7 @@ _EXTRA_DECLS: list = [
     ("gbd_dgemm_emu_host", [_c, _c, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _i, _d, _vp, _sz,
                             ctypes.POINTER(GbdEmuInfo), _vp], _i),
     ("gbd_watchdog_selftest", [_i, _vp], _i),
+    ("gbd_fp64_mma_probe", [_i64, ctypes.POINTER(_d), _vp], _i),
     ("gbd_create", [ctypes.POINTER(_vp), _i], _i),
     ("gbd_destroy", [_vp], None),
     ("gbd_workspace_size", [_vp, _i, _i64, _i64, _i64, ctypes.POINTER(_sz)], _i),
@@ -428,6 +429,13 @@ def gbd_sync_error(ctx, stream=None) -> int:
 
 def gbd_ctx_pool_bytes(ctx) -> int:
     return int(load().gbd_ctx_pool_bytes(ctx))
+
+
+def gbd_fp64_mma_probe(iters: int = 20000, stream=None):
+    """Returns (status, measured FP64 tensor-core TFLOP/s)."""
+    out = _d(0.0)
+    rc = load().gbd_fp64_mma_probe(int(iters), ctypes.byref(out), _stream(stream))
+    return rc, float(out.value)
 
 
 def gbd_watchdog_selftest(limit_ms: int, stream=None) -> int:

@@ -13,6 +13,10 @@ FP64 or emulated with a target relative error) arrive over time.  The loop:
 4. polls the batches' completion events, frees finished requests' memory and
    records each request's latency from arrival to observed completion.
 
+Emulated requests are modular problems of the grouped plan: their precision is
+certified and planned on the device inside the batch, so forming and launching a
+batch never waits for the GPU.
+
 Every GEMM step runs in the CUDA library; this module only schedules.  A
 request's result does not depend on the batch it lands in: the grouped kernels
 compute every problem exactly as the single-problem calls do.
@@ -32,7 +36,9 @@ import numpy as np
 from . import gbdgemm, synth
 
 NATIVE = gbdgemm.GBD_MODE_NATIVE
-EMULATED = gbdgemm.GBD_MODE_EMULATED
+# emulated requests run as modular problems: certified and planned on the device, so that making a
+# batch's plan never waits for the stream
+EMULATED = gbdgemm.GBD_MODE_MODULAR
 
 
 @dataclass
@@ -150,7 +156,7 @@ class Server:
         rb, cb = (r.n, r.k) if r.transb == "T" else (r.k, r.n)
         b = 8 * (ra * ca + rb * cb + r.m * r.n)
         if r.mode == EMULATED:
-            b += gbdgemm.gbd_dgemm_emu_workspace_size(r.m, r.n, r.k, 0)
+            b += gbdgemm.gbd_dgemm_emu_mod_workspace_size(r.m, r.n, r.k, 0)
         return b + 1024
 
     def _admit(self, r: Request, now: float) -> None:
@@ -280,8 +286,9 @@ def serving_benchmark(count: int = 2000, fractions=(0.5, 0.8, 0.95), seed: int =
         d = rep.as_dict()
         d.update({"fraction_of_saturation": f, "rate_per_s": rate})
         out["rates"].append(d)
-    out["config"] = {"requests_per_rate": count, "mix": "90% m,n,k log-uniform [32,2048], 10% 4096^3; "
-                     "50/50 native FP64 / emulated with target 1e-14; random transposes", "budget_gb": budget_gb,
+    out["config"] = {"requests_per_rate": count, "saturation_requests": sat_n,
+                     "mix": "90% m,n,k log-uniform [32,2048], 10% 4096^3; 50/50 native FP64 / emulated (modular, "
+                     "certified on the device) with target 1e-14; random transposes", "budget_gb": budget_gb,
                      "slots": slots}
     return out
 

@@ -1,9 +1,11 @@
 """The continuous-batching request loop (paper_1609_00076_gb300.serving).
 
 Checks: every request completes; each result is the same bits alone (single
-native or emulated call, the emulated one choosing its slices itself from the
-same target) as in the mix; results are within the FP64 bound of the oracle
-(sampled); the HBM budget is respected while requests wait for admission.
+native call, or the single modular call choosing its bits on the device from the
+same target) as in the mix, for small requests and for 4096^3 ones (which the
+single call runs on the CTA-pair kernels and the batch on the one-SM kernels);
+results are within the bound of the oracle (sampled); the HBM budget is respected
+while requests wait for admission.
 """
 from __future__ import annotations
 
@@ -20,13 +22,11 @@ def _alone(r):
     import torch
     dC = torch.zeros(r.m * r.n, dtype=torch.float64, device="cuda")
     if r.mode == serving.EMULATED:
-        wsb = gbdgemm.gbd_dgemm_emu_workspace_size(r.m, r.n, r.k, 0)
+        wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(r.m, r.n, r.k, -1)
         ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
-        info = gbdgemm.GbdEmuInfo()
-        rc = gbdgemm.gbd_dgemm_emu(r.transa, r.transb, r.m, r.n, r.k, r.alpha, r.A, r.lda, r.B, r.ldb, r.beta, dC,
-                                   r.ldc, 0, r.tol, ws, wsb, info)
+        rc = gbdgemm.gbd_dgemm_emu_mod(r.transa, r.transb, r.m, r.n, r.k, r.alpha, r.A, r.lda, r.B, r.ldb, r.beta,
+                                       dC, r.ldc, -1, r.tol, ws, wsb)
         assert rc == 0, gbdgemm.gbd_last_error()
-        assert info.slices == r.slices
     else:
         rc = gbdgemm.gbd_dgemm(r.transa, r.transb, r.m, r.n, r.k, r.alpha, r.A, r.lda, r.B, r.ldb, r.beta, dC, r.ldc)
         assert rc == 0, gbdgemm.gbd_last_error()
@@ -36,7 +36,12 @@ def _alone(r):
 
 def test_mixed_stream_same_alone_and_in_the_mix(oracle_mod):
     reqs = serving.request_stream(7, 80, rate=2000.0, big_fraction=0.0, lo=32, hi=384)
-    srv = serving.Server(budget_bytes=2e9, slots=3, max_batch=16, keep_results=True)
+    # and two 4096^3 requests among them, one of each kind
+    for i, mode in enumerate((serving.NATIVE, serving.EMULATED)):
+        reqs.append(serving.Request(rid=80 + i, arrival=reqs[20 + 10 * i].arrival, m=4096, n=4096, k=4096,
+                                    transa="N", transb="T", mode=mode, tol=1e-14 if mode == serving.EMULATED else 0.0,
+                                    seed=777 + i))
+    srv = serving.Server(budget_bytes=4e9, slots=3, max_batch=16, keep_results=True)
     rep = srv.run(reqs)
     assert rep.requests == len(reqs)
     assert rep.p99_ms >= rep.p50_ms > 0
