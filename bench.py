@@ -529,14 +529,55 @@ def split_measure(dev, stream, A, B, C, ws, wsb, steps: int, warmup: int):
             "steps": steps}
 
 
+def calls_only(dev, stream, which: str, steps: int, warmup: int, seed: int = 2000):
+    """The headline's modular calls (bits chosen on the device) or the split calls (automatic
+    slices) alone, on the headline's inputs at the current size: `warmup` calls, then `steps`
+    calls timed with events (for profiling runs: nothing else launches)."""
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm
+    A_h, B_h = host_inputs(seed)
+    A = torch.from_numpy(A_h).to(dev)
+    B = torch.from_numpy(B_h).to(dev)
+    C = torch.zeros(M * N, dtype=torch.float64, device=dev)
+    if which == "split":
+        wsb = gbdgemm.gbd_dgemm_emu_workspace_size(M, N, K, 0)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize()
+        res = split_measure(dev, stream, A, B, C, ws, wsb, steps=steps, warmup=warmup)
+        res["path"] = "split"
+        return res
+    wsb = gbdgemm.gbd_dgemm_emu_mod_workspace_size(M, N, K, -1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    def call():
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod("N", "N", M, N, K, 1.0, A, M, B, K, 0.0, C, M, -1, 0.0, ws, wsb,
+                                                None, stream=stream))
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            call()
+    torch.cuda.synchronize()
+    ev = _events(steps + 1)
+    ev[0].record(stream)
+    for i in range(steps):
+        call()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+    ms = ev[0].elapsed_time(ev[-1]) / steps
+    return {"path": "modular", "size": M, "ms": ms, "value": 2.0 * M * N * K / (ms / 1000.0) / 1e12,
+            "steps": steps, "warmup": warmup}
+
+
 def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
     """Device time of the GEMM-based DSYRK, DTRMM and DTRSM (side L, lower, N, non-unit) at n,
     native and emulated (each product at its FP64 bound): DSYRK on uniform[-1,1) A (the GEMM's
     inputs), the triangular operations on the well-conditioned A/n + 1.5 I; emulated DSYRK also
     on that diagonally dominant A ("dsyrk_dominant"): the off-diagonal entries of A A^T whose two
-    small factors next to the 1.5 are themselves small need more than 16 moduli and more than 9
-    slices at the FP64 bound (the row scale is set by the 1.5), so every block product of that call
-    is certified onto the FP64 path and the leg runs at the native rate."""
+    small factors next to the 1.5 are themselves small need many more integer bits at the FP64
+    bound (the row scale is set by the 1.5; more than 9 slices of the split emulation); the rows'
+    small square sums keep the moduli that many bits need within 16."""
     import numpy as np
     import torch
 
@@ -806,8 +847,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["grouped", "serving", "level3", "cpu"],
-                    help="run only the grouped-batch, serving, level-3 or host five-loop measurement and print it")
+    ap.add_argument("--only", choices=["grouped", "serving", "level3", "cpu", "modular", "split"],
+                    help="run only the grouped-batch, serving, level-3 or host five-loop measurement, or only the "
+                         "modular or split emulated calls at --size (profiling runs), and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the grouped-batch and serving measurements (profiling runs)")
     ap.add_argument("--size", type=int, default=8192,
@@ -827,7 +869,9 @@ def main():
         gbdgemm.load()
         dev = torch.device("cuda", 0)
         stream = torch.cuda.Stream(device=dev)
-        if args.only == "grouped":
+        if args.only in ("modular", "split"):
+            res = calls_only(dev, stream, args.only, args.steps, args.warmup)
+        elif args.only == "grouped":
             res = grouped_measure(dev, stream, reps=1)
         elif args.only == "level3":
             res = level3_measure(dev, stream, n=args.size)

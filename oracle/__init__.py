@@ -48,7 +48,7 @@ class CertChoice(ctypes.Structure):
     _fields_ = [("t_cert", ctypes.c_int), ("t_exact", ctypes.c_int), ("t", ctypes.c_int),
                 ("moduli", ctypes.c_int), ("s_cert", ctypes.c_int), ("s_exact", ctypes.c_int),
                 ("s", ctypes.c_int), ("pad", ctypes.c_int), ("rho", ctypes.c_double),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("alpha2", ctypes.c_double), ("beta2", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -104,6 +104,8 @@ def _load():
     lib.oracle_certify.restype = i
     lib.oracle_cert_moduli.argtypes = [i, i64]
     lib.oracle_cert_moduli.restype = i
+    lib.oracle_cert_moduli_cs.argtypes = [i, i64, ctypes.c_double, ctypes.c_double]
+    lib.oracle_cert_moduli_cs.restype = i
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = i
     _lib = lib
@@ -249,7 +251,7 @@ def certify(transa, transb, m, n, k, A, lda, B, ldb, tol=0.0, rows=None, nthread
     """The certified precision choice of both emulations (certify.c) for rows ``rows``
     (default: all) of op(A) against every column of op(B).  Keys: t_cert, t_exact, t
     (63: infeasible), moduli (0: infeasible), s_cert, s_exact, s (10: infeasible), rho,
-    gamma."""
+    gamma, alpha2, beta2."""
     lib = _load()
     r, nr = _rows_arg(rows, m)
     out = CertChoice()
@@ -264,3 +266,10 @@ def certify(transa, transb, m, n, k, A, lda, B, ldb, tol=0.0, rows=None, nthread
 def cert_moduli(t: int, k: int) -> int:
     """Fewest leading moduli whose product exceeds 2 k 2^(2t) (0: more than 16)."""
     return _load().oracle_cert_moduli(int(t), int(k))
+
+
+def cert_moduli_cs(t: int, k: int, alpha2: float, beta2: float) -> int:
+    """Fewest leading moduli whose product exceeds twice min(k 2^(2t),
+    (2^t alpha + sqrt(k)/2)(2^t beta + sqrt(k)/2)) (0: more than 16), alpha^2 and beta^2 the
+    largest scaled square sums of the rows of op(A) and the columns of op(B)."""
+    return _load().oracle_cert_moduli_cs(int(t), int(k), float(alpha2), float(beta2))

@@ -40,7 +40,13 @@
  * target must still cover (2 u for the modular emulation, (g ceil(s/4) + 1) u for the split).
  * The choice takes the smaller of the two.  The modular emulation also needs the fewest
  * leading moduli of {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199,
- * 197, 193} whose product exceeds 2 k 2^(2t); more than 16, or t above 62, is infeasible.
+ * 197, 193} whose product exceeds twice a bound of every |(A'B')_ij|, A'_ip = rn(a^_ip 2^t) and
+ * B'_pj = rn(b^_pj 2^t) the rounded integers, so that each element is the representative of its
+ * residues in (-M/2, M/2]; more than 16, or t above 62, is infeasible.  The bound is the smaller
+ * of k 2^(2t) (every |A'_ip|, |B'_pj| <= 2^t) and, by Cauchy-Schwarz and |A'_ip - a^_ip 2^t| <= 1/2,
+ *     (2^t alpha + sqrt(k)/2) (2^t beta + sqrt(k)/2),
+ * alpha^2 = max_i sum_p a^_ip^2 over every row of op(A), beta^2 = max_j sum_p b^_pj^2 over every
+ * column of op(B) (finite entries).
  */
 #include <math.h>
 #include <pthread.h>
@@ -60,6 +66,8 @@ typedef struct {
   int pad;
   double rho;   /* max over the elements of (min(mu_i, G^/phi_j) + min(nu_j, G^/theta_i)) / G^_ij */
   double gamma; /* max over the elements of min(k, G^/(theta_i phi_j)) / (k G^_ij) */
+  double alpha2; /* max over all rows of op(A) of sum_p a^_ip^2 */
+  double beta2;  /* max over all columns of op(B) of sum_p b^_pj^2 */
 } oracle_cert_t;
 
 static const int oc_moduli[16] = {256, 255, 253, 251, 247, 241, 239, 233,
@@ -104,6 +112,23 @@ int oracle_cert_moduli(int t, int64_t k) {
     if (M > need) return l + 1;
   }
   return 0;
+}
+
+/* fewest leading moduli whose product exceeds 2 min(k 2^(2t), (2^t alpha + sqrt(k)/2)(2^t beta + sqrt(k)/2));
+   0 when none of the 16 does */
+int oracle_cert_moduli_cs(int t, int64_t k, double alpha2, double beta2) {
+  const int nk = oracle_cert_moduli(t, k);
+  if (t < 1 || t > 62 || k < 1 || !(alpha2 >= 0.0) || !(beta2 >= 0.0)) return nk;
+  const long double h = sqrtl((long double)k) / 2.0L;
+  const long double bound = (ldexpl(sqrtl((long double)alpha2), t) + h) * (ldexpl(sqrtl((long double)beta2), t) + h);
+  if (!(bound < ldexpl((long double)k, 2 * t))) return nk;
+  unsigned __int128 M = 1;
+  for (int l = 0; l < 16; ++l) {
+    M *= (unsigned __int128)oc_moduli[l];
+    const long double Ml = (long double)(uint64_t)(M >> 64) * 18446744073709551616.0L + (long double)(uint64_t)M;
+    if (Ml > 2.0L * bound) return (nk == 0 || l + 1 < nk) ? l + 1 : nk;
+  }
+  return nk;
 }
 
 /* Two-sum / two-product compensated sum of non-negative terms (Ogita, Rump, Oishi). */
@@ -230,8 +255,9 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
   if (!(tol > 0.0)) tol = 2.0 * kd * u;
   const int64_t segs = (k + 8191) / 8192;
 
-  /* exactness widths over all of op(A) (rows) and op(B) (columns) */
+  /* exactness widths and largest scaled square sums over all of op(A) (rows) and op(B) (columns) */
   int tA = 0, tB = 0;
+  double alpha2 = 0.0, beta2 = 0.0;
   for (int64_t i = 0; i < m; ++i) {
     int sig = 0, any = 0;
     for (int64_t p = 0; p < k; ++p) {
@@ -242,13 +268,17 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
         any = 1;
       }
     }
+    oc_acc sq = {0.0, 0.0};
     for (int64_t p = 0; p < k; ++p) {
       const double v = ta ? A[i * lda + p] : A[p * lda + i];
       if (isfinite(v) && v != 0.0) {
         const int w = sig - oc_lowbit(v);
         if (w > tA) tA = w;
+        const double x = ldexp(fabs(v), -sig);
+        oc_add_prod(&sq, x, x);
       }
     }
+    if (sq.hi + sq.lo > alpha2) alpha2 = sq.hi + sq.lo;
   }
   for (int64_t j = 0; j < n; ++j) {
     int tau = 0, any = 0;
@@ -260,13 +290,17 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
         any = 1;
       }
     }
+    oc_acc sq = {0.0, 0.0};
     for (int64_t p = 0; p < k; ++p) {
       const double v = tb ? B[p * ldb + j] : B[j * ldb + p];
       if (isfinite(v) && v != 0.0) {
         const int w = tau - oc_lowbit(v);
         if (w > tB) tB = w;
+        const double x = ldexp(fabs(v), -tau);
+        oc_add_prod(&sq, x, x);
       }
     }
+    if (sq.hi + sq.lo > beta2) beta2 = sq.hi + sq.lo;
   }
 
   /* the scaled magnitudes of the requested rows */
@@ -356,7 +390,7 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
     const int te = tx < 1 ? 1 : tx;
     if (te < t) t = te;
   }
-  out->moduli = t <= 62 ? oracle_cert_moduli(t, k > 0 ? k : 1) : 0;
+  out->moduli = t <= 62 ? oracle_cert_moduli_cs(t, k > 0 ? k : 1, alpha2, beta2) : 0;
   out->t = out->moduli ? t : 63;
 
   const int dA = (tA + 6) / 7, dB = (tB + 6) / 7;
@@ -369,5 +403,7 @@ int oracle_certify(char transa, char transb, int64_t m, int64_t n, int64_t k, co
   out->s = s;
   out->rho = rho;
   out->gamma = gamma;
+  out->alpha2 = alpha2;
+  out->beta2 = beta2;
   return 0;
 }

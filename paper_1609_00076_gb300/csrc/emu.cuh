@@ -118,8 +118,10 @@ struct ExpMagParts {
   int* e[2];
   float* s[2];
   int* b[2];
+  float* q[2];   // sums of squares relative to the same exponents
   int nkr;       // k-blocks of kRedChunk per row
   float* stats;  // {min mu over rows, min nu over columns, any bad row, any bad column}
+  unsigned int* norms;  // [2] upper bounds of the largest scaled square sum of each side (float bits)
 };
 int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
@@ -212,6 +214,10 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
 // max_j nu_j / min_i G_ij and gamma = 1 / min G_ij (float bits; G the certified lower bound of
 // (|A||B|)_ij 2^-(sigma_i + tau_j)), and the exactness widths of op(A) and op(B).
 constexpr int kCertRhoA = 0, kCertRhoB = 1, kCertGamma = 2, kCertTexA = 3, kCertTexB = 4;
+// the modular emulation's automatic mode also keeps, from the exponent and magnitude pass, upper
+// bounds of max_i ||a^_i||_2^2 and max_j ||b^_j||_2^2 (rows of op(A) and columns of op(B) scaled by
+// 2^-sigma_i and 2^-tau_j; float bits), which bound |A'B'| for the moduli count
+constexpr int kCertNormA = 5, kCertNormB = 6;
 // two sets of words: the FP8 certification's, then (kCertRetry on) the BF16 one's, which runs only
 // when the FP8 planes' looser bound leaves the target out of reach
 constexpr int kCertRetry = 8;

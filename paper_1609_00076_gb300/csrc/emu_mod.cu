@@ -814,6 +814,13 @@ struct ModProducts {
   uint64_t lo[kMaxModuli], hi[kMaxModuli];
 };
 
+// fewest moduli whose product exceeds `need`; 0 when none is enough
+__host__ __device__ inline int moduli_above(hu128 need, const ModProducts& mp) {
+  for (int n = 1; n <= kMaxModuli; ++n)
+    if ((((hu128)mp.hi[n - 1] << 64) | mp.lo[n - 1]) > need) return n;
+  return 0;
+}
+
 // fewest moduli whose product exceeds 2 k 2^(2t) >= 2 max |A'B'|; 0 when none is enough
 __host__ __device__ int moduli_for_products(int t, int64_t k, const ModProducts& mp) {
   if (t < 1 || k < 1) return 0;
@@ -822,10 +829,28 @@ __host__ __device__ int moduli_for_products(int t, int64_t k, const ModProducts&
   int kb = 0;
   while (((int64_t)1 << kb) < k) ++kb;
   if (2 * t + kb >= 126) return 0;
-  const hu128 need = ((hu128)2 * (hu128)k) << (2 * t);
-  for (int n = 1; n <= kMaxModuli; ++n)
-    if ((((hu128)mp.hi[n - 1] << 64) | mp.lo[n - 1]) > need) return n;
-  return 0;
+  return moduli_above(((hu128)2 * (hu128)k) << (2 * t), mp);
+}
+
+// The same from the square sums: with a2 >= max_i ||a^_i||^2 and b2 >= max_j ||b^_j||^2 (rows of
+// op(A), columns of op(B), scaled by 2^-sigma_i, 2^-tau_j) and the rounded integers
+// A'_ip = rn(a^_ip 2^t), |A'_ip - a^_ip 2^t| <= 1/2, Cauchy-Schwarz and the triangle inequality give
+//     |(A'B')_ij| <= ||A'_i|| ||B'_j|| <= 2^(2t) (sqrt(a2) + sqrt(k) 2^(-t-1)) (sqrt(b2) + sqrt(k) 2^(-t-1)),
+// which is below k 2^(2t) when the rows are not all of full magnitude.  The product is formed in
+// double precision (a few correctly rounded operations, covered by the factor 1 + 2^-40) and
+// rounded up to an integer.
+__host__ __device__ int moduli_for_norms(int t, int64_t k, float a2, float b2, const ModProducts& mp) {
+  const int nk = moduli_for_products(t, k, mp);
+  if (t < 1 || k < 1 || t > 62 || !(a2 >= 0.0f) || !(b2 >= 0.0f)) return nk;
+  const double h = ldexp(sqrt((double)k), -t - 1);
+  double x = (sqrt((double)a2) + h) * (sqrt((double)b2) + h) * (1.0 + 0x1p-40);
+  if (x >= (double)k) return nk;
+  const double need = ldexp(x, 2 * t + 1);  // 2 x 2^(2t) < 2 k 2^(2t) <= 2^126 unless nk == 0
+  if (need >= 0x1p126) return nk;
+  const double hi = floor(ldexp(need, -64));
+  const double lo = ceil(need - ldexp(hi, 64));  // an integer below 2^64
+  const int ncs = moduli_above(((hu128)(uint64_t)hi << 64) | (hu128)(uint64_t)lo, mp);
+  return (ncs && (nk == 0 || ncs < nk)) ? ncs : nk;
 }
 
 // The call's plan, on one warp: t given (fixed_t > 0), or the certified choice from the
@@ -839,6 +864,8 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
                                                   ModPlan* __restrict__ plan, unsigned int* err, int flag,
                                                   int retry) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  // the automatic mode's square-sum bounds (written by the exponent pass into the first set)
+  const float a2 = __uint_as_float(cert[kCertNormA]), b2 = __uint_as_float(cert[kCertNormB]);
   if (retry) {
     if (plan->feasible) return;
     cert += kCertRetry;
@@ -849,7 +876,7 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
     cert_rho_gamma(cert, &rho, &gamma);
     t = cert_mod_bits(rho, gamma, (int)cert[kCertTexA], (int)cert[kCertTexB], k, tol, &bound, &exact);
   }
-  const int n = t <= 62 ? moduli_for_products(t, k, mp) : 0;
+  const int n = t > 62 ? 0 : fixed_t <= 0 ? moduli_for_norms(t, k, a2, b2, mp) : moduli_for_products(t, k, mp);
   ModPlan pl;
   pl.t = n ? t : 1;
   pl.n = n ? n : 1;
@@ -951,9 +978,9 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
   const size_t o_emin = off; off = up(off + sizeof(int) * (size_t)(m + n));
   const int64_t nkr = (k + 1023) / 1024;  // k-blocks of the exponent and magnitude pass
-  size_t o_part[2][3];
+  size_t o_part[2][4];
   for (int side = 0; side < 2; ++side)
-    for (int f = 0; f < 3; ++f) {
+    for (int f = 0; f < 4; ++f) {
       o_part[side][f] = off;
       off = up(off + 4 * (size_t)(side == 0 ? m : n) * (size_t)nkr);
     }
@@ -981,9 +1008,11 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
       ws->parts.e[side] = reinterpret_cast<int*>(b + o_part[side][0]);
       ws->parts.s[side] = reinterpret_cast<float*>(b + o_part[side][1]);
       ws->parts.b[side] = reinterpret_cast<int*>(b + o_part[side][2]);
+      ws->parts.q[side] = reinterpret_cast<float*>(b + o_part[side][3]);
     }
     ws->parts.nkr = (int)nkr;
     ws->parts.stats = ws->stats;
+    ws->parts.norms = ws->cert + kCertNormA;
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -1249,13 +1278,13 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   const int prec = cert_prec_default();
-  if (automatic) {  // exponents and magnitude sums in one pass over the operands
-    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
-    // the certification: magnitude planes (in the residue planes' place, which are written
-    // after the plan) and their product with the reduction of the bound's ratios
+  if (automatic) {  // exponents, magnitude sums and square sums in one pass over the operands
     if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu_mod: clearing the certification words");
+    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
+    // the certification: magnitude planes (in the residue planes' place, which are written
+    // after the plan) and their product with the reduction of the bound's ratios
     if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
     if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
                           ws.eminB, ws.cert, nullptr, 0, sms, s)))

@@ -102,14 +102,25 @@ __device__ __forceinline__ void exponents_body(const double* __restrict__ X, int
   }
 }
 
-// |x| * 2^-sigma as a float (truncated mantissa; an estimate for slice selection)
+// |x| * 2^-sigma as a float, the mantissa truncated (so within a factor 1 - 2^-23 of the value,
+// below it); 0 for a non-finite x and where the result is below 2^-126
 __device__ __forceinline__ float scaled_magnitude(uint64_t bits, int sigma) {
   const int E = (int)((bits >> 52) & 0x7FFu);
-  if (E == 0 || E == 0x7FF) return 0.0f;
-  const int fe = E - 1023 - sigma + 127;
+  if (E == 0x7FF) return 0.0f;
+  uint64_t frac = bits & 0xFFFFFFFFFFFFFull;  // |x| = 1.frac 2^ex
+  int ex;
+  if (E) {
+    ex = E - 1023;
+  } else {  // subnormal: frac 2^-1074, normalised here
+    if (!frac) return 0.0f;
+    const int nb = 64 - __clzll((long long)frac);
+    ex = nb - 1 - 1074;
+    frac = (frac << (53 - nb)) & 0xFFFFFFFFFFFFFull;
+  }
+  const int fe = ex - sigma + 127;
   if (fe <= 0) return 0.0f;
   if (fe >= 255) return 3.0e38f;
-  const uint32_t fb = ((uint32_t)fe << 23) | (uint32_t)((bits >> 29) & 0x7FFFFFu);
+  const uint32_t fb = ((uint32_t)fe << 23) | (uint32_t)(frac >> 29);
   return __uint_as_float(fb);
 }
 
@@ -623,8 +634,9 @@ __global__ void __launch_bounds__(256) k_magnitudes_pair(const __grid_constant__
 // 2^d for d <= 0 as a float (0 below 2^-126)
 __device__ __forceinline__ float pow2f_nonpos(int d) { return d < -126 ? 0.0f : __int_as_float((127 + d) << 23); }
 
-// folds element bits b into a running (largest exponent E, sum acc of |x| 2^-E, non-finite flag)
-__device__ __forceinline__ void expmag_add(uint64_t b, int& E, float& acc, int& bad) {
+// folds element bits b into a running (largest exponent E, sum acc of |x| 2^-E, sum sq of
+// x^2 2^-2E, non-finite flag); a rescaling that underflows drops parts below 2^-126 each
+__device__ __forceinline__ void expmag_add(uint64_t b, int& E, float& acc, float& sq, int& bad) {
   if (is_nonfinite(b)) {
     bad = 1;
     return;
@@ -632,32 +644,43 @@ __device__ __forceinline__ void expmag_add(uint64_t b, int& E, float& acc, int& 
   if (is_zero(b)) return;
   const int e = exponent_of(b);
   if (e > E) {
-    acc = E == kExpEmpty ? 0.0f : acc * pow2f_nonpos(E - e);
+    if (E == kExpEmpty) {
+      acc = 0.0f;
+      sq = 0.0f;
+    } else {
+      acc *= pow2f_nonpos(E - e);
+      sq *= pow2f_nonpos(2 * (E - e));
+    }
     E = e;
   }
-  acc += scaled_magnitude(b, E);
+  const float v = scaled_magnitude(b, E);
+  acc += v;
+  sq = fmaf(v, v, sq);
 }
-// (E, acc) := (E, acc) + (E2, acc2), both relative to their own largest exponent
-__device__ __forceinline__ void expmag_merge(int& E, float& acc, int E2, float acc2) {
+// (E, acc, sq) := (E, acc, sq) + (E2, acc2, sq2), each relative to its own largest exponent
+__device__ __forceinline__ void expmag_merge(int& E, float& acc, float& sq, int E2, float acc2, float sq2) {
   if (E2 == kExpEmpty) return;
   if (E == kExpEmpty) {
     E = E2;
     acc = acc2;
+    sq = sq2;
     return;
   }
   if (E2 > E) {
     acc = acc * pow2f_nonpos(E - E2) + acc2;
+    sq = sq * pow2f_nonpos(2 * (E - E2)) + sq2;
     E = E2;
   } else {
     acc += acc2 * pow2f_nonpos(E2 - E);
+    sq += sq2 * pow2f_nonpos(2 * (E2 - E));
   }
 }
 
 template <bool ROWS_CONTIG>
 __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K, int nkr,
-                                            int* __restrict__ pe, float* __restrict__ ps, int* __restrict__ pb,
-                                            int64_t bx, int64_t by, int (*s_e)[33], float (*s_s)[33],
-                                            int (*s_b)[33]) {
+                                            int* __restrict__ pe, float* __restrict__ ps, float* __restrict__ pq,
+                                            int* __restrict__ pb, int64_t bx, int64_t by, int (*s_e)[33],
+                                            float (*s_s)[33], float (*s_q)[33], int (*s_b)[33]) {
   const int64_t p_begin = by * kRedChunk;
   const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
   if (ROWS_CONTIG) {
@@ -665,7 +688,7 @@ __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t r = bx * 32 + tx;
     int E = kExpEmpty, bd = 0;
-    float acc = 0.0f;
+    float acc = 0.0f, sq = 0.0f;
     if (r < R) {
       // eight loads in flight per thread, then their folds in the same order
       int64_t p = p_begin + ty;
@@ -674,21 +697,23 @@ __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = load_bits<true>(X, ld, r, p + 8 * u);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, bd);
+        for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, sq, bd);
       }
-      for (; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, bd);
+      for (; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, sq, bd);
     }
     s_e[ty][tx] = E;
     s_s[ty][tx] = acc;
+    s_q[ty][tx] = sq;
     s_b[ty][tx] = bd;
     __syncthreads();
     if (ty == 0 && r < R) {
       for (int q = 1; q < 8; ++q) {
-        expmag_merge(E, acc, s_e[q][tx], s_s[q][tx]);
+        expmag_merge(E, acc, sq, s_e[q][tx], s_s[q][tx], s_q[q][tx]);
         bd |= s_b[q][tx];
       }
       pe[r * nkr + by] = E;
       ps[r * nkr + by] = acc;
+      pq[r * nkr + by] = sq;
       pb[r * nkr + by] = bd;
     }
   } else {
@@ -697,34 +722,37 @@ __device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_
     const int64_t r = bx * 8 + w;
     if (r >= R) return;
     int E = kExpEmpty, bd = 0;
-    float acc = 0.0f;
+    float acc = 0.0f, sq = 0.0f;
     int64_t p = p_begin + lane;
     for (; p + 224 < p_end; p += 256) {  // eight loads in flight per lane, then their folds in order
       uint64_t v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = load_bits<false>(X, ld, r, p + 32 * u);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, bd);
+      for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, sq, bd);
     }
-    for (; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, bd);
+    for (; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, sq, bd);
     for (int o = 16; o; o >>= 1) {  // a fixed butterfly: deterministic
       const int E2 = __shfl_xor_sync(0xffffffffu, E, o);
       const float a2 = __shfl_xor_sync(0xffffffffu, acc, o);
+      const float q2 = __shfl_xor_sync(0xffffffffu, sq, o);
       bd |= __shfl_xor_sync(0xffffffffu, bd, o);
       // both partners merge the same pair, lower lane first, so they agree bit for bit
       if (lane & o) {
         int El = E2;
-        float al = a2;
-        expmag_merge(El, al, E, acc);
+        float al = a2, ql = q2;
+        expmag_merge(El, al, ql, E, acc, sq);
         E = El;
         acc = al;
+        sq = ql;
       } else {
-        expmag_merge(E, acc, E2, a2);
+        expmag_merge(E, acc, sq, E2, a2, q2);
       }
     }
     if (lane == 0) {
       pe[r * nkr + by] = E;
       ps[r * nkr + by] = acc;
+      pq[r * nkr + by] = sq;
       pb[r * nkr + by] = bd;
     }
   }
@@ -734,6 +762,7 @@ __global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ Pre
                                                      const __grid_constant__ ExpMagParts parts) {
   __shared__ int s_e[8][33];
   __shared__ float s_s[8][33];
+  __shared__ float s_q[8][33];
   __shared__ int s_b[8][33];
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // the minima start empty (k_rowstats_pair runs after this grid)
     parts.stats[0] = 3.0e38f;
@@ -746,61 +775,83 @@ __global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ Pre
   const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
   const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
   if (j.rows_contig)
-    expmag_body<true>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.b[ji], bx, by, s_e, s_s, s_b);
+    expmag_body<true>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.q[ji], parts.b[ji], bx, by, s_e,
+                      s_s, s_q, s_b);
   else
-    expmag_body<false>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.b[ji], bx, by, s_e, s_s, s_b);
+    expmag_body<false>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.q[ji], parts.b[ji], bx, by,
+                       s_e, s_s, s_q, s_b);
 }
 
 // per row of both sides: sig = the largest block exponent, bad = any flag, mu = the blocks'
 // sums rescaled to sig and added in block order (32.32 fixed point, as the magnitude pass);
 // then the side's minimum of the non-zero mu and its any-bad flag into stats (a minimum and an
-// OR: the same values in any order)
+// OR: the same values in any order), and the side's largest square sum, raised to an upper
+// bound, into norms.
+//
+// The square sum of a row is computed in FP32 from at most K terms v^2 (v = |x| 2^-sig rounded
+// to FP32, v^2 added by a fused multiply-add) and fewer than 9 nkr merges, each one rounding of
+// a sum of non-negative values; the rescalings are exact except where they underflow, which
+// drops parts below K 2^-126 in all.  So the computed value q satisfies
+// sum_p (x_p 2^-sig)^2 <= q (1 + (K + 9 nkr + 2) 2^-24 (1 + 2^-20)) + K 2^-126, and
+// q (1 + (K + 8 nkr + 64) 2^-22) + K 2^-125, rounded upward, covers it.
 __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp,
                                                        const __grid_constant__ ExpMagParts parts) {
   __shared__ float s_mn[8];
+  __shared__ float s_mx[8];
   __shared__ int s_bd[8];
   const int ji = blockIdx.y;
   const PrepJob& j = pp.j[ji];
-  float mn = 3.0e38f;
+  const float grow = __fadd_ru(1.0f, __fmul_ru((float)(j.K + 8 * (int64_t)parts.nkr + 64), 0x1p-22f));
+  const float floor_add = __fmul_ru((float)j.K, 0x1p-125f);
+  float mn = 3.0e38f, mx = 0.0f;
   int any_bad = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
     const int* pe = parts.e[ji] + r * parts.nkr;
     const float* ps = parts.s[ji] + r * parts.nkr;
+    const float* pq = parts.q[ji] + r * parts.nkr;
     const int* pb = parts.b[ji] + r * parts.nkr;
     int E = kExpEmpty, bd = 0;
     for (int q = 0; q < parts.nkr; ++q) {
       E = max(E, pe[q]);
       bd |= pb[q];
     }
-    float mu = 0.0f;
+    float mu = 0.0f, sq = 0.0f;
     if (E != kExpEmpty)
       for (int q = 0; q < parts.nkr; ++q)
-        if (pe[q] != kExpEmpty) mu += ps[q] * pow2f_nonpos(pe[q] - E);
+        if (pe[q] != kExpEmpty) {
+          mu += ps[q] * pow2f_nonpos(pe[q] - E);
+          sq += pq[q] * pow2f_nonpos(2 * (pe[q] - E));
+        }
     j.sig[r] = E;
     j.bad[r] = bd;
     const unsigned long long mq = magnitude_fixed(mu);
     if (j.mu) j.mu[r] = mq;
     if (mq > 0ull) mn = fminf(mn, magnitude_value(mq));
+    if (E != kExpEmpty) mx = fmaxf(mx, __fmaf_ru(sq, grow, floor_add));
     any_bad |= bd;
   }
   for (int o = 16; o; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     any_bad |= __shfl_xor_sync(0xffffffffu, any_bad, o);
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     s_mn[w] = mn;
+    s_mx[w] = mx;
     s_bd[w] = any_bad;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
       mn = fminf(mn, s_mn[q]);
+      mx = fmaxf(mx, s_mx[q]);
       any_bad |= s_bd[q];
     }
     // non-negative floats order as their bit patterns
     if (mn < 3.0e38f) atomicMin(reinterpret_cast<int*>(parts.stats + ji), __float_as_int(mn));
     if (any_bad) atomicOr(reinterpret_cast<int*>(parts.stats + 2 + ji), __float_as_int(1.0f));
+    if (parts.norms && mx > 0.0f) atomicMax(parts.norms + ji, __float_as_uint(mx));
   }
 }
 

@@ -172,7 +172,7 @@ def cert_dtype(request, monkeypatch):
     return request.param
 
 
-@pytest.mark.parametrize("kind", ["uniform", "e8", "e32", "halves4", "halves8", "sparse", "blocks", "int8"])
+@pytest.mark.parametrize("kind", ["uniform", "e8", "e32", "halves4", "halves8", "sparse", "blocks", "int8", "extreme"])
 @pytest.mark.parametrize("tol", [0.0, 1e-10])
 def test_modular_choice_matches_the_rule(oracle_mod, kind, tol, cert_dtype):
     m, n, k = 260, 190, 900
@@ -191,6 +191,10 @@ def test_modular_choice_matches_the_rule(oracle_mod, kind, tol, cert_dtype):
     else:
         assert c["t"] <= info.digit_bits <= c["t"] + 1, (c, info.digit_bits)
         assert info.rho >= c["rho"] * (1 - 1e-6) and info.gamma >= c["gamma"] * (1 - 1e-6)
+    # the moduli: the Cauchy-Schwarz count from upper bounds of the square sums, never more than
+    # the k 2^(2t) count and at most one more than the exact square sums give
+    n_cs = oracle_mod.cert_moduli_cs(info.digit_bits, k, c["alpha2"], c["beta2"])
+    assert n_cs <= info.products <= min(oracle_mod.cert_moduli(info.digit_bits, k), n_cs + 1), (c, info.products)
     _check_bound(oracle_mod, ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.5, C, m, out, tol if tol > 0 else 2 * k * U)
     model = oracle_mod.ozmod_dgemm_rows(ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.5, C, m, info.digit_bits)
     assert first_mismatch(synth.view(out, m, n, m).flatten(order="F"), model, None, m) is None

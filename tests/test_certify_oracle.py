@@ -227,3 +227,75 @@ def test_rational_evaluation_on_tiny_problems(oracle_mod):
                     s += 1
                 t_need, s_need = max(t_need, t), max(s_need, s)
         assert (c["t_cert"], c["s_cert"]) == (t_need, s_need), (trial, c, t_need, s_need)
+
+
+def _moduli_products():
+    mods = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193]
+    out, p = [], 1
+    for q in mods:
+        p *= q
+        out.append(p)
+    return out
+
+
+def test_cauchy_schwarz_moduli_hand_values(oracle_mod):
+    # all-ones rows of k = 1024: every scaled entry is 1/2, alpha^2 = beta^2 = k/4 = 256, and
+    # A'B' = k (2^(t-1))^2 = 2^(2t + 8) exactly, the Cauchy-Schwarz bound (2^t 16 + 16)^2 with it.
+    # At t = 42: 2 k 2^(2t) = 2^95 needs 13 moduli (12 multiply to 2^94.80); twice the
+    # Cauchy-Schwarz bound, 2^93 (1 + 2^-42)^2, needs 12 (11 give 2^87.04)
+    k = 1024
+    c = oracle_mod.certify("N", "N", 3, 3, k, np.ones(3 * k), 3, np.ones(k * 3), k)
+    assert c["alpha2"] == 256.0 and c["beta2"] == 256.0
+    assert oracle_mod.cert_moduli(42, k) == 13
+    assert oracle_mod.cert_moduli_cs(42, k, 256.0, 256.0) == 12
+    P = _moduli_products()
+    assert P[10] < 2 * k * 2 ** 82 < P[11]  # the exact |A'B'| needs the 12th modulus
+    # rows of full magnitude (alpha^2 = beta^2 = k) leave the bound k 2^(2t)
+    for t in (10, 30, 44):
+        assert oracle_mod.cert_moduli_cs(t, 4096, 4096.0, 4096.0) == oracle_mod.cert_moduli(t, 4096)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_cauchy_schwarz_moduli_cover_the_exact_products(oracle_mod, seed):
+    # brute force: the integers A'_ip = rn(a^_ip 2^t), B'_pj = rn(b^_pj 2^t) in exact arithmetic,
+    # their product in Python integers; the chosen moduli must multiply to more than 2 max |A'B'|
+    rng = np.random.default_rng(seed)
+    m, n, k = 6, 5, 37
+    kind = seed % 4
+    A = rng.uniform(-1, 1, (m, k))
+    B = rng.uniform(-1, 1, (k, n))
+    if kind == 1:  # one large entry per row, the rest small: small square sums
+        A *= 2.0 ** -12
+        A[np.arange(m), rng.integers(0, k, m)] = 0.75
+    elif kind == 2:  # powers of two over a wide range
+        A *= 2.0 ** rng.integers(-20, 3, (m, k))
+        B *= 2.0 ** rng.integers(-20, 3, (k, n))
+    elif kind == 3:  # full-magnitude rows
+        A = np.sign(A) * 0.999
+        B = np.sign(B) * 0.999
+    Acm = np.asfortranarray(A).ravel(order="F")
+    Bcm = np.asfortranarray(B).ravel(order="F")
+    c = oracle_mod.certify("N", "N", m, n, k, Acm, m, Bcm, k)
+
+    def scaled(rowvals):
+        e = int(max(np.frexp(v)[1] for v in rowvals if v != 0))
+        return [Fraction(float(v)) / Fraction(2) ** e for v in rowvals]
+
+    As = [scaled(A[i, :]) for i in range(m)]
+    Bs = [scaled(B[:, j]) for j in range(n)]
+    a2 = max(sum(x * x for x in r) for r in As)
+    b2 = max(sum(x * x for x in r) for r in Bs)
+    assert abs(c["alpha2"] - float(a2)) <= 1e-15 * float(a2)
+    assert abs(c["beta2"] - float(b2)) <= 1e-15 * float(b2)
+    P = _moduli_products()
+    fewer = []
+    for t in (3, 8, 20, 31, 45):
+        Ai = [[round(x * 2 ** t) for x in r] for r in As]
+        Bi = [[round(x * 2 ** t) for x in r] for r in Bs]
+        cmax = max(abs(sum(a * b for a, b in zip(Ai[i], Bi[j]))) for i in range(m) for j in range(n))
+        nm = oracle_mod.cert_moduli_cs(t, k, c["alpha2"], c["beta2"])
+        assert nm >= 1 and P[nm - 1] > 2 * cmax, (t, nm)
+        assert nm <= oracle_mod.cert_moduli(t, k)
+        fewer.append(nm < oracle_mod.cert_moduli(t, k))
+    if kind == 1:  # small square sums: fewer moduli than the k 2^(2t) bound somewhere
+        assert any(fewer)
