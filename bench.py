@@ -750,7 +750,9 @@ def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int =
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
                 gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
-            graph.replay()
+            with torch.cuda.stream(stream):
+                graph.replay()
+            torch.cuda.synchronize()  # the timed replays below must not overlap this one
             best = float("inf")
             for _ in range(reps):
                 e0, e1 = _events(2)

@@ -95,6 +95,15 @@ struct PrepJob {
   // the smallest frexp exponent of each row's non-zero finite entries (atomic minimum by the
   // magnitude planes; kEminNone until then), or null
   int* emin;
+  // grouped modular problems: the per row and k-block partials of the one-pass exponent and
+  // magnitude statistics ([R][nkr] each, as ExpMagParts), and the word that receives the side's
+  // largest scaled square sum (float bits)
+  int* pe;
+  float* ps;
+  float* pq;
+  int* pb;
+  int nkr;
+  unsigned int* norm;
 };
 constexpr int kEminNone = 0x7F7F7F7F;  // a row without a non-zero finite entry (memset byte 0x7F)
 // fills j's block ranges, advancing the running block counts of both launches
@@ -194,7 +203,7 @@ int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_bl
 // its tex; then, after the plans, the residues of every job with its problem's plan (nothing for
 // an infeasible plan)
 int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s,
-                            int prec = kCertFP8, bool retry = false);
+                            int prec = kCertFP8, const unsigned int* retry_if = nullptr);
 int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
                            cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
@@ -202,6 +211,11 @@ int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, 
                         bool exponents, bool split, cudaStream_t s);
 // magnitude sums of every job (after the batched exponents; the jobs' mu arrays zeroed by them)
 int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
+// grouped modular problems: exponents, flags, magnitude sums and square-sum bounds of every job in
+// one pass over the operands (the jobs' partial arrays), then per row sig, bad, mu and emin's
+// initial value, and the side's largest square-sum bound into the job's norm word: the same
+// arithmetic, in the same order, as launch_expmag_pair
+int launch_expmag_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
 // exponents and magnitude statistics of every problem (jobs 2q, 2q+1 = op(A), op(B)^T of
 // problem q) into stats_dev[4q .. 4q+3] = {min mu, min nu, bad row, bad column}
 int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
@@ -282,8 +296,9 @@ int make_cert_entry(int64_t m, int64_t n, int64_t k, int prec, const void* PA, c
                     const unsigned long long* muA, const unsigned long long* muB, const int* badA, const int* badB,
                     const int* sigA, const int* sigB, const int* eminA, const int* eminB, unsigned int* words,
                     const struct ModPlan* gate, CertTableEntry* e);
+// run_if: when given, the launch returns at once unless *run_if is non-zero (the BF16 retry)
 int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int prec, int sms,
-                        cudaStream_t stream);
+                        cudaStream_t stream, const unsigned int* run_if = nullptr);
 
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 // exactness width of the modular integers: t at which every scaled entry is an integer (0: both
@@ -425,6 +440,9 @@ struct ModGrouped {
   ColJob* coljobs_dev = nullptr;
   ModTableEntry* table_dev = nullptr;
   unsigned int* words_dev = nullptr;       // kCertWords per problem
+  // [0]: some problem's first plan found no feasible t (the BF16 retry runs); [1]: some problem's
+  // final plan did (its FP64 fallback tiles run)
+  unsigned int* flags_dev = nullptr;
   uint8_t* scr = nullptr;                  // park slots of the product launch
   int scr_ctas = 0;
 };

@@ -80,10 +80,11 @@ template <bool PAIR, bool FP8, bool TABLE = false>
 __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
     k_cert_gemm(const __grid_constant__ CertArgs p, const __grid_constant__ CUtensorMap tmA,
                 const __grid_constant__ CUtensorMap tmB, const CertTableEntry* __restrict__ table = nullptr,
-                int count = 0, int total_tiles = 0) {
+                int count = 0, int total_tiles = 0, const unsigned int* __restrict__ run_if = nullptr) {
   static_assert(!(PAIR && TABLE), "grouped certification runs on one SM per tile");
   using L = CertCfg<PAIR, FP8>;
   if (!TABLE && p.gate && p.gate->feasible) return;  // the retry of a certification that succeeded
+  if (TABLE && run_if && *run_if == 0u) return;     // a grouped retry that no problem needs
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOffBar);
@@ -439,7 +440,8 @@ int launch_cert_kernel(const CertArgs& a, const CUtensorMap& tmA, const CUtensor
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = PAIR ? 1 : 0;
-  e = cudaLaunchKernelEx(&cfg, kern, a, tmA, tmB, static_cast<const CertTableEntry*>(nullptr), 0, 0);
+  e = cudaLaunchKernelEx(&cfg, kern, a, tmA, tmB, static_cast<const CertTableEntry*>(nullptr), 0, 0,
+                         static_cast<const unsigned int*>(nullptr));
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "certification gemm launch");
 }
 
@@ -571,7 +573,7 @@ int make_cert_entry(int64_t m, int64_t n, int64_t k, int prec, const void* PA, c
 }
 
 int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_tiles, int prec, int sms,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, const unsigned int* run_if) {
   if (count <= 0 || total_tiles <= 0) return GBD_OK;
   using L = CertCfg<false, true>;  // the same shared memory and threads in both precisions
   auto kern = prec == kCertFP8 ? k_cert_gemm<false, true, true> : k_cert_gemm<false, false, true>;
@@ -582,7 +584,7 @@ int launch_cert_grouped(const CertTableEntry* table_dev, int count, int total_ti
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
   const int grid = total_tiles < sms ? total_tiles : sms;
-  kern<<<grid, L::kThreads, L::kAlloc, stream>>>(dummy_args, dummy, dummy, table_dev, count, total_tiles);
+  kern<<<grid, L::kThreads, L::kAlloc, stream>>>(dummy_args, dummy, dummy, table_dev, count, total_tiles, run_if);
   e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped certification launch");
 }

@@ -892,9 +892,11 @@ __global__ void __launch_bounds__(32) k_mod_plan(const unsigned int* __restrict_
 }
 
 // the plans of a grouped launch, one thread per problem (as k_mod_plan; an infeasible plan needs no
-// error bit: the grouped FP64 kernel computes that problem)
+// error bit: the grouped FP64 kernel computes that problem).  An infeasible plan sets flags[0] on
+// the first pass and flags[1] on the final one (the retry, or the first when no retry follows).
 __global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __restrict__ jobs, int count,
-                                                          const __grid_constant__ ModProducts mp, int retry) {
+                                                          const __grid_constant__ ModProducts mp, int retry,
+                                                          unsigned int* __restrict__ flags, int final_pass) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const ModPlanJob j = jobs[q];
@@ -906,7 +908,10 @@ __global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __re
     cert_rho_gamma(words, &rho, &gamma);
     t = cert_mod_bits(rho, gamma, (int)words[kCertTexA], (int)words[kCertTexB], j.k, j.tol, &bound, &exact);
   }
-  const int n = t <= 62 ? moduli_for_products(t, j.k, mp) : 0;
+  const int n = t > 62 ? 0
+                : j.fixed_t <= 0
+                    ? moduli_for_norms(t, j.k, __uint_as_float(j.words[kCertNormA]), __uint_as_float(j.words[kCertNormB]), mp)
+                    : moduli_for_products(t, j.k, mp);
   ModPlan pl;
   pl.t = n ? t : 1;
   pl.n = n ? n : 1;
@@ -918,6 +923,10 @@ __global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __re
   pl.gamma = gamma;
   pl.bound = bound;
   *j.plan = pl;
+  if (!n) {
+    if (!retry) atomicOr(flags, 1u);
+    if (final_pass) atomicOr(flags + 1, 1u);
+  }
 }
 
 // the column scales alpha 2^(tau_j - 2t) of a grouped launch, one block per problem
@@ -1395,7 +1404,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   const size_t o_plj = off; off = up256(off + sizeof(ModPlanJob) * (size_t)count);
   const size_t o_col = off; off = up256(off + sizeof(ColJob) * (size_t)count);
   const size_t o_tab = off; off = up256(off + sizeof(ModTableEntry) * (size_t)count);
-  const size_t o_words = off; off = up256(off + sizeof(unsigned int) * kCertWords * (size_t)count);
+  const size_t o_words = off; off = up256(off + sizeof(unsigned int) * kCertWords * (size_t)(count + 1));
   const size_t o_scr = off; off = up256(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
   std::vector<size_t> o_ws(count);
   std::vector<int> nmod_ws(count);
@@ -1424,6 +1433,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   g->coljobs_dev = reinterpret_cast<ColJob*>(b + o_col);
   g->table_dev = reinterpret_cast<ModTableEntry*>(b + o_tab);
   g->words_dev = reinterpret_cast<unsigned int*>(b + o_words);
+  g->flags_dev = g->words_dev + (size_t)kCertWords * count;
   g->scr = reinterpret_cast<uint8_t*>(b + o_scr);
   g->scr_ctas = ctas;
   g->jobs.assign(2 * (size_t)count, PrepJob{});
@@ -1445,14 +1455,16 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
     ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
     ja.sig = w.sigA; ja.bad = w.badA; ja.mu = w.muA; ja.D = w.DA; ja.kp = w.kp;
-    ja.tex = words + kCertTexA; ja.plan = w.plan; ja.emin = w.eminA;
+    ja.tex = words + kCertTexA; ja.plan = w.plan; ja.emin = w.eminA; ja.norm = words + kCertNormA;
+    ja.pe = w.parts.e[0]; ja.ps = w.parts.s[0]; ja.pq = w.parts.q[0]; ja.pb = w.parts.b[0]; ja.nkr = w.parts.nkr;
     jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
     jb.sig = w.sigB; jb.bad = w.badB; jb.mu = w.muB; jb.D = w.DB; jb.kp = w.kp;
-    jb.tex = words + kCertTexB; jb.plan = w.plan; jb.emin = w.eminB;
+    jb.tex = words + kCertTexB; jb.plan = w.plan; jb.emin = w.eminB; jb.norm = words + kCertNormB;
+    jb.pe = w.parts.e[1]; jb.ps = w.parts.s[1]; jb.pq = w.parts.q[1]; jb.pb = w.parts.b[1]; jb.nkr = w.parts.nkr;
     prep_job_blocks(ja, g->exp_blocks, g->split_blocks);
     prep_job_blocks(jb, g->exp_blocks, g->split_blocks);
     CertTableEntry& ce = g->cert[q];
-    if ((*rc = make_cert_entry(p.m, p.n, p.k, kCertFP8, w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, w.sigA, w.sigB,
+    if ((*rc = make_cert_entry(p.m, p.n, p.k, cert_prec_default(), w.DA, w.DB, w.muA, w.muB, w.badA, w.badB, w.sigA, w.sigB,
                                w.eminA, w.eminB, words, nullptr, &ce)))
       return off;
     CertTableEntry& cr = g->cert[count + q];  // the BF16 retry, for a plan that found no feasible t
@@ -1539,24 +1551,28 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   cudaError_t e;
   int rc;
   const int njobs = (int)g.jobs.size();
-  if ((e = cudaMemsetAsync(g.words_dev, 0, sizeof(unsigned int) * kCertWords * (size_t)g.count, s)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(g.words_dev, 0, sizeof(unsigned int) * kCertWords * (size_t)(g.count + 1), s)) !=
+      cudaSuccess)
     return cuda_fail(e, "grouped modular: clearing the certification words");
-  // exponents, flags and magnitude sums of every side (the sums zeroed by the first launch)
-  if ((rc = launch_prep_batched(g.jobs_dev, njobs, g.exp_blocks, 0, true, false, s))) return rc;
-  if ((rc = launch_magnitudes_batched(g.jobs_dev, njobs, g.exp_blocks, s))) return rc;
+  // exponents, flags, magnitude sums and square-sum bounds of every side in one pass
+  if ((rc = launch_expmag_batched(g.jobs_dev, njobs, g.exp_blocks, s))) return rc;
   // the certification: magnitude planes, their products, the plans (the same precision as the
   // single call's, so that a problem gets the same plan alone and in a batch)
   const int prec = cert_prec_default();
-  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec, false))) return rc;
+  const bool retry = prec == kCertFP8;
+  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec))) return rc;
   if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, prec, sms, s))) return rc;
   const ModProducts prods = moduli_products();
-  k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 0);
+  k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 0, g.flags_dev,
+                                                           retry ? 0 : 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped plan launch");
-  if (prec == kCertFP8) {
-    // the BF16 retry of every problem whose plan found no feasible t (the others return at once)
-    if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, kCertBF16, true))) return rc;
-    if ((rc = launch_cert_grouped(g.cert_dev + g.count, g.count, g.cert_tiles, kCertBF16, sms, s))) return rc;
-    k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 1);
+  if (retry) {
+    // the BF16 retry of every problem whose plan found no feasible t; the launches return at once
+    // when no problem needs it, and skip the problems whose plan is feasible
+    if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, kCertBF16, g.flags_dev))) return rc;
+    if ((rc = launch_cert_grouped(g.cert_dev + g.count, g.count, g.cert_tiles, kCertBF16, sms, s, g.flags_dev)))
+      return rc;
+    k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 1, g.flags_dev, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped plan launch");
   }
   // residues and column scales with each problem's plan

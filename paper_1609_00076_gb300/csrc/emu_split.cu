@@ -384,44 +384,48 @@ struct MagWriter {
   int64_t R, K;
   void* D;
   int64_t kp;
-  unsigned int* tex;  // the side's exactness width (atomic maximum)
-  int* emin;          // per row: the smallest frexp exponent of a non-zero entry (atomic minimum)
+  unsigned int* s_tex;  // the block's exactness width (shared-memory maximum; the kernel flushes it)
+  int* s_emin;          // [kTile] the block's rows: smallest frexp exponent of a non-zero entry (shared
+                        // minimum; the kernel flushes it), or null
   __device__ __forceinline__ void operator()(const uint64_t (&x)[kPerThread], int sg, int64_t r,
                                              int64_t pbase) const {
     constexpr int kMant = FP8 ? 2 : 7;     // stored fraction bits
     constexpr int kBias = FP8 ? 15 : 127;  // exponent bias
     constexpr int kFloor = FP8 ? -14 : -63;  // exponent of the floor in plane units
+    const int base = S - sg - 1023;          // a normal x: exponent of |x| 2^(S - sigma) = E + base
     uint32_t h[kPerThread];
     int w = 0, em = kEminNone;
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
-      const uint64_t b = x[v];
-      const uint32_t E = (uint32_t)(b >> 52) & 0x7FFu;
-      if (E == 0x7FFu || (b << 1) == 0) {
+      const uint32_t hi = (uint32_t)(x[v] >> 32), lo = (uint32_t)x[v];
+      const int E = (int)((hi >> 20) & 0x7FFu);
+      if (E == 0x7FF || ((hi << 1) | lo) == 0u) {
         h[v] = 0u;
         continue;
       }
-      uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-      int e2;  // |x| = mant 2^e2
-      if (E) {
-        mant |= 1ull << 52;
-        e2 = (int)E - 1075;
-      } else {
-        e2 = -1074;
+      if (E != 0) {  // normal: the 53-bit significand 1.f, its top fraction bits in hi
+        const int eb = E + base;
+        h[v] = eb < kFloor ? (uint32_t)(kFloor + kBias) << kMant
+                           : ((uint32_t)(eb + kBias) << kMant) | ((hi >> (20 - kMant)) & ((1u << kMant) - 1u));
+        // trailing zeros of the significand (the implicit bit bounds them by 52)
+        const int tz = lo ? __ffs((int)lo) - 1 : 31 + __ffs((int)((hi & 0xFFFFFu) | 0x100000u));
+        w = max(w, min(255, sg - (E - 1075 + tz)));
+        em = min(em, E - 1022);
+      } else {  // subnormal: |x| = f 2^-1074
+        const uint64_t mant = x[v] & 0xFFFFFFFFFFFFFull;
+        const int nb = 64 - __clzll((long long)mant);  // bit length, 1..52
+        const int eb = nb - 1 - 1074 - sg + S;
+        if (eb < kFloor) {
+          h[v] = (uint32_t)(kFloor + kBias) << kMant;
+        } else {
+          const uint32_t mf = (uint32_t)((nb >= kMant + 1 ? (mant >> (nb - kMant - 1)) : (mant << (kMant + 1 - nb))) &
+                                         ((1u << kMant) - 1u));
+          h[v] = ((uint32_t)(eb + kBias) << kMant) | mf;
+        }
+        w = max(w, min(255, sg - (-1074 + __ffsll((long long)mant) - 1)));
+        em = min(em, nb - 1074);
       }
-      const int nb = 64 - __clzll((long long)mant);  // bit length, 1..53
-      const int eb = nb - 1 + e2 - sg + S;           // exponent of |x| 2^(S - sigma)
-      if (eb < kFloor) {
-        h[v] = (uint32_t)(kFloor + kBias) << kMant;  // the floor
-      } else {
-        const uint32_t mf = (uint32_t)((nb >= kMant + 1 ? (mant >> (nb - kMant - 1)) : (mant << (kMant + 1 - nb))) &
-                                       ((1u << kMant) - 1u));
-        h[v] = ((uint32_t)(eb + kBias) << kMant) | mf;
-      }
-      w = max(w, min(255, sg - (e2 + __ffsll((long long)mant) - 1)));
-      em = min(em, nb + e2);  // the frexp exponent of x
     }
-    if (emin && em < __ldcg(emin + r)) atomicMin(emin + r, em);
     const bool full = pbase + kPerThread <= K;
     if (FP8) {
       uint8_t* row = static_cast<uint8_t*>(D) + r * kp + pbase;
@@ -440,13 +444,34 @@ struct MagWriter {
         for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint16_t)h[v];
       }
     }
-    // the lanes that are here together reduce their widths; one of them raises the stored width
-    namespace cg = cooperative_groups;
-    const cg::coalesced_group g = cg::coalesced_threads();
-    const unsigned wm = cg::reduce(g, (unsigned)w, cg::greater<unsigned>());
-    if (g.thread_rank() == 0 && wm > __ldcg(tex)) atomicMax(tex, wm);
+    // the row's minimum into shared memory; the width reduced over the lanes here together (one
+    // mask for all of them), one shared maximum per warp
+    if (s_emin && em != kEminNone) atomicMin(s_emin + (r & (kTile - 1)), em);
+    const unsigned act = __activemask();
+    const unsigned wm = __reduce_max_sync(act, (unsigned)w);
+    if ((int)(threadIdx.x & 31) == __ffs((int)act) - 1 && wm) atomicMax(s_tex, wm);
   }
 };
+
+// the block's shared width and row minima start empty (before the block's split_body)
+__device__ __forceinline__ void mag_shared_init(unsigned int* s_tex, int* s_emin) {
+  if (threadIdx.x == 0) *s_tex = 0u;
+  if (threadIdx.x < kTile) s_emin[threadIdx.x] = kEminNone;
+}
+// after a barrier: the block's width into *tex (atomic maximum) and its row minima into emin (rows
+// r0 .. r0 + kTile of a side with R rows); then empty again
+__device__ __forceinline__ void mag_shared_flush(unsigned int* s_tex, int* s_emin, unsigned int* tex, int* emin,
+                                                 int64_t r0, int64_t R) {
+  if (threadIdx.x == 0 && *s_tex) {
+    atomicMax(tex, *s_tex);
+    *s_tex = 0u;
+  }
+  if (threadIdx.x < kTile) {
+    const int v = s_emin[threadIdx.x];
+    if (emin && v != kEminNone && r0 + threadIdx.x < R) atomicMin(emin + r0 + threadIdx.x, v);
+    s_emin[threadIdx.x] = kEminNone;
+  }
+}
 
 template <bool ROWS_CONTIG, class Writer>
 __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
@@ -468,7 +493,7 @@ __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t
       tile[ri][(pi & ~7) | ((pi ^ (pi >> 3)) & 7)] = (rg < R && pg < K) ? load_bits<true>(X, ld, rg, pg) : 0ull;
     }
     __syncthreads();
-    if (r >= R || pbase >= K) return;
+    if (r >= R || pbase >= K) return;  // no barrier follows in here (the grid-stride callers hold theirs)
     const int grp = pp0 >> 3;
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) x[v] = tile[rr][pp0 + (v ^ grp)];
@@ -524,6 +549,7 @@ __global__ void __launch_bounds__(256) k_magnitudes_batched(const PrepJob* __res
   else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum);
 }
 
+
 // block q: problem q, whose operand sides are jobs 2q (op(A)) and 2q+1 (op(B)^T)
 __global__ void __launch_bounds__(256) k_min_stats_batched(const PrepJob* __restrict__ jobs,
                                                            float* __restrict__ stats) {
@@ -559,24 +585,41 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
 // grouped modular problems: magnitude planes (FP8) and residues over a job table
 // FP8 planes (the certification), or BF16 planes for its retry: then only the jobs whose problem's
 // plan found no feasible precision, with the widths into the retry's words
+// RETRY: a grid-stride loop over the blocks that starts only when `run_if` is non-zero (some
+// problem's first plan found no feasible t), and skips the jobs whose plan is feasible
 template <bool FP8, bool RETRY>
-__global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const PrepJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const PrepJob* __restrict__ jobs, int njobs,
+                                                                    int64_t nblocks,
+                                                                    const unsigned int* __restrict__ run_if) {
   __shared__ uint64_t tile[kTile][kTile + 1];
-  const int ji = find_job(jobs, njobs, blockIdx.x, true);
-  const PrepJob& j = jobs[ji];
-  if (RETRY && j.plan->feasible) return;
-  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
-  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  int S = 15;  // the E5M2 plane scale; BF16: the largest with K 2^(2S) < 2^124
-  if (!FP8) {
-    int kb = 0;
-    while (((int64_t)1 << kb) < j.K) ++kb;
-    S = (124 - kb) / 2;
+  __shared__ unsigned int s_tex;
+  __shared__ int s_emin[kTile];
+  if (RETRY && *run_if == 0u) return;
+  mag_shared_init(&s_tex, s_emin);
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int ji = find_job(jobs, njobs, b, true);
+    const PrepJob& j = jobs[ji];
+    const bool live = !RETRY || !j.plan->feasible;  // uniform over the block
+    const int64_t local = b - j.split_begin;
+    const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+    if (live) {
+      int S = 15;  // the E5M2 plane scale; BF16: the largest with K 2^(2S) < 2^124
+      if (!FP8) {
+        int kb = 0;
+        while (((int64_t)1 << kb) < j.K) ++kb;
+        S = (124 - kb) / 2;
+      }
+      const int64_t pitch = FP8 ? (j.K + 15) / 16 * 16 : (j.K + 7) / 8 * 8;
+      const MagWriter<FP8> w{S, j.R, j.K, j.D, pitch, &s_tex, j.emin ? s_emin : nullptr};
+      if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+      else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+    }
+    __syncthreads();  // the block's width and row minima are complete (and the tile free)
+    mag_shared_flush(&s_tex, s_emin, RETRY ? j.tex + kCertRetry : j.tex, j.emin, by * kTile, j.R);
+    if (!RETRY) break;  // one block per grid index
+    __syncthreads();
   }
-  const int64_t pitch = FP8 ? (j.K + 15) / 16 * 16 : (j.K + 7) / 8 * 8;
-  const MagWriter<FP8> w{S, j.R, j.K, j.D, pitch, RETRY ? j.tex + kCertRetry : j.tex, j.emin};
-  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
-  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_batched(const PrepJob* __restrict__ jobs, int njobs,
@@ -794,6 +837,41 @@ __global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ Pre
 // drops parts below K 2^-126 in all.  So the computed value q satisfies
 // sum_p (x_p 2^-sig)^2 <= q (1 + (K + 9 nkr + 2) 2^-24 (1 + 2^-20)) + K 2^-126, and
 // q (1 + (K + 8 nkr + 64) 2^-22) + K 2^-125, rounded upward, covers it.
+// one row's merge of its block partials (in block order): sig, bad, mu (32.32) and the square-sum
+// bound (0 for a row without a non-zero finite entry)
+struct RowMerge {
+  int E, bad;
+  unsigned long long mu;
+  float sq_up;
+};
+__device__ __forceinline__ RowMerge merge_row(const int* __restrict__ pe, const float* __restrict__ ps,
+                                              const float* __restrict__ pq, const int* __restrict__ pb, int nkr,
+                                              float grow, float floor_add) {
+  RowMerge o;
+  int E = kExpEmpty, bd = 0;
+  for (int q = 0; q < nkr; ++q) {
+    E = max(E, pe[q]);
+    bd |= pb[q];
+  }
+  float mu = 0.0f, sq = 0.0f;
+  if (E != kExpEmpty)
+    for (int q = 0; q < nkr; ++q)
+      if (pe[q] != kExpEmpty) {
+        mu += ps[q] * pow2f_nonpos(pe[q] - E);
+        sq += pq[q] * pow2f_nonpos(2 * (pe[q] - E));
+      }
+  o.E = E;
+  o.bad = bd;
+  o.mu = magnitude_fixed(mu);
+  o.sq_up = E != kExpEmpty ? __fmaf_ru(sq, grow, floor_add) : 0.0f;
+  return o;
+}
+// the factor and the addend that raise a row's computed square sum to an upper bound (see below)
+__device__ __forceinline__ float square_grow(int64_t K, int nkr) {
+  return __fadd_ru(1.0f, __fmul_ru((float)(K + 8 * (int64_t)nkr + 64), 0x1p-22f));
+}
+__device__ __forceinline__ float square_floor(int64_t K) { return __fmul_ru((float)K, 0x1p-125f); }
+
 __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp,
                                                        const __grid_constant__ ExpMagParts parts) {
   __shared__ float s_mn[8];
@@ -801,34 +879,19 @@ __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ P
   __shared__ int s_bd[8];
   const int ji = blockIdx.y;
   const PrepJob& j = pp.j[ji];
-  const float grow = __fadd_ru(1.0f, __fmul_ru((float)(j.K + 8 * (int64_t)parts.nkr + 64), 0x1p-22f));
-  const float floor_add = __fmul_ru((float)j.K, 0x1p-125f);
+  const float grow = square_grow(j.K, parts.nkr), floor_add = square_floor(j.K);
   float mn = 3.0e38f, mx = 0.0f;
   int any_bad = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
-    const int* pe = parts.e[ji] + r * parts.nkr;
-    const float* ps = parts.s[ji] + r * parts.nkr;
-    const float* pq = parts.q[ji] + r * parts.nkr;
-    const int* pb = parts.b[ji] + r * parts.nkr;
-    int E = kExpEmpty, bd = 0;
-    for (int q = 0; q < parts.nkr; ++q) {
-      E = max(E, pe[q]);
-      bd |= pb[q];
-    }
-    float mu = 0.0f, sq = 0.0f;
-    if (E != kExpEmpty)
-      for (int q = 0; q < parts.nkr; ++q)
-        if (pe[q] != kExpEmpty) {
-          mu += ps[q] * pow2f_nonpos(pe[q] - E);
-          sq += pq[q] * pow2f_nonpos(2 * (pe[q] - E));
-        }
-    j.sig[r] = E;
-    j.bad[r] = bd;
-    const unsigned long long mq = magnitude_fixed(mu);
-    if (j.mu) j.mu[r] = mq;
-    if (mq > 0ull) mn = fminf(mn, magnitude_value(mq));
-    if (E != kExpEmpty) mx = fmaxf(mx, __fmaf_ru(sq, grow, floor_add));
-    any_bad |= bd;
+    const int64_t o = r * parts.nkr;
+    const RowMerge rm = merge_row(parts.e[ji] + o, parts.s[ji] + o, parts.q[ji] + o, parts.b[ji] + o, parts.nkr,
+                                  grow, floor_add);
+    j.sig[r] = rm.E;
+    j.bad[r] = rm.bad;
+    if (j.mu) j.mu[r] = rm.mu;
+    if (rm.mu > 0ull) mn = fminf(mn, magnitude_value(rm.mu));
+    mx = fmaxf(mx, rm.sq_up);
+    any_bad |= rm.bad;
   }
   for (int o = 16; o; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -852,6 +915,48 @@ __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ P
     if (mn < 3.0e38f) atomicMin(reinterpret_cast<int*>(parts.stats + ji), __float_as_int(mn));
     if (any_bad) atomicOr(reinterpret_cast<int*>(parts.stats + 2 + ji), __float_as_int(1.0f));
     if (parts.norms && mx > 0.0f) atomicMax(parts.norms + ji, __float_as_uint(mx));
+  }
+}
+
+// grouped modular problems: the one-pass exponent and magnitude partials of every job (as
+// k_expmag_pair), then one block per job merging its rows (as k_rowstats_pair, without the
+// minima), which also initialises emin and raises the side's largest square-sum bound into the
+// job's norm word
+__global__ void __launch_bounds__(256) k_expmag_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ int s_e[8][33];
+  __shared__ float s_s[8][33];
+  __shared__ float s_q[8][33];
+  __shared__ int s_b[8][33];
+  const int ji = find_job(jobs, njobs, blockIdx.x, false);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
+  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
+  if (j.rows_contig)
+    expmag_body<true>(j.X, j.ld, j.R, j.K, j.nkr, j.pe, j.ps, j.pq, j.pb, bx, by, s_e, s_s, s_q, s_b);
+  else
+    expmag_body<false>(j.X, j.ld, j.R, j.K, j.nkr, j.pe, j.ps, j.pq, j.pb, bx, by, s_e, s_s, s_q, s_b);
+}
+
+__global__ void __launch_bounds__(256) k_rowstats_batched(const PrepJob* __restrict__ jobs) {
+  __shared__ float s_mx[8];
+  const PrepJob& j = jobs[blockIdx.x];
+  const float grow = square_grow(j.K, j.nkr), floor_add = square_floor(j.K);
+  float mx = 0.0f;
+  for (int64_t r = threadIdx.x; r < j.R; r += blockDim.x) {
+    const int64_t o = r * j.nkr;
+    const RowMerge rm = merge_row(j.pe + o, j.ps + o, j.pq + o, j.pb + o, j.nkr, grow, floor_add);
+    j.sig[r] = rm.E;
+    j.bad[r] = rm.bad;
+    j.mu[r] = rm.mu;
+    j.emin[r] = kEminNone;
+    mx = fmaxf(mx, rm.sq_up);
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = fmaxf(mx, s_mx[q]);
+    if (mx > 0.0f) atomicMax(j.norm, __float_as_uint(mx));  // non-negative floats order as their bits
   }
 }
 
@@ -882,17 +987,30 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_pair(const __grid_
 // the magnitude planes of both sides (plane scale S, rows of kp elements): job j writes its D,
 // side j's width to tex[j]
 template <bool FP8>
+// a grid-stride loop over the nblocks blocks of both sides (a gated retry runs on a small grid
+// and returns at once when the certification it would repeat succeeded)
 __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_pair(const __grid_constant__ PrepPair pp, int S,
-                                                                 int64_t kp, unsigned int* tex, const ModPlan* gate) {
+                                                                 int64_t kp, unsigned int* tex, const ModPlan* gate,
+                                                                 int64_t nblocks) {
   __shared__ uint64_t tile[kTile][kTile + 1];
+  __shared__ unsigned int s_tex;
+  __shared__ int s_emin[kTile];
   if (gate && gate->feasible) return;  // the retry of a certification that already succeeded
-  const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
-  const PrepJob& j = pp.j[ji];
-  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
-  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
-  const MagWriter<FP8> w{S, j.R, j.K, j.D, kp, tex + ji, j.emin};
-  if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
-  else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+  mag_shared_init(&s_tex, s_emin);
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int ji = b >= pp.j[1].split_begin ? 1 : 0;
+    const PrepJob& j = pp.j[ji];
+    const int64_t local = b - j.split_begin;
+    const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+    const MagWriter<FP8> w{S, j.R, j.K, j.D, kp, &s_tex, j.emin ? s_emin : nullptr};
+    if (j.rows_contig) split_body<true>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+    else split_body<false>(j.X, j.ld, j.R, j.K, j.sig, bx, by, tile, w);
+    __syncthreads();  // the block's width and row minima are complete (and the tile free)
+    mag_shared_flush(&s_tex, s_emin, tex + ji, j.emin, by * kTile, j.R);
+    if ((int64_t)gridDim.x >= nblocks) break;  // one block per grid index
+    __syncthreads();
+  }
 }
 
 int launch_check(const char* what) {
@@ -1011,16 +1129,22 @@ int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, 
 }
 
 int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s, int prec,
-                            bool retry) {
+                            const unsigned int* retry_if) {
   if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
-  const unsigned g = (unsigned)split_blocks;
+  unsigned g = (unsigned)split_blocks;
+  if (retry_if) {
+    int sms = 0;
+    if (int rc = current_device(nullptr, &sms)) return rc;
+    const int64_t cap = 3 * (int64_t)sms;  // resident blocks of one wave
+    if ((int64_t)g > cap) g = (unsigned)cap;
+  }
   if (prec == kCertFP8) {
-    if (retry) k_magplane_batched<true, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
-    else k_magplane_batched<true, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    if (retry_if) k_magplane_batched<true, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if);
+    else k_magplane_batched<true, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr);
   } else {
-    if (retry) k_magplane_batched<false, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
-    else k_magplane_batched<false, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    if (retry_if) k_magplane_batched<false, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if);
+    else k_magplane_batched<false, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr);
   }
   return launch_check("batched magnitude plane launch");
 }
@@ -1044,6 +1168,16 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
   }
   k_min_stats_batched<<<njobs / 2, 256, 0, s>>>(jobs_dev, stats_dev);
   return launch_check("batched statistics launch");
+}
+
+int launch_expmag_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s) {
+  if (njobs <= 0 || exp_blocks <= 0) return GBD_OK;
+  if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many exponent blocks");
+  k_expmag_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
+  int rc = launch_check("batched exponent and magnitude launch");
+  if (rc) return rc;
+  k_rowstats_batched<<<(unsigned)njobs, 256, 0, s>>>(jobs_dev);
+  return launch_check("batched row statistics launch");
 }
 
 int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s) {
@@ -1112,11 +1246,19 @@ int launch_magplane_pair(const PrepPair& pp, int prec, unsigned int* tex, int64_
   if (split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
   const int64_t K = pp.j[0].K;
-  const unsigned g = (unsigned)split_blocks;
+  unsigned g = (unsigned)split_blocks;
+  if (gate) {  // a retry: usually returns at once, so one wave of blocks loops over the rest
+    int sms = 0;
+    if (int rc = current_device(nullptr, &sms)) return rc;
+    const int64_t cap = 3 * (int64_t)sms;
+    if ((int64_t)g > cap) g = (unsigned)cap;
+  }
   if (prec == kCertFP8)
-    k_magplane_pair<true><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate);
+    k_magplane_pair<true><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate,
+                                                      split_blocks);
   else
-    k_magplane_pair<false><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate);
+    k_magplane_pair<false><<<g, kSplitThreads, 0, s>>>(pp, plane_scale(K, prec), plane_pitch(K, prec), tex, gate,
+                                                       split_blocks);
   return launch_check("magnitude plane launch");
 }
 

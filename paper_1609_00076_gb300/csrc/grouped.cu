@@ -38,11 +38,14 @@ struct NativeTableEntry {
   const emu::ModPlan* only_if_infeasible;
 };
 
+// run_if: when given, the launch returns at once unless *run_if is non-zero (the fallback launch,
+// which has work only when some modular plan found no certified bit count)
 __global__ void __launch_bounds__(kNativeThreads)
     k_grouped_native(const NativeTableEntry* __restrict__ table, int count, int64_t total_tiles,
-                     unsigned long long* __restrict__ counter) {
+                     unsigned long long* __restrict__ counter, const unsigned int* __restrict__ run_if) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_tile;
+  if (run_if && *run_if == 0u) return;
   for (;;) {
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
     __syncthreads();
@@ -91,7 +94,11 @@ struct gbd_plan {
   std::vector<gbd::NativeTableEntry> native;
   int64_t native_tiles = 0;
   gbd::NativeTableEntry* native_dev = nullptr;
-  unsigned long long* counter_dev = nullptr;
+  unsigned long long* counter_dev = nullptr;  // [0] native launch, [1] fallback launch
+  // the FP64 fallbacks of the modular problems: a second launch, after the native table, that runs
+  // only when some modular plan found no certified bit count
+  std::vector<gbd::NativeTableEntry> fallback;
+  int64_t fallback_tiles = 0;
   // emulated part
   struct Emu {
     gbd_problem p;
@@ -299,7 +306,7 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   for (int q = 0; q < plan->mod.count; ++q) {
     NativeTableEntry t = native_entry(probs[plan->mod.index[q]], false);
     t.only_if_infeasible = plan->mod.plans[q];
-    plan->native.push_back(t);
+    plan->fallback.push_back(t);
   }
 
   // preparation jobs: op(A) and op(B)^T of every emulated problem
@@ -489,6 +496,14 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     nt += (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
   }
   plan->native_tiles = nt;
+  std::stable_sort(plan->fallback.begin(), plan->fallback.end(),
+                   [](const NativeTableEntry& a, const NativeTableEntry& b) { return a.a.k > b.a.k; });
+  int64_t ft = 0;
+  for (auto& t : plan->fallback) {
+    t.tile_begin = ft;
+    ft += (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
+  }
+  plan->fallback_tiles = ft;
   // tables to the device, through page-locked staging owned by the plan: the copies are stream-ordered
   // and need no synchronisation
   struct Part {
@@ -498,6 +513,8 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   };
   const Part parts[] = {
       {plan->native_dev, plan->native.data(), sizeof(NativeTableEntry) * plan->native.size()},
+      {plan->native_dev + plan->native.size(), plan->fallback.data(),
+       sizeof(NativeTableEntry) * plan->fallback.size()},
       {plan->emu_dev, plan->emu_table.data(), sizeof(emu::EmuTableEntry) * plan->emu_table.size()},
       {plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size()},
       {plan->mod.jobs_dev, plan->mod.jobs.data(), sizeof(emu::PrepJob) * plan->mod.jobs.size()},
@@ -552,10 +569,10 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
   }
   // modular: preparation, certification and plans on the device, then one persistent product launch
   if ((rc = emu::mod_grouped_run(plan->mod, sms, s))) return rc;
-  // native (and the fallbacks of modular problems whose plans found no certified bit count): one
-  // persistent launch over all tiles
-  if (plan->native_tiles > 0) {
-    if ((e = cudaMemsetAsync(plan->counter_dev, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+  // native: one persistent launch over all tiles; then the fallbacks of the modular problems whose
+  // plans found no certified bit count (a launch that returns at once when there is none)
+  if (plan->native_tiles > 0 || plan->fallback_tiles > 0) {
+    if ((e = cudaMemsetAsync(plan->counter_dev, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess)
       return cuda_fail(e, "grouped: counter reset");
     constexpr size_t smem = native_smem_bytes<64, 64>();
     e = cudaFuncSetAttribute(k_grouped_native, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -563,11 +580,20 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grouped_native, kNativeThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)sms * per_sm;
-    if (grid > plan->native_tiles) grid = plan->native_tiles;
-    k_grouped_native<<<(unsigned)grid, kNativeThreads, smem, s>>>(plan->native_dev, (int)plan->native.size(),
-                                                                 plan->native_tiles, plan->counter_dev);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped native launch");
+    const int64_t full = (int64_t)sms * per_sm;
+    if (plan->native_tiles > 0) {
+      const int64_t grid = full < plan->native_tiles ? full : plan->native_tiles;
+      k_grouped_native<<<(unsigned)grid, kNativeThreads, smem, s>>>(plan->native_dev, (int)plan->native.size(),
+                                                                   plan->native_tiles, plan->counter_dev, nullptr);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped native launch");
+    }
+    if (plan->fallback_tiles > 0) {
+      const int64_t grid = full < plan->fallback_tiles ? full : plan->fallback_tiles;
+      k_grouped_native<<<(unsigned)grid, kNativeThreads, smem, s>>>(
+          plan->native_dev + plan->native.size(), (int)plan->fallback.size(), plan->fallback_tiles,
+          plan->counter_dev + 1, plan->mod.flags_dev + 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped fallback launch");
+    }
   }
   return GBD_OK;
 }
