@@ -103,14 +103,15 @@ __global__ void __launch_bounds__(CertCfg<PAIR>::kThreads, 1)
   const int num_tiles = TABLE ? total_tiles : p.num_tiles;
   // the arguments and the tile coordinates of tile `tile` (grouped: of its problem)
   auto tile_args = [&](int tile, int& cur, int& tm, int& tn) -> const CertArgs* {
-    if (!TABLE) {
+    if constexpr (!TABLE) {
       tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
       return &p;  // a __grid_constant__ parameter: its address is that of the parameter itself
+    } else {
+      while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
+      const CertArgs* q = &table[cur].a;
+      tile_coords(tile - (int)table[cur].tile_begin, q->tiles_m, q->group_m, q->num_tiles, tm, tn);
+      return q;
     }
-    while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
-    const CertArgs* q = &table[cur].a;
-    tile_coords(tile - (int)table[cur].tile_begin, q->tiles_m, q->group_m, q->num_tiles, tm, tn);
-    return q;
   };
   // grouped retry: the tiles of a problem whose plan is already feasible are skipped by every role
   auto skipped = [&](const CertArgs& q) { return TABLE && q.gate && q.gate->feasible; };

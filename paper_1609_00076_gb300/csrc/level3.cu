@@ -12,8 +12,11 @@
 //          smaller, and each pays the emulation's fixed costs).
 //   DTRMM  one half through the recursion, the coupling block as one GEMM with beta = 1,
 //          ordered so every GEMM reads only blocks not yet overwritten.  A diagonal block of
-//          at most 512: the triangle packed with zeros (and a unit diagonal), one GEMM into
-//          scratch, copied back.
+//          at most 512: its strictly triangular part packed with zeros, one GEMM into scratch,
+//          and the diagonal applied in the update B := fma(alpha d, B, T).  Apart from the
+//          diagonal, the rows of the packed triangle keep their own scale: a large diagonal
+//          (a diagonally dominant triangle) would otherwise set the scale of its row, and the
+//          emulations could not certify the products of the row's small entries.
 //   DTRSM  the leading half solved, the trailing right-hand sides updated by one GEMM
 //          (beta = alpha folds the scaling in), the trailing half solved with alpha = 1.  The
 //          diagonal blocks of at most 64 are inverted together in one launch before the
@@ -85,17 +88,30 @@ __global__ void __launch_bounds__(256) k_tri_scale(double* __restrict__ C, int64
   if (upper ? i <= j : i >= j) C[j * ldc + i] = beta == 0.0 ? 0.0 : beta * C[j * ldc + i];
 }
 
-// D := the stored triangle of the b x b block of A at `a` (zeros elsewhere; a unit diagonal
-// written as 1 and not read)
+// D := the strictly triangular part of the b x b block of A at `a` (zeros on the diagonal and
+// off the triangle; the diagonal is not read)
 __global__ void __launch_bounds__(256) k_tri_pack(const double* __restrict__ a, int64_t lda, double* __restrict__ D,
-                                                  int64_t ldd, int64_t b, int upper, int unit) {
+                                                  int64_t ldd, int64_t b, int upper) {
   const int64_t i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
   const int64_t j = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5);
   if (i >= b || j >= b) return;
-  double v = 0.0;
-  if (i == j) v = unit ? 1.0 : a[j * lda + i];
-  else if (upper ? i < j : i > j) v = a[j * lda + i];
-  D[j * ldd + i] = v;
+  D[j * ldd + i] = (upper ? i < j : i > j) ? a[j * lda + i] : 0.0;
+}
+
+// X[i, j] := fma(alpha d_q, X[i, j], T[i, j]) over a rows x cols block, q = i (by_row) or j, with
+// d_q = 1 for a unit diagonal and otherwise the diagonal element q of the block of A at `a`
+// (columns in a grid-stride loop)
+__global__ void __launch_bounds__(256) k_diag_update(const double* __restrict__ a, int64_t lda, int unit,
+                                                     double alpha, const double* __restrict__ T, int64_t ldt,
+                                                     double* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+                                                     int by_row) {
+  const int64_t i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  if (i >= rows) return;
+  for (int64_t j = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5); j < cols; j += (int64_t)gridDim.y * 8) {
+    const int64_t q = by_row ? i : j;
+    const double d = unit ? 1.0 : a[q * lda + q];
+    X[j * ldx + i] = fma(alpha * d, X[j * ldx + i], T[j * ldt + i]);
+  }
 }
 
 // The diagonal blocks of the solve, inverted once per call: block q covers rows
@@ -204,6 +220,11 @@ __global__ void __launch_bounds__(32 * kTrsmVecs) k_trsm_apply(const double* __r
 }
 
 dim3 grid2(int64_t rows, int64_t cols) { return dim3((unsigned)((rows + 31) / 32), (unsigned)((cols + 7) / 8)); }
+// the same with the column blocks capped (kernels that loop over columns)
+dim3 grid2_capped(int64_t rows, int64_t cols) {
+  const int64_t gy = (cols + 7) / 8;
+  return dim3((unsigned)((rows + 31) / 32), (unsigned)(gy < 65535 ? (gy > 0 ? gy : 1) : 65535));
+}
 
 // ---------------------------------------------------------------------------- driver
 // One call's context: the GEMM dispatch and scratch.  In `dry` mode nothing is launched and
@@ -339,15 +360,18 @@ struct Tri {
     if (b <= kTrmmBase) {
       double* D = c->scr;
       double* T = c->scr + kTrmmBase * kTrmmBase;
-      if (!c->dry) k_tri_pack<<<grid2(b, b), 256, 0, c->s>>>(A + r0 * lda + r0, lda, D, b, b, upper, unit);
+      const double* Ab = A + r0 * lda + r0;
+      if (!c->dry) k_tri_pack<<<grid2(b, b), 256, 0, c->s>>>(Ab, lda, D, b, b, upper);
       if ((rc = c->check("triangle pack launch"))) return rc;
-      if (side == 0) {  // T := alpha op(D) B[r0:r1, :]
+      if (side == 0) {  // T := alpha op(D) B[r0:r1, :] (D strictly triangular); B := alpha diag B + T
         if ((rc = c->gemm(ta(), 'N', b, n, b, alpha, D, b, Brow(r0), ldb, 0.0, T, b))) return rc;
-        return c->copy2d(Brow(r0), ldb, T, b, b, n);
+        if (!c->dry) k_diag_update<<<grid2_capped(b, n), 256, 0, c->s>>>(Ab, lda, unit, alpha, T, b, Brow(r0), ldb, b, n, 1);
+        return c->check("diagonal update launch");
       }
-      // T := alpha B[:, r0:r1] op(D)
+      // T := alpha B[:, r0:r1] op(D); B := alpha B diag + T
       if ((rc = c->gemm('N', ta(), m, b, b, alpha, Bcol(r0), ldb, D, b, 0.0, T, m))) return rc;
-      return c->copy2d(Bcol(r0), ldb, T, m, m, b);
+      if (!c->dry) k_diag_update<<<grid2_capped(m, b), 256, 0, c->s>>>(Ab, lda, unit, alpha, T, m, Bcol(r0), ldb, m, b, 0);
+      return c->check("diagonal update launch");
     }
     const int64_t h = split_point(r0, r1);
     const bool lo = eff_lower();
