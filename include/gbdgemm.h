@@ -329,6 +329,11 @@ GBD_API int gbd_dgemm_emu_mod_host(char transa, char transb, int64_t m, int64_t 
  * not write overlapping parts of C. */
 typedef struct gbd_problem {
   char transa, transb;
+  uint8_t ksplit;  /* native: parts of the inner dimension per output tile, 2..16 (each part a
+                      separate work item, the parts' sums added in part order by the last one to
+                      finish: the same bits whatever order they run in), or 0/1 = none; capped at
+                      the problem's 16-deep k-blocks */
+  uint8_t reserved;  /* zero */
   int32_t mode;    /* GBD_MODE_NATIVE, GBD_MODE_EMULATED or GBD_MODE_MODULAR */
   int32_t slices;  /* emulated: 1..9, or 0 = certified automatically when the plan is created;
                       modular: integer bits 1..62, or 0 = certified on the device by every run */

@@ -1,13 +1,16 @@
-"""Measured tile selection for grouped native problems, cached as JSON.
+"""Measured schedule selection for grouped native problems, cached as JSON.
 
 The grouped FP64-MMA kernel can run each problem with 32 x 32 or 64 x 64 CTA
-tiles (gbd_problem.tile); both give the same bits (same k order, same
-epilogue), so the choice is purely about speed: small and ragged problems waste
-less work in 32 x 32 tiles, large ones keep more independent MMAs per warp in
-64 x 64 tiles.  The tuner times both on synthetic batches of each size bucket
-(bucket = floor(log2(sqrt(m*n))), i.e. the geometric mean of the output edges)
-and records the faster one.  Every measurement goes through the library's own
-grouped entry points; nothing here computes a GEMM.
+tiles (gbd_problem.tile) and with its inner dimension split into 2..16 parts per
+output tile (gbd_problem.ksplit; the parts' sums are added in part order, so a
+split is deterministic but rounds differently from the unsplit sum).  Small and
+ragged outputs waste less work in 32 x 32 tiles, large ones keep more
+independent MMAs per warp in 64 x 64 tiles; a small output with a deep k has few
+tiles, each a long chain, and splitting k gives the persistent grid more items to
+balance.  The tuner times the candidates on synthetic batches of each bucket
+(output bucket = floor(log2(sqrt(m*n))), the geometric mean of the output edges;
+k bucket = floor(log2(k))) and records the fastest.  Every measurement goes
+through the library's own grouped entry points; nothing here computes a GEMM.
 """
 from __future__ import annotations
 
@@ -18,11 +21,18 @@ import os
 from . import gbdgemm, synth
 
 CANDIDATES = (32, 64)
+KSPLITS = (1, 2, 4, 8)
+# split k only where an output bucket has few tiles: edges up to 2^SPLIT_MAX_BUCKET
+SPLIT_MAX_BUCKET = 8
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gbdgemm", "tune.json")
 
 
 def bucket_of(m: int, n: int) -> int:
     return int(math.floor(math.log2(max(1.0, math.sqrt(max(1, m) * max(1, n))))))
+
+
+def kbucket_of(k: int) -> int:
+    return int(math.floor(math.log2(max(1, k))))
 
 
 class Autotuner:
@@ -31,6 +41,7 @@ class Autotuner:
     def __init__(self, cache_path: str | None = None):
         self.cache_path = cache_path or os.environ.get("GBD_TUNE_CACHE", DEFAULT_CACHE)
         self.table: dict[str, dict] = {}
+        self.split_table: dict[str, dict] = {}
         self.load()
 
     # --- cache ---
@@ -39,8 +50,10 @@ class Autotuner:
             with open(self.cache_path) as f:
                 data = json.load(f)
             self.table = data.get("native_tile", {})
+            self.split_table = data.get("native_ksplit", {})
         except (OSError, ValueError):
             self.table = {}
+            self.split_table = {}
 
     def save(self) -> None:
         d = os.path.dirname(self.cache_path)
@@ -48,7 +61,8 @@ class Autotuner:
             os.makedirs(d, exist_ok=True)
         tmp = self.cache_path + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:
-            json.dump({"native_tile": self.table, "version": gbdgemm.gbd_version()}, f, indent=1, sort_keys=True)
+            json.dump({"native_tile": self.table, "native_ksplit": self.split_table, "version": gbdgemm.gbd_version()},
+                      f, indent=1, sort_keys=True)
         os.replace(tmp, self.cache_path)
 
     # --- lookup ---
@@ -57,11 +71,21 @@ class Autotuner:
         e = self.table.get(str(bucket_of(m, n)))
         return int(e["tile"]) if e else 0
 
+    def ksplit_for(self, m: int, n: int, k: int) -> int:
+        """Tuned inner-dimension split for an m x n x k problem, or 1 when untuned."""
+        e = self.split_table.get(f"{bucket_of(m, n)}_{kbucket_of(k)}")
+        return int(e["ksplit"]) if e else 1
+
     def apply(self, descriptors: list[dict]) -> list[dict]:
-        """Fills the 'tile' field of native problem descriptors (dicts of gbd_problem fields)."""
+        """Fills the 'tile' and 'ksplit' fields of native problem descriptors (dicts of gbd_problem
+        fields) that leave them at 0."""
         for d in descriptors:
-            if d.get("mode", 0) == gbdgemm.GBD_MODE_NATIVE and not d.get("tile"):
+            if d.get("mode", 0) != gbdgemm.GBD_MODE_NATIVE:
+                continue
+            if not d.get("tile"):
                 d["tile"] = self.tile_for(d["m"], d["n"], d.get("k", 0))
+            if not d.get("ksplit"):
+                d["ksplit"] = self.ksplit_for(d["m"], d["n"], d.get("k", 0))
         return descriptors
 
     # --- measurement ---
@@ -87,26 +111,61 @@ class Autotuner:
             for tile in CANDIDATES:
                 for p in probs:
                     p["tile"] = tile
-                arr = gbdgemm.problem_array(probs)
-                wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
-                ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-                rc, plan = gbdgemm.gbd_grouped_plan_create(arr, ws, wsb)
-                gbdgemm.check(rc)
-                try:
-                    gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan))  # warm-up
-                    best = float("inf")
-                    for _ in range(reps):
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        e0.record()
-                        gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan))
-                        e1.record()
-                        torch.cuda.synchronize()
-                        best = min(best, e0.elapsed_time(e1))
-                    timings[tile] = best
-                finally:
-                    gbdgemm.gbd_grouped_plan_destroy(plan)
+                timings[tile] = self._time_batch(probs, reps)
             tile = min(timings, key=timings.get)
             self.table[str(b)] = {"tile": tile, "ms": {str(t): v for t, v in timings.items()},
                                   "tflops": flops / (timings[tile] / 1e3) / 1e12}
         self.save()
         return self.table
+
+    def tune_native_ksplit(self, out_buckets=range(5, SPLIT_MAX_BUCKET + 1), k_buckets=range(9, 12),
+                           per_bucket: int = 8, reps: int = 3, seed: int = 11) -> dict:
+        """Times each split in KSPLITS on a synthetic batch per (output bucket, k bucket), with the
+        tuned (or default) tile of the output bucket; returns and caches the table."""
+        import torch
+        dev = torch.device("cuda")
+        for b in out_buckets:
+            for kb in k_buckets:
+                sizes = synth.log_uniform_sizes(seed + 17 * b + kb, per_bucket, 2 ** b, 2 ** (b + 1) - 1)
+                ks = synth.log_uniform_sizes(seed + 1000 + 17 * b + kb, per_bucket, 2 ** kb, 2 ** (kb + 1) - 1)[:, 2]
+                probs, keep = [], []
+                for i in range(per_bucket):
+                    m, n, k = int(sizes[i, 0]), int(sizes[i, 1]), int(ks[i])
+                    A = torch.from_numpy(synth.uniform_pm1(seed + 5 * i, m * k)).to(dev)
+                    B = torch.from_numpy(synth.uniform_pm1(seed + 5 * i + 1, k * n)).to(dev)
+                    C = torch.zeros(m * n, dtype=torch.float64, device=dev)
+                    keep += [A, B, C]
+                    probs.append(dict(transa="N", transb="N", mode=gbdgemm.GBD_MODE_NATIVE, m=m, n=n, k=k, alpha=1.0,
+                                      beta=0.0, A=A, lda=m, B=B, ldb=k, C=C, ldc=m, tile=self.tile_for(m, n)))
+                timings = {}
+                for ksplit in KSPLITS:
+                    for p in probs:
+                        p["ksplit"] = ksplit
+                    timings[ksplit] = self._time_batch(probs, reps)
+                best = min(timings, key=timings.get)
+                self.split_table[f"{b}_{kb}"] = {"ksplit": best, "ms": {str(t): v for t, v in timings.items()}}
+        self.save()
+        return self.split_table
+
+    @staticmethod
+    def _time_batch(probs, reps: int) -> float:
+        """Best device time (ms) of `reps` runs of one grouped plan over `probs`."""
+        import torch
+        arr = gbdgemm.problem_array(probs)
+        wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        rc, plan = gbdgemm.gbd_grouped_plan_create(arr, ws, wsb)
+        gbdgemm.check(rc)
+        try:
+            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan))  # warm-up
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan))
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best
+        finally:
+            gbdgemm.gbd_grouped_plan_destroy(plan)

@@ -36,6 +36,11 @@ struct NativeTableEntry {
   // the FP64 fallback of a modular problem: its tiles run only when the problem's device plan
   // found the target out of reach (otherwise the modular kernel computes it)
   const emu::ModPlan* only_if_infeasible;
+  // inner-dimension split: `ksplit` parts per tile (work items tile * ksplit + part), each
+  // tile's part slots at part + tile * ksplit * tile^2 and its arrival counter at done + tile
+  int32_t ksplit, nkb;
+  double* part;
+  unsigned int* done;
 };
 
 // run_if: when given, the launch returns at once unless *run_if is non-zero (the fallback launch,
@@ -61,18 +66,31 @@ __global__ void __launch_bounds__(kNativeThreads)
     const NativeTableEntry& e = table[lo];
     if (e.only_if_infeasible && e.only_if_infeasible->feasible) continue;  // uniform over the block
     const NativeArgs a = e.a;
-    const int64_t local = tile - e.tile_begin;
+    int64_t local = tile - e.tile_begin;
+    KSplit split;
+    const KSplit* ks = nullptr;
+    if (e.ksplit > 1) {  // item = output tile * ksplit + part
+      const int part = (int)(local % e.ksplit);
+      local /= e.ksplit;
+      split.kb0 = (int)((int64_t)part * e.nkb / e.ksplit);
+      split.kb1 = (int)((int64_t)(part + 1) * e.nkb / e.ksplit);
+      split.parts = e.ksplit;
+      split.index = part;
+      split.part = e.part + local * e.ksplit * (int64_t)e.tile * e.tile;
+      split.done = e.done + local;
+      ks = &split;
+    }
     const int64_t tm = local % e.tiles_m, tn = local / e.tiles_m;
     const int code = (e.ta << 2) | (e.tb << 1) | (e.tile == 32 ? 1 : 0);
     switch (code) {
-      case 0: native_tile<false, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
-      case 1: native_tile<false, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
-      case 2: native_tile<false, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
-      case 3: native_tile<false, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
-      case 4: native_tile<true, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
-      case 5: native_tile<true, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
-      case 6: native_tile<true, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw); break;
-      default: native_tile<true, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw); break;
+      case 0: native_tile<false, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw, ks); break;
+      case 1: native_tile<false, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw, ks); break;
+      case 2: native_tile<false, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw, ks); break;
+      case 3: native_tile<false, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw, ks); break;
+      case 4: native_tile<true, false, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw, ks); break;
+      case 5: native_tile<true, false, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw, ks); break;
+      case 6: native_tile<true, true, 64, 64, false>(a, nullptr, nullptr, tm * 64, tn * 64, smem_raw, ks); break;
+      default: native_tile<true, true, 32, 32, false>(a, nullptr, nullptr, tm * 32, tn * 32, smem_raw, ks); break;
     }
   }
 }
@@ -94,6 +112,10 @@ struct gbd_plan {
   std::vector<gbd::NativeTableEntry> native;
   int64_t native_tiles = 0;
   gbd::NativeTableEntry* native_dev = nullptr;
+  // split-k native problems: their tiles' part slots and arrival counters (zeroed by the plan)
+  double* ksplit_parts = nullptr;
+  unsigned int* ksplit_done = nullptr;
+  size_t ksplit_done_count = 0;
   unsigned long long* counter_dev = nullptr;  // [0] native launch, [1] fallback launch
   // the FP64 fallbacks of the modular problems: a second launch, after the native table, that runs
   // only when some modular plan found no certified bit count
@@ -139,9 +161,35 @@ bool pair_class(const gbd_problem& p) {
   return p.m >= emu::kGroupedPairMinMN && p.n >= emu::kGroupedPairMinMN && p.k >= emu::kGroupedPairMinK;
 }
 
+int default_tile(int64_t, int64_t);
+
+// the effective inner-dimension split of a native problem (1: none)
+int native_ksplit(const gbd_problem& p) {
+  const bool quick = p.m == 0 || p.n == 0 || p.alpha == 0.0 || p.k == 0;
+  if (p.mode != GBD_MODE_NATIVE || quick || p.ksplit <= 1) return 1;
+  const int64_t nkb = (p.k + kNativeBK - 1) / kNativeBK;
+  return (int)(p.ksplit < nkb ? p.ksplit : nkb);
+}
+int native_edge(const gbd_problem& p) { return p.tile ? p.tile : default_tile(p.m, p.n); }
+int64_t native_tiles_of(const gbd_problem& p, int edge) { return ((p.m + edge - 1) / edge) * ((p.n + edge - 1) / edge); }
+
 // Layout of the grouped workspace; with base == nullptr only the size is computed.
 size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_override, void* base, gbd_plan* plan) {
-  size_t off = 256;  // tile counter
+  size_t off = 256;  // tile counters (native launch, fallback launch)
+  // split-k native problems: part slots (one tile of doubles per part) and a counter per tile
+  size_t ks_doubles = 0, ks_counters = 0;
+  for (int i = 0; i < count; ++i) {
+    const int S = native_ksplit(probs[i]);
+    if (S <= 1) continue;
+    const int e = native_edge(probs[i]);
+    const int64_t t = native_tiles_of(probs[i], e);
+    ks_doubles += (size_t)t * S * e * e;
+    ks_counters += (size_t)t;
+  }
+  const size_t o_ksp = off;
+  off = up256(off + sizeof(double) * ks_doubles);
+  const size_t o_ksd = off;
+  off = up256(off + sizeof(unsigned int) * ks_counters);
   const size_t o_native = off;
   int nnat = 0, nemu = 0;
   for (int i = 0; i < count; ++i) {
@@ -197,6 +245,9 @@ size_t grouped_layout(const gbd_problem* probs, int count, const int* slices_ove
   }
   if (base && plan) {
     plan->counter_dev = reinterpret_cast<unsigned long long*>(base);
+    plan->ksplit_parts = reinterpret_cast<double*>(static_cast<char*>(base) + o_ksp);
+    plan->ksplit_done = reinterpret_cast<unsigned int*>(static_cast<char*>(base) + o_ksd);
+    plan->ksplit_done_count = ks_counters;
     plan->native_dev = reinterpret_cast<NativeTableEntry*>(static_cast<char*>(base) + o_native);
     plan->emu_dev = reinterpret_cast<emu::EmuTableEntry*>(static_cast<char*>(base) + o_emu);
     plan->jobs_dev = reinterpret_cast<emu::PrepJob*>(static_cast<char*>(base) + o_jobs);
@@ -222,6 +273,8 @@ NativeTableEntry native_entry(const gbd_problem& p, bool quick) {
   t.tb = trans_code(p.transb);
   t.tile = p.tile ? p.tile : default_tile(p.m, p.n);
   t.tiles_m = (int32_t)((p.m + t.tile - 1) / t.tile);
+  t.ksplit = quick ? 1 : native_ksplit(p);
+  t.nkb = (int32_t)((a.k + kNativeBK - 1) / kNativeBK);
   return t;
 }
 
@@ -239,6 +292,7 @@ int validate(const gbd_problem* probs, int count) {
       return set_error(GBD_ERR_ARG, "grouped problem %d: bits %d (0 automatic, or 1..62)", i, p.slices);
     if (p.tile != 0 && p.tile != 32 && p.tile != 64)
       return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0, 32 or 64)", i, p.tile);
+    if (p.ksplit > 16) return set_error(GBD_ERR_ARG, "grouped problem %d: ksplit %d (0..16)", i, (int)p.ksplit);
     const int64_t lim = (int64_t)1 << 31;
     if (p.m >= lim || p.n >= lim || p.k >= lim || (p.m + 63) / 64 > 65535 || (p.n + 63) / 64 > 65535)
       return set_error(GBD_ERR_LIMIT, "grouped problem %d: size beyond the supported range", i);
@@ -491,11 +545,22 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
   std::stable_sort(plan->native.begin(), plan->native.end(),
                    [](const NativeTableEntry& a, const NativeTableEntry& b) { return a.a.k > b.a.k; });
   int64_t nt = 0;
+  size_t ks_at = 0, ks_tile = 0;  // running offsets into the part slots and the counters
   for (auto& t : plan->native) {
     t.tile_begin = nt;
-    nt += (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
+    const int64_t tiles = (int64_t)t.tiles_m * ((t.a.n + t.tile - 1) / t.tile);
+    if (t.ksplit > 1) {
+      t.part = plan->ksplit_parts + ks_at;
+      t.done = plan->ksplit_done + ks_tile;
+      ks_at += (size_t)tiles * t.ksplit * t.tile * t.tile;
+      ks_tile += (size_t)tiles;
+    }
+    nt += tiles * (t.ksplit > 1 ? t.ksplit : 1);
   }
   plan->native_tiles = nt;
+  if (plan->ksplit_done_count &&
+      (e = cudaMemsetAsync(plan->ksplit_done, 0, sizeof(unsigned int) * plan->ksplit_done_count, s)) != cudaSuccess)
+    return cuda_fail(e, "grouped: clearing the split-k counters");
   std::stable_sort(plan->fallback.begin(), plan->fallback.end(),
                    [](const NativeTableEntry& a, const NativeTableEntry& b) { return a.a.k > b.a.k; });
   int64_t ft = 0;

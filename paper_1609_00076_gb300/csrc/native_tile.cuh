@@ -35,13 +35,25 @@ constexpr size_t native_smem_bytes() {
   return (size_t)kNativeStages * (BM * kNativeBK + kNativeBK * BN) * sizeof(double) + kNativeStages * sizeof(uint64_t);
 }
 
+// One part of a tile whose inner dimension is split (grouped problems with a small output
+// and a deep k): the part's k-blocks [kb0, kb1), its slot of BM x BN doubles in `part` (the
+// tile's `parts` slots in part order) and the tile's arrival counter.  The last part to
+// arrive adds the slots in part order, so the sum is the same whatever order the parts run in,
+// applies the epilogue and clears the counter for the next run.
+struct KSplit {
+  int kb0, kb1;
+  int parts, index;
+  double* part;
+  unsigned int* done;
+};
+
 // One BM x BN tile of C at (m0, n0): staged mainloop and fused epilogue.  Shared by
 // the single-problem kernel and the persistent grouped kernel (grouped.cu), so a
 // problem gets the same bits alone and inside a batch.
 template <bool TA, bool TB, int BM, int BN, bool USE_TMA>
 __device__ __forceinline__ void native_tile(const NativeArgs& p, const CUtensorMap* tmA_p,
                                             const CUtensorMap* tmB_p, int64_t m0, int64_t n0,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw, const KSplit* ks = nullptr) {
   constexpr int A_EL = BM * kNativeBK, B_EL = kNativeBK * BN;
   constexpr int WM = BM / 2, WN = BN / 2, MI = WM / 16, NI = WN / 8;
   static_assert(MI >= 1 && NI >= 1, "warp tile too small");
@@ -51,7 +63,9 @@ __device__ __forceinline__ void native_tile(const NativeArgs& p, const CUtensorM
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int nkb = (int)((p.k + kNativeBK - 1) / kNativeBK);
+  // the k-blocks of this tile (all of them, or one part's)
+  const int kbase = ks ? ks->kb0 : 0;
+  const int nkb = ks ? ks->kb1 - ks->kb0 : (int)((p.k + kNativeBK - 1) / kNativeBK);
   const int wm0 = (warp >> 1) * WM, wn0 = (warp & 1) * WN;
 
   __syncthreads();  // the shared memory of a previous tile is no longer in use
@@ -63,10 +77,10 @@ __device__ __forceinline__ void native_tile(const NativeArgs& p, const CUtensorM
   }
   __syncthreads();
 
-  // stage kb of the k loop into ring slot kb % kNativeStages
+  // stage kb of the tile's k loop into ring slot kb % kNativeStages
   auto issue = [&](int kb) {
     const int s = kb % kNativeStages;
-    const int64_t k0 = (int64_t)kb * kNativeBK;
+    const int64_t k0 = (int64_t)(kbase + kb) * kNativeBK;
     if (USE_TMA) {
       if (tid == 0 && kb < nkb) {
         mbar_arrive_expect_tx(&full[s], (uint32_t)((A_EL + B_EL) * sizeof(double)));
@@ -162,6 +176,25 @@ __device__ __forceinline__ void native_tile(const NativeArgs& p, const CUtensorM
       sC[(c + 1) * LDS + r + 8] = acc[mi][ni][3];
     }
   __syncthreads();
+  if (ks) {
+    // this part's sums into its slot; the last part to arrive adds all slots in part order
+    __shared__ unsigned int s_last;
+    double* mine = ks->part + (int64_t)ks->index * BM * BN;
+    for (int idx = tid; idx < BM * BN; idx += kNativeThreads) mine[idx] = sC[(idx / BM) * LDS + idx % BM];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ks->done, 1u) == (unsigned)(ks->parts - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int idx = tid; idx < BM * BN; idx += kNativeThreads) {
+      double v = __ldcg(ks->part + idx);
+      for (int q = 1; q < ks->parts; ++q) v += __ldcg(ks->part + (int64_t)q * BM * BN + idx);
+      sC[(idx / BM) * LDS + idx % BM] = v;
+    }
+    if (tid == 0) *ks->done = 0u;  // ready for the next run of the plan
+    __syncthreads();
+  }
   const double alpha = p.alpha, beta = p.beta;
   for (int jj = warp; jj < BN; jj += kNativeThreads / 32) {
     const int64_t j = n0 + jj;

@@ -104,7 +104,8 @@ GBD_PATH_NATIVE = 3
 
 class GbdProblem(ctypes.Structure):
     """Mirror of gbd_problem (one problem of a grouped call)."""
-    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char), ("mode", ctypes.c_int32),
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char), ("ksplit", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8), ("mode", ctypes.c_int32),
                 ("slices", ctypes.c_int32), ("tile", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("k", ctypes.c_int64), ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("A", ctypes.c_void_p),
                 ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p),

@@ -53,6 +53,7 @@ def test_problem_struct_layout(lib):
     P = gbdgemm.GbdProblem
     assert ctypes.sizeof(P) == 112
     assert P.m.offset == 16 and P.A.offset == 56 and P.tol.offset == 104
+    assert P.ksplit.offset == 2 and P.mode.offset == 4  # ksplit sits in what was padding
 
 
 def test_grouped_argument_errors_without_gpu(lib):
@@ -67,6 +68,23 @@ def test_grouped_argument_errors_without_gpu(lib):
     bad[0]["mode"] = 7
     rc, _ = gbdgemm.gbd_grouped_plan_create(bad, 0, ws, stream=0)
     assert rc == gbdgemm.GBD_ERR_ARG and "mode 7" in gbdgemm.gbd_last_error()
+    bad[0]["mode"] = 0
+    bad[0]["ksplit"] = 17
+    rc, _ = gbdgemm.gbd_grouped_plan_create(bad, 0, ws, stream=0)
+    assert rc == gbdgemm.GBD_ERR_ARG and "ksplit 17" in gbdgemm.gbd_last_error()
+
+
+def test_ksplit_workspace_is_host_only(lib):
+    # split-k native problems need part slots (one tile of doubles per part) and tile counters
+    base = dict(transa="N", transb="N", mode=0, m=40, n=40, k=4096, alpha=1.0, beta=0.0, A=0, lda=40, B=0,
+                ldb=4096, C=0, ldc=40, tile=32)
+    w1 = gbdgemm.gbd_dgemm_grouped_workspace_size([dict(base, ksplit=1)])
+    w8 = gbdgemm.gbd_dgemm_grouped_workspace_size([dict(base, ksplit=8)])
+    assert w8 >= w1 + 4 * 8 * 32 * 32 * 8  # 2 x 2 tiles of 32, 8 parts each
+    # a split beyond the 16-deep k-blocks is capped: k = 32 has two
+    w16 = gbdgemm.gbd_dgemm_grouped_workspace_size([dict(base, k=32, ldb=32, ksplit=16)])
+    w2 = gbdgemm.gbd_dgemm_grouped_workspace_size([dict(base, k=32, ldb=32, ksplit=2)])
+    assert w16 == w2
 
 
 def test_emu_workspace_size_is_host_only(lib):
