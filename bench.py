@@ -420,7 +420,7 @@ def run_ours(args, world, rank, local, pg):
     # ---- the FP64 tensor-core rate of this GPU (the native path's roofline), measured ----
     rc_probe, fp64_peak = gbdgemm.gbd_fp64_mma_probe(2000, stream=stream)  # about 0.3 s
     gbdgemm.check(rc_probe)
-    # ---- configuration 3's wider exponent ranges (rank 0; the headline's inputs are overwritten) ----
+    # ---- the 8192^3 workload with wider exponent ranges (rank 0; the headline's inputs are overwritten) ----
     e_legs = exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb) if rank == 0 else None
     del ws, split_ws
     # ---- grouped batch of 512 uneven problems, the serving loop, level-3 BLAS (rank 0, default size only) ----
@@ -632,7 +632,7 @@ def level3_measure(dev, stream, n: int = 8192, seed: int = 6000):
 
 def exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb, es=(8, 32), seed: int = 2100, calls: int = 3,
                   sample_rows: int = 16):
-    """Configuration 3's wider exponent ranges: entries uniform[-1,1) * 2^U, U uniform on {-e..e}.
+    """The 8192^3 workload with wider exponent ranges: entries uniform[-1,1) * 2^U, U uniform on {-e..e}.
     Each leg takes the fastest certified path (the modular emulation, else the split one, which
     computes natively when no slice count is certified), as gbd_ctx_dgemm's automatic method does;
     reports the path, its precision, the time per call and the error against the oracle on sampled
@@ -697,7 +697,7 @@ def exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb, es=(8, 32)
 
 
 def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
-    """Configuration 4: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
+    """The grouped batch: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
     uniform[-1,1).  Native problems take the autotuner's tile per output bucket and inner-dimension
     split per (output, k) bucket (measured here first; also timed without the split); every plan
     run is captured once in a CUDA graph and replayed.  Modes: native FP64; modular (certified and
@@ -784,7 +784,7 @@ def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int =
 
 
 def serving_measure(requests: int = 2000, seed: int = 5000):
-    """Configuration 5: the saturated rate of the mixed request stream (all requests at once), then
+    """The served request stream: the saturated rate of the mixed stream (all requests at once), then
     Poisson streams of `requests` requests at 0.5, 0.8 and 0.95 of it: p50/p99 latency and TFLOP/s
     per rate."""
     from paper_1609_00076_gb300 import serving

@@ -68,7 +68,7 @@ def check_against_oracle(oracle_mod, ta, tb, m, n, k, alpha, A, lda, B, ldb, bet
     assert msg is None, msg
 
 
-# --- configuration 1: 256^3, N,N, alpha=1, beta=0 (uniform and small integers) ---
+# --- 256^3, N,N, alpha=1, beta=0 (uniform and small integers) ---
 def test_square_256_uniform(oracle_mod):
     m = n = k = 256
     A, lda, B, ldb, C, ldc = _problem("N", "N", m, n, k, "uniform", synth.seed_for(0))
@@ -83,7 +83,7 @@ def test_square_256_integers_bit_exact(oracle_mod):
     check_against_oracle(oracle_mod, "N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, out, exact=True)
 
 
-# --- configuration 2: 1000 x 1200 x 800, four transposes, ld + 8, alpha 1.5, beta -0.5 ---
+# --- 1000 x 1200 x 800, four transposes, ld + 8, alpha 1.5, beta -0.5 ---
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 def test_padded_ld_all_transposes(oracle_mod, ta, tb):
     m, n, k = 1000, 1200, 800
@@ -176,7 +176,7 @@ def test_deterministic_and_stream():
     assert np.array_equal(o1.view(np.uint64), o2.view(np.uint64))
 
 
-# --- configuration 3 (native leg): 8192^3 at the bench's launch, sampled rows ---
+# --- 8192^3 (native leg) at the bench's launch, sampled rows ---
 @pytest.mark.parametrize("e", [0, 8, 32])
 def test_large_square_sampled_rows(oracle_mod, e):
     import torch
