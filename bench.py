@@ -699,7 +699,8 @@ def exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb, es=(8, 32)
 def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
     """The grouped batch: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
     uniform[-1,1).  Native problems take the autotuner's tile per output bucket and inner-dimension
-    split per (output, k) bucket (measured here first; also timed without the split); every plan
+    split per (output, k) bucket, split-emulated ones its kernel class per (output, k) bucket
+    (measured here first; native also timed without the split); every plan
     run is captured once in a CUDA graph and replayed.  Modes: native FP64; modular (certified and
     planned on the device in every replay); split digits (slices certified when the plan is
     made).  TFLOP/s of graph replays (best of `reps`)."""
@@ -731,10 +732,12 @@ def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int =
     tuner = autotune.Autotuner(cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"))
     tuner.tune_native_tiles(per_bucket=8, reps=2)
     tuner.tune_native_ksplit(per_bucket=32, reps=2)
+    tuner.tune_emulated_class(per_bucket=8, reps=2)
     tune_s = time.perf_counter() - t0
     out = {"problems": count, "flops_per_batch": flops, "graph": True,
            "autotuner": {"seconds": tune_s, "native_tile_by_bucket": {b: e["tile"] for b, e in tuner.table.items()},
-                         "native_ksplit_by_bucket": {b: e["ksplit"] for b, e in tuner.split_table.items()}}}
+                         "native_ksplit_by_bucket": {b: e["ksplit"] for b, e in tuner.split_table.items()},
+                         "emulated_class_by_bucket": {b: e["tile"] for b, e in tuner.emu_table.items()}}}
     for name, mode in (("native", gbdgemm.GBD_MODE_NATIVE), ("native_no_ksplit", gbdgemm.GBD_MODE_NATIVE),
                        ("emulated", gbdgemm.GBD_MODE_MODULAR), ("emulated_split", gbdgemm.GBD_MODE_EMULATED)):
         desc = [dict(p, mode=mode) for p in base]

@@ -7,7 +7,9 @@ split is deterministic but rounds differently from the unsplit sum).  Small and
 ragged outputs waste less work in 32 x 32 tiles, large ones keep more
 independent MMAs per warp in 64 x 64 tiles; a small output with a deep k has few
 tiles, each a long chain, and splitting k gives the persistent grid more items to
-balance.  The tuner times the candidates on synthetic batches of each bucket
+balance.  For emulated (split) problems the tile field names the kernel class:
+128 the one-SM 128 x 128 kernel, 256 the two-SM 256 x 256 kernel (same bits
+either way).  The tuner times the candidates on synthetic batches of each bucket
 (output bucket = floor(log2(sqrt(m*n))), the geometric mean of the output edges;
 k bucket = floor(log2(k))) and records the fastest.  Every measurement goes
 through the library's own grouped entry points; nothing here computes a GEMM.
@@ -22,6 +24,7 @@ from . import gbdgemm, synth
 
 CANDIDATES = (32, 64)
 KSPLITS = (1, 2, 4, 8)
+EMU_CLASSES = (128, 256)
 # split k only where an output bucket has few tiles: edges up to 2^SPLIT_MAX_BUCKET
 SPLIT_MAX_BUCKET = 8
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gbdgemm", "tune.json")
@@ -42,6 +45,7 @@ class Autotuner:
         self.cache_path = cache_path or os.environ.get("GBD_TUNE_CACHE", DEFAULT_CACHE)
         self.table: dict[str, dict] = {}
         self.split_table: dict[str, dict] = {}
+        self.emu_table: dict[str, dict] = {}
         self.load()
 
     # --- cache ---
@@ -51,9 +55,11 @@ class Autotuner:
                 data = json.load(f)
             self.table = data.get("native_tile", {})
             self.split_table = data.get("native_ksplit", {})
+            self.emu_table = data.get("emulated_class", {})
         except (OSError, ValueError):
             self.table = {}
             self.split_table = {}
+            self.emu_table = {}
 
     def save(self) -> None:
         d = os.path.dirname(self.cache_path)
@@ -61,8 +67,8 @@ class Autotuner:
             os.makedirs(d, exist_ok=True)
         tmp = self.cache_path + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:
-            json.dump({"native_tile": self.table, "native_ksplit": self.split_table, "version": gbdgemm.gbd_version()},
-                      f, indent=1, sort_keys=True)
+            json.dump({"native_tile": self.table, "native_ksplit": self.split_table, "emulated_class": self.emu_table,
+                       "version": gbdgemm.gbd_version()}, f, indent=1, sort_keys=True)
         os.replace(tmp, self.cache_path)
 
     # --- lookup ---
@@ -76,11 +82,21 @@ class Autotuner:
         e = self.split_table.get(f"{bucket_of(m, n)}_{kbucket_of(k)}")
         return int(e["ksplit"]) if e else 1
 
+    def emulated_class_for(self, m: int, n: int, k: int) -> int:
+        """Tuned kernel class (128 or 256) of an emulated m x n x k problem, or 0 (library default)."""
+        e = self.emu_table.get(f"{bucket_of(m, n)}_{kbucket_of(k)}")
+        return int(e["tile"]) if e else 0
+
     def apply(self, descriptors: list[dict]) -> list[dict]:
-        """Fills the 'tile' and 'ksplit' fields of native problem descriptors (dicts of gbd_problem
-        fields) that leave them at 0."""
+        """Fills the 'tile' and 'ksplit' fields of native problem descriptors, and the 'tile' (kernel
+        class) of emulated ones, where they are left at 0 (dicts of gbd_problem fields)."""
         for d in descriptors:
-            if d.get("mode", 0) != gbdgemm.GBD_MODE_NATIVE:
+            mode = d.get("mode", 0)
+            if mode == gbdgemm.GBD_MODE_EMULATED:
+                if not d.get("tile"):
+                    d["tile"] = self.emulated_class_for(d["m"], d["n"], d.get("k", 0))
+                continue
+            if mode != gbdgemm.GBD_MODE_NATIVE:
                 continue
             if not d.get("tile"):
                 d["tile"] = self.tile_for(d["m"], d["n"], d.get("k", 0))
@@ -146,6 +162,35 @@ class Autotuner:
                 self.split_table[f"{b}_{kb}"] = {"ksplit": best, "ms": {str(t): v for t, v in timings.items()}}
         self.save()
         return self.split_table
+
+    def tune_emulated_class(self, out_buckets=range(8, 12), k_buckets=range(9, 12), per_bucket: int = 8,
+                            reps: int = 2, seed: int = 13, slices: int = 7) -> dict:
+        """Times the one-SM and two-SM kernel classes on a synthetic batch of split-emulated problems
+        per (output bucket, k bucket) at a fixed slice count; returns and caches the table."""
+        import torch
+        dev = torch.device("cuda")
+        for b in out_buckets:
+            for kb in k_buckets:
+                sizes = synth.log_uniform_sizes(seed + 17 * b + kb, per_bucket, 2 ** b, 2 ** (b + 1) - 1)
+                ks = synth.log_uniform_sizes(seed + 1000 + 17 * b + kb, per_bucket, 2 ** kb, 2 ** (kb + 1) - 1)[:, 2]
+                probs, keep = [], []
+                for i in range(per_bucket):
+                    m, n, k = int(sizes[i, 0]), int(sizes[i, 1]), int(ks[i])
+                    A = torch.from_numpy(synth.uniform_pm1(seed + 5 * i, m * k)).to(dev)
+                    B = torch.from_numpy(synth.uniform_pm1(seed + 5 * i + 1, k * n)).to(dev)
+                    C = torch.zeros(m * n, dtype=torch.float64, device=dev)
+                    keep += [A, B, C]
+                    probs.append(dict(transa="N", transb="N", mode=gbdgemm.GBD_MODE_EMULATED, slices=slices, m=m, n=n,
+                                      k=k, alpha=1.0, beta=0.0, A=A, lda=m, B=B, ldb=k, C=C, ldc=m))
+                timings = {}
+                for tile in EMU_CLASSES:
+                    for p in probs:
+                        p["tile"] = tile
+                    timings[tile] = self._time_batch(probs, reps)
+                best = min(timings, key=timings.get)
+                self.emu_table[f"{b}_{kb}"] = {"tile": best, "ms": {str(t): v for t, v in timings.items()}}
+        self.save()
+        return self.emu_table
 
     @staticmethod
     def _time_batch(probs, reps: int) -> float:

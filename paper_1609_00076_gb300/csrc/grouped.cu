@@ -157,7 +157,10 @@ namespace gbd {
 namespace {
 
 // Emulated problems large enough for the two-SM 256 x 256 kernel
+// (the tile field chooses it: 256 the two-SM kernel, 128 the one-SM kernel, 0 this default)
 bool pair_class(const gbd_problem& p) {
+  if (p.tile == 256) return true;
+  if (p.tile == 128) return false;
   return p.m >= emu::kGroupedPairMinMN && p.n >= emu::kGroupedPairMinMN && p.k >= emu::kGroupedPairMinK;
 }
 
@@ -170,7 +173,7 @@ int native_ksplit(const gbd_problem& p) {
   const int64_t nkb = (p.k + kNativeBK - 1) / kNativeBK;
   return (int)(p.ksplit < nkb ? p.ksplit : nkb);
 }
-int native_edge(const gbd_problem& p) { return p.tile ? p.tile : default_tile(p.m, p.n); }
+int native_edge(const gbd_problem& p) { return (p.mode == GBD_MODE_NATIVE && p.tile) ? p.tile : default_tile(p.m, p.n); }
 int64_t native_tiles_of(const gbd_problem& p, int edge) { return ((p.m + edge - 1) / edge) * ((p.n + edge - 1) / edge); }
 
 // Layout of the grouped workspace; with base == nullptr only the size is computed.
@@ -271,7 +274,7 @@ NativeTableEntry native_entry(const gbd_problem& p, bool quick) {
   a.vec_c = ((reinterpret_cast<uintptr_t>(p.C) & 15u) == 0 && (p.ldc & 1) == 0) ? 1 : 0;
   t.ta = trans_code(p.transa);
   t.tb = trans_code(p.transb);
-  t.tile = p.tile ? p.tile : default_tile(p.m, p.n);
+  t.tile = (p.mode == GBD_MODE_NATIVE && p.tile) ? p.tile : default_tile(p.m, p.n);  // emulated tiles name kernels
   t.tiles_m = (int32_t)((p.m + t.tile - 1) / t.tile);
   t.ksplit = quick ? 1 : native_ksplit(p);
   t.nkb = (int32_t)((a.k + kNativeBK - 1) / kNativeBK);
@@ -290,8 +293,12 @@ int validate(const gbd_problem* probs, int count) {
       return set_error(GBD_ERR_ARG, "grouped problem %d: slices %d", i, p.slices);
     if (p.mode == GBD_MODE_MODULAR && (p.slices < 0 || p.slices > 62))
       return set_error(GBD_ERR_ARG, "grouped problem %d: bits %d (0 automatic, or 1..62)", i, p.slices);
-    if (p.tile != 0 && p.tile != 32 && p.tile != 64)
+    if (p.mode == GBD_MODE_NATIVE && p.tile != 0 && p.tile != 32 && p.tile != 64)
       return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0, 32 or 64)", i, p.tile);
+    if (p.mode == GBD_MODE_EMULATED && p.tile != 0 && p.tile != 128 && p.tile != 256)
+      return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0, 128 or 256)", i, p.tile);
+    if (p.mode == GBD_MODE_MODULAR && p.tile != 0 && p.tile != 128)
+      return set_error(GBD_ERR_ARG, "grouped problem %d: tile %d (0 or 128)", i, p.tile);
     if (p.ksplit > 16) return set_error(GBD_ERR_ARG, "grouped problem %d: ksplit %d (0..16)", i, (int)p.ksplit);
     const int64_t lim = (int64_t)1 << 31;
     if (p.m >= lim || p.n >= lim || p.k >= lim || (p.m + 63) / 64 > 65535 || (p.n + 63) / 64 > 65535)

@@ -4,7 +4,8 @@ Bars: with ksplit parts per tile, every result is within the FP64 bound of the D
 (the parts' sums add k/S-deep partial sums, still a recursive sum over k); the bits do not
 depend on the order the parts run in (two runs and a CUDA-graph replay agree bit for bit, and
 the counters are ready for the next run); ksplit = 1 gives gbd_dgemm's bits; the tuner's
-table, applied to a batch, keeps those properties.
+table, applied to a batch, keeps those properties; an emulated problem's kernel class (the
+tile field: one-SM or two-SM) does not change its bits.
 """
 from __future__ import annotations
 
@@ -135,3 +136,34 @@ def test_tuner_chooses_a_split_and_the_batch_keeps_its_properties(oracle_mod):
     for a, b in zip(outs[0], outs[1]):
         assert bits_equal(a, b)
     _check_bound(oracle_mod, probs, outs[0])
+
+
+def test_emulated_kernel_class_choice_keeps_the_bits():
+    # the tile field of an emulated problem names its kernel (128: one-SM, 256: two-SM); both give
+    # the single call's bits, and the tuner's choice per bucket is one of them
+    import torch
+    from test_grouped_gpu import run_single
+    tuner = autotune.Autotuner(cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"))
+    table = tuner.tune_emulated_class(out_buckets=range(10, 11), k_buckets=range(10, 11), per_bucket=4, reps=1)
+    assert set(table) == {"10_10"} and table["10_10"]["tile"] in autotune.EMU_CLASSES
+    probs = make_batch(74, 4, 1024, 1500, modes=("emu",), slices=(6,), alpha_beta=(1.0, 0.5))
+    to_device(probs)
+    outs = {}
+    for tile in (128, 256, 0):
+        for p in probs:
+            p["dC"].copy_(torch.from_numpy(p["C"]))
+        desc = [dict(transa=p["ta"], transb=p["tb"], mode=gbdgemm.GBD_MODE_EMULATED, slices=6, tile=tile, m=p["m"],
+                     n=p["n"], k=p["k"], alpha=p["alpha"], beta=p["beta"], A=p["dA"], lda=p["lda"], B=p["dB"],
+                     ldb=p["ldb"], C=p["dC"], ldc=p["ldc"]) for p in probs]
+        if tile == 0:
+            tuner.apply(desc)
+        arr = gbdgemm.problem_array(desc)
+        wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        assert gbdgemm.gbd_dgemm_grouped(arr, ws, wsb) == 0, gbdgemm.gbd_last_error()
+        torch.cuda.synchronize()
+        outs[tile] = [p["dC"].cpu().numpy() for p in probs]
+    for q, p in enumerate(probs):
+        ref = run_single(p, 6)
+        for tile in (128, 256, 0):
+            assert bits_equal(outs[tile][q], ref), (tile, p["m"], p["n"], p["k"])
