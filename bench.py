@@ -172,11 +172,12 @@ def host_inputs(seed: int):
     return _HOST_INPUTS[seed]
 
 
-# kernels of one modular call with the bits chosen on the device: exponents and magnitudes, row
-# statistics, magnitude planes (FP8), the certification product, the plan, the BF16 retry's planes,
-# product and plan (three launches that return at once when the FP8 plan is feasible), residues,
-# column scales and the products (the tail launch comes on top, see mod_tail_launches)
-MOD_LAUNCHES = 11
+# kernels of one modular call with the bits chosen on the device: statistics and FP8 magnitude
+# planes in one pass, the row merge (which also moves the planes to each row's scale), the
+# certification product, the plan, the BF16 retry's planes, product and plan (three launches that
+# return at once when the FP8 plan is feasible), residues, column scales and the products (the tail
+# launch comes on top, see mod_tail_launches)
+MOD_LAUNCHES = 10
 
 
 def mod_tail_launches(m, n, sms):

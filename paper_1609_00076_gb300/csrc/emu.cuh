@@ -78,6 +78,20 @@ int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned lo
 
 // One operand side of one problem for the preparation kernels.  Rows r of op(X) (R rows, K
 // columns): element (r, p) is X[p*ld + r] when rows_contig, X[r*ld + p] otherwise.
+// Partials of the one-pass statistics of one operand side, per row and 64-wide k tile ([R][nkt]
+// each): the tile's largest exponent (kExpEmpty: no non-zero finite entry), a non-finite flag, the
+// smallest frexp exponent of a non-zero entry and the smallest exponent of a lowest set bit
+// (kEminNone: none), and the magnitude and square sums relative to the tile's exponent.
+struct StatSide {
+  int* e;
+  int* b;
+  int* lo;
+  int* low;
+  float* s;
+  float* q;
+  int nkt;
+};
+
 struct PrepJob {
   const double* X;
   int64_t ld, R, K;
@@ -95,14 +109,10 @@ struct PrepJob {
   // the smallest frexp exponent of each row's non-zero finite entries (atomic minimum by the
   // magnitude planes; kEminNone until then), or null
   int* emin;
-  // grouped modular problems: the per row and k-block partials of the one-pass exponent and
-  // magnitude statistics ([R][nkr] each, as ExpMagParts), and the word that receives the side's
-  // largest scaled square sum (float bits)
-  int* pe;
-  float* ps;
-  float* pq;
-  int* pb;
-  int nkr;
+  // the modular emulation's automatic mode: the one-pass statistics' tile partials, and (grouped
+  // problems) the words that receive the side's largest square-sum bound (float bits) and, in
+  // `tex`, its exactness width
+  StatSide st;
   unsigned int* norm;
 };
 constexpr int kEminNone = 0x7F7F7F7F;  // a row without a non-zero finite entry (memset byte 0x7F)
@@ -119,20 +129,14 @@ void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks);
 // K <= 1024 every row has one block, which stores its result and needs no initialisation
 int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s);
 int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t s);
-// Exponents and magnitude sums of both sides in one pass over the operands: per row and
-// k-block the largest exponent, a non-finite flag and the magnitude sum relative to that
-// exponent (partials [row][nkr]); then per row sig, bad and mu (32.32 fixed point) from the
-// partials in a fixed order.  Writes what launch_exponents_pair + launch_magnitudes_pair do.
-struct ExpMagParts {
-  int* e[2];
-  float* s[2];
-  int* b[2];
-  float* q[2];   // sums of squares relative to the same exponents
-  int nkr;       // k-blocks of kRedChunk per row
-  float* stats;  // {min mu over rows, min nu over columns, any bad row, any bad column}
-  unsigned int* norms;  // [2] upper bounds of the largest scaled square sum of each side (float bits)
-};
-int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s);
+// The modular emulation's automatic mode, both sides in one pass over the operands: per row and
+// 64-wide k tile the partial statistics (the jobs' `st`) and the FP8 magnitude planes relative to
+// the tile's exponent (into the jobs' D, pitch round_up(K, 16)); then, a warp per row, sig, bad, mu
+// and emin, the planes moved to each row's sigma, and the sides' exactness widths (tex[2]) and
+// square-sum bounds (norms[2], float bits) by atomic maxima (the words zeroed beforehand).  Two
+// launches.
+int launch_statplane_pair(const PrepPair& pp, int64_t split_blocks, unsigned int* tex, unsigned int* norms,
+                          cudaStream_t s);
 int launch_split_pair(const PrepPair& pp, int64_t split_blocks, cudaStream_t s);
 
 // ---- modular emulation (Ozaki scheme II) ----
@@ -211,11 +215,11 @@ int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, 
                         bool exponents, bool split, cudaStream_t s);
 // magnitude sums of every job (after the batched exponents; the jobs' mu arrays zeroed by them)
 int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
-// grouped modular problems: exponents, flags, magnitude sums and square-sum bounds of every job in
-// one pass over the operands (the jobs' partial arrays), then per row sig, bad, mu and emin's
-// initial value, and the side's largest square-sum bound into the job's norm word: the same
-// arithmetic, in the same order, as launch_expmag_pair
-int launch_expmag_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
+// grouped modular problems: launch_statplane_pair's three steps over every job (each job's width
+// and norm words): the same arithmetic in the same order, so a problem gets the same statistics
+// and planes alone and in a batch
+int launch_statplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, int64_t max_rows,
+                             cudaStream_t s);
 // exponents and magnitude statistics of every problem (jobs 2q, 2q+1 = op(A), op(B)^T of
 // problem q) into stats_dev[4q .. 4q+3] = {min mu, min nu, bad row, bad column}
 int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,

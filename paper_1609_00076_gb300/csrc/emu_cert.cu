@@ -465,8 +465,11 @@ int launch_cert(int64_t m, int64_t n, int64_t k, int prec, const void* PA, const
   // the floor of the planes, w = 2^(-63-S) (BF16) or 2^(-14-S) (E5M2's smallest normal)
   const double w = std::ldexp(1.0, (fp8 ? -14 : -63) - S);
   a.slack = float_up((double)k * (2.0 * w + w * w) * (1.0 + std::ldexp(1.0, -40)));
-  const double nkr = (double)((k + 1023) / 1024);
-  a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + nkr * std::ldexp(1.0, -22));
+  // the magnitude sums' FP32 roundings: within 2^-10 relatively for every 1024-deep block of terms
+  // and 2^-22 for every one of at most ceil(k/64) partial sums merged (tiles of the one-pass
+  // statistics; the magnitude pass's 1024-deep blocks are fewer)
+  const double nkt = (double)((k + 63) / 64);
+  a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + nkt * std::ldexp(1.0, -22));
   a.muA = muA;
   a.muB = muB;
   a.badA = badA;
@@ -546,7 +549,7 @@ int make_cert_entry(int64_t m, int64_t n, int64_t k, int prec, const void* PA, c
   a.f = float_down(std::ldexp(1.0 - (double)chunk_k * std::ldexp(1.0, -19), -2 * S));
   const double w = std::ldexp(1.0, (fp8 ? -14 : -63) - S);
   a.slack = float_up((double)k * (2.0 * w + w * w) * (1.0 + std::ldexp(1.0, -40)));
-  a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + (double)((k + 1023) / 1024) * std::ldexp(1.0, -22));
+  a.mu_scale = float_up(1.0 + std::ldexp(1.0, -10) + (double)((k + 63) / 64) * std::ldexp(1.0, -22));
   a.muA = muA;
   a.muB = muB;
   a.badA = badA;

@@ -948,12 +948,11 @@ struct ModWorkspace {
   int* badB;
   unsigned long long* muA;
   unsigned long long* muB;
-  float* stats;
   ModPlan* plan;
   unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
   int* eminA;          // [m] smallest exponent of each row's non-zero entries, then eminB [n]
   int* eminB;
-  ExpMagParts parts;  // automatic mode: per row and k-block exponents, flags and magnitude sums
+  StatSide st[2];      // automatic mode: the one-pass statistics' tile partials of op(A), op(B)^T
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
   uint16_t* DB;  // [nmod][n][kp]
@@ -982,16 +981,15 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_badB = off; off = up(off + sizeof(int) * (size_t)n);
   const size_t o_muA = off; off = up(off + sizeof(unsigned long long) * (size_t)m);
   const size_t o_muB = off; off = up(off + sizeof(unsigned long long) * (size_t)n);
-  const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_plan = off; off = up(off + sizeof(ModPlan));
   const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
   const size_t o_emin = off; off = up(off + sizeof(int) * (size_t)(m + n));
-  const int64_t nkr = (k + 1023) / 1024;  // k-blocks of the exponent and magnitude pass
-  size_t o_part[2][4];
+  const int64_t nkt = (k + 63) / 64;  // 64-wide k tiles of the one-pass statistics
+  size_t o_part[2][6];
   for (int side = 0; side < 2; ++side)
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < 6; ++f) {
       o_part[side][f] = off;
-      off = up(off + 4 * (size_t)(side == 0 ? m : n) * (size_t)nkr);
+      off = up(off + 4 * (size_t)(side == 0 ? m : n) * (size_t)nkt);
     }
   const size_t o_cs = off; off = up(off + sizeof(double) * (size_t)n);
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
@@ -1008,20 +1006,20 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->badB = reinterpret_cast<int*>(b + o_badB);
     ws->muA = reinterpret_cast<unsigned long long*>(b + o_muA);
     ws->muB = reinterpret_cast<unsigned long long*>(b + o_muB);
-    ws->stats = reinterpret_cast<float*>(b + o_stats);
     ws->plan = reinterpret_cast<ModPlan*>(b + o_plan);
     ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
     ws->eminA = reinterpret_cast<int*>(b + o_emin);
     ws->eminB = ws->eminA + m;
     for (int side = 0; side < 2; ++side) {
-      ws->parts.e[side] = reinterpret_cast<int*>(b + o_part[side][0]);
-      ws->parts.s[side] = reinterpret_cast<float*>(b + o_part[side][1]);
-      ws->parts.b[side] = reinterpret_cast<int*>(b + o_part[side][2]);
-      ws->parts.q[side] = reinterpret_cast<float*>(b + o_part[side][3]);
+      StatSide& st = ws->st[side];
+      st.e = reinterpret_cast<int*>(b + o_part[side][0]);
+      st.b = reinterpret_cast<int*>(b + o_part[side][1]);
+      st.lo = reinterpret_cast<int*>(b + o_part[side][2]);
+      st.low = reinterpret_cast<int*>(b + o_part[side][3]);
+      st.s = reinterpret_cast<float*>(b + o_part[side][4]);
+      st.q = reinterpret_cast<float*>(b + o_part[side][5]);
+      st.nkt = (int)nkt;
     }
-    ws->parts.nkr = (int)nkr;
-    ws->parts.stats = ws->stats;
-    ws->parts.norms = ws->cert + kCertNormA;
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
@@ -1284,17 +1282,19 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = automatic ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
   ja.emin = automatic ? ws.eminA : nullptr;
   jb.emin = automatic ? ws.eminB : nullptr;
+  ja.st = ws.st[0];
+  jb.st = ws.st[1];
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
   const int prec = cert_prec_default();
-  if (automatic) {  // exponents, magnitude sums and square sums in one pass over the operands
-    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s)) != cudaSuccess)
+  if (automatic) {
+    // one pass over the operands: exponents, flags, magnitude and square sums, exactness widths,
+    // and the FP8 magnitude planes (in the residue planes' place, which are written after the
+    // plan); then the certification product with the reduction of the bound's ratios
+    if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu_mod: clearing the certification words");
-    if ((rc = launch_expmag_pair(pp, exp_blocks, ws.parts, s))) return rc;
-    // the certification: magnitude planes (in the residue planes' place, which are written
-    // after the plan) and their product with the reduction of the bound's ratios
-    if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
+    if ((rc = launch_statplane_pair(pp, split_blocks, ws.cert + kCertTexA, ws.cert + kCertNormA, s))) return rc;
+    if (prec == kCertBF16 && (rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
     if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
                           ws.eminB, ws.cert, nullptr, 0, sms, s)))
       return rc;
@@ -1455,12 +1455,10 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     // op(A) rows: A[p*lda + i] when 'N' (rows contiguous); op(B)^T rows: B[p*ldb + j] when 'T'
     ja.X = p.A; ja.ld = p.lda; ja.R = p.m; ja.K = p.k; ja.rows_contig = trans_code(p.transa) == 0;
     ja.sig = w.sigA; ja.bad = w.badA; ja.mu = w.muA; ja.D = w.DA; ja.kp = w.kp;
-    ja.tex = words + kCertTexA; ja.plan = w.plan; ja.emin = w.eminA; ja.norm = words + kCertNormA;
-    ja.pe = w.parts.e[0]; ja.ps = w.parts.s[0]; ja.pq = w.parts.q[0]; ja.pb = w.parts.b[0]; ja.nkr = w.parts.nkr;
+    ja.tex = words + kCertTexA; ja.plan = w.plan; ja.emin = w.eminA; ja.norm = words + kCertNormA; ja.st = w.st[0];
     jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
     jb.sig = w.sigB; jb.bad = w.badB; jb.mu = w.muB; jb.D = w.DB; jb.kp = w.kp;
-    jb.tex = words + kCertTexB; jb.plan = w.plan; jb.emin = w.eminB; jb.norm = words + kCertNormB;
-    jb.pe = w.parts.e[1]; jb.ps = w.parts.s[1]; jb.pq = w.parts.q[1]; jb.pb = w.parts.b[1]; jb.nkr = w.parts.nkr;
+    jb.tex = words + kCertTexB; jb.plan = w.plan; jb.emin = w.eminB; jb.norm = words + kCertNormB; jb.st = w.st[1];
     prep_job_blocks(ja, g->exp_blocks, g->split_blocks);
     prep_job_blocks(jb, g->exp_blocks, g->split_blocks);
     CertTableEntry& ce = g->cert[q];
@@ -1554,13 +1552,15 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   if ((e = cudaMemsetAsync(g.words_dev, 0, sizeof(unsigned int) * kCertWords * (size_t)(g.count + 1), s)) !=
       cudaSuccess)
     return cuda_fail(e, "grouped modular: clearing the certification words");
-  // exponents, flags, magnitude sums and square-sum bounds of every side in one pass
-  if ((rc = launch_expmag_batched(g.jobs_dev, njobs, g.exp_blocks, s))) return rc;
+  // one pass over every side: statistics and FP8 magnitude planes (as the single call)
+  int64_t max_rows = 0;
+  for (const PrepJob& j : g.jobs) max_rows = j.R > max_rows ? j.R : max_rows;
+  if ((rc = launch_statplane_batched(g.jobs_dev, njobs, g.split_blocks, max_rows, s))) return rc;
   // the certification: magnitude planes, their products, the plans (the same precision as the
   // single call's, so that a problem gets the same plan alone and in a batch)
   const int prec = cert_prec_default();
   const bool retry = prec == kCertFP8;
-  if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec))) return rc;
+  if (prec == kCertBF16 && (rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec))) return rc;
   if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, prec, sms, s))) return rc;
   const ModProducts prods = moduli_products();
   k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 0, g.flags_dev,

@@ -673,291 +673,316 @@ __global__ void __launch_bounds__(256) k_magnitudes_pair(const __grid_constant__
   else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum, direct);
 }
 
-// ---- exponents and magnitudes in one pass (the modular emulation's automatic mode) ----
+// ---- statistics and FP8 magnitude planes in one pass (the modular emulation's automatic mode) ----
 // 2^d for d <= 0 as a float (0 below 2^-126)
 __device__ __forceinline__ float pow2f_nonpos(int d) { return d < -126 ? 0.0f : __int_as_float((127 + d) << 23); }
 
-// folds element bits b into a running (largest exponent E, sum acc of |x| 2^-E, sum sq of
-// x^2 2^-2E, non-finite flag); a rescaling that underflows drops parts below 2^-126 each
-__device__ __forceinline__ void expmag_add(uint64_t b, int& E, float& acc, float& sq, int& bad) {
-  if (is_nonfinite(b)) {
-    bad = 1;
-    return;
-  }
-  if (is_zero(b)) return;
-  const int e = exponent_of(b);
-  if (e > E) {
-    if (E == kExpEmpty) {
-      acc = 0.0f;
-      sq = 0.0f;
-    } else {
-      acc *= pow2f_nonpos(E - e);
-      sq *= pow2f_nonpos(2 * (E - e));
-    }
-    E = e;
-  }
-  const float v = scaled_magnitude(b, E);
-  acc += v;
-  sq = fmaf(v, v, sq);
-}
-// (E, acc, sq) := (E, acc, sq) + (E2, acc2, sq2), each relative to its own largest exponent
-__device__ __forceinline__ void expmag_merge(int& E, float& acc, float& sq, int E2, float acc2, float sq2) {
-  if (E2 == kExpEmpty) return;
-  if (E == kExpEmpty) {
-    E = E2;
-    acc = acc2;
-    sq = sq2;
-    return;
-  }
-  if (E2 > E) {
-    acc = acc * pow2f_nonpos(E - E2) + acc2;
-    sq = sq * pow2f_nonpos(2 * (E - E2)) + sq2;
-    E = E2;
-  } else {
-    acc += acc2 * pow2f_nonpos(E2 - E);
-    sq += sq2 * pow2f_nonpos(2 * (E2 - E));
-  }
-}
-
+// One 64 x 64 tile of one side (rows r0 + 0..63, k p0 + 0..63), eight threads per row, each with
+// eight consecutive entries (split_body's layout; no thread leaves early, so the eight threads of
+// a row can reduce together).  For each row of the tile: its largest exponent E_t, the FP8 E5M2
+// magnitude-plane bytes of its entries relative to E_t (MagWriter's bytes with E_t in place of
+// sigma; the row merge moves them to sigma), and the tile's partial statistics, written by
+// the row's first thread at [r][bx]: E_t, a non-finite flag, the magnitude and square sums
+// relative to E_t (FP32, in a fixed order), the smallest frexp exponent of a non-zero entry and
+// the smallest exponent of a lowest set bit.
 template <bool ROWS_CONTIG>
-__device__ __forceinline__ void expmag_body(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K, int nkr,
-                                            int* __restrict__ pe, float* __restrict__ ps, float* __restrict__ pq,
-                                            int* __restrict__ pb, int64_t bx, int64_t by, int (*s_e)[33],
-                                            float (*s_s)[33], float (*s_q)[33], int (*s_b)[33]) {
-  const int64_t p_begin = by * kRedChunk;
-  const int64_t p_end = p_begin + kRedChunk < K ? p_begin + kRedChunk : K;
+__device__ __forceinline__ void statplane_tile(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                                               uint8_t* __restrict__ D, int64_t kp, const StatSide& st, int64_t bx,
+                                               int64_t by, uint64_t (*tile)[kTile + 1]) {
+  constexpr int S = 15, kMant = 2, kBias = 15, kFloor = -14;  // E5M2, as MagWriter<true>
+  const int64_t p0 = bx * kTile, r0 = by * kTile;
+  const int tid = threadIdx.x;
+  const int rr = tid >> 3, pp0 = (tid & 7) * kPerThread;
+  const int64_t r = r0 + rr, pbase = p0 + pp0;
+  const bool row_in = r < R;
+  uint64_t x[kPerThread];
   if (ROWS_CONTIG) {
-    // 32 consecutive rows per warp (coalesced), 8 warps split the k range
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t r = bx * 32 + tx;
-    int E = kExpEmpty, bd = 0;
-    float acc = 0.0f, sq = 0.0f;
-    if (r < R) {
-      // eight loads in flight per thread, then their folds in the same order
-      int64_t p = p_begin + ty;
-      for (; p + 56 < p_end; p += 64) {
-        uint64_t v[8];
+    // column pi of a tile row is stored at (pi & ~7) | ((pi ^ (pi >> 3)) & 7) (as split_body)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = load_bits<true>(X, ld, r, p + 8 * u);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, sq, bd);
-      }
-      for (; p < p_end; p += 8) expmag_add(load_bits<true>(X, ld, r, p), E, acc, sq, bd);
+    for (int it = 0; it < kTile * kTile / kSplitThreads; ++it) {
+      const int idx = tid + it * kSplitThreads;
+      const int ri = idx % kTile, pi = idx / kTile;  // coalesced along rows
+      const int64_t rg = r0 + ri, pg = p0 + pi;
+      tile[ri][(pi & ~7) | ((pi ^ (pi >> 3)) & 7)] = (rg < R && pg < K) ? load_bits<true>(X, ld, rg, pg) : 0ull;
     }
-    s_e[ty][tx] = E;
-    s_s[ty][tx] = acc;
-    s_q[ty][tx] = sq;
-    s_b[ty][tx] = bd;
     __syncthreads();
-    if (ty == 0 && r < R) {
-      for (int q = 1; q < 8; ++q) {
-        expmag_merge(E, acc, sq, s_e[q][tx], s_s[q][tx], s_q[q][tx]);
-        bd |= s_b[q][tx];
-      }
-      pe[r * nkr + by] = E;
-      ps[r * nkr + by] = acc;
-      pq[r * nkr + by] = sq;
-      pb[r * nkr + by] = bd;
-    }
+    const int grp = pp0 >> 3;
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) x[v] = tile[rr][pp0 + (v ^ grp)];
   } else {
-    // one row per warp, lanes along the contiguous k direction
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t r = bx * 8 + w;
-    if (r >= R) return;
-    int E = kExpEmpty, bd = 0;
-    float acc = 0.0f, sq = 0.0f;
-    int64_t p = p_begin + lane;
-    for (; p + 224 < p_end; p += 256) {  // eight loads in flight per lane, then their folds in order
-      uint64_t v[8];
+    const double* src = X + (row_in ? r : 0) * ld + pbase;
+    if (row_in && pbase + kPerThread <= K && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+      const longlong2* s2 = reinterpret_cast<const longlong2*>(src);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = load_bits<false>(X, ld, r, p + 32 * u);
+      for (int v = 0; v < kPerThread / 2; ++v) {
+        const longlong2 w = __ldg(s2 + v);
+        x[2 * v] = (uint64_t)w.x;
+        x[2 * v + 1] = (uint64_t)w.y;
+      }
+    } else {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) expmag_add(v[u], E, acc, sq, bd);
+      for (int v = 0; v < kPerThread; ++v)
+        x[v] = (row_in && pbase + v < K) ? (uint64_t)__double_as_longlong(__ldg(src + v)) : 0ull;
     }
-    for (; p < p_end; p += 32) expmag_add(load_bits<false>(X, ld, r, p), E, acc, sq, bd);
-    for (int o = 16; o; o >>= 1) {  // a fixed butterfly: deterministic
-      const int E2 = __shfl_xor_sync(0xffffffffu, E, o);
-      const float a2 = __shfl_xor_sync(0xffffffffu, acc, o);
-      const float q2 = __shfl_xor_sync(0xffffffffu, sq, o);
-      bd |= __shfl_xor_sync(0xffffffffu, bd, o);
-      // both partners merge the same pair, lower lane first, so they agree bit for bit
-      if (lane & o) {
-        int El = E2;
-        float al = a2, ql = q2;
-        expmag_merge(El, al, ql, E, acc, sq);
-        E = El;
-        acc = al;
-        sq = ql;
+  }
+  // the row's largest exponent over the tile (its eight threads: lanes 8q .. 8q + 7 of the warp)
+  int emax = kExpEmpty, bad = 0;
+#pragma unroll
+  for (int v = 0; v < kPerThread; ++v) {
+    if (is_nonfinite(x[v])) bad = 1;
+    else if (!is_zero(x[v])) emax = max(emax, exponent_of(x[v]));
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  const int sg = emax == kExpEmpty ? 0 : emax;
+  const int base = S - sg - 1023;  // a normal x: exponent of |x| 2^(S - E_t) = E + base
+  uint32_t h[kPerThread];
+  float acc = 0.0f, sq = 0.0f;
+  int em = kEminNone, low = kEminNone;
+#pragma unroll
+  for (int v = 0; v < kPerThread; ++v) {
+    const uint32_t hi = (uint32_t)(x[v] >> 32), lo = (uint32_t)x[v];
+    const int E = (int)((hi >> 20) & 0x7FFu);
+    if (E == 0x7FF || ((hi << 1) | lo) == 0u) {
+      h[v] = 0u;
+      continue;
+    }
+    if (E != 0) {  // normal: the 53-bit significand 1.f, its top fraction bits in hi
+      const int eb = E + base;
+      h[v] = eb < kFloor ? (uint32_t)(kFloor + kBias) << kMant
+                         : ((uint32_t)(eb + kBias) << kMant) | ((hi >> (20 - kMant)) & ((1u << kMant) - 1u));
+      const int tz = lo ? __ffs((int)lo) - 1 : 31 + __ffs((int)((hi & 0xFFFFFu) | 0x100000u));
+      low = min(low, E - 1075 + tz);
+      em = min(em, E - 1022);
+      // |x| 2^-E_t as a float, its mantissa truncated (as scaled_magnitude; below 2^-126: 0)
+      const int fe = E - sg - 896;  // <= 126: |x| < 2^E_t
+      const float vf = fe > 0 ? __uint_as_float(((uint32_t)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29)) : 0.0f;
+      acc += vf;
+      sq = fmaf(vf, vf, sq);
+    } else {  // subnormal: |x| = f 2^-1074
+      const uint64_t mant = x[v] & 0xFFFFFFFFFFFFFull;
+      const int nb = 64 - __clzll((long long)mant);
+      const int eb = nb - 1 - 1074 - sg + S;
+      if (eb < kFloor) {
+        h[v] = (uint32_t)(kFloor + kBias) << kMant;
       } else {
-        expmag_merge(E, acc, sq, E2, a2, q2);
+        const uint32_t mf = (uint32_t)((nb >= kMant + 1 ? (mant >> (nb - kMant - 1)) : (mant << (kMant + 1 - nb))) &
+                                       ((1u << kMant) - 1u));
+        h[v] = ((uint32_t)(eb + kBias) << kMant) | mf;
       }
+      low = min(low, -1074 + __ffsll((long long)mant) - 1);
+      em = min(em, nb - 1074);
+      const float vf = scaled_magnitude(x[v], sg);
+      acc += vf;
+      sq = fmaf(vf, vf, sq);
     }
-    if (lane == 0) {
-      pe[r * nkr + by] = E;
-      ps[r * nkr + by] = acc;
-      pq[r * nkr + by] = sq;
-      pb[r * nkr + by] = bd;
+  }
+  if (row_in && pbase < K) {
+    uint8_t* row = D + r * kp + pbase;
+    if (pbase + kPerThread <= K) {
+      *reinterpret_cast<uint2*>(row) = make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
+                                                  h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
+    } else {
+      for (int v = 0; v < kPerThread && pbase + v < K; ++v) row[v] = (uint8_t)h[v];
     }
+  }
+  // the row's partials over its eight threads: a fixed butterfly, so every lane holds the same bits
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    em = min(em, __shfl_xor_sync(0xffffffffu, em, o));
+    low = min(low, __shfl_xor_sync(0xffffffffu, low, o));
+  }
+  if ((tid & 7) == 0 && row_in) {
+    const int64_t o = r * st.nkt + bx;
+    st.e[o] = emax;
+    st.b[o] = bad;
+    st.s[o] = acc;
+    st.q[o] = sq;
+    st.lo[o] = em;
+    st.low[o] = low;
   }
 }
 
-__global__ void __launch_bounds__(256) k_expmag_pair(const __grid_constant__ PrepPair pp,
-                                                     const __grid_constant__ ExpMagParts parts) {
-  __shared__ int s_e[8][33];
-  __shared__ float s_s[8][33];
-  __shared__ float s_q[8][33];
-  __shared__ int s_b[8][33];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the minima start empty (k_rowstats_pair runs after this grid)
-    parts.stats[0] = 3.0e38f;
-    parts.stats[1] = 3.0e38f;
-    parts.stats[2] = 0.0f;
-    parts.stats[3] = 0.0f;
-  }
-  const int ji = (int64_t)blockIdx.x >= pp.j[1].exp_begin ? 1 : 0;
+__global__ void __launch_bounds__(kSplitThreads, 3) k_statplane_pair(const __grid_constant__ PrepPair pp) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = (int64_t)blockIdx.x >= pp.j[1].split_begin ? 1 : 0;
   const PrepJob& j = pp.j[ji];
-  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
-  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
-  if (j.rows_contig)
-    expmag_body<true>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.q[ji], parts.b[ji], bx, by, s_e,
-                      s_s, s_q, s_b);
-  else
-    expmag_body<false>(j.X, j.ld, j.R, j.K, parts.nkr, parts.e[ji], parts.s[ji], parts.q[ji], parts.b[ji], bx, by,
-                       s_e, s_s, s_q, s_b);
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  uint8_t* D = static_cast<uint8_t*>(static_cast<void*>(j.D));
+  const int64_t kp = (j.K + 15) / 16 * 16;  // FP8 plane pitch
+  if (j.rows_contig) statplane_tile<true>(j.X, j.ld, j.R, j.K, D, kp, j.st, bx, by, tile);
+  else statplane_tile<false>(j.X, j.ld, j.R, j.K, D, kp, j.st, bx, by, tile);
 }
 
-// per row of both sides: sig = the largest block exponent, bad = any flag, mu = the blocks'
-// sums rescaled to sig and added in block order (32.32 fixed point, as the magnitude pass);
-// then the side's minimum of the non-zero mu and its any-bad flag into stats (a minimum and an
-// OR: the same values in any order), and the side's largest square sum, raised to an upper
-// bound, into norms.
-//
-// The square sum of a row is computed in FP32 from at most K terms v^2 (v = |x| 2^-sig rounded
-// to FP32, v^2 added by a fused multiply-add) and fewer than 9 nkr merges, each one rounding of
-// a sum of non-negative values; the rescalings are exact except where they underflow, which
-// drops parts below K 2^-126 in all.  So the computed value q satisfies
-// sum_p (x_p 2^-sig)^2 <= q (1 + (K + 9 nkr + 2) 2^-24 (1 + 2^-20)) + K 2^-126, and
-// q (1 + (K + 8 nkr + 64) 2^-22) + K 2^-125, rounded upward, covers it.
-// one row's merge of its block partials (in block order): sig, bad, mu (32.32) and the square-sum
-// bound (0 for a row without a non-zero finite entry)
-struct RowMerge {
-  int E, bad;
-  unsigned long long mu;
-  float sq_up;
-};
-__device__ __forceinline__ RowMerge merge_row(const int* __restrict__ pe, const float* __restrict__ ps,
-                                              const float* __restrict__ pq, const int* __restrict__ pb, int nkr,
-                                              float grow, float floor_add) {
-  RowMerge o;
-  int E = kExpEmpty, bd = 0;
-  for (int q = 0; q < nkr; ++q) {
-    E = max(E, pe[q]);
-    bd |= pb[q];
-  }
-  float mu = 0.0f, sq = 0.0f;
-  if (E != kExpEmpty)
-    for (int q = 0; q < nkr; ++q)
-      if (pe[q] != kExpEmpty) {
-        mu += ps[q] * pow2f_nonpos(pe[q] - E);
-        sq += pq[q] * pow2f_nonpos(2 * (pe[q] - E));
-      }
-  o.E = E;
-  o.bad = bd;
-  o.mu = magnitude_fixed(mu);
-  o.sq_up = E != kExpEmpty ? __fmaf_ru(sq, grow, floor_add) : 0.0f;
-  return o;
+__global__ void __launch_bounds__(kSplitThreads, 3) k_statplane_batched(const PrepJob* __restrict__ jobs, int njobs) {
+  __shared__ uint64_t tile[kTile][kTile + 1];
+  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const PrepJob& j = jobs[ji];
+  const int64_t local = (int64_t)blockIdx.x - j.split_begin;
+  const int64_t bx = local % j.split_gx, by = local / j.split_gx;
+  uint8_t* D = static_cast<uint8_t*>(static_cast<void*>(j.D));
+  const int64_t kp = (j.K + 15) / 16 * 16;
+  if (j.rows_contig) statplane_tile<true>(j.X, j.ld, j.R, j.K, D, kp, j.st, bx, by, tile);
+  else statplane_tile<false>(j.X, j.ld, j.R, j.K, D, kp, j.st, bx, by, tile);
 }
-// the factor and the addend that raise a row's computed square sum to an upper bound (see below)
-__device__ __forceinline__ float square_grow(int64_t K, int nkr) {
-  return __fadd_ru(1.0f, __fmul_ru((float)(K + 8 * (int64_t)nkr + 64), 0x1p-22f));
+
+// The square sum of a row is computed in FP32 from at most K terms v^2 (v = |x| 2^-E_t rounded
+// toward zero to FP32, v^2 added by a fused multiply-add), three butterfly levels per tile, and the
+// row's merge (at most ceil(nkt/32) additions per lane and five butterfly levels), each a rounding
+// of a sum of non-negative values; the rescalings by powers of two are exact except where they
+// underflow, which drops parts below K 2^-126 in all.  So the computed q satisfies
+// sum_p (x_p 2^-sigma)^2 <= q (1 + (K + 4 nkt + 16) 2^-24 (1 + 2^-20)) + K 2^-126, and
+// q (1 + (K + 8 nkt + 64) 2^-22) + K 2^-125, rounded upward, covers it.
+__device__ __forceinline__ float square_grow(int64_t K, int nkt) {
+  return __fadd_ru(1.0f, __fmul_ru((float)(K + 8 * (int64_t)nkt + 64), 0x1p-22f));
 }
 __device__ __forceinline__ float square_floor(int64_t K) { return __fmul_ru((float)K, 0x1p-125f); }
 
-__global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp,
-                                                       const __grid_constant__ ExpMagParts parts) {
-  __shared__ float s_mn[8];
-  __shared__ float s_mx[8];
-  __shared__ int s_bd[8];
-  const int ji = blockIdx.y;
-  const PrepJob& j = pp.j[ji];
-  const float grow = square_grow(j.K, parts.nkr), floor_add = square_floor(j.K);
-  float mn = 3.0e38f, mx = 0.0f;
-  int any_bad = 0;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < j.R; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = r * parts.nkr;
-    const RowMerge rm = merge_row(parts.e[ji] + o, parts.s[ji] + o, parts.q[ji] + o, parts.b[ji] + o, parts.nkr,
-                                  grow, floor_add);
-    j.sig[r] = rm.E;
-    j.bad[r] = rm.bad;
-    if (j.mu) j.mu[r] = rm.mu;
-    if (rm.mu > 0ull) mn = fminf(mn, magnitude_value(rm.mu));
-    mx = fmaxf(mx, rm.sq_up);
-    any_bad |= rm.bad;
+// FP8 E5M2 plane bytes scaled by 2^-d (d >= 0, four bytes of a word): the exponent field lowered
+// by d, the smallest normal value (0x04) where it would fall below it; zeros stay zero.  A byte
+// v = RZ(max(|x| 2^-E_t, w) 2^S) so becomes RZ(max(|x| 2^-sigma, w) 2^S) for d = sigma - E_t:
+// scaling by a power of two commutes with rounding toward zero while the result stays normal,
+// and below the smallest normal both sides take the floor.
+__device__ __forceinline__ uint32_t plane_shift4(uint32_t w, int d) {
+  uint32_t out = 0u;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    uint32_t v = (w >> (8 * b)) & 0xFFu;
+    if (v) {
+      const int ne = (int)(v >> 2) - d;
+      v = ne >= 1 ? ((uint32_t)ne << 2) | (v & 3u) : 0x04u;
+    }
+    out |= v << (8 * b);
   }
-  for (int o = 16; o; o >>= 1) {
-    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    any_bad |= __shfl_xor_sync(0xffffffffu, any_bad, o);
+  return out;
+}
+
+// Row r of job j, on one warp: its tile partials merged (sigma = the largest tile exponent, bad,
+// mu and the square sum rescaled to sigma, added per lane in tile order and then over a fixed
+// butterfly, so every lane holds the same bits; the smallest exponents), written to sig, bad, mu
+// and emin; the FP8 plane bytes of the row's tiles below sigma moved to sigma; returns (to every
+// lane) the row's square-sum bound and exactness width (0 for a row without a non-zero entry).
+__device__ __forceinline__ void merge_row_warp(const PrepJob& j, int64_t r, int lane, float grow, float floor_add,
+                                               float& sq_up, int& width) {
+  const StatSide& st = j.st;
+  const int64_t o = r * st.nkt;
+  int E = kExpEmpty, bd = 0, mn = kEminNone, lw = kEminNone;
+  for (int q = lane; q < st.nkt; q += 32) {
+    E = max(E, st.e[o + q]);
+    bd |= st.b[o + q];
+    mn = min(mn, st.lo[o + q]);
+    lw = min(lw, st.low[o + q]);
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = 16; d; d >>= 1) {
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, d));
+    bd |= __shfl_xor_sync(0xffffffffu, bd, d);
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+    lw = min(lw, __shfl_xor_sync(0xffffffffu, lw, d));
+  }
+  float mu = 0.0f, sq = 0.0f;
+  if (E != kExpEmpty) {
+    uint8_t* prow = static_cast<uint8_t*>(static_cast<void*>(j.D)) + r * ((j.K + 15) / 16 * 16);
+    for (int q = lane; q < st.nkt; q += 32) {
+      const int e = st.e[o + q];
+      if (e == kExpEmpty) continue;
+      mu += st.s[o + q] * pow2f_nonpos(e - E);
+      sq += st.q[o + q] * pow2f_nonpos(2 * (e - E));
+      const int d = E - e;
+      if (d > 0) {  // this tile's plane bytes, relative to its own exponent: move them to sigma
+        const int64_t p0 = (int64_t)q * kTile;
+        const int64_t nb = j.K - p0 < kTile ? j.K - p0 : kTile;
+        uint8_t* b = prow + p0;
+        if (nb == kTile) {
+          uint4* b4 = reinterpret_cast<uint4*>(b);  // 16-byte aligned: the pitch and p0 are multiples of 16
+#pragma unroll
+          for (int v = 0; v < kTile / 16; ++v) {
+            uint4 w = b4[v];
+            w.x = plane_shift4(w.x, d);
+            w.y = plane_shift4(w.y, d);
+            w.z = plane_shift4(w.z, d);
+            w.w = plane_shift4(w.w, d);
+            b4[v] = w;
+          }
+        } else {
+          for (int64_t v = 0; v < nb; ++v) b[v] = (uint8_t)plane_shift4(b[v], d);
+        }
+      }
+    }
+    for (int d = 16; d; d >>= 1) {
+      mu += __shfl_xor_sync(0xffffffffu, mu, d);
+      sq += __shfl_xor_sync(0xffffffffu, sq, d);
+    }
+  }
   if (lane == 0) {
-    s_mn[w] = mn;
-    s_mx[w] = mx;
-    s_bd[w] = any_bad;
+    j.sig[r] = E;
+    j.bad[r] = bd;
+    if (j.mu) j.mu[r] = magnitude_fixed(mu);
+    if (j.emin) j.emin[r] = mn;
+  }
+  width = (E != kExpEmpty && lw != kEminNone) ? min(255, E - lw) : 0;
+  sq_up = E != kExpEmpty ? __fmaf_ru(sq, grow, floor_add) : 0.0f;
+}
+
+// the block's maxima of (sq_up, width) over its warps into *norm and *tex (atomic maxima)
+__device__ __forceinline__ void flush_row_maxima(float mx, int wmax, unsigned int* norm, unsigned int* tex) {
+  __shared__ float s_mx[8];
+  __shared__ int s_w[8];
+  if ((threadIdx.x & 31) == 0) {
+    s_mx[threadIdx.x >> 5] = mx;
+    s_w[threadIdx.x >> 5] = wmax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-      mn = fminf(mn, s_mn[q]);
       mx = fmaxf(mx, s_mx[q]);
-      any_bad |= s_bd[q];
+      wmax = max(wmax, s_w[q]);
     }
-    // non-negative floats order as their bit patterns
-    if (mn < 3.0e38f) atomicMin(reinterpret_cast<int*>(parts.stats + ji), __float_as_int(mn));
-    if (any_bad) atomicOr(reinterpret_cast<int*>(parts.stats + 2 + ji), __float_as_int(1.0f));
-    if (parts.norms && mx > 0.0f) atomicMax(parts.norms + ji, __float_as_uint(mx));
+    if (mx > 0.0f) atomicMax(norm, __float_as_uint(mx));  // non-negative floats order as their bits
+    if (wmax > 0) atomicMax(tex, (unsigned int)wmax);
   }
 }
 
-// grouped modular problems: the one-pass exponent and magnitude partials of every job (as
-// k_expmag_pair), then one block per job merging its rows (as k_rowstats_pair, without the
-// minima), which also initialises emin and raises the side's largest square-sum bound into the
-// job's norm word
-__global__ void __launch_bounds__(256) k_expmag_batched(const PrepJob* __restrict__ jobs, int njobs) {
-  __shared__ int s_e[8][33];
-  __shared__ float s_s[8][33];
-  __shared__ float s_q[8][33];
-  __shared__ int s_b[8][33];
-  const int ji = find_job(jobs, njobs, blockIdx.x, false);
-  const PrepJob& j = jobs[ji];
-  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
-  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
-  if (j.rows_contig)
-    expmag_body<true>(j.X, j.ld, j.R, j.K, j.nkr, j.pe, j.ps, j.pq, j.pb, bx, by, s_e, s_s, s_q, s_b);
-  else
-    expmag_body<false>(j.X, j.ld, j.R, j.K, j.nkr, j.pe, j.ps, j.pq, j.pb, bx, by, s_e, s_s, s_q, s_b);
-}
-
-__global__ void __launch_bounds__(256) k_rowstats_batched(const PrepJob* __restrict__ jobs) {
-  __shared__ float s_mx[8];
-  const PrepJob& j = jobs[blockIdx.x];
-  const float grow = square_grow(j.K, j.nkr), floor_add = square_floor(j.K);
+// per row of both sides (a warp per row): the merged statistics and the planes moved to sigma;
+// then each side's largest square-sum bound and exactness width into norms[side] and tex[side]
+__global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ PrepPair pp, unsigned int* tex,
+                                                       unsigned int* norms) {
+  const int ji = blockIdx.y;
+  const PrepJob& j = pp.j[ji];
+  const float grow = square_grow(j.K, j.st.nkt), floor_add = square_floor(j.K);
+  const int lane = threadIdx.x & 31;
   float mx = 0.0f;
-  for (int64_t r = threadIdx.x; r < j.R; r += blockDim.x) {
-    const int64_t o = r * j.nkr;
-    const RowMerge rm = merge_row(j.pe + o, j.ps + o, j.pq + o, j.pb + o, j.nkr, grow, floor_add);
-    j.sig[r] = rm.E;
-    j.bad[r] = rm.bad;
-    j.mu[r] = rm.mu;
-    j.emin[r] = kEminNone;
-    mx = fmaxf(mx, rm.sq_up);
+  int wmax = 0;
+  for (int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < j.R; r += (int64_t)gridDim.x * 8) {
+    float sq_up;
+    int width;
+    merge_row_warp(j, r, lane, grow, floor_add, sq_up, width);
+    mx = fmaxf(mx, sq_up);
+    wmax = max(wmax, width);
   }
-  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = fmaxf(mx, s_mx[q]);
-    if (mx > 0.0f) atomicMax(j.norm, __float_as_uint(mx));  // non-negative floats order as their bits
+  flush_row_maxima(mx, wmax, norms + ji, tex + ji);
+}
+
+// grouped modular problems: blockIdx.y = job, the same per-row work (the job's norm and width words)
+__global__ void __launch_bounds__(256) k_rowstats_batched(const PrepJob* __restrict__ jobs) {
+  const PrepJob& j = jobs[blockIdx.y];
+  const float grow = square_grow(j.K, j.st.nkt), floor_add = square_floor(j.K);
+  const int lane = threadIdx.x & 31;
+  float mx = 0.0f;
+  int wmax = 0;
+  for (int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < j.R; r += (int64_t)gridDim.x * 8) {
+    float sq_up;
+    int width;
+    merge_row_warp(j, r, lane, grow, floor_add, sq_up, width);
+    mx = fmaxf(mx, sq_up);
+    wmax = max(wmax, width);
   }
+  flush_row_maxima(mx, wmax, j.norm, j.tex);
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 3) k_split_pair(const __grid_constant__ PrepPair pp) {
@@ -1170,13 +1195,16 @@ int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks,
   return launch_check("batched statistics launch");
 }
 
-int launch_expmag_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s) {
-  if (njobs <= 0 || exp_blocks <= 0) return GBD_OK;
-  if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many exponent blocks");
-  k_expmag_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
-  int rc = launch_check("batched exponent and magnitude launch");
+int launch_statplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, int64_t max_rows,
+                             cudaStream_t s) {
+  if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+  if (njobs > 65535) return set_error(GBD_ERR_LIMIT, "grouped: too many modular problems for one batch");
+  k_statplane_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+  int rc = launch_check("batched statistics and planes launch");
   if (rc) return rc;
-  k_rowstats_batched<<<(unsigned)njobs, 256, 0, s>>>(jobs_dev);
+  const int64_t gx = (max_rows + 7) / 8 < 64 ? (max_rows + 7) / 8 : 64;  // warps per row, blocks per job
+  k_rowstats_batched<<<dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)njobs), 256, 0, s>>>(jobs_dev);
   return launch_check("batched row statistics launch");
 }
 
@@ -1215,15 +1243,16 @@ int launch_magnitudes_pair(const PrepPair& pp, int64_t exp_blocks, cudaStream_t 
   return launch_check("magnitude launch");
 }
 
-int launch_expmag_pair(const PrepPair& pp, int64_t exp_blocks, const ExpMagParts& parts, cudaStream_t s) {
-  if (exp_blocks <= 0) return GBD_OK;
-  if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many exponent blocks");
-  k_expmag_pair<<<(unsigned)exp_blocks, 256, 0, s>>>(pp, parts);
-  int rc = launch_check("exponent and magnitude launch");
+int launch_statplane_pair(const PrepPair& pp, int64_t split_blocks, unsigned int* tex, unsigned int* norms,
+                          cudaStream_t s) {
+  if (split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "too many split blocks");
+  k_statplane_pair<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(pp);
+  int rc = launch_check("statistics and planes launch");
   if (rc) return rc;
   const int64_t rmax = pp.j[0].R > pp.j[1].R ? pp.j[0].R : pp.j[1].R;
-  const unsigned gx = (unsigned)((rmax + 255) / 256 < 4096 ? (rmax + 255) / 256 : 4096);
-  k_rowstats_pair<<<dim3(gx > 0 ? gx : 1, 2), 256, 0, s>>>(pp, parts);
+  const int64_t gx = (rmax + 7) / 8 < 4096 ? (rmax + 7) / 8 : 4096;  // a warp per row
+  k_rowstats_pair<<<dim3((unsigned)(gx > 0 ? gx : 1), 2), 256, 0, s>>>(pp, tex, norms);
   return launch_check("row statistics launch");
 }
 
