@@ -78,19 +78,22 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
   jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = slices == 0 ? ws.muB : nullptr; jb.D = ws.DB; jb.kp = ws.kp;
   ja.emin = slices == 0 ? ws.eminA : nullptr;
   jb.emin = slices == 0 ? ws.eminB : nullptr;
+  ja.st = ws.st[0];
+  jb.st = ws.st[1];
   int64_t exp_blocks = 0, split_blocks = 0;
   prep_pair_blocks(pp, exp_blocks, split_blocks);
-  if ((rc = launch_exponents_pair(pp, exp_blocks, ws.ysum, ws.zero_bytes, s))) return rc;
 
   int s_use = slices, exact = 0;
   double bound = 0.0, rho = 0.0, gamma = 0.0;
-  if (slices == 0) {  // the certified choice: magnitude planes (in the slices' place) and their product
-    if ((rc = launch_magnitudes_pair(pp, exp_blocks, s))) return rc;
+  if (slices == 0) {
+    // the certified choice: one pass for the exponents, magnitude sums and FP8 magnitude planes (in
+    // the slices' place), then the planes' product
     if ((e = cudaMemsetAsync(ws.cert, 0, sizeof(unsigned int) * kCertWords, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ws.eminA, 0x7F, sizeof(int) * (size_t)(m + n), s)) != cudaSuccess)
+        (ws.zero_bytes && (e = cudaMemsetAsync(ws.ysum, 0, ws.zero_bytes, s)) != cudaSuccess))
       return cuda_fail(e, "dgemm_emu: clearing the certification words");
     const int prec = cert_prec_default();
-    if ((rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
+    if ((rc = launch_statplane_pair(pp, split_blocks, ws.cert + kCertTexA, ws.cert + kCertNormA, s))) return rc;
+    if (prec == kCertBF16 && (rc = launch_magplane_pair(pp, prec, ws.cert + kCertTexA, split_blocks, s))) return rc;
     if ((rc = launch_cert(m, n, k, prec, ws.DA, ws.DB, ws.muA, ws.muB, ws.badA, ws.badB, ws.sigA, ws.sigB, ws.eminA,
                           ws.eminB, ws.cert, nullptr, 0, sms, s)))
       return rc;
@@ -134,6 +137,7 @@ int gbd_dgemm_emu(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
       return GBD_OK;
     }
   }
+  if (slices != 0 && (rc = launch_exponents_pair(pp, exp_blocks, ws.ysum, ws.zero_bytes, s))) return rc;
   ja.slices = s_use;
   jb.slices = s_use;
   if ((rc = launch_split_pair(pp, split_blocks, s))) return rc;

@@ -36,6 +36,20 @@ constexpr int kParkSlots = 2 * kGroupLevels;  // parked level sums: the group be
 constexpr int kExpEmpty = (int)0x80808080;  // exponent of a row/column with no non-zero entry
 
 // Layout of the caller's workspace (every array 256-byte aligned).
+// Partials of the one-pass statistics of one operand side, per row and 64-wide k tile ([R][nkt]
+// each): the tile's largest exponent (kExpEmpty: no non-zero finite entry), a non-finite flag, the
+// smallest frexp exponent of a non-zero entry and the smallest exponent of a lowest set bit
+// (kEminNone: none), and the magnitude and square sums relative to the tile's exponent.
+struct StatSide {
+  int* e;
+  int* b;
+  int* lo;
+  int* low;
+  float* s;
+  float* q;
+  int nkt;
+};
+
 struct Workspace {
   int* sigA;        // [m] row exponents of op(A)
   int* sigB;        // [n] column exponents of op(B)
@@ -47,6 +61,7 @@ struct Workspace {
   unsigned int* cert;  // [kCertWords] the certification's maxima and exactness widths
   int* eminA;       // [m] smallest exponent of a row's non-zero entries (the certification)
   int* eminB;       // [n]
+  StatSide st[2];   // automatic slices: the one-pass statistics' tile partials of op(A), op(B)^T
   uint16_t* DA;     // [s][m][kp] BF16 digit slices of op(A), k contiguous
   uint16_t* DB;     // [s][n][kp] BF16 digit slices of op(B)^T, k contiguous
   double* scratch;     // [scratch_ctas][128 * 256] FP64 running sums of the two-SM kernel
@@ -78,20 +93,6 @@ int launch_min_stats(const unsigned long long* muA, int64_t m, const unsigned lo
 
 // One operand side of one problem for the preparation kernels.  Rows r of op(X) (R rows, K
 // columns): element (r, p) is X[p*ld + r] when rows_contig, X[r*ld + p] otherwise.
-// Partials of the one-pass statistics of one operand side, per row and 64-wide k tile ([R][nkt]
-// each): the tile's largest exponent (kExpEmpty: no non-zero finite entry), a non-finite flag, the
-// smallest frexp exponent of a non-zero entry and the smallest exponent of a lowest set bit
-// (kEminNone: none), and the magnitude and square sums relative to the tile's exponent.
-struct StatSide {
-  int* e;
-  int* b;
-  int* lo;
-  int* low;
-  float* s;
-  float* q;
-  int nkt;
-};
-
 struct PrepJob {
   const double* X;
   int64_t ld, R, K;

@@ -1070,6 +1070,13 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
   const size_t o_stats = off; off = up(off + sizeof(float) * 4);
   const size_t o_cert = off; off = up(off + sizeof(unsigned int) * kCertWords);
   const size_t o_emin = off; off = up(off + sizeof(int) * (size_t)(m + n));
+  const int64_t nkt = (k + kTile - 1) / kTile;  // 64-wide k tiles of the one-pass statistics
+  size_t o_part[2][6];
+  for (int side = 0; side < 2; ++side)
+    for (int f = 0; f < 6; ++f) {
+      o_part[side][f] = off;
+      off = up(off + 4 * (size_t)(side == 0 ? m : n) * (size_t)nkt);
+    }
   const size_t o_DA = off; off = up(off + 2 * (size_t)s * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)s * (size_t)n * (size_t)kp);
   // two-SM kernel: one 128 x 256 FP64 running-sum slot per CTA (at most one pair per 256 x 256 tile)
@@ -1102,6 +1109,16 @@ size_t layout(int64_t m, int64_t n, int64_t k, int s, void* base, Workspace* ws,
     ws->cert = reinterpret_cast<unsigned int*>(b + o_cert);
     ws->eminA = reinterpret_cast<int*>(b + o_emin);
     ws->eminB = ws->eminA + m;
+    for (int side = 0; side < 2; ++side) {
+      StatSide& st = ws->st[side];
+      st.e = reinterpret_cast<int*>(b + o_part[side][0]);
+      st.b = reinterpret_cast<int*>(b + o_part[side][1]);
+      st.lo = reinterpret_cast<int*>(b + o_part[side][2]);
+      st.low = reinterpret_cast<int*>(b + o_part[side][3]);
+      st.s = reinterpret_cast<float*>(b + o_part[side][4]);
+      st.q = reinterpret_cast<float*>(b + o_part[side][5]);
+      st.nkt = (int)nkt;
+    }
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
     ws->scratch = reinterpret_cast<double*>(b + o_scr);

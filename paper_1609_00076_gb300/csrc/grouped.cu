@@ -388,6 +388,10 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     ja.sig = ws.sigA; ja.bad = ws.badA; ja.mu = ws.muA; ja.D = ws.DA; ja.kp = ws.kp; ja.emin = ws.eminA;
     jb.X = p.B; jb.ld = p.ldb; jb.R = p.n; jb.K = p.k; jb.rows_contig = trans_code(p.transb) != 0;
     jb.sig = ws.sigB; jb.bad = ws.badB; jb.mu = ws.muB; jb.D = ws.DB; jb.kp = ws.kp; jb.emin = ws.eminB;
+    // automatic slices: the one-pass statistics' partials and the problem's certification words
+    unsigned int* words = reinterpret_cast<unsigned int*>(plan->stats_dev) + emu::kCertWords * q;
+    ja.st = ws.st[0]; ja.tex = words + emu::kCertTexA; ja.norm = words + emu::kCertNormA;
+    jb.st = ws.st[1]; jb.tex = words + emu::kCertTexB; jb.norm = words + emu::kCertNormB;
     emu::prep_job_blocks(ja, plan->exp_blocks, plan->split_blocks);
     emu::prep_job_blocks(jb, plan->exp_blocks, plan->split_blocks);
   }
@@ -399,23 +403,22 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     if ((e = cudaMemcpyAsync(plan->jobs_dev, plan->jobs.data(), sizeof(emu::PrepJob) * plan->jobs.size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "grouped: job table copy");
-    if ((rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, 0, true, false, s)))
-      return rc;
-    if ((rc = emu::launch_magnitudes_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, s))) return rc;
     unsigned int* words = reinterpret_cast<unsigned int*>(plan->stats_dev);  // kCertWords per emulated problem
     if ((e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * emu::kCertWords * plan->emu.size(), s)) != cudaSuccess)
       return cuda_fail(e, "grouped: clearing the certification words");
+    // one pass over every problem's operands: statistics and FP8 magnitude planes, as the single call
+    int64_t max_rows = 0;
+    for (const auto& j : plan->jobs) max_rows = j.R > max_rows ? j.R : max_rows;
+    if ((rc = emu::launch_statplane_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->split_blocks, max_rows, s)))
+      return rc;
     const int prec = emu::cert_prec_default();
+    if (prec == emu::kCertBF16 &&
+        (rc = emu::launch_magplane_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->split_blocks, s, prec)))
+      return rc;
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       const auto& em = plan->emu[q];
       if (em.slices != 0) continue;
-      emu::PrepPair pp;
-      pp.j[0] = plan->jobs[2 * q];
-      pp.j[1] = plan->jobs[2 * q + 1];
-      int64_t eb = 0, sb = 0;
-      emu::prep_pair_blocks(pp, eb, sb);
       unsigned int* w = words + emu::kCertWords * q;
-      if ((rc = emu::launch_magplane_pair(pp, prec, w + emu::kCertTexA, sb, s))) return rc;
       if ((rc = emu::launch_cert(em.p.m, em.p.n, em.p.k, prec, em.ws.DA, em.ws.DB, em.ws.muA, em.ws.muB,
                                  em.ws.badA, em.ws.badB, em.ws.sigA, em.ws.sigB, em.ws.eminA, em.ws.eminB, w,
                                  nullptr, 0, sms, s)))
