@@ -49,7 +49,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram bytes (read + write) of the product phase of one 8192^3 call (dram__bytes_read.sum +
 # dram__bytes_write.sum of the product launches, one ncu pass at full size; the modular entry is
 # the two-SM launch plus its one-SM tail launch), None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 39.310e9, "mod": 22.232e9}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 18.270e9}
 
 
 def load_peaks():
