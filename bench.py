@@ -49,7 +49,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram bytes (read + write) of the product phase of one 8192^3 call (dram__bytes_read.sum +
 # dram__bytes_write.sum of the product launches, one ncu pass at full size; the modular entry is
 # the two-SM launch plus its one-SM tail launch), None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 18.270e9}
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": None}
 
 
 def load_peaks():
@@ -175,9 +175,9 @@ def host_inputs(seed: int):
 # kernels of one modular call with the bits chosen on the device: statistics and FP8 magnitude
 # planes in one pass, the row merge (which also moves the planes to each row's scale), the
 # certification product, the plan, the BF16 retry's planes, product and plan (three launches that
-# return at once when the FP8 plan is feasible), residues, column scales and the products (the tail
-# launch comes on top, see mod_tail_launches)
-MOD_LAUNCHES = 10
+# return at once when the FP8 plan is feasible), residues, column scales, the products and the
+# reconstruction of C from their parked residues (the tail launch comes on top, see mod_tail_launches)
+MOD_LAUNCHES = 11
 
 
 def mod_tail_launches(m, n, sms):
@@ -322,11 +322,12 @@ def run_ours(args, world, rank, local, pg):
     total_ms = max_over_ranks(pg, total_ms, dev)
     value = replica_value(world, flops, args.steps, total_ms)
     # phases and the device's choice, from three further calls that read them back (untimed above)
-    gemm_ms, prep_ms = [], []
+    gemm_ms, prep_ms, recon_ms = [], [], []
     for _ in range(3):
         mod_step(stream, report=True)
         gemm_ms.append(info.gemm_ms)
         prep_ms.append(info.prep_ms)
+        recon_ms.append(info.recon_ms)
     moduli, bits, bound_est = info.products, info.digit_bits, info.bound
     results = {"modular": C.cpu().numpy()} if rank == 0 else {}  # for the accuracy report (untimed)
 
@@ -441,9 +442,6 @@ def run_ours(args, world, rank, local, pg):
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads, rows, ref = oracle_sample(target_s=8.0, want_rows=True)
     accuracy = accuracy_report(results, rows, ref)
-    # exponents and magnitudes, row statistics and their minima, plan, residues, column scales,
-    # residue products (+ CRT) on SM pairs, and the products of a partial last wave of 256 x 256
-    # tiles on one-SM CTAs when their 128 x 128 quarters fit one wave of SMs
     launches_per_step = MOD_LAUNCHES + mod_tail_launches(M, N, torch.cuda.get_device_properties(dev).multi_processor_count)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -459,12 +457,12 @@ def run_ours(args, world, rank, local, pg):
                    "fp64_peak_source": "measured: gbd_fp64_mma_probe (independent mma.sync.m16n8k16.f64 streams)"},
         "exponent_ranges": e_legs,
         "emulated_over_native": value / nat_tflops,
-        "phases_ms": {"prep": statistics.mean(prep_ms), "products_and_reconstruction": g_ms},
+        "phases_ms": {"prep": statistics.mean(prep_ms), "products": g_ms, "reconstruction": statistics.mean(recon_ms)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
                      "frac": achieved / bf16_burst, "frac_of_sustained": achieved / bf16_sust,
                      "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
-                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, fused CRT), with "
-                               "k_mod_gemm<0> for the last wave's tiles (cta_group::1)",
+                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, residues parked), "
+                               "with k_mod_gemm<0> for the last wave's tiles (cta_group::1)",
                      "peak_source": f"{src} bf16_tflops (burst: one call of about 10 ms)"},
         "split": {
             "value": split["value"], "unit": "TFLOP/s", "ms_per_call": split["ms"], "steps": split["steps"],

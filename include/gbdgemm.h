@@ -108,6 +108,8 @@ typedef struct gbd_emu_info {
                        error at the chosen precision (0 when exact) */
   double prep_ms;   /* record_phases: device time of the preparation and certification kernels */
   double gemm_ms;   /* record_phases: device time of the product kernels */
+  double recon_ms;  /* record_phases, modular path: device time of the reconstruction of C from
+                       the parked residues (after the products); 0 for the other paths */
 } gbd_emu_info;
 
 /*

@@ -166,15 +166,29 @@ struct ModPlan {
 struct ModTableEntry {
   CUtensorMap tmA;  // residue planes of op(A): dims {k, m, kMaxModuli}, box {64, 128, 1}
   CUtensorMap tmB;  // residue planes of op(B)^T: dims {k, n, kMaxModuli}, box {64, 128, 1}
-  int64_t m, n, ldc;
-  double beta;
-  double* C;
-  const int* sigA;
-  const int* badA;
-  const double* cs;     // [n] alpha 2^(tau_j - 2t), from the problem's plan
+  int64_t m, n;
   const ModPlan* plan;  // the problem's t, n and feasibility
+  uint8_t* park;        // the problem's parked residues (layout of ModArgs::park)
   int64_t tile_begin;   // first tile of this problem in the launch
   int nkb, tiles_m, group_m, num_tiles;
+  int park_mods, nbn;   // moduli per block of the park array; 128-column blocks of C
+};
+// The reconstruction of one product from its parked residues: every 128 x 128 block of C (in a
+// batched launch, the jobs' blocks one after the other from blk_begin)
+struct CrtJob {
+  const uint8_t* park;  // [nbm * nbn blocks][park_mods][128 x 128 bytes]
+  const ModPlan* plan;
+  double* C;
+  const int* sigA;      // row exponents of op(A) (and non-finite flags)
+  const int* badA;
+  const double* cs;     // [n] alpha 2^(tau_j - 2t) (NaN for a column with a non-finite entry)
+  int64_t m, n, ldc;
+  double beta;
+  int64_t blk_begin;
+  int park_mods, nbm, nbn;
+  int tri;              // 0: all of C; 1: its lower triangle (i >= j); 2: its upper one
+  int skip_infeasible;  // grouped: a problem whose plan is infeasible is left to the FP64 kernel
+  int pad;
 };
 // the device plan of one problem of a grouped launch, and its column scales
 struct ModPlanJob {
@@ -448,14 +462,13 @@ struct ModGrouped {
   // [0]: some problem's first plan found no feasible t (the BF16 retry runs); [1]: some problem's
   // final plan did (its FP64 fallback tiles run)
   unsigned int* flags_dev = nullptr;
-  uint8_t* scr = nullptr;                  // park slots of the product launch
-  int scr_ctas = 0;
+  std::vector<CrtJob> crt;                 // the reconstructions, in the product table's order
+  CrtJob* crt_dev = nullptr;
+  int64_t crt_blocks = 0;
 };
 // Bytes of the grouped modular part for the problems probs[which[q]], q < count (host-only).
 // With base, lays out the workspace from there and builds the host tables into g.
 size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count, void* base, ModGrouped* g, int* rc);
-// copies the tables to the device (asynchronous on s; the host vectors must live until it ran)
-int mod_grouped_upload(const ModGrouped& g, cudaStream_t s);
 // one run: preparation, certification, plans, residues, column scales and the products
 int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s);
 

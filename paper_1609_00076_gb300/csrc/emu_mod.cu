@@ -30,51 +30,43 @@ namespace {
 using namespace tc;
 
 constexpr int kReduceChunks = 63;  // 63 chunks of 1024 k (each below 2^24) plus a residue stay below 2^30
-// parked residue bytes: per CTA two slots (the tile being multiplied and the one being
-// reconstructed) of [modulus][column / 4][128 rows][4 columns] bytes, sized for the widest tile:
-// a thread moves four columns in one 32-bit word and a warp 128 contiguous bytes
-constexpr int kSlotCols = 256;
-constexpr int64_t kLStride = (int64_t)kSlotCols * 128;
-constexpr int64_t kSlotBytes = (int64_t)kMaxModuli * kLStride;
-constexpr int kMaxModCtas = 256;
-// few-tile problems split each 128 x 128 tile's moduli over several CTAs (at most this many tiles)
-constexpr int kSplitMaxTiles = 64;
-constexpr int64_t kTileSlotBytes = (int64_t)kMaxModuli * (128 / 4) * 128 * 4;  // one tile's parked bytes
+// The parked residues: for every 128 x 128 block of C (row block rb, column block cb, block
+// rb * nbn + cb) and modulus l, one plane of [column / 4][row][4 columns] bytes, so that a thread
+// moves four columns in one word and a warp 128 contiguous bytes
+constexpr int64_t kParkBlock = 128 * 128;
 
-// the reconstruction constants of the first n moduli (M = p_0 ... p_(n-1))
+// the reconstruction constants of the first n moduli (M = p_0 ... p_(n-1), W_l = M / p_l,
+// c_l = W_l^-1 mod p_l): with r_l = C' mod p_l in [0, p_l), X = sum_l r_l V_l, V_l = c_l W_l < M,
+// is congruent to C' modulo M, and X / M = sum_l r_l c_l / p_l
 struct CrtSet {
-  int c[kMaxModuli];            // (M/p_l)^-1 mod p_l
-  uint32_t mpl[kMaxModuli][4];  // M/p_l in 32-bit limbs, least significant first
-  uint64_t M_lo, M_hi, half_lo, half_hi;  // M and floor(M/2)
+  uint32_t v[kMaxModuli][4];  // V_l in 32-bit limbs, least significant first
+  uint32_t e[kMaxModuli];     // ceil(c_l 2^16 / p_l): sum_l r_l e_l / 2^16 exceeds X / M by less than 1/16
+  uint32_t M[4];              // M
+  uint32_t H[4];              // M / 2 - 1 (M is even: p_0 = 256)
+};
+struct CrtConsts {
+  CrtSet set[kMaxModuli];  // set[n - 1]: the constants for the first n moduli
 };
 
 struct ModArgs {
-  int64_t m, n, ldc;
+  int64_t m, n;
   int nkb;
   int tiles_m, num_tiles, group_m;
   int tile_end;  // the two-SM form computes tiles [0, tile_end) of its num_tiles
-  int tri;       // 0: all of C; 1: only its lower triangle (i >= j), 2: its upper one (m = n): the
-                 // tiles are those that meet the triangle, and elements outside it are neither
-                 // read nor written
+  int tri;       // 0: all of C; 1: only the tiles that meet its lower triangle (i >= j), 2: its
+                 // upper one (m = n), by rows of tiles
   // a one-SM launch over the tail of a two-SM raster (tail_from >= 0): its tile u is quadrant
   // u % 4 of the 256 x 256 tile tail_from + u / 4 of that raster (tail_tiles_m, tail_group_m,
   // tail_num as tiles_m, group_m and num_tiles of the two-SM launch)
   int tail_from, tail_tiles_m, tail_group_m, tail_num;
   int p[kMaxModuli];         // moduli
   uint32_t bar[kMaxModuli];  // floor(2^32 / p_l), for Barrett reduction
-  uint32_t rq[kMaxModuli];   // ceil(2^24 / p_l)
-  CrtSet set[kMaxModuli];    // set[n - 1]: the constants for the first n moduli
   const ModPlan* plan;       // the call's n (and whether the target was reachable)
-  double beta;
-  double* C;
-  const int* sigA;
-  const int* badA;
-  const double* cs;  // [n] alpha 2^(tau_j - 2t); NaN for a column with a non-finite entry
-  uint8_t* scr;      // [CTA][2][kMaxModuli][kSlotCols / 4][128][4] parked u_l
+  uint8_t* park;             // [blocks][park_mods][kParkBlock] the residues of the products
+  int park_mods;             // moduli the park array holds per block
+  int nbn;                   // 128-column blocks of C
   // split over moduli (one-SM form, few tiles): each tile's moduli in `groups` work units
   int groups;
-  uint8_t* tslot;            // [tile][kMaxModuli][kBN / 4][128][4] parked u_l of every unit of the tile
-  unsigned int* tile_done;   // [tile] finished units (zero at launch)
   unsigned int* err;
 };
 
@@ -130,89 +122,21 @@ __device__ __forceinline__ int mod_nonneg(int v, uint32_t p, uint32_t b) {
   return (int)mod_barrett((uint32_t)v + (p << 23), p, b);
 }
 
-typedef unsigned __int128 u128;
-
-__device__ __forceinline__ u128 make_u128(uint64_t hi, uint64_t lo) { return ((u128)hi << 64) | lo; }
-
-// C' from its parked bytes u_l = (C' mod p_l) c_l mod p_l: sum_l u_l (M/p_l) = (C' mod M) + q M
-// with q = floor(sum_l u_l / p_l).  Returns the representative of (-M/2, M/2] in two's
-// complement 128 bits.
-__device__ __forceinline__ u128 crt_combine(const uint32_t (&u)[kMaxModuli], const ModArgs& p, const CrtSet& cs,
-                                            int nmod) {
-  uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // limb sums, each below 16 * 255 * 2^32 < 2^44
-  uint32_t qfix = 0;                         // sum_l u_l ceil(2^24/p_l) < 2^29
-#pragma unroll
-  for (int l = 0; l < kMaxModuli; ++l) {
-    if (l < nmod) {
-      a0 += (uint64_t)u[l] * cs.mpl[l][0];
-      a1 += (uint64_t)u[l] * cs.mpl[l][1];
-      a2 += (uint64_t)u[l] * cs.mpl[l][2];
-      a3 += (uint64_t)u[l] * cs.mpl[l][3];
-      qfix += u[l] * p.rq[l];
-    }
-  }
-  const u128 s = (u128)a0 + ((u128)a1 << 32) + ((u128)a2 << 64) + ((u128)a3 << 96);  // modulo 2^128
-  // qfix / 2^24 exceeds sum_l u_l/p_l by less than 16 * 255 / 2^24, so its floor is q or q + 1
-  const u128 M = make_u128(cs.M_hi, cs.M_lo);
-  u128 cu = s - (u128)(qfix >> 24) * M;
-  if ((uint64_t)(cu >> 127)) cu += M;  // the estimate was one too large
-  else if (cu >= M) cu -= M;
-  const u128 half = make_u128(cs.half_hi, cs.half_lo);
-  return cu > half ? cu - M : cu;
-}
-
-// fl(v) 2^sig for a two's complement 128-bit v: fl rounds to nearest (ties to even); the
-// scaling rounds again only where the result leaves the normal range (as ldexp).  The common
-// case builds the double from integers.
-__device__ __forceinline__ double scaled_double(u128 v, int sig) {
-  const bool neg = (uint64_t)(v >> 127) != 0;
-  const u128 a = neg ? (u128)0 - v : v;
-  const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
-  if ((hi | lo) == 0ull) return 0.0;
-  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-  uint64_t mant = lo;
-  int e = 0;
-  if (nbits > 53) {
-    const int shift = nbits - 53;
-    mant = (uint64_t)(a >> shift);
-    const u128 rem = a & (((u128)1 << shift) - 1), hf = (u128)1 << (shift - 1);
-    e = shift;
-    if (rem > hf || (rem == hf && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++e;
-      }
-    }
-  }
-  // |v| rounded = mant 2^e with mant < 2^53
-  const int L = 64 - __clzll((long long)mant);
-  const int E = e + sig + L - 1;  // exponent of the scaled value
-  if (E >= -1022 && E <= 1023) {
-    const uint64_t bits = ((uint64_t)(E + 1023) << 52) | ((mant << (53 - L)) & 0xFFFFFFFFFFFFFull) |
-                          (neg ? 0x8000000000000000ull : 0ull);
-    return __longlong_as_double((long long)bits);
-  }
-  const double y = ldexp(ldexp((double)mant, e), sig);  // the first ldexp is exact
-  return neg ? -y : y;
-}
-
-// The epilogue of both product kernels.  Each thread owns one TMEM lane (a row of the CTA's
-// 128) and COLS columns of the TBN-wide tile.  Per modulus: drain the chunks into int32 sums,
-// park u_l; at each modulus boundary (sums dead), reconstruct a few groups of four columns of
-// the previous tile from its parked bytes and write them to C.  All loads of a group are
-// issued before its arithmetic, so a group waits for memory once.  nan_out: the plan found the
-// target unreachable; every result is NaN.
-// TABLE: the tiles belong to the problems of a grouped launch (table entries in tile order); each
-// tile takes its problem's sizes, C, scales and moduli count from its entry, and a tile whose
-// problem's plan is infeasible is skipped (another kernel computes that problem).
-template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE = false>
-__device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool nan_out, uint32_t tmem_base,
-                                             uint64_t* acc_full, uint64_t* acc_empty, int warp, int lane, int tile0,
-                                             int tile_step, int tbm, int row_off,
-                                             const ModTableEntry* table = nullptr, int count = 0) {
-  const CrtSet* cset = &p.set[nmod - 1];
+// The epilogue of the product kernels.  Each thread owns one TMEM lane (a row of the CTA's 128)
+// and COLS columns of the TBN-wide tile.  Per modulus: drain the 1024-deep chunks into int32
+// sums (reduced modulo p_l every kReduceChunks chunks), reduce modulo p_l and park the residues,
+// one byte each, in the block's plane of the park array (k_mod_crt rebuilds C from them).
+// SPLIT: the work units are (tile, group of moduli); TABLE: the tiles belong to the problems of a
+// grouped launch (table entries in tile order), and a tile whose problem's plan is infeasible is
+// skipped (another kernel computes that problem).
+template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE, bool SPLIT>
+__device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tmem_base, uint64_t* acc_full,
+                                         uint64_t* acc_empty, int warp, int lane, int unit0, int unit_step,
+                                         int units, int row_off, const ModTableEntry* table = nullptr,
+                                         int count = 0) {
   constexpr int COLS = TBN / (EPI_WARPS / 4);
+  constexpr int kGroups = COLS / 4;
+  static_assert(COLS % 4 == 0 && 128 % COLS == 0, "a thread's columns lie in one 128-column block");
   const int ew = warp - 2;
   const int quad = warp & 3;
   const int part = ew >> 2;
@@ -224,89 +148,43 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
     empty_remote[0] = map_to_rank(smem_u32(&acc_empty[0]), 0);
     empty_remote[1] = map_to_rank(smem_u32(&acc_empty[1]), 0);
   }
-  uint8_t* const scr_cta = p.scr + (int64_t)blockIdx.x * 2 * kSlotBytes + (int64_t)(col0 / 4) * 512 + row * 4;
-  constexpr int kGroups = COLS / 4;
-  int per_boundary = (kGroups + nmod - 1) / nmod;  // groups of four columns
-
-  // the pending reconstruction: this thread's row and columns of the previous tile
-  bool pd_active = false, pd_bad = false;
-  int pd_done = 0, pd_slot = 0, pd_sig = 0, pd_cols = 0, pd_first = 0;  // columns [pd_first, pd_cols) are written
-  double* pd_c = nullptr;
-  const double* pd_cs = nullptr;
-  // grouped: the pending tile's problem (its moduli, beta and leading dimension)
-  int pd_nmod = nmod;
-  const CrtSet* pd_cset = cset;
-  double pd_beta = p.beta;
-  int64_t pd_ldc = p.ldc;
-  auto advance = [&](int ngroups) {
-    const int g1 = min(pd_done + ngroups, kGroups);
-    const uint8_t* ub = scr_cta + (int64_t)pd_slot * kSlotBytes;
-    for (int g = pd_done; g < g1; ++g) {
-      const int c0 = 4 * g;
-      if (c0 >= pd_cols) break;
-      if (c0 + 4 <= pd_first) continue;
-      const int nm = TABLE ? pd_nmod : nmod;
-      const double beta = TABLE ? pd_beta : p.beta;
-      const int64_t ldc = TABLE ? pd_ldc : p.ldc;
-      uint32_t w4[kMaxModuli];  // the bytes of columns c0..c0+3, one word per modulus
-#pragma unroll
-      for (int l = 0; l < kMaxModuli; ++l)
-        w4[l] = l < nm ? *reinterpret_cast<const uint32_t*>(ub + l * kLStride + g * 512) : 0u;
-      double c0v[4], csv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool in = c0 + q < pd_cols && c0 + q >= pd_first;
-        c0v[q] = (in && beta != 0.0) ? pd_c[(int64_t)(c0 + q) * ldc] : 0.0;
-        csv[q] = in ? pd_cs[c0 + q] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (c0 + q >= pd_cols) break;
-        if (c0 + q < pd_first) continue;
-        uint32_t u[kMaxModuli];
-#pragma unroll
-        for (int l = 0; l < kMaxModuli; ++l) u[l] = (w4[l] >> (8 * q)) & 0xFFu;
-        const double w0 = beta != 0.0 ? beta * c0v[q] : 0.0;
-        double w;
-        if (nan_out || pd_bad || csv[q] != csv[q]) w = __longlong_as_double(0x7FF8000000000000ll);
-        else w = fma(csv[q], scaled_double(crt_combine(u, p, TABLE ? *pd_cset : *cset, nm), pd_sig), w0);
-        pd_c[(int64_t)(c0 + q) * ldc] = w;
-      }
-    }
-    pd_done = g1;
-    if (pd_done >= kGroups) pd_active = false;
-  };
-
+  const int groups = SPLIT ? min(p.groups, nmod) : 1;
   uint32_t chunk = 0;
   int acc[COLS];
-  int tcount = 0;
-  const int tile_end = PAIR ? p.tile_end : p.num_tiles;
   int cur = 0;  // grouped: the table entry of the current tile (a CTA's tiles increase)
-  for (int tile = tile0; tile < tile_end; tile += tile_step) {
-    int tm, tn, nkb = p.nkb;
-    const ModTableEntry* e = nullptr;
+  for (int u = unit0; u < units; u += unit_step) {
+    const int tile = SPLIT ? u / groups : u;
+    int l0 = 0, l1 = nmod, nkb = p.nkb, tm, tn;
+    uint8_t* park = p.park;
+    int pmods = p.park_mods, nbn = p.nbn;
+    int64_t pm = p.m, pn = p.n;
+    if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
     if (TABLE) {
       while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
-      e = &table[cur];
-      const ModPlan* pl = e->plan;
+      const ModTableEntry& e = table[cur];
+      const ModPlan* pl = e.plan;
       if (!pl->feasible) continue;  // computed by the FP64 kernel instead
-      nmod = pl->n;
-      nkb = e->nkb;
-      cset = &p.set[nmod - 1];
-      per_boundary = (kGroups + nmod - 1) / nmod;
-      tile_coords(tile - (int)e->tile_begin, e->tiles_m, e->group_m, e->num_tiles, tm, tn);
+      l1 = pl->n;
+      nkb = e.nkb;
+      tile_coords(tile - (int)e.tile_begin, e.tiles_m, e.group_m, e.num_tiles, tm, tn);
+      park = e.park;
+      pmods = e.park_mods;
+      nbn = e.nbn;
+      pm = e.m;
+      pn = e.n;
     } else if (PAIR) {
       raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
     } else {
       tile128_coords(p, tile, tm, tn);
     }
-    const int64_t i = (int64_t)tm * tbm + row_off + row;
-    const int64_t jc0 = (int64_t)tn * TBN + col0;
-    const int slot = tcount & 1;
-    ++tcount;
-    uint8_t* const ub = scr_cta + (int64_t)slot * kSlotBytes;
-    for (int l = 0; l < nmod; ++l) {
-      const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
+    // this thread's 128 x 128 block of C; a block wholly outside C is not parked
+    const int rb = PAIR ? 2 * tm + (row_off >> 7) : tm;
+    const int cb = PAIR ? 2 * tn + (col0 >> 7) : tn;
+    const bool inside = (int64_t)rb * 128 < pm && (int64_t)cb * 128 < pn;
+    uint8_t* const pb = park + ((int64_t)rb * nbn + cb) * pmods * kParkBlock + (int64_t)((col0 & 127) / 4) * 512 +
+                        row * 4;
+    for (int l = l0; l < l1; ++l) {
+      const uint32_t pmod = (uint32_t)p.p[l], bm = p.bar[l];
 #pragma unroll
       for (int c = 0; c < COLS; ++c) acc[c] = 0;
       int nch = 0;
@@ -328,155 +206,18 @@ __device__ __forceinline__ void mod_epilogue(const ModArgs& p, int nmod, bool na
         if (++nch == kReduceChunks) {  // keep the running sums below 2^30 in magnitude
           nch = 0;
 #pragma unroll
-          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
+          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pmod, bm);
         }
       }
-      const uint32_t cl = (uint32_t)cset->c[l];
+      if (inside) {
+        unsigned int* const dst = reinterpret_cast<unsigned int*>(pb + (int64_t)l * kParkBlock);
 #pragma unroll
-      for (int g = 0; g < kGroups; ++g) {
-        uint32_t w = 0u;
+        for (int g = 0; g < kGroups; ++g) {
+          uint32_t w = 0u;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          w |= mod_barrett((uint32_t)mod_nonneg(acc[4 * g + b], pm, bm) * cl, pm, bm) << (8 * b);
-        *reinterpret_cast<uint32_t*>(ub + l * kLStride + g * 512) = w;
-      }
-      if (pd_active) advance(l + 1 == nmod ? kGroups : per_boundary);
-    }
-    // this tile's residues are complete: it becomes the pending reconstruction
-    const int64_t pm = TABLE ? e->m : p.m, pn = TABLE ? e->n : p.n;
-    const bool row_ok = i < pm;
-    pd_active = true;
-    pd_done = 0;
-    pd_slot = slot;
-    pd_cols = row_ok && jc0 < pn ? (int)min((int64_t)COLS, pn - jc0) : 0;
-    pd_first = 0;
-    if (!TABLE && p.tri == 1) pd_cols = (int)max((int64_t)0, min((int64_t)pd_cols, i - jc0 + 1));  // j <= i
-    else if (!TABLE && p.tri == 2) pd_first = (int)max((int64_t)0, i - jc0);                      // j >= i
-    pd_sig = 0;
-    pd_bad = false;
-    const int* sigA = TABLE ? e->sigA : p.sigA;
-    const int* badA = TABLE ? e->badA : p.badA;
-    if (row_ok) {
-      const int sg = sigA[i];
-      pd_sig = sg == kExpEmpty ? 0 : sg;
-      pd_bad = badA[i] != 0;
-    }
-    if (TABLE) {
-      pd_nmod = nmod;
-      pd_cset = cset;
-      pd_beta = e->beta;
-      pd_ldc = e->ldc;
-      pd_c = e->C + jc0 * e->ldc + i;  // dereferenced only for the pd_cols columns inside C
-      pd_cs = e->cs + jc0;
-    } else {
-      pd_c = p.C + jc0 * p.ldc + i;
-      pd_cs = p.cs + jc0;
-    }
-  }
-  if (pd_active) advance(kGroups);
-}
-
-// The epilogue of the split form (one-SM kernel, 128 x 128 tiles, few of them): the moduli
-// of a tile are spread over `groups` work units on different CTAs.  Each unit drains its
-// moduli and parks their bytes in the tile's global slot; after a barrier of the epilogue
-// warps one thread publishes the unit (fence, then a counter per tile); the CTA that
-// finishes the tile's last unit rebuilds the whole tile from the slot, immediately.
-template <int EPI_WARPS, int TBN>
-__device__ __forceinline__ void mod_epilogue_split(const ModArgs& p, int nmod, bool nan_out, uint32_t tmem_base,
-                                                   uint64_t* acc_full, uint64_t* acc_empty, int* last_flag, int warp,
-                                                   int lane) {
-  constexpr int COLS = TBN / (EPI_WARPS / 4);
-  constexpr int kGroups = COLS / 4;
-  constexpr int64_t kTileStride = (int64_t)TBN / 4 * 128 * 4;  // one modulus of one tile
-  const CrtSet& cset = p.set[nmod - 1];
-  const int ew = warp - 2;
-  const int quad = warp & 3;
-  const int part = ew >> 2;
-  const int row = quad * 32 + lane;
-  const int col0 = part * COLS;
-  const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16);
-  const int groups = min(p.groups, nmod);
-  const int units = p.num_tiles * groups;
-  uint32_t chunk = 0;
-  int acc[COLS];
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
-    const int tile = u / groups;
-    int l0, l1;
-    unit_range(u % groups, groups, nmod, l0, l1);
-    uint8_t* const ub = p.tslot + (int64_t)tile * kMaxModuli * kTileStride + (int64_t)(col0 / 4) * 512 + row * 4;
-    for (int l = l0; l < l1; ++l) {
-      const uint32_t pm = (uint32_t)p.p[l], bm = p.bar[l];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) acc[c] = 0;
-      int nch = 0;
-      for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
-        const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-        mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
-        tc_fence_after();
-        const uint32_t taddr = trow + buf * TBN + col0;
-#pragma unroll
-        for (int q = 0; q < COLS / 16; ++q) {
-          uint32_t v[16];
-          tmem_ld_16(taddr + q * 16, v);
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
+          for (int b = 0; b < 4; ++b) w |= (uint32_t)mod_nonneg(acc[4 * g + b], pmod, bm) << (8 * b);
+          __stcs(dst + g * 128, w);  // read once, by the reconstruction
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[buf]);
-        if (++nch == kReduceChunks) {
-          nch = 0;
-#pragma unroll
-          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pm, bm);
-        }
-      }
-      const uint32_t cl = (uint32_t)cset.c[l];
-#pragma unroll
-      for (int g = 0; g < kGroups; ++g) {
-        uint32_t w = 0u;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          w |= mod_barrett((uint32_t)mod_nonneg(acc[4 * g + b], pm, bm) * cl, pm, bm) << (8 * b);
-        *reinterpret_cast<uint32_t*>(ub + l * kTileStride + g * 512) = w;
-      }
-    }
-    // publish the unit; the last of the tile's units rebuilds it
-    epi_barrier<EPI_WARPS>();
-    if (warp == 2 && lane == 0) {
-      __threadfence();
-      const unsigned int prev = atomicAdd(p.tile_done + tile, 1u);
-      *last_flag = prev + 1u == (unsigned int)groups;
-    }
-    epi_barrier<EPI_WARPS>();
-    if (!*last_flag) continue;
-    __threadfence();  // the other units' bytes, published before their counts
-    int tm, tn;
-    tile_coords(tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-    const int64_t i = (int64_t)tm * 128 + row;
-    const int64_t jc0 = (int64_t)tn * TBN + col0;
-    if (i >= p.m || jc0 >= p.n) continue;
-    const int cols = (int)min((int64_t)COLS, p.n - jc0);
-    const int sg = p.sigA[i];
-    const int sig = sg == kExpEmpty ? 0 : sg;
-    const bool bad = p.badA[i] != 0;
-    double* crow = p.C + jc0 * p.ldc + i;
-    for (int g = 0; g * 4 < cols; ++g) {
-      uint32_t w4[kMaxModuli];
-#pragma unroll
-      for (int l = 0; l < kMaxModuli; ++l)
-        w4[l] = l < nmod ? __ldcg(reinterpret_cast<const unsigned int*>(ub + l * kTileStride + g * 512)) : 0u;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = 4 * g + q;
-        if (c >= cols) break;
-        uint32_t uu[kMaxModuli];
-#pragma unroll
-        for (int l = 0; l < kMaxModuli; ++l) uu[l] = (w4[l] >> (8 * q)) & 0xFFu;
-        const double csv = p.cs[jc0 + c];
-        const double w0 = p.beta != 0.0 ? p.beta * crow[(int64_t)c * p.ldc] : 0.0;
-        double w;
-        if (nan_out || bad || csv != csv) w = __longlong_as_double(0x7FF8000000000000ll);
-        else w = fma(csv, scaled_double(crt_combine(uu, p, cset, nmod), sig), w0);
-        crow[(int64_t)c * p.ldc] = w;
       }
     }
   }
@@ -521,7 +262,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_empty = bars + 2 * kStages + 2;
   uint64_t* done = bars + 2 * kStages + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffTmemSlot);
-  int* last_flag = reinterpret_cast<int*>(smem + L::kOffTmemSlot + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0 && lane == 0) {
@@ -641,12 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     __syncwarp();
-  } else if (SPLIT) {
-    mod_epilogue_split<kEpiWarps, kBN>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, last_flag, warp,
-                                       lane);
   } else {
-    mod_epilogue<kEpiWarps, kBN, false, TABLE>(p, nmod, !TABLE && plan.feasible == 0, tmem_base, acc_full, acc_empty,
-                                               warp, lane, blockIdx.x, gridDim.x, kBM, 0, table, count);
+    mod_park<kEpiWarps, kBN, false, TABLE, SPLIT>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, blockIdx.x,
+                                                  gridDim.x, units, 0, table, count);
   }
 
   tc_fence_before();
@@ -667,7 +404,7 @@ constexpr int k2Stages = 6;
 constexpr int k2EpiWarps = 16;  // 4 x 4 warps over 128 TMEM lanes x 256 columns
 constexpr int k2Threads = 64 + 32 * k2EpiWarps;
 constexpr int k2TmemCols = 2 * k2BN;
-static_assert(k2BN <= kSlotCols && kBN <= kSlotCols, "parked bytes of a tile fit one slot");
+static_assert(kBM == 128 && kBN == 128 && k2BN == 256, "the park array is laid out in 128 x 128 blocks");
 
 struct Smem2 {
   static constexpr int kABytes = 128 * kBK * 2;
@@ -782,8 +519,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     __syncwarp();
   } else {
-    mod_epilogue<k2EpiWarps, k2BN, true>(p, nmod, plan.feasible == 0, tmem_base, acc_full, acc_empty, warp, lane,
-                                         pair_id, num_pairs, k2BM, (int)rank * 128);
+    mod_park<k2EpiWarps, k2BN, true, false, false>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
+                                                   num_pairs, p.tile_end, (int)rank * 128);
   }
 
   tc_fence_before();
@@ -793,6 +530,260 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(k2TmemCols)
                  : "memory");
+  }
+}
+
+// ---- the reconstruction: C from the parked residues ----
+// One CTA of 256 threads per 128 x 128 block of C at a time: thread (row, g) rebuilds the four
+// columns 4g .. 4g+3 of its row from one word per modulus, g = threadIdx.x / 128 + 2 i.  A warp
+// reads 128 contiguous bytes per modulus and writes 32 consecutive rows of a column.
+// C := fma(alpha 2^(tau_j - 2t), fl(C') 2^sigma_i, beta C0), fl correctly rounded (ties to even)
+// and the scaling as ldexp; NaN for a row or column with a non-finite entry, and everywhere when
+// the plan found the target unreachable.  The arithmetic is on 32-bit limbs, specialised for the
+// number of moduli N (L = 3 limbs while M < 2^95, that is N <= 12, else 4), so that the
+// constants are immediate operands; when beta = 0 and alpha 2^(tau_j - 2t) is a power of two
+// (alpha a power of two) the result is assembled from integers, without FP64 arithmetic.
+constexpr int kCrtThreads = 256;
+
+template <int L>
+__device__ __forceinline__ void limbs_add(uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  if constexpr (L == 3) {
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2])
+        : "r"(y[0]), "r"(y[1]), "r"(y[2]));
+  } else {
+    asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, %5;\n\taddc.cc.u32 %2, %2, %6;\n\taddc.u32 %3, %3, %7;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3])
+        : "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]));
+  }
+}
+template <int L>
+__device__ __forceinline__ void limbs_sub(uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  if constexpr (L == 3) {
+    asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, %5;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2])
+        : "r"(y[0]), "r"(y[1]), "r"(y[2]));
+  } else {
+    asm("sub.cc.u32 %0, %0, %4;\n\tsubc.cc.u32 %1, %1, %5;\n\tsubc.cc.u32 %2, %2, %6;\n\tsubc.u32 %3, %3, %7;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3])
+        : "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]));
+  }
+}
+
+// fl(C') for the residues r_l = byte q of w[l]: the sign, the unbiased exponent E of the rounded
+// value and its 53-bit significand with the implicit bit (mant in [2^52, 2^53], 2^53 when the
+// rounding carried), or zero.  X = sum_l r_l V_l modulo 2^(32 L); Qe = floor(sum_l r_l e_l / 2^16
+// + 1/2) is round(X / M) or one more, and one more only when X - Qe M <= -M/2: then M is added
+// back.  The result lies in (-M/2, M/2].
+template <int N>
+__device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[kMaxModuli], int q, uint32_t& sign,
+                                          int& E, uint64_t& mant) {
+  constexpr int L = N <= 12 ? 3 : 4;
+  uint64_t a[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) a[j] = 0;
+  uint32_t qe = 1u << 15;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const uint32_t r = __byte_perm(w[l], 0u, 0x4440u + (uint32_t)q);
+#pragma unroll
+    for (int j = 0; j < L; ++j) a[j] += (uint64_t)r * S.v[l][j];
+    qe += r * S.e[l];
+  }
+  // X modulo 2^(32 L) from the limb sums (each below 2^44)
+  uint32_t x[L];
+  uint64_t t = a[0];
+  x[0] = (uint32_t)t;
+#pragma unroll
+  for (int j = 1; j < L; ++j) {
+    t = (t >> 32) + a[j];
+    x[j] = (uint32_t)t;
+  }
+  // X - Qe M
+  const uint32_t Q = qe >> 16;
+  uint32_t qm[L];
+  t = (uint64_t)Q * S.M[0];
+  qm[0] = (uint32_t)t;
+#pragma unroll
+  for (int j = 1; j < L; ++j) {
+    t = (t >> 32) + (uint64_t)Q * S.M[j];
+    qm[j] = (uint32_t)t;
+  }
+  limbs_sub<L>(x, qm);
+  // X - Qe M <= -M/2 exactly when X - Qe M + (M/2 - 1) is negative
+  uint32_t h[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) h[j] = x[j];
+  uint32_t hc[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) hc[j] = S.H[j];
+  limbs_add<L>(h, hc);
+  const uint32_t fix = 0u - (h[L - 1] >> 31);
+  uint32_t mm[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) mm[j] = S.M[j] & fix;
+  limbs_add<L>(x, mm);
+  // sign and magnitude
+  sign = x[L - 1] >> 31;
+  const uint32_t neg = 0u - sign;
+  uint32_t sg[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    x[j] ^= neg;
+    sg[j] = j == 0 ? sign : 0u;
+  }
+  limbs_add<L>(x, sg);
+  // normalise: the leading one to bit 32 L - 1
+  int lz = 0;
+#pragma unroll
+  for (int step = 0; step < L - 1; ++step) {
+    if (x[L - 1] == 0u) {
+#pragma unroll
+      for (int j = L - 1; j > 0; --j) x[j] = x[j - 1];
+      x[0] = 0u;
+      lz += 32;
+    }
+  }
+  if (x[L - 1] == 0u) return false;  // C' = 0
+  const int c = __clz((int)x[L - 1]);
+#pragma unroll
+  for (int j = L - 1; j > 0; --j) x[j] = __funnelshift_l(x[j - 1], x[j], c);
+  x[0] <<= c;
+  lz += c;
+  E = 32 * L - 1 - lz;
+  // the top 53 bits, rounded to nearest, ties to even, on the 32 L - 53 bits below
+  const uint64_t m = ((uint64_t)x[L - 1] << 21) | (x[L - 2] >> 11);
+  uint32_t sticky = x[L - 2] & 0x3FFu;
+#pragma unroll
+  for (int j = 0; j < L - 2; ++j) sticky |= x[j];
+  const uint32_t half = (x[L - 2] >> 10) & 1u;
+  mant = m + (half & ((sticky != 0u) | (uint32_t)(m & 1u)));
+  return true;
+}
+
+template <int N>
+__device__ __forceinline__ void crt_rows(const CrtSet& S, const CrtJob& job, bool nan_out, int rb, int cb) {
+  // the job's fields in registers (the stores to C cannot alias them then)
+  const int64_t m = job.m, n = job.n, ldc = job.ldc;
+  const double beta = job.beta;
+  const int tri = job.tri;
+  double* const C = job.C;
+  const double* const cs = job.cs;
+  const int row = threadIdx.x & 127;
+  const int64_t i = (int64_t)rb * 128 + row;
+  if (i >= m) return;
+  const int sg = job.sigA[i];
+  const int sig = sg == kExpEmpty ? 0 : sg;
+  const bool bad = nan_out || job.badA[i] != 0;
+  const bool beta0 = beta == 0.0;
+  const uint8_t* const pb = job.park + ((int64_t)rb * job.nbn + cb) * job.park_mods * kParkBlock + row * 4;
+  for (int g = threadIdx.x >> 7; g < 32; g += kCrtThreads / 128) {
+    const int64_t j0 = (int64_t)cb * 128 + 4 * g;
+    if (j0 >= n) break;
+    uint32_t w[kMaxModuli];
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+      w[l] = __ldcs(reinterpret_cast<const unsigned int*>(pb + (int64_t)l * kParkBlock + g * 512));
+#pragma unroll
+    for (int l = N; l < kMaxModuli; ++l) w[l] = 0u;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int64_t jj = j0 + q;
+      const bool in = jj < n && (tri == 0 || (tri == 1 ? jj <= i : jj >= i));
+      if (!in) continue;
+      const double csv = cs[jj];
+      const uint64_t cbits = (uint64_t)__double_as_longlong(csv);
+      double* const dst = C + jj * ldc + i;
+      if (bad || (cbits << 1) > 0xFFE0000000000000ull) {  // a non-finite row or column (NaN scale)
+        *dst = __longlong_as_double(0x7FF8000000000000ll);
+        continue;
+      }
+      uint32_t sign;
+      int E;
+      uint64_t mant;
+      const bool nz = crt_round<N>(S, w, q, sign, E, mant);
+      // y = fl(C') 2^sigma_i: its bits while it is a normal number (the rounding's carry moves
+      // into the exponent field)
+      const int ey = E + sig + 1023;  // biased exponent before the carry
+      const uint64_t ybits = nz ? ((uint64_t)(ey - 1) << 52) + mant : 0ull;
+      const bool y_normal = !nz || (ey >= 1 && (ybits >> 52) <= 2046);
+      const int ecs = (int)((cbits >> 52) & 0x7FF);
+      if (beta0 && y_normal && (cbits & 0x000FFFFFFFFFFFFFull) == 0 && ecs >= 1 && ecs <= 2046) {
+        // alpha 2^(tau_j - 2t) = +-2^(ecs - 1023): an exact scaling while the result stays normal
+        if (!nz) {
+          *dst = 0.0;  // fma(cs, +0, +0) = +0
+          continue;
+        }
+        const int eo = (int)(ybits >> 52) + ecs - 1023;
+        if (eo >= 1 && eo <= 2046) {
+          const uint64_t ob = (ybits + ((uint64_t)(int64_t)(ecs - 1023) << 52)) |
+                              ((uint64_t)(sign ^ (uint32_t)(cbits >> 63)) << 63);
+          *dst = __longlong_as_double((long long)ob);
+          continue;
+        }
+      }
+      double y = 0.0;
+      if (nz) {
+        if (y_normal) y = __longlong_as_double((long long)ybits);
+        else y = ldexp((double)mant, E - 52 + sig);  // one rounding of the exact fl(C') 2^sigma_i
+        if (sign) y = -y;
+      }
+      const double w0 = beta0 ? 0.0 : beta * *dst;
+      *dst = fma(csv, y, w0);
+    }
+  }
+}
+
+// each count of moduli its own function (register allocation of one specialisation at a time)
+template <int N>
+__device__ __noinline__ void crt_block_n(const CrtConsts& K, const CrtJob& j, bool nan_out, int rb, int cb) {
+  crt_rows<N>(K.set[N - 1], j, nan_out, rb, cb);
+}
+
+__device__ __forceinline__ void crt_block(const CrtConsts& K, const CrtJob& j, int64_t blk) {
+  const ModPlan pl = *j.plan;
+  if (!pl.feasible && j.skip_infeasible) return;
+  const int rb = (int)(blk / j.nbn), cb = (int)(blk % j.nbn);
+  // a triangular output: the blocks wholly outside the triangle were never multiplied
+  if ((j.tri == 1 && cb > rb) || (j.tri == 2 && cb < rb)) return;
+  const bool nan_out = !pl.feasible;
+  switch (pl.n) {
+    case 1: crt_block_n<1>(K, j, nan_out, rb, cb); break;
+    case 2: crt_block_n<2>(K, j, nan_out, rb, cb); break;
+    case 3: crt_block_n<3>(K, j, nan_out, rb, cb); break;
+    case 4: crt_block_n<4>(K, j, nan_out, rb, cb); break;
+    case 5: crt_block_n<5>(K, j, nan_out, rb, cb); break;
+    case 6: crt_block_n<6>(K, j, nan_out, rb, cb); break;
+    case 7: crt_block_n<7>(K, j, nan_out, rb, cb); break;
+    case 8: crt_block_n<8>(K, j, nan_out, rb, cb); break;
+    case 9: crt_block_n<9>(K, j, nan_out, rb, cb); break;
+    case 10: crt_block_n<10>(K, j, nan_out, rb, cb); break;
+    case 11: crt_block_n<11>(K, j, nan_out, rb, cb); break;
+    case 12: crt_block_n<12>(K, j, nan_out, rb, cb); break;
+    case 13: crt_block_n<13>(K, j, nan_out, rb, cb); break;
+    case 14: crt_block_n<14>(K, j, nan_out, rb, cb); break;
+    case 15: crt_block_n<15>(K, j, nan_out, rb, cb); break;
+    default: crt_block_n<16>(K, j, nan_out, rb, cb); break;
+  }
+}
+
+// one product (jobs == nullptr: `one`), or the jobs of a grouped launch (blocks in job order)
+__global__ void __launch_bounds__(kCrtThreads, 3) k_mod_crt(const __grid_constant__ CrtConsts K,
+                                                            const __grid_constant__ CrtJob one,
+                                                            const CrtJob* __restrict__ jobs, int count, int64_t total) {
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    if (!jobs) {
+      crt_block(K, one, b);
+      continue;
+    }
+    int lo = 0, hi = count - 1;  // the last job whose blocks begin at or before b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].blk_begin <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const CrtJob jb = jobs[lo];
+    crt_block(K, jb, b - jb.blk_begin);
   }
 }
 
@@ -956,24 +947,16 @@ struct ModWorkspace {
   double* cs;    // [n]
   uint16_t* DA;  // [nmod][m][kp]
   uint16_t* DB;  // [nmod][n][kp]
-  uint8_t* scr;  // [scr_ctas][2][kSlotBytes]
-  int scr_ctas;
-  uint8_t* tslot;            // [tiles][kTileSlotBytes] when the split form may run, else null
-  unsigned int* tile_done;   // [tiles]
+  uint8_t* park;  // [nbm * nbn][nmod][kParkBlock] the residues of the products
+  int nbm, nbn;   // 128-row and 128-column blocks of C
+  int park_mods;
   int64_t kp;
 };
 
-// scratch = false (a problem of a grouped launch): no park slots, no split-form slots; the
-// launch has its own
-size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWorkspace* ws, bool scratch = true) {
+size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWorkspace* ws) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int64_t kp = (k + 7) / 8 * 8;
-  // one CTA per 128 x 128 tile (one-SM form) or two per 256 x 256 tile (two-SM form), at most kMaxModCtas
-  const int64_t tiles1 = ((m + 127) / 128) * ((n + 127) / 128);
-  const int64_t tiles2 = ((m + 255) / 256) * ((n + 255) / 256);
-  int64_t ctas = tiles1 > 2 * tiles2 ? tiles1 : 2 * tiles2;
-  if (ctas > kMaxModCtas) ctas = kMaxModCtas;
-  if (!scratch) ctas = 0;
+  const int64_t nbm = (m + 127) / 128, nbn = (n + 127) / 128;
   size_t off = 0;
   const size_t o_sigA = off; off = up(off + sizeof(int) * (size_t)m);
   const size_t o_sigB = off; off = up(off + sizeof(int) * (size_t)n);
@@ -994,10 +977,7 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
   const size_t o_cs = off; off = up(off + sizeof(double) * (size_t)n);
   const size_t o_DA = off; off = up(off + 2 * (size_t)nmod * (size_t)m * (size_t)kp);
   const size_t o_DB = off; off = up(off + 2 * (size_t)nmod * (size_t)n * (size_t)kp);
-  const size_t o_scr = off; off = up(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
-  const int64_t split_tiles = (scratch && tiles1 <= kSplitMaxTiles) ? tiles1 : 0;
-  const size_t o_tslot = off; off = up(off + (size_t)kTileSlotBytes * (size_t)split_tiles);
-  const size_t o_tdone = off; off = up(off + sizeof(unsigned int) * (size_t)split_tiles);
+  const size_t o_park = off; off = up(off + (size_t)kParkBlock * (size_t)nmod * (size_t)(nbm * nbn));
   if (base && ws) {
     char* b = static_cast<char*>(base);
     ws->sigA = reinterpret_cast<int*>(b + o_sigA);
@@ -1023,10 +1003,10 @@ size_t mod_layout(int64_t m, int64_t n, int64_t k, int nmod, void* base, ModWork
     ws->cs = reinterpret_cast<double*>(b + o_cs);
     ws->DA = reinterpret_cast<uint16_t*>(b + o_DA);
     ws->DB = reinterpret_cast<uint16_t*>(b + o_DB);
-    ws->scr = reinterpret_cast<uint8_t*>(b + o_scr);
-    ws->scr_ctas = (int)ctas;
-    ws->tslot = split_tiles ? reinterpret_cast<uint8_t*>(b + o_tslot) : nullptr;
-    ws->tile_done = split_tiles ? reinterpret_cast<unsigned int*>(b + o_tdone) : nullptr;
+    ws->park = reinterpret_cast<uint8_t*>(b + o_park);
+    ws->nbm = (int)nbm;
+    ws->nbn = (int)nbn;
+    ws->park_mods = nmod;
     ws->kp = kp;
   }
   return off;
@@ -1056,27 +1036,50 @@ int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
   return t < 0 ? t + p : t;
 }
 
-// the moduli, their Barrett constants and the reconstruction constants of every n = 1..kMaxModuli;
-// the rest of `a` zeroed
-void mod_constants(ModArgs& a, const ModProducts& prods) {
+// the moduli and their Barrett constants; the rest of `a` zeroed
+void mod_constants(ModArgs& a) {
   memset(&a, 0, sizeof(a));
   for (int l = 0; l < kMaxModuli; ++l) {
     a.p[l] = kModuli[l];
     a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
-    a.rq[l] = ((1u << 24) + (uint32_t)kModuli[l] - 1u) / (uint32_t)kModuli[l];
   }
-  for (int nn = 1; nn <= kMaxModuli; ++nn) {
-    CrtSet& cs = a.set[nn - 1];
-    const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
-    for (int l = 0; l < nn; ++l) {
-      const hu128 Mp = M / (hu128)kModuli[l];
-      cs.c[l] = (int)inverse_mod((int64_t)(Mp % (hu128)kModuli[l]), kModuli[l]);
-      for (int w = 0; w < 4; ++w) cs.mpl[l][w] = (uint32_t)(Mp >> (32 * w));
+}
+
+// the reconstruction constants of every n = 1..kMaxModuli (computed once)
+const CrtConsts& crt_constants() {
+  static const CrtConsts K = [] {
+    CrtConsts k;
+    memset(&k, 0, sizeof(k));
+    const ModProducts prods = moduli_products();
+    for (int nn = 1; nn <= kMaxModuli; ++nn) {
+      CrtSet& cs = k.set[nn - 1];
+      const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
+      for (int l = 0; l < nn; ++l) {
+        const hu128 W = M / (hu128)kModuli[l];
+        const int64_t c = inverse_mod((int64_t)(W % (hu128)kModuli[l]), kModuli[l]);
+        const hu128 V = (hu128)c * W;  // below M
+        for (int w = 0; w < 4; ++w) cs.v[l][w] = (uint32_t)(V >> (32 * w));
+        cs.e[l] = (uint32_t)((((uint64_t)c << 16) + (uint64_t)kModuli[l] - 1) / (uint64_t)kModuli[l]);
+      }
+      const hu128 H = M / 2 - 1;
+      for (int w = 0; w < 4; ++w) {
+        cs.M[w] = (uint32_t)(M >> (32 * w));
+        cs.H[w] = (uint32_t)(H >> (32 * w));
+      }
     }
-    cs.M_lo = (uint64_t)M; cs.M_hi = (uint64_t)(M >> 64);
-    const hu128 half = M / 2;
-    cs.half_lo = (uint64_t)half; cs.half_hi = (uint64_t)(half >> 64);
-  }
+    return k;
+  }();
+  return K;
+}
+
+// the reconstruction of one product (jobs == nullptr: `one`) or of a grouped launch's jobs
+int launch_mod_crt(const CrtJob& one, const CrtJob* jobs, int count, int64_t total, int sms, cudaStream_t s) {
+  if (total <= 0) return GBD_OK;
+  const int64_t cap = (int64_t)sms * 8;
+  const int grid = (int)(total < cap ? total : cap);
+  k_mod_crt<<<grid, kCrtThreads, 0, s>>>(crt_constants(), one, jobs, count, total);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "modular reconstruction launch");
 }
 
 // the residue split parameters of every modulus (t and n come from a plan)
@@ -1116,7 +1119,7 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const char* force = getenv("GBD_EMU_KERNEL");
   const bool force_split = force && strcmp(force, "split") == 0;
   if (force_split) force = nullptr;
-  const int cta_cap = sms < ws.scr_ctas ? sms : ws.scr_ctas;
+  const int cta_cap = sms;
   // a triangular output (m = n) covers the tiles that meet its triangle
   auto count = [&](int64_t bm, int64_t bn) {
     const int64_t tm = (m + bm - 1) / bm, tn = (n + bn - 1) / bn;
@@ -1157,19 +1160,15 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   a.tail_from = -1;
   a.tail_tiles_m = a.tail_group_m = a.tail_num = 0;
   cudaError_t e;
-  const bool split = !pair && ws.tslot != nullptr && a.tri == 0 &&
+  const bool split = !pair && a.tri == 0 &&
                      (force_split || (!force && (tiles <= 8 || (2 * tiles < sms && k >= 2048))));
   if (split) {
     int groups = (int)((sms + tiles - 1) / tiles);  // the kernel keeps at most nmod of them
     if (groups > kMaxModuli) groups = kMaxModuli;
     a.groups = groups;
-    a.tslot = ws.tslot;
-    a.tile_done = ws.tile_done;
     a.group_m = 1;
     const int64_t units = tiles * groups;
     const int grid = (int)(units < sms ? units : sms);
-    if ((e = cudaMemsetAsync(ws.tile_done, 0, sizeof(unsigned int) * (size_t)tiles, stream)) != cudaSuccess)
-      return cuda_fail(e, "modular gemm: clearing the tile counters");
     e = cudaFuncSetAttribute(k_mod_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm split)");
     k_mod_gemm<true><<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
@@ -1254,17 +1253,17 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   ModWorkspace ws;
   mod_layout(m, n, k, nmod_ws, workspace, &ws);
   const bool timing = info && info->record_phases;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   struct EventGuard {
     cudaEvent_t* e;
     ~EventGuard() {
-      for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 4; ++i)
         if (e[i]) cudaEventDestroy(e[i]);
     }
   } guard{ev};
   cudaError_t e;
   if (timing) {
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 4; ++i)
       if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventCreate");
     if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
   }
@@ -1339,28 +1338,47 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   k_mod_colscale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.sigB, ws.badB, n, alpha, ws.plan, ws.cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "column scale launch");
 
-  // products modulo each modulus and the reconstruction; the constants of every n ride along
+  // products modulo each modulus, parked; then the reconstruction of C
   ModArgs a;
-  mod_constants(a, prods);
+  mod_constants(a);
   a.tri = tri;
-  a.m = m; a.n = n; a.ldc = ldc;
+  a.m = m;
+  a.n = n;
   a.plan = ws.plan;
-  a.beta = beta;
-  a.C = C;
-  a.sigA = ws.sigA; a.badA = ws.badA;
-  a.cs = ws.cs;
-  a.scr = ws.scr;
+  a.park = ws.park;
+  a.park_mods = ws.park_mods;
+  a.nbn = ws.nbn;
   a.err = device_error_word();
   if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
   if ((rc = launch_mod_gemm(m, n, k, nmod_ws, a, ws, sms, s))) return rc;
+  if (timing && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
+  CrtJob job;
+  memset(&job, 0, sizeof(job));
+  job.park = ws.park;
+  job.plan = ws.plan;
+  job.C = C;
+  job.sigA = ws.sigA;
+  job.badA = ws.badA;
+  job.cs = ws.cs;
+  job.m = m;
+  job.n = n;
+  job.ldc = ldc;
+  job.beta = beta;
+  job.park_mods = ws.park_mods;
+  job.nbm = ws.nbm;
+  job.nbn = ws.nbn;
+  job.tri = tri;
+  if ((rc = launch_mod_crt(job, nullptr, 0, (int64_t)ws.nbm * ws.nbn, sms, s))) return rc;
   if (timing) {
-    float t0 = 0.f, t1 = 0.f;
-    if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[2])) != cudaSuccess ||
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    if ((e = cudaEventRecord(ev[3], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[3])) != cudaSuccess ||
         (e = cudaEventElapsedTime(&t0, ev[0], ev[1])) != cudaSuccess ||
-        (e = cudaEventElapsedTime(&t1, ev[1], ev[2])) != cudaSuccess)
+        (e = cudaEventElapsedTime(&t1, ev[1], ev[2])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t2, ev[2], ev[3])) != cudaSuccess)
       return cuda_fail(e, "dgemm_emu_mod: phase timing");
     info->prep_ms = t0;
     info->gemm_ms = t1;
+    info->recon_ms = t2;
   }
   if (info) {
     if (bits > 0) {
@@ -1385,7 +1403,6 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
 
 // ---- grouped modular problems ----
 namespace {
-constexpr int kGroupedModCtas = 160;  // park slots of the grouped product launch (one CTA per SM)
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
@@ -1393,19 +1410,13 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   *rc = GBD_OK;
   char* b = static_cast<char*>(base);
   size_t off = 0;
-  int64_t tiles = 0;
-  for (int q = 0; q < count; ++q) {
-    const gbd_problem& p = probs[which[q]];
-    tiles += ((p.m + kBM - 1) / kBM) * ((p.n + kBN - 1) / kBN);
-  }
-  const int ctas = (int)(tiles < kGroupedModCtas ? (tiles > 0 ? tiles : 1) : kGroupedModCtas);
   const size_t o_jobs = off; off = up256(off + sizeof(PrepJob) * 2 * (size_t)count);
   const size_t o_cert = off; off = up256(off + sizeof(CertTableEntry) * 2 * (size_t)count);  // FP8, BF16 retry
   const size_t o_plj = off; off = up256(off + sizeof(ModPlanJob) * (size_t)count);
   const size_t o_col = off; off = up256(off + sizeof(ColJob) * (size_t)count);
   const size_t o_tab = off; off = up256(off + sizeof(ModTableEntry) * (size_t)count);
+  const size_t o_crt = off; off = up256(off + sizeof(CrtJob) * (size_t)count);
   const size_t o_words = off; off = up256(off + sizeof(unsigned int) * kCertWords * (size_t)(count + 1));
-  const size_t o_scr = off; off = up256(off + 2 * (size_t)kSlotBytes * (size_t)ctas);
   std::vector<size_t> o_ws(count);
   std::vector<int> nmod_ws(count);
   for (int q = 0; q < count; ++q) {
@@ -1421,7 +1432,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     }
     nmod_ws[q] = nm;
     o_ws[q] = off;
-    off = up256(off + mod_layout(p.m, p.n, p.k, nm, nullptr, nullptr, false));
+    off = up256(off + mod_layout(p.m, p.n, p.k, nm, nullptr, nullptr));
   }
   if (!base || !g || *rc) return off;
 
@@ -1434,8 +1445,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   g->table_dev = reinterpret_cast<ModTableEntry*>(b + o_tab);
   g->words_dev = reinterpret_cast<unsigned int*>(b + o_words);
   g->flags_dev = g->words_dev + (size_t)kCertWords * count;
-  g->scr = reinterpret_cast<uint8_t*>(b + o_scr);
-  g->scr_ctas = ctas;
+  g->crt_dev = reinterpret_cast<CrtJob*>(b + o_crt);
   g->jobs.assign(2 * (size_t)count, PrepJob{});
   g->cert.assign(2 * (size_t)count, CertTableEntry{});
   g->planjobs.assign(count, ModPlanJob{});
@@ -1447,7 +1457,7 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   int64_t cert_tiles = 0;
   for (int q = 0; q < count; ++q) {
     const gbd_problem& p = probs[which[q]];
-    mod_layout(p.m, p.n, p.k, nmod_ws[q], b + o_ws[q], &ws[q], false);
+    mod_layout(p.m, p.n, p.k, nmod_ws[q], b + o_ws[q], &ws[q]);
     const ModWorkspace& w = ws[q];
     unsigned int* words = g->words_dev + (size_t)kCertWords * q;
     PrepJob& ja = g->jobs[2 * q];
@@ -1493,7 +1503,8 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return probs[which[x]].k > probs[which[y]].k; });
   g->table.assign(count, ModTableEntry{});
-  int64_t mt = 0;
+  g->crt.assign(count, CrtJob{});
+  int64_t mt = 0, blocks = 0;
   for (int r = 0; r < count; ++r) {
     const int q = order[r];
     const gbd_problem& p = probs[which[q]];
@@ -1509,39 +1520,41 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     const uint32_t bB[3] = {(uint32_t)kBK, (uint32_t)kBN, 1u};
     if ((*rc = encode_tmap(&e.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.DB, dB, pB, bB, CU_TENSOR_MAP_SWIZZLE_128B)))
       return off;
-    e.m = p.m; e.n = p.n; e.ldc = p.ldc;
-    e.beta = p.beta;
-    e.C = p.C;
-    e.sigA = w.sigA; e.badA = w.badA;
-    e.cs = w.cs;
+    e.m = p.m;
+    e.n = p.n;
     e.plan = w.plan;
+    e.park = w.park;
+    e.park_mods = w.park_mods;
+    e.nbn = w.nbn;
     e.nkb = (int)((p.k + kBK - 1) / kBK);
     e.tiles_m = (int)((p.m + kBM - 1) / kBM);
     e.num_tiles = e.tiles_m * (int)((p.n + kBN - 1) / kBN);
     e.group_m = e.tiles_m;  // within one problem the tiles walk down the rows
     e.tile_begin = mt;
     mt += e.num_tiles;
+    CrtJob& cj = g->crt[r];
+    cj.park = w.park;
+    cj.plan = w.plan;
+    cj.C = p.C;
+    cj.sigA = w.sigA;
+    cj.badA = w.badA;
+    cj.cs = w.cs;
+    cj.m = p.m;
+    cj.n = p.n;
+    cj.ldc = p.ldc;
+    cj.beta = p.beta;
+    cj.blk_begin = blocks;
+    cj.park_mods = w.park_mods;
+    cj.nbm = w.nbm;
+    cj.nbn = w.nbn;
+    cj.tri = 0;
+    cj.skip_infeasible = 1;
+    blocks += (int64_t)w.nbm * w.nbn;
   }
   g->mod_tiles = (int)mt;
+  g->crt_blocks = blocks;
   if (mt > ((int64_t)1 << 30) || cert_tiles > ((int64_t)1 << 30)) *rc = set_error(GBD_ERR_LIMIT, "grouped: too many tiles");
   return off;
-}
-
-int mod_grouped_upload(const ModGrouped& g, cudaStream_t s) {
-  if (g.count == 0) return GBD_OK;
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(g.jobs_dev, g.jobs.data(), sizeof(PrepJob) * g.jobs.size(), cudaMemcpyHostToDevice, s)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(g.cert_dev, g.cert.data(), sizeof(CertTableEntry) * g.cert.size(), cudaMemcpyHostToDevice,
-                           s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(g.planjobs_dev, g.planjobs.data(), sizeof(ModPlanJob) * g.planjobs.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(g.coljobs_dev, g.coljobs.data(), sizeof(ColJob) * g.coljobs.size(), cudaMemcpyHostToDevice,
-                           s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(g.table_dev, g.table.data(), sizeof(ModTableEntry) * g.table.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(e, "grouped modular: table copies");
-  return GBD_OK;
 }
 
 int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
@@ -1584,9 +1597,8 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   // the products of every feasible problem in one persistent launch
   if (g.mod_tiles <= 0) return GBD_OK;
   ModArgs a;
-  mod_constants(a, moduli_products());
+  mod_constants(a);
   a.plan = g.plans[0];  // read at kernel start; the tiles use their own problems' plans
-  a.scr = g.scr;
   a.err = device_error_word();
   a.num_tiles = g.mod_tiles;
   a.tile_end = g.mod_tiles;
@@ -1597,13 +1609,15 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   a.groups = 1;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
-  int grid = g.mod_tiles < sms ? g.mod_tiles : sms;
-  if (grid > g.scr_ctas) grid = g.scr_ctas;
+  const int grid = g.mod_tiles < sms ? g.mod_tiles : sms;
   e = cudaFuncSetAttribute(k_mod_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped modular gemm)");
   k_mod_gemm<false, true><<<grid, kThreads, Smem::kAlloc, s>>>(a, dummy, dummy, g.table_dev, g.count);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? GBD_OK : cuda_fail(e, "grouped modular gemm launch");
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped modular gemm launch");
+  // the reconstruction of every feasible problem
+  CrtJob none;
+  memset(&none, 0, sizeof(none));
+  return launch_mod_crt(none, g.crt_dev, g.count, g.crt_blocks, sms, s);
 }
 
 }  // namespace emu

@@ -597,6 +597,7 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
       {plan->mod.planjobs_dev, plan->mod.planjobs.data(), sizeof(emu::ModPlanJob) * plan->mod.planjobs.size()},
       {plan->mod.coljobs_dev, plan->mod.coljobs.data(), sizeof(emu::ColJob) * plan->mod.coljobs.size()},
       {plan->mod.table_dev, plan->mod.table.data(), sizeof(emu::ModTableEntry) * plan->mod.table.size()},
+      {plan->mod.crt_dev, plan->mod.crt.data(), sizeof(emu::CrtJob) * plan->mod.crt.size()},
   };
   size_t staged = 0;
   for (const Part& q : parts) staged += up256(q.bytes);

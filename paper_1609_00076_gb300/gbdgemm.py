@@ -78,7 +78,8 @@ class GbdEmuInfo(ctypes.Structure):
     _fields_ = [("record_phases", ctypes.c_int), ("slices", ctypes.c_int), ("digit_bits", ctypes.c_int),
                 ("products", ctypes.c_int), ("path", ctypes.c_int), ("exact", ctypes.c_int),
                 ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("bound", ctypes.c_double),
-                ("prep_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double)]
+                ("prep_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double),
+                ("recon_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -203,8 +203,8 @@ def test_deterministic():
 @pytest.mark.parametrize("m,n,k", [(2048, 2048, 256), (4096, 4096, 256)])
 def test_kernel_launches_per_call(m, n, k):
     # one call with the bits chosen on the device launches the kernels that the benchmark's
-    # launch count claims: eight (preparation, certification, plan, residues, column scales,
-    # products), plus one when the last two-SM wave runs on one-SM CTAs
+    # launch count claims (preparation, certification, plans, residues, column scales, products,
+    # reconstruction), plus one when the last two-SM wave runs on one-SM CTAs
     import torch
     from torch.profiler import ProfilerActivity, profile
 

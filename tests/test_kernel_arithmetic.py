@@ -7,7 +7,13 @@
    r = x - p q.  The BF16 operand is exact only if |r| <= 256 and the product bound of
    the chunked FP32 sums needs |r| <= 128: checked here for every byte sum the kernel can
    form, with fl(1/p) the FP32 reciprocal and the rounding done in exact integers.
-2. Triangle tiles (DSYRK's triangular product).  Tile t of a triangle of T x T tiles is
+2. The reconstruction (k_mod_crt).  With W_l = M/p_l, c_l = W_l^-1 mod p_l and the parked
+   residues r_l = C' mod p_l in [0, p_l): X = sum_l r_l (c_l W_l) is congruent to C' modulo M,
+   the quotient estimate Qe = floor(sum_l r_l ceil(c_l 2^16/p_l) / 2^16 + 1/2) is the quotient of
+   the symmetric representative or one more (and then X - Qe M <= -M/2), and X - Qe M is formed
+   modulo 2^96 (at most 12 moduli, M < 2^95) or 2^128 from 64-bit limb sums; the representative
+   of (-M/2, M/2] must come out for every C'.
+3. Triangle tiles (DSYRK's triangular product).  Tile t of a triangle of T x T tiles is
    (r, c) with t = r (r + 1) / 2 + c, found from an FP32 square-root estimate corrected by
    integer steps; every tile that meets the triangle comes out exactly once.
 """
@@ -47,6 +53,70 @@ def test_residue_in_range_for_every_byte_sum(p):
     r = x - p * q
     assert np.all((r - s) % p == 0)  # the residue class of s
     assert int(np.abs(r).max()) <= 128
+
+
+def _crt_constants(n: int):
+    M = 1
+    for p in MODULI[:n]:
+        M *= p
+    V, e = [], []
+    for p in MODULI[:n]:
+        W = M // p
+        c = pow(W % p, -1, p)
+        assert c * W < M
+        V.append(c * W)
+        e.append((c * 2 ** 16 + p - 1) // p)
+    return M, V, e
+
+
+def _crt_kernel(r, n, M, V, e):
+    """The kernel's reconstruction, step by step in exact integers; returns C' modulo 2^(32 L)."""
+    L = 3 if n <= 12 else 4
+    mod = 2 ** (32 * L)
+    limbs = [0] * L
+    qe = 2 ** 15
+    for rl, Vl, el in zip(r, V, e):
+        for j in range(L):
+            limbs[j] += rl * ((Vl >> (32 * j)) & 0xFFFFFFFF)
+        qe += rl * el
+    assert max(limbs) < 2 ** 44 and qe < 2 ** 32  # the 64-bit limb sums and the 32-bit estimate
+    x = sum(a << (32 * j) for j, a in enumerate(limbs)) % mod
+    x = (x - (qe >> 16) * M) % mod
+    if ((x + M // 2 - 1) % mod) >> (32 * L - 1):  # X - Qe M <= -M/2: one too many
+        x = (x + M) % mod
+    return x, mod
+
+
+@pytest.mark.parametrize("n", range(1, 17))
+def test_reconstruction_gives_the_symmetric_representative(n):
+    M, V, e = _crt_constants(n)
+    assert M < (2 ** 95 if n <= 12 else 2 ** 127)
+    rng = np.random.default_rng(n)
+    half = M // 2
+    values = [0, 1, -1, half, -half + 1, half - 1, -half + 2]
+    values += [int(x) for x in rng.integers(0, 2 ** 62, 200)]
+    values += [int(rng.integers(0, 2 ** 62)) * 2 ** 64 % M - half for _ in range(200)]
+    for cp in values:
+        cp = (cp + half - 1) % M - half + 1  # the representative of (-M/2, M/2]
+        r = [cp % p for p in MODULI[:n]]
+        X = sum(rl * Vl for rl, Vl in zip(r, V))
+        Qn = (X - cp) // M
+        Qe = (sum(rl * el for rl, el in zip(r, e)) + 2 ** 15) >> 16
+        assert Qe == Qn or (Qe == Qn + 1 and X - Qe * M <= -half)
+        got, mod = _crt_kernel(r, n, M, V, e)
+        assert got == cp % mod
+
+
+@pytest.mark.parametrize("n", [1, 12, 13, 16])
+def test_reconstruction_at_the_largest_residues(n):
+    # every residue p_l - 1: the largest limb sums and quotient estimate
+    M, V, e = _crt_constants(n)
+    r = [p - 1 for p in MODULI[:n]]
+    X = sum(rl * Vl for rl, Vl in zip(r, V))
+    cp = X % M
+    cp = cp - M if cp > M // 2 else cp
+    got, mod = _crt_kernel(r, n, M, V, e)
+    assert got == cp % mod
 
 
 def _tri_tile(t: int) -> tuple[int, int]:
