@@ -38,15 +38,86 @@ constexpr int64_t kParkBlock = 128 * 128;
 // the reconstruction constants of the first n moduli (M = p_0 ... p_(n-1), W_l = M / p_l,
 // c_l = W_l^-1 mod p_l): with r_l = C' mod p_l in [0, p_l), X = sum_l r_l V_l, V_l = c_l W_l < M,
 // is congruent to C' modulo M, and X / M = sum_l r_l c_l / p_l
+// V_l and e_l = ceil(c_l 2^16 / p_l) enter as bytes, four moduli per word, for the byte dot
+// products of dp4a: wp[G][d] holds byte d of V_4G .. V_4G+3, ep[G][d] byte d of e_4G .. e_4G+3;
+// sum_l r_l e_l / 2^16 exceeds X / M by less than 1/16
 struct CrtSet {
-  uint32_t v[kMaxModuli][4];  // V_l in 32-bit limbs, least significant first
-  uint32_t e[kMaxModuli];     // ceil(c_l 2^16 / p_l): sum_l r_l e_l / 2^16 exceeds X / M by less than 1/16
-  uint32_t M[4];              // M
-  uint32_t H[4];              // M / 2 - 1 (M is even: p_0 = 256)
+  uint32_t wp[kMaxModuli / 4][16];
+  uint32_t ep[kMaxModuli / 4][2];
+  uint32_t M[4];  // M in 32-bit limbs, least significant first
+  uint32_t H[4];  // M / 2 - 1 (M is even: p_0 = 256)
 };
 struct CrtConsts {
   CrtSet set[kMaxModuli];  // set[n - 1]: the constants for the first n moduli
 };
+
+// multi-word arithmetic on 32-bit limbs (least significant first) for the constants, at compile time
+constexpr void limbs_mul_small(uint32_t (&x)[5], uint32_t f) {
+  uint64_t carry = 0;
+  for (int j = 0; j < 5; ++j) {
+    const uint64_t t = (uint64_t)x[j] * f + carry;
+    x[j] = (uint32_t)t;
+    carry = t >> 32;
+  }
+}
+constexpr uint32_t limbs_div_small(uint32_t (&x)[5], uint32_t d) {  // x := x / d, returns x mod d
+  uint64_t rem = 0;
+  for (int j = 4; j >= 0; --j) {
+    const uint64_t t = (rem << 32) | x[j];
+    x[j] = (uint32_t)(t / d);
+    rem = t % d;
+  }
+  return (uint32_t)rem;
+}
+constexpr uint32_t inverse_small(uint32_t a, uint32_t p) {  // a^-1 mod p, gcd(a, p) = 1
+  int64_t t = 0, nt = 1, r = p, nr = a % p;
+  while (nr != 0) {
+    const int64_t q = r / nr;
+    const int64_t x = t - q * nt;
+    t = nt;
+    nt = x;
+    const int64_t y = r - q * nr;
+    r = nr;
+    nr = y;
+  }
+  return (uint32_t)(t < 0 ? t + p : t);
+}
+constexpr CrtConsts make_crt_consts() {
+  CrtConsts k{};
+  for (int nn = 1; nn <= kMaxModuli; ++nn) {
+    CrtSet& cs = k.set[nn - 1];
+    uint32_t M[5] = {1u, 0u, 0u, 0u, 0u};
+    for (int l = 0; l < nn; ++l) limbs_mul_small(M, (uint32_t)kModuli[l]);
+    for (int l = 0; l < nn; ++l) {
+      const uint32_t p = (uint32_t)kModuli[l];
+      uint32_t W[5] = {M[0], M[1], M[2], M[3], M[4]};
+      limbs_div_small(W, p);  // exact: p divides M
+      uint32_t Wr[5] = {W[0], W[1], W[2], W[3], W[4]};
+      const uint32_t c = inverse_small(limbs_div_small(Wr, p), p);
+      limbs_mul_small(W, c);  // V_l = c_l W_l < M
+      const uint32_t e = (uint32_t)((((uint64_t)c << 16) + p - 1) / p);  // below 2^16
+      const int G = l / 4, b = 8 * (l % 4);
+      for (int d = 0; d < 16; ++d) cs.wp[G][d] |= ((W[d / 4] >> (8 * (d % 4))) & 0xFFu) << b;
+      for (int d = 0; d < 2; ++d) cs.ep[G][d] |= ((e >> (8 * d)) & 0xFFu) << b;
+    }
+    uint32_t H[5] = {M[0], M[1], M[2], M[3], M[4]};
+    limbs_div_small(H, 2u);
+    for (int j = 0; j < 5; ++j) {  // H := M / 2 - 1
+      if (H[j] != 0u) {
+        --H[j];
+        break;
+      }
+      H[j] = 0xFFFFFFFFu;
+    }
+    for (int j = 0; j < 4; ++j) {
+      cs.M[j] = M[j];
+      cs.H[j] = H[j];
+    }
+  }
+  return k;
+}
+// in constant memory: the specialisations address them as immediate operands
+__constant__ CrtConsts kCrt = make_crt_consts();
 
 struct ModArgs {
   int64_t m, n;
@@ -572,33 +643,48 @@ __device__ __forceinline__ void limbs_sub(uint32_t (&x)[L], const uint32_t (&y)[
 
 // fl(C') for the residues r_l = byte q of w[l]: the sign, the unbiased exponent E of the rounded
 // value and its 53-bit significand with the implicit bit (mant in [2^52, 2^53], 2^53 when the
-// rounding carried), or zero.  X = sum_l r_l V_l modulo 2^(32 L); Qe = floor(sum_l r_l e_l / 2^16
-// + 1/2) is round(X / M) or one more, and one more only when X - Qe M <= -M/2: then M is added
-// back.  The result lies in (-M/2, M/2].
+// rounding carried), or zero.  X = sum_l r_l V_l modulo 2^(32 L) from the byte sums
+// S_d = sum_l r_l (byte d of V_l) < 2^20 (four moduli per dp4a), as
+// X = sum_k 2^(32 k) (A_k + 2^16 B_k), A_k = S_4k + 2^8 S_4k+1, B_k = S_4k+2 + 2^8 S_4k+3 (each
+// below 2^29).  Qe = floor(sum_l r_l e_l / 2^16 + 1/2) is round(X / M) or one more, and one more
+// only when X - Qe M <= -M/2: then M is added back.  The result lies in (-M/2, M/2].
 template <int N>
 __device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[kMaxModuli], int q, uint32_t& sign,
                                           int& E, uint64_t& mant) {
   constexpr int L = N <= 12 ? 3 : 4;
-  uint64_t a[L];
+  constexpr int NG = (N + 3) / 4;
+  // this column's residues, four moduli per word
+  uint32_t T[NG];
+  const uint32_t sel = 0x4400u | ((4u + (uint32_t)q) << 4) | (uint32_t)q;  // bytes q of x and of y
 #pragma unroll
-  for (int j = 0; j < L; ++j) a[j] = 0;
-  uint32_t qe = 1u << 15;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const uint32_t r = __byte_perm(w[l], 0u, 0x4440u + (uint32_t)q);
-#pragma unroll
-    for (int j = 0; j < L; ++j) a[j] += (uint64_t)r * S.v[l][j];
-    qe += r * S.e[l];
-  }
-  // X modulo 2^(32 L) from the limb sums (each below 2^44)
+  for (int G = 0; G < NG; ++G)
+    T[G] = __byte_perm(__byte_perm(w[4 * G], w[4 * G + 1], sel), __byte_perm(w[4 * G + 2], w[4 * G + 3], sel),
+                       0x5410u);
   uint32_t x[L];
-  uint64_t t = a[0];
-  x[0] = (uint32_t)t;
+  uint64_t t = 0;
 #pragma unroll
-  for (int j = 1; j < L; ++j) {
-    t = (t >> 32) + a[j];
-    x[j] = (uint32_t)t;
+  for (int k = 0; k < L; ++k) {
+    uint32_t s1 = 0u, s3 = 0u;
+#pragma unroll
+    for (int G = 0; G < NG; ++G) {
+      s1 = __dp4a(T[G], S.wp[G][4 * k + 1], s1);
+      s3 = __dp4a(T[G], S.wp[G][4 * k + 3], s3);
+    }
+    uint32_t A = s1 << 8, B = s3 << 8;
+#pragma unroll
+    for (int G = 0; G < NG; ++G) {
+      A = __dp4a(T[G], S.wp[G][4 * k], A);
+      B = __dp4a(T[G], S.wp[G][4 * k + 2], B);
+    }
+    t = (t >> 32) + A + ((uint64_t)B << 16);  // below 2^46
+    x[k] = (uint32_t)t;
   }
+  uint32_t qh = 0u;
+#pragma unroll
+  for (int G = 0; G < NG; ++G) qh = __dp4a(T[G], S.ep[G][1], qh);
+  uint32_t qe = (qh << 8) + (1u << 15);
+#pragma unroll
+  for (int G = 0; G < NG; ++G) qe = __dp4a(T[G], S.ep[G][0], qe);
   // X - Qe M
   const uint32_t Q = qe >> 16;
   uint32_t qm[L];
@@ -662,7 +748,8 @@ __device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[k
 }
 
 template <int N>
-__device__ __forceinline__ void crt_rows(const CrtSet& S, const CrtJob& job, bool nan_out, int rb, int cb) {
+__device__ __forceinline__ void crt_rows(const CrtJob& job, bool nan_out, int rb, int cb) {
+  const CrtSet& S = kCrt.set[N - 1];
   // the job's fields in registers (the stores to C cannot alias them then)
   const int64_t m = job.m, n = job.n, ldc = job.ldc;
   const double beta = job.beta;
@@ -736,11 +823,11 @@ __device__ __forceinline__ void crt_rows(const CrtSet& S, const CrtJob& job, boo
 
 // each count of moduli its own function (register allocation of one specialisation at a time)
 template <int N>
-__device__ __noinline__ void crt_block_n(const CrtConsts& K, const CrtJob& j, bool nan_out, int rb, int cb) {
-  crt_rows<N>(K.set[N - 1], j, nan_out, rb, cb);
+__device__ __noinline__ void crt_block_n(const CrtJob& j, bool nan_out, int rb, int cb) {
+  crt_rows<N>(j, nan_out, rb, cb);
 }
 
-__device__ __forceinline__ void crt_block(const CrtConsts& K, const CrtJob& j, int64_t blk) {
+__device__ __forceinline__ void crt_block(const CrtJob& j, int64_t blk) {
   const ModPlan pl = *j.plan;
   if (!pl.feasible && j.skip_infeasible) return;
   const int rb = (int)(blk / j.nbn), cb = (int)(blk % j.nbn);
@@ -748,32 +835,31 @@ __device__ __forceinline__ void crt_block(const CrtConsts& K, const CrtJob& j, i
   if ((j.tri == 1 && cb > rb) || (j.tri == 2 && cb < rb)) return;
   const bool nan_out = !pl.feasible;
   switch (pl.n) {
-    case 1: crt_block_n<1>(K, j, nan_out, rb, cb); break;
-    case 2: crt_block_n<2>(K, j, nan_out, rb, cb); break;
-    case 3: crt_block_n<3>(K, j, nan_out, rb, cb); break;
-    case 4: crt_block_n<4>(K, j, nan_out, rb, cb); break;
-    case 5: crt_block_n<5>(K, j, nan_out, rb, cb); break;
-    case 6: crt_block_n<6>(K, j, nan_out, rb, cb); break;
-    case 7: crt_block_n<7>(K, j, nan_out, rb, cb); break;
-    case 8: crt_block_n<8>(K, j, nan_out, rb, cb); break;
-    case 9: crt_block_n<9>(K, j, nan_out, rb, cb); break;
-    case 10: crt_block_n<10>(K, j, nan_out, rb, cb); break;
-    case 11: crt_block_n<11>(K, j, nan_out, rb, cb); break;
-    case 12: crt_block_n<12>(K, j, nan_out, rb, cb); break;
-    case 13: crt_block_n<13>(K, j, nan_out, rb, cb); break;
-    case 14: crt_block_n<14>(K, j, nan_out, rb, cb); break;
-    case 15: crt_block_n<15>(K, j, nan_out, rb, cb); break;
-    default: crt_block_n<16>(K, j, nan_out, rb, cb); break;
+    case 1: crt_block_n<1>(j, nan_out, rb, cb); break;
+    case 2: crt_block_n<2>(j, nan_out, rb, cb); break;
+    case 3: crt_block_n<3>(j, nan_out, rb, cb); break;
+    case 4: crt_block_n<4>(j, nan_out, rb, cb); break;
+    case 5: crt_block_n<5>(j, nan_out, rb, cb); break;
+    case 6: crt_block_n<6>(j, nan_out, rb, cb); break;
+    case 7: crt_block_n<7>(j, nan_out, rb, cb); break;
+    case 8: crt_block_n<8>(j, nan_out, rb, cb); break;
+    case 9: crt_block_n<9>(j, nan_out, rb, cb); break;
+    case 10: crt_block_n<10>(j, nan_out, rb, cb); break;
+    case 11: crt_block_n<11>(j, nan_out, rb, cb); break;
+    case 12: crt_block_n<12>(j, nan_out, rb, cb); break;
+    case 13: crt_block_n<13>(j, nan_out, rb, cb); break;
+    case 14: crt_block_n<14>(j, nan_out, rb, cb); break;
+    case 15: crt_block_n<15>(j, nan_out, rb, cb); break;
+    default: crt_block_n<16>(j, nan_out, rb, cb); break;
   }
 }
 
 // one product (jobs == nullptr: `one`), or the jobs of a grouped launch (blocks in job order)
-__global__ void __launch_bounds__(kCrtThreads, 3) k_mod_crt(const __grid_constant__ CrtConsts K,
-                                                            const __grid_constant__ CrtJob one,
+__global__ void __launch_bounds__(kCrtThreads, 3) k_mod_crt(const __grid_constant__ CrtJob one,
                                                             const CrtJob* __restrict__ jobs, int count, int64_t total) {
   for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
     if (!jobs) {
-      crt_block(K, one, b);
+      crt_block(one, b);
       continue;
     }
     int lo = 0, hi = count - 1;  // the last job whose blocks begin at or before b
@@ -783,7 +869,7 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_mod_crt(const __grid_constan
       else hi = mid - 1;
     }
     const CrtJob jb = jobs[lo];
-    crt_block(K, jb, b - jb.blk_begin);
+    crt_block(jb, b - jb.blk_begin);
   }
 }
 
@@ -1026,16 +1112,6 @@ ModProducts moduli_products() {
 
 int moduli_for(int t, int64_t k) { return moduli_for_products(t, k, moduli_products()); }
 
-int64_t inverse_mod(int64_t a, int64_t p) {  // a^-1 mod p, gcd(a, p) = 1
-  int64_t t = 0, nt = 1, r = p, nr = ((a % p) + p) % p;
-  while (nr) {
-    const int64_t q = r / nr;
-    int64_t x = t - q * nt; t = nt; nt = x;
-    x = r - q * nr; r = nr; nr = x;
-  }
-  return t < 0 ? t + p : t;
-}
-
 // the moduli and their Barrett constants; the rest of `a` zeroed
 void mod_constants(ModArgs& a) {
   memset(&a, 0, sizeof(a));
@@ -1045,39 +1121,12 @@ void mod_constants(ModArgs& a) {
   }
 }
 
-// the reconstruction constants of every n = 1..kMaxModuli (computed once)
-const CrtConsts& crt_constants() {
-  static const CrtConsts K = [] {
-    CrtConsts k;
-    memset(&k, 0, sizeof(k));
-    const ModProducts prods = moduli_products();
-    for (int nn = 1; nn <= kMaxModuli; ++nn) {
-      CrtSet& cs = k.set[nn - 1];
-      const hu128 M = ((hu128)prods.hi[nn - 1] << 64) | prods.lo[nn - 1];
-      for (int l = 0; l < nn; ++l) {
-        const hu128 W = M / (hu128)kModuli[l];
-        const int64_t c = inverse_mod((int64_t)(W % (hu128)kModuli[l]), kModuli[l]);
-        const hu128 V = (hu128)c * W;  // below M
-        for (int w = 0; w < 4; ++w) cs.v[l][w] = (uint32_t)(V >> (32 * w));
-        cs.e[l] = (uint32_t)((((uint64_t)c << 16) + (uint64_t)kModuli[l] - 1) / (uint64_t)kModuli[l]);
-      }
-      const hu128 H = M / 2 - 1;
-      for (int w = 0; w < 4; ++w) {
-        cs.M[w] = (uint32_t)(M >> (32 * w));
-        cs.H[w] = (uint32_t)(H >> (32 * w));
-      }
-    }
-    return k;
-  }();
-  return K;
-}
-
 // the reconstruction of one product (jobs == nullptr: `one`) or of a grouped launch's jobs
 int launch_mod_crt(const CrtJob& one, const CrtJob* jobs, int count, int64_t total, int sms, cudaStream_t s) {
   if (total <= 0) return GBD_OK;
   const int64_t cap = (int64_t)sms * 8;
   const int grid = (int)(total < cap ? total : cap);
-  k_mod_crt<<<grid, kCrtThreads, 0, s>>>(crt_constants(), one, jobs, count, total);
+  k_mod_crt<<<grid, kCrtThreads, 0, s>>>(one, jobs, count, total);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "modular reconstruction launch");
 }
