@@ -119,6 +119,19 @@ struct PrepJob {
 constexpr int kEminNone = 0x7F7F7F7F;  // a row without a non-zero finite entry (memset byte 0x7F)
 // fills j's block ranges, advancing the running block counts of both launches
 void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks);
+// The first block of every job of a batched launch (exponent blocks, 64 x 64 split tiles or rows),
+// passed by value in the kernel parameters when there are at most kBeginCache jobs: a
+// block then finds its job by a binary search in constant memory instead of one through the job
+// table in device memory (a chain of dependent loads per block)
+constexpr int kBeginCache = 1900;
+struct JobBegins {
+  int n;  // jobs whose begins are here (0: search the table)
+  int pad;
+  int64_t b[kBeginCache];
+};
+enum JobNumbering { kByExponentBlock = 0, kBySplitTile = 1, kByRow = 2 };
+// fills `out` from the host copy of the job table; returns the launch's block count
+int64_t job_begins(const PrepJob* jobs_host, int njobs, JobNumbering which, JobBegins& out);
 
 // Both operand sides of one problem (j[0] = op(A), j[1] = op(B)^T), passed to the kernels by
 // value: a single call prepares them with one launch per step.
@@ -221,24 +234,19 @@ int launch_residue_pair(const PrepPair& pp, const ModSplit& mp, int64_t split_bl
 // grouped modular problems: the magnitude planes (FP8 E5M2) of every job into its D, widths to
 // its tex; then, after the plans, the residues of every job with its problem's plan (nothing for
 // an infeasible plan)
-int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s,
-                            int prec = kCertFP8, const unsigned int* retry_if = nullptr);
-int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
-                           cudaStream_t s);
+// (jobs_host: the host copy of the device job table jobs_dev, for the block begins)
+int launch_magplane_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t split_blocks,
+                            cudaStream_t s, int prec = kCertFP8, const unsigned int* retry_if = nullptr);
+int launch_residue_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, const ModSplit& mp,
+                           int64_t split_blocks, cudaStream_t s);
 // exponents: initialise, then one launch for every job; split: one launch for every job
-int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
-                        bool exponents, bool split, cudaStream_t s);
-// magnitude sums of every job (after the batched exponents; the jobs' mu arrays zeroed by them)
-int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s);
+int launch_prep_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t exp_blocks,
+                        int64_t split_blocks, bool exponents, bool split, cudaStream_t s);
 // grouped modular problems: launch_statplane_pair's three steps over every job (each job's width
 // and norm words): the same arithmetic in the same order, so a problem gets the same statistics
 // and planes alone and in a batch
-int launch_statplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, int64_t max_rows,
-                             cudaStream_t s);
-// exponents and magnitude statistics of every problem (jobs 2q, 2q+1 = op(A), op(B)^T of
-// problem q) into stats_dev[4q .. 4q+3] = {min mu, min nu, bad row, bad column}
-int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
-                         cudaStream_t s);
+int launch_statplane_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t split_blocks,
+                             int64_t max_rows, cudaStream_t s);
 
 // ---- the certified precision choice (emu_cert.cu, emu_split.cu) ----
 // The choice certifies, for every element with a non-zero |A||B| term, that the a-priori

@@ -854,22 +854,24 @@ __device__ __forceinline__ void crt_block(const CrtJob& j, int64_t blk) {
   }
 }
 
-// one product (jobs == nullptr: `one`), or the jobs of a grouped launch (blocks in job order)
+// one product (jobs == nullptr: `one`), or the jobs of a grouped launch (blocks in job order; their
+// first blocks in `begins` when it holds every job, else read from the table)
 __global__ void __launch_bounds__(kCrtThreads, 3) k_mod_crt(const __grid_constant__ CrtJob one,
-                                                            const CrtJob* __restrict__ jobs, int count, int64_t total) {
+                                                            const CrtJob* __restrict__ jobs, int count, int64_t total,
+                                                            const __grid_constant__ JobBegins begins) {
   for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
     if (!jobs) {
       crt_block(one, b);
       continue;
     }
     int lo = 0, hi = count - 1;  // the last job whose blocks begin at or before b
+    const bool cached = begins.n == count;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].blk_begin <= b) lo = mid;
+      if ((cached ? begins.b[mid] : jobs[mid].blk_begin) <= b) lo = mid;
       else hi = mid - 1;
     }
-    const CrtJob jb = jobs[lo];
-    crt_block(jb, b - jb.blk_begin);
+    crt_block(jobs[lo], b - (cached ? begins.b[lo] : jobs[lo].blk_begin));
   }
 }
 
@@ -1122,11 +1124,15 @@ void mod_constants(ModArgs& a) {
 }
 
 // the reconstruction of one product (jobs == nullptr: `one`) or of a grouped launch's jobs
-int launch_mod_crt(const CrtJob& one, const CrtJob* jobs, int count, int64_t total, int sms, cudaStream_t s) {
+int launch_mod_crt(const CrtJob& one, const CrtJob* jobs, const CrtJob* jobs_host, int count, int64_t total, int sms,
+                   cudaStream_t s) {
   if (total <= 0) return GBD_OK;
   const int64_t cap = (int64_t)sms * 8;
   const int grid = (int)(total < cap ? total : cap);
-  k_mod_crt<<<grid, kCrtThreads, 0, s>>>(one, jobs, count, total);
+  static thread_local JobBegins begins;  // 15 KB: not on the stack
+  begins.n = (jobs && count <= kBeginCache) ? count : 0;
+  for (int q = 0; q < begins.n; ++q) begins.b[q] = jobs_host[q].blk_begin;
+  k_mod_crt<<<grid, kCrtThreads, 0, s>>>(one, jobs, count, total, begins);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBD_OK : cuda_fail(e, "modular reconstruction launch");
 }
@@ -1417,7 +1423,7 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   job.nbm = ws.nbm;
   job.nbn = ws.nbn;
   job.tri = tri;
-  if ((rc = launch_mod_crt(job, nullptr, 0, (int64_t)ws.nbm * ws.nbn, sms, s))) return rc;
+  if ((rc = launch_mod_crt(job, nullptr, nullptr, 0, (int64_t)ws.nbm * ws.nbn, sms, s))) return rc;
   if (timing) {
     float t0 = 0.f, t1 = 0.f, t2 = 0.f;
     if ((e = cudaEventRecord(ev[3], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[3])) != cudaSuccess ||
@@ -1617,12 +1623,12 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   // one pass over every side: statistics and FP8 magnitude planes (as the single call)
   int64_t max_rows = 0;
   for (const PrepJob& j : g.jobs) max_rows = j.R > max_rows ? j.R : max_rows;
-  if ((rc = launch_statplane_batched(g.jobs_dev, njobs, g.split_blocks, max_rows, s))) return rc;
+  if ((rc = launch_statplane_batched(g.jobs_dev, g.jobs.data(), njobs, g.split_blocks, max_rows, s))) return rc;
   // the certification: magnitude planes, their products, the plans (the same precision as the
   // single call's, so that a problem gets the same plan alone and in a batch)
   const int prec = cert_prec_default();
   const bool retry = prec == kCertFP8;
-  if (prec == kCertBF16 && (rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, prec))) return rc;
+  if (prec == kCertBF16 && (rc = launch_magplane_batched(g.jobs_dev, g.jobs.data(), njobs, g.split_blocks, s, prec))) return rc;
   if ((rc = launch_cert_grouped(g.cert_dev, g.count, g.cert_tiles, prec, sms, s))) return rc;
   const ModProducts prods = moduli_products();
   k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 0, g.flags_dev,
@@ -1631,7 +1637,7 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   if (retry) {
     // the BF16 retry of every problem whose plan found no feasible t; the launches return at once
     // when no problem needs it, and skip the problems whose plan is feasible
-    if ((rc = launch_magplane_batched(g.jobs_dev, njobs, g.split_blocks, s, kCertBF16, g.flags_dev))) return rc;
+    if ((rc = launch_magplane_batched(g.jobs_dev, g.jobs.data(), njobs, g.split_blocks, s, kCertBF16, g.flags_dev))) return rc;
     if ((rc = launch_cert_grouped(g.cert_dev + g.count, g.count, g.cert_tiles, kCertBF16, sms, s, g.flags_dev)))
       return rc;
     k_mod_plan_batched<<<(g.count + 127) / 128, 128, 0, s>>>(g.planjobs_dev, g.count, prods, 1, g.flags_dev, 1);
@@ -1640,7 +1646,7 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   // residues and column scales with each problem's plan
   ModSplit ms;
   mod_split_params(ms);
-  if ((rc = launch_residue_batched(g.jobs_dev, njobs, ms, g.split_blocks, s))) return rc;
+  if ((rc = launch_residue_batched(g.jobs_dev, g.jobs.data(), njobs, ms, g.split_blocks, s))) return rc;
   k_mod_colscale_batched<<<g.count, 256, 0, s>>>(g.coljobs_dev);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped column scale launch");
   // the products of every feasible problem in one persistent launch
@@ -1666,7 +1672,7 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   // the reconstruction of every feasible problem
   CrtJob none;
   memset(&none, 0, sizeof(none));
-  return launch_mod_crt(none, g.crt_dev, g.count, g.crt_blocks, sms, s);
+  return launch_mod_crt(none, g.crt_dev, g.crt.data(), g.count, g.crt_blocks, sms, s);
 }
 
 }  // namespace emu

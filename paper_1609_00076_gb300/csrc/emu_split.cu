@@ -519,8 +519,19 @@ __device__ __forceinline__ void split_body(const double* __restrict__ X, int64_t
 }
 
 // ---- batched forms over a job table (one operand side of one problem per job) ----
-__device__ __forceinline__ int find_job(const PrepJob* __restrict__ jobs, int njobs, int64_t b, bool split) {
+// the job of block b: the last whose first block is at most b (begins from the kernel parameters
+// when they hold every job, else from the table)
+__device__ __forceinline__ int find_job(const JobBegins& jb, const PrepJob* __restrict__ jobs, int njobs, int64_t b,
+                                        bool split) {
   int lo = 0, hi = njobs - 1;
+  if (jb.n == njobs) {
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jb.b[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if ((split ? jobs[mid].split_begin : jobs[mid].exp_begin) <= b) lo = mid;
@@ -539,31 +550,11 @@ __global__ void __launch_bounds__(256) k_prep_init_batched(const PrepJob* __rest
   }
 }
 
-__global__ void __launch_bounds__(256) k_magnitudes_batched(const PrepJob* __restrict__ jobs, int njobs) {
-  __shared__ float s_sum[8][33];
-  const int ji = find_job(jobs, njobs, blockIdx.x, false);
-  const PrepJob& j = jobs[ji];
-  const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
-  const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
-  if (j.rows_contig) magnitudes_body<true>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum);
-  else magnitudes_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.mu, bx, by, s_sum);
-}
-
-
-// block q: problem q, whose operand sides are jobs 2q (op(A)) and 2q+1 (op(B)^T)
-__global__ void __launch_bounds__(256) k_min_stats_batched(const PrepJob* __restrict__ jobs,
-                                                           float* __restrict__ stats) {
-  __shared__ float s_min[2][256];
-  __shared__ int s_bad[2][256];
-  const PrepJob& a = jobs[2 * blockIdx.x];
-  const PrepJob& b = jobs[2 * blockIdx.x + 1];
-  min_stats_body(a.mu, a.R, b.mu, b.R, a.bad, b.bad, stats + 4 * blockIdx.x, s_min, s_bad);
-}
-
-__global__ void __launch_bounds__(256) k_exponents_batched(const PrepJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256) k_exponents_batched(const PrepJob* __restrict__ jobs, int njobs,
+                                                           const __grid_constant__ JobBegins jb) {
   __shared__ int s_max[8][33];
   __shared__ int s_bad[8][33];
-  const int ji = find_job(jobs, njobs, blockIdx.x, false);
+  const int ji = find_job(jb, jobs, njobs, blockIdx.x, false);
   const PrepJob& j = jobs[ji];
   const int64_t local = (int64_t)blockIdx.x - j.exp_begin;
   const int64_t bx = local % j.exp_gx, by = local / j.exp_gx;
@@ -571,9 +562,10 @@ __global__ void __launch_bounds__(256) k_exponents_batched(const PrepJob* __rest
   else exponents_body<false>(j.X, j.ld, j.R, j.K, j.sig, j.bad, bx, by, s_max, s_bad);
 }
 
-__global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* __restrict__ jobs, int njobs,
+                                                                 const __grid_constant__ JobBegins jb) {
   __shared__ uint64_t tile[kTile][kTile + 1];
-  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const int ji = find_job(jb, jobs, njobs, blockIdx.x, true);
   const PrepJob& j = jobs[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
@@ -590,7 +582,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_batched(const PrepJob* 
 template <bool FP8, bool RETRY>
 __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const PrepJob* __restrict__ jobs, int njobs,
                                                                     int64_t nblocks,
-                                                                    const unsigned int* __restrict__ run_if) {
+                                                                    const unsigned int* __restrict__ run_if,
+                                                                    const __grid_constant__ JobBegins jb) {
   __shared__ uint64_t tile[kTile][kTile + 1];
   __shared__ unsigned int s_tex;
   __shared__ int s_emin[kTile];
@@ -598,7 +591,7 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const Pre
   mag_shared_init(&s_tex, s_emin);
   __syncthreads();
   for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int ji = find_job(jobs, njobs, b, true);
+    const int ji = find_job(jb, jobs, njobs, b, true);
     const PrepJob& j = jobs[ji];
     const bool live = !RETRY || !j.plan->feasible;  // uniform over the block
     const int64_t local = b - j.split_begin;
@@ -623,9 +616,10 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_magplane_batched(const Pre
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 3) k_residue_batched(const PrepJob* __restrict__ jobs, int njobs,
-                                                                   const __grid_constant__ ModSplit mp) {
+                                                                   const __grid_constant__ ModSplit mp,
+                                                                   const __grid_constant__ JobBegins jb) {
   __shared__ uint64_t tile[kTile][kTile + 1];
-  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const int ji = find_job(jb, jobs, njobs, blockIdx.x, true);
   const PrepJob& j = jobs[ji];
   const ModPlan pl = *j.plan;
   if (!pl.feasible) return;  // the problem is computed by the FP64 kernel
@@ -820,9 +814,10 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_statplane_pair(const __gri
   else statplane_tile<false>(j.X, j.ld, j.R, j.K, D, kp, j.st, bx, by, tile);
 }
 
-__global__ void __launch_bounds__(kSplitThreads, 3) k_statplane_batched(const PrepJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(kSplitThreads, 3) k_statplane_batched(const PrepJob* __restrict__ jobs, int njobs,
+                                                                     const __grid_constant__ JobBegins jb) {
   __shared__ uint64_t tile[kTile][kTile + 1];
-  const int ji = find_job(jobs, njobs, blockIdx.x, true);
+  const int ji = find_job(jb, jobs, njobs, blockIdx.x, true);
   const PrepJob& j = jobs[ji];
   const int64_t local = (int64_t)blockIdx.x - j.split_begin;
   const int64_t bx = local % j.split_gx, by = local / j.split_gx;
@@ -968,7 +963,8 @@ __global__ void __launch_bounds__(256) k_rowstats_pair(const __grid_constant__ P
   flush_row_maxima(mx, wmax, norms + ji, tex + ji);
 }
 
-// grouped modular problems: blockIdx.y = job, the same per-row work (the job's norm and width words)
+// grouped modular problems: the same per-row work (the job's norm and width words), a block row
+// per job (blockIdx.y)
 __global__ void __launch_bounds__(256) k_rowstats_batched(const PrepJob* __restrict__ jobs) {
   const PrepJob& j = jobs[blockIdx.y];
   const float grow = square_grow(j.K, j.st.nkt), floor_add = square_floor(j.K);
@@ -983,6 +979,48 @@ __global__ void __launch_bounds__(256) k_rowstats_batched(const PrepJob* __restr
     wmax = max(wmax, width);
   }
   flush_row_maxima(mx, wmax, j.norm, j.tex);
+}
+
+// The same over the rows of all jobs numbered one after the other (jb: each job's first row): warp
+// w of the grid takes the rows [w c, (w + 1) c), and its maxima go to a job's words when the job
+// changes and at the end
+__global__ void __launch_bounds__(256) k_rowstats_flat(const PrepJob* __restrict__ jobs, int njobs, int64_t rows,
+                                                       const __grid_constant__ JobBegins jb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * 8, w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t c = (rows + warps - 1) / warps;
+  const int64_t g0 = w * c, g1 = g0 + c < rows ? g0 + c : rows;
+  if (g0 >= g1) return;
+  int lo = 0, hi = njobs - 1;  // the job of row g0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jb.b[mid] <= g0) lo = mid;
+    else hi = mid - 1;
+  }
+  int ji = lo;
+  float mx = 0.0f;
+  int wmax = 0;
+  for (int64_t g = g0; g < g1; ++g) {
+    while (ji + 1 < njobs && jb.b[ji + 1] <= g) {  // the next job: flush this one's maxima
+      if (lane == 0) {
+        if (mx > 0.0f) atomicMax(jobs[ji].norm, __float_as_uint(mx));
+        if (wmax > 0) atomicMax(jobs[ji].tex, (unsigned int)wmax);
+      }
+      mx = 0.0f;
+      wmax = 0;
+      ++ji;
+    }
+    const PrepJob& j = jobs[ji];
+    float sq_up;
+    int width;
+    merge_row_warp(j, g - jb.b[ji], lane, square_grow(j.K, j.st.nkt), square_floor(j.K), sq_up, width);
+    mx = fmaxf(mx, sq_up);
+    wmax = max(wmax, width);
+  }
+  if (lane == 0) {
+    if (mx > 0.0f) atomicMax(jobs[ji].norm, __float_as_uint(mx));
+    if (wmax > 0) atomicMax(jobs[ji].tex, (unsigned int)wmax);
+  }
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 3) k_split_pair(const __grid_constant__ PrepPair pp) {
@@ -1149,31 +1187,49 @@ void prep_job_blocks(PrepJob& j, int64_t& exp_blocks, int64_t& split_blocks) {
   split_blocks += (j.R > 0 && j.K > 0) ? (int64_t)j.split_gx * ((j.R + kTile - 1) / kTile) : 0;
 }
 
-int launch_prep_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, int64_t split_blocks,
-                        bool exponents, bool split, cudaStream_t s) {
+int64_t job_begins(const PrepJob* jobs_host, int njobs, JobNumbering which, JobBegins& out) {
+  out.n = njobs <= kBeginCache ? njobs : 0;
+  out.pad = 0;
+  int64_t total = 0;
+  for (int q = 0; q < njobs; ++q) {
+    const PrepJob& j = jobs_host[q];
+    const int64_t begin = which == kByExponentBlock ? j.exp_begin : which == kBySplitTile ? j.split_begin : total;
+    if (q < kBeginCache) out.b[q] = begin;
+    if (which == kByRow) total += j.R;
+  }
+  return total;
+}
+
+int launch_prep_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t exp_blocks,
+                        int64_t split_blocks, bool exponents, bool split, cudaStream_t s) {
   if (njobs <= 0) return GBD_OK;
+  static thread_local JobBegins jb;  // 15 KB: not on the stack
   if (exponents) {
     k_prep_init_batched<<<njobs, 256, 0, s>>>(jobs_dev);
     int rc = launch_check("batched init launch");
     if (rc) return rc;
     if (exp_blocks > 0) {
       if (exp_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many exponent blocks");
-      k_exponents_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
+      job_begins(jobs_host, njobs, kByExponentBlock, jb);
+      k_exponents_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs, jb);
       if ((rc = launch_check("batched exponent launch"))) return rc;
     }
   }
   if (split && split_blocks > 0) {
     if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
-    k_split_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
+    job_begins(jobs_host, njobs, kBySplitTile, jb);
+    k_split_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs, jb);
     return launch_check("batched split launch");
   }
   return GBD_OK;
 }
 
-int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, cudaStream_t s, int prec,
-                            const unsigned int* retry_if) {
+int launch_magplane_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t split_blocks,
+                            cudaStream_t s, int prec, const unsigned int* retry_if) {
   if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+  static thread_local JobBegins jb;
+  job_begins(jobs_host, njobs, kBySplitTile, jb);
   unsigned g = (unsigned)split_blocks;
   if (retry_if) {
     int sms = 0;
@@ -1182,53 +1238,23 @@ int launch_magplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_bl
     if ((int64_t)g > cap) g = (unsigned)cap;
   }
   if (prec == kCertFP8) {
-    if (retry_if) k_magplane_batched<true, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if);
-    else k_magplane_batched<true, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr);
+    if (retry_if) k_magplane_batched<true, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if, jb);
+    else k_magplane_batched<true, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr, jb);
   } else {
-    if (retry_if) k_magplane_batched<false, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if);
-    else k_magplane_batched<false, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr);
+    if (retry_if) k_magplane_batched<false, true><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, retry_if, jb);
+    else k_magplane_batched<false, false><<<g, kSplitThreads, 0, s>>>(jobs_dev, njobs, split_blocks, nullptr, jb);
   }
   return launch_check("batched magnitude plane launch");
 }
 
-int launch_residue_batched(const PrepJob* jobs_dev, int njobs, const ModSplit& mp, int64_t split_blocks,
-                           cudaStream_t s) {
+int launch_residue_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, const ModSplit& mp,
+                           int64_t split_blocks, cudaStream_t s) {
   if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
   if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
-  k_residue_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs, mp);
+  static thread_local JobBegins jb;
+  job_begins(jobs_host, njobs, kBySplitTile, jb);
+  k_residue_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs, mp, jb);
   return launch_check("batched residue launch");
-}
-
-int launch_stats_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, float* stats_dev,
-                         cudaStream_t s) {
-  if (njobs <= 0) return GBD_OK;
-  int rc = launch_prep_batched(jobs_dev, njobs, exp_blocks, 0, true, false, s);
-  if (rc) return rc;
-  if (exp_blocks > 0) {
-    k_magnitudes_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
-    if ((rc = launch_check("batched magnitude launch"))) return rc;
-  }
-  k_min_stats_batched<<<njobs / 2, 256, 0, s>>>(jobs_dev, stats_dev);
-  return launch_check("batched statistics launch");
-}
-
-int launch_statplane_batched(const PrepJob* jobs_dev, int njobs, int64_t split_blocks, int64_t max_rows,
-                             cudaStream_t s) {
-  if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
-  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
-  if (njobs > 65535) return set_error(GBD_ERR_LIMIT, "grouped: too many modular problems for one batch");
-  k_statplane_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs);
-  int rc = launch_check("batched statistics and planes launch");
-  if (rc) return rc;
-  const int64_t gx = (max_rows + 7) / 8 < 64 ? (max_rows + 7) / 8 : 64;  // warps per row, blocks per job
-  k_rowstats_batched<<<dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)njobs), 256, 0, s>>>(jobs_dev);
-  return launch_check("batched row statistics launch");
-}
-
-int launch_magnitudes_batched(const PrepJob* jobs_dev, int njobs, int64_t exp_blocks, cudaStream_t s) {
-  if (njobs <= 0 || exp_blocks <= 0) return GBD_OK;
-  k_magnitudes_batched<<<(unsigned)exp_blocks, 256, 0, s>>>(jobs_dev, njobs);
-  return launch_check("batched magnitude launch");
 }
 
 void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks) {
@@ -1237,6 +1263,32 @@ void prep_pair_blocks(PrepPair& pp, int64_t& exp_blocks, int64_t& split_blocks) 
   prep_job_blocks(pp.j[0], exp_blocks, split_blocks);
   prep_job_blocks(pp.j[1], exp_blocks, split_blocks);
 }
+
+int launch_statplane_batched(const PrepJob* jobs_dev, const PrepJob* jobs_host, int njobs, int64_t split_blocks,
+                             int64_t max_rows, cudaStream_t s) {
+  if (njobs <= 0 || split_blocks <= 0) return GBD_OK;
+  if (split_blocks > 0x7FFFFFFF) return set_error(GBD_ERR_LIMIT, "grouped: too many split blocks");
+  if (njobs > 65535) return set_error(GBD_ERR_LIMIT, "grouped: too many modular problems for one batch");
+  static thread_local JobBegins jb;
+  job_begins(jobs_host, njobs, kBySplitTile, jb);
+  k_statplane_batched<<<(unsigned)split_blocks, kSplitThreads, 0, s>>>(jobs_dev, njobs, jb);
+  int rc = launch_check("batched statistics and planes launch");
+  if (rc) return rc;
+  // the rows of all jobs in equal ranges over one wave of warps when the begins fit the
+  // parameters, else a block row per job
+  const int64_t rows = job_begins(jobs_host, njobs, kByRow, jb);
+  if (jb.n == njobs) {
+    int sms = 0;
+    if ((rc = current_device(nullptr, &sms))) return rc;
+    const int64_t blocks = (rows + 7) / 8 < 8 * (int64_t)sms ? (rows + 7) / 8 : 8 * (int64_t)sms;
+    if (blocks > 0) k_rowstats_flat<<<(unsigned)blocks, 256, 0, s>>>(jobs_dev, njobs, rows, jb);
+  } else {
+    const int64_t gx = (max_rows + 7) / 8 < 64 ? (max_rows + 7) / 8 : 64;  // warps per row, blocks per job
+    k_rowstats_batched<<<dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)njobs), 256, 0, s>>>(jobs_dev);
+  }
+  return launch_check("batched row statistics launch");
+}
+
 
 int launch_exponents_pair(const PrepPair& pp, int64_t exp_blocks, void* zero, size_t zero_bytes, cudaStream_t s) {
   if (exp_blocks <= 0) return GBD_OK;

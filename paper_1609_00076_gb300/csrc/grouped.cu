@@ -409,11 +409,13 @@ int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* workspace
     // one pass over every problem's operands: statistics and FP8 magnitude planes, as the single call
     int64_t max_rows = 0;
     for (const auto& j : plan->jobs) max_rows = j.R > max_rows ? j.R : max_rows;
-    if ((rc = emu::launch_statplane_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->split_blocks, max_rows, s)))
+    if ((rc = emu::launch_statplane_batched(plan->jobs_dev, plan->jobs.data(), (int)plan->jobs.size(), plan->split_blocks,
+                                             max_rows, s)))
       return rc;
     const int prec = emu::cert_prec_default();
     if (prec == emu::kCertBF16 &&
-        (rc = emu::launch_magplane_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->split_blocks, s, prec)))
+        (rc = emu::launch_magplane_batched(plan->jobs_dev, plan->jobs.data(), (int)plan->jobs.size(), plan->split_blocks, s,
+                                            prec)))
       return rc;
     for (size_t q = 0; q < plan->emu.size(); ++q) {
       const auto& em = plan->emu[q];
@@ -633,7 +635,8 @@ int gbd_grouped_plan_run(gbd_plan* plan, void* stream) {
   // emulated: exponents and digit slices of every problem (three launches), then one slice-product
   // launch per slice count
   if (!plan->jobs.empty() &&
-      (rc = emu::launch_prep_batched(plan->jobs_dev, (int)plan->jobs.size(), plan->exp_blocks, plan->split_blocks,
+      (rc = emu::launch_prep_batched(plan->jobs_dev, plan->jobs.data(), (int)plan->jobs.size(), plan->exp_blocks,
+                                     plan->split_blocks,
                                      true, true, s)))
     return rc;
   for (const auto& sg : plan->segments) {
