@@ -48,8 +48,9 @@ def workload_name():
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram bytes (read + write) of the product phase of one 8192^3 call (dram__bytes_read.sum +
 # dram__bytes_write.sum of the product launches, one ncu pass at full size; the modular entry is
-# the two-SM launch plus its one-SM tail launch), None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": None}
+# the two-SM launch plus its one-SM tail launch: 29.60 + 0.68 GB), None until captured for the
+# current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 30.279e9}
 
 
 def load_peaks():
@@ -695,20 +696,12 @@ def exponent_legs(dev, stream, A, B, C, ws, wsb, split_ws, split_wsb, es=(8, 32)
     return out
 
 
-def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
-    """The grouped batch: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
-    uniform[-1,1).  Native problems take the autotuner's tile per output bucket and inner-dimension
-    split per (output, k) bucket, split-emulated ones its kernel class per (output, k) bucket
-    (measured here first; native also timed without the split); every plan
-    run is captured once in a CUDA graph and replayed.  Modes: native FP64; modular (certified and
-    planned on the device in every replay); split digits (slices certified when the plan is
-    made).  TFLOP/s of graph replays (best of `reps`)."""
-    import ctypes
-    import tempfile
-
+def grouped_batch(dev, count: int = 512, seed: int = 3000):
+    """The grouped batch's problems (descriptors without a mode), the tensors they use and their
+    flops: m, n, k each log-uniform on [32, 2048], random transposes, uniform[-1,1) operands."""
     import torch
 
-    from paper_1609_00076_gb300 import autotune, gbdgemm, synth
+    from paper_1609_00076_gb300 import synth
     sizes = synth.log_uniform_sizes(seed, count, 32, 2048)
     flips = synth.coin(seed + 1, 2 * count)
     keep, base = [], []
@@ -726,6 +719,56 @@ def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int =
         base.append(dict(transa=ta, transb=tb, m=m, n=n, k=k, alpha=1.0, beta=0.0, A=A, lda=ra, B=B, ldb=rb,
                          C=C, ldc=m, slices=0, tile=0, tol=0.0))
     flops = sum(2.0 * p["m"] * p["n"] * p["k"] for p in base)
+    return base, keep, flops
+
+
+def grouped_calls_only(dev, stream, which: str, count: int, steps: int, warmup: int):
+    """One mode of the grouped batch alone (profiling runs): the plan of `count` problems in modular
+    or split mode, `warmup` runs, then `steps` runs timed with events (nothing else launches)."""
+    import torch
+
+    from paper_1609_00076_gb300 import gbdgemm
+    base, keep, flops = grouped_batch(dev, count)
+    mode = gbdgemm.GBD_MODE_MODULAR if which == "grouped-modular" else gbdgemm.GBD_MODE_EMULATED
+    arr = gbdgemm.problem_array([dict(p, mode=mode) for p in base])
+    wsb = gbdgemm.gbd_dgemm_grouped_workspace_size(arr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    rc, plan = gbdgemm.gbd_grouped_plan_create(arr, ws, wsb, stream=stream)
+    gbdgemm.check(rc)
+    try:
+        for _ in range(warmup):
+            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+        torch.cuda.synchronize()
+        ev = _events(steps + 1)
+        ev[0].record(stream)
+        for i in range(steps):
+            gbdgemm.check(gbdgemm.gbd_grouped_plan_run(plan, stream=stream))
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        gbdgemm.check(gbdgemm.gbd_check_device_error(stream))
+    finally:
+        gbdgemm.gbd_grouped_plan_destroy(plan)
+    ms = ev[0].elapsed_time(ev[-1]) / steps
+    return {"path": which, "problems": count, "ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+            "workspace_bytes": wsb, "steps": steps, "warmup": warmup}
+
+
+def grouped_measure(dev, stream, count: int = 512, seed: int = 3000, reps: int = 3):
+    """The grouped batch: 512 problems, m, n, k each log-uniform on [32, 2048], random transposes,
+    uniform[-1,1).  Native problems take the autotuner's tile per output bucket and inner-dimension
+    split per (output, k) bucket, split-emulated ones its kernel class per (output, k) bucket
+    (measured here first; native also timed without the split); every plan
+    run is captured once in a CUDA graph and replayed.  Modes: native FP64; modular (certified and
+    planned on the device in every replay); split digits (slices certified when the plan is
+    made).  TFLOP/s of graph replays (best of `reps`)."""
+    import ctypes
+    import tempfile
+
+    import torch
+
+    from paper_1609_00076_gb300 import autotune, gbdgemm
+    base, keep, flops = grouped_batch(dev, count, seed)
     # the autotuner: native tile per output-size bucket, measured on this GPU into a fresh cache
     t0 = time.perf_counter()
     tuner = autotune.Autotuner(cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"))
@@ -858,9 +901,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["grouped", "serving", "level3", "cpu", "modular", "split"],
-                    help="run only the grouped-batch, serving, level-3 or host five-loop measurement, or only the "
-                         "modular or split emulated calls at --size (profiling runs), and print it")
+    ap.add_argument("--only", choices=["grouped", "serving", "level3", "cpu", "modular", "split", "grouped-modular",
+                                       "grouped-split"],
+                    help="run only the grouped-batch, serving, level-3 or host five-loop measurement, only the "
+                         "modular or split emulated calls at --size, or only one emulated mode of the grouped batch "
+                         "of --problems problems (profiling runs), and print it")
+    ap.add_argument("--problems", type=int, default=512, help="problems of the grouped batch in --only grouped-*")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the grouped-batch and serving measurements (profiling runs)")
     ap.add_argument("--size", type=int, default=8192,
@@ -884,6 +930,8 @@ def main():
             res = calls_only(dev, stream, args.only, args.steps, args.warmup)
         elif args.only == "grouped":
             res = grouped_measure(dev, stream, reps=1)
+        elif args.only in ("grouped-modular", "grouped-split"):
+            res = grouped_calls_only(dev, stream, args.only, args.problems, args.steps, args.warmup)
         elif args.only == "level3":
             res = level3_measure(dev, stream, n=args.size)
         else:
