@@ -46,11 +46,10 @@ def workload_name():
 
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram bytes (read + write) of the product phase of one 8192^3 call (dram__bytes_read.sum +
-# dram__bytes_write.sum of the product launches, one ncu pass at full size; the modular entry is
-# the two-SM launch plus its one-SM tail launch: 29.60 + 0.68 GB), None until captured for the
-# current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 30.279e9}
+# dram bytes (read + write) of the product launch of one 8192^3 call (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu pass at full size; the modular entry is the mean of two launches,
+# 12.93 + 1.10 and 13.51 + 1.10 GB), None until captured for the current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 14.32e9}
 
 
 def load_peaks():
@@ -177,18 +176,11 @@ def host_inputs(seed: int):
 # planes in one pass, the row merge (which also moves the planes to each row's scale), the
 # certification product, the plan, the BF16 retry's planes, product and plan (three launches that
 # return at once when the FP8 plan is feasible), residues, column scales, the products and the
-# reconstruction of C from their parked residues (the tail launch comes on top, see mod_tail_launches)
+# reconstruction of C from their parked residues
 MOD_LAUNCHES = 11
+# host threads (each with its own stream and device buffer) of the end-to-end measurement
+E2E_STREAMS = 2
 
-
-def mod_tail_launches(m, n, sms):
-    """1 when the modular call at m x n runs its last wave of 256 x 256 tiles as 128 x 128 tiles on
-    one-SM CTAs (the last wave leaves SM pairs idle and its quarters fit one wave), else 0."""
-    tiles = -(-m // 256) * -(-n // 256)
-    pairs = min(tiles, min(sms, 256) // 2)
-    waves = -(-tiles // pairs)
-    last = tiles - (waves - 1) * pairs
-    return 1 if waves > 1 and last < pairs and 4 * last <= min(sms, 256) else 0
 
 
 def oracle_sample(target_s: float, seed: int = 2000, want_rows: bool = False):
@@ -359,23 +351,25 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- end to end through the host-buffer C-ABI call (pinned host memory), copies inside the region ----
     # Each step is one gbd_dgemm_emu_mod_host call: upload of A and B, the emulated product, download of C.
-    # Serial: one call at a time.  Overlapped (the reported value): two host threads, each driving its own
-    # stream and device buffer, so one call's transfers run under the other's products.
+    # Serial: one call at a time.  Overlapped (the reported value): E2E_STREAMS host threads, each driving
+    # its own stream and device buffer, so the calls' transfers run under the other calls' products (a
+    # call's own chain, upload, products and download, is about twice the products alone).
     A_p = torch.from_numpy(A_h).pin_memory()
     B_p = torch.from_numpy(B_h).pin_memory()
-    C_p = [torch.empty(M * N, dtype=torch.float64).pin_memory() for _ in range(2)]
+    C_p = [torch.empty(M * N, dtype=torch.float64).pin_memory() for _ in range(E2E_STREAMS)]
     hsize = gbdgemm.gbd_dgemm_emu_mod_host_buffer_size("N", "N", M, N, K, -1)
-    hbufs = [torch.empty(hsize, dtype=torch.uint8, device=dev) for _ in range(2)]
-    hstreams = [stream, torch.cuda.Stream(device=dev)]
+    hbufs = [torch.empty(hsize, dtype=torch.uint8, device=dev) for _ in range(E2E_STREAMS)]
+    hstreams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(E2E_STREAMS - 1)]
     # enough calls that the first upload and the last download, which nothing hides, weigh little
-    e2e_steps = max(4, min(args.steps, 16))
+    e2e_steps = max(2 * E2E_STREAMS, min(args.steps, 18))
 
     def host_call(i):
-        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[i % 2], M, -1,
-                                                     0.0, hbufs[i % 2], hsize, None, stream=hstreams[i % 2]))
+        j = i % E2E_STREAMS
+        gbdgemm.check(gbdgemm.gbd_dgemm_emu_mod_host("N", "N", M, N, K, 1.0, A_p, M, B_p, K, 0.0, C_p[j], M, -1,
+                                                     0.0, hbufs[j], hsize, None, stream=hstreams[j]))
 
-    host_call(0)  # untimed warm-up of both buffers and streams (first use of the pinned memory)
-    host_call(1)
+    for i in range(E2E_STREAMS):  # untimed warm-up of every buffer and stream (first use of the pinned memory)
+        host_call(i)
     torch.cuda.synchronize()
     e2e_sampler = ClockSampler(local)
     e2e_sampler.start()
@@ -387,28 +381,31 @@ def run_ours(args, world, rank, local, pg):
         sev[i + 1].record(stream)
     torch.cuda.synchronize()
     serial_ms = max_over_ranks(pg, sev[0].elapsed_time(sev[-1]), dev)
-    # overlapped: stream 1 starts after e0 on stream 0; e1 on stream 0 after both streams are done
-    e0, e1, last1 = _events(3)
+    # overlapped: the other streams start after e0 on stream 0; e1 on stream 0 after every stream is done
+    e0, e1 = _events(2)
     e0.record(hstreams[0])
-    hstreams[1].wait_event(e0)
+    for hs in hstreams[1:]:
+        hs.wait_event(e0)
     errors = []
 
     def driver(t):
         try:
-            for i in range(t, e2e_steps, 2):
+            for i in range(t, e2e_steps, E2E_STREAMS):
                 host_call(i)
         except Exception as exc:  # re-raised below, on the main thread
             errors.append(exc)
 
-    threads = [threading.Thread(target=driver, args=(t,)) for t in (0, 1)]
+    threads = [threading.Thread(target=driver, args=(t,)) for t in range(E2E_STREAMS)]
     for th in threads:
         th.start()
     for th in threads:
         th.join()
     if errors:
         raise errors[0]
-    last1.record(hstreams[1])
-    hstreams[0].wait_event(last1)
+    for hs in hstreams[1:]:
+        last = torch.cuda.Event(enable_timing=False)
+        last.record(hs)
+        hstreams[0].wait_event(last)
     e1.record(hstreams[0])
     torch.cuda.synchronize()
     e2e_clocks = e2e_sampler.stop()
@@ -443,7 +440,7 @@ def run_ours(args, world, rank, local, pg):
     s_achieved = split["products"] * flops / (split["gemm_ms"] / 1000.0) / 1e12
     cpu_v, cpu_dt, cpu_rows, cpu_threads, rows, ref = oracle_sample(target_s=8.0, want_rows=True)
     accuracy = accuracy_report(results, rows, ref)
-    launches_per_step = MOD_LAUNCHES + mod_tail_launches(M, N, torch.cuda.get_device_properties(dev).multi_processor_count)
+    launches_per_step = MOD_LAUNCHES
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -462,8 +459,8 @@ def run_ours(args, world, rank, local, pg):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
                      "frac": achieved / bf16_burst, "frac_of_sustained": achieved / bf16_sust,
                      "traffic": TRAFFIC_PER_LAUNCH.get("mod"),
-                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, residues parked), "
-                               "with k_mod_gemm<0> for the last wave's tiles (cta_group::1)",
+                     "kernel": "k_mod_gemm_pair (tcgen05 kind::f16 cta_group::2, BF16 -> FP32, residues parked; "
+                               "(256 x 256 tile, modulus) work units, modulus-major)",
                      "peak_source": f"{src} bf16_tflops (burst: one call of about 10 ms)"},
         "split": {
             "value": split["value"], "unit": "TFLOP/s", "ms_per_call": split["ms"], "steps": split["steps"],
@@ -486,8 +483,8 @@ def run_ours(args, world, rank, local, pg):
         "accuracy": accuracy,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * M * K * 8,
                 "d2h_bytes_per_step": M * N * 8, "steps": e2e_steps,
-                "call": "gbd_dgemm_emu_mod_host (bits = -1), pinned host A, B, C; two host threads, one stream and "
-                        "buffer each",
+                "call": f"gbd_dgemm_emu_mod_host (bits = -1), pinned host A, B, C; {E2E_STREAMS} host threads, one "
+                        "stream and buffer each",
                 "ms_per_step": e2e_ms / e2e_steps,
                 "serial": {"value": e2e_serial, "ms_per_step": serial_ms / e2e_steps}, "clocks": e2e_clocks},
         "gpu_launches": launches_per_step * args.steps,

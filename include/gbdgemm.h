@@ -256,13 +256,12 @@ GBD_API int gbd_dgemm_emu_noalloc(char transa, char transb, int64_t m, int64_t n
  *   preparation with the certification (prep_ms) and the products with the reconstruction
  *   (gemm_ms).
  * Kernels: the preparation, the certification (magnitude planes and their product) and the
- *   plan, then the residues and the products: 256 x 256 tiles on
- *   SM pairs, or 128 x 128 tiles on single SMs (with each tile's moduli spread over several
- *   SMs when there are few tiles), by a wave-quantised estimate of their times; a last
- *   wave of 256 x 256 tiles that would leave SM pairs idle runs as 128 x 128 quarters in
- *   one more launch when they fit one wave.  The environment variables GBD_EMU_KERNEL
- *   (pair, single or split) and GBD_EMU_TAIL=0 override the choice (tests and tuning);
- *   the result is the same bits either way.
+ *   plan, then the residues and the products: (256 x 256 tile, modulus) work units on
+ *   SM pairs, modulus by modulus, or 128 x 128 tiles on single SMs (with each tile's moduli
+ *   spread over several SMs when there are few tiles), by a wave-quantised estimate of their
+ *   times.  The environment variables GBD_EMU_KERNEL (pair, single or split) and
+ *   GBD_EMU_GROUP_M (rows of 256 x 256 tiles per raster group of the pair form) override
+ *   the choice (tests and tuning); the result is the same bits either way.
  * Returns 0, a BLAS argument index, or GBD_ERR_*.
  */
 GBD_API size_t gbd_dgemm_emu_mod_workspace_size(int64_t m, int64_t n, int64_t k, int bits);

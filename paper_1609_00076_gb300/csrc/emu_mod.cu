@@ -123,13 +123,8 @@ struct ModArgs {
   int64_t m, n;
   int nkb;
   int tiles_m, num_tiles, group_m;
-  int tile_end;  // the two-SM form computes tiles [0, tile_end) of its num_tiles
-  int tri;       // 0: all of C; 1: only the tiles that meet its lower triangle (i >= j), 2: its
-                 // upper one (m = n), by rows of tiles
-  // a one-SM launch over the tail of a two-SM raster (tail_from >= 0): its tile u is quadrant
-  // u % 4 of the 256 x 256 tile tail_from + u / 4 of that raster (tail_tiles_m, tail_group_m,
-  // tail_num as tiles_m, group_m and num_tiles of the two-SM launch)
-  int tail_from, tail_tiles_m, tail_group_m, tail_num;
+  int tri;  // 0: all of C; 1: only the tiles that meet its lower triangle (i >= j), 2: its
+            // upper one (m = n), by rows of tiles
   int p[kMaxModuli];         // moduli
   uint32_t bar[kMaxModuli];  // floor(2^32 / p_l), for Barrett reduction
   const ModPlan* plan;       // the call's n (and whether the target was reachable)
@@ -166,14 +161,7 @@ __device__ __forceinline__ void raster_coords(int tri, int tile, int tiles_m, in
 
 // the coordinates, in 128 x 128 tiles, of tile `tile` of a one-SM launch
 __device__ __forceinline__ void tile128_coords(const ModArgs& p, int tile, int& tm, int& tn) {
-  if (p.tail_from < 0) {
-    raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
-    return;
-  }
-  int tm2, tn2;
-  raster_coords(p.tri, p.tail_from + tile / 4, p.tail_tiles_m, p.tail_group_m, p.tail_num, tm2, tn2);
-  tm = 2 * tm2 + (tile & 1);
-  tn = 2 * tn2 + ((tile >> 1) & 1);
+  raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
 }
 
 // the moduli [l0, l1) of work unit g of `groups` (at most nmod units per tile)
@@ -197,7 +185,8 @@ __device__ __forceinline__ int mod_nonneg(int v, uint32_t p, uint32_t b) {
 // and COLS columns of the TBN-wide tile.  Per modulus: drain the 1024-deep chunks into int32
 // sums (reduced modulo p_l every kReduceChunks chunks), reduce modulo p_l and park the residues,
 // one byte each, in the block's plane of the park array (k_mod_crt rebuilds C from them).
-// SPLIT: the work units are (tile, group of moduli); TABLE: the tiles belong to the problems of a
+// SPLIT: the work units are (tile, group of moduli); PAIR: (tile, modulus), modulus-major (unit u
+// is modulus u / num_tiles of tile u % num_tiles); TABLE: the tiles belong to the problems of a
 // grouped launch (table entries in tile order), and a tile whose problem's plan is infeasible is
 // skipped (another kernel computes that problem).
 template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE, bool SPLIT>
@@ -224,12 +213,16 @@ __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tm
   int acc[COLS];
   int cur = 0;  // grouped: the table entry of the current tile (a CTA's tiles increase)
   for (int u = unit0; u < units; u += unit_step) {
-    const int tile = SPLIT ? u / groups : u;
+    const int tile = SPLIT ? u / groups : PAIR ? u % p.num_tiles : u;
     int l0 = 0, l1 = nmod, nkb = p.nkb, tm, tn;
     uint8_t* park = p.park;
     int pmods = p.park_mods, nbn = p.nbn;
     int64_t pm = p.m, pn = p.n;
     if (SPLIT) unit_range(u % groups, groups, nmod, l0, l1);
+    if (PAIR) {
+      l0 = u / p.num_tiles;
+      l1 = l0 + 1;
+    }
     if (TABLE) {
       while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
       const ModTableEntry& e = table[cur];
@@ -535,26 +528,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
   const uint32_t tmem_base = *tmem_slot;
   const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
   const int nmod = plan.n;
+  // work units (tile, modulus), modulus-major: the pairs sweep the tiles of one modulus's planes
+  // together, so a band of them stays in L2, and every pair has work down to the last wave
+  const int units = p.num_tiles * nmod;
 
   if (warp == 0) {
     // ------------------------------ TMA producer (both CTAs) ------------------------------
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
-      for (int tile = pair_id; tile < p.tile_end; tile += num_pairs) {
+      for (int u = pair_id; u < units; u += num_pairs) {
+        const int tile = u % p.num_tiles, l = u / p.num_tiles;
         int tm, tn;
         raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
         const int m0 = tm * k2BM + (int)rank * 128;
         const int nb0 = tn * k2BN + (int)rank * 128;
-        for (int l = 0; l < nmod; ++l)
-          for (int kb = 0; kb < p.nkb; ++kb) {
-            mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
-            if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
-            const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
-            tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, l);
-            tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, l);
-            if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
-          }
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
+          if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
+          const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
+          tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, l);
+          tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, l);
+          if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
+        }
       }
     }
     __syncwarp();
@@ -564,34 +560,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
       constexpr uint32_t idesc = idesc_bf16(k2BM, k2BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int tile = pair_id; tile < p.tile_end; tile += num_pairs)
-        for (int l = 0; l < nmod; ++l)
-          for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
-            const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
-            mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
+      for (int u = pair_id; u < units; u += num_pairs)
+        for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+          const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+          mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + buf * k2BN;
+          const int i1 = min(p.nkb, i0 + kChunkBlocks);
+          for (int it = i0; it < i1; ++it) {
+            mbar_wait_cluster(&full[stage], phase, p.err, kErrWaitTma);
             tc_fence_after();
-            const uint32_t dtm = tmem_base + buf * k2BN;
-            const int i1 = min(p.nkb, i0 + kChunkBlocks);
-            for (int it = i0; it < i1; ++it) {
-              mbar_wait_cluster(&full[stage], phase, p.err, kErrWaitTma);
-              tc_fence_after();
-              const uint64_t da = smem_desc_sw128(a_base + stage * L::kABytes);
-              const uint64_t db = smem_desc_sw128(b_base + stage * L::kBBytes);
+            const uint64_t da = smem_desc_sw128(a_base + stage * L::kABytes);
+            const uint64_t db = smem_desc_sw128(b_base + stage * L::kBBytes);
 #pragma unroll
-              for (int kk = 0; kk < kBK / 16; ++kk)
-                umma_bf16_pair(dtm, da + 2 * kk, db + 2 * kk, idesc, (it > i0 || kk > 0) ? 1u : 0u);
-              umma_commit_pair(&empty[stage]);  // frees this stage in both CTAs
-              if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
-            }
-            umma_commit_pair(&acc_full[buf]);  // chunk complete in both CTAs' TMEM
+            for (int kk = 0; kk < kBK / 16; ++kk)
+              umma_bf16_pair(dtm, da + 2 * kk, db + 2 * kk, idesc, (it > i0 || kk > 0) ? 1u : 0u);
+            umma_commit_pair(&empty[stage]);  // frees this stage in both CTAs
+            if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
           }
-      umma_commit_pair(done);
-      mbar_wait_cluster(done, 0, p.err, kErrWaitMma);
+          umma_commit_pair(&acc_full[buf]);  // chunk complete in both CTAs' TMEM
+        }
+      if (chunk > 0) {  // a pair without a unit issued nothing and has nothing to wait for
+        umma_commit_pair(done);
+        mbar_wait_cluster(done, 0, p.err, kErrWaitMma);
+      }
     }
     __syncwarp();
   } else {
     mod_park<k2EpiWarps, k2BN, true, false, false>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
-                                                   num_pairs, p.tile_end, (int)rank * 128);
+                                                   num_pairs, units, (int)rank * 128);
   }
 
   tc_fence_before();
@@ -1158,22 +1155,25 @@ void mod_split_params(ModSplit& ms) {
 
 // Relative throughput per SM of the two-SM form over the one-SM form when both fill the GPU
 constexpr double kModPairGain = 1.2;
+// moduli assumed by the kernel choice when the device picks the count (12 at the FP64 bound for
+// uniform inputs at k = 8192)
+constexpr int kModTypical = 12;
 
 // the product kernel of one call; `a` carries everything but the tile geometry; the residue
 // planes hold up to nmod_ws moduli (the plan's n is at most that)
-int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, const ModWorkspace& ws, int sms,
-                    cudaStream_t stream) {
+int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, int bits, ModArgs& a, const ModWorkspace& ws,
+                    int sms, cudaStream_t stream) {
   // GBD_EMU_KERNEL=pair|single|split overrides the choice (tests and tuning).  Otherwise the
-  // expected time in units of one 128 x 128 tile on one SM: whole waves of tiles over the SMs
-  // (or SM pairs), a 256 x 256 tile being four units on two SMs at kModPairGain, a last wave
-  // that leaves pairs idle going to one-SM CTAs when its quarters fit one wave; and the one-SM
-  // form splits the moduli of each tile over several CTAs for at most 8 tiles, or for fewer
-  // tiles than half the SMs with a deep inner dimension (k >= 2048); measured at 256^3 (4
-  // tiles) 0.145 against 0.169 ms, 256^2 x 4096 0.25 against 0.47 ms, but 512^3 (16 tiles) 0.22
-  // against 0.20 ms and 1024^3 (64 tiles) 0.34 against 0.30 ms.
+  // smallest expected time, in units of one 128 x 128 tile with all its moduli on one SM, with
+  // whole waves of work units over the SMs (or SM pairs):
+  //   single: units are tiles;
+  //   split (one-SM, no triangle; at most 8 tiles, or fewer tiles than half the SMs with
+  //     k >= 2048): units are (tile, group of moduli), at most 16 groups per tile;
+  //   pair: units are (256 x 256 tile, modulus), each four quarter-tiles of one modulus on two
+  //     SMs at kModPairGain.
+  // The split rule's region is the measured one (256^3: 0.145 against 0.169 ms for single;
+  // 256^2 x 4096: 0.25 against 0.47 ms), where it also wins the estimate.
   const char* force = getenv("GBD_EMU_KERNEL");
-  const bool force_split = force && strcmp(force, "split") == 0;
-  if (force_split) force = nullptr;
   const int cta_cap = sms;
   // a triangular output (m = n) covers the tiles that meet its triangle
   auto count = [&](int64_t bm, int64_t bn) {
@@ -1183,14 +1183,26 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const int64_t tiles1 = count(kBM, kBN);
   const int64_t tiles2 = count(k2BM, k2BN);
   const int64_t pairs_avail = cta_cap / 2 > 0 ? cta_cap / 2 : 1;
-  const int64_t pairs = tiles2 < pairs_avail ? tiles2 : pairs_avail;
-  const int64_t waves2 = (tiles2 + pairs - 1) / pairs;
-  const int64_t last = tiles2 - (waves2 - 1) * pairs;  // tiles of the last two-SM wave
-  const char* tail_env = getenv("GBD_EMU_TAIL");       // GBD_EMU_TAIL=0 keeps the last wave on the pairs
-  const bool tail = waves2 > 1 && last < pairs && 4 * last <= cta_cap && !(tail_env && tail_env[0] == '0');
-  const double t_one = (double)((tiles1 + cta_cap - 1) / cta_cap);
-  const double t_pair = tail ? (double)(waves2 - 1) * 2.0 / kModPairGain + 1.0 : (double)waves2 * 2.0 / kModPairGain;
-  const bool pair = (force ? force[0] == 'p' : t_pair < t_one) && cta_cap >= 2;
+  const int nm = bits > 0 ? nmod_ws : kModTypical;
+  auto waves = [](int64_t units, int64_t slots) { return (double)((units + slots - 1) / slots); };
+  const double t_one = waves(tiles1, cta_cap);
+  int64_t groups = (cta_cap + tiles1 - 1) / tiles1;  // the kernel keeps at most nmod of them
+  if (groups > kMaxModuli) groups = kMaxModuli;
+  const int64_t g_eff = groups < nm ? groups : nm;
+  const double t_split = waves(tiles1 * g_eff, cta_cap) * (double)((nm + g_eff - 1) / g_eff) / nm;
+  const double t_pair = waves(tiles2 * nm, pairs_avail) * 2.0 / (kModPairGain * nm);
+  const bool split_ok = a.tri == 0 && (tiles1 <= 8 || (2 * tiles1 < sms && k >= 2048));
+  char choice = 's';  // single
+  if (force && (force[0] == 'p' || force[0] == 's')) {
+    choice = strcmp(force, "split") == 0 ? 'x' : force[0];
+  } else if (split_ok && t_split <= t_pair && t_split <= t_one) {
+    choice = 'x';
+  } else if (t_pair < t_one) {
+    choice = 'p';
+  }
+  if (choice == 'x' && a.tri != 0) choice = 's';
+  if (choice == 'p' && cta_cap < 2) choice = 's';
+  const bool pair = choice == 'p';
   const uint32_t brows = pair ? 128u : (uint32_t)kBM;  // rows of A (and of op(B)^T) one CTA stages
   CUtensorMap tmA, tmB;
   memset(&tmA, 0, sizeof(tmA));
@@ -1211,16 +1223,9 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
   const int64_t tiles = count(tbm, tbn);
   if (tiles > (int64_t)1 << 30) return set_error(GBD_ERR_LIMIT, "too many output tiles");
   a.num_tiles = (int)tiles;
-  a.tile_end = (int)tiles;
-  a.tail_from = -1;
-  a.tail_tiles_m = a.tail_group_m = a.tail_num = 0;
   cudaError_t e;
-  const bool split = !pair && a.tri == 0 &&
-                     (force_split || (!force && (tiles <= 8 || (2 * tiles < sms && k >= 2048))));
-  if (split) {
-    int groups = (int)((sms + tiles - 1) / tiles);  // the kernel keeps at most nmod of them
-    if (groups > kMaxModuli) groups = kMaxModuli;
-    a.groups = groups;
+  if (choice == 'x') {
+    a.groups = (int)groups;
     a.group_m = 1;
     const int64_t units = tiles * groups;
     const int grid = (int)(units < sms ? units : sms);
@@ -1228,28 +1233,18 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, ModArgs& a, co
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm split)");
     k_mod_gemm<true><<<grid, kThreads, Smem::kAlloc, stream>>>(a, tmA, tmB);
   } else if (pair) {
-    a.group_m = group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
-    // a last wave that would leave SM pairs idle goes to one-SM CTAs instead, as four 128 x 128
-    // tiles per 256 x 256 tile, when they fill at most one wave of SMs: it then takes about
-    // kModPairGain / 2 of a two-SM wave
-    if (tail) a.tile_end = (int)(tiles - last);
+    // (tile, modulus) units, at most nmod_ws per tile; pairs left without one return at once
+    const int64_t units = tiles * nmod_ws;
+    if (units >= ((int64_t)1 << 31)) return set_error(GBD_ERR_LIMIT, "too many output tiles");
+    const int64_t pairs = units < pairs_avail ? units : pairs_avail;
+    // GBD_EMU_GROUP_M sets the rows of tiles per raster group (tuning); by default about the
+    // square root of the pairs' concurrent tiles
+    const char* gm_env = getenv("GBD_EMU_GROUP_M");
+    const int gm_set = gm_env ? atoi(gm_env) : 0;
+    a.group_m = gm_set > 0 ? (gm_set < a.tiles_m ? gm_set : a.tiles_m) : group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
     e = cudaFuncSetAttribute(k_mod_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm pair)");
     k_mod_gemm_pair<<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
-    if (tail) {
-      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "modular gemm pair launch");
-      ModArgs b = a;
-      b.tail_from = a.tile_end;
-      b.tail_tiles_m = a.tiles_m;
-      b.tail_group_m = a.group_m;
-      b.tail_num = a.num_tiles;
-      b.tiles_m = 0;
-      b.group_m = 1;
-      b.num_tiles = b.tile_end = (int)(4 * last);
-      e = cudaFuncSetAttribute(k_mod_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm)");
-      k_mod_gemm<false><<<(unsigned)(4 * last), kThreads, Smem::kAlloc, stream>>>(b, tmA, tmB);
-    }
   } else {
     const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);
@@ -1405,7 +1400,7 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
   a.nbn = ws.nbn;
   a.err = device_error_word();
   if (timing && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
-  if ((rc = launch_mod_gemm(m, n, k, nmod_ws, a, ws, sms, s))) return rc;
+  if ((rc = launch_mod_gemm(m, n, k, nmod_ws, bits, a, ws, sms, s))) return rc;
   if (timing && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return cuda_fail(e, "dgemm_emu_mod: cudaEventRecord");
   CrtJob job;
   memset(&job, 0, sizeof(job));
@@ -1656,8 +1651,6 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   a.plan = g.plans[0];  // read at kernel start; the tiles use their own problems' plans
   a.err = device_error_word();
   a.num_tiles = g.mod_tiles;
-  a.tile_end = g.mod_tiles;
-  a.tail_from = -1;
   a.tiles_m = 1;
   a.group_m = 1;
   a.nkb = 1;

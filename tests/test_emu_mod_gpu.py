@@ -86,16 +86,25 @@ def test_model_parity_fringes(oracle_mod, monkeypatch, kernel, m, n, k):
     check_model(oracle_mod, "T", "N", m, n, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, out, 30)
 
 
-@pytest.mark.parametrize("tail", ["1", "0"])
-def test_model_parity_pair_with_tail_wave(oracle_mod, monkeypatch, tail):
-    # 9 x 10 tiles of 256 x 256 over the SM pairs leave a partial last wave; by default its
-    # tiles run as 128 x 128 quarters on one-SM CTAs after the two-SM launch (ragged in m, n, k)
+@pytest.mark.parametrize("m,n,k", [(2300, 2310, 100), (700, 300, 1500)])
+def test_model_parity_pair_partial_last_wave(oracle_mod, monkeypatch, m, n, k):
+    # the two-SM kernel's (tile, modulus) units leave a partial last wave over the SM pairs
+    # (9 x 10 tiles of 256 x 256, or 3 x 2, times the moduli); ragged in m, n and k
     monkeypatch.setenv("GBD_EMU_KERNEL", "pair")
-    monkeypatch.setenv("GBD_EMU_TAIL", tail)
-    m, n, k = 2300, 2310, 100
-    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "uniform", 77, pads=(1, 2, 3))
+    A, lda, B, ldb, C, ldc = _problem("N", "T", m, n, k, "uniform", 77 + m, pads=(1, 2, 3))
     out, _ = run_mod("N", "T", m, n, k, 0.5, A, lda, B, ldb, -1.5, C, ldc, 36)
     check_model(oracle_mod, "N", "T", m, n, k, 0.5, A, lda, B, ldb, -1.5, C, ldc, out, 36)
+
+
+@pytest.mark.parametrize("group_m", ["1", "3", "64"])
+def test_model_parity_pair_raster_groups(oracle_mod, monkeypatch, group_m):
+    # the raster group height only reorders the pairs' work: the same bits for any of them
+    monkeypatch.setenv("GBD_EMU_KERNEL", "pair")
+    monkeypatch.setenv("GBD_EMU_GROUP_M", group_m)
+    m, n, k = 1300, 1100, 300
+    A, lda, B, ldb, C, ldc = _problem("T", "N", m, n, k, "uniform", 91, pads=(2, 1, 4))
+    out, _ = run_mod("T", "N", m, n, k, 1.25, A, lda, B, ldb, 0.0, C, ldc, 40)
+    check_model(oracle_mod, "T", "N", m, n, k, 1.25, A, lda, B, ldb, 0.0, C, ldc, out, 40)
 
 
 def test_integer_inputs_bit_exact(oracle_mod):
@@ -204,7 +213,7 @@ def test_deterministic():
 def test_kernel_launches_per_call(m, n, k):
     # one call with the bits chosen on the device launches the kernels that the benchmark's
     # launch count claims (preparation, certification, plans, residues, column scales, products,
-    # reconstruction), plus one when the last two-SM wave runs on one-SM CTAs
+    # reconstruction)
     import torch
     from torch.profiler import ProfilerActivity, profile
 
@@ -231,8 +240,7 @@ def test_kernel_launches_per_call(m, n, k):
     kernels = [x for x in names if "k_" in x and ("emu::" in x or "gbd::" in x)]
     if not names:
         pytest.skip("the profiler recorded no device activity here")
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert len(kernels) == bench.MOD_LAUNCHES + bench.mod_tail_launches(m, n, sms), kernels
+    assert len(kernels) == bench.MOD_LAUNCHES, kernels
     assert gbdgemm.gbd_check_device_error() == 0
 
 
