@@ -183,7 +183,7 @@ struct ModTableEntry {
   const ModPlan* plan;  // the problem's t, n and feasibility
   uint8_t* park;        // the problem's parked residues (layout of ModArgs::park)
   int64_t tile_begin;   // first tile of this problem in the launch
-  int nkb, tiles_m, group_m, num_tiles;
+  int nkb, tiles_m, group_m, num_tiles;  // tiles of 128 x 128, or 256 x 256 in the two-SM launch
   int park_mods, nbn;   // moduli per block of the park array; 128-column blocks of C
 };
 // The reconstruction of one product from its parked residues: every 128 x 128 block of C (in a
@@ -457,9 +457,11 @@ struct ModGrouped {
   std::vector<CertTableEntry> cert;        // FP8 certification, then its BF16 retry (count each)
   std::vector<ModPlanJob> planjobs;
   std::vector<ColJob> coljobs;
-  std::vector<ModTableEntry> table;        // in launch order (decreasing k)
+  // in launch order: the pair_count problems of the two-SM launch (pair_tiles tiles of 256 x 256),
+  // then those of the one-SM launch (mod_tiles tiles of 128 x 128), each part by decreasing k
+  std::vector<ModTableEntry> table;
   int64_t exp_blocks = 0, split_blocks = 0;
-  int cert_tiles = 0, mod_tiles = 0;
+  int cert_tiles = 0, mod_tiles = 0, pair_tiles = 0, pair_count = 0;
   // device memory in the grouped workspace
   PrepJob* jobs_dev = nullptr;
   CertTableEntry* cert_dev = nullptr;
@@ -468,7 +470,7 @@ struct ModGrouped {
   ModTableEntry* table_dev = nullptr;
   unsigned int* words_dev = nullptr;       // kCertWords per problem
   // [0]: some problem's first plan found no feasible t (the BF16 retry runs); [1]: some problem's
-  // final plan did (its FP64 fallback tiles run)
+  // final plan did (its FP64 fallback tiles run); [2]: the largest moduli count of a feasible plan
   unsigned int* flags_dev = nullptr;
   std::vector<CrtJob> crt;                 // the reconstructions, in the product table's order
   CrtJob* crt_dev = nullptr;

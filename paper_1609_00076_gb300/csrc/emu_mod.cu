@@ -181,6 +181,41 @@ __device__ __forceinline__ int mod_nonneg(int v, uint32_t p, uint32_t b) {
   return (int)mod_barrett((uint32_t)v + (p << 23), p, b);
 }
 
+// A grouped launch's table as the product kernels look units up in it: per entry its first tile,
+// k-blocks, tile rows and tiles, and its plan's moduli count (0 for an infeasible plan).  Each CTA
+// copies it into shared memory at its start when it fits (kTabCache entries), so that finding a
+// unit's problem costs shared-memory reads instead of a chain of dependent global loads (table
+// entry, plan); larger tables are read in global memory.
+struct TabInfo {
+  int tile_begin, nkb, tiles_m, group_m, num_tiles, nmod;
+};
+constexpr int kTabCache = 1024;
+struct TabView {
+  const ModTableEntry* table;
+  const TabInfo* tab;  // the shared-memory copy, or null
+  int count;
+  __device__ __forceinline__ int begin(int i) const { return tab ? tab[i].tile_begin : (int)table[i].tile_begin; }
+  __device__ __forceinline__ TabInfo info(int i) const {
+    if (tab) return tab[i];
+    const ModTableEntry& e = table[i];
+    const ModPlan* pl = e.plan;
+    return TabInfo{(int)e.tile_begin, e.nkb, e.tiles_m, e.group_m, e.num_tiles, pl->feasible ? pl->n : 0};
+  }
+  // the entry of `tile`, from entry cur on (the tiles a walk asks for increase)
+  __device__ __forceinline__ int find(int tile, int cur) const {
+    while (cur + 1 < count && begin(cur + 1) <= tile) ++cur;
+    return cur;
+  }
+};
+// the copy (every thread of the CTA takes part; a __syncthreads() must follow before its use)
+__device__ __forceinline__ void tab_fill(TabInfo* tab, const ModTableEntry* table, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const ModTableEntry& e = table[i];
+    const ModPlan* pl = e.plan;
+    tab[i] = TabInfo{(int)e.tile_begin, e.nkb, e.tiles_m, e.group_m, e.num_tiles, pl->feasible ? pl->n : 0};
+  }
+}
+
 // The epilogue of the product kernels.  Each thread owns one TMEM lane (a row of the CTA's 128)
 // and COLS columns of the TBN-wide tile.  Per modulus: drain the 1024-deep chunks into int32
 // sums (reduced modulo p_l every kReduceChunks chunks), reduce modulo p_l and park the residues,
@@ -193,7 +228,8 @@ template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE, bool SPLIT>
 __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tmem_base, uint64_t* acc_full,
                                          uint64_t* acc_empty, int warp, int lane, int unit0, int unit_step,
                                          int units, int row_off, const ModTableEntry* table = nullptr,
-                                         int count = 0) {
+                                         int count = 0, const TabInfo* tab = nullptr) {
+  const TabView tv{table, tab, count};
   constexpr int COLS = TBN / (EPI_WARPS / 4);
   constexpr int kGroups = COLS / 4;
   static_assert(COLS % 4 == 0 && 128 % COLS == 0, "a thread's columns lie in one 128-column block");
@@ -211,7 +247,8 @@ __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tm
   const int groups = SPLIT ? min(p.groups, nmod) : 1;
   uint32_t chunk = 0;
   int acc[COLS];
-  int cur = 0;  // grouped: the table entry of the current tile (a CTA's tiles increase)
+  int cur = 0;      // grouped: the table entry of the current tile (a CTA's tiles increase)
+  int cur_l = -1;   // grouped pairs: the modulus of the current sweep (the tiles restart with it)
   for (int u = unit0; u < units; u += unit_step) {
     const int tile = SPLIT ? u / groups : PAIR ? u % p.num_tiles : u;
     int l0 = 0, l1 = nmod, nkb = p.nkb, tm, tn;
@@ -224,13 +261,21 @@ __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tm
       l1 = l0 + 1;
     }
     if (TABLE) {
-      while (cur + 1 < count && table[cur + 1].tile_begin <= tile) ++cur;
+      if (PAIR && l0 != cur_l) {
+        cur = 0;
+        cur_l = l0;
+      }
+      cur = tv.find(tile, cur);
+      const TabInfo ti = tv.info(cur);
+      if (ti.nmod == 0) continue;  // an infeasible plan: computed by the FP64 kernel instead
+      if (PAIR) {
+        if (l0 >= ti.nmod) continue;  // this problem has fewer moduli than the launch's largest
+      } else {
+        l1 = ti.nmod;
+      }
+      nkb = ti.nkb;
+      tile_coords(tile - ti.tile_begin, ti.tiles_m, ti.group_m, ti.num_tiles, tm, tn);
       const ModTableEntry& e = table[cur];
-      const ModPlan* pl = e.plan;
-      if (!pl->feasible) continue;  // computed by the FP64 kernel instead
-      l1 = pl->n;
-      nkb = e.nkb;
-      tile_coords(tile - (int)e.tile_begin, e.tiles_m, e.group_m, e.num_tiles, tm, tn);
       park = e.park;
       pmods = e.park_mods;
       nbn = e.nbn;
@@ -302,7 +347,8 @@ struct Smem {
   static constexpr int kOffBar = kOffB + kStages * kBBytes;
   static constexpr int kNumBars = 2 * kStages + 5;
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
-  static constexpr int kBytes = kOffTmemSlot + 16;
+  static constexpr int kOffTab = kOffTmemSlot + 16;  // grouped launches: the table's copy
+  static constexpr int kBytes = kOffTab + kTabCache * (int)sizeof(TabInfo);
   static constexpr int kAlloc = kBytes + 1024;
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
@@ -348,6 +394,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  TabInfo* const tab_s = reinterpret_cast<TabInfo*>(smem + L::kOffTab);
+  const bool tab_cached = TABLE && count <= kTabCache;
+  if (tab_cached) tab_fill(tab_s, table, count);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -358,16 +407,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int groups = SPLIT ? min(p.groups, nmod) : 1;
   const int units = p.num_tiles * groups;
   // grouped: the moduli count and k-blocks of unit u's problem (0 moduli: skipped), its maps
+  const TabView tv{table, tab_cached ? tab_s : nullptr, count};
   auto table_unit = [&](int u, int& cur, int& tm, int& tn, int& nm, int& nkb, const CUtensorMap*& ma,
                         const CUtensorMap*& mb) {
-    while (cur + 1 < count && table[cur + 1].tile_begin <= u) ++cur;
-    const ModTableEntry& e = table[cur];
-    const ModPlan* pl = e.plan;
-    nm = pl->feasible ? pl->n : 0;
-    nkb = e.nkb;
-    tile_coords(u - (int)e.tile_begin, e.tiles_m, e.group_m, e.num_tiles, tm, tn);
-    ma = &e.tmA;
-    mb = &e.tmB;
+    cur = tv.find(u, cur);
+    const TabInfo ti = tv.info(cur);
+    nm = ti.nmod;
+    nkb = ti.nkb;
+    tile_coords(u - ti.tile_begin, ti.tiles_m, ti.group_m, ti.num_tiles, tm, tn);
+    ma = &table[cur].tmA;
+    mb = &table[cur].tmB;
   };
 
   if (warp == 0) {
@@ -447,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     mod_park<kEpiWarps, kBN, false, TABLE, SPLIT>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, blockIdx.x,
-                                                  gridDim.x, units, 0, table, count);
+                                                  gridDim.x, units, 0, table, count, tab_cached ? tab_s : nullptr);
   }
 
   tc_fence_before();
@@ -478,14 +527,20 @@ struct Smem2 {
   static constexpr int kOffBar = kOffB + k2Stages * kBBytes;
   static constexpr int kNumBars = 2 * k2Stages + 5;
   static constexpr int kOffTmemSlot = kOffBar + kNumBars * 8;
-  static constexpr int kBytes = kOffTmemSlot + 16;
+  static constexpr int kOffTab = kOffTmemSlot + 16;  // grouped launches: the table's copy
+  static constexpr int kBytes = kOffTab + kTabCache * (int)sizeof(TabInfo);
   static constexpr int kAlloc = kBytes + 1024;
   static_assert(kAlloc <= 227 * 1024, "shared memory of one CTA");
 };
 
+// TABLE: the tiles of several problems (a grouped launch, `count` table entries whose tiles are
+// numbered in order, 256 x 256 each), their moduli swept together up to the largest count of any
+// plan (*nmax); a unit beyond its own problem's count, or of an infeasible plan, is skipped.
+template <bool TABLE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     k_mod_gemm_pair(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
-                    const __grid_constant__ CUtensorMap tmB) {
+                    const __grid_constant__ CUtensorMap tmB, const ModTableEntry* __restrict__ table = nullptr,
+                    int count = 0, const unsigned int* __restrict__ nmax = nullptr) {
   using L = Smem2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -502,8 +557,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
   const int num_pairs = gridDim.x / 2, pair_id = blockIdx.x / 2;
 
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+    if (!TABLE) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+    }
     for (int i = 0; i < k2Stages; ++i) {
       mbar_init(&full[i], 1);   // the leader's producer arrives (with both CTAs' bytes)
       mbar_init(&empty[i], 1);  // one commit per phase, multicast to both CTAs
@@ -521,34 +578,67 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
+  TabInfo* const tab_s = reinterpret_cast<TabInfo*>(smem + L::kOffTab);
+  const bool tab_cached = TABLE && count <= kTabCache;
+  if (tab_cached) tab_fill(tab_s, table, count);
   tc_fence_before();
   __syncthreads();
   cluster_sync_all();  // the peer's barriers are initialised and its TMEM is allocated
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const ModPlan plan = *p.plan;  // written by k_mod_plan earlier on the stream
-  const int nmod = plan.n;
+  // single product: the call's plan; grouped: the largest moduli count of the problems' plans
+  // (written by the plan kernels earlier on the stream; 0 when no plan is feasible)
+  const int nmod = TABLE ? (int)*nmax : p.plan->n;
   // work units (tile, modulus), modulus-major: the pairs sweep the tiles of one modulus's planes
   // together, so a band of them stays in L2, and every pair has work down to the last wave
   const int units = p.num_tiles * nmod;
+  // grouped: unit u's problem (table cursor `cur`, restarted with each modulus `cur_l`), its tile
+  // coordinates, k-blocks and residue maps; false when the unit is skipped
+  const TabView tv{table, tab_cached ? tab_s : nullptr, count};
+  auto table_unit = [&](int u, int& cur, int& cur_l, int& tm, int& tn, int& nkb, const CUtensorMap*& ma,
+                        const CUtensorMap*& mb) {
+    const int tile = u % p.num_tiles, l = u / p.num_tiles;
+    if (l != cur_l) {
+      cur = 0;
+      cur_l = l;
+    }
+    cur = tv.find(tile, cur);
+    const TabInfo ti = tv.info(cur);
+    if (l >= ti.nmod) return false;  // an infeasible plan (no moduli), or fewer moduli than l + 1
+    nkb = ti.nkb;
+    tile_coords(tile - ti.tile_begin, ti.tiles_m, ti.group_m, ti.num_tiles, tm, tn);
+    ma = &table[cur].tmA;
+    mb = &table[cur].tmB;
+    return true;
+  };
 
   if (warp == 0) {
     // ------------------------------ TMA producer (both CTAs) ------------------------------
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       const uint32_t pair_bytes = (uint32_t)(2 * (L::kABytes + L::kBBytes));
+      int cur = 0, cur_l = -1;
       for (int u = pair_id; u < units; u += num_pairs) {
-        const int tile = u % p.num_tiles, l = u / p.num_tiles;
-        int tm, tn;
-        raster_coords(p.tri, tile, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        const int l = u / p.num_tiles;
+        int tm, tn, nkb = p.nkb;
+        const CUtensorMap* ma = &tmA;
+        const CUtensorMap* mb = &tmB;
+        if (TABLE) {
+          if (!table_unit(u, cur, cur_l, tm, tn, nkb, ma, mb)) continue;
+          // maps written into global memory before the launch: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb) : "memory");
+        } else {
+          raster_coords(p.tri, u % p.num_tiles, p.tiles_m, p.group_m, p.num_tiles, tm, tn);
+        }
         const int m0 = tm * k2BM + (int)rank * 128;
         const int nb0 = tn * k2BN + (int)rank * 128;
-        for (int kb = 0; kb < p.nkb; ++kb) {
+        for (int kb = 0; kb < nkb; ++kb) {
           mbar_wait_cluster(&empty[stage], phase ^ 1u, p.err, kErrWaitSlot);
           if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
           const uint32_t fbar = map_to_rank(smem_u32(&full[stage]), 0);
-          tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, &tmA, fbar, kb * kBK, m0, l);
-          tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, &tmB, fbar, kb * kBK, nb0, l);
+          tma_load_3d_pair(smem + L::kOffA + stage * L::kABytes, ma, fbar, kb * kBK, m0, l);
+          tma_load_3d_pair(smem + L::kOffB + stage * L::kBBytes, mb, fbar, kb * kBK, nb0, l);
           if (++stage == k2Stages) { stage = 0; phase ^= 1u; }
         }
       }
@@ -560,13 +650,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
       constexpr uint32_t idesc = idesc_bf16(k2BM, k2BN);
       uint32_t stage = 0, phase = 0, chunk = 0;
       const uint32_t a_base = smem_u32(smem + L::kOffA), b_base = smem_u32(smem + L::kOffB);
-      for (int u = pair_id; u < units; u += num_pairs)
-        for (int i0 = 0; i0 < p.nkb; i0 += kChunkBlocks, ++chunk) {
+      int cur = 0, cur_l = -1;
+      for (int u = pair_id; u < units; u += num_pairs) {
+        int nkb = p.nkb;
+        if (TABLE) {
+          int tm, tn;
+          const CUtensorMap *ma, *mb;
+          if (!table_unit(u, cur, cur_l, tm, tn, nkb, ma, mb)) continue;
+        }
+        for (int i0 = 0; i0 < nkb; i0 += kChunkBlocks, ++chunk) {
           const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
           mbar_wait_cluster(&acc_empty[buf], cph ^ 1u, p.err, kErrWaitEpi);
           tc_fence_after();
           const uint32_t dtm = tmem_base + buf * k2BN;
-          const int i1 = min(p.nkb, i0 + kChunkBlocks);
+          const int i1 = min(nkb, i0 + kChunkBlocks);
           for (int it = i0; it < i1; ++it) {
             mbar_wait_cluster(&full[stage], phase, p.err, kErrWaitTma);
             tc_fence_after();
@@ -580,6 +677,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
           }
           umma_commit_pair(&acc_full[buf]);  // chunk complete in both CTAs' TMEM
         }
+      }
       if (chunk > 0) {  // a pair without a unit issued nothing and has nothing to wait for
         umma_commit_pair(done);
         mbar_wait_cluster(done, 0, p.err, kErrWaitMma);
@@ -587,8 +685,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     __syncwarp();
   } else {
-    mod_park<k2EpiWarps, k2BN, true, false, false>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
-                                                   num_pairs, units, (int)rank * 128);
+    mod_park<k2EpiWarps, k2BN, true, TABLE, false>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
+                                                   num_pairs, units, (int)rank * 128, table, count,
+                                                   tab_cached ? tab_s : nullptr);
   }
 
   tc_fence_before();
@@ -1002,6 +1101,8 @@ __global__ void __launch_bounds__(128) k_mod_plan_batched(const ModPlanJob* __re
   if (!n) {
     if (!retry) atomicOr(flags, 1u);
     if (final_pass) atomicOr(flags + 1, 1u);
+  } else {
+    atomicMax(flags + 2, (unsigned int)n);  // the largest moduli count, for the two-SM products
   }
 }
 
@@ -1242,9 +1343,9 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, int bits, ModA
     const char* gm_env = getenv("GBD_EMU_GROUP_M");
     const int gm_set = gm_env ? atoi(gm_env) : 0;
     a.group_m = gm_set > 0 ? (gm_set < a.tiles_m ? gm_set : a.tiles_m) : group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
-    e = cudaFuncSetAttribute(k_mod_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
+    e = cudaFuncSetAttribute(k_mod_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm pair)");
-    k_mod_gemm_pair<<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
+    k_mod_gemm_pair<false><<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
   } else {
     const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);
@@ -1454,6 +1555,15 @@ int dgemm_emu_mod_impl(char transa, char transb, int64_t m, int64_t n, int64_t k
 // ---- grouped modular problems ----
 namespace {
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// GBD_EMU_KERNEL=single keeps every grouped modular problem on the one-SM kernel (tests and tuning)
+bool mod_grouped_pairs_enabled() {
+  const char* force = getenv("GBD_EMU_KERNEL");
+  return !(force && strcmp(force, "single") == 0);
+}
+// A problem whose products run on CTA pairs: at least 256 on every side, so that a 256 x 256 tile
+// pads little, and a k that keeps the tensor pipe busy while the epilogue drains a unit
+bool mod_grouped_pair_problem(const gbd_problem& p) { return p.m >= 256 && p.n >= 256 && p.k >= 256; }
 }  // namespace
 
 size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count, void* base, ModGrouped* g, int* rc) {
@@ -1547,17 +1657,26 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     g->plans[q] = w.plan;
   }
   g->cert_tiles = (int)cert_tiles;
-  // the product table: the deepest problems' tiles first (longest tiles first over the SMs)
+  // the product table: first the problems for the two-SM kernel, then those for the one-SM
+  // kernel, each part with the deepest problems' tiles first (longest tiles first over the SMs)
   std::vector<int> order(count);
   for (int q = 0; q < count; ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return probs[which[x]].k > probs[which[y]].k; });
+  const bool pairs_on = mod_grouped_pairs_enabled();
+  auto on_pair = [&](int q) { return pairs_on && mod_grouped_pair_problem(probs[which[q]]); };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const bool px = on_pair(x), py = on_pair(y);
+    if (px != py) return px;
+    return probs[which[x]].k > probs[which[y]].k;
+  });
   g->table.assign(count, ModTableEntry{});
   g->crt.assign(count, CrtJob{});
-  int64_t mt = 0, blocks = 0;
+  g->pair_count = 0;
+  int64_t mt = 0, pt = 0, blocks = 0;
   for (int r = 0; r < count; ++r) {
     const int q = order[r];
     const gbd_problem& p = probs[which[q]];
+    const bool pair = on_pair(q);
+    if (pair) g->pair_count = r + 1;
     const ModWorkspace& w = ws[q];
     ModTableEntry& e = g->table[r];
     const uint64_t dA[3] = {(uint64_t)p.k, (uint64_t)p.m, (uint64_t)nmod_ws[q]};
@@ -1577,11 +1696,13 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     e.park_mods = w.park_mods;
     e.nbn = w.nbn;
     e.nkb = (int)((p.k + kBK - 1) / kBK);
-    e.tiles_m = (int)((p.m + kBM - 1) / kBM);
-    e.num_tiles = e.tiles_m * (int)((p.n + kBN - 1) / kBN);
+    const int tbm = pair ? k2BM : kBM, tbn = pair ? k2BN : kBN;  // the maps' boxes (128 rows) serve both
+    e.tiles_m = (int)((p.m + tbm - 1) / tbm);
+    e.num_tiles = e.tiles_m * (int)((p.n + tbn - 1) / tbn);
     e.group_m = e.tiles_m;  // within one problem the tiles walk down the rows
-    e.tile_begin = mt;
-    mt += e.num_tiles;
+    int64_t& tiles = pair ? pt : mt;
+    e.tile_begin = tiles;
+    tiles += e.num_tiles;
     CrtJob& cj = g->crt[r];
     cj.park = w.park;
     cj.plan = w.plan;
@@ -1602,8 +1723,10 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
     blocks += (int64_t)w.nbm * w.nbn;
   }
   g->mod_tiles = (int)mt;
+  g->pair_tiles = (int)pt;
   g->crt_blocks = blocks;
-  if (mt > ((int64_t)1 << 30) || cert_tiles > ((int64_t)1 << 30)) *rc = set_error(GBD_ERR_LIMIT, "grouped: too many tiles");
+  if (mt > ((int64_t)1 << 30) || pt * kMaxModuli >= ((int64_t)1 << 31) || cert_tiles > ((int64_t)1 << 30))
+    *rc = set_error(GBD_ERR_LIMIT, "grouped: too many tiles");
   return off;
 }
 
@@ -1644,23 +1767,36 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
   if ((rc = launch_residue_batched(g.jobs_dev, g.jobs.data(), njobs, ms, g.split_blocks, s))) return rc;
   k_mod_colscale_batched<<<g.count, 256, 0, s>>>(g.coljobs_dev);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped column scale launch");
-  // the products of every feasible problem in one persistent launch
-  if (g.mod_tiles <= 0) return GBD_OK;
+  // the products of every feasible problem: the large problems' (256 x 256 tile, modulus) units
+  // on CTA pairs, then the other problems' tiles on single SMs, each a persistent launch
   ModArgs a;
   mod_constants(a);
   a.plan = g.plans[0];  // read at kernel start; the tiles use their own problems' plans
   a.err = device_error_word();
-  a.num_tiles = g.mod_tiles;
   a.tiles_m = 1;
   a.group_m = 1;
   a.nkb = 1;
   a.groups = 1;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
+  if (g.pair_tiles > 0) {
+    a.num_tiles = g.pair_tiles;
+    const int64_t pairs_avail = sms / 2 > 0 ? sms / 2 : 1;
+    const int64_t units = (int64_t)g.pair_tiles * kMaxModuli;  // at most; the plans' largest count bounds them
+    const int64_t pairs = units < pairs_avail ? units : pairs_avail;
+    e = cudaFuncSetAttribute(k_mod_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped modular gemm pair)");
+    k_mod_gemm_pair<true><<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, s>>>(a, dummy, dummy, g.table_dev,
+                                                                                  g.pair_count, g.flags_dev + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped modular gemm pair launch");
+  }
+  if (g.mod_tiles <= 0) return GBD_OK;
+  a.num_tiles = g.mod_tiles;
   const int grid = g.mod_tiles < sms ? g.mod_tiles : sms;
   e = cudaFuncSetAttribute(k_mod_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem::kAlloc);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped modular gemm)");
-  k_mod_gemm<false, true><<<grid, kThreads, Smem::kAlloc, s>>>(a, dummy, dummy, g.table_dev, g.count);
+  k_mod_gemm<false, true><<<grid, kThreads, Smem::kAlloc, s>>>(a, dummy, dummy, g.table_dev + g.pair_count,
+                                                               g.count - g.pair_count);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped modular gemm launch");
   // the reconstruction of every feasible problem
   CrtJob none;

@@ -90,6 +90,38 @@ def test_modular_batch_matches_single_calls(oracle_mod):
         assert first_mismatch(got, ref, 2 * k * U * G, m) is None
 
 
+@pytest.mark.parametrize("kernel", ["default", "single"])
+def test_large_problems_on_cta_pairs_match_single_calls(oracle_mod, monkeypatch, kernel):
+    # problems with m, n, k >= 256 run their (256 x 256 tile, modulus) units on CTA pairs, the
+    # others on single SMs (GBD_EMU_KERNEL=single: all on single SMs); ragged sizes, a problem with
+    # fixed bits (fewer moduli than the launch's largest count: its later units are skipped), one
+    # with a target no bit count certifies (its units are skipped, its FP64 fallback runs) and a
+    # quick return among them
+    if kernel == "single":
+        monkeypatch.setenv("GBD_EMU_KERNEL", "single")
+    probs = make_batch(61, 16, 160, 1400, modes=("mod",), slices=(0,), kinds=("uniform", "scaled"),
+                       alpha_beta=(1.5, -0.5))
+    big = [i for i, p in enumerate(probs) if min(p["m"], p["n"], p["k"]) >= 256]
+    assert len(big) >= 4 and len(big) < len(probs)
+    probs[big[0]]["slices"] = 20  # fixed bits: few moduli
+    _structured(probs[big[1]])    # no certified bit count: the FP64 fallback
+    probs[big[2]]["alpha"] = 0.0  # a quick return: C := beta C
+    to_device(probs)
+    outs, used = run_grouped(probs)
+    for i, (p, out) in enumerate(zip(probs, outs)):
+        want = _native_of(p) if i == big[1] else run_single(p)
+        assert bits_equal(out, want), (i, p["m"], p["n"], p["k"], p["slices"])
+    for i in big[3:5]:
+        p, out = probs[i], outs[i]
+        m, n, k = p["m"], p["n"], p["k"]
+        ref = oracle_mod.dgemm_rows(p["ta"], p["tb"], m, n, k, p["alpha"], p["A"], p["lda"], p["B"], p["ldb"],
+                                    p["beta"], p["C"], p["ldc"], rows=list(range(8)))
+        G = oracle_mod.abs_bound_rows(p["ta"], p["tb"], m, n, k, p["alpha"], p["A"], p["lda"], p["B"], p["ldb"],
+                                      p["beta"], p["C"], p["ldc"], rows=list(range(8)))
+        got = synth.view(out, m, n, p["ldc"])[:8].flatten(order="F")
+        assert first_mismatch(got, ref, 2 * k * U * G, 8) is None
+
+
 def _structured(p, d=30):
     """Make problem p's operands the half-scaled structure (op(A)'s second half of k, op(B)'s first)."""
     k = p["k"]
