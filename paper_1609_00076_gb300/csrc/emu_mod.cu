@@ -309,9 +309,14 @@ __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tm
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
         }
+        // the warp's TMEM loads are complete (waited on) and fenced: one arrive per warp frees the
+        // buffer (a release-ordered remote arrive per thread stalled the epilogue on its fences)
         tc_fence_before();
-        if (PAIR) mbar_arrive_remote(empty_remote[buf]);
-        else mbar_arrive(&acc_empty[buf]);
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR) mbar_arrive_remote(empty_remote[buf]);
+          else mbar_arrive(&acc_empty[buf]);
+        }
         if (++nch == kReduceChunks) {  // keep the running sums below 2^30 in magnitude
           nch = 0;
 #pragma unroll
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 32 * kEpiWarps);
+      mbar_init(&acc_empty[i], kEpiWarps);  // one arrive per epilogue warp
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -567,7 +572,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 2 * 32 * k2EpiWarps);  // every epilogue thread of both CTAs
+      mbar_init(&acc_empty[i], 2 * k2EpiWarps);  // one arrive per epilogue warp of both CTAs
     }
     mbar_init(done, 1);
     fence_mbar_init();
