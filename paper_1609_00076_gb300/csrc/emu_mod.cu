@@ -742,27 +742,21 @@ __device__ __forceinline__ void limbs_sub(uint32_t (&x)[L], const uint32_t (&y)[
   }
 }
 
-// fl(C') for the residues r_l = byte q of w[l]: the sign, the unbiased exponent E of the rounded
-// value and its 53-bit significand with the implicit bit (mant in [2^52, 2^53], 2^53 when the
-// rounding carried), or zero.  X = sum_l r_l V_l modulo 2^(32 L) from the byte sums
-// S_d = sum_l r_l (byte d of V_l) < 2^20 (four moduli per dp4a), as
+// fl(C') for the residues T (four moduli per word, modulus 4G + b in byte b of T[G]): the sign,
+// the unbiased exponent E of the rounded value and its 53-bit significand with the implicit bit
+// (mant in [2^52, 2^53], 2^53 when the rounding carried), or zero.  X = sum_l r_l V_l modulo
+// 2^(32 L) from the byte sums S_d = sum_l r_l (byte d of V_l) < 2^20 (four moduli per dp4a), as
 // X = sum_k 2^(32 k) (A_k + 2^16 B_k), A_k = S_4k + 2^8 S_4k+1, B_k = S_4k+2 + 2^8 S_4k+3 (each
-// below 2^29).  Qe = floor(sum_l r_l e_l / 2^16 + 1/2) is round(X / M) or one more, and one more
-// only when X - Qe M <= -M/2: then M is added back.  The result lies in (-M/2, M/2].
+// below 2^29): limb k is A_k + (B_k << 16 mod 2^32) + (B_k-1 >> 16) plus the carry of limb k - 1,
+// the first two terms summed with carries (the third keeps A_k below 2^30).  Qe = floor(sum_l
+// r_l e_l / 2^16 + 1/2) is round(X / M) or one more, and one more only when X - Qe M <= -M/2:
+// then M is added back.  The result lies in (-M/2, M/2].
 template <int N>
-__device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[kMaxModuli], int q, uint32_t& sign,
-                                          int& E, uint64_t& mant) {
+__device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&T)[(N + 3) / 4], uint32_t& sign, int& E,
+                                          uint64_t& mant) {
   constexpr int L = N <= 12 ? 3 : 4;
   constexpr int NG = (N + 3) / 4;
-  // this column's residues, four moduli per word
-  uint32_t T[NG];
-  const uint32_t sel = 0x4400u | ((4u + (uint32_t)q) << 4) | (uint32_t)q;  // bytes q of x and of y
-#pragma unroll
-  for (int G = 0; G < NG; ++G)
-    T[G] = __byte_perm(__byte_perm(w[4 * G], w[4 * G + 1], sel), __byte_perm(w[4 * G + 2], w[4 * G + 3], sel),
-                       0x5410u);
-  uint32_t x[L];
-  uint64_t t = 0;
+  uint32_t a[L], lo[L], bprev = 0u;
 #pragma unroll
   for (int k = 0; k < L; ++k) {
     uint32_t s1 = 0u, s3 = 0u;
@@ -777,9 +771,14 @@ __device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[k
       A = __dp4a(T[G], S.wp[G][4 * k], A);
       B = __dp4a(T[G], S.wp[G][4 * k + 2], B);
     }
-    t = (t >> 32) + A + ((uint64_t)B << 16);  // below 2^46
-    x[k] = (uint32_t)t;
+    a[k] = A + (bprev >> 16);
+    lo[k] = B << 16;
+    bprev = B;
   }
+  uint32_t x[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) x[k] = a[k];
+  limbs_add<L>(x, lo);
   uint32_t qh = 0u;
 #pragma unroll
   for (int G = 0; G < NG; ++G) qh = __dp4a(T[G], S.ep[G][1], qh);
@@ -789,7 +788,7 @@ __device__ __forceinline__ bool crt_round(const CrtSet& S, const uint32_t (&w)[k
   // X - Qe M
   const uint32_t Q = qe >> 16;
   uint32_t qm[L];
-  t = (uint64_t)Q * S.M[0];
+  uint64_t t = (uint64_t)Q * S.M[0];
   qm[0] = (uint32_t)t;
 #pragma unroll
   for (int j = 1; j < L; ++j) {
@@ -868,13 +867,28 @@ __device__ __forceinline__ void crt_rows(const CrtJob& job, bool nan_out, int rb
   for (int g = threadIdx.x >> 7; g < 32; g += kCrtThreads / 128) {
     const int64_t j0 = (int64_t)cb * 128 + 4 * g;
     if (j0 >= n) break;
-    uint32_t w[kMaxModuli];
+    constexpr int NG = (N + 3) / 4;
+    uint32_t w[4 * NG];
 #pragma unroll
     for (int l = 0; l < N; ++l)
       w[l] = __ldcs(reinterpret_cast<const unsigned int*>(pb + (int64_t)l * kParkBlock + g * 512));
 #pragma unroll
-    for (int l = N; l < kMaxModuli; ++l) w[l] = 0u;
-#pragma unroll 1
+    for (int l = N; l < 4 * NG; ++l) w[l] = 0u;
+    // word l holds column 4g + q's residue modulo p_l in byte q: a 4 x 4 byte transpose per group
+    // of four moduli gives each column its residues, four moduli per word (byte b: modulus 4G + b)
+    uint32_t T[4][NG];
+#pragma unroll
+    for (int G = 0; G < NG; ++G) {
+      const uint32_t t01 = __byte_perm(w[4 * G], w[4 * G + 1], 0x5140u);      // bytes 0, 1 of both
+      const uint32_t t23 = __byte_perm(w[4 * G + 2], w[4 * G + 3], 0x5140u);
+      const uint32_t u01 = __byte_perm(w[4 * G], w[4 * G + 1], 0x7362u);      // bytes 2, 3 of both
+      const uint32_t u23 = __byte_perm(w[4 * G + 2], w[4 * G + 3], 0x7362u);
+      T[0][G] = __byte_perm(t01, t23, 0x5410u);
+      T[1][G] = __byte_perm(t01, t23, 0x7632u);
+      T[2][G] = __byte_perm(u01, u23, 0x5410u);
+      T[3][G] = __byte_perm(u01, u23, 0x7632u);
+    }
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t jj = j0 + q;
       const bool in = jj < n && (tri == 0 || (tri == 1 ? jj <= i : jj >= i));
@@ -889,7 +903,7 @@ __device__ __forceinline__ void crt_rows(const CrtJob& job, bool nan_out, int rb
       uint32_t sign;
       int E;
       uint64_t mant;
-      const bool nz = crt_round<N>(S, w, q, sign, E, mant);
+      const bool nz = crt_round<N>(S, T[q], sign, E, mant);
       // y = fl(C') 2^sigma_i: its bits while it is a normal number (the rounding's carry moves
       // into the exponent field)
       const int ey = E + sig + 1023;  // biased exponent before the carry
