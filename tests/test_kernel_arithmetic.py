@@ -11,8 +11,10 @@
    residues r_l = C' mod p_l in [0, p_l): X = sum_l r_l (c_l W_l) is congruent to C' modulo M,
    the quotient estimate Qe = floor(sum_l r_l ceil(c_l 2^16/p_l) / 2^16 + 1/2) is the quotient of
    the symmetric representative or one more (and then X - Qe M <= -M/2), and X - Qe M is formed
-   modulo 2^96 (at most 12 moduli, M < 2^95) or 2^128 from 64-bit limb sums; the representative
-   of (-M/2, M/2] must come out for every C'.
+   modulo 2^96 (at most 12 moduli, M < 2^95) or 2^128 from byte dot products: S_d = sum_l r_l
+   (byte d of V_l) < 2^20, per 32-bit limb k A_k = S_4k + 2^8 S_4k+1 and B_k = S_4k+2 + 2^8 S_4k+3
+   (below 2^29), limb k = A_k + (B_k-1 >> 16) (below 2^30) plus (B_k << 16 mod 2^32) plus the
+   carry of limb k - 1 (at most one); the representative of (-M/2, M/2] must come out for every C'.
 3. Triangle tiles (DSYRK's triangular product).  Tile t of a triangle of T x T tiles is
    (r, c) with t = r (r + 1) / 2 + c, found from an FP32 square-root estimate corrected by
    integer steps; every tile that meets the triangle comes out exactly once.
@@ -73,18 +75,29 @@ def _crt_kernel(r, n, M, V, e):
     """The kernel's reconstruction, step by step in exact integers; returns C' modulo 2^(32 L)."""
     L = 3 if n <= 12 else 4
     mod = 2 ** (32 * L)
-    limbs = [0] * L
-    qe = 2 ** 15
-    for rl, Vl, el in zip(r, V, e):
-        for j in range(L):
-            limbs[j] += rl * ((Vl >> (32 * j)) & 0xFFFFFFFF)
-        qe += rl * el
-    assert max(limbs) < 2 ** 44 and qe < 2 ** 32  # the 64-bit limb sums and the 32-bit estimate
-    x = sum(a << (32 * j) for j, a in enumerate(limbs)) % mod
-    x = (x - (qe >> 16) * M) % mod
-    if ((x + M // 2 - 1) % mod) >> (32 * L - 1):  # X - Qe M <= -M/2: one too many
-        x = (x + M) % mod
-    return x, mod
+    S = [sum(rl * ((Vl >> (8 * d)) & 0xFF) for rl, Vl in zip(r, V)) for d in range(4 * L)]
+    assert max(S) < 2 ** 20  # the byte dot products of up to 16 moduli
+    x, carry, bprev = [], 0, 0
+    for k in range(L):
+        A = S[4 * k] + (S[4 * k + 1] << 8)
+        B = S[4 * k + 2] + (S[4 * k + 3] << 8)
+        assert A < 2 ** 29 and B < 2 ** 29
+        a = A + (bprev >> 16)
+        assert a < 2 ** 30
+        t = a + ((B << 16) & 0xFFFFFFFF) + carry  # add.cc / addc on 32-bit words
+        assert t < 2 ** 33
+        x.append(t & 0xFFFFFFFF)
+        carry, bprev = t >> 32, B
+        assert carry <= 1
+    X = sum(w << (32 * j) for j, w in enumerate(x))
+    assert X == sum(rl * Vl for rl, Vl in zip(r, V)) % mod
+    qh = sum(rl * (el >> 8) for rl, el in zip(r, e))
+    qe = (qh << 8) + 2 ** 15 + sum(rl * (el & 0xFF) for rl, el in zip(r, e))
+    assert max(e) < 2 ** 16 and qe < 2 ** 32  # the 32-bit estimate
+    xm = (X - (qe >> 16) * M) % mod
+    if ((xm + M // 2 - 1) % mod) >> (32 * L - 1):  # X - Qe M <= -M/2: one too many
+        xm = (xm + M) % mod
+    return xm, mod
 
 
 @pytest.mark.parametrize("n", range(1, 17))
