@@ -127,6 +127,7 @@ struct ModArgs {
             // upper one (m = n), by rows of tiles
   int p[kMaxModuli];         // moduli
   uint32_t bar[kMaxModuli];  // floor(2^32 / p_l), for Barrett reduction
+  float pinv[kMaxModuli];    // fl(1 / p_l) in FP32 (the reduction of a single exact FP32 chunk)
   const ModPlan* plan;       // the call's n (and whether the target was reachable)
   uint8_t* park;             // [blocks][park_mods][kParkBlock] the residues of the products
   int park_mods;             // moduli the park array holds per block
@@ -216,6 +217,16 @@ __device__ __forceinline__ void tab_fill(TabInfo* tab, const ModTableEntry* tabl
   }
 }
 
+// v mod p for an FP32 integer |v| <= 2^24 (one exact 1024-deep chunk), as the FP32 number
+// 2^23 + r whose low byte is r in [0, p): with inv = fl(1/p), |v inv - v/p| <= 2^24 2^-24 / p < 0.01,
+// so q = rint(v inv) (one fma against 1.5 2^23) is within 0.51 of v/p and r = v - p q (exact in
+// one fma) lies in (-0.51 p, 0.51 p); p is added when r is negative.
+__device__ __forceinline__ uint32_t mod_f32_byte(float v, float pf, float inv) {
+  const float q = fmaf(v, inv, 12582912.0f) - 12582912.0f;
+  const float r = fmaf(-pf, q, v);
+  return __float_as_uint(r + (r < 0.0f ? 8388608.0f + pf : 8388608.0f));
+}
+
 // The epilogue of the product kernels.  Each thread owns one TMEM lane (a row of the CTA's 128)
 // and COLS columns of the TBN-wide tile.  Per modulus: drain the 1024-deep chunks into int32
 // sums (reduced modulo p_l every kReduceChunks chunks), reduce modulo p_l and park the residues,
@@ -224,7 +235,9 @@ __device__ __forceinline__ void tab_fill(TabInfo* tab, const ModTableEntry* tabl
 // is modulus u / num_tiles of tile u % num_tiles); TABLE: the tiles belong to the problems of a
 // grouped launch (table entries in tile order), and a tile whose problem's plan is infeasible is
 // skipped (another kernel computes that problem).
-template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE, bool SPLIT>
+// ONE: a modulus of one chunk (k <= 1024) is reduced in FP32 never (0), always (1: the launch's k
+// is that small) or when its problem's k is (2)
+template <int EPI_WARPS, int TBN, bool PAIR, bool TABLE, bool SPLIT, int ONE = 2>
 __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tmem_base, uint64_t* acc_full,
                                          uint64_t* acc_empty, int warp, int lane, int unit0, int unit_step,
                                          int units, int row_off, const ModTableEntry* table = nullptr,
@@ -294,43 +307,83 @@ __device__ __forceinline__ void mod_park(const ModArgs& p, int nmod, uint32_t tm
                         row * 4;
     for (int l = l0; l < l1; ++l) {
       const uint32_t pmod = (uint32_t)p.p[l], bm = p.bar[l];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) acc[c] = 0;
-      int nch = 0;
-      for (int i0 = 0; i0 < nkb; i0 += kChunkBlocks, ++chunk) {
+      if (ONE == 1 || (ONE == 2 && nkb <= kChunkBlocks)) {
+        // one chunk: its exact FP32 sums reduced in FP32 and parked slice by slice, each 16-column
+        // TMEM load issued before the previous slice's arithmetic; the buffer is freed at the end
         const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+        ++chunk;
         mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
         tc_fence_after();
         const uint32_t taddr = trow + buf * TBN + col0;
+        const float pf = (float)pmod, inv = p.pinv[l];
+        unsigned int* const dst = reinterpret_cast<unsigned int*>(pb + (int64_t)l * kParkBlock);
+        uint32_t va[16], vb[16];
+        tmem_ld_16_issue(taddr, va);
 #pragma unroll
         for (int q = 0; q < COLS / 16; ++q) {
-          uint32_t v[16];
-          tmem_ld_16(taddr + q * 16, v);
+          uint32_t(&cur)[16] = (q & 1) ? vb : va;
+          uint32_t(&nxt)[16] = (q & 1) ? va : vb;
+          tmem_wait_ld_16(cur);
+          if (q + 1 < COLS / 16) tmem_ld_16_issue(taddr + (q + 1) * 16, nxt);
+          uint32_t b[16];
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
+          for (int jj = 0; jj < 16; ++jj) b[jj] = mod_f32_byte(__uint_as_float(cur[jj]), pf, inv);
+          if (inside) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const uint32_t lo = __byte_perm(b[4 * g], b[4 * g + 1], 0x0040u);
+              const uint32_t hi = __byte_perm(b[4 * g + 2], b[4 * g + 3], 0x0040u);
+              __stcs(dst + (4 * q + g) * 128, __byte_perm(lo, hi, 0x5410u));  // read once, by the reconstruction
+            }
+          }
         }
-        // the warp's TMEM loads are complete (waited on) and fenced: one arrive per warp frees the
-        // buffer (a release-ordered remote arrive per thread stalled the epilogue on its fences)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
           if (PAIR) mbar_arrive_remote(empty_remote[buf]);
           else mbar_arrive(&acc_empty[buf]);
         }
-        if (++nch == kReduceChunks) {  // keep the running sums below 2^30 in magnitude
-          nch = 0;
-#pragma unroll
-          for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pmod, bm);
-        }
+        continue;
       }
-      if (inside) {
-        unsigned int* const dst = reinterpret_cast<unsigned int*>(pb + (int64_t)l * kParkBlock);
+      if constexpr (ONE != 1) {  // int32 sums over the chunks, reduced modulo p_l every kReduceChunks
 #pragma unroll
-        for (int g = 0; g < kGroups; ++g) {
-          uint32_t w = 0u;
+        for (int c = 0; c < COLS; ++c) acc[c] = 0;
+        int nch = 0;
+        for (int i0 = 0; i0 < nkb; i0 += kChunkBlocks, ++chunk) {
+          const uint32_t buf = chunk & 1u, cph = (chunk >> 1) & 1u;
+          mbar_wait(&acc_full[buf], cph, p.err, kErrWaitMma);
+          tc_fence_after();
+          const uint32_t taddr = trow + buf * TBN + col0;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) w |= (uint32_t)mod_nonneg(acc[4 * g + b], pmod, bm) << (8 * b);
-          __stcs(dst + g * 128, w);  // read once, by the reconstruction
+          for (int q = 0; q < COLS / 16; ++q) {
+            uint32_t v[16];
+            tmem_ld_16(taddr + q * 16, v);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) acc[q * 16 + jj] += __float2int_rn(__uint_as_float(v[jj]));
+          }
+          // the warp's TMEM loads are complete (waited on) and fenced: one arrive per warp frees the
+          // buffer (a release-ordered remote arrive per thread stalled the epilogue on its fences)
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if (PAIR) mbar_arrive_remote(empty_remote[buf]);
+            else mbar_arrive(&acc_empty[buf]);
+          }
+          if (++nch == kReduceChunks) {  // keep the running sums below 2^30 in magnitude
+            nch = 0;
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) acc[c] = mod_nonneg(acc[c], pmod, bm);
+          }
+        }
+        if (inside) {
+          unsigned int* const dst = reinterpret_cast<unsigned int*>(pb + (int64_t)l * kParkBlock);
+#pragma unroll
+          for (int g = 0; g < kGroups; ++g) {
+            uint32_t w = 0u;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) w |= (uint32_t)mod_nonneg(acc[4 * g + b], pmod, bm) << (8 * b);
+            __stcs(dst + g * 128, w);  // read once, by the reconstruction
+          }
         }
       }
     }
@@ -541,7 +594,8 @@ struct Smem2 {
 // TABLE: the tiles of several problems (a grouped launch, `count` table entries whose tiles are
 // numbered in order, 256 x 256 each), their moduli swept together up to the largest count of any
 // plan (*nmax); a unit beyond its own problem's count, or of an infeasible plan, is skipped.
-template <bool TABLE>
+// ONE as for mod_park (single products: 1 when k <= 1024, else 0; grouped: 2)
+template <bool TABLE, int ONE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     k_mod_gemm_pair(const __grid_constant__ ModArgs p, const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB, const ModTableEntry* __restrict__ table = nullptr,
@@ -690,7 +744,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
     }
     __syncwarp();
   } else {
-    mod_park<k2EpiWarps, k2BN, true, TABLE, false>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
+    mod_park<k2EpiWarps, k2BN, true, TABLE, false, ONE>(p, nmod, tmem_base, acc_full, acc_empty, warp, lane, pair_id,
                                                    num_pairs, units, (int)rank * 128, table, count,
                                                    tab_cached ? tab_s : nullptr);
   }
@@ -1237,6 +1291,7 @@ void mod_constants(ModArgs& a) {
   for (int l = 0; l < kMaxModuli; ++l) {
     a.p[l] = kModuli[l];
     a.bar[l] = (uint32_t)((1ull << 32) / (uint64_t)kModuli[l]);
+    a.pinv[l] = 1.0f / (float)kModuli[l];
   }
 }
 
@@ -1362,9 +1417,12 @@ int launch_mod_gemm(int64_t m, int64_t n, int64_t k, int nmod_ws, int bits, ModA
     const char* gm_env = getenv("GBD_EMU_GROUP_M");
     const int gm_set = gm_env ? atoi(gm_env) : 0;
     a.group_m = gm_set > 0 ? (gm_set < a.tiles_m ? gm_set : a.tiles_m) : group_rows((int)pairs, k2BM, k2BN, a.tiles_m);
-    e = cudaFuncSetAttribute(k_mod_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
+    // one exact FP32 chunk per modulus (k <= 1024): its own instance, so that the int32 path of
+    // deeper products keeps its registers
+    auto kern = a.nkb <= kChunkBlocks ? k_mod_gemm_pair<false, 1> : k_mod_gemm_pair<false, 0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(modular gemm pair)");
-    k_mod_gemm_pair<false><<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB);
+    kern<<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, stream>>>(a, tmA, tmB, nullptr, 0, nullptr);
   } else {
     const int grid = (int)(tiles < cta_cap ? tiles : cta_cap);
     a.group_m = group_rows(grid, kBM, kBN, a.tiles_m);
@@ -1803,9 +1861,9 @@ int mod_grouped_run(const ModGrouped& g, int sms, cudaStream_t s) {
     const int64_t pairs_avail = sms / 2 > 0 ? sms / 2 : 1;
     const int64_t units = (int64_t)g.pair_tiles * kMaxModuli;  // at most; the plans' largest count bounds them
     const int64_t pairs = units < pairs_avail ? units : pairs_avail;
-    e = cudaFuncSetAttribute(k_mod_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
+    e = cudaFuncSetAttribute(k_mod_gemm_pair<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem2::kAlloc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped modular gemm pair)");
-    k_mod_gemm_pair<true><<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, s>>>(a, dummy, dummy, g.table_dev,
+    k_mod_gemm_pair<true, 2><<<(unsigned)(2 * pairs), k2Threads, Smem2::kAlloc, s>>>(a, dummy, dummy, g.table_dev,
                                                                                   g.pair_count, g.flags_dev + 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "grouped modular gemm pair launch");
   }
