@@ -48,8 +48,8 @@ def workload_name():
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram bytes (read + write) of the product launch of one 8192^3 call (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu pass at full size; the modular entry is the mean of two launches,
-# 12.93 + 1.10 and 13.51 + 1.10 GB), None until captured for the current kernels
-TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 14.32e9}
+# 15.00 + 1.10 and 16.03 + 1.10 GB), None until captured for the current kernels
+TRAFFIC_PER_LAUNCH = {"native": None, "emu": 79.827e9, "mod": 16.62e9}
 
 
 def load_peaks():

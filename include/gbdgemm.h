@@ -339,7 +339,9 @@ typedef struct gbd_problem {
   int32_t slices;  /* emulated: 1..9, or 0 = certified automatically when the plan is created;
                       modular: integer bits 1..62, or 0 = certified on the device by every run */
   int32_t tile;    /* native: CTA tile edge 32 or 64; emulated: 128 (one-SM kernel) or 256 (two-SM
-                      kernel); modular: 128; 0 = library default (the autotuner's hook) */
+                      kernel); modular: 128 (one-SM kernel), or 0: 256 x 256 tiles on CTA pairs
+                      when m, n and k are all at least 256, else the one-SM kernel; 0 = library
+                      default (the autotuner's hook) */
   int64_t m, n, k;
   double alpha, beta;
   const double* A;

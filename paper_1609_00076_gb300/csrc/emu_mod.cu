@@ -1739,7 +1739,10 @@ size_t mod_grouped_layout(const gbd_problem* probs, const int* which, int count,
   std::vector<int> order(count);
   for (int q = 0; q < count; ++q) order[q] = q;
   const bool pairs_on = mod_grouped_pairs_enabled();
-  auto on_pair = [&](int q) { return pairs_on && mod_grouped_pair_problem(probs[which[q]]); };
+  auto on_pair = [&](int q) {
+    const gbd_problem& p = probs[which[q]];
+    return pairs_on && p.tile != 128 && mod_grouped_pair_problem(p);  // tile 128: single SMs only
+  };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     const bool px = on_pair(x), py = on_pair(y);
     if (px != py) return px;
