@@ -15,7 +15,11 @@
    (byte d of V_l) < 2^20, per 32-bit limb k A_k = S_4k + 2^8 S_4k+1 and B_k = S_4k+2 + 2^8 S_4k+3
    (below 2^29), limb k = A_k + (B_k-1 >> 16) (below 2^30) plus (B_k << 16 mod 2^32) plus the
    carry of limb k - 1 (at most one); the representative of (-M/2, M/2] must come out for every C'.
-3. Triangle tiles (DSYRK's triangular product).  Tile t of a triangle of T x T tiles is
+3. The reduction of one exact FP32 chunk (the product epilogue when k <= 1024).  A chunk sum v is
+   an integer with |v| <= 2^24; q = rint(v fl(1/p)) comes from one fma against 1.5 2^23 (round to
+   nearest even at unit spacing while the sum stays in [2^23, 2^24)), r = v - p q from one exact
+   fma, and p is added to a negative r: the result must be v mod p in [0, p) for every v.
+4. Triangle tiles (DSYRK's triangular product).  Tile t of a triangle of T x T tiles is
    (r, c) with t = r (r + 1) / 2 + c, found from an FP32 square-root estimate corrected by
    integer steps; every tile that meets the triangle comes out exactly once.
 """
@@ -130,6 +134,27 @@ def test_reconstruction_at_the_largest_residues(n):
     cp = cp - M if cp > M // 2 else cp
     got, mod = _crt_kernel(r, n, M, V, e)
     assert got == cp % mod
+
+
+@pytest.mark.parametrize("p", MODULI)
+def test_single_chunk_reduction_for_every_chunk_sum(p):
+    N, E = _f32_recip(p)
+    magic = 3 * 2 ** 22  # 1.5 2^23
+    step = 1 << 22
+    for lo in range(-(1 << 24), (1 << 24) + 1, step):
+        v = np.arange(lo, min(lo + step, (1 << 24) + 1), dtype=np.int64)
+        prod = v * N  # v fl(1/p) = prod / 2^E exactly (|prod| < 2^48)
+        q = prod >> E  # floor
+        rem = prod - (q << E)
+        half = 1 << (E - 1)
+        q = q + ((rem > half) | ((rem == half) & ((q & 1) == 1)))  # round to nearest, ties to even
+        # the fma's sum v fl(1/p) + 1.5 2^23 stays where FP32 numbers are the integers
+        assert int((prod >> E).min()) + magic >= 2 ** 23 and int((prod >> E).max()) + 1 + magic < 2 ** 24
+        r = v - p * q  # exact: an integer below 2^8 in magnitude
+        assert int(np.abs(r).max()) < p
+        out = r + p * (r < 0)
+        assert int(out.min()) >= 0 and int(out.max()) < p
+        assert np.array_equal(out, v % p)
 
 
 def _tri_tile(t: int) -> tuple[int, int]:
