@@ -237,7 +237,7 @@ def test_auto_large_square_sampled_rows(oracle_mod, e):
     assert rc == 0, gbdgemm.gbd_last_error()
     torch.cuda.synchronize()
     assert gbdgemm.gbd_check_device_error() == 0
-    rows = sorted(set(int(x) for x in synth.splitmix64(synth.seed_for(2, e) + 7, 8) % m))
+    rows = sorted(set([0, m - 1] + [int(x) for x in synth.splitmix64(synth.seed_for(2, e) + 7, 24) % m]))
     got = dC.view(n, m)[:, rows].t().cpu().numpy().flatten(order="F")
     ref = oracle_mod.dgemm_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, rows=rows)
     G = oracle_mod.abs_bound_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, rows=rows)

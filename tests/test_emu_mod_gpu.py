@@ -170,7 +170,8 @@ def test_auto_large_square_sampled_rows(oracle_mod):
     torch.cuda.synchronize()
     assert gbdgemm.gbd_check_device_error() == 0
     out = dC.cpu().numpy()
-    rows = [int(r) for r in synth.splitmix64(9002, 24) % m]
+    # 96 seeded rows and the first and last ones, each against the Dot2 oracle's bound
+    rows = sorted(set([0, m - 1] + [int(r) for r in synth.splitmix64(9002, 96) % m]))
     ref = oracle_mod.dgemm_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, rows=rows)
     G = oracle_mod.abs_bound_rows("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, None, m, rows=rows)
     got = out.reshape(n, m)[:, rows].flatten()
