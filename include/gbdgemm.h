@@ -389,8 +389,10 @@ GBD_API int gbd_grouped_plan_create(const gbd_problem* probs, int count, void* w
  * Runs a plan on `stream`: for emulated problems their exponent and split kernels
  * and one persistent slice-product launch per slice count over all their tiles; for
  * modular problems their batched preparation, the certification product (FP8), one
- * plan per problem, the residues, and one persistent launch of the modular products
- * over all their tiles; then one persistent FP64-MMA launch for native problems,
+ * plan per problem, the residues, the modular products in two persistent launches (the
+ * problems with m, n, k >= 256 as (256 x 256 tile, modulus) units on CTA pairs, the
+ * others' 128 x 128 tiles on single SMs) and the reconstruction of C; then one
+ * persistent FP64-MMA launch for native problems,
  * every quick return, and each modular problem whose plan found the target out of the
  * reach of 16 moduli (its tiles in that launch test the plan on the device).  Only
  * kernel launches and memsets are issued, so the call may be captured in a CUDA graph
