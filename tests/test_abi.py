@@ -227,3 +227,17 @@ def test_context_creation_reports_a_missing_device(lib):
         pytest.skip("a GPU is present: creation is tested with the GPU tests")
     rc, ctx = gbdgemm.gbd_create(0)
     assert rc in (gbdgemm.GBD_ERR_CUDA, gbdgemm.GBD_ERR_DEVICE) and not ctx.value
+
+
+def test_serving_memory_accounting_without_gpu(lib):
+    # a request holds its stored operands, C and (emulated) the modular workspace, plus slack
+    from paper_1609_00076_gb300 import serving
+    nat = serving.Request(0, 0.0, 300, 200, 100, "T", "N", serving.NATIVE)
+    assert serving.Server.bytes_needed(nat) == 8 * (100 * 300 + 100 * 200 + 300 * 200) + 1024
+    emu = serving.Request(1, 0.0, 300, 200, 100, "N", "T", serving.EMULATED)
+    ws = gbdgemm.gbd_dgemm_emu_mod_workspace_size(300, 200, 100, 0)
+    assert ws > 0
+    assert serving.Server.bytes_needed(emu) == 8 * (300 * 100 + 200 * 100 + 300 * 200) + ws + 1024
+    # a 4096^3 emulated request, the stream's largest, fits the 40 GB budget many times over
+    big = serving.Request(2, 0.0, 4096, 4096, 4096, "N", "N", serving.EMULATED)
+    assert 40e9 / serving.Server.bytes_needed(big) > 10
