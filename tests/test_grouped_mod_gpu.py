@@ -25,8 +25,8 @@ _MODES = {"native": gbdgemm.GBD_MODE_NATIVE, "emu": gbdgemm.GBD_MODE_EMULATED, "
 
 
 def descriptors(probs, tol=0.0):
-    return [dict(transa=p["ta"], transb=p["tb"], mode=_MODES[p["mode"]], slices=p["slices"], tile=0, m=p["m"],
-                 n=p["n"], k=p["k"], alpha=p["alpha"], beta=p["beta"], A=p["dA"], lda=p["lda"], B=p["dB"],
+    return [dict(transa=p["ta"], transb=p["tb"], mode=_MODES[p["mode"]], slices=p["slices"],
+                 tile=p.get("tile", 0), m=p["m"], n=p["n"], k=p["k"], alpha=p["alpha"], beta=p["beta"], A=p["dA"], lda=p["lda"], B=p["dB"],
                  ldb=p["ldb"], C=p["dC"], ldc=p["ldc"], tol=tol) for p in probs]
 
 
@@ -90,10 +90,11 @@ def test_modular_batch_matches_single_calls(oracle_mod):
         assert first_mismatch(got, ref, 2 * k * U * G, m) is None
 
 
-@pytest.mark.parametrize("kernel", ["default", "single"])
+@pytest.mark.parametrize("kernel", ["default", "single", "tile128"])
 def test_large_problems_on_cta_pairs_match_single_calls(oracle_mod, monkeypatch, kernel):
     # problems with m, n, k >= 256 run their (256 x 256 tile, modulus) units on CTA pairs, the
-    # others on single SMs (GBD_EMU_KERNEL=single: all on single SMs); ragged sizes, a problem with
+    # others on single SMs (GBD_EMU_KERNEL=single, or tile 128 in the problem: all on single SMs,
+    # the tile field naming the kernel of one problem); ragged sizes, a problem with
     # fixed bits (fewer moduli than the launch's largest count: its later units are skipped), one
     # with a target no bit count certifies (its units are skipped, its FP64 fallback runs) and a
     # quick return among them
@@ -101,6 +102,9 @@ def test_large_problems_on_cta_pairs_match_single_calls(oracle_mod, monkeypatch,
         monkeypatch.setenv("GBD_EMU_KERNEL", "single")
     probs = make_batch(61, 16, 160, 1400, modes=("mod",), slices=(0,), kinds=("uniform", "scaled"),
                        alpha_beta=(1.5, -0.5))
+    if kernel == "tile128":
+        for p in probs[::2]:
+            p["tile"] = 128
     big = [i for i, p in enumerate(probs) if min(p["m"], p["n"], p["k"]) >= 256]
     assert len(big) >= 4 and len(big) < len(probs)
     probs[big[0]]["slices"] = 20  # fixed bits: few moduli
