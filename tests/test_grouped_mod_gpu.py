@@ -26,8 +26,9 @@ _MODES = {"native": gbdgemm.GBD_MODE_NATIVE, "emu": gbdgemm.GBD_MODE_EMULATED, "
 
 def descriptors(probs, tol=0.0):
     return [dict(transa=p["ta"], transb=p["tb"], mode=_MODES[p["mode"]], slices=p["slices"],
-                 tile=p.get("tile", 0), m=p["m"], n=p["n"], k=p["k"], alpha=p["alpha"], beta=p["beta"], A=p["dA"], lda=p["lda"], B=p["dB"],
-                 ldb=p["ldb"], C=p["dC"], ldc=p["ldc"], tol=tol) for p in probs]
+                 tile=p.get("tile", 0), m=p["m"], n=p["n"], k=p["k"], alpha=p["alpha"], beta=p["beta"],
+                 A=p["dA"], lda=p["lda"], B=p["dB"], ldb=p["ldb"], C=p["dC"], ldc=p["ldc"], tol=tol)
+            for p in probs]
 
 
 def run_grouped(probs, tol=0.0):
